@@ -1,0 +1,245 @@
+"""CPU oracle of the compressed-patch time step (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg import
+this package.  The library under paper_2302_09883_gb300/ never does.
+
+The arithmetic lives in plain C++ (oracle/*.hpp), FP64, with an FP32
+instantiation of the same source for decisions the GPU takes in FP32.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import build_oracle
+
+SCHEME = {"d2q9": 0, "d3q19": 1, "euler2d": 2}
+WAVELET = {"bl53": 0, "haar": 1}
+STORE = {"f64": 0, "f32": 1, "bf16": 2, "i8": 3}
+RULE = {"const": 0, "accum": 1, "capped": 2}
+PREC = {"f64": 0, "f32": 1}
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_oracle()
+        L = C.CDLL(path)
+        vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+        dp = C.POINTER(C.c_double)
+        L.orc_create.restype = vp
+        L.orc_create.argtypes = [i32, i32, i32, i32, i32, i64, i64, i32, i32, i32, dbl, dbl, dbl, dbl]
+        L.orc_destroy.argtypes = [vp]
+        L.orc_init_macro.argtypes = [vp, dp, dp, dp, dp]
+        L.orc_step.argtypes = [vp, i64]
+        L.orc_export_field.argtypes = [vp, i32, dp]
+        L.orc_export_all.argtypes = [vp, dp]
+        L.orc_npatch.restype = i64
+        L.orc_npatch.argtypes = [vp]
+        L.orc_record_bytes.restype = i64
+        L.orc_record_bytes.argtypes = [vp, i64]
+        L.orc_record.argtypes = [vp, i64, C.c_char_p, i64]
+        L.orc_stats.argtypes = [vp, dp]
+        L.orc_ref_create.restype = vp
+        L.orc_ref_create.argtypes = [i32, i32, i32, i64, i64, i32, dbl, dbl, dbl]
+        L.orc_ref_init_macro.argtypes = [vp, dp, dp, dp, dp]
+        L.orc_ref_step.argtypes = [vp, i64]
+        L.orc_ref_export_field.argtypes = [vp, i32, dp]
+        L.orc_ref_time.restype = dbl
+        L.orc_ref_time.argtypes = [vp]
+        L.orc_dwt.argtypes = [i32, i32, i64, i32, i32, i32, dp]
+        L.orc_layout.argtypes = [i32, i32, i64, i32, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_uint8), C.POINTER(C.c_int64)]
+        L.orc_band_factor.restype = dbl
+        L.orc_band_factor.argtypes = [i32, i32, i64, i32, i32, i32]
+        L.orc_encode.restype = i64
+        L.orc_encode.argtypes = [i32, i32, i64, i32, i32, i32, i32, dbl, i32, dp, C.c_char_p, i64]
+        L.orc_decode.argtypes = [i32, i32, i64, i32, i32, i32, C.c_char_p, i64, dp]
+        L.orc_bf16.argtypes = [C.POINTER(C.c_float), C.POINTER(C.c_uint16), i64]
+        L.orc_d2q9_equilibrium.argtypes = [i32, dbl, dbl, dbl, dp]
+        L.orc_d2q9_collide.argtypes = [i32, dp, dbl]
+        L.orc_rusanov.argtypes = [dp, dp, i32, i32, dbl, dp]
+        L.orc_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise RuntimeError("oracle: " + lib().orc_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _macro_ptrs(fields):
+    arrs = [np.ascontiguousarray(f, dtype=np.float64) for f in fields]
+    while len(arrs) < 4:
+        arrs.append(arrs[0])
+    return arrs, [_dp(a) for a in arrs[:4]]
+
+
+def nfields(scheme):
+    return {"d2q9": 9, "d3q19": 19, "euler2d": 4}[scheme]
+
+
+class OracleSim:
+    """Compressed-patch run (2-D).  Global arrays are (ny_nodes, nx_nodes)."""
+
+    def __init__(self, scheme, wavelet, nx, ny, P, L, eps, prec="f64", store="f64", rule="const",
+                 periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4):
+        self.scheme, self.wavelet, self.prec = scheme, wavelet, prec
+        self.P, self.L = P, L
+        pmask = int(periodic[0]) | (int(periodic[1]) << 1)
+        self.G = [n + 1 if (wavelet == "bl53" and not per) else n for n, per in zip((nx, ny), periodic)]
+        self.F = nfields(scheme)
+        self.h = lib().orc_create(SCHEME[scheme], WAVELET[wavelet], PREC[prec], STORE[store], RULE[rule],
+                                  nx, ny, pmask, P, L, eps, tau, cfl, gamma)
+        if not self.h:
+            raise RuntimeError("oracle: " + lib().orc_last_error().decode())
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_destroy(self.h)
+            self.h = None
+
+    def init_macro(self, fields):
+        arrs, ptrs = _macro_ptrs(fields)
+        _check(lib().orc_init_macro(self.h, *ptrs))
+
+    def step(self, n=1):
+        _check(lib().orc_step(self.h, n))
+
+    def export_field(self, f):
+        out = np.empty((self.G[1], self.G[0]), np.float64)
+        _check(lib().orc_export_field(self.h, f, _dp(out)))
+        return out
+
+    def export_all(self):
+        out = np.empty((self.F, self.G[1], self.G[0]), np.float64)
+        _check(lib().orc_export_all(self.h, _dp(out)))
+        return out
+
+    @property
+    def npatch(self):
+        return lib().orc_npatch(self.h)
+
+    def record(self, p):
+        n = lib().orc_record_bytes(self.h, p)
+        buf = C.create_string_buffer(n)
+        _check(lib().orc_record(self.h, p, buf, n))
+        return buf.raw[:n]
+
+    def stats(self):
+        out = np.zeros(32, np.float64)
+        _check(lib().orc_stats(self.h, _dp(out)))
+        return {"coef_sums": out[:self.F].copy(), "nstep": int(out[20]), "time": out[21],
+                "shared_mismatch": int(out[22]), "compressed_bytes": int(out[23])}
+
+
+class OracleRef:
+    """Uncompressed run of the same scheme on the global arrays."""
+
+    def __init__(self, scheme, wavelet, nx, ny, prec="f64", periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4):
+        pmask = int(periodic[0]) | (int(periodic[1]) << 1)
+        self.G = [n + 1 if (wavelet == "bl53" and not per) else n for n, per in zip((nx, ny), periodic)]
+        self.F = nfields(scheme)
+        self.h = lib().orc_ref_create(SCHEME[scheme], WAVELET[wavelet], PREC[prec], nx, ny, pmask, tau, cfl, gamma)
+        if not self.h:
+            raise RuntimeError("oracle: " + lib().orc_last_error().decode())
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_destroy(self.h)
+            self.h = None
+
+    def init_macro(self, fields):
+        arrs, ptrs = _macro_ptrs(fields)
+        _check(lib().orc_ref_init_macro(self.h, *ptrs))
+
+    def step(self, n=1):
+        _check(lib().orc_ref_step(self.h, n))
+
+    def export_field(self, f):
+        out = np.empty((self.G[1], self.G[0]), np.float64)
+        _check(lib().orc_ref_export_field(self.h, f, _dp(out)))
+        return out
+
+    @property
+    def time(self):
+        return lib().orc_ref_time(self.h)
+
+
+def dwt(u, wavelet, P, L, inverse=False, prec="f64"):
+    """Tensor lifting transform of a d-D block (returns a new array)."""
+    a = np.ascontiguousarray(u, dtype=np.float64).copy()
+    _check(lib().orc_dwt(WAVELET[wavelet], a.ndim, P, L, int(inverse), PREC[prec], _dp(a)))
+    return a
+
+
+def layout(wavelet, dims, P, L):
+    sizes = np.zeros(5, np.int64)
+    _check(lib().orc_layout(WAVELET[wavelet], dims, P, L, None, None, None,
+                            sizes.ctypes.data_as(C.POINTER(C.c_int64))))
+    n = int(sizes[0])
+    pos = np.zeros(n, np.int64)
+    band = np.zeros(n, np.int32)
+    edge = np.zeros(n, np.uint8)
+    _check(lib().orc_layout(WAVELET[wavelet], dims, P, L, pos.ctypes.data_as(C.POINTER(C.c_int64)),
+                            band.ctypes.data_as(C.POINTER(C.c_int32)), edge.ctypes.data_as(C.POINTER(C.c_uint8)),
+                            sizes.ctypes.data_as(C.POINTER(C.c_int64))))
+    return {"canon_pos": pos, "band": band, "edge": edge.astype(bool), "n_all": n, "n_c": int(sizes[1]),
+            "n_d": int(sizes[2]), "n_w": int(sizes[3]), "nb": int(sizes[4])}
+
+
+def band_factor(wavelet, dims, P, L, band, rule):
+    return lib().orc_band_factor(WAVELET[wavelet], dims, P, L, band, RULE[rule])
+
+
+def encode(coef, wavelet, P, L, eps, prec="f64", store="f64", rule="const"):
+    """coef: (F, E, E[, E]) transformed coefficients in place.  Returns bytes."""
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    dims = c.ndim - 1
+    cap = c.size * 8 + 4096 + 64 * c.shape[0]
+    buf = C.create_string_buffer(cap)
+    n = lib().orc_encode(WAVELET[wavelet], dims, P, L, PREC[prec], STORE[store], RULE[rule], eps, c.shape[0],
+                         _dp(c), buf, cap)
+    if n < 0:
+        raise RuntimeError("oracle: " + lib().orc_last_error().decode())
+    return buf.raw[:n]
+
+
+def decode(rec, nfields_, shape, wavelet, P, L, prec="f64", store="f64"):
+    out = np.zeros((nfields_,) + tuple(shape), np.float64)
+    _check(lib().orc_decode(WAVELET[wavelet], len(shape), P, L, PREC[prec], STORE[store], rec, len(rec), _dp(out)))
+    return out
+
+
+def bf16_bits(x):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.zeros(x.shape, np.uint16)
+    lib().orc_bf16(x.ctypes.data_as(C.POINTER(C.c_float)), out.ctypes.data_as(C.POINTER(C.c_uint16)), x.size)
+    return out
+
+
+def d2q9_equilibrium(rho, ux, uy, prec="f64"):
+    out = np.zeros(9, np.float64)
+    lib().orc_d2q9_equilibrium(PREC[prec], rho, ux, uy, _dp(out))
+    return out
+
+
+def d2q9_collide(f, tau, prec="f64"):
+    g = np.ascontiguousarray(f, dtype=np.float64).copy()
+    lib().orc_d2q9_collide(PREC[prec], _dp(g), tau)
+    return g
+
+
+def rusanov(WL, WR, nx, ny, gamma=1.4):
+    a = np.ascontiguousarray(WL, np.float64)
+    b = np.ascontiguousarray(WR, np.float64)
+    out = np.zeros(4, np.float64)
+    lib().orc_rusanov(_dp(a), _dp(b), nx, ny, gamma, _dp(out))
+    return out

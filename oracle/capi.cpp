@@ -1,0 +1,313 @@
+// Oracle C entry points (test infrastructure only: called from tests/,
+// __graft_entry__.smoke() and bench.py's CPU baseline, never from the
+// library).  Plain FP64 (and an FP32 instantiation of the very same source,
+// used to take integer decisions such as threshold masks in the precision the
+// GPU kernel computes in).
+#include <cstdint>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "codec.hpp"
+#include "schemes.hpp"
+#include "sim.hpp"
+#include "wavelet.hpp"
+
+using namespace orc;
+
+namespace {
+thread_local std::string g_err;
+
+struct Handle {
+  int prec = 0;  // 0 = FP64, 1 = FP32
+  std::unique_ptr<Sim<double>> s64;
+  std::unique_ptr<Sim<float>> s32;
+  std::unique_ptr<Ref<double>> r64;
+  std::unique_ptr<Ref<float>> r32;
+};
+
+template <class F> int guard(F&& f) {
+  try {
+    f();
+    return 0;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return -1;
+  }
+}
+
+std::vector<const double*> fields4(const double* a, const double* b, const double* c, const double* d) {
+  return {a, b, c, d};
+}
+
+template <class T> void stats_of(Sim<T>& s, double* out) {
+  // out[0..F-1] coefficient-domain sums; out[20..] diagnostics
+  std::vector<double> cs = s.coef_sums();
+  for (int f = 0; f < s.F; ++f) out[f] = cs[f];
+  out[20] = double(s.nstep);
+  out[21] = s.time;
+  out[22] = double(s.shared_mismatch);
+  out[23] = double(s.compressed_bytes());
+}
+
+template <class T> void export_of(Sim<T>& s, int field, double* dst) {
+  auto U = s.decode_all();
+  if (field < 0 || field >= s.F) throw std::runtime_error("bad field");
+  for (size_t g = 0; g < U[field].size(); ++g) dst[g] = double(U[field][g]);
+}
+
+template <class T> void export_all_of(Sim<T>& s, double* dst) {
+  auto U = s.decode_all();
+  const size_t n = U[0].size();
+  for (int f = 0; f < s.F; ++f)
+    for (size_t g = 0; g < n; ++g) dst[f * n + g] = double(U[f][g]);
+}
+}  // namespace
+
+extern "C" {
+
+const char* orc_last_error() { return g_err.c_str(); }
+
+// prec: 0 FP64, 1 FP32.  scheme: 0 D2Q9, 2 Euler.  wavelet: 0 BL5/3, 1 Haar.
+void* orc_create(int scheme, int wavelet, int prec, int store, int rule, int64_t nx, int64_t ny, int pmask,
+                 int P, int L, double eps, double tau, double cfl, double gamma) {
+  Handle* h = new Handle();
+  h->prec = prec;
+  int rc = guard([&] {
+    if (prec == 0) h->s64.reset(new Sim<double>(scheme, wavelet, store, rule, nx, ny, pmask, P, L, eps, tau, cfl, gamma));
+    else h->s32.reset(new Sim<float>(scheme, wavelet, store, rule, nx, ny, pmask, P, L, eps, tau, cfl, gamma));
+  });
+  if (rc) { delete h; return nullptr; }
+  return h;
+}
+
+void orc_destroy(void* p) { delete static_cast<Handle*>(p); }
+
+int orc_init_macro(void* p, const double* a, const double* b, const double* c, const double* d) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    if (h->s64) h->s64->init_macro(fields4(a, b, c, d));
+    else h->s32->init_macro(fields4(a, b, c, d));
+  });
+}
+
+int orc_step(void* p, int64_t n) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    for (int64_t i = 0; i < n; ++i) {
+      if (h->s64) h->s64->step();
+      else h->s32->step();
+    }
+  });
+}
+
+int orc_export_field(void* p, int field, double* dst) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    if (h->s64) export_of(*h->s64, field, dst);
+    else export_of(*h->s32, field, dst);
+  });
+}
+
+int orc_export_all(void* p, double* dst) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    if (h->s64) export_all_of(*h->s64, dst);
+    else export_all_of(*h->s32, dst);
+  });
+}
+
+int64_t orc_npatch(void* p) {
+  Handle* h = static_cast<Handle*>(p);
+  return h->s64 ? h->s64->npatch() : h->s32->npatch();
+}
+
+int64_t orc_record_bytes(void* p, int64_t patch) {
+  Handle* h = static_cast<Handle*>(p);
+  const auto& rec = h->s64 ? h->s64->rec : h->s32->rec;
+  if (patch < 0 || patch >= int64_t(rec.size())) return -1;
+  return int64_t(rec[patch].size());
+}
+
+int orc_record(void* p, int64_t patch, uint8_t* dst, int64_t cap) {
+  Handle* h = static_cast<Handle*>(p);
+  const auto& rec = h->s64 ? h->s64->rec : h->s32->rec;
+  if (patch < 0 || patch >= int64_t(rec.size()) || int64_t(rec[patch].size()) > cap) {
+    g_err = "bad patch or buffer too small";
+    return -1;
+  }
+  std::memcpy(dst, rec[patch].data(), rec[patch].size());
+  return 0;
+}
+
+int orc_stats(void* p, double* out) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    if (h->s64) stats_of(*h->s64, out);
+    else stats_of(*h->s32, out);
+  });
+}
+
+// ------------------------------------------------------------- reference
+void* orc_ref_create(int scheme, int wavelet, int prec, int64_t nx, int64_t ny, int pmask, double tau, double cfl,
+                     double gamma) {
+  Handle* h = new Handle();
+  h->prec = prec;
+  int rc = guard([&] {
+    if (prec == 0) h->r64.reset(new Ref<double>(scheme, wavelet, nx, ny, pmask, tau, cfl, gamma));
+    else h->r32.reset(new Ref<float>(scheme, wavelet, nx, ny, pmask, tau, cfl, gamma));
+  });
+  if (rc) { delete h; return nullptr; }
+  return h;
+}
+
+int orc_ref_init_macro(void* p, const double* a, const double* b, const double* c, const double* d) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    if (h->r64) h->r64->init_macro(fields4(a, b, c, d));
+    else h->r32->init_macro(fields4(a, b, c, d));
+  });
+}
+
+int orc_ref_step(void* p, int64_t n) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    for (int64_t i = 0; i < n; ++i) {
+      if (h->r64) h->r64->step();
+      else h->r32->step();
+    }
+  });
+}
+
+int orc_ref_export_field(void* p, int field, double* dst) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    if (h->r64) {
+      const auto& u = h->r64->U.at(field);
+      for (size_t g = 0; g < u.size(); ++g) dst[g] = u[g];
+    } else {
+      const auto& u = h->r32->U.at(field);
+      for (size_t g = 0; g < u.size(); ++g) dst[g] = double(u[g]);
+    }
+  });
+}
+
+double orc_ref_time(void* p) {
+  Handle* h = static_cast<Handle*>(p);
+  return h->r64 ? h->r64->time : h->r32->time;
+}
+
+// ----------------------------------------------------------- pure helpers
+// In-place tensor transform of a dims-D block (FP64 arithmetic, or FP32 when
+// prec = 1, values passed as doubles).
+int orc_dwt(int wavelet, int dims, int64_t P, int L, int inverse, int prec, double* u) {
+  return guard([&] {
+    const int64_t E = wavelet == BL53 ? P + 1 : P;
+    int64_t n = 1;
+    for (int a = 0; a < dims; ++a) n *= E;
+    if (prec == 0) {
+      if (inverse) inv_nd<double>(wavelet, u, dims, P, L);
+      else fwd_nd<double>(wavelet, u, dims, P, L);
+    } else {
+      std::vector<float> v(u, u + n);
+      if (inverse) inv_nd<float>(wavelet, v.data(), dims, P, L);
+      else fwd_nd<float>(wavelet, v.data(), dims, P, L);
+      for (int64_t i = 0; i < n; ++i) u[i] = v[i];
+    }
+  });
+}
+
+// Canonical layout: canon_pos[n_all], band[n_all], edge[n_all]; sizes[0..4]
+// = n_all, n_c, n_d, n_w, nb.
+int orc_layout(int wavelet, int dims, int64_t P, int L, int64_t* canon_pos, int32_t* band, uint8_t* edge,
+               int64_t* sizes) {
+  return guard([&] {
+    Layout lay(wavelet, dims, P, L);
+    sizes[0] = lay.n_all; sizes[1] = lay.n_c; sizes[2] = lay.n_d; sizes[3] = lay.n_w; sizes[4] = lay.nb;
+    if (canon_pos)
+      for (int64_t i = 0; i < lay.n_all; ++i) { canon_pos[i] = lay.canon_pos[i]; band[i] = lay.canon_band[i]; edge[i] = lay.canon_edge[i]; }
+  });
+}
+
+double orc_band_factor(int wavelet, int dims, int64_t P, int L, int band, int rule) {
+  Layout lay(wavelet, dims, P, L);
+  return band_factor(lay, band, rule);
+}
+
+// Encode nfields blocks of transformed coefficients (in-place order, given as
+// doubles, converted to the compute type first).  Returns the byte count.
+int64_t orc_encode(int wavelet, int dims, int64_t P, int L, int prec, int store, int rule, double eps, int nfields,
+                   const double* coef, uint8_t* out, int64_t cap) {
+  int64_t nbytes = -1;
+  int rc = guard([&] {
+    Layout lay(wavelet, dims, P, L);
+    std::vector<uint8_t> r;
+    std::vector<double> ef(nfields, eps);
+    const uint32_t flags = uint32_t(store) | (uint32_t(wavelet) << 8) | (prec == 0 ? (1u << 16) : 0u);
+    if (prec == 0) {
+      std::vector<std::vector<double>> c(nfields, std::vector<double>(lay.n_all));
+      for (int f = 0; f < nfields; ++f)
+        for (int64_t i = 0; i < lay.n_all; ++i) c[f][i] = coef[f * lay.n_all + i];
+      r = encode_patch<double>(lay, c, store, rule, ef, eps, 0, flags);
+    } else {
+      std::vector<std::vector<float>> c(nfields, std::vector<float>(lay.n_all));
+      for (int f = 0; f < nfields; ++f)
+        for (int64_t i = 0; i < lay.n_all; ++i) c[f][i] = float(coef[f * lay.n_all + i]);
+      r = encode_patch<float>(lay, c, store, rule, ef, eps, 0, flags);
+    }
+    if (int64_t(r.size()) > cap) throw std::runtime_error("output buffer too small");
+    std::memcpy(out, r.data(), r.size());
+    nbytes = int64_t(r.size());
+  });
+  return rc ? -1 : nbytes;
+}
+
+int orc_decode(int wavelet, int dims, int64_t P, int L, int prec, int store, const uint8_t* rec, int64_t nbytes,
+               double* coef) {
+  return guard([&] {
+    Layout lay(wavelet, dims, P, L);
+    if (prec == 0) {
+      auto c = decode_patch<double>(lay, rec, nbytes, store);
+      for (size_t f = 0; f < c.size(); ++f)
+        for (int64_t i = 0; i < lay.n_all; ++i) coef[f * lay.n_all + i] = c[f][i];
+    } else {
+      auto c = decode_patch<float>(lay, rec, nbytes, store);
+      for (size_t f = 0; f < c.size(); ++f)
+        for (int64_t i = 0; i < lay.n_all; ++i) coef[f * lay.n_all + i] = c[f][i];
+    }
+  });
+}
+
+int orc_bf16(const float* x, uint16_t* out, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) out[i] = bf16_rne(x[i]);
+  return 0;
+}
+
+int orc_d2q9_equilibrium(int prec, double rho, double ux, double uy, double* out) {
+  if (prec == 0) d2q9_equilibrium<double>(rho, ux, uy, out);
+  else {
+    float f[9];
+    d2q9_equilibrium<float>(float(rho), float(ux), float(uy), f);
+    for (int i = 0; i < 9; ++i) out[i] = f[i];
+  }
+  return 0;
+}
+
+int orc_d2q9_collide(int prec, double* f, double tau) {
+  if (prec == 0) d2q9_collide<double>(f, 1.0 / tau);
+  else {
+    float g[9];
+    for (int i = 0; i < 9; ++i) g[i] = float(f[i]);
+    d2q9_collide<float>(g, float(1.0 / tau));
+    for (int i = 0; i < 9; ++i) f[i] = g[i];
+  }
+  return 0;
+}
+
+int orc_rusanov(const double* WL, const double* WR, int nx, int ny, double gamma, double* F) {
+  rusanov<double>(WL, WR, double(nx), double(ny), gamma - 1.0, gamma, F);
+  return 0;
+}
+
+}  // extern "C"

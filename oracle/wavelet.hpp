@@ -1,0 +1,142 @@
+// Oracle (test infrastructure only: the CUDA library never includes, links or
+// calls anything under oracle/).
+//
+// Plain, slow lifting transforms written from the paper's definitions.
+//
+//  * Folded BL5/3 lifting on 2^j+1 nodes (Sec. 2.1.2): boundary samples are
+//    kept (eq. boundary_values); predict d_k = s_{2k+1} - (s_{2k}+s_{2k+2})/2;
+//    update s'_k = s_{2k} + a_{k-1} d_{k-1} + a_k d_k for 0<k<K with
+//    a = 1/2 at the two end details and 1/4 inside (the alpha equation, which
+//    is the unique choice giving the trapezoid conservation of eq.
+//    conservation).  Repeated L times ("compression level").
+//  * Haar (not in the paper; textbook unnormalised average/difference
+//    lifting on 2^j cells): d = b - a, s = a + d/2.
+//  * N-D: the 1-D transform is applied along x for every line, then along y,
+//    then z (Sec. 2.1.2, last paragraphs: "first all the rows and then all
+//    the columns").  This tensor reading is the one that reproduces the
+//    paper's 481 non-null coefficients of the 129x129 example.
+//
+// Coefficients stay at their node positions ("in place"): after L levels the
+// samples sit at positions multiple of 2^L and the level-m detail (m = 1 the
+// finest) at positions congruent to 2^(m-1) mod 2^m.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace orc {
+
+enum Wavelet { BL53 = 0, HAAR = 1 };
+
+// Class of in-place position k along one axis after L levels: 0 = coarse
+// sample, m in 1..L = detail of level m (1 = finest).
+inline int pos_class(int64_t k, int L) {
+  if (k % (int64_t(1) << L) == 0) return 0;
+  int m = 1;
+  while (((k >> (m - 1)) & 1) == 0) ++m;
+  return m;
+}
+// Index of position k inside its class.
+inline int64_t pos_index(int64_t k, int c, int L) { return c == 0 ? (k >> L) : (k >> c); }
+// Inverse of (pos_class, pos_index).
+inline int64_t class_pos(int c, int64_t i, int L) {
+  return c == 0 ? (i << L) : ((2 * i + 1) << (c - 1));
+}
+// Number of positions of class c on an axis of P cells (P+1 nodes for BL5/3).
+inline int64_t class_size(int wavelet, int64_t P, int c, int L) {
+  if (c == 0) return wavelet == BL53 ? (P >> L) + 1 : (P >> L);
+  return P >> c;
+}
+
+// alpha of the BL5/3 update (Sec. 2.1.2, alpha equation), K details.
+template <class T> inline T bl53_alpha(int64_t k, int64_t K) {
+  return (k == 0 || k == K - 1) ? T(0.5) : T(0.25);
+}
+
+// One axis, in place.  u[i*stride] for i in [0, n] (BL5/3, n = P) or
+// [0, n) (Haar, n = P).
+template <class T> void fwd1(int wavelet, T* u, int64_t stride, int64_t P, int L) {
+  for (int lev = 1; lev <= L; ++lev) {
+    const int64_t st = int64_t(1) << (lev - 1);
+    auto at = [&](int64_t k) -> T& { return u[k * st * stride]; };
+    if (wavelet == BL53) {
+      const int64_t K = (P / st) / 2;  // details at this level
+      std::vector<T> d(K);
+      for (int64_t k = 0; k < K; ++k) {
+        d[k] = at(2 * k + 1) - T(0.5) * (at(2 * k) + at(2 * k + 2));
+        at(2 * k + 1) = d[k];
+      }
+      for (int64_t k = 1; k < K; ++k) {
+        T e = at(2 * k);
+        e = e + bl53_alpha<T>(k - 1, K) * d[k - 1];
+        e = e + bl53_alpha<T>(k, K) * d[k];
+        at(2 * k) = e;
+      }
+    } else {
+      const int64_t K = (P / st) / 2;  // pairs
+      for (int64_t k = 0; k < K; ++k) {
+        const T a = at(2 * k), b = at(2 * k + 1);
+        const T d = b - a;
+        at(2 * k) = a + T(0.5) * d;
+        at(2 * k + 1) = d;
+      }
+    }
+  }
+}
+
+template <class T> void inv1(int wavelet, T* u, int64_t stride, int64_t P, int L) {
+  for (int lev = L; lev >= 1; --lev) {
+    const int64_t st = int64_t(1) << (lev - 1);
+    auto at = [&](int64_t k) -> T& { return u[k * st * stride]; };
+    if (wavelet == BL53) {
+      const int64_t K = (P / st) / 2;
+      for (int64_t k = 1; k < K; ++k) {
+        T e = at(2 * k);
+        e = e - bl53_alpha<T>(k - 1, K) * at(2 * k - 1);
+        e = e - bl53_alpha<T>(k, K) * at(2 * k + 1);
+        at(2 * k) = e;
+      }
+      for (int64_t k = 0; k < K; ++k)
+        at(2 * k + 1) = at(2 * k + 1) + T(0.5) * (at(2 * k) + at(2 * k + 2));
+    } else {
+      const int64_t K = (P / st) / 2;
+      for (int64_t k = 0; k < K; ++k) {
+        const T s = at(2 * k), d = at(2 * k + 1);
+        const T a = s - T(0.5) * d;
+        at(2 * k) = a;
+        at(2 * k + 1) = a + d;
+      }
+    }
+  }
+}
+
+// Tensor transform of a dims-dimensional block with E points per axis
+// (E = P+1 for BL5/3, P for Haar), x fastest.
+template <class T> void fwd_nd(int wavelet, T* u, int dims, int64_t P, int L) {
+  const int64_t E = wavelet == BL53 ? P + 1 : P;
+  int64_t n = 1;
+  for (int a = 0; a < dims; ++a) n *= E;
+  for (int a = 0; a < dims; ++a) {
+    int64_t stride = 1;
+    for (int b = 0; b < a; ++b) stride *= E;
+    for (int64_t base = 0; base < n; ++base) {
+      if ((base / stride) % E != 0) continue;  // one call per line
+      fwd1<T>(wavelet, u + base, stride, P, L);
+    }
+  }
+}
+
+template <class T> void inv_nd(int wavelet, T* u, int dims, int64_t P, int L) {
+  const int64_t E = wavelet == BL53 ? P + 1 : P;
+  int64_t n = 1;
+  for (int a = 0; a < dims; ++a) n *= E;
+  for (int a = dims - 1; a >= 0; --a) {
+    int64_t stride = 1;
+    for (int b = 0; b < a; ++b) stride *= E;
+    for (int64_t base = 0; base < n; ++base) {
+      if ((base / stride) % E != 0) continue;
+      inv1<T>(wavelet, u + base, stride, P, L);
+    }
+  }
+}
+
+}  // namespace orc

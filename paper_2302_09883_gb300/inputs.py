@@ -1,0 +1,99 @@
+"""Seeded synthetic inputs (macroscopic initial fields) and workload shapes.
+
+This module holds no arithmetic of the method: it only produces the initial
+macroscopic fields (density, velocity, pressure) that both the CUDA library
+and the CPU oracle turn into their state.  Arrays are float64, shaped
+(ny_nodes, nx_nodes), x fastest.
+"""
+import numpy as np
+
+# Workloads: the shapes, sizes and parameters of the benchmark cases.
+WORKLOADS = {
+    # D2Q9 BGK, 128^2 periodic, 16 Haar patches of 32^2, 3 levels, FP64.
+    "d2q9_haar_128": dict(scheme="d2q9", wavelet="haar", n=128, P=32, L=3, eps=1e-4, prec="f64",
+                          store="f64", rule="const", tau=0.8, steps=100, init="bump"),
+    # D2Q9 BGK, 2048^2 periodic, BL5/3 patches of 64 cells, 4 levels, FP32
+    # compute, BF16 details with per-band scale, shear wave + noise.
+    "d2q9_bl53_2048": dict(scheme="d2q9", wavelet="bl53", n=2048, P=64, L=4, eps=1e-4, prec="f32",
+                           store="bf16", rule="const", tau=0.6, steps=2000, init="shear"),
+    # 2-D Euler, Rusanov, 4096 cells (4097 nodes) per axis, outflow, BL5/3
+    # patches of 64, 4 levels, FP32 compute, int8 details.
+    "euler_bl53_4096": dict(scheme="euler2d", wavelet="bl53", n=4096, P=64, L=4, eps=1e-3, prec="f32",
+                            store="i8", rule="const", cfl=0.4, gamma=1.4, steps=1500, init="quadrants",
+                            periodic=(False, False)),
+}
+
+
+def gaussian_bump(n, amp=0.1, sigma=8.0, center=None):
+    """rho = 1 + amp*exp(-r^2/(2 sigma^2)) around the centre node, u = 0."""
+    c = (n / 2.0, n / 2.0) if center is None else center
+    j, i = np.meshgrid(np.arange(n, dtype=np.float64), np.arange(n, dtype=np.float64), indexing="ij")
+    r2 = (i - c[0]) ** 2 + (j - c[1]) ** 2
+    rho = 1.0 + amp * np.exp(-r2 / (2.0 * sigma * sigma))
+    return [rho, np.zeros_like(rho), np.zeros_like(rho)]
+
+
+def shear_wave(n, u0=0.05, noise=1e-4, seed=0):
+    """rho = 1, u_x = u0 sin(2 pi y / n) + N(0, noise) per node, u_y = 0."""
+    y = np.arange(n, dtype=np.float64)[:, None]
+    ux = u0 * np.sin(2.0 * np.pi * y / n) * np.ones((1, n))
+    if noise > 0:
+        ux = ux + np.random.default_rng(seed).normal(0.0, noise, size=(n, n))
+    return [np.ones((n, n)), ux, np.zeros((n, n))]
+
+
+# Four-quadrant Riemann data (rho, u, v, p), quadrants split at x = y = 1/2.
+QUADRANTS = {
+    "NE": (1.5, 0.0, 0.0, 1.5),
+    "NW": (0.5323, 1.206, 0.0, 0.3),
+    "SW": (0.138, 1.206, 1.206, 0.029),
+    "SE": (0.5323, 0.0, 1.206, 0.3),
+}
+
+
+def four_quadrant(n):
+    """Nodes x_k = k/n, k = 0..n on [0,1]^2; a node with x >= 1/2 is east."""
+    x = np.arange(n + 1, dtype=np.float64) / n
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    out = [np.zeros_like(X) for _ in range(4)]
+    for name, st in QUADRANTS.items():
+        east = X >= 0.5 if name in ("NE", "SE") else X < 0.5
+        north = Y >= 0.5 if name in ("NE", "NW") else Y < 0.5
+        m = east & north
+        for q in range(4):
+            out[q][m] = st[q]
+    return out
+
+
+def sod_x(n, periodic=False):
+    """1-D Sod tube along x, replicated along y (n+1 nodes for outflow)."""
+    m = n if periodic else n + 1
+    x = np.arange(m, dtype=np.float64) / n
+    left = x < 0.5
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    ones = np.ones((m, 1))
+    return [ones * rho, np.zeros((m, m)), np.zeros((m, m)), ones * p]
+
+
+def batch_specs(count=96, seed=0, sides=(256, 512, 1024, 2048)):
+    """Independent D2Q9 runs: side, bump amplitude, width and centre."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        side = int(rng.choice(sides))
+        out.append(dict(side=side, amp=float(rng.uniform(0.01, 0.1)), sigma=float(rng.uniform(4.0, 32.0)),
+                        cx=float(rng.uniform(0, side)), cy=float(rng.uniform(0, side))))
+    return out
+
+
+def initial_fields(w, n=None, seed=0):
+    """Initial macroscopic fields of a workload dict (optionally resized)."""
+    n = w["n"] if n is None else n
+    if w["init"] == "bump":
+        return gaussian_bump(n)
+    if w["init"] == "shear":
+        return shear_wave(n, seed=seed)
+    if w["init"] == "quadrants":
+        return four_quadrant(n)
+    raise ValueError(w["init"])
