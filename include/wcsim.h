@@ -1,0 +1,178 @@
+/* wcsim: wavelet-compressed patch time stepping for LBM / FV schemes on one
+ * GB300 (sm_103a).
+ *
+ * The method (Flint & Helluy, "Reducing the memory usage of Lattice-Boltzmann
+ * schemes with a DWT-based compression"):
+ *   - the domain is split into patches (Sec. 3.1.1); with the folded BL5/3
+ *     wavelet a patch of P cells holds P+1 nodes and shares its bordering
+ *     nodes with its neighbours so that mass is conserved exactly;
+ *   - every patch stays in device memory only as thresholded wavelet
+ *     coefficients (Sec. 2: DWT of Sec. 2.1.2, hard threshold of Sec. 2.2,
+ *     lossless stage of Sec. 2.3);
+ *   - every time step decodes a patch, applies one scheme step (Sec. 1, eq.
+ *     vf_scheme, or a D2Q9 BGK collide-stream) and re-encodes it.  The paper
+ *     decodes the whole grid each step and names per-patch decoding as future
+ *     work (Sec. 3.2.4, last paragraph); that is what this library does, one
+ *     fused kernel launch per time step.
+ *
+ * Conventions for every entry point:
+ *   - every call returns a wcs_status; nothing throws across this boundary;
+ *   - the caller owns every buffer it passes (host or device, as stated); the
+ *     library owns all device state of a simulation and frees it in
+ *     wcs_destroy;
+ *   - work is enqueued on the stream given at creation (NULL = legacy default
+ *     stream); calls that return data to the host synchronise that stream;
+ *   - errors detected on the device (arena overflow, NaN) are sticky: they are
+ *     reported by the next synchronising call (wcs_sync, wcs_stats,
+ *     wcs_export_field, wcs_step with sync) and the state is left at the last
+ *     completed step;
+ *   - a simulation is not thread-safe: one host thread at a time.
+ */
+#ifndef WCSIM_H
+#define WCSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wcs_sim wcs_sim;
+
+typedef enum {
+  WCS_OK = 0,
+  WCS_E_ARG = 1,          /* invalid argument or combination */
+  WCS_E_OOM = 2,          /* device allocation failed */
+  WCS_E_ARENA_FULL = 3,   /* compressed state outgrew its arena */
+  WCS_E_NAN = 4,          /* a NaN/Inf coefficient was produced */
+  WCS_E_TIMEOUT = 5,      /* a bounded device wait gave up */
+  WCS_E_CUDA = 6,         /* a CUDA runtime call failed */
+  WCS_E_UNSUPPORTED = 7   /* no compiled kernel for this configuration */
+} wcs_status;
+
+/* Schemes.  D2Q9: 9 populations, lattice units, periodic axes only.
+ * EULER2D: (rho, rho u, rho v, E), perfect gas, Rusanov flux in the form of
+ * the paper's eq. vf_scheme, periodic or outflow axes. */
+typedef enum { WCS_D2Q9 = 0, WCS_D3Q19 = 1, WCS_EULER2D = 2 } wcs_scheme;
+
+/* Wavelets: folded BL5/3 on P+1 nodes (Sec. 2.1.2), or Haar on P cells. */
+typedef enum { WCS_BL53 = 0, WCS_HAAR = 1 } wcs_wavelet;
+
+/* Threshold rules of Sec. 2.2 (accumulation / capped under the reading that
+ * the finest band gets eps and coarser bands smaller thresholds). */
+typedef enum { WCS_RULE_CONST = 0, WCS_RULE_ACCUM = 1, WCS_RULE_CAPPED = 2 } wcs_rule;
+
+/* Storage of the surviving detail coefficients. */
+typedef enum { WCS_STORE_F64 = 0, WCS_STORE_F32 = 1, WCS_STORE_BF16 = 2, WCS_STORE_I8 = 3 } wcs_store;
+
+/* Arithmetic precision of the whole step (FP64 computes stores F64). */
+typedef enum { WCS_FP64 = 0, WCS_FP32 = 1 } wcs_prec;
+
+typedef struct {
+  int dims;               /* 2 */
+  int64_t n[3];           /* cells per axis (multiple of the patch size) */
+  uint32_t periodic_mask; /* bit a set: axis a periodic, else outflow */
+} wcs_grid;
+
+typedef struct {
+  int wavelet;            /* wcs_wavelet */
+  int rule;               /* wcs_rule */
+  int detail_store;       /* wcs_store */
+  int compute;            /* wcs_prec */
+  double tau;             /* D2Q9 relaxation time (omega = 1/tau) */
+  double cfl;             /* EULER2D: dt = cfl h / max(|u|+c, |v|+c) */
+  double gamma;           /* EULER2D ratio of specific heats */
+  double arena_factor;    /* arena capacity per buffer, as a fraction of the
+                             uncompressed state size in the compute type
+                             (0 = default 0.25) */
+  void* cuda_stream;      /* cudaStream_t, NULL = default stream */
+} wcs_opts;
+
+/* Per-step diagnostics, all reductions in FP64 in a fixed order. */
+typedef struct {
+  int64_t step;              /* completed time steps */
+  double time;               /* physical time (EULER2D) or steps (D2Q9) */
+  double field_sum[19];      /* per field: trapezoid-weighted sum computed
+                                from the coarse coefficients (details carry
+                                no mass, eq. conservation) */
+  double mass;               /* D2Q9: sum of populations; EULER2D: rho */
+  double momentum[3];        /* D2Q9: sum c_i f_i; EULER2D: rho u, rho v */
+  double energy;             /* EULER2D: E */
+  double smax;               /* EULER2D: largest signal speed of the state */
+  int64_t live_bytes;        /* bytes of the records of the current state */
+  int64_t resident_bytes;    /* every device byte the simulation holds */
+  int64_t uncompressed_bytes;/* one uncompressed copy of the state */
+  uint32_t status;           /* sticky device status bits */
+} wcs_step_stats;
+
+/* Creates a simulation.  grid: cells per axis; patch: P (power of two,
+ * P/2^levels >= 2 for BL5/3); levels: L >= 1; eps: threshold constant c of
+ * Sec. 2.2 (0 = lossless up to rounding).  Allocates all device memory.
+ * Returns WCS_E_UNSUPPORTED if no kernel was compiled for the combination
+ * (scheme, wavelet, compute, detail_store, P, L). */
+wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int levels, double eps,
+                          const wcs_opts* opts, wcs_sim** out);
+
+/* Frees everything the simulation holds.  NULL is accepted. */
+void wcs_destroy(wcs_sim* sim);
+
+/* Initial state from macroscopic fields, each a dense array of doubles laid
+ * out [ny][nx] over the unique nodes (nx = n[0] cells, or n[0]+1 nodes on a
+ * non-periodic BL5/3 axis), x fastest.  D2Q9: (rho, u_x, u_y), the state is
+ * the equilibrium.  EULER2D: (rho, u, v, p).  fields[k] are host pointers if
+ * src_is_device == 0, else device pointers.  Encodes state 0. */
+wcs_status wcs_init_macro(wcs_sim* sim, const double* const* fields, int nfields, int src_is_device);
+
+/* Advances n time steps (one fused kernel launch each, enqueued on the
+ * simulation's stream; does not synchronise). */
+wcs_status wcs_step(wcs_sim* sim, int64_t n);
+
+/* Waits for the stream and returns the sticky device status as a status. */
+wcs_status wcs_sync(wcs_sim* sim);
+
+/* Decodes the current state of one field (D2Q9: population i; EULER2D: 0..3)
+ * into a dense [ny][nx] array over the unique nodes.  dtype: 0 = double,
+ * 1 = float.  dst is a device pointer if dst_is_device, else host.
+ * field = -1 writes every field, one after the other. */
+wcs_status wcs_export_field(wcs_sim* sim, int field, void* dst, int dst_is_device, int dtype);
+
+/* Bytes of device memory that hold the compressed state: the records of
+ * the current state plus the ghost ring it needs and the patch table. */
+int64_t wcs_compressed_bytes(const wcs_sim* sim);
+
+/* FP64 diagnostics of the current state (synchronises). */
+wcs_status wcs_stats(wcs_sim* sim, wcs_step_stats* out);
+
+/* Copies the record of one patch of the current state (the byte format of
+ * the oracle) to host memory.  *nbytes receives its size; if cap is too
+ * small nothing is copied and WCS_E_ARG is returned. */
+wcs_status wcs_export_record(wcs_sim* sim, int64_t patch, void* dst, int64_t cap, int64_t* nbytes);
+
+/* Number of patches and fields, dense node counts. */
+wcs_status wcs_shape(const wcs_sim* sim, int64_t* npatch, int* nfields, int64_t* nodes_x, int64_t* nodes_y);
+
+/* Per-launch device time of the last wcs_step kernels is not tracked here;
+ * callers time with events on the stream.  This returns the stream. */
+void* wcs_stream(const wcs_sim* sim);
+
+/* Last error message of the simulation (or of the last failed create when
+ * sim is NULL).  Valid until the next call on the same simulation. */
+const char* wcs_last_error(const wcs_sim* sim);
+
+/* ------------------------------------------------------------------------
+ * Uncompressed baseline (the "uncompressed" side of the metric): the same
+ * scheme on dense FP32 arrays, two lattices, one kernel per step.
+ * ---------------------------------------------------------------------- */
+typedef struct wcs_dense wcs_dense;
+
+wcs_status wcs_dense_create(const wcs_grid* grid, int scheme, const wcs_opts* opts, wcs_dense** out);
+void wcs_dense_destroy(wcs_dense* d);
+wcs_status wcs_dense_init_macro(wcs_dense* d, const double* const* fields, int nfields, int src_is_device);
+wcs_status wcs_dense_step(wcs_dense* d, int64_t n);
+wcs_status wcs_dense_export_field(wcs_dense* d, int field, void* dst, int dst_is_device, int dtype);
+int64_t wcs_dense_bytes(const wcs_dense* d);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WCSIM_H */

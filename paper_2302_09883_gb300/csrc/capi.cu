@@ -1,0 +1,467 @@
+// C-ABI of the compressed-patch simulation (declared in include/wcsim.h).
+//
+// Device state of one simulation:
+//   arena[2]   ping-pong compressed arenas; step n reads arena n%2 and
+//              bump-allocates the records of state n+1 in arena (n+1)%2
+//   tab[2]     per patch (record offset << 24 | record bytes)
+//   ring[2]    ghost rings exported by every patch for the next step
+//   ctl        cursors, max signal speed, time, sticky status
+//   pstats     FP64 coarse-block sums per patch and field
+//   tables     canonical order -> shared-memory tile offset, band, edge bits,
+//              threshold multiplier per band (Sec. 2.2)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/wcsim.h"
+#include "patch2d.cuh"
+#include "registry.h"
+
+namespace wcs {
+void reg_d2q9_haar_f64_p32l3(std::vector<KernelEntry>&);
+void reg_d2q9_bl53_f64_p32l3(std::vector<KernelEntry>&);
+void reg_d2q9_bl53_bf16_p64l4(std::vector<KernelEntry>&);
+void reg_d2q9_bl53_f32_p64l4(std::vector<KernelEntry>&);
+void reg_d2q9_bl53_i8_p64l4(std::vector<KernelEntry>&);
+void reg_euler_bl53_i8_p64l4(std::vector<KernelEntry>&);
+void reg_euler_bl53_f64_p32l3(std::vector<KernelEntry>&);
+
+void register_all(std::vector<KernelEntry>& v) {
+  reg_d2q9_haar_f64_p32l3(v);
+  reg_d2q9_bl53_f64_p32l3(v);
+  reg_d2q9_bl53_bf16_p64l4(v);
+  reg_d2q9_bl53_f32_p64l4(v);
+  reg_d2q9_bl53_i8_p64l4(v);
+  reg_euler_bl53_i8_p64l4(v);
+  reg_euler_bl53_f64_p32l3(v);
+}
+}  // namespace wcs
+
+using wcs::KernelEntry;
+
+namespace {
+std::string g_create_err;
+
+const std::vector<KernelEntry>& kernels() {
+  static std::vector<KernelEntry> v;
+  static bool done = false;
+  if (!done) {
+    wcs::register_all(v);
+    done = true;
+  }
+  return v;
+}
+
+int pos_class(int k, int L) {
+  if (k % (1 << L) == 0) return 0;
+  int m = 1;
+  while (((k >> (m - 1)) & 1) == 0) ++m;
+  return m;
+}
+int class_pos(int c, int i, int L) { return c == 0 ? (i << L) : ((2 * i + 1) << (c - 1)); }
+int class_size(int wavelet, int P, int c, int L) {
+  if (c == 0) return wavelet == WCS_BL53 ? (P >> L) + 1 : (P >> L);
+  return P >> c;
+}
+}  // namespace
+
+struct wcs_sim {
+  int scheme = 0, wavelet = 0, prec = 0, store = 0, rule = 0, P = 0, L = 0;
+  double eps = 0, tau = 1, cfl = 0.4, gamma = 1.4;
+  int64_t n[2] = {0, 0};
+  int per[2] = {1, 1};
+  int64_t G[2] = {0, 0};
+  int npx = 0, npy = 0, npatch = 0, F = 0, E = 0, NC1 = 0, nc = 0, nd = 0, nw = 0, nb = 0;
+  size_t tsize = 8;
+  KernelEntry ke;
+  cudaStream_t stream = nullptr;
+  unsigned char* arena[2] = {nullptr, nullptr};
+  unsigned long long cap = 0;
+  unsigned long long* tab[2] = {nullptr, nullptr};
+  void* ring[2] = {nullptr, nullptr};
+  wcs::Ctl* ctl = nullptr;
+  double* pstats = nullptr;
+  unsigned short* canon_tile = nullptr;
+  unsigned char* canon_band = nullptr;
+  unsigned int* edgew = nullptr;
+  double* bfactor = nullptr;
+  int64_t nstep = 0;
+  bool inited = false;
+  int64_t resident = 0;
+  std::string err;
+};
+
+static wcs_status fail(wcs_sim* s, wcs_status st, const std::string& msg) {
+  if (s) s->err = msg;
+  else g_create_err = msg;
+  return st;
+}
+
+static wcs_status cuda_fail(wcs_sim* s, cudaError_t e, const char* what) {
+  return fail(s, WCS_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(s, e_, #call); \
+  } while (0)
+
+static wcs_status dalloc(wcs_sim* s, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(s, WCS_E_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  s->resident += int64_t(bytes);
+  return WCS_OK;
+}
+
+static wcs::PatchArgs base_args(const wcs_sim* s) {
+  wcs::PatchArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.npx = s->npx;
+  a.npy = s->npy;
+  a.per_x = s->per[0];
+  a.per_y = s->per[1];
+  a.cap_out = s->cap;
+  a.ctl = s->ctl;
+  a.pstats = s->pstats;
+  a.canon_tile = s->canon_tile;
+  a.canon_band = s->canon_band;
+  a.edgew = s->edgew;
+  a.band_factor = s->bfactor;
+  a.eps = s->eps;
+  a.eps_edge = s->eps;
+  a.eps_patch = nullptr;
+  a.omega = 1.0 / s->tau;
+  a.gamma = s->gamma;
+  a.cfl = s->cfl;
+  a.ncell_x = s->n[0];
+  a.G0 = s->G[0];
+  a.G1 = s->G[1];
+  a.field_sel = -1;
+  a.flags = unsigned(s->store) | (unsigned(s->wavelet) << 8) | (s->prec == WCS_FP64 ? (1u << 16) : 0u);
+  return a;
+}
+
+extern "C" {
+
+wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int levels, double eps, const wcs_opts* opts,
+                          wcs_sim** out) {
+  if (!grid || !opts || !out) return fail(nullptr, WCS_E_ARG, "null argument");
+  *out = nullptr;
+  if (grid->dims != 2) return fail(nullptr, WCS_E_UNSUPPORTED, "only 2-D grids are compiled");
+  if (!(eps >= 0)) return fail(nullptr, WCS_E_ARG, "eps must be >= 0");
+  const KernelEntry* ke = nullptr;
+  for (const KernelEntry& k : kernels())
+    if (k.scheme == scheme && k.wavelet == opts->wavelet && k.prec == opts->compute && k.store == opts->detail_store &&
+        k.P == patch && k.L == levels)
+      ke = &k;
+  if (!ke)
+    return fail(nullptr, WCS_E_UNSUPPORTED,
+                "no compiled kernel for scheme " + std::to_string(scheme) + " wavelet " + std::to_string(opts->wavelet) +
+                    " compute " + std::to_string(opts->compute) + " store " + std::to_string(opts->detail_store) +
+                    " P " + std::to_string(patch) + " L " + std::to_string(levels));
+  for (int a = 0; a < 2; ++a)
+    if (grid->n[a] <= 0 || grid->n[a] % patch) return fail(nullptr, WCS_E_ARG, "grid not a multiple of the patch size");
+  if (scheme == WCS_D2Q9 && (grid->periodic_mask & 3u) != 3u) return fail(nullptr, WCS_E_ARG, "D2Q9 needs periodic axes");
+  if (opts->rule < 0 || opts->rule > 2) return fail(nullptr, WCS_E_ARG, "bad threshold rule");
+
+  wcs_sim* s = new wcs_sim();
+  s->ke = *ke;
+  s->scheme = scheme;
+  s->wavelet = opts->wavelet;
+  s->prec = opts->compute;
+  s->store = opts->detail_store;
+  s->rule = opts->rule;
+  s->P = patch;
+  s->L = levels;
+  s->eps = eps;
+  s->tau = opts->tau > 0 ? opts->tau : 1.0;
+  s->cfl = opts->cfl > 0 ? opts->cfl : 0.4;
+  s->gamma = opts->gamma > 1 ? opts->gamma : 1.4;
+  s->stream = static_cast<cudaStream_t>(opts->cuda_stream);
+  for (int a = 0; a < 2; ++a) {
+    s->n[a] = grid->n[a];
+    s->per[a] = (grid->periodic_mask >> a) & 1u;
+    s->G[a] = (s->wavelet == WCS_BL53 && !s->per[a]) ? s->n[a] + 1 : s->n[a];
+  }
+  s->npx = int(s->n[0] / patch);
+  s->npy = int(s->n[1] / patch);
+  s->npatch = s->npx * s->npy;
+  s->F = scheme == WCS_D2Q9 ? 9 : 4;
+  s->E = s->wavelet == WCS_BL53 ? patch + 1 : patch;
+  s->NC1 = (patch >> levels) + (s->wavelet == WCS_BL53 ? 1 : 0);
+  s->nc = s->NC1 * s->NC1;
+  s->nd = s->E * s->E - s->nc;
+  s->nw = (s->nd + 31) / 32;
+  s->nb = (levels + 1) * (levels + 1);
+  s->tsize = s->prec == WCS_FP64 ? 8 : 4;
+
+  // ---- canonical layout tables (bands (c_x, c_y), c_x slowest, row-major)
+  const int nall = s->E * s->E, pw = ke->pitch;
+  std::vector<unsigned short> ctile(nall);
+  std::vector<unsigned char> cband(nall);
+  std::vector<unsigned int> ew(s->nw, 0u);
+  std::vector<double> bf(s->nb);
+  int ci = 0;
+  for (int cx = 0; cx <= levels; ++cx)
+    for (int cy = 0; cy <= levels; ++cy) {
+      const int b = cx * (levels + 1) + cy;
+      const int sx = class_size(s->wavelet, patch, cx, levels), sy = class_size(s->wavelet, patch, cy, levels);
+      for (int iy = 0; iy < sy; ++iy)
+        for (int ix = 0; ix < sx; ++ix) {
+          const int kx = class_pos(cx, ix, levels), ky = class_pos(cy, iy, levels);
+          ctile[ci] = (unsigned short)(ky * pw + kx);
+          cband[ci] = (unsigned char)b;
+          const bool edge = s->wavelet == WCS_BL53 && (kx == 0 || kx == patch || ky == 0 || ky == patch);
+          if (ci >= s->nc && edge) {
+            const int d = ci - s->nc;
+            ew[d / 32] |= 1u << (d % 32);
+          }
+          ++ci;
+        }
+      int sum = 0, mx = 0;
+      for (int c : {cx, cy}) {
+        const int m = c == 0 ? levels : c;
+        sum += m - 1;
+        mx = std::max(mx, m);
+      }
+      bf[b] = s->rule == WCS_RULE_CONST ? 1.0 : (s->rule == WCS_RULE_ACCUM ? std::ldexp(1.0, -sum) : std::ldexp(1.0, -(mx - 1)));
+    }
+  (void)pos_class;
+
+  wcs_status st;
+  const size_t state_bytes = size_t(s->F) * size_t(s->G[0]) * size_t(s->G[1]) * s->tsize;
+  const double factor = opts->arena_factor > 0 ? opts->arena_factor : 0.25;
+  s->cap = (unsigned long long)(std::max(double(state_bytes) * factor, double(s->npatch) * 4096.0) + 255) / 256 * 256;
+  for (int b = 0; b < 2; ++b) {
+    if ((st = dalloc(s, (void**)&s->arena[b], s->cap)) != WCS_OK) goto bad;
+    if ((st = dalloc(s, (void**)&s->tab[b], size_t(s->npatch) * 8)) != WCS_OK) goto bad;
+    if ((st = dalloc(s, &s->ring[b], size_t(s->npatch) * ke->ring * s->tsize)) != WCS_OK) goto bad;
+  }
+  if ((st = dalloc(s, (void**)&s->ctl, sizeof(wcs::Ctl))) != WCS_OK) goto bad;
+  if ((st = dalloc(s, (void**)&s->pstats, size_t(s->npatch) * s->F * 8)) != WCS_OK) goto bad;
+  if ((st = dalloc(s, (void**)&s->canon_tile, nall * 2)) != WCS_OK) goto bad;
+  if ((st = dalloc(s, (void**)&s->canon_band, nall)) != WCS_OK) goto bad;
+  if ((st = dalloc(s, (void**)&s->edgew, size_t(s->nw) * 4)) != WCS_OK) goto bad;
+  if ((st = dalloc(s, (void**)&s->bfactor, size_t(s->nb) * 8)) != WCS_OK) goto bad;
+  {
+    cudaError_t e;
+    if ((e = cudaMemcpy(s->canon_tile, ctile.data(), nall * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(s->canon_band, cband.data(), nall, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(s->edgew, ew.data(), size_t(s->nw) * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(s->bfactor, bf.data(), size_t(s->nb) * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(s->ctl, 0, sizeof(wcs::Ctl))) != cudaSuccess) {
+      st = cuda_fail(s, e, "table upload");
+      goto bad;
+    }
+  }
+  *out = s;
+  return WCS_OK;
+bad:
+  g_create_err = s->err;
+  wcs_destroy(s);
+  return st;
+}
+
+void wcs_destroy(wcs_sim* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  else cudaDeviceSynchronize();
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(s->arena[b]);
+    cudaFree(s->tab[b]);
+    cudaFree(s->ring[b]);
+  }
+  cudaFree(s->ctl);
+  cudaFree(s->pstats);
+  cudaFree(s->canon_tile);
+  cudaFree(s->canon_band);
+  cudaFree(s->edgew);
+  cudaFree(s->bfactor);
+  delete s;
+}
+
+const char* wcs_last_error(const wcs_sim* s) { return s ? s->err.c_str() : g_create_err.c_str(); }
+
+void* wcs_stream(const wcs_sim* s) { return s ? static_cast<void*>(s->stream) : nullptr; }
+
+wcs_status wcs_shape(const wcs_sim* s, int64_t* npatch, int* nfields, int64_t* nx, int64_t* ny) {
+  if (!s) return WCS_E_ARG;
+  if (npatch) *npatch = s->npatch;
+  if (nfields) *nfields = s->F;
+  if (nx) *nx = s->G[0];
+  if (ny) *ny = s->G[1];
+  return WCS_OK;
+}
+
+wcs_status wcs_init_macro(wcs_sim* s, const double* const* fields, int nfields, int src_is_device) {
+  if (!s || !fields) return WCS_E_ARG;
+  const int need = s->scheme == WCS_D2Q9 ? 3 : 4;
+  if (nfields < need) return fail(s, WCS_E_ARG, "init needs " + std::to_string(need) + " macroscopic fields");
+  const size_t plane = size_t(s->G[0]) * size_t(s->G[1]);
+  double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
+  wcs::PatchArgs a = base_args(s);
+  for (int q = 0; q < need; ++q) {
+    if (src_is_device) {
+      a.macro[q] = fields[q];
+    } else {
+      CK(cudaMalloc(&tmp[q], plane * 8));
+      CK(cudaMemcpyAsync(tmp[q], fields[q], plane * 8, cudaMemcpyHostToDevice, s->stream));
+      a.macro[q] = tmp[q];
+    }
+  }
+  CK(cudaMemsetAsync(s->ctl, 0, sizeof(wcs::Ctl), s->stream));
+  a.step = -1;
+  a.arena_out = s->arena[0];
+  a.tab_out = s->tab[0];
+  a.ring_out = s->ring[0];
+  a.cur_out = 0;
+  a.smax_wr = 0;
+  CK(s->ke.launch(wcs::MODE_INIT, a, s->npatch, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  for (int q = 0; q < 4; ++q)
+    if (tmp[q]) cudaFree(tmp[q]);
+  s->nstep = 0;
+  s->inited = true;
+  return wcs_sync(s);
+}
+
+wcs_status wcs_step(wcs_sim* s, int64_t n) {
+  if (!s || n < 0) return WCS_E_ARG;
+  if (!s->inited) return fail(s, WCS_E_ARG, "wcs_step before wcs_init_macro");
+  wcs::PatchArgs a = base_args(s);
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t k = s->nstep;
+    const int in = int(k % 2), out = 1 - in;
+    a.step = k;
+    a.arena_in = s->arena[in];
+    a.tab_in = s->tab[in];
+    a.arena_out = s->arena[out];
+    a.tab_out = s->tab[out];
+    a.ring_in = s->ring[in];
+    a.ring_out = s->ring[out];
+    a.cur_out = out;
+    a.cur_rst = in;
+    a.smax_rd = int(k % 3);
+    a.smax_wr = int((k + 1) % 3);
+    a.smax_rst = int((k + 2) % 3);
+    CK(s->ke.launch(wcs::MODE_STEP, a, s->npatch, s->stream));
+    s->nstep = k + 1;
+  }
+  return WCS_OK;
+}
+
+wcs_status wcs_sync(wcs_sim* s) {
+  if (!s) return WCS_E_ARG;
+  CK(cudaStreamSynchronize(s->stream));
+  wcs::Ctl c;
+  CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+  if (c.status) {
+    // the state stays at the input of the failed step
+    if (c.err_step >= 0 && c.err_step < s->nstep) s->nstep = c.err_step;
+    if (c.status & wcs::STAT_ARENA_FULL)
+      return fail(s, WCS_E_ARENA_FULL, "compressed arena full at step " + std::to_string(c.err_step) +
+                                           " (capacity " + std::to_string(s->cap) + " bytes)");
+    if (c.status & wcs::STAT_NAN) return fail(s, WCS_E_NAN, "non-finite coefficient at step " + std::to_string(c.err_step));
+    return fail(s, WCS_E_CUDA, "device status " + std::to_string(c.status));
+  }
+  return WCS_OK;
+}
+
+wcs_status wcs_export_field(wcs_sim* s, int field, void* dst, int dst_is_device, int dtype) {
+  if (!s || !dst || field < -1 || field >= s->F || (dtype != 0 && dtype != 1)) return WCS_E_ARG;
+  if (!s->inited) return fail(s, WCS_E_ARG, "export before init");
+  wcs_status st = wcs_sync(s);
+  if (st != WCS_OK) return st;
+  const size_t plane = size_t(s->G[0]) * size_t(s->G[1]);
+  const size_t bytes = plane * (field < 0 ? s->F : 1) * (dtype == 0 ? 8 : 4);
+  void* d = dst;
+  if (!dst_is_device) CK(cudaMalloc(&d, bytes));
+  wcs::PatchArgs a = base_args(s);
+  const int cur = int(s->nstep % 2);
+  a.arena_in = s->arena[cur];
+  a.tab_in = s->tab[cur];
+  a.dense = d;
+  a.dense_dtype = dtype;
+  a.field_sel = field;
+  CK(s->ke.launch(wcs::MODE_EXPORT, a, s->npatch, s->stream));
+  if (!dst_is_device) {
+    CK(cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    cudaFree(d);
+  }
+  return WCS_OK;
+}
+
+static int64_t live_bytes(const wcs_sim* s) {
+  wcs::Ctl c;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return -1;
+  if (cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  return int64_t(c.cursor[s->nstep % 2]);
+}
+
+int64_t wcs_compressed_bytes(const wcs_sim* s) {
+  if (!s || !s->inited) return -1;
+  const int64_t live = live_bytes(s);
+  if (live < 0) return -1;
+  return live + int64_t(s->npatch) * s->ke.ring * int64_t(s->tsize) + int64_t(s->npatch) * 8;
+}
+
+wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
+  if (!s || !o) return WCS_E_ARG;
+  std::memset(o, 0, sizeof(*o));
+  CK(cudaStreamSynchronize(s->stream));
+  wcs::Ctl c;
+  CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+  std::vector<double> ps(size_t(s->npatch) * s->F);
+  CK(cudaMemcpy(ps.data(), s->pstats, ps.size() * 8, cudaMemcpyDeviceToHost));
+  for (int f = 0; f < s->F; ++f) {
+    double acc = 0;
+    for (int p = 0; p < s->npatch; ++p) acc += ps[size_t(p) * s->F + f];
+    o->field_sum[f] = acc;
+  }
+  if (s->scheme == WCS_D2Q9) {
+    static const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    for (int i = 0; i < 9; ++i) {
+      o->mass += o->field_sum[i];
+      o->momentum[0] += cx[i] * o->field_sum[i];
+      o->momentum[1] += cy[i] * o->field_sum[i];
+    }
+  } else {
+    o->mass = o->field_sum[0];
+    o->momentum[0] = o->field_sum[1];
+    o->momentum[1] = o->field_sum[2];
+    o->energy = o->field_sum[3];
+  }
+  o->step = s->nstep;
+  o->time = c.time;
+  unsigned long long sb = c.smax[s->nstep % 3];
+  std::memcpy(&o->smax, &sb, 8);
+  o->live_bytes = int64_t(c.cursor[s->nstep % 2]);
+  o->resident_bytes = s->resident;
+  o->uncompressed_bytes = int64_t(s->F) * s->G[0] * s->G[1] * int64_t(s->tsize);
+  o->status = c.status;
+  return WCS_OK;
+}
+
+wcs_status wcs_export_record(wcs_sim* s, int64_t patch, void* dst, int64_t cap, int64_t* nbytes) {
+  if (!s || patch < 0 || patch >= s->npatch) return WCS_E_ARG;
+  CK(cudaStreamSynchronize(s->stream));
+  unsigned long long ent;
+  CK(cudaMemcpy(&ent, s->tab[s->nstep % 2] + patch, 8, cudaMemcpyDeviceToHost));
+  const int64_t nb = int64_t(ent & 0xffffffull), off = int64_t(ent >> 24);
+  if (nbytes) *nbytes = nb;
+  if (!dst || cap < nb) return WCS_E_ARG;
+  CK(cudaMemcpy(dst, s->arena[s->nstep % 2] + off, size_t(nb), cudaMemcpyDeviceToHost));
+  return WCS_OK;
+}
+
+}  // extern "C"

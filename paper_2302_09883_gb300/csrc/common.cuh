@@ -1,0 +1,235 @@
+// Device building blocks shared by the patch kernels.
+//
+// Every floating-point operation below is written in one fixed order and the
+// library is compiled with -fmad=false, so each operation rounds once: the
+// FP32 and FP64 results are reproducible from the written formulas.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wcs {
+
+enum { SCH_D2Q9 = 0, SCH_D3Q19 = 1, SCH_EULER2D = 2 };
+enum { WV_BL53 = 0, WV_HAAR = 1 };
+enum { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2, ST_I8 = 3 };
+enum { MODE_INIT = 0, MODE_STEP = 1, MODE_EXPORT = 2 };
+
+// Sticky device status bits.
+enum : uint32_t { STAT_ARENA_FULL = 1u, STAT_NAN = 2u, STAT_BAD_RECORD = 4u };
+
+// Per-simulation control block in device memory.
+struct Ctl {
+  unsigned long long cursor[2];  // bump allocators of the two arenas
+  unsigned long long live[2];    // bytes of the last completed state in each
+  unsigned long long smax[3];    // double bits of the max signal speed
+  double time;                   // physical time (Euler) or step count
+  unsigned int status;
+  int err_step;
+};
+
+template <int S> struct StoreType;
+template <> struct StoreType<ST_F64> { typedef double type; };
+template <> struct StoreType<ST_F32> { typedef float type; };
+template <> struct StoreType<ST_BF16> { typedef uint16_t type; };
+template <> struct StoreType<ST_I8> { typedef int8_t type; };
+
+// ------------------------------------------------------------------ lifting
+// Folded BL5/3 (Sec. 2.1.2): boundary samples kept; predict
+// d_k = s_{2k+1} - (s_{2k} + s_{2k+2})/2; update for 0 < k < K
+// s'_k = s_{2k} + a_{k-1} d_{k-1} + a_k d_k, a = 1/2 at the end details and
+// 1/4 inside (the alpha equation).  Haar: d = b - a, s = a + d/2.  Values sit
+// at their node positions; level LEV works on stride 2^(LEV-1).
+template <typename T> __device__ __forceinline__ constexpr T bl53_alpha(int k, int K) {
+  return (k == 0 || k == K - 1) ? T(0.5) : T(0.25);
+}
+
+template <int WV, int P, int LEV, int L, typename T> __device__ __forceinline__ void fwd_levels(T* v) {
+  if constexpr (LEV <= L) {
+    constexpr int st = 1 << (LEV - 1);
+    constexpr int K = (P / st) / 2;
+    if constexpr (WV == WV_BL53) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] - T(0.5) * (v[2 * k * st] + v[(2 * k + 2) * st]);
+#pragma unroll
+      for (int k = 1; k < K; ++k) {
+        T e = v[2 * k * st];
+        e = e + bl53_alpha<T>(k - 1, K) * v[(2 * k - 1) * st];
+        e = e + bl53_alpha<T>(k, K) * v[(2 * k + 1) * st];
+        v[2 * k * st] = e;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const T a = v[2 * k * st], b = v[(2 * k + 1) * st];
+        const T d = b - a;
+        v[2 * k * st] = a + T(0.5) * d;
+        v[(2 * k + 1) * st] = d;
+      }
+    }
+    fwd_levels<WV, P, LEV + 1, L, T>(v);
+  }
+}
+
+template <int WV, int P, int LEV, typename T> __device__ __forceinline__ void inv_levels(T* v) {
+  if constexpr (LEV >= 1) {
+    constexpr int st = 1 << (LEV - 1);
+    constexpr int K = (P / st) / 2;
+    if constexpr (WV == WV_BL53) {
+#pragma unroll
+      for (int k = 1; k < K; ++k) {
+        T e = v[2 * k * st];
+        e = e - bl53_alpha<T>(k - 1, K) * v[(2 * k - 1) * st];
+        e = e - bl53_alpha<T>(k, K) * v[(2 * k + 1) * st];
+        v[2 * k * st] = e;
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] + T(0.5) * (v[2 * k * st] + v[(2 * k + 2) * st]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const T s = v[2 * k * st], d = v[(2 * k + 1) * st];
+        const T a = s - T(0.5) * d;
+        v[2 * k * st] = a;
+        v[(2 * k + 1) * st] = a + d;
+      }
+    }
+    inv_levels<WV, P, LEV - 1, T>(v);
+  }
+}
+
+// One line of E values in shared memory (p[i*stride]), transformed in
+// registers.
+template <int WV, int P, int L, bool INVERSE, typename T>
+__device__ __forceinline__ void line_transform(T* p, int stride) {
+  constexpr int E = WV == WV_BL53 ? P + 1 : P;
+  T v[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) v[i] = p[i * stride];
+  if constexpr (INVERSE) inv_levels<WV, P, L, T>(v);
+  else fwd_levels<WV, P, 1, L, T>(v);
+#pragma unroll
+  for (int i = 0; i < E; ++i) p[i * stride] = v[i];
+}
+
+// ------------------------------------------------------------ quantisation
+// BF16 with a per-band power-of-two scale s = 2^e >= max|d| (exact scaling),
+// int8 with s = max|d|/127 and round-half-even.
+__device__ __forceinline__ int pow2_ceil_exp(float m) {
+  int x;
+  const float fr = frexpf(m, &x);
+  int e = (fr == 0.5f) ? x - 1 : x;
+  return e < -126 ? -126 : e;
+}
+__device__ __forceinline__ float exp2_int(int e) { return __int_as_float((e + 127) << 23); }
+
+// ------------------------------------------------------------------ D2Q9
+// Velocity numbering 0 rest, 1 +x, 2 +y, 3 -x, 4 -y, 5 (+,+), 6 (-,+),
+// 7 (-,-), 8 (+,-); BGK with the second-order equilibrium.
+__host__ __device__ constexpr int d2q9_cx(int i) { return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0); }
+__host__ __device__ constexpr int d2q9_cy(int i) { return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0); }
+
+template <typename T> __device__ __forceinline__ T d2q9_w(int i) {
+  return i == 0 ? T(4.0 / 9.0) : (i <= 4 ? T(1.0 / 9.0) : T(1.0 / 36.0));
+}
+template <typename T> __device__ __forceinline__ T d2q9_cu(int i, T ux, T uy) {
+  switch (i) {
+    case 0: return T(0);
+    case 1: return ux;
+    case 2: return uy;
+    case 3: return -ux;
+    case 4: return -uy;
+    case 5: return ux + uy;
+    case 6: return uy - ux;
+    case 7: return -(ux + uy);
+    default: return ux - uy;
+  }
+}
+template <typename T> __device__ __forceinline__ void d2q9_equilibrium(T rho, T ux, T uy, T* feq) {
+  const T usq = ux * ux + uy * uy;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const T cu = d2q9_cu<T>(i, ux, uy);
+    T t = T(1) + T(3) * cu;
+    t = t + (T(4.5) * cu) * cu;
+    t = t - T(1.5) * usq;
+    feq[i] = (d2q9_w<T>(i) * rho) * t;
+  }
+}
+template <typename T> __device__ __forceinline__ void d2q9_collide(T* f, T omega) {
+  const T rho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+  const T jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+  const T jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+  const T ux = jx / rho, uy = jy / rho;
+  T feq[9];
+  d2q9_equilibrium<T>(rho, ux, uy, feq);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = f[i] - omega * (f[i] - feq[i]);
+}
+
+// -------------------------------------------------------------- Euler 2-D
+// W = (rho, rho u, rho v, E); Rusanov flux F(WL, WR, N) =
+// (Q(WL,N) + Q(WR,N))/2 - lambda (WR - WL)/2 with the four normals of the
+// paper's eq. directions, perfect gas.
+template <typename T> __device__ __forceinline__ void euler_prim(const T* W, T gm1, T gamma, T& u, T& v, T& p, T& c) {
+  u = W[1] / W[0];
+  v = W[2] / W[0];
+  T ke = W[1] * u + W[2] * v;
+  ke = T(0.5) * ke;
+  p = gm1 * (W[3] - ke);
+  c = sqrt((gamma * p) / W[0]);
+}
+template <typename T> __device__ __forceinline__ void euler_rusanov(const T* WL, const T* WR, T nx, T ny, T gm1, T gamma, T* F) {
+  T uL, vL, pL, cL, uR, vR, pR, cR;
+  euler_prim<T>(WL, gm1, gamma, uL, vL, pL, cL);
+  euler_prim<T>(WR, gm1, gamma, uR, vR, pR, cR);
+  const T unL = uL * nx + vL * ny, unR = uR * nx + vR * ny;
+  T QL[4], QR[4];
+  QL[0] = WL[0] * unL;
+  QL[1] = WL[1] * unL + pL * nx;
+  QL[2] = WL[2] * unL + pL * ny;
+  QL[3] = (WL[3] + pL) * unL;
+  QR[0] = WR[0] * unR;
+  QR[1] = WR[1] * unR + pR * nx;
+  QR[2] = WR[2] * unR + pR * ny;
+  QR[3] = (WR[3] + pR) * unR;
+  const T sL = fabs(uL * nx + vL * ny) + cL;
+  const T sR = fabs(uR * nx + vR * ny) + cR;
+  const T lam = sL > sR ? sL : sR;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T a = QL[k] + QR[k];
+    a = T(0.5) * a;
+    T b = WR[k] - WL[k];
+    b = lam * b;
+    b = T(0.5) * b;
+    F[k] = a - b;
+  }
+}
+template <typename T> __device__ __forceinline__ T euler_speed(const T* W, T gm1, T gamma) {
+  T u, v, p, c;
+  euler_prim<T>(W, gm1, gamma, u, v, p, c);
+  const T su = fabs(u) + c, sv = fabs(v) + c;
+  return su > sv ? su : sv;
+}
+template <typename T> __device__ __forceinline__ void euler_cons(T rho, T u, T v, T p, T gm1, T* W) {
+  W[0] = rho;
+  W[1] = rho * u;
+  W[2] = rho * v;
+  T ke = W[1] * u + W[2] * v;
+  ke = T(0.5) * ke;
+  W[3] = p / gm1 + ke;
+}
+
+// Warp exclusive scan helper.
+__device__ __forceinline__ unsigned warp_incl_scan(unsigned v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+}  // namespace wcs

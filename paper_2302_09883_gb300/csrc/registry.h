@@ -1,0 +1,21 @@
+// Table of compiled patch kernels, one entry per (scheme, wavelet, compute
+// precision, detail storage, P, L).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <vector>
+
+namespace wcs {
+struct PatchArgs;
+
+struct KernelEntry {
+  int scheme, wavelet, prec, store, P, L;
+  int ring;          // ghost-ring values per patch (compute type)
+  int pitch;         // shared-memory row pitch (canonical tile offsets)
+  size_t smem;       // dynamic shared memory per CTA
+  int threads;
+  cudaError_t (*launch)(int mode, const PatchArgs& a, int npatch, cudaStream_t s);
+};
+
+void register_all(std::vector<KernelEntry>& v);
+}  // namespace wcs

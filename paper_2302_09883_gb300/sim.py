@@ -1,0 +1,167 @@
+"""Python front end of the C-ABI: a compressed-patch simulation and the
+uncompressed baseline.  PyTorch supplies the CUDA stream and, when the caller
+passes device tensors, the device memory of inputs and outputs."""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as B
+
+
+def _grid(nx, ny, periodic):
+    g = B.Grid()
+    g.dims = 2
+    g.n[0], g.n[1], g.n[2] = nx, ny, 1
+    g.periodic_mask = int(periodic[0]) | (int(periodic[1]) << 1)
+    return g
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _field_ptrs(fields):
+    """Host numpy arrays or CUDA tensors -> (keepalive, pointer array, is_device)."""
+    keep, ptrs, dev = [], [], None
+    for f in fields:
+        if hasattr(f, "data_ptr"):
+            import torch
+            t = f.to(torch.float64).contiguous()
+            keep.append(t)
+            ptrs.append(t.data_ptr())
+            d = 1 if t.is_cuda else 0
+        else:
+            a = np.ascontiguousarray(f, dtype=np.float64)
+            keep.append(a)
+            ptrs.append(a.ctypes.data)
+            d = 0
+        if dev is None:
+            dev = d
+        elif dev != d:
+            raise ValueError("mixed host/device inputs")
+    arr = (C.c_void_p * len(ptrs))(*ptrs)
+    return keep, arr, dev or 0
+
+
+class Sim:
+    """One compressed-patch simulation on the current CUDA device."""
+
+    def __init__(self, scheme, wavelet, nx, ny, P, L, eps, prec="f32", store="bf16", rule="const",
+                 periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, arena_factor=0.25, stream=None):
+        self.scheme = scheme
+        o = B.Opts()
+        o.wavelet, o.rule, o.detail_store, o.compute = B.WAVELET[wavelet], B.RULE[rule], B.STORE[store], B.PREC[prec]
+        o.tau, o.cfl, o.gamma, o.arena_factor = tau, cfl, gamma, arena_factor
+        o.cuda_stream = _stream_ptr(stream)
+        h = C.c_void_p()
+        g = _grid(nx, ny, periodic)
+        B.check(B.lib().wcs_create_sim(C.byref(g), B.SCHEME[scheme], P, L, eps, C.byref(o), C.byref(h)), None)
+        self.h = h
+        npatch, nf, gx, gy = C.c_int64(), C.c_int(), C.c_int64(), C.c_int64()
+        B.lib().wcs_shape(h, C.byref(npatch), C.byref(nf), C.byref(gx), C.byref(gy))
+        self.npatch, self.F, self.G = npatch.value, nf.value, (gx.value, gy.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            B.lib().wcs_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def init_macro(self, fields):
+        keep, arr, dev = _field_ptrs(fields)
+        B.check(B.lib().wcs_init_macro(self.h, arr, len(fields), dev), self.h)
+
+    def step(self, n=1):
+        B.check(B.lib().wcs_step(self.h, n), self.h)
+
+    def sync(self):
+        B.check(B.lib().wcs_sync(self.h), self.h)
+
+    def export_field(self, f, out=None, dtype=np.float64):
+        """Decoded field f ([ny][nx]); f = -1 gives all fields.  `out` may be a
+        CUDA tensor (device export) or a host numpy array."""
+        shape = ((self.F,) if f < 0 else ()) + (self.G[1], self.G[0])
+        dt = 0 if np.dtype(dtype) == np.float64 else 1
+        if out is None:
+            out = np.empty(shape, dtype=dtype)
+        if hasattr(out, "data_ptr"):
+            B.check(B.lib().wcs_export_field(self.h, f, out.data_ptr(), 1 if out.is_cuda else 0, dt), self.h)
+        else:
+            B.check(B.lib().wcs_export_field(self.h, f, out.ctypes.data, 0, dt), self.h)
+        return out
+
+    def compressed_bytes(self):
+        return B.lib().wcs_compressed_bytes(self.h)
+
+    def stats(self):
+        s = B.StepStats()
+        B.check(B.lib().wcs_stats(self.h, C.byref(s)), self.h)
+        return {"step": s.step, "time": s.time, "field_sum": np.array(s.field_sum[:self.F]), "mass": s.mass,
+                "momentum": np.array(s.momentum[:2]), "energy": s.energy, "smax": s.smax,
+                "live_bytes": s.live_bytes, "resident_bytes": s.resident_bytes,
+                "uncompressed_bytes": s.uncompressed_bytes, "status": s.status}
+
+    def record(self, p):
+        n = C.c_int64()
+        B.lib().wcs_export_record(self.h, p, None, 0, C.byref(n))
+        buf = C.create_string_buffer(max(n.value, 1))
+        B.check(B.lib().wcs_export_record(self.h, p, buf, n.value, C.byref(n)), self.h)
+        return buf.raw[:n.value]
+
+    @property
+    def stream(self):
+        return B.lib().wcs_stream(self.h)
+
+
+class Dense:
+    """Uncompressed FP32 baseline of the same scheme."""
+
+    def __init__(self, scheme, nx, ny, periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, stream=None):
+        o = B.Opts()
+        o.tau, o.cfl, o.gamma = tau, cfl, gamma
+        o.cuda_stream = _stream_ptr(stream)
+        g = _grid(nx, ny, periodic)
+        h = C.c_void_p()
+        st = B.lib().wcs_dense_create(C.byref(g), B.SCHEME[scheme], C.byref(o), C.byref(h))
+        if st != 0:
+            raise B.WcsError(st, "dense baseline create failed")
+        self.h = h
+        self.F = 9 if scheme == "d2q9" else 4
+        self.G = tuple(n if per else n + 1 for n, per in zip((nx, ny), periodic))
+
+    def close(self):
+        if getattr(self, "h", None):
+            B.lib().wcs_dense_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def init_macro(self, fields):
+        keep, arr, dev = _field_ptrs(fields)
+        st = B.lib().wcs_dense_init_macro(self.h, arr, len(fields), dev)
+        if st != 0:
+            raise B.WcsError(st, "dense init failed")
+
+    def step(self, n=1):
+        st = B.lib().wcs_dense_step(self.h, n)
+        if st != 0:
+            raise B.WcsError(st, "dense step failed")
+
+    def export_field(self, f, dtype=np.float64):
+        out = np.empty((self.G[1], self.G[0]), dtype=dtype)
+        st = B.lib().wcs_dense_export_field(self.h, f, out.ctypes.data, 0, 0 if np.dtype(dtype) == np.float64 else 1)
+        if st != 0:
+            raise B.WcsError(st, "dense export failed")
+        return out
+
+    def nbytes(self):
+        return B.lib().wcs_dense_bytes(self.h)

@@ -1,0 +1,140 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle on the
+same seeded inputs.  FP64 runs must match byte for byte (records) and bit for
+bit (fields); FP32 runs match the FP32 instantiation of the oracle bit for bit
+and the FP64 oracle within a relative L2 of 1e-5."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2302_09883_gb300 import Dense, Sim, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_pair(scheme, wavelet, n, P, L, eps, prec, store, steps, fields, periodic=(True, True), tau=0.8,
+             cfl=0.4, arena=0.5, check_records_at=()):
+    g = Sim(scheme, wavelet, n, n, P, L, eps, prec=prec, store=store, periodic=periodic, tau=tau, cfl=cfl,
+            arena_factor=arena)
+    o = O.OracleSim(scheme, wavelet, n, n, P, L, eps, prec=prec, store=store, periodic=periodic, tau=tau, cfl=cfl)
+    g.init_macro(fields)
+    o.init_macro(fields)
+    done = 0
+    for s in sorted(set([0] + list(check_records_at) + [steps])):
+        g.step(s - done)
+        o.step(s - done)
+        done = s
+        g.sync()
+        for p in range(g.npatch):
+            assert g.record(p) == o.record(p), "patch %d record differs after %d steps" % (p, s)
+    return g, o
+
+
+def test_d2q9_haar_fp64_128_full_run_bit_exact():
+    # Haar, FP64, 128^2 periodic, 16 patches of 32^2, 3 levels, eps 1e-4,
+    # 100 steps, Gaussian bump: records byte-identical, fields bit-identical.
+    f = inputs.gaussian_bump(128)
+    g, o = run_pair("d2q9", "haar", 128, 32, 3, 1e-4, "f64", "f64", 100, f, check_records_at=(1, 10, 50))
+    assert np.array_equal(g.export_field(-1), o.export_all())
+    st, so = g.stats(), o.stats()
+    assert np.array_equal(st["field_sum"], so["coef_sums"])
+    m0 = O.OracleSim("d2q9", "haar", 128, 128, 32, 3, 1e-4)
+    m0.init_macro(f)
+    mass0 = m0.stats()["coef_sums"].sum()
+    assert abs(st["mass"] - mass0) <= 1e-12 * mass0
+
+
+def test_d2q9_bl53_fp64_bit_exact_and_conservative():
+    f = inputs.gaussian_bump(128, sigma=6.0)
+    g, o = run_pair("d2q9", "bl53", 128, 32, 3, 1e-4, "f64", "f64", 60, f, check_records_at=(1, 7))
+    assert np.array_equal(g.export_field(-1), o.export_all())
+    assert o.stats()["shared_mismatch"] == 0
+    st = g.stats()
+    o0 = O.OracleSim("d2q9", "bl53", 128, 128, 32, 3, 1e-4)
+    o0.init_macro(f)
+    m0 = o0.stats()["coef_sums"].sum()
+    assert abs(st["mass"] - m0) <= 1e-12 * m0
+
+
+@pytest.mark.parametrize("store", ["bf16", "f32", "i8"])
+def test_d2q9_bl53_fp32_matches_fp32_oracle_bitwise(store):
+    # 256^2 (4x4 patches of 64 cells, 4 levels), shear wave + noise, tau 0.6.
+    f = inputs.shear_wave(256, seed=1)
+    g, o = run_pair("d2q9", "bl53", 256, 64, 4, 1e-4, "f32", store, 20, f, tau=0.6, check_records_at=(1, 5))
+    assert np.array_equal(g.export_field(-1), o.export_all())
+
+
+def test_d2q9_fp32_bf16_against_fp64_oracle():
+    f = inputs.shear_wave(256, seed=2)
+    g = Sim("d2q9", "bl53", 256, 256, 64, 4, 1e-4, prec="f32", store="bf16", tau=0.6)
+    o = O.OracleSim("d2q9", "bl53", 256, 256, 64, 4, 1e-4, prec="f64", store="f64", tau=0.6)
+    g.init_macro(f)
+    o.init_macro(f)
+    g.step(30)
+    o.step(30)
+    a, b = g.export_field(-1), o.export_all()
+    for i in range(9):
+        assert rel_l2(a[i], b[i]) < 1e-5
+
+
+def test_d2q9_single_patch_per_axis_and_eps_zero():
+    # one periodic patch per axis: the patch is its own neighbour on all
+    # sides; eps = 0 keeps every coefficient.
+    f = inputs.gaussian_bump(64, sigma=5.0)
+    g, o = run_pair("d2q9", "bl53", 64, 64, 4, 0.0, "f32", "f32", 10, f, tau=0.7, arena=2.0)
+    assert np.array_equal(g.export_field(-1), o.export_all())
+    r = O.OracleRef("d2q9", "bl53", 64, 64, prec="f64", tau=0.7)
+    r.init_macro(f)
+    r.step(10)
+    assert rel_l2(g.export_field(0), r.export_field(0)) < 1e-6
+
+
+def test_dense_baseline_matches_oracle_reference():
+    f = inputs.shear_wave(256, seed=3)
+    d = Dense("d2q9", 256, 256, tau=0.6)
+    r = O.OracleRef("d2q9", "bl53", 256, 256, prec="f32", tau=0.6)
+    d.init_macro(f)
+    r.init_macro(f)
+    d.step(25)
+    r.step(25)
+    for i in range(9):
+        assert np.array_equal(d.export_field(i), r.export_field(i))
+
+
+def test_euler_fp32_i8_matches_fp32_oracle_bitwise():
+    f = inputs.four_quadrant(256)
+    g, o = run_pair("euler2d", "bl53", 256, 64, 4, 1e-3, "f32", "i8", 20, f, periodic=(False, False), cfl=0.4,
+                    check_records_at=(1, 5))
+    assert np.array_equal(g.export_field(-1), o.export_all())
+
+
+def test_euler_fp64_bit_exact():
+    f = inputs.four_quadrant(128)
+    g, o = run_pair("euler2d", "bl53", 128, 32, 3, 1e-3, "f64", "f64", 20, f, periodic=(False, False), cfl=0.4,
+                    check_records_at=(1,))
+    assert np.array_equal(g.export_field(-1), o.export_all())
+    assert abs(g.stats()["time"] - o.stats()["time"]) <= 1e-15
+
+
+def test_euler_dense_baseline_matches_oracle_reference():
+    f = inputs.four_quadrant(256)
+    d = Dense("euler2d", 256, 256, periodic=(False, False), cfl=0.4)
+    r = O.OracleRef("euler2d", "bl53", 256, 256, prec="f32", periodic=(False, False), cfl=0.4)
+    d.init_macro(f)
+    r.init_macro(f)
+    d.step(15)
+    r.step(15)
+    for q in range(4):
+        assert np.array_equal(d.export_field(q), r.export_field(q))
+
+
+def test_arena_overflow_is_reported_and_state_kept():
+    from paper_2302_09883_gb300._lib import WcsError
+    f = inputs.shear_wave(256, seed=4)
+    g = Sim("d2q9", "bl53", 256, 256, 64, 4, 0.0, prec="f32", store="f32", tau=0.6, arena_factor=0.05)
+    with pytest.raises(WcsError) as ei:
+        g.init_macro(f)
+    assert ei.value.status == 3
