@@ -50,7 +50,7 @@ def lib():
         L.orc_ref_time.restype = dbl
         L.orc_ref_time.argtypes = [vp]
         L.orc_dwt.argtypes = [i32, i32, i64, i32, i32, i32, dp]
-        L.orc_layout.argtypes = [i32, i32, i64, i32, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+        L.orc_layout.argtypes = [i32, i32, i64, i32, C.POINTER(C.c_int32), C.POINTER(C.c_uint8),
                                  C.POINTER(C.c_uint8), C.POINTER(C.c_int64)]
         L.orc_band_factor.restype = dbl
         L.orc_band_factor.argtypes = [i32, i32, i64, i32, i32, i32]
@@ -181,18 +181,20 @@ def dwt(u, wavelet, P, L, inverse=False, prec="f64"):
 
 
 def layout(wavelet, dims, P, L):
-    sizes = np.zeros(5, np.int64)
+    """Per node position (row-major, x fastest): band id, edge-line and
+    coarse flags."""
+    sizes = np.zeros(4, np.int64)
     _check(lib().orc_layout(WAVELET[wavelet], dims, P, L, None, None, None,
                             sizes.ctypes.data_as(C.POINTER(C.c_int64))))
     n = int(sizes[0])
-    pos = np.zeros(n, np.int64)
     band = np.zeros(n, np.int32)
     edge = np.zeros(n, np.uint8)
-    _check(lib().orc_layout(WAVELET[wavelet], dims, P, L, pos.ctypes.data_as(C.POINTER(C.c_int64)),
-                            band.ctypes.data_as(C.POINTER(C.c_int32)), edge.ctypes.data_as(C.POINTER(C.c_uint8)),
+    coarse = np.zeros(n, np.uint8)
+    _check(lib().orc_layout(WAVELET[wavelet], dims, P, L, band.ctypes.data_as(C.POINTER(C.c_int32)),
+                            edge.ctypes.data_as(C.POINTER(C.c_uint8)), coarse.ctypes.data_as(C.POINTER(C.c_uint8)),
                             sizes.ctypes.data_as(C.POINTER(C.c_int64))))
-    return {"canon_pos": pos, "band": band, "edge": edge.astype(bool), "n_all": n, "n_c": int(sizes[1]),
-            "n_d": int(sizes[2]), "n_w": int(sizes[3]), "nb": int(sizes[4])}
+    return {"band": band, "edge": edge.astype(bool), "coarse": coarse.astype(bool), "n_all": n,
+            "n_c": int(sizes[1]), "n_w": int(sizes[2]), "nb": int(sizes[3])}
 
 
 def band_factor(wavelet, dims, P, L, band, rule):

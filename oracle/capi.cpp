@@ -218,15 +218,15 @@ int orc_dwt(int wavelet, int dims, int64_t P, int L, int inverse, int prec, doub
   });
 }
 
-// Canonical layout: canon_pos[n_all], band[n_all], edge[n_all]; sizes[0..4]
-// = n_all, n_c, n_d, n_w, nb.
-int orc_layout(int wavelet, int dims, int64_t P, int L, int64_t* canon_pos, int32_t* band, uint8_t* edge,
+// Per node position of a patch: band, edge-line flag, coarse flag;
+// sizes[0..3] = n_all, n_c, n_w, nb.
+int orc_layout(int wavelet, int dims, int64_t P, int L, int32_t* band, uint8_t* edge, uint8_t* coarse,
                int64_t* sizes) {
   return guard([&] {
     Layout lay(wavelet, dims, P, L);
-    sizes[0] = lay.n_all; sizes[1] = lay.n_c; sizes[2] = lay.n_d; sizes[3] = lay.n_w; sizes[4] = lay.nb;
-    if (canon_pos)
-      for (int64_t i = 0; i < lay.n_all; ++i) { canon_pos[i] = lay.canon_pos[i]; band[i] = lay.canon_band[i]; edge[i] = lay.canon_edge[i]; }
+    sizes[0] = lay.n_all; sizes[1] = lay.n_c; sizes[2] = lay.n_w; sizes[3] = lay.nb;
+    if (band)
+      for (int64_t i = 0; i < lay.n_all; ++i) { band[i] = lay.pos_band[i]; edge[i] = lay.pos_edge[i]; coarse[i] = lay.pos_coarse[i]; }
   });
 }
 

@@ -13,17 +13,22 @@
 //    for the first level of details").  Parity unpinned for accumulation and
 //    capped (no number in the paper fixes them).
 //  * Sec. 2.3.1: the lossless stage stores only the surviving values plus
-//    their positions (the paper uses CSR).  Here positions are a bitmask over
-//    the canonical detail order with a presence bitmap over its 32-bit words.
+//    their positions (the paper uses CSR).  Here positions are a bitmask in
+//    "row order" over the in-place nodes of the patch (the layout of the
+//    paper's optimised kernels, Sec. 3.2.4, samples and details interleaved):
+//    each x-row of nodes k_x in [0, P) takes ceil(P/32) whole 32-bit words,
+//    rows in row-major order of the other axes; with BL5/3 the shared face
+//    k_x = P follows as one bit per row.  A presence bitmap marks the
+//    non-zero mask words; survivors are stored in bit order.
 //  * Quantisation (not in the paper): BF16 round-to-nearest-even with a
 //    per-band power-of-two scale, or int8 rint(d/s) with s = max|d|/127 per
 //    band.  Coefficients on a patch edge line (node index 0 or P along some
 //    axis, BL5/3 only) are never quantised: both patches sharing that line
 //    must decode it bit-identically so that the shared nodes agree.
 //
-// Canonical order: bands are tuples (c_x, c_y[, c_z]) of per-axis classes,
-// ordered lexicographically with c_x slowest; band (0,..,0) is the coarse
-// block; inside a band, row-major with x fastest.
+// Bands are tuples (c_x, c_y[, c_z]) of per-axis classes (0 = coarse sample,
+// m = detail of level m), numbered lexicographically with c_x slowest; band
+// 0 is the coarse block, stored densely in row-major order of its nodes.
 //
 // Record byte format (little endian), written identically by the CUDA path:
 //   header   16 B : u32 nbytes, u32 patch, u32 nfields, u32 flags
@@ -32,10 +37,11 @@
 //     coarse[n_c]            compute type T
 //     (BF16/I8 only) u32 bandmask[2], f32 scale[popcount(bandmask)]
 //     presence[n_pw]         u32, bit w set iff mask word w is non-zero
-//     words[nwords]          u32, the non-zero mask words in order
+//     words[nwords]          u32, the non-zero mask words in order (bit p of
+//                            the mask = node p of the patch survives)
 //     zero pad to 8 B
-//     edge[nedge]            T, edge-line survivors in canonical order
-//     int[nint]              storage type, the other survivors
+//     edge[nedge]            T, edge-line survivors in node order
+//     int[nint]              storage type, the other survivors in node order
 //     zero pad to 16 B
 #pragma once
 #include <algorithm>
@@ -61,11 +67,12 @@ struct Layout {
   int64_t P = 0, E = 0, n_all = 0;
   int nb = 0;
   std::vector<std::array<int, 3>> band_cls;
-  std::vector<int64_t> band_size, band_off;
-  int64_t n_c = 0, n_d = 0, n_w = 0, n_pw = 0;
-  std::vector<int64_t> canon_pos;  // canonical index -> flat in-place index
-  std::vector<int> canon_band;
-  std::vector<uint8_t> canon_edge;
+  int64_t n_c = 0, n_w = 0, n_pw = 0;
+  std::vector<int> pos_band;          // band of every node position
+  std::vector<uint8_t> pos_edge, pos_coarse;
+  std::vector<int64_t> coarse_pos;    // coarse positions in row-major order
+  int64_t rows = 0, wr = 0;           // x-rows, mask words per row
+  std::vector<int64_t> bit_pos;       // mask bit -> node position (-1: padding)
 
   Layout() = default;
   Layout(int wavelet_, int dims_, int64_t P_, int L_) : wavelet(wavelet_), dims(dims_), L(L_), P(P_) {
@@ -76,46 +83,44 @@ struct Layout {
     for (int a = 0; a < dims; ++a) nb *= (L + 1);
     for (int b = 0; b < nb; ++b) {
       std::array<int, 3> c{0, 0, 0};
-      // c_x slowest: decompose b with the last axis fastest
-      int r = b;
+      int r = b;  // c_x slowest: the last axis varies fastest
       for (int a = dims - 1; a >= 0; --a) { c[a] = r % (L + 1); r /= (L + 1); }
       band_cls.push_back(c);
     }
-    int64_t off = 0;
-    for (int b = 0; b < nb; ++b) {
-      int64_t sz = 1;
-      for (int a = 0; a < dims; ++a) sz *= class_size(wavelet, P, band_cls[b][a], L);
-      band_size.push_back(sz);
-      band_off.push_back(off);
-      off += sz;
-    }
-    if (off != n_all) throw std::runtime_error("layout: band sizes do not cover the patch");
-    n_c = band_size[0];
-    n_d = n_all - n_c;
-    n_w = (n_d + 31) / 32;
-    n_pw = (n_w + 31) / 32;
-    canon_pos.resize(n_all);
-    canon_band.resize(n_all);
-    canon_edge.resize(n_all);
-    for (int b = 0; b < nb; ++b) {
-      int64_t sz[3] = {1, 1, 1};
-      for (int a = 0; a < dims; ++a) sz[a] = class_size(wavelet, P, band_cls[b][a], L);
-      for (int64_t i = 0; i < band_size[b]; ++i) {
-        int64_t idx[3] = {i % sz[0], (i / sz[0]) % sz[1], i / (sz[0] * sz[1])};
-        int64_t pos = 0, mul = 1;
-        bool edge = false;
-        for (int a = 0; a < dims; ++a) {
-          const int64_t k = class_pos(band_cls[b][a], idx[a], L);
-          if (wavelet == BL53 && (k == 0 || k == P)) edge = true;
-          pos += k * mul;
-          mul *= E;
-        }
-        const int64_t ci = band_off[b] + i;
-        canon_pos[ci] = pos;
-        canon_band[ci] = b;
-        canon_edge[ci] = edge ? 1 : 0;
+    pos_band.resize(n_all);
+    pos_edge.resize(n_all);
+    pos_coarse.resize(n_all);
+    for (int64_t p = 0; p < n_all; ++p) {
+      int64_t r = p;
+      int b = 0;
+      bool edge = false, coarse = true;
+      int cls[3] = {0, 0, 0};
+      for (int a = 0; a < dims; ++a) {
+        const int64_t k = r % E;
+        r /= E;
+        cls[a] = pos_class(k, L);
+        if (cls[a] != 0) coarse = false;
+        if (wavelet == BL53 && (k == 0 || k == P)) edge = true;
       }
+      for (int a = 0; a < dims; ++a) b = b * (L + 1) + cls[a];
+      pos_band[p] = b;
+      pos_edge[p] = edge ? 1 : 0;
+      pos_coarse[p] = coarse ? 1 : 0;
+      if (coarse) coarse_pos.push_back(p);
     }
+    n_c = int64_t(coarse_pos.size());
+    // row order of the mask bits
+    rows = n_all / E;
+    wr = (P + 31) / 32;
+    const int64_t row_bits = rows * wr * 32;
+    const int64_t face_bits = E > P ? rows : 0;
+    bit_pos.assign(row_bits + (face_bits + 31) / 32 * 32, -1);
+    for (int64_t r = 0; r < rows; ++r) {
+      for (int64_t kx = 0; kx < P; ++kx) bit_pos[r * wr * 32 + kx] = r * E + kx;
+      if (E > P) bit_pos[row_bits + r] = r * E + P;
+    }
+    n_w = int64_t(bit_pos.size()) / 32;
+    n_pw = (n_w + 31) / 32;
   }
 };
 
@@ -193,21 +198,22 @@ std::vector<uint8_t> encode_patch(const Layout& lay, const std::vector<std::vect
     }
     std::vector<uint32_t> words(lay.n_w, 0);
     std::vector<T> edge_vals;
-    std::vector<int64_t> int_idx;  // canonical indices of interior survivors
+    std::vector<int64_t> int_idx;  // positions of interior survivors
     std::vector<float> bmax(lay.nb, 0.0f);
     std::vector<uint8_t> bpresent(lay.nb, 0);
-    for (int64_t d = 0; d < lay.n_d; ++d) {
-      const int64_t ci = lay.n_c + d;
-      const T v = c[lay.canon_pos[ci]];
-      const int b = lay.canon_band[ci];
-      const bool edge = lay.canon_edge[ci] != 0;
+    for (int64_t bit = 0; bit < lay.n_w * 32; ++bit) {
+      const int64_t p = lay.bit_pos[bit];
+      if (p < 0 || lay.pos_coarse[p]) continue;
+      const T v = c[p];
+      const int b = lay.pos_band[p];
+      const bool edge = lay.pos_edge[p] != 0;
       const T t = edge ? tau_e[b] : tau[b];
       if (!(std::fabs(v) >= t)) continue;  // zeroed (NaN never survives)
-      words[d / 32] |= (1u << (d % 32));
+      words[bit / 32] |= (1u << (bit % 32));
       if (edge) {
         edge_vals.push_back(v);
       } else {
-        int_idx.push_back(ci);
+        int_idx.push_back(p);
         bpresent[b] = 1;
         bmax[b] = std::max(bmax[b], float(std::fabs(v)));
       }
@@ -215,7 +221,7 @@ std::vector<uint8_t> encode_patch(const Layout& lay, const std::vector<std::vect
     put<uint32_t>(buf, 16 + 16 * f + 0, uint32_t(off));
     int64_t p = off;
     for (int64_t i = 0; i < lay.n_c; ++i) {
-      put<T>(buf, p, c[lay.canon_pos[i]]);
+      put<T>(buf, p, c[lay.coarse_pos[i]]);
       p += sizeof(T);
     }
     std::vector<float> scale(lay.nb, 0.0f);
@@ -245,9 +251,9 @@ std::vector<uint8_t> encode_patch(const Layout& lay, const std::vector<std::vect
       if (words[w]) { put<uint32_t>(buf, p, words[w]); p += 4; }
     p = align_up(p, 8);
     for (const T& v : edge_vals) { put<T>(buf, p, v); p += sizeof(T); }
-    for (int64_t ci : int_idx) {
-      const T v = c[lay.canon_pos[ci]];
-      const int b = lay.canon_band[ci];
+    for (int64_t pi : int_idx) {
+      const T v = c[pi];
+      const int b = lay.pos_band[pi];
       if (store == S_F64) { put<double>(buf, p, double(v)); p += 8; }
       else if (store == S_F32) { put<float>(buf, p, float(v)); p += 4; }
       else if (store == S_BF16) {
@@ -297,7 +303,7 @@ std::vector<std::vector<T>> decode_patch(const Layout& lay, const uint8_t* rec, 
     const uint32_t nint = get<uint32_t>(rec, nbytes, 16 + 16 * f + 12);
     std::vector<T>& c = out[f];
     int64_t p = off;
-    for (int64_t i = 0; i < lay.n_c; ++i) { c[lay.canon_pos[i]] = get<T>(rec, nbytes, p); p += sizeof(T); }
+    for (int64_t i = 0; i < lay.n_c; ++i) { c[lay.coarse_pos[i]] = get<T>(rec, nbytes, p); p += sizeof(T); }
     std::vector<float> scale(lay.nb, 0.0f);
     if (quant) {
       const uint64_t bm = uint64_t(get<uint32_t>(rec, nbytes, p)) | (uint64_t(get<uint32_t>(rec, nbytes, p + 4)) << 32);
@@ -315,12 +321,13 @@ std::vector<std::vector<T>> decode_patch(const Layout& lay, const uint8_t* rec, 
     p = align_up(p, 8);
     int64_t pe = p, pi = p + int64_t(nedge) * int64_t(sizeof(T));
     uint32_t ne = 0, ni = 0;
-    for (int64_t d = 0; d < lay.n_d; ++d) {
-      if (!(words[d / 32] & (1u << (d % 32)))) continue;
-      const int64_t ci = lay.n_c + d;
-      const int b = lay.canon_band[ci];
+    for (int64_t bit = 0; bit < lay.n_w * 32; ++bit) {
+      if (!(words[bit / 32] & (1u << (bit % 32)))) continue;
+      const int64_t q = lay.bit_pos[bit];
+      if (q < 0 || lay.pos_coarse[q]) throw std::runtime_error("record: mask bit on a coarse or padding node");
+      const int b = lay.pos_band[q];
       T v;
-      if (lay.canon_edge[ci]) { v = get<T>(rec, nbytes, pe); pe += sizeof(T); ++ne; }
+      if (lay.pos_edge[q]) { v = get<T>(rec, nbytes, pe); pe += sizeof(T); ++ne; }
       else {
         if (store == S_F64) { v = T(get<double>(rec, nbytes, pi)); pi += 8; }
         else if (store == S_F32) { v = T(get<float>(rec, nbytes, pi)); pi += 4; }
@@ -328,7 +335,7 @@ std::vector<std::vector<T>> decode_patch(const Layout& lay, const uint8_t* rec, 
         else { v = T(float(get<int8_t>(rec, nbytes, pi)) * scale[b]); pi += 1; }
         ++ni;
       }
-      c[lay.canon_pos[ci]] = v;
+      c[q] = v;
     }
     if (ne != nedge || ni != nint) throw std::runtime_error("record: survivor count mismatch");
   }

@@ -271,7 +271,10 @@ template <class T> struct Sim {
 
   // Mass (trapezoid-weighted sum) of every field from the coarse blocks alone:
   // the details carry no mass (eq. conservation), so 2^(L*dims) times the
-  // trapezoid sum of the coarse samples is the patch mass.
+  // trapezoid sum of the coarse samples is the patch mass.  FP64, in one
+  // fixed order: coarse sample c (row-major) goes to partial sum c mod 32
+  // (added in increasing c), then the 32 partials are added pairwise
+  // (slot i += slot i+16, then +8, +4, +2, +1); patches are added in order.
   std::vector<double> coef_sums() const {
     std::vector<double> s(F, 0.0);
     const int64_t nc1 = class_size(grid.wavelet, P, 0, L);
@@ -280,18 +283,20 @@ template <class T> struct Sim {
       const auto& r = rec[pid];
       for (int f = 0; f < F; ++f) {
         const int64_t off = get<uint32_t>(r.data(), int64_t(r.size()), 16 + 16 * f);
-        double acc = 0;
-        for (int64_t iy = 0; iy < nc1; ++iy)
-          for (int64_t ix = 0; ix < nc1; ++ix) {
-            double w = 1.0;
-            if (grid.wavelet == BL53) {
-              if (ix == 0 || ix == nc1 - 1) w *= 0.5;
-              if (iy == 0 || iy == nc1 - 1) w *= 0.5;
-            }
-            const T v = get<T>(r.data(), int64_t(r.size()), off + int64_t(sizeof(T)) * (iy * nc1 + ix));
-            acc += w * double(v);
+        double part[32] = {0};
+        for (int64_t c = 0; c < nc1 * nc1; ++c) {
+          const int64_t iy = c / nc1, ix = c % nc1;
+          double w = 1.0;
+          if (grid.wavelet == BL53) {
+            if (ix == 0 || ix == nc1 - 1) w *= 0.5;
+            if (iy == 0 || iy == nc1 - 1) w *= 0.5;
           }
-        s[f] += acc * scale;
+          const T v = get<T>(r.data(), int64_t(r.size()), off + int64_t(sizeof(T)) * c);
+          part[c % 32] = part[c % 32] + w * double(v);
+        }
+        for (int o = 16; o >= 1; o /= 2)
+          for (int i = 0; i < o; ++i) part[i] = part[i] + part[i + o];
+        s[f] += part[0] * scale;
       }
     }
     return s;

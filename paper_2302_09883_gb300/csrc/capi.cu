@@ -7,8 +7,7 @@
 //   ring[2]    ghost rings exported by every patch for the next step
 //   ctl        cursors, max signal speed, time, sticky status
 //   pstats     FP64 coarse-block sums per patch and field
-//   tables     canonical order -> shared-memory tile offset, band, edge bits,
-//              threshold multiplier per band (Sec. 2.2)
+//   bfactor    threshold multiplier per band (Sec. 2.2)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -57,17 +56,6 @@ const std::vector<KernelEntry>& kernels() {
   return v;
 }
 
-int pos_class(int k, int L) {
-  if (k % (1 << L) == 0) return 0;
-  int m = 1;
-  while (((k >> (m - 1)) & 1) == 0) ++m;
-  return m;
-}
-int class_pos(int c, int i, int L) { return c == 0 ? (i << L) : ((2 * i + 1) << (c - 1)); }
-int class_size(int wavelet, int P, int c, int L) {
-  if (c == 0) return wavelet == WCS_BL53 ? (P >> L) + 1 : (P >> L);
-  return P >> c;
-}
 }  // namespace
 
 struct wcs_sim {
@@ -76,7 +64,7 @@ struct wcs_sim {
   int64_t n[2] = {0, 0};
   int per[2] = {1, 1};
   int64_t G[2] = {0, 0};
-  int npx = 0, npy = 0, npatch = 0, F = 0, E = 0, NC1 = 0, nc = 0, nd = 0, nw = 0, nb = 0;
+  int npx = 0, npy = 0, npatch = 0, F = 0, E = 0, NC1 = 0, nc = 0, nb = 0;
   size_t tsize = 8;
   KernelEntry ke;
   cudaStream_t stream = nullptr;
@@ -86,9 +74,6 @@ struct wcs_sim {
   void* ring[2] = {nullptr, nullptr};
   wcs::Ctl* ctl = nullptr;
   double* pstats = nullptr;
-  unsigned short* canon_tile = nullptr;
-  unsigned char* canon_band = nullptr;
-  unsigned int* edgew = nullptr;
   double* bfactor = nullptr;
   int64_t nstep = 0;
   bool inited = false;
@@ -132,9 +117,6 @@ static wcs::PatchArgs base_args(const wcs_sim* s) {
   a.cap_out = s->cap;
   a.ctl = s->ctl;
   a.pstats = s->pstats;
-  a.canon_tile = s->canon_tile;
-  a.canon_band = s->canon_band;
-  a.edgew = s->edgew;
   a.band_factor = s->bfactor;
   a.eps = s->eps;
   a.eps_edge = s->eps;
@@ -199,34 +181,14 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
   s->E = s->wavelet == WCS_BL53 ? patch + 1 : patch;
   s->NC1 = (patch >> levels) + (s->wavelet == WCS_BL53 ? 1 : 0);
   s->nc = s->NC1 * s->NC1;
-  s->nd = s->E * s->E - s->nc;
-  s->nw = (s->nd + 31) / 32;
   s->nb = (levels + 1) * (levels + 1);
   s->tsize = s->prec == WCS_FP64 ? 8 : 4;
 
-  // ---- canonical layout tables (bands (c_x, c_y), c_x slowest, row-major)
-  const int nall = s->E * s->E, pw = ke->pitch;
-  std::vector<unsigned short> ctile(nall);
-  std::vector<unsigned char> cband(nall);
-  std::vector<unsigned int> ew(s->nw, 0u);
+  // ---- threshold multiplier of each band (c_x slowest; Sec. 2.2)
   std::vector<double> bf(s->nb);
-  int ci = 0;
   for (int cx = 0; cx <= levels; ++cx)
     for (int cy = 0; cy <= levels; ++cy) {
       const int b = cx * (levels + 1) + cy;
-      const int sx = class_size(s->wavelet, patch, cx, levels), sy = class_size(s->wavelet, patch, cy, levels);
-      for (int iy = 0; iy < sy; ++iy)
-        for (int ix = 0; ix < sx; ++ix) {
-          const int kx = class_pos(cx, ix, levels), ky = class_pos(cy, iy, levels);
-          ctile[ci] = (unsigned short)(ky * pw + kx);
-          cband[ci] = (unsigned char)b;
-          const bool edge = s->wavelet == WCS_BL53 && (kx == 0 || kx == patch || ky == 0 || ky == patch);
-          if (ci >= s->nc && edge) {
-            const int d = ci - s->nc;
-            ew[d / 32] |= 1u << (d % 32);
-          }
-          ++ci;
-        }
       int sum = 0, mx = 0;
       for (int c : {cx, cy}) {
         const int m = c == 0 ? levels : c;
@@ -235,7 +197,6 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
       }
       bf[b] = s->rule == WCS_RULE_CONST ? 1.0 : (s->rule == WCS_RULE_ACCUM ? std::ldexp(1.0, -sum) : std::ldexp(1.0, -(mx - 1)));
     }
-  (void)pos_class;
 
   wcs_status st;
   const size_t state_bytes = size_t(s->F) * size_t(s->G[0]) * size_t(s->G[1]) * s->tsize;
@@ -248,16 +209,10 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
   }
   if ((st = dalloc(s, (void**)&s->ctl, sizeof(wcs::Ctl))) != WCS_OK) goto bad;
   if ((st = dalloc(s, (void**)&s->pstats, size_t(s->npatch) * s->F * 8)) != WCS_OK) goto bad;
-  if ((st = dalloc(s, (void**)&s->canon_tile, nall * 2)) != WCS_OK) goto bad;
-  if ((st = dalloc(s, (void**)&s->canon_band, nall)) != WCS_OK) goto bad;
-  if ((st = dalloc(s, (void**)&s->edgew, size_t(s->nw) * 4)) != WCS_OK) goto bad;
   if ((st = dalloc(s, (void**)&s->bfactor, size_t(s->nb) * 8)) != WCS_OK) goto bad;
   {
     cudaError_t e;
-    if ((e = cudaMemcpy(s->canon_tile, ctile.data(), nall * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(s->canon_band, cband.data(), nall, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(s->edgew, ew.data(), size_t(s->nw) * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(s->bfactor, bf.data(), size_t(s->nb) * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+    if ((e = cudaMemcpy(s->bfactor, bf.data(), size_t(s->nb) * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(s->ctl, 0, sizeof(wcs::Ctl))) != cudaSuccess) {
       st = cuda_fail(s, e, "table upload");
       goto bad;
@@ -282,9 +237,6 @@ void wcs_destroy(wcs_sim* s) {
   }
   cudaFree(s->ctl);
   cudaFree(s->pstats);
-  cudaFree(s->canon_tile);
-  cudaFree(s->canon_band);
-  cudaFree(s->edgew);
   cudaFree(s->bfactor);
   delete s;
 }

@@ -44,26 +44,30 @@ template <typename T> __device__ __forceinline__ constexpr T bl53_alpha(int k, i
   return (k == 0 || k == K - 1) ? T(0.5) : T(0.25);
 }
 
+// a*b + c with one rounding; the lifting multiplies only by 1/2 or 1/4, so
+// a*b is exact and this equals the separately rounded (a*b) + c.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <int WV, int P, int LEV, int L, typename T> __device__ __forceinline__ void fwd_levels(T* v) {
   if constexpr (LEV <= L) {
     constexpr int st = 1 << (LEV - 1);
     constexpr int K = (P / st) / 2;
     if constexpr (WV == WV_BL53) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] - T(0.5) * (v[2 * k * st] + v[(2 * k + 2) * st]);
+      for (int k = 0; k < K; ++k)
+        v[(2 * k + 1) * st] = fma_rn(T(-0.5), v[2 * k * st] + v[(2 * k + 2) * st], v[(2 * k + 1) * st]);
 #pragma unroll
       for (int k = 1; k < K; ++k) {
-        T e = v[2 * k * st];
-        e = e + bl53_alpha<T>(k - 1, K) * v[(2 * k - 1) * st];
-        e = e + bl53_alpha<T>(k, K) * v[(2 * k + 1) * st];
-        v[2 * k * st] = e;
+        const T e = fma_rn(bl53_alpha<T>(k - 1, K), v[(2 * k - 1) * st], v[2 * k * st]);
+        v[2 * k * st] = fma_rn(bl53_alpha<T>(k, K), v[(2 * k + 1) * st], e);
       }
     } else {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const T a = v[2 * k * st], b = v[(2 * k + 1) * st];
         const T d = b - a;
-        v[2 * k * st] = a + T(0.5) * d;
+        v[2 * k * st] = fma_rn(T(0.5), d, a);
         v[(2 * k + 1) * st] = d;
       }
     }
@@ -78,23 +82,58 @@ template <int WV, int P, int LEV, typename T> __device__ __forceinline__ void in
     if constexpr (WV == WV_BL53) {
 #pragma unroll
       for (int k = 1; k < K; ++k) {
-        T e = v[2 * k * st];
-        e = e - bl53_alpha<T>(k - 1, K) * v[(2 * k - 1) * st];
-        e = e - bl53_alpha<T>(k, K) * v[(2 * k + 1) * st];
-        v[2 * k * st] = e;
+        const T e = fma_rn(-bl53_alpha<T>(k - 1, K), v[(2 * k - 1) * st], v[2 * k * st]);
+        v[2 * k * st] = fma_rn(-bl53_alpha<T>(k, K), v[(2 * k + 1) * st], e);
       }
 #pragma unroll
-      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] + T(0.5) * (v[2 * k * st] + v[(2 * k + 2) * st]);
+      for (int k = 0; k < K; ++k)
+        v[(2 * k + 1) * st] = fma_rn(T(0.5), v[2 * k * st] + v[(2 * k + 2) * st], v[(2 * k + 1) * st]);
     } else {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const T s = v[2 * k * st], d = v[(2 * k + 1) * st];
-        const T a = s - T(0.5) * d;
+        const T a = fma_rn(T(-0.5), d, s);
         v[2 * k * st] = a;
         v[(2 * k + 1) * st] = a + d;
       }
     }
     inv_levels<WV, P, LEV - 1, T>(v);
+  }
+}
+
+// Forward lifting that hands every node to cb(y) as soon as its value is
+// final: the details of each level right after that level, then the coarse
+// samples.  Lets a caller threshold and store while the line streams.
+template <int WV, int P, int LEV, int L, typename T, typename CB>
+__device__ __forceinline__ void fwd_levels_cb(T* v, CB& cb) {
+  if constexpr (LEV <= L) {
+    constexpr int st = 1 << (LEV - 1);
+    constexpr int K = (P / st) / 2;
+    if constexpr (WV == WV_BL53) {
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        v[(2 * k + 1) * st] = fma_rn(T(-0.5), v[2 * k * st] + v[(2 * k + 2) * st], v[(2 * k + 1) * st]);
+#pragma unroll
+      for (int k = 1; k < K; ++k) {
+        const T e = fma_rn(bl53_alpha<T>(k - 1, K), v[(2 * k - 1) * st], v[2 * k * st]);
+        v[2 * k * st] = fma_rn(bl53_alpha<T>(k, K), v[(2 * k + 1) * st], e);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const T a = v[2 * k * st], b = v[(2 * k + 1) * st];
+        const T d = b - a;
+        v[2 * k * st] = fma_rn(T(0.5), d, a);
+        v[(2 * k + 1) * st] = d;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) cb((2 * k + 1) * st);
+    fwd_levels_cb<WV, P, LEV + 1, L, T, CB>(v, cb);
+  } else {
+    constexpr int E = WV == WV_BL53 ? P + 1 : P;
+#pragma unroll
+    for (int y = 0; y < E; y += (1 << L)) cb(y);
   }
 }
 

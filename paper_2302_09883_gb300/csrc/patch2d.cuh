@@ -1,25 +1,28 @@
 // Fused compressed-patch time step for 2-D schemes: one CTA owns one patch
 // for the whole step, every intermediate lives in shared memory.
 //
-//   stage record (16-B vector loads) -> decode (bitmask prefix popcounts,
-//   dequantise) -> inverse tensor lifting -> ghost ring from the neighbours'
-//   exports -> scheme (D2Q9 collide in place + pull via per-population shifted
-//   windows, or the Rusanov FV update) -> forward tensor lifting -> threshold
-//   (ballot), quantise, compact (warp prefix sums), bump-allocate and write the
-//   record -> re-decode the stored coefficients in place -> export the ghost
-//   ring the neighbours need next step (post-collision populations for D2Q9)
-//   and FP64 per-patch sums of the coarse blocks.
+//   stage record (16-B vector loads) -> decode (zero the tiles, scatter the
+//   coarse block and the survivors of the non-zero mask words only) ->
+//   inverse tensor lifting -> ghost ring from the neighbours' exports ->
+//   scheme (D2Q9 collide in place + pull via per-population shifted windows,
+//   or the Rusanov FV update) -> forward tensor lifting -> threshold over the
+//   node order with warp ballots -> prefix sums, bump-allocate, write the
+//   record (survivors only) and the dequantised values back in place ->
+//   re-decode -> export the ghost ring the neighbours need next step
+//   (post-collision populations for D2Q9) and FP64 coarse-block sums.
 //
-// The record byte format, canonical coefficient order, threshold rules and
-// quantisers are those of the paper's compression pipeline (Sec. 2: DWT of
-// Sec. 2.1.2, hard threshold of Sec. 2.2, a bitmask + values lossless stage
-// in place of Sec. 2.3's CSR):
+// Record byte format (the paper's pipeline, Sec. 2: DWT of Sec. 2.1.2, hard
+// threshold of Sec. 2.2, a bitmask + values lossless stage in place of
+// Sec. 2.3's CSR):
 //   header 16 B: u32 nbytes, u32 patch, u32 nfields, u32 flags
 //   table 16 B per field: u32 offset, u32 nwords, u32 nedge, u32 nint
-//   per field (16-B aligned): coarse[NC] (T); BF16/I8: u32 bandmask[2] and
-//   f32 scale per present band; presence bitmap over the mask words; the
-//   non-zero mask words; pad to 8; edge-line survivors (T); other survivors
-//   (storage type); pad to 16.
+//   per field (16-B aligned): coarse[NC] (T, row-major coarse nodes);
+//   BF16/I8: u32 bandmask[2] and f32 scale per present band; presence
+//   bitmap over the mask words; the non-zero mask words; pad to 8; edge-line
+//   survivors (T); other survivors (storage type); pad to 16.  Mask bits
+//   are in row order: each row y of nodes x in [0, P) takes WR = ceil(P/32)
+//   whole words (rows in order), then (BL5/3) the shared column x = P, one
+//   bit per row; survivors are stored in bit order.
 #pragma once
 #include "common.cuh"
 
@@ -38,9 +41,6 @@ struct PatchArgs {
   Ctl* ctl;
   int cur_out, cur_rst, smax_rd, smax_wr, smax_rst;
   double* pstats;               // npatch * F coarse-block sums
-  const unsigned short* canon_tile;  // canonical index -> ky*PW + kx
-  const unsigned char* canon_band;
-  const unsigned int* edgew;    // per mask word: bits of edge-line coefficients
   const double* band_factor;    // threshold multiplier per band
   double eps, eps_edge;
   const double* eps_patch;      // optional per-patch threshold constant
@@ -64,33 +64,74 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   static constexpr int NC1 = (P >> L) + (WV == WV_BL53 ? 1 : 0);
   static constexpr int NC = NC1 * NC1;
   static constexpr int NALL = E * E;
-  static constexpr int ND = NALL - NC;
-  static constexpr int NW = (ND + 31) / 32;
+  static constexpr int WR = (P + 31) / 32;        // mask words per row
+  static constexpr int NRW = E * WR;              // row words
+  static constexpr int NCW = E > P ? (E + 31) / 32 : 0;  // column x = P words
+  static constexpr int NW = NRW + NCW;
   static constexpr int NPW = (NW + 31) / 32;
   static constexpr int NB = (L + 1) * (L + 1);
   static constexpr bool QUANT = ST == ST_BF16 || ST == ST_I8;
   typedef typename StoreType<ST>::type S;
   static constexpr int SB = sizeof(S);
   static constexpr int RING = SCH == SCH_D2Q9 ? 12 * E + 4 : 16 * E;
-  static constexpr int NT = 512;
+  static constexpr int NT = sizeof(T) == 8 ? 512 : 768;
   static constexpr int NWARP = NT / 32;
   static constexpr int XLO = WV == WV_BL53 ? 1 : 0;
   static constexpr int XHI = P - 1;
+  static constexpr int LMASK = (1 << L) - 1;
   // shared memory carve-up (bytes)
   static constexpr size_t OFF_MW = size_t(NTILE) * TS * sizeof(T);
   static constexpr size_t OFF_PRE = OFF_MW + size_t(F) * NW * 4;
-  static constexpr size_t OFF_BMAX = (OFF_PRE + size_t(3) * F * NW * 2 + 15) / 16 * 16;
+  static constexpr size_t OFF_EMW = (OFF_PRE + size_t(3) * F * NW * 2 + 15) / 16 * 16;
+  static constexpr size_t OFF_BMAX = OFF_EMW + size_t(F) * NW * 4;
   static constexpr size_t OFF_SCL = OFF_BMAX + size_t(F) * NB * 4;
   static constexpr size_t OFF_SINV = OFF_SCL + size_t(F) * NB * 4;
   static constexpr size_t OFF_TAU = (OFF_SINV + size_t(F) * NB * 4 + 15) / 16 * 16;
   static constexpr size_t OFF_FINFO = OFF_TAU + size_t(2) * NB * sizeof(T);
-  static constexpr size_t OFF_MISC = OFF_FINFO + size_t(F) * 8 * 4;
-  static constexpr size_t OFF_STAGE = (OFF_MISC + 64 * 4 + 15) / 16 * 16;
+  static constexpr size_t OFF_MISC = OFF_FINFO + size_t(F) * 16 * 4;  // 64 ints + 2F window offsets
+  static constexpr size_t OFF_STAGE = (OFF_MISC + (64 + 2 * F) * 4 + 15) / 16 * 16;
   static constexpr size_t SMEM_MAX = 232448;
   static constexpr size_t STG = (SMEM_MAX - OFF_STAGE) / 16 * 16 > 49152 ? 49152 : (SMEM_MAX - OFF_STAGE) / 16 * 16;
   static constexpr size_t SMEM = OFF_STAGE + STG;
   static_assert(OFF_STAGE + 4096 <= SMEM_MAX, "patch does not fit in shared memory");
 };
+
+// Per-axis class of node index k after L levels: 0 = coarse sample, m =
+// detail of level m (k = 2^(m-1) mod 2^m).
+template <int L> __host__ __device__ __forceinline__ constexpr int node_class(int k) {
+  int c = 0;  // the lowest set bit below 2^L decides; folds for constant k
+#pragma unroll
+  for (int m = L; m >= 1; --m)
+    if (k & (1 << (m - 1))) c = m;
+  return c;
+}
+
+// Edge-line bits of mask word w (BL5/3: nodes with x or y in {0, P}); coarse
+// nodes may be included, they never carry a mask bit.
+template <int WV, int P, int E, int WR> __device__ __forceinline__ unsigned int word_edges(int w) {
+  if constexpr (WV != WV_BL53) return 0u;
+  if (w < E * WR) {
+    const int y = w / WR, h = w - y * WR;
+    const int n = P - 32 * h;
+    const unsigned int vm = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+    return (y == 0 || y == P) ? vm : (h == 0 ? 1u : 0u);
+  }
+  const int n = E - 32 * (w - E * WR);
+  return n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+}
+
+// Node of mask bit `lane` of word w (row order); valid = not padding.
+template <int P, int E, int WR> __device__ __forceinline__ void word_node(int w, int lane, int& kx, int& ky, bool& valid) {
+  if (w < E * WR) {
+    ky = w / WR;
+    kx = 32 * (w - ky * WR) + lane;
+    valid = kx < P;
+  } else {
+    kx = P;
+    ky = 32 * (w - E * WR) + lane;
+    valid = ky < E;
+  }
+}
 
 template <typename U> __device__ __forceinline__ U ldr(const unsigned char* p) { return *reinterpret_cast<const U*>(p); }
 template <typename U> __device__ __forceinline__ void stg(unsigned char* p, U v) { *reinterpret_cast<U*>(p) = v; }
@@ -98,17 +139,18 @@ template <typename U> __device__ __forceinline__ void stg(unsigned char* p, U v)
 __device__ __forceinline__ unsigned long long dbl_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
 template <int SCH, int WV, typename T, int ST, int P, int L, int MODE>
-__global__ void __launch_bounds__(512, 1) patch_kernel(PatchArgs a) {
+__global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1) patch_kernel(PatchArgs a) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
   typedef typename C::S S;
-  constexpr int F = C::F, E = C::E, PW = C::PW, TS = C::TS, NC = C::NC, ND = C::ND, NW = C::NW, NPW = C::NPW,
-                NB = C::NB, NT = C::NT, NWARP = C::NWARP;
+  constexpr int F = C::F, E = C::E, PW = C::PW, TS = C::TS, NC = C::NC, NW = C::NW, NPW = C::NPW, NB = C::NB,
+                NT = C::NT, NWARP = C::NWARP, NALL = C::NALL;
   extern __shared__ __align__(16) unsigned char smem[];
   T* tiles = reinterpret_cast<T*>(smem);
   unsigned int* mw = reinterpret_cast<unsigned int*>(smem + C::OFF_MW);
   unsigned short* pre_e = reinterpret_cast<unsigned short*>(smem + C::OFF_PRE);
   unsigned short* pre_i = pre_e + F * NW;
-  unsigned short* pre_w = pre_i + F * NW;
+  unsigned short* plist = pre_i + F * NW;  // non-zero mask words, in order
+  unsigned int* emw_sm = reinterpret_cast<unsigned int*>(smem + C::OFF_EMW);  // edge bits per present word
   unsigned int* bmax = reinterpret_cast<unsigned int*>(smem + C::OFF_BMAX);
   float* scl = reinterpret_cast<float*>(smem + C::OFF_SCL);
   float* sinv = reinterpret_cast<float*>(smem + C::OFF_SINV);
@@ -124,37 +166,97 @@ __global__ void __launch_bounds__(512, 1) patch_kernel(PatchArgs a) {
   const T omega = T(a.omega), gamma = T(a.gamma), gm1 = T(a.gamma - 1.0);
 
   // Window of field f: where node (0,0) of the state being read (in) or
-  // written (out) sits in shared memory.
-  auto win_in = [&](int f) -> int { return f * TS + PW + 1; };
-  auto win_out = [&](int f) -> int {
+  // written (out) sits in shared memory (D2Q9 step: the out window of
+  // population i is shifted by -c_i, which is the pull streaming).
+  int* woff_in = misc + 64;
+  int* woff_out = woff_in + F;
+  if (tid < F) {
+    const int f = tid;
+    woff_in[f] = f * TS + PW + 1;
+    int o;
     if constexpr (SCH == SCH_D2Q9) {
-      if constexpr (MODE == MODE_STEP) return f * TS + (1 - d2q9_cy(f)) * PW + (1 - d2q9_cx(f));
-      else return f * TS + PW + 1;
+      if constexpr (MODE == MODE_STEP) o = f * TS + (1 - d2q9_cy(f)) * PW + (1 - d2q9_cx(f));
+      else o = f * TS + PW + 1;
     } else {
-      if constexpr (MODE == MODE_EXPORT) return f * TS + PW + 1;
-      else return (F + f) * TS + PW + 1;
+      if constexpr (MODE == MODE_EXPORT) o = f * TS + PW + 1;
+      else o = (F + f) * TS + PW + 1;
     }
-  };
+    woff_out[f] = o;
+  }
+  auto win_in = [&](int f) -> int { return woff_in[f]; };
+  auto win_out = [&](int f) -> int { return woff_out[f]; };
+  // per-lane classes of the x nodes this lane covers in a row (loop invariant)
+  int cls_x[C::WR];
+#pragma unroll
+  for (int h = 0; h < C::WR; ++h) cls_x[h] = node_class<L>(32 * h + lane);
 
-  // ----------------------------------------------------------- housekeeping
+  // ------------------------------------------ early global reads (STEP)
+  // The status word (a failed earlier step freezes the state) and the ghost
+  // ring values are fetched into registers now so that their latency hides
+  // behind the record staging and the decode.
+  constexpr int NGH = SCH == SCH_D2Q9 ? 12 * E + 4 : 16 * E;  // ghost cells to fill
+  constexpr int NG = (NGH + NT - 1) / NT;
+  T gv[NG];
+  int gdst[NG], gsrc[NG];  // ghost tile index (-1: none); own-node source for outflow copies (-1: ring value)
+  unsigned int status0 = 0u;
   if constexpr (MODE == MODE_STEP) {
-    // A failed earlier step freezes the state: read the status once per block
-    // so that every thread takes the same branch.
-    if (tid == 0) misc[63] = int(*((volatile unsigned int*)&a.ctl->status));
-    __syncthreads();
-    if (misc[63] & int(STAT_ARENA_FULL | STAT_NAN | STAT_BAD_RECORD)) return;
-    if (pid == 0 && tid == 0) {
-      a.ctl->live[a.cur_rst] = a.ctl->cursor[a.cur_rst];
-      a.ctl->cursor[a.cur_rst] = 0ull;
-      if constexpr (SCH == SCH_EULER2D) {
-        const double smax = __longlong_as_double((long long)a.ctl->smax[a.smax_rd]);
-        a.ctl->time += a.cfl / smax / double(a.ncell_x);
+    if (tid == 0) status0 = *((volatile unsigned int*)&a.ctl->status);
+    const int pxm = (px - 1 + a.npx) % a.npx, pxp = (px + 1) % a.npx;
+    const int pym = (py - 1 + a.npy) % a.npy, pyp = (py + 1) % a.npy;
+    const T* rin = reinterpret_cast<const T*>(a.ring_in);
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const int t = tid + g * NT;
+      gdst[g] = -1;
+      gsrc[g] = -1;
+      gv[g] = T(0);
+      if (t >= NGH) continue;
+      if constexpr (SCH == SCH_D2Q9) {
+        if (t < 12 * E) {
+          const int sd = t / (3 * E), r = t - sd * 3 * E, k = r / 3, j = r - 3 * k;
+          int pop, x, y;
+          if (sd == 0) {  // west ghost column <- west neighbour's east strip {1,5,8}
+            pop = j == 0 ? 1 : (j == 1 ? 5 : 8); x = -1; y = k; gv[g] = rin[size_t(py * a.npx + pxm) * C::RING + 3 * E + 3 * k + j];
+          } else if (sd == 1) {  // east ghost column <- east neighbour's west strip {3,6,7}
+            pop = j == 0 ? 3 : (j == 1 ? 6 : 7); x = E; y = k; gv[g] = rin[size_t(py * a.npx + pxp) * C::RING + 3 * k + j];
+          } else if (sd == 2) {  // south ghost row <- south neighbour's north strip {2,5,6}
+            pop = j == 0 ? 2 : (j == 1 ? 5 : 6); x = k; y = -1; gv[g] = rin[size_t(pym * a.npx + px) * C::RING + 9 * E + 3 * k + j];
+          } else {  // north ghost row <- north neighbour's south strip {4,7,8}
+            pop = j == 0 ? 4 : (j == 1 ? 7 : 8); x = k; y = E; gv[g] = rin[size_t(pyp * a.npx + px) * C::RING + 6 * E + 3 * k + j];
+          }
+          gdst[g] = pop * TS + PW + 1 + y * PW + x;
+        } else {  // diagonal corners: the one population streaming inward
+          const int c = t - 12 * E;
+          if (c == 0) { gdst[g] = 5 * TS; gv[g] = rin[size_t(pym * a.npx + pxm) * C::RING + 12 * E + 2]; }
+          else if (c == 1) { gdst[g] = 6 * TS + E + 1; gv[g] = rin[size_t(pym * a.npx + pxp) * C::RING + 12 * E + 3]; }
+          else if (c == 2) { gdst[g] = 7 * TS + (E + 1) * PW + E + 1; gv[g] = rin[size_t(pyp * a.npx + pxp) * C::RING + 12 * E + 0]; }
+          else { gdst[g] = 8 * TS + (E + 1) * PW; gv[g] = rin[size_t(pyp * a.npx + pxm) * C::RING + 12 * E + 1]; }
+        }
       } else {
-        a.ctl->time += 1.0;
+        const int sd = t / (4 * E), r = t - sd * 4 * E, k = r / 4, q = r - 4 * k;
+        const int base = q * TS + PW + 1;
+        if (sd == 0) {
+          gdst[g] = base + k * PW - 1;
+          if (a.per_x || px > 0) gv[g] = rin[size_t(py * a.npx + pxm) * C::RING + 4 * E + 4 * k + q];
+          else gsrc[g] = base + k * PW;
+        } else if (sd == 1) {
+          gdst[g] = base + k * PW + E;
+          if (a.per_x || px < a.npx - 1) gv[g] = rin[size_t(py * a.npx + pxp) * C::RING + 4 * k + q];
+          else gsrc[g] = base + k * PW + (E - 1);
+        } else if (sd == 2) {
+          gdst[g] = base - PW + k;
+          if (a.per_y || py > 0) gv[g] = rin[size_t(pym * a.npx + px) * C::RING + 12 * E + 4 * k + q];
+          else gsrc[g] = base + k;
+        } else {
+          gdst[g] = base + E * PW + k;
+          if (a.per_y || py < a.npy - 1) gv[g] = rin[size_t(pyp * a.npx + px) * C::RING + 8 * E + 4 * k + q];
+          else gsrc[g] = base + (E - 1) * PW + k;
+        }
       }
-      a.ctl->smax[a.smax_rst] = 0ull;
     }
   }
+
+  if constexpr (MODE == MODE_INIT) __syncthreads();
 
   // ------------------------------------------------------ decode (in state)
   if constexpr (MODE == MODE_STEP || MODE == MODE_EXPORT) {
@@ -166,8 +268,31 @@ __global__ void __launch_bounds__(512, 1) patch_kernel(PatchArgs a) {
       const uint4* src = reinterpret_cast<const uint4*>(R);
       uint4* dst = reinterpret_cast<uint4*>(stage);
       for (int i = tid; i < nbytes / 16; i += NT) dst[i] = __ldg(src + i);
-      __syncthreads();
       R = stage;
+    }
+    if constexpr (MODE == MODE_STEP) {
+      if (tid == 0) misc[63] = int(status0);
+    }
+    __syncthreads();
+    if constexpr (MODE == MODE_STEP) {
+      if (misc[63] & int(STAT_ARENA_FULL | STAT_NAN | STAT_BAD_RECORD)) return;
+      if (pid == 0 && tid == 0) {
+        a.ctl->live[a.cur_rst] = a.ctl->cursor[a.cur_rst];
+        a.ctl->cursor[a.cur_rst] = 0ull;
+        if constexpr (SCH == SCH_EULER2D) {
+          const double smax = __longlong_as_double((long long)a.ctl->smax[a.smax_rd]);
+          a.ctl->time += a.cfl / smax / double(a.ncell_x);
+        } else {
+          a.ctl->time += 1.0;
+        }
+        a.ctl->smax[a.smax_rst] = 0ull;
+      }
+    }
+    {  // zero every tile: the details that were not stored are zeros
+      uint4* z = reinterpret_cast<uint4*>(tiles);
+      constexpr int NZ = int(size_t(F) * TS * sizeof(T) / 16), NREM = int(size_t(F) * TS - NZ * 16 / sizeof(T));
+      for (int i = tid; i < NZ; i += NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (tid < NREM) tiles[size_t(F) * TS - NREM + tid] = T(0);
     }
     if (tid < F) {
       const int f = tid;
@@ -179,88 +304,95 @@ __global__ void __launch_bounds__(512, 1) patch_kernel(PatchArgs a) {
         bm1 = ldr<unsigned int>(R + p + 4);
         p += 8 + 4 * (__popc(bm0) + __popc(bm1));
       }
-      const int p_pres = p;
       const int nwords = int(ldr<unsigned int>(R + 16 + 16 * f + 4));
       const int nedge = int(ldr<unsigned int>(R + 16 + 16 * f + 8));
-      const int p_edge = (p_pres + 4 * NPW + 4 * nwords + 7) & ~7;
-      int* fi = finfo + 8 * f;
+      const int p_edge = (p + 4 * NPW + 4 * nwords + 7) & ~7;
+      int* fi = finfo + 16 * f;
       fi[0] = off;
-      fi[1] = p_pres;
+      fi[1] = p;  // presence bitmap
       fi[2] = p_edge;
       fi[3] = p_edge + nedge * int(sizeof(T));
       fi[4] = int(bm0);
       fi[5] = int(bm1);
+      fi[6] = nwords;
     }
     __syncthreads();
-    // mask words and per-word survivor counts
-    for (int t = tid; t < F * NW; t += NT) {
-      const int f = t / NW, w = t - f * NW;
-      const int p_pres = finfo[8 * f + 1];
-      const unsigned int pres = ldr<unsigned int>(R + p_pres + 4 * (w >> 5));
-      unsigned int word = 0;
-      if ((pres >> (w & 31)) & 1u) {
-        int rank = __popc(pres & ((1u << (w & 31)) - 1u));
-        for (int j = 0; j < (w >> 5); ++j) rank += __popc(ldr<unsigned int>(R + p_pres + 4 * j));
-        word = ldr<unsigned int>(R + p_pres + 4 * NPW + 4 * rank);
-      }
-      const unsigned int em = __ldg(a.edgew + w);
-      mw[t] = word;
-      pre_e[t] = (unsigned short)__popc(word & em);
-      pre_i[t] = (unsigned short)__popc(word & ~em);
+    // coarse block (row-major over the coarse nodes)
+    for (int t = tid; t < F * NC; t += NT) {
+      const int f = t / NC, c = t - f * NC;
+      const int iy = c / C::NC1, ix = c - iy * C::NC1;
+      tiles[win_in(f) + (iy << L) * PW + (ix << L)] = ldr<T>(R + finfo[16 * f] + c * int(sizeof(T)));
     }
-    __syncthreads();
+    // present mask words: word index, survivor prefix counts (warp per field)
     if (warp < F) {
+      const int f = warp, *fi = finfo + 16 * f;
+      const int nwords = fi[6], p_pres = fi[1];
       unsigned ce = 0, ci = 0;
-      for (int b0 = 0; b0 < NW; b0 += 32) {
-        const int w = b0 + lane;
-        const unsigned ve = w < NW ? pre_e[warp * NW + w] : 0u, vi = w < NW ? pre_i[warp * NW + w] : 0u;
+      for (int j0 = 0; j0 < nwords; j0 += 32) {
+        const int j = j0 + lane;
+        unsigned ve = 0, vi = 0;
+        int w = 0;
+        unsigned int word = 0;
+        if (j < nwords) {
+          int r = j;
+          for (int k = 0; k < NPW; ++k) {
+            const unsigned int pres = ldr<unsigned int>(R + p_pres + 4 * k);
+            const int c = __popc(pres);
+            if (r < c) {
+              w = 32 * k + __fns(pres, 0, r + 1);
+              break;
+            }
+            r -= c;
+          }
+          word = ldr<unsigned int>(R + p_pres + 4 * NPW + 4 * j);
+        }
+        const unsigned int em_mine = word_edges<WV, P, E, C::WR>(w);
+        if (j < nwords) {
+          ve = __popc(word & em_mine);
+          vi = __popc(word & ~em_mine);
+          emw_sm[f * NW + j] = em_mine;
+        }
         const unsigned ie = warp_incl_scan(ve), ii = warp_incl_scan(vi);
-        if (w < NW) {
-          pre_e[warp * NW + w] = (unsigned short)(ce + ie - ve);
-          pre_i[warp * NW + w] = (unsigned short)(ci + ii - vi);
+        if (j < nwords) {
+          plist[f * NW + j] = (unsigned short)w;
+          mw[f * NW + j] = word;
+          pre_e[f * NW + j] = (unsigned short)(ce + ie - ve);
+          pre_i[f * NW + j] = (unsigned short)(ci + ii - vi);
         }
         ce += __shfl_sync(0xffffffffu, ie, 31);
         ci += __shfl_sync(0xffffffffu, ii, 31);
       }
     }
     __syncthreads();
-    // coarse block
-    for (int t = tid; t < F * NC; t += NT) {
-      const int f = t / NC, c = t - f * NC;
-      tiles[win_in(f) + __ldg(a.canon_tile + c)] = ldr<T>(R + finfo[8 * f] + c * int(sizeof(T)));
-    }
-    // details: one warp per mask word, one lane per bit
-    for (int t = warp; t < F * NW; t += NWARP) {
-      const int f = t / NW, w = t - f * NW;
-      const int d = 32 * w + lane;
-      if (d < ND) {
-        const int ci = NC + d;
-        const unsigned int word = mw[t];
-        T v = T(0);
-        if ((word >> lane) & 1u) {
-          const unsigned int em = __ldg(a.edgew + w), lt = (1u << lane) - 1u;
-          const int* fi = finfo + 8 * f;
-          if ((em >> lane) & 1u) {
-            v = ldr<T>(R + fi[2] + (pre_e[t] + __popc(word & em & lt)) * int(sizeof(T)));
+    // survivors: one warp per non-zero mask word, one lane per node
+    for (int f = 0; f < F; ++f) {
+      const int* fi = finfo + 16 * f;
+      for (int j = warp; j < fi[6]; j += NWARP) {
+        const unsigned int word = mw[f * NW + j];
+        if (!((word >> lane) & 1u)) continue;
+        const int w = plist[f * NW + j];
+        int kx, ky;
+        bool valid;
+        word_node<P, E, C::WR>(w, lane, kx, ky, valid);
+        const unsigned int em = emw_sm[f * NW + j], lt = (1u << lane) - 1u;
+        T v;
+        if ((em >> lane) & 1u) {
+          v = ldr<T>(R + fi[2] + int(pre_e[f * NW + j] + __popc(word & em & lt)) * int(sizeof(T)));
+        } else {
+          const int idx = pre_i[f * NW + j] + __popc(word & ~em & lt);
+          const S q = ldr<S>(R + fi[3] + idx * C::SB);
+          if constexpr (ST == ST_F64 || ST == ST_F32) {
+            v = T(q);
           } else {
-            const int idx = pre_i[t] + __popc(word & ~em & lt);
-            const S q = ldr<S>(R + fi[3] + idx * C::SB);
-            if constexpr (ST == ST_F64 || ST == ST_F32) {
-              v = T(q);
-            } else {
-              const int b = __ldg(a.canon_band + ci);
-              const unsigned long long bm = (unsigned long long)(unsigned int)fi[4] | ((unsigned long long)(unsigned int)fi[5] << 32);
-              const int si = __popcll(bm & ((1ull << b) - 1ull));
-              const float s = ldr<float>(R + fi[0] + NC * int(sizeof(T)) + 8 + 4 * si);
-              if constexpr (ST == ST_BF16) {
-                v = T(__uint_as_float((unsigned int)q << 16) * s);
-              } else {
-                v = T(float(q) * s);
-              }
-            }
+            const int b = node_class<L>(kx) * (L + 1) + node_class<L>(ky);
+            const unsigned long long bm = (unsigned long long)(unsigned int)fi[4] | ((unsigned long long)(unsigned int)fi[5] << 32);
+            const int si = __popcll(bm & ((1ull << b) - 1ull));
+            const float sc = ldr<float>(R + fi[0] + NC * int(sizeof(T)) + 8 + 4 * si);
+            if constexpr (ST == ST_BF16) v = T(__uint_as_float((unsigned int)q << 16) * sc);
+            else v = T(float(q) * sc);
           }
         }
-        tiles[win_in(f) + __ldg(a.canon_tile + ci)] = v;
+        tiles[win_in(f) + ky * PW + kx] = v;
       }
     }
     __syncthreads();
@@ -295,37 +427,10 @@ __global__ void __launch_bounds__(512, 1) patch_kernel(PatchArgs a) {
 
   // -------------------------------------------------------- ghosts + scheme
   if constexpr (MODE == MODE_STEP) {
-    const int pxm = (px - 1 + a.npx) % a.npx, pxp = (px + 1) % a.npx;
-    const int pym = (py - 1 + a.npy) % a.npy, pyp = (py + 1) % a.npy;
-    const T* rin = reinterpret_cast<const T*>(a.ring_in);
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+      if (gdst[g] >= 0) tiles[gdst[g]] = gsrc[g] >= 0 ? tiles[gsrc[g]] : gv[g];
     if constexpr (SCH == SCH_D2Q9) {
-      const T* rW = rin + size_t(py * a.npx + pxm) * C::RING;
-      const T* rE = rin + size_t(py * a.npx + pxp) * C::RING;
-      const T* rS = rin + size_t(pym * a.npx + px) * C::RING;
-      const T* rN = rin + size_t(pyp * a.npx + px) * C::RING;
-      for (int t = tid; t < 12 * E + 4; t += NT) {
-        if (t < 12 * E) {
-          const int s = t / (3 * E), r = t - s * 3 * E, k = r / 3, j = r - 3 * k;
-          int pop, x, y;
-          T v;
-          if (s == 0) {  // west ghost column <- west neighbour's east strip {1,5,8}
-            pop = j == 0 ? 1 : (j == 1 ? 5 : 8); x = -1; y = k; v = rW[3 * E + 3 * k + j];
-          } else if (s == 1) {  // east ghost column <- east neighbour's west strip {3,6,7}
-            pop = j == 0 ? 3 : (j == 1 ? 6 : 7); x = E; y = k; v = rE[3 * k + j];
-          } else if (s == 2) {  // south ghost row <- south neighbour's north strip {2,5,6}
-            pop = j == 0 ? 2 : (j == 1 ? 5 : 6); x = k; y = -1; v = rS[9 * E + 3 * k + j];
-          } else {  // north ghost row <- north neighbour's south strip {4,7,8}
-            pop = j == 0 ? 4 : (j == 1 ? 7 : 8); x = k; y = E; v = rN[6 * E + 3 * k + j];
-          }
-          tiles[win_in(pop) + y * PW + x] = v;
-        } else {
-          const int c = t - 12 * E;
-          if (c == 0) tiles[win_in(5) - PW - 1] = rin[size_t(pym * a.npx + pxm) * C::RING + 12 * E + 2];
-          else if (c == 1) tiles[win_in(6) - PW + E] = rin[size_t(pym * a.npx + pxp) * C::RING + 12 * E + 3];
-          else if (c == 2) tiles[win_in(7) + E * PW + E] = rin[size_t(pyp * a.npx + pxp) * C::RING + 12 * E + 0];
-          else tiles[win_in(8) + E * PW - 1] = rin[size_t(pyp * a.npx + pxm) * C::RING + 12 * E + 1];
-        }
-      }
       // BGK collision of every own node, in place
       for (int t = tid; t < E * E; t += NT) {
         const int y = t / E, x = t - y * E;
@@ -338,27 +443,6 @@ __global__ void __launch_bounds__(512, 1) patch_kernel(PatchArgs a) {
       }
       __syncthreads();
     } else {
-      for (int t = tid; t < 4 * E * 4; t += NT) {
-        const int s = t / (4 * E), r = t - s * 4 * E, k = r / 4, q = r - 4 * k;
-        int x, y;
-        T v;
-        if (s == 0) {
-          x = -1; y = k;
-          v = (a.per_x || px > 0) ? rin[size_t(py * a.npx + pxm) * C::RING + 4 * E + 4 * k + q] : tiles[win_in(q) + k * PW];
-        } else if (s == 1) {
-          x = E; y = k;
-          v = (a.per_x || px < a.npx - 1) ? rin[size_t(py * a.npx + pxp) * C::RING + 4 * k + q]
-                                          : tiles[win_in(q) + k * PW + (E - 1)];
-        } else if (s == 2) {
-          x = k; y = -1;
-          v = (a.per_y || py > 0) ? rin[size_t(pym * a.npx + px) * C::RING + 12 * E + 4 * k + q] : tiles[win_in(q) + k];
-        } else {
-          x = k; y = E;
-          v = (a.per_y || py < a.npy - 1) ? rin[size_t(pyp * a.npx + px) * C::RING + 8 * E + 4 * k + q]
-                                          : tiles[win_in(q) + (E - 1) * PW + k];
-        }
-        tiles[win_in(q) + y * PW + x] = v;
-      }
       __syncthreads();
       const double smax = __longlong_as_double((long long)a.ctl->smax[a.smax_rd]);
       const T lam = T(a.cfl / smax);
@@ -404,15 +488,10 @@ __global__ void __launch_bounds__(512, 1) patch_kernel(PatchArgs a) {
     __syncthreads();
   }
 
-  // -------------------------------------------------- forward tensor lifting
+  // ------------------------------------------ forward tensor lifting (x)
   for (int t = tid; t < F * E; t += NT) {
     const int f = t / E, y = t - f * E;
     line_transform<WV, P, L, false, T>(tiles + win_out(f) + y * PW, 1);
-  }
-  __syncthreads();
-  for (int t = tid; t < F * E; t += NT) {
-    const int f = t / E, x = t - f * E;
-    line_transform<WV, P, L, false, T>(tiles + win_out(f) + x, PW);
   }
   // thresholds of this patch (Sec. 2.2), in the compute type
   if (tid < NB) {
@@ -423,54 +502,92 @@ __global__ void __launch_bounds__(512, 1) patch_kernel(PatchArgs a) {
   for (int t = tid; t < F * NB; t += NT) bmax[t] = 0u;
   __syncthreads();
 
-  // ------------------------------------------- encode pass 1: masks, counts
+  // ------------- forward lifting (y) fused with the threshold (Sec. 2.2):
+  // warp (f, h) lifts the 32 columns x = 32h + lane of field f in registers,
+  // then for every row y one ballot gives mask word (y, h) directly; the
+  // zeroed details go back to shared memory as zeros.  One more warp does
+  // the shared column x = P of every field (lane = field).
   bool bad = false;
-  for (int t = warp; t < F * NW; t += NWARP) {
-    const int f = t / NW, w = t - f * NW;
-    const int d = 32 * w + lane;
-    const unsigned int em = __ldg(a.edgew + w);
-    bool keep = false;
-    if (d < ND) {
-      const int ci = NC + d;
-      const T v = tiles[win_out(f) + __ldg(a.canon_tile + ci)];
-      const int b = __ldg(a.canon_band + ci);
-      const bool edge = (em >> lane) & 1u;
-      keep = fabs(v) >= (edge ? tau_e[b] : tau_i[b]);
-      if (!isfinite(v)) bad = true;
-      if constexpr (C::QUANT) {
-        if (keep && !edge) atomicMax(bmax + f * NB + b, __float_as_uint(fabsf(float(v))) + 1u);
+  static_assert(F * C::WR + (C::NCW > 0 ? 1 : 0) <= NWARP, "not enough warps for the fused pass");
+  if (warp < F * C::WR) {
+    const int f = warp / C::WR, h = warp - f * C::WR;
+    const int x = 32 * h + lane;
+    const bool valid = x < P;
+    const int cx = cls_x[h];
+    T* col = tiles + win_out(f) + (valid ? x : 0);
+    const T* ti = tau_i + cx * (L + 1);
+    const T* te = tau_e + cx * (L + 1);
+    const bool xedge = WV == WV_BL53 && x == 0;
+    unsigned int myw[(E + 31) / 32];
+#pragma unroll
+    for (int k = 0; k < (E + 31) / 32; ++k) myw[k] = 0u;
+    T v[E];
+#pragma unroll
+    for (int y = 0; y < E; ++y) v[y] = valid ? col[y * PW] : T(0);
+    auto node = [&](int y) {
+      const int cy = node_class<L>(y);
+      bool keep = false;
+      if (valid && (cx | cy)) {
+        const bool edge = xedge || (WV == WV_BL53 && (y == 0 || y == P));
+        keep = fabs(v[y]) >= (edge ? te[cy] : ti[cy]);
+        if (!isfinite(v[y])) bad = true;
+        if constexpr (C::QUANT) {
+          if (keep && !edge) atomicMax(bmax + f * NB + cx * (L + 1) + cy, __float_as_uint(fabsf(float(v[y]))) + 1u);
+        }
+        if (!keep) v[y] = T(0);
+      } else if (valid && !isfinite(v[y])) {
+        bad = true;
       }
+      const unsigned int bal = __ballot_sync(0xffffffffu, keep);
+      if (lane == (y & 31)) myw[y >> 5] = bal;
+      if (valid) col[y * PW] = v[y];
+    };
+    fwd_levels_cb<WV, P, 1, L, T>(v, node);
+#pragma unroll
+    for (int k = 0; k < (E + 31) / 32; ++k) {
+      const int y = 32 * k + lane;
+      if (y < E) mw[f * NW + y * C::WR + h] = myw[k];
     }
-    const unsigned int word = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) {
-      mw[t] = word;
-      pre_e[t] = (unsigned short)__popc(word & em);
-      pre_i[t] = (unsigned short)__popc(word & ~em);
-      pre_w[t] = word ? 1 : 0;
-    }
-  }
-  for (int t = tid; t < F * NC; t += NT) {
-    const int f = t / NC;
-    const T v = tiles[win_out(f) + __ldg(a.canon_tile + t - f * NC)];
-    if (!isfinite(v)) bad = true;
+  } else if (C::NCW > 0 && warp == F * C::WR && lane < F) {
+    const int f = lane;
+    T* col = tiles + win_out(f) + P;
+    unsigned int cw[(E + 31) / 32];
+#pragma unroll
+    for (int k = 0; k < (E + 31) / 32; ++k) cw[k] = 0u;
+    T v[E];
+#pragma unroll
+    for (int y = 0; y < E; ++y) v[y] = col[y * PW];
+    auto node = [&](int y) {
+      const int cy = node_class<L>(y);
+      if (!isfinite(v[y])) bad = true;
+      if (cy) {  // x = P is a coarse x-node; every node of the column is on an edge line
+        if (fabs(v[y]) >= tau_e[cy]) cw[y >> 5] |= 1u << (y & 31);
+        else v[y] = T(0);
+      }
+      col[y * PW] = v[y];
+    };
+    fwd_levels_cb<WV, P, 1, L, T>(v, node);
+#pragma unroll
+    for (int k = 0; k < C::NCW; ++k) mw[f * NW + C::NRW + k] = cw[k];
   }
   if (bad) {
     if (atomicOr(&a.ctl->status, STAT_NAN) == 0u) a.ctl->err_step = int(a.step);
   }
   __syncthreads();
-  // per-field scans and section sizes
+  // per-field scans, list of non-zero words, band scales, section sizes
   if (warp < F) {
     const int f = warp;
     unsigned ce = 0, ci = 0, cw = 0;
     for (int b0 = 0; b0 < NW; b0 += 32) {
       const int w = b0 + lane;
-      const unsigned ve = w < NW ? pre_e[f * NW + w] : 0u, vi = w < NW ? pre_i[f * NW + w] : 0u,
-                     vw = w < NW ? pre_w[f * NW + w] : 0u;
+      const unsigned int word = w < NW ? mw[f * NW + w] : 0u;
+      const unsigned int emw = w < NW ? word_edges<WV, P, E, C::WR>(w) : 0u;
+      const unsigned ve = __popc(word & emw), vi = __popc(word & ~emw), vw = word ? 1u : 0u;
       const unsigned ie = warp_incl_scan(ve), ii = warp_incl_scan(vi), iw = warp_incl_scan(vw);
       if (w < NW) {
         pre_e[f * NW + w] = (unsigned short)(ce + ie - ve);
         pre_i[f * NW + w] = (unsigned short)(ci + ii - vi);
-        pre_w[f * NW + w] = (unsigned short)(cw + iw - vw);
+        if (word) plist[f * NW + cw + iw - 1] = (unsigned short)w;
       }
       ce += __shfl_sync(0xffffffffu, ie, 31);
       ci += __shfl_sync(0xffffffffu, ii, 31);
@@ -502,7 +619,7 @@ __global__ void __launch_bounds__(512, 1) patch_kernel(PatchArgs a) {
       const int p_edge = (p_pres + 4 * NPW + 4 * int(cw) + 7) & ~7;
       const int p_int = p_edge + int(ce) * int(sizeof(T));
       const int size = (p_int + int(ci) * C::SB + 15) & ~15;
-      int* fi = finfo + 8 * f;
+      int* fi = finfo + 16 * f;
       fi[0] = size;
       fi[1] = p_pres;
       fi[2] = p_edge;
@@ -511,15 +628,15 @@ __global__ void __launch_bounds__(512, 1) patch_kernel(PatchArgs a) {
       fi[5] = int(ce);
       fi[6] = int(ci);
       fi[7] = int((unsigned int)(bm & 0xffffffffull));
-      misc[8 + f] = int((unsigned int)(bm >> 32));
+      fi[8] = int((unsigned int)(bm >> 32));
     }
   }
   __syncthreads();
   if (tid == 0) {
     int off = (16 + 16 * F + 15) & ~15;
     for (int f = 0; f < F; ++f) {
-      misc[32 + f] = off;
-      off += finfo[8 * f];
+      finfo[16 * f + 9] = off;
+      off += finfo[16 * f];
     }
     const unsigned long long total = (unsigned long long)off;
     const unsigned long long base = atomicAdd(&a.ctl->cursor[a.cur_out], total);
@@ -539,25 +656,42 @@ __global__ void __launch_bounds__(512, 1) patch_kernel(PatchArgs a) {
   if (!misc[0]) return;
   unsigned char* O = a.arena_out + ((unsigned long long)(unsigned int)misc[2] | ((unsigned long long)(unsigned int)misc[3] << 32));
 
-  // ---------------------------------------------- encode pass 2: the record
+  // ----------------------------- encode pass 2: the record, survivors only
+  // FP64 coarse-block sums: 2^(2L) times the trapezoid sum of the coarse
+  // samples is the patch mass of the field (details carry no mass).  One warp
+  // per field (the last warps, lightly loaded here): coarse sample c goes to
+  // lane c mod 32, then a shuffle tree.  Coarse nodes are read-only in pass 2.
+  if (warp >= NWARP - F) {
+    const int f = warp - (NWARP - F);
+    double acc = 0.0;
+    for (int c = lane; c < NC; c += 32) {
+      const int iy = c / C::NC1, ix = c - iy * C::NC1;
+      double w = 1.0;
+      if constexpr (WV == WV_BL53) {
+        if (ix == 0 || ix == C::NC1 - 1) w *= 0.5;
+        if (iy == 0 || iy == C::NC1 - 1) w *= 0.5;
+      }
+      acc = acc + w * double(tiles[win_out(f) + (iy << L) * PW + (ix << L)]);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc = acc + __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) a.pstats[size_t(pid) * F + f] = acc * double(1ll << (2 * L));
+  }
   if (tid == 0) stg<uint4>(O, make_uint4((unsigned)misc[1], (unsigned)pid, (unsigned)F, a.flags));
   if (tid < F) {
-    const int* fi = finfo + 8 * tid;
-    stg<uint4>(O + 16 + 16 * tid, make_uint4((unsigned)misc[32 + tid], (unsigned)fi[4], (unsigned)fi[5], (unsigned)fi[6]));
-  }
-  {
-    const int npad_hdr = ((16 + 16 * F + 15) & ~15) - (16 + 16 * F);
-    if (tid < npad_hdr) O[16 + 16 * F + tid] = 0;
+    const int* fi = finfo + 16 * tid;
+    stg<uint4>(O + 16 + 16 * tid, make_uint4((unsigned)fi[9], (unsigned)fi[4], (unsigned)fi[5], (unsigned)fi[6]));
   }
   for (int t = tid; t < F * NC; t += NT) {
     const int f = t / NC, c = t - f * NC;
-    stg<T>(O + misc[32 + f] + c * int(sizeof(T)), tiles[win_out(f) + __ldg(a.canon_tile + c)]);
+    const int iy = c / C::NC1, ix = c - iy * C::NC1;
+    stg<T>(O + finfo[16 * f + 9] + c * int(sizeof(T)), tiles[win_out(f) + (iy << L) * PW + (ix << L)]);
   }
   if constexpr (C::QUANT) {
     for (int t = tid; t < F * NB; t += NT) {
       const int f = t / NB, b = t - f * NB;
-      const unsigned long long bm = (unsigned long long)(unsigned int)finfo[8 * f + 7] | ((unsigned long long)(unsigned int)misc[8 + f] << 32);
-      unsigned char* base = O + misc[32 + f] + NC * int(sizeof(T));
+      const unsigned long long bm = (unsigned long long)(unsigned int)finfo[16 * f + 7] | ((unsigned long long)(unsigned int)finfo[16 * f + 8] << 32);
+      unsigned char* base = O + finfo[16 * f + 9] + NC * int(sizeof(T));
       if (b == 0) {
         stg<unsigned int>(base, (unsigned int)(bm & 0xffffffffull));
         stg<unsigned int>(base + 4, (unsigned int)(bm >> 32));
@@ -565,85 +699,69 @@ __global__ void __launch_bounds__(512, 1) patch_kernel(PatchArgs a) {
       if ((bm >> b) & 1ull) stg<float>(base + 8 + 4 * __popcll(bm & ((1ull << b) - 1ull)), scl[t]);
     }
   }
-  for (int t = tid; t < F * NPW; t += NT) {
+  for (int t = warp; t < F * NPW; t += NWARP) {
     const int f = t / NPW, j = t - f * NPW;
-    unsigned int bits = 0;
-    for (int i = 0; i < 32; ++i) {
-      const int w = 32 * j + i;
-      if (w < NW && mw[f * NW + w]) bits |= 1u << i;
-    }
-    stg<unsigned int>(O + misc[32 + f] + finfo[8 * f + 1] + 4 * j, bits);
+    const int w = 32 * j + lane;
+    const unsigned int bits = __ballot_sync(0xffffffffu, w < NW && mw[f * NW + (w < NW ? w : 0)] != 0u);
+    if (lane == 0) stg<unsigned int>(O + finfo[16 * f + 9] + finfo[16 * f + 1] + 4 * j, bits);
   }
-  for (int t = tid; t < F * NW; t += NT) {
-    const int f = t / NW;
-    if (mw[t]) stg<unsigned int>(O + misc[32 + f] + finfo[8 * f + 1] + 4 * NPW + 4 * pre_w[t], mw[t]);
+  for (int f = 0; f < F; ++f) {
+    const int* fi = finfo + 16 * f;
+    for (int j = tid; j < fi[4]; j += NT)
+      stg<unsigned int>(O + fi[9] + fi[1] + 4 * NPW + 4 * j, mw[f * NW + plist[f * NW + j]]);
   }
   if (tid < F) {  // zero padding
-    const int f = tid, *fi = finfo + 8 * f;
-    unsigned char* base = O + misc[32 + f];
+    const int f = tid, *fi = finfo + 16 * f;
+    unsigned char* base = O + fi[9];
     for (int p = fi[1] + 4 * NPW + 4 * fi[4]; p < fi[2]; ++p) base[p] = 0;
     for (int p = fi[3] + fi[6] * C::SB; p < fi[0]; ++p) base[p] = 0;
   }
-  for (int t = warp; t < F * NW; t += NWARP) {
-    const int f = t / NW, w = t - f * NW;
-    const int d = 32 * w + lane;
-    if (d < ND) {
-      const int ci = NC + d;
-      const int to = win_out(f) + __ldg(a.canon_tile + ci);
-      const unsigned int word = mw[t];
-      T back = T(0);
-      if ((word >> lane) & 1u) {
-        const T v = tiles[to];
-        const unsigned int em = __ldg(a.edgew + w), lt = (1u << lane) - 1u;
-        unsigned char* base = O + misc[32 + f];
-        if ((em >> lane) & 1u) {
-          stg<T>(base + finfo[8 * f + 2] + (pre_e[t] + __popc(word & em & lt)) * int(sizeof(T)), v);
-          back = v;
+  for (int f = 0; f < F; ++f) {
+    const int* fi = finfo + 16 * f;
+    for (int j = warp; j < fi[4]; j += NWARP) {
+      const int w = plist[f * NW + j];
+      const unsigned int word = mw[f * NW + w];
+      if (!((word >> lane) & 1u)) continue;
+      int kx, ky;
+      bool valid;
+      word_node<P, E, C::WR>(w, lane, kx, ky, valid);
+      const unsigned int em = word_edges<WV, P, E, C::WR>(w);
+      const bool edge = (em >> lane) & 1u;
+      const unsigned int lt = (1u << lane) - 1u;
+      const int to = win_out(f) + ky * PW + kx;
+      const T v = tiles[to];
+      unsigned char* base = O + fi[9];
+      if (edge) {
+        stg<T>(base + fi[2] + int(pre_e[f * NW + w] + __popc(word & em & lt)) * int(sizeof(T)), v);
+      } else {
+        const int idx = pre_i[f * NW + w] + __popc(word & ~em & lt);
+        unsigned char* dst = base + fi[3] + idx * C::SB;
+        T back;
+        if constexpr (ST == ST_F64 || ST == ST_F32) {
+          const S q = S(v);
+          stg<S>(dst, q);
+          back = T(q);
         } else {
-          const int idx = pre_i[t] + __popc(word & ~em & lt);
-          unsigned char* dst = base + finfo[8 * f + 3] + idx * C::SB;
-          if constexpr (ST == ST_F64 || ST == ST_F32) {
-            const S q = S(v);
-            stg<S>(dst, q);
-            back = T(q);
+          const int b = node_class<L>(kx) * (L + 1) + node_class<L>(ky);
+          const float sc = scl[f * NB + b];
+          if constexpr (ST == ST_BF16) {
+            unsigned short q = 0;
+            if (sc != 0.0f) q = __bfloat16_as_ushort(__float2bfloat16_rn(float(v) * sinv[f * NB + b]));
+            stg<unsigned short>(dst, q);
+            back = T(__uint_as_float((unsigned int)q << 16) * sc);
           } else {
-            const int b = __ldg(a.canon_band + ci);
-            const float s = scl[f * NB + b];
-            if constexpr (ST == ST_BF16) {
-              unsigned short q = 0;
-              if (s != 0.0f) q = __bfloat16_as_ushort(__float2bfloat16_rn(float(v) * sinv[f * NB + b]));
-              stg<unsigned short>(dst, q);
-              back = T(__uint_as_float((unsigned int)q << 16) * s);
-            } else {
-              int q = 0;
-              if (s != 0.0f) {
-                q = __float2int_rn(__fdiv_rn(float(v), s));
-                q = q > 127 ? 127 : (q < -127 ? -127 : q);
-              }
-              stg<signed char>(dst, (signed char)q);
-              back = T(float(q) * s);
+            int q = 0;
+            if (sc != 0.0f) {
+              q = __float2int_rn(__fdiv_rn(float(v), sc));
+              q = q > 127 ? 127 : (q < -127 ? -127 : q);
             }
+            stg<signed char>(dst, (signed char)q);
+            back = T(float(q) * sc);
           }
         }
+        tiles[to] = back;
       }
-      tiles[to] = back;
     }
-  }
-  // FP64 coarse-block sums: 2^(2L) times the trapezoid sum of the coarse
-  // samples is the patch mass of the field (details carry no mass).
-  if (tid < F) {
-    const int f = tid;
-    double acc = 0.0;
-    for (int iy = 0; iy < C::NC1; ++iy)
-      for (int ix = 0; ix < C::NC1; ++ix) {
-        double w = 1.0;
-        if constexpr (WV == WV_BL53) {
-          if (ix == 0 || ix == C::NC1 - 1) w *= 0.5;
-          if (iy == 0 || iy == C::NC1 - 1) w *= 0.5;
-        }
-        acc += w * double(tiles[win_out(f) + __ldg(a.canon_tile + iy * C::NC1 + ix)]);
-      }
-    a.pstats[size_t(pid) * F + f] = acc * double(1ll << (2 * L));
   }
   __syncthreads();
 

@@ -107,16 +107,15 @@ def test_e2_nonnull_count_is_481():
     f = np.exp(X - Y) * np.sin(2 * np.pi * (X + Y)) * np.where(Y - X ** 2 >= 0, 1.0, 2.0)
     c = O.dwt(f, "bl53", 128, L).reshape(-1)
     lay = O.layout("bl53", 2, 128, L)
-    flat = c[lay["canon_pos"]]
-    nc = lay["n_c"]
-    count = np.count_nonzero(flat[:nc]) + np.count_nonzero(np.abs(flat[nc:]) >= tau)
+    co = lay["coarse"]
+    count = np.count_nonzero(c[co]) + np.count_nonzero(np.abs(c[~co]) >= tau)
     assert lay["n_all"] == int(meta["total"])
     assert count == int(meta["nonnull"])
     # the same count through the codec
     rec = O.encode(O.dwt(f, "bl53", 128, L)[None], "bl53", 128, L, eps=tau)
     nedge = int.from_bytes(rec[16 + 8:16 + 12], "little")
     nint = int.from_bytes(rec[16 + 12:16 + 16], "little")
-    assert np.count_nonzero(flat[:nc]) + nedge + nint == int(meta["nonnull"])
+    assert np.count_nonzero(c[co]) + nedge + nint == int(meta["nonnull"])
 
 
 def test_haar_closed_forms():
@@ -148,27 +147,30 @@ def test_tensor_equals_kronecker_bruteforce(wavelet, P, L):
     assert np.allclose(back, u, atol=1e-13)
 
 
-def test_layout_is_a_permutation_with_expected_class_sizes():
+def test_layout_band_sizes_and_edges():
     for wavelet, P, L in [("bl53", 64, 4), ("haar", 32, 3), ("bl53", 32, 3)]:
         lay = O.layout(wavelet, 2, P, L)
-        pos = lay["canon_pos"]
-        assert np.array_equal(np.sort(pos), np.arange(lay["n_all"]))
-        n0 = (P >> L) + (1 if wavelet == "bl53" else 0)
-        assert lay["n_c"] == n0 * n0
-        assert lay["nb"] == (L + 1) ** 2
-        # edge coefficients: BL5/3 detail positions on lines x or y in {0, P}
         E = P + 1 if wavelet == "bl53" else P
-        ky, kx = np.divmod(pos, E)
+        n0 = (P >> L) + (1 if wavelet == "bl53" else 0)
+        assert lay["n_c"] == n0 * n0 == lay["coarse"].sum()
+        assert lay["nb"] == (L + 1) ** 2
+        size = lambda c: n0 if c == 0 else P >> c
+        counts = np.bincount(lay["band"], minlength=lay["nb"])
+        for b in range(lay["nb"]):
+            cx, cy = divmod(b, L + 1)
+            assert counts[b] == size(cx) * size(cy)
+        ky, kx = np.divmod(np.arange(E * E), E)
         expect = (wavelet == "bl53") & ((kx == 0) | (kx == P) | (ky == 0) | (ky == P))
-        assert np.array_equal(lay["edge"][lay["n_c"]:], expect[lay["n_c"]:])
+        assert np.array_equal(lay["edge"], expect)
+        assert np.array_equal(lay["coarse"], (kx % (1 << L) == 0) & (ky % (1 << L) == 0))
 
 
 def _bruteforce_survivors(c, wavelet, P, L, eps, rule="const"):
     lay = O.layout(wavelet, 2, P, L)
-    flat = c.reshape(-1)[lay["canon_pos"]]
+    flat = c.reshape(-1)
     taus = np.array([eps * O.band_factor(wavelet, 2, P, L, b, rule) for b in range(lay["nb"])])
     keep = np.abs(flat) >= taus[lay["band"]]
-    keep[: lay["n_c"]] = True
+    keep[lay["coarse"]] = True
     return lay, flat, keep
 
 
@@ -182,7 +184,7 @@ def test_threshold_mask_bruteforce(rule):
     rec = O.encode(c[None], "bl53", P, L, eps, rule=rule)
     d = O.decode(rec, 1, (P + 1, P + 1), "bl53", P, L)[0]
     lay, flat, keep = _bruteforce_survivors(c, "bl53", P, L, eps, rule)
-    got = d.reshape(-1)[lay["canon_pos"]]
+    got = d.reshape(-1)
     assert np.array_equal(got[keep], flat[keep])  # F64 storage is exact
     assert np.all(got[~keep] == 0)
 
@@ -220,21 +222,18 @@ def test_quantised_storage_roundtrip():
     rec = O.encode(c, "bl53", P, L, 0.0, prec="f32", store="bf16")
     d = O.decode(rec, 1, (P + 1, P + 1), "bl53", P, L, prec="f32", store="bf16")[0].reshape(-1)
     flat = c[0].reshape(-1)
-    interior = ~lay["edge"]
-    interior[: lay["n_c"]] = False
-    p = lay["canon_pos"][interior]
-    want = torch.from_numpy(flat[p].astype(np.float32)).to(torch.bfloat16).float().numpy()
-    assert np.array_equal(d[p].astype(np.float32), want)
-    pe = lay["canon_pos"][lay["edge"]]
-    assert np.array_equal(d[pe], flat[pe])  # edge lines kept in FP32
+    interior = ~lay["edge"] & ~lay["coarse"]
+    want = torch.from_numpy(flat[interior].astype(np.float32)).to(torch.bfloat16).float().numpy()
+    assert np.array_equal(d[interior].astype(np.float32), want)
+    assert np.array_equal(d[lay["edge"]], flat[lay["edge"]])  # edge lines kept in FP32
     rec8 = O.encode(c, "bl53", P, L, 0.0, prec="f32", store="i8")
     d8 = O.decode(rec8, 1, (P + 1, P + 1), "bl53", P, L, prec="f32", store="i8")[0].reshape(-1)
-    band = lay["band"][interior]
-    for b in np.unique(band):
-        v = flat[p[band == b]].astype(np.float32)
+    for b in np.unique(lay["band"][interior]):
+        m = interior & (lay["band"] == b)
+        v = flat[m].astype(np.float32)
         s = np.float32(np.abs(v).max()) / np.float32(127)
         q = np.clip(np.rint(v / s), -127, 127).astype(np.float32)
-        assert np.array_equal(d8[p[band == b]].astype(np.float32), q * s)
+        assert np.array_equal(d8[m].astype(np.float32), q * s)
 
 
 def test_accumulation_and_capped_factor_reading():
