@@ -148,6 +148,27 @@ wcs_status wcs_stats(wcs_sim* sim, wcs_step_stats* out);
  * small nothing is copied and WCS_E_ARG is returned. */
 wcs_status wcs_export_record(wcs_sim* sim, int64_t patch, void* dst, int64_t cap, int64_t* nbytes);
 
+/* Export without device allocation.  Same result as wcs_export_field with a
+ * host destination, for callers that cannot call cudaMalloc at that point:
+ * a process whose device memory is already taken up by its simulations (the
+ * temporary buffer of wcs_export_field could fail with WCS_E_OOM), or a
+ * latency-bound loop that must not pay for cudaMalloc/cudaFree and the
+ * device-wide synchronisation they imply.  The paper has no counterpart.
+ *
+ * The decoded field is staged in one library-wide device array of
+ * WCS_NOALLOC_SCRATCH_BYTES bytes, reserved on every GPU that loads the
+ * library until the process exits, then copied to host_dst (caller-owned,
+ * ny*nx values of the given dtype; field = -1 writes every field).  Requests
+ * larger than the array return WCS_E_ARG with a message saying so.  The
+ * first call on a device looks the array's device address up (with that
+ * device current); make that first call before any CUDA stream capture.
+ * Every call shares the array and overwrites it completely for the range it
+ * exports; calls whose work overlaps on the GPU (several simulations on
+ * different streams or host threads) race on it and must be serialised by
+ * the caller.  Synchronises the simulation's stream; allocates nothing. */
+#define WCS_NOALLOC_SCRATCH_BYTES (16u << 20)
+wcs_status wcs_export_field_noalloc(wcs_sim* sim, int field, void* host_dst, int dtype);
+
 /* Number of patches and fields, dense node counts. */
 wcs_status wcs_shape(const wcs_sim* sim, int64_t* npatch, int* nfields, int64_t* nodes_x, int64_t* nodes_y);
 

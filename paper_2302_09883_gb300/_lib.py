@@ -58,6 +58,7 @@ def lib():
         L.wcs_step.argtypes = [vp, i64]
         L.wcs_sync.argtypes = [vp]
         L.wcs_export_field.argtypes = [vp, i32, vp, i32, i32]
+        L.wcs_export_field_noalloc.argtypes = [vp, i32, vp, i32]
         L.wcs_compressed_bytes.restype = i64
         L.wcs_compressed_bytes.argtypes = [vp]
         L.wcs_stats.argtypes = [vp, C.POINTER(StepStats)]

@@ -416,4 +416,55 @@ wcs_status wcs_export_record(wcs_sim* s, int64_t patch, void* dst, int64_t cap, 
   return WCS_OK;
 }
 
+// ------------------------------------------------------------------------
+// Export without device allocation (see wcs_export_field_noalloc in
+// include/wcsim.h).  The staging array lives in this file; host code may
+// only use its name through cudaGetSymbolAddress, which is done once per
+// device, with that device current, on the first call there.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[WCS_NOALLOC_SCRATCH_BYTES];
+static void* g_noalloc_ptr[64];
+static bool g_noalloc_ready[64];
+
+static wcs_status noalloc_scratch(wcs_sim* s, void** ptr) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(s, e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(s, WCS_E_ARG, "device index out of range for the staging table");
+  if (!g_noalloc_ready[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaGetSymbolAddress(staging array)");
+    g_noalloc_ptr[dev] = p;
+    g_noalloc_ready[dev] = true;
+  }
+  *ptr = g_noalloc_ptr[dev];
+  return WCS_OK;
+}
+
+wcs_status wcs_export_field_noalloc(wcs_sim* s, int field, void* host_dst, int dtype) {
+  if (!s || !host_dst || field < -1 || field >= s->F || (dtype != 0 && dtype != 1)) return WCS_E_ARG;
+  if (!s->inited) return fail(s, WCS_E_ARG, "export before init");
+  const size_t plane = size_t(s->G[0]) * size_t(s->G[1]);
+  const size_t bytes = plane * (field < 0 ? s->F : 1) * (dtype == 0 ? 8 : 4);
+  if (bytes > WCS_NOALLOC_SCRATCH_BYTES)
+    return fail(s, WCS_E_ARG, "wcs_export_field_noalloc: " + std::to_string(bytes) +
+                                  " bytes requested, the staging array holds " +
+                                  std::to_string(WCS_NOALLOC_SCRATCH_BYTES) + " (use wcs_export_field)");
+  wcs_status st = wcs_sync(s);
+  if (st != WCS_OK) return st;
+  void* scratch = nullptr;
+  if ((st = noalloc_scratch(s, &scratch)) != WCS_OK) return st;
+  wcs::PatchArgs a = base_args(s);
+  const int cur = int(s->nstep % 2);
+  a.arena_in = s->arena[cur];
+  a.tab_in = s->tab[cur];
+  a.dense = scratch;
+  a.dense_dtype = dtype;
+  a.field_sel = field;
+  CK(s->ke.launch(wcs::MODE_EXPORT, a, s->npatch, s->stream));
+  CK(cudaMemcpyAsync(host_dst, scratch, bytes, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return WCS_OK;
+}
+
 }  // extern "C"
