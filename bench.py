@@ -15,7 +15,9 @@ shear wave u_x = 0.05 sin(2 pi y/2048) + N(0, 1e-4), tau = 0.6.
      timed step; MLUPS = 2048^2 * K / sum of step times;
   4. the uncompressed baseline timed the same way, the C-ABI end to end with
      host buffers, nvidia-smi clocks during the timed region, and the CPU
-     oracle on a bounded sample (--impl reference times only the oracle).
+     oracle on a bounded sample (--impl reference times only the oracle);
+  5. the 2-D Euler workload (4096^2 cells, outflow, int8 details) the same
+     way, reported under "euler".
 
 --gpus N (under torchrun) runs N independent replicas (weak scaling); rank 0
 prints the line with the max time over ranks.
@@ -50,6 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quality-steps", type=int, default=None)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-euler", action="store_true")
     return ap.parse_args()
 
 
@@ -187,6 +190,71 @@ def quality_pass(torch, w, steps):
     return res
 
 
+def euler_section(torch, K, W, flush, bs, qsteps=None, eps_sweep=(3e-5, 1e-4, 3e-4), stores=("i8", "bf16"),
+                  fixed_dth=0.15):
+    """2-D Euler (Rusanov), 4096 cells (4097 nodes) per axis, outflow, BL5/3
+    P = 64, L = 4, FP32 compute, four-quadrant Riemann data.  Quality: every
+    (storage, eps) against the uncompressed FP32 run with the same fixed
+    step dt/h (so both runs are compared at the same physical times);
+    timing: the workload's adaptive CFL 0.4."""
+    from paper_2302_09883_gb300 import Dense, Sim
+    from paper_2302_09883_gb300._lib import WcsError
+    w = dict(inputs.WORKLOADS["euler_bl53_4096"])
+    n, qs = w["n"], qsteps or w["steps"]
+    f = macro_fields(w)
+    kwq = dict(periodic=(False, False), cfl=-fixed_dth, gamma=w["gamma"], stream=bs)
+    kwt = dict(periodic=(False, False), cfl=w["cfl"], gamma=w["gamma"], stream=bs)
+    d = Dense("euler2d", n, n, **kwq)
+    d.init_macro(f)
+    d.step(qs)
+    Wd = [d.export_field(q) for q in range(4)]
+    d.close()
+    sweep, heads = [], {}
+    for store in stores:
+        good = []
+        for eps in eps_sweep:
+            s = Sim("euler2d", "bl53", n, n, w["P"], w["L"], eps, prec=w["prec"], store=store, arena_factor=0.35, **kwq)
+            s.init_macro(f)
+            s.step(qs)
+            try:
+                s.sync()
+            except WcsError as ex:  # the lossy state lost positivity: the step reported non-finite values
+                sweep.append({"store": store, "eps": eps, "failed": str(ex)})
+                s.close()
+                continue
+            Wc = s.export_field(-1)
+            st = s.stats()
+            q = {"store": store, "eps": eps, "rel_l2": [rel_l2(Wc[k], Wd[k]) for k in range(4)],
+                 "compression_ratio": st["uncompressed_bytes"] / s.compressed_bytes()}
+            sweep.append(q)
+            good.append(q)
+            s.close()
+        ok = [q for q in good if max(q["rel_l2"]) <= 1e-3]
+        if good:
+            heads[store] = max(ok, key=lambda q: q["eps"]) if ok else min(good, key=lambda q: q["eps"])
+    out = {"workload": "euler_bl53_4096", "grid_nodes": [n + 1, n + 1], "P": w["P"], "levels": w["L"],
+           "quality_steps": qs, "quality_dt_over_h": fixed_dth, "sweep": sweep}
+    lu = (n + 1) * (n + 1)
+    for store, head in heads.items():
+        s = Sim("euler2d", "bl53", n, n, w["P"], w["L"], head["eps"], prec=w["prec"], store=store,
+                arena_factor=0.35, **kwt)
+        s.init_macro(f)
+        s.step(W)
+        s.sync()
+        ms = timed_steps(torch, s, bs, K, flush)
+        s.sync()
+        s.close()
+        out[store] = {"eps": head["eps"], "mlups": lu * K / (ms * 1e-3) / 1e6, "ms_per_step": ms / K,
+                      "compression_ratio": head["compression_ratio"], "rel_l2_rho_rhou_rhov_E": head["rel_l2"]}
+    d = Dense("euler2d", n, n, **kwt)
+    d.init_macro(f)
+    d.step(W)
+    dms = timed_steps(torch, d, bs, K, flush)
+    d.close()
+    out["uncompressed_mlups"] = lu * K / (dms * 1e-3) / 1e6
+    return out
+
+
 def roofline_bytes(sim, w):
     """Algorithmic bytes of one step launch: records of state n read, records
     of state n+1 written, ghost rings read and written, patch tables, the
@@ -197,6 +265,51 @@ def roofline_bytes(sim, w):
     npatch = sim.npatch
     live = st["live_bytes"]
     return 2 * live + 2 * npatch * ring + 2 * npatch * 8 + npatch * 9 * 8
+
+
+def lifting_flops_per_line(P, L):
+    """FP32 operations of one BL5/3 line of P+1 nodes over L levels, counting
+    each add/sub/mul separately: predict 3 (add, mul, sub) per detail, update
+    4 (2 mul, 2 add) per interior sample (Sec. 2.1.2)."""
+    ops = 0
+    for lev in range(1, L + 1):
+        K = (P >> (lev - 1)) // 2
+        ops += 3 * K + 4 * (K - 1)
+    return ops
+
+
+def algorithmic_flops_per_lu(P, L, F=9):
+    """Per lattice update of the D2Q9 compressed step: one inverse and one
+    forward 2-D transform of every field (2 passes of E lines each), the BGK
+    collision (135 operations, counted from the formula), the threshold test
+    (|d| and a compare per coefficient)."""
+    E = P + 1
+    dwt = 2 * (2 * E * lifting_flops_per_line(P, L)) * F / (P * P)
+    return dwt + 135 + 2 * F * E * E / (P * P)
+
+
+def kernel_src_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ["common.cuh", "patch2d.cuh", "launch.cuh"]:
+        h.update(open(os.path.join(ROOT, "paper_2302_09883_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(md_name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    try:
+        txt = open(os.path.join(ROOT, "profiles", md_name)).read()
+    except OSError:
+        return None
+    tr, hs = None, None
+    for line in txt.splitlines():
+        if line.startswith("DRAM traffic per launch"):
+            tr = int(line.split(":")[1].split()[0])
+        if line.startswith("Kernel source hash"):
+            hs = line.split(":")[-1].strip()
+    return tr if hs == kernel_src_hash() else None
 
 
 def cpu_oracle_mlups(w, seconds_target=15.0):
@@ -290,6 +403,7 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         ms = timed_steps(torch, sim, bs, K, flush)
+    clk_summary = clk.summary()
     sim.sync()
     torch.cuda.synchronize()
     if world > 1:
@@ -338,6 +452,10 @@ def main():
     h2d = sum(x.nbytes for x in host_f)
     d2h = out.nbytes + K * (n // w["P"]) ** 2 * 9 * 8
 
+    euler = None
+    if not args.no_euler:
+        euler = euler_section(torch, K, W, flush, bs, qsteps=None if args.quality_steps is None else args.quality_steps)
+
     mlups = lu * K * world / (ms * 1e-3) / 1e6
     peaks = {}
     try:
@@ -345,16 +463,15 @@ def main():
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = bytes_per_launch / (ms * 1e-3 / K) / 1e9
-    traffic = None
-    tr_file = os.path.join(ROOT, "profiles", "traffic_d2q9_bl53_2048.json")
-    if os.path.exists(tr_file):
-        try:
-            tr = json.load(open(tr_file))
-            if tr.get("eps") == eps:
-                traffic = tr.get("bytes_per_launch")
-        except Exception:
-            pass
+    launch_s = ms * 1e-3 / K
+    hbm_achieved = bytes_per_launch / launch_s / 1e9
+    flops_lu = algorithmic_flops_per_lu(w["P"], w["L"])
+    clk = clk_summary
+    sm_mhz = clk["sm_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, 128 FP32 lanes per SM, FMA = 2
+    alu_achieved = flops_lu * lu / launch_s / 1e12
+    traffic = profiled_traffic("patch_kernel_d2q9_bl53_2048.md")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
@@ -378,14 +495,20 @@ def main():
             "warm_mlups": lu * K / (warm_ms * 1e-3) / 1e6,
             "sweep": sweep,
             "compressed_bytes": comp_bytes, "uncompressed_bytes": st["uncompressed_bytes"],
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": traffic,
-                         "bytes_per_launch": bytes_per_launch, "kernel": "patch_kernel<D2Q9,BL53,f32,BF16,64,4,STEP>",
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
-            "clocks": clk.summary(),
+            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": alu_achieved / fp32_peak, "traffic": traffic,
+                         "flops_per_lu": flops_lu, "bytes_per_launch": bytes_per_launch,
+                         "kernel": "patch_kernel<D2Q9,BL53,f32,BF16,64,4,STEP>",
+                         "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (median SM clock sampled "
+                                        "during the timed steps)" % (nsm, sm_mhz),
+                         "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": hbm_achieved / hbm_peak,
+                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}},
+            "clocks": clk_summary,
             "e2e": {"value": lu * K / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / K,
                     "d2h_bytes_per_step": d2h / K},
             "gpu_launches": K,
+            "euler": euler,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

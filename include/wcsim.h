@@ -80,7 +80,8 @@ typedef struct {
   int detail_store;       /* wcs_store */
   int compute;            /* wcs_prec */
   double tau;             /* D2Q9 relaxation time (omega = 1/tau) */
-  double cfl;             /* EULER2D: dt = cfl h / max(|u|+c, |v|+c) */
+  double cfl;             /* EULER2D: > 0: dt = cfl h / max(|u|+c, |v|+c) of
+                             the current state; < 0: fixed step dt/h = -cfl */
   double gamma;           /* EULER2D ratio of specific heats */
   double arena_factor;    /* arena capacity per buffer, as a fraction of the
                              uncompressed state size in the compute type

@@ -240,8 +240,11 @@ template <class T> struct Sim {
     T lam = T(0);
     if (prm.scheme == SC_EULER2D) {
       const T smax = global_speed_max<T>(prm, U);
-      lam = T(prm.cfl / double(smax));
-      time += prm.cfl / double(smax) / double(grid.N[0]);
+      // cfl > 0: dt = cfl h / smax (eq. dt of Sec. 3.1.2 with Euler's max
+      // signal speed); cfl < 0: a fixed step dt/h = -cfl
+      const double dth = prm.cfl > 0 ? prm.cfl / double(smax) : -prm.cfl;
+      lam = T(dth);
+      time += dth / double(grid.N[0]);
     } else {
       time += 1.0;
     }
@@ -357,8 +360,11 @@ template <class T> struct Ref {
     T lam = T(0);
     if (prm.scheme == SC_EULER2D) {
       const T smax = global_speed_max<T>(prm, U);
-      lam = T(prm.cfl / double(smax));
-      time += prm.cfl / double(smax) / double(grid.N[0]);
+      // cfl > 0: dt = cfl h / smax (eq. dt of Sec. 3.1.2 with Euler's max
+      // signal speed); cfl < 0: a fixed step dt/h = -cfl
+      const double dth = prm.cfl > 0 ? prm.cfl / double(smax) : -prm.cfl;
+      lam = T(dth);
+      time += dth / double(grid.N[0]);
     } else {
       time += 1.0;
     }

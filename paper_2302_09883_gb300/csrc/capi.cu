@@ -29,6 +29,7 @@ void reg_d2q9_bl53_f32_p64l4(std::vector<KernelEntry>&);
 void reg_d2q9_bl53_i8_p64l4(std::vector<KernelEntry>&);
 void reg_euler_bl53_i8_p64l4(std::vector<KernelEntry>&);
 void reg_euler_bl53_f64_p32l3(std::vector<KernelEntry>&);
+void reg_euler_bl53_bf16_p64l4(std::vector<KernelEntry>&);
 
 void register_all(std::vector<KernelEntry>& v) {
   reg_d2q9_haar_f64_p32l3(v);
@@ -38,6 +39,7 @@ void register_all(std::vector<KernelEntry>& v) {
   reg_d2q9_bl53_i8_p64l4(v);
   reg_euler_bl53_i8_p64l4(v);
   reg_euler_bl53_f64_p32l3(v);
+  reg_euler_bl53_bf16_p64l4(v);
 }
 }  // namespace wcs
 
@@ -123,6 +125,10 @@ static wcs::PatchArgs base_args(const wcs_sim* s) {
   a.eps_patch = nullptr;
   a.omega = 1.0 / s->tau;
   a.gamma = s->gamma;
+  a.omega32 = float(1.0 / s->tau);
+  a.gamma32 = float(s->gamma);
+  a.gm1_32 = float(s->gamma - 1.0);
+  a.gm1_64 = s->gamma - 1.0;
   a.cfl = s->cfl;
   a.ncell_x = s->n[0];
   a.G0 = s->G[0];
@@ -166,7 +172,7 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
   s->L = levels;
   s->eps = eps;
   s->tau = opts->tau > 0 ? opts->tau : 1.0;
-  s->cfl = opts->cfl > 0 ? opts->cfl : 0.4;
+  s->cfl = opts->cfl != 0 ? opts->cfl : 0.4;
   s->gamma = opts->gamma > 1 ? opts->gamma : 1.4;
   s->stream = static_cast<cudaStream_t>(opts->cuda_stream);
   for (int a = 0; a < 2; ++a) {

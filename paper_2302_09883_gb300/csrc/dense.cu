@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) euler_update(const float* __restrict__ sr
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) smax[rst] = 0ull;
   const double sm = __longlong_as_double((long long)smax[rd]);
-  const float lam = float(cfl / sm);
+  const float lam = float(cfl > 0 ? cfl / sm : -cfl);
   float s_new = 0.0f;
   if (x < nx) {
     const size_t plane = size_t(nx) * ny;
@@ -134,7 +134,7 @@ wcs_status wcs_dense_create(const wcs_grid* grid, int scheme, const wcs_opts* op
   }
   d->F = scheme == WCS_D2Q9 ? 9 : 4;
   d->tau = opts->tau > 0 ? opts->tau : 1.0;
-  d->cfl = opts->cfl > 0 ? opts->cfl : 0.4;
+  d->cfl = opts->cfl != 0 ? opts->cfl : 0.4;
   d->gamma = opts->gamma > 1 ? opts->gamma : 1.4;
   d->stream = static_cast<cudaStream_t>(opts->cuda_stream);
   const size_t bytes = size_t(d->F) * d->n[0] * d->n[1] * 4;

@@ -45,6 +45,8 @@ struct PatchArgs {
   double eps, eps_edge;
   const double* eps_patch;      // optional per-patch threshold constant
   double omega, gamma, cfl;
+  float omega32, gamma32, gm1_32;   // the same parameters rounded once on the host
+  double gm1_64;
   long long ncell_x;            // cells along x (time accounting)
   const double* macro[4];       // MODE_INIT inputs, [G1][G0]
   long long G0, G1;
@@ -163,7 +165,18 @@ __global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1) patch_kernel
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int pid = blockIdx.x;
   const int px = pid % a.npx, py = pid / a.npx;
-  const T omega = T(a.omega), gamma = T(a.gamma), gm1 = T(a.gamma - 1.0);
+  // scheme parameters in the compute type (rounded once on the host: the
+  // FP64 units of this GPU are too few to convert them in every thread)
+  T omega, gamma, gm1;
+  if constexpr (sizeof(T) == 8) {
+    omega = T(a.omega);
+    gamma = T(a.gamma);
+    gm1 = T(a.gm1_64);
+  } else {
+    omega = T(a.omega32);
+    gamma = T(a.gamma32);
+    gm1 = T(a.gm1_32);
+  }
 
   // Window of field f: where node (0,0) of the state being read (in) or
   // written (out) sits in shared memory (D2Q9 step: the out window of
@@ -281,7 +294,7 @@ __global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1) patch_kernel
         a.ctl->cursor[a.cur_rst] = 0ull;
         if constexpr (SCH == SCH_EULER2D) {
           const double smax = __longlong_as_double((long long)a.ctl->smax[a.smax_rd]);
-          a.ctl->time += a.cfl / smax / double(a.ncell_x);
+          a.ctl->time += (a.cfl > 0 ? a.cfl / smax : -a.cfl) / double(a.ncell_x);
         } else {
           a.ctl->time += 1.0;
         }
@@ -444,8 +457,12 @@ __global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1) patch_kernel
       __syncthreads();
     } else {
       __syncthreads();
-      const double smax = __longlong_as_double((long long)a.ctl->smax[a.smax_rd]);
-      const T lam = T(a.cfl / smax);
+      // dt/h = CFL / max signal speed, formed in FP64 once per block
+      T* lam_sm = reinterpret_cast<T*>(misc + 48);
+      if (tid == 0)  // cfl < 0: fixed step dt/h = -cfl
+        *lam_sm = T(a.cfl > 0 ? a.cfl / __longlong_as_double((long long)a.ctl->smax[a.smax_rd]) : -a.cfl);
+      __syncthreads();
+      const T lam = *lam_sm;
       for (int t = tid; t < E * E; t += NT) {
         const int y = t / E, x = t - y * E;
         T W0[4], acc[4];
@@ -515,9 +532,11 @@ __global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1) patch_kernel
     const bool valid = x < P;
     const int cx = cls_x[h];
     T* col = tiles + win_out(f) + (valid ? x : 0);
-    const T* ti = tau_i + cx * (L + 1);
     const T* te = tau_e + cx * (L + 1);
     const bool xedge = WV == WV_BL53 && x == 0;
+    T thr[L + 1];  // this lane's threshold per y class (rows y = 0, P use te)
+#pragma unroll
+    for (int c = 0; c <= L; ++c) thr[c] = xedge ? te[c] : tau_i[cx * (L + 1) + c];
     unsigned int myw[(E + 31) / 32];
 #pragma unroll
     for (int k = 0; k < (E + 31) / 32; ++k) myw[k] = 0u;
@@ -528,11 +547,11 @@ __global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1) patch_kernel
       const int cy = node_class<L>(y);
       bool keep = false;
       if (valid && (cx | cy)) {
-        const bool edge = xedge || (WV == WV_BL53 && (y == 0 || y == P));
-        keep = fabs(v[y]) >= (edge ? te[cy] : ti[cy]);
+        const bool yedge = WV == WV_BL53 && (y == 0 || y == P);  // folds: y is a constant here
+        keep = fabs(v[y]) >= (yedge ? te[cy] : thr[cy]);
         if (!isfinite(v[y])) bad = true;
         if constexpr (C::QUANT) {
-          if (keep && !edge) atomicMax(bmax + f * NB + cx * (L + 1) + cy, __float_as_uint(fabsf(float(v[y]))) + 1u);
+          if (keep && !(yedge || xedge)) atomicMax(bmax + f * NB + cx * (L + 1) + cy, __float_as_uint(fabsf(float(v[y]))) + 1u);
         }
         if (!keep) v[y] = T(0);
       } else if (valid && !isfinite(v[y])) {

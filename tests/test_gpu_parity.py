@@ -138,3 +138,28 @@ def test_arena_overflow_is_reported_and_state_kept():
     with pytest.raises(WcsError) as ei:
         g.init_macro(f)
     assert ei.value.status == 3
+
+
+def test_euler_fp32_bf16_fixed_step_matches_fp32_oracle_bitwise():
+    # fixed time step (cfl < 0: dt/h = -cfl), BF16 details
+    f = inputs.four_quadrant(256)
+    g, o = run_pair("euler2d", "bl53", 256, 64, 4, 1e-4, "f32", "bf16", 15, f, periodic=(False, False), cfl=-0.15,
+                    check_records_at=(1, 6))
+    assert np.array_equal(g.export_field(-1), o.export_all())
+    assert g.stats()["time"] == o.stats()["time"]
+    assert abs(g.stats()["time"] - 15 * 0.15 / 256) < 1e-15
+
+
+def test_euler_nonfinite_state_is_reported_and_frozen():
+    # A lossy step that breaks positivity must surface as a sticky status,
+    # with the state kept at the input of the failed step.
+    from paper_2302_09883_gb300._lib import WcsError
+    f = inputs.four_quadrant(256)
+    g = Sim("euler2d", "bl53", 256, 256, 64, 4, 5e-2, prec="f32", store="i8", periodic=(False, False), cfl=0.4)
+    g.init_macro(f)
+    g.step(200)
+    with pytest.raises(WcsError) as ei:
+        g.sync()
+    assert ei.value.status == 4
+    st = g.stats()
+    assert st["status"] != 0 and st["step"] < 200

@@ -250,3 +250,13 @@ def test_euler_compressed_eps0_matches_reference_and_conserves():
     m1 = p.stats()["coef_sums"]
     assert np.all(np.abs(m1 - m0) <= 1e-12 * np.abs(m0).max())
     assert p.stats()["shared_mismatch"] == 0
+
+
+def test_euler_fixed_time_step_mode():
+    # cfl < 0 selects a fixed step dt/h = -cfl (used to compare runs at equal
+    # physical times)
+    n = 64
+    r = O.OracleRef("euler2d", "bl53", n, n, periodic=(False, False), cfl=-0.1)
+    r.init_macro(inputs.four_quadrant(n))
+    r.step(7)
+    assert abs(r.time - 7 * 0.1 / n) < 1e-15
