@@ -182,6 +182,33 @@ void* wcs_stream(const wcs_sim* sim);
 const char* wcs_last_error(const wcs_sim* sim);
 
 /* ------------------------------------------------------------------------
+ * Batches of independent simulations (many grids of different sizes, one
+ * launch per kind of kernel per step, six steps captured in one CUDA graph
+ * and replayed).  Every simulation must be initialised, created on the same
+ * stream and at the same step.  The batch borrows the simulations (destroy
+ * the batch before them); stepping one of them outside the batch makes the
+ * next wcs_batch_step fail with WCS_E_ARG.
+ * ---------------------------------------------------------------------- */
+typedef struct wcs_batch wcs_batch;
+wcs_status wcs_batch_create(wcs_sim* const* sims, int nsims, wcs_batch** out);
+void wcs_batch_destroy(wcs_batch* b);
+/* Advances every simulation of the batch by n steps (asynchronous). */
+wcs_status wcs_batch_step(wcs_batch* b, int64_t n);
+/* Waits and returns the first device error of any simulation. */
+wcs_status wcs_batch_sync(wcs_batch* b);
+const char* wcs_batch_last_error(const wcs_batch* b);
+
+/* Patch-size autotuner: for each candidate (P[i], levels L[i]) creates a
+ * simulation on the caller's initial fields (layout of wcs_init_macro),
+ * times `steps` steps with CUDA events and writes the index of the fastest
+ * to *best (and the per-step times to ms_per_step[ncand] if not NULL).
+ * Candidates without a compiled kernel are skipped.  Results are cached for
+ * the process per (grid, scheme, options, eps, candidate list). */
+wcs_status wcs_autotune(const wcs_grid* grid, int scheme, const wcs_opts* opts, double eps, const int* P, const int* L,
+                        int ncand, const double* const* fields, int nfields, int src_is_device, int steps, int* best,
+                        double* ms_per_step);
+
+/* ------------------------------------------------------------------------
  * Uncompressed baseline (the "uncompressed" side of the metric): the same
  * scheme on dense FP32 arrays, two lattices, one kernel per step.
  * ---------------------------------------------------------------------- */

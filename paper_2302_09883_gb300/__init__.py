@@ -4,4 +4,5 @@ Import is cheap; the CUDA library is loaded (and must exist) when a Sim or
 Dense is created.
 """
 from .sim import Dense, Sim  # noqa: F401
+from .batch import Batch, autotune  # noqa: F401
 from . import inputs  # noqa: F401

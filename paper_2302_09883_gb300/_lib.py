@@ -68,6 +68,14 @@ def lib():
         L.wcs_stream.argtypes = [vp]
         L.wcs_last_error.restype = C.c_char_p
         L.wcs_last_error.argtypes = [vp]
+        L.wcs_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp)]
+        L.wcs_batch_destroy.argtypes = [vp]
+        L.wcs_batch_step.argtypes = [vp, i64]
+        L.wcs_batch_sync.argtypes = [vp]
+        L.wcs_batch_last_error.restype = C.c_char_p
+        L.wcs_batch_last_error.argtypes = [vp]
+        L.wcs_autotune.argtypes = [C.POINTER(Grid), i32, C.POINTER(Opts), C.c_double, C.POINTER(i32), C.POINTER(i32),
+                                   i32, C.POINTER(vp), i32, i32, i32, C.POINTER(i32), C.POINTER(C.c_double)]
         L.wcs_dense_create.argtypes = [C.POINTER(Grid), i32, C.POINTER(Opts), C.POINTER(vp)]
         L.wcs_dense_destroy.argtypes = [vp]
         L.wcs_dense_init_macro.argtypes = [vp, C.POINTER(vp), i32, i32]

@@ -12,6 +12,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -25,6 +28,7 @@ namespace wcs {
 void reg_d2q9_haar_f64_p32l3(std::vector<KernelEntry>&);
 void reg_d2q9_bl53_f64_p32l3(std::vector<KernelEntry>&);
 void reg_d2q9_bl53_bf16_p64l4(std::vector<KernelEntry>&);
+void reg_d2q9_bl53_bf16_p32l3(std::vector<KernelEntry>&);
 void reg_d2q9_bl53_f32_p64l4(std::vector<KernelEntry>&);
 void reg_d2q9_bl53_i8_p64l4(std::vector<KernelEntry>&);
 void reg_euler_bl53_i8_p64l4(std::vector<KernelEntry>&);
@@ -35,6 +39,7 @@ void register_all(std::vector<KernelEntry>& v) {
   reg_d2q9_haar_f64_p32l3(v);
   reg_d2q9_bl53_f64_p32l3(v);
   reg_d2q9_bl53_bf16_p64l4(v);
+  reg_d2q9_bl53_bf16_p32l3(v);
   reg_d2q9_bl53_f32_p64l4(v);
   reg_d2q9_bl53_i8_p64l4(v);
   reg_euler_bl53_i8_p64l4(v);
@@ -138,6 +143,27 @@ static wcs::PatchArgs base_args(const wcs_sim* s) {
   return a;
 }
 
+// Arguments of the step that advances state k to k+1: it reads arena,
+// table and ring k%2 and writes (k+1)%2; the max signal speed rotates over
+// three slots (read k%3, write (k+1)%3, clear (k+2)%3).
+static wcs::PatchArgs step_args(const wcs_sim* s, int64_t k) {
+  wcs::PatchArgs a = base_args(s);
+  const int in = int(k % 2), out = 1 - in;
+  a.step = k;
+  a.arena_in = s->arena[in];
+  a.tab_in = s->tab[in];
+  a.arena_out = s->arena[out];
+  a.tab_out = s->tab[out];
+  a.ring_in = s->ring[in];
+  a.ring_out = s->ring[out];
+  a.cur_out = out;
+  a.cur_rst = in;
+  a.smax_rd = int(k % 3);
+  a.smax_wr = int((k + 1) % 3);
+  a.smax_rst = int((k + 2) % 3);
+  return a;
+}
+
 extern "C" {
 
 wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int levels, double eps, const wcs_opts* opts,
@@ -161,6 +187,16 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
   if (scheme == WCS_D2Q9 && (grid->periodic_mask & 3u) != 3u) return fail(nullptr, WCS_E_ARG, "D2Q9 needs periodic axes");
   if (opts->rule < 0 || opts->rule > 2) return fail(nullptr, WCS_E_ARG, "bad threshold rule");
 
+  {
+    static std::mutex mu;
+    static std::vector<const KernelEntry*> prepared;
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(prepared.begin(), prepared.end(), ke) == prepared.end()) {
+      const cudaError_t e = ke->prepare();
+      if (e != cudaSuccess) return fail(nullptr, WCS_E_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+      prepared.push_back(ke);
+    }
+  }
   wcs_sim* s = new wcs_sim();
   s->ke = *ke;
   s->scheme = scheme;
@@ -295,23 +331,9 @@ wcs_status wcs_init_macro(wcs_sim* s, const double* const* fields, int nfields, 
 wcs_status wcs_step(wcs_sim* s, int64_t n) {
   if (!s || n < 0) return WCS_E_ARG;
   if (!s->inited) return fail(s, WCS_E_ARG, "wcs_step before wcs_init_macro");
-  wcs::PatchArgs a = base_args(s);
   for (int64_t i = 0; i < n; ++i) {
     const int64_t k = s->nstep;
-    const int in = int(k % 2), out = 1 - in;
-    a.step = k;
-    a.arena_in = s->arena[in];
-    a.tab_in = s->tab[in];
-    a.arena_out = s->arena[out];
-    a.tab_out = s->tab[out];
-    a.ring_in = s->ring[in];
-    a.ring_out = s->ring[out];
-    a.cur_out = out;
-    a.cur_rst = in;
-    a.smax_rd = int(k % 3);
-    a.smax_wr = int((k + 1) % 3);
-    a.smax_rst = int((k + 2) % 3);
-    CK(s->ke.launch(wcs::MODE_STEP, a, s->npatch, s->stream));
+    CK(s->ke.launch(wcs::MODE_STEP, step_args(s, k), s->npatch, s->stream));
     s->nstep = k + 1;
   }
   return WCS_OK;
@@ -421,6 +443,254 @@ wcs_status wcs_export_record(wcs_sim* s, int64_t patch, void* dst, int64_t cap, 
   CK(cudaMemcpy(dst, s->arena[s->nstep % 2] + off, size_t(nb), cudaMemcpyDeviceToHost));
   return WCS_OK;
 }
+
+// ------------------------------------------------------------------------
+// Batches: many independent simulations advanced by one graph launch.
+// Simulations with the same compiled kernel form a group; a group's step is
+// one launch over the (simulation, patch) pairs of its work list; six steps
+// of all groups (the period of the arena, ring and signal-speed slots) are
+// captured in one CUDA graph and replayed.
+struct wcs_batch {
+  struct Group {
+    KernelEntry ke;
+    std::vector<wcs_sim*> sims;
+    wcs::PatchArgs* args = nullptr;  // [6][sims]: arguments of each step phase
+    unsigned int* work = nullptr;    // (sim << 20) | patch per block
+    int nblocks = 0;
+  };
+  std::vector<wcs_sim*> sims;
+  std::vector<Group> groups;
+  cudaStream_t stream = nullptr;  // the simulations' stream
+  cudaStream_t priv = nullptr;    // the batch's own stream (capturable), fenced by events
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t nstep = 0;
+  std::string err;
+};
+
+static void batch_free(wcs_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->priv) cudaStreamDestroy(b->priv);
+  for (auto& g : b->groups) {
+    cudaFree(g.args);
+    cudaFree(g.work);
+  }
+  delete b;
+}
+
+static cudaError_t batch_launch_step(wcs_batch* b, int64_t k) {
+  const int ph = int(k % 6);
+  for (auto& g : b->groups) {
+    const cudaError_t e = g.ke.launch_batch(g.args + size_t(ph) * g.sims.size(), g.work, g.nblocks, b->priv);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+extern "C" {
+
+wcs_status wcs_batch_create(wcs_sim* const* sims, int nsims, wcs_batch** out) {
+  if (!sims || nsims <= 0 || !out) return WCS_E_ARG;
+  *out = nullptr;
+  wcs_batch* b = new wcs_batch();
+  b->stream = sims[0]->stream;
+  b->nstep = sims[0]->nstep;
+  for (int i = 0; i < nsims; ++i) {
+    wcs_sim* s = sims[i];
+    if (!s || !s->inited || s->stream != b->stream || s->nstep != b->nstep) {
+      g_create_err = "batch: every simulation must be initialised, share one stream and be at the same step";
+      batch_free(b);
+      return WCS_E_ARG;
+    }
+    if (s->npatch >= (1 << 20)) {
+      g_create_err = "batch: more than 2^20 patches in one simulation";
+      batch_free(b);
+      return WCS_E_ARG;
+    }
+    b->sims.push_back(s);
+    wcs_batch::Group* g = nullptr;
+    for (auto& gg : b->groups)
+      if (gg.ke.launch_batch == s->ke.launch_batch) g = &gg;
+    if (!g) {
+      b->groups.push_back(wcs_batch::Group());
+      g = &b->groups.back();
+      g->ke = s->ke;
+    }
+    if (g->sims.size() >= 4095) {
+      g_create_err = "batch: more than 4095 simulations of one kind";
+      batch_free(b);
+      return WCS_E_ARG;
+    }
+    g->sims.push_back(s);
+  }
+  if (cudaStreamCreateWithFlags(&b->priv, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    g_create_err = "batch: stream/event creation failed";
+    batch_free(b);
+    return WCS_E_CUDA;
+  }
+  for (auto& g : b->groups) {
+    std::vector<wcs::PatchArgs> args(6 * g.sims.size());
+    std::vector<unsigned int> work;
+    for (size_t j = 0; j < g.sims.size(); ++j) {
+      for (int ph = 0; ph < 6; ++ph) {
+        // phase ph serves every step k with k % 6 == ph
+        args[ph * g.sims.size() + j] = step_args(g.sims[j], ph);
+      }
+      for (int p = 0; p < g.sims[j]->npatch; ++p) work.push_back((unsigned(j) << 20) | unsigned(p));
+    }
+    g.nblocks = int(work.size());
+    if (cudaMalloc(&g.args, args.size() * sizeof(wcs::PatchArgs)) != cudaSuccess ||
+        cudaMalloc(&g.work, work.size() * 4) != cudaSuccess ||
+        cudaMemcpy(g.args, args.data(), args.size() * sizeof(wcs::PatchArgs), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g.work, work.data(), work.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      g_create_err = "batch: device allocation failed";
+      batch_free(b);
+      return WCS_E_OOM;
+    }
+  }
+  *out = b;
+  return WCS_OK;
+}
+
+void wcs_batch_destroy(wcs_batch* b) {
+  if (b && b->priv) cudaStreamSynchronize(b->priv);
+  batch_free(b);
+}
+
+wcs_status wcs_batch_step(wcs_batch* b, int64_t n) {
+  if (!b || n < 0) return WCS_E_ARG;
+  for (wcs_sim* s : b->sims)
+    if (s->nstep != b->nstep) {
+      b->err = "batch: a simulation was stepped outside the batch";
+      return WCS_E_ARG;
+    }
+  // the batch's stream waits for earlier work of the simulations' stream
+  cudaError_t e = cudaEventRecord(b->ev_in, b->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->priv, b->ev_in, 0);
+  int64_t done = 0;
+  // single launches up to the next multiple of six, then whole graphs
+  while (done < n && (b->nstep + done) % 6 != 0) {
+    if ((e = batch_launch_step(b, b->nstep + done)) != cudaSuccess) break;
+    ++done;
+  }
+  if (e == cudaSuccess && n - done >= 6 && !b->exec) {
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(b->priv, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = batch_launch_step(b, k);
+      const cudaError_t e2 = cudaStreamEndCapture(b->priv, &graph);
+      if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+  }
+  while (e == cudaSuccess && n - done >= 6) {
+    e = cudaGraphLaunch(b->exec, b->priv);
+    done += 6;
+  }
+  while (e == cudaSuccess && done < n) {
+    e = batch_launch_step(b, b->nstep + done);
+    ++done;
+  }
+  // later work on the simulations' stream waits for the batch
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_out, b->priv);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_out, 0);
+  b->nstep += done;
+  for (wcs_sim* s : b->sims) s->nstep = b->nstep;
+  if (e != cudaSuccess) {
+    b->err = std::string("batch step: ") + cudaGetErrorString(e);
+    return WCS_E_CUDA;
+  }
+  return WCS_OK;
+}
+
+wcs_status wcs_batch_sync(wcs_batch* b) {
+  if (!b) return WCS_E_ARG;
+  for (wcs_sim* s : b->sims) {
+    const wcs_status st = wcs_sync(s);
+    if (st != WCS_OK) {
+      b->err = s->err;
+      return st;
+    }
+  }
+  return WCS_OK;
+}
+
+const char* wcs_batch_last_error(const wcs_batch* b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+// ------------------------------------------------------------------------
+// Patch-size autotuner: times `steps` steps of every candidate (P[i], L[i])
+// on the caller's initial fields and returns the fastest.  Results are
+// cached for the process by (grid, scheme, options, eps, candidates).
+wcs_status wcs_autotune(const wcs_grid* grid, int scheme, const wcs_opts* opts, double eps, const int* P, const int* L,
+                        int ncand, const double* const* fields, int nfields, int src_is_device, int steps, int* best,
+                        double* ms_per_step) {
+  if (!grid || !opts || !P || !L || ncand <= 0 || !best || steps <= 0) return WCS_E_ARG;
+  typedef std::tuple<int64_t, int64_t, unsigned, int, int, int, int, int, double, std::vector<int>> Key;
+  static std::map<Key, std::pair<int, std::vector<double>>> cache;
+  static std::mutex mu;
+  std::vector<int> cand;
+  for (int i = 0; i < ncand; ++i) {
+    cand.push_back(P[i]);
+    cand.push_back(L[i]);
+  }
+  const Key key(grid->n[0], grid->n[1], grid->periodic_mask, scheme, opts->wavelet, opts->compute, opts->detail_store,
+                opts->rule, eps, cand);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *best = it->second.first;
+      if (ms_per_step)
+        for (int i = 0; i < ncand; ++i) ms_per_step[i] = it->second.second[i];
+      return WCS_OK;
+    }
+  }
+  std::vector<double> ms(ncand, -1.0);
+  int bi = -1;
+  for (int i = 0; i < ncand; ++i) {
+    wcs_sim* s = nullptr;
+    if (wcs_create_sim(grid, scheme, P[i], L[i], eps, opts, &s) != WCS_OK) continue;
+    if (wcs_init_macro(s, fields, nfields, src_is_device) != WCS_OK || wcs_step(s, 2) != WCS_OK ||
+        wcs_sync(s) != WCS_OK) {
+      wcs_destroy(s);
+      continue;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s->stream);
+    const wcs_status st = wcs_step(s, steps);
+    cudaEventRecord(e1, s->stream);
+    if (st == WCS_OK && wcs_sync(s) == WCS_OK) {
+      float t = 0;
+      cudaEventElapsedTime(&t, e0, e1);
+      ms[i] = double(t) / steps;
+      if (bi < 0 || ms[i] < ms[bi]) bi = i;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    wcs_destroy(s);
+  }
+  if (bi < 0) return fail(nullptr, WCS_E_UNSUPPORTED, "autotune: no candidate could run");
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = std::make_pair(bi, ms);
+  }
+  *best = bi;
+  if (ms_per_step)
+    for (int i = 0; i < ncand; ++i) ms_per_step[i] = ms[i];
+  return WCS_OK;
+}
+
+}  // extern "C"
 
 // ------------------------------------------------------------------------
 // Export without device allocation (see wcs_export_field_noalloc in

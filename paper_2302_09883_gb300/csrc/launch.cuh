@@ -5,13 +5,35 @@
 
 namespace wcs {
 
+template <int SCH, int WV, typename T, int ST, int P, int L>
+cudaError_t prepare_patch() {
+  typedef Cfg<SCH, WV, T, ST, P, L> C;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(C::SMEM))) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(C::SMEM))) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_EXPORT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM))) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(patch_kernel_batch<SCH, WV, T, ST, P, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(C::SMEM));
+}
+
 template <int SCH, int WV, typename T, int ST, int P, int L, int MODE>
 cudaError_t launch_mode(const PatchArgs& a, int npatch, cudaStream_t s) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
-  auto kern = patch_kernel<SCH, WV, T, ST, P, L, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
-  if (e != cudaSuccess) return e;
-  kern<<<npatch, C::NT, C::SMEM, s>>>(a);
+  patch_kernel<SCH, WV, T, ST, P, L, MODE><<<npatch, C::NT, C::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int SCH, int WV, typename T, int ST, int P, int L>
+cudaError_t launch_batch(const PatchArgs* args, const unsigned int* work, int nblocks, cudaStream_t s) {
+  typedef Cfg<SCH, WV, T, ST, P, L> C;
+  if (nblocks <= 0) return cudaSuccess;
+  patch_kernel_batch<SCH, WV, T, ST, P, L><<<nblocks, C::NT, C::SMEM, s>>>(args, work);
   return cudaGetLastError();
 }
 
@@ -38,6 +60,8 @@ KernelEntry make_entry() {
   k.smem = C::SMEM;
   k.threads = C::NT;
   k.launch = &launch_patch<SCH, WV, T, ST, P, L>;
+  k.launch_batch = &launch_batch<SCH, WV, T, ST, P, L>;
+  k.prepare = &prepare_patch<SCH, WV, T, ST, P, L>;
   return k;
 }
 

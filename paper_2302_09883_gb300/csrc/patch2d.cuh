@@ -140,8 +140,9 @@ template <typename U> __device__ __forceinline__ void stg(unsigned char* p, U v)
 
 __device__ __forceinline__ unsigned long long dbl_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
+// The whole patch step for patch `pid` of the simulation described by `a`.
 template <int SCH, int WV, typename T, int ST, int P, int L, int MODE>
-__global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1) patch_kernel(PatchArgs a) {
+__device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
   typedef typename C::S S;
   constexpr int F = C::F, E = C::E, PW = C::PW, TS = C::TS, NC = C::NC, NW = C::NW, NPW = C::NPW, NB = C::NB,
@@ -163,7 +164,6 @@ __global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1) patch_kernel
   unsigned char* stage = smem + C::OFF_STAGE;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int pid = blockIdx.x;
   const int px = pid % a.npx, py = pid / a.npx;
   // scheme parameters in the compute type (rounded once on the host: the
   // FP64 units of this GPU are too few to convert them in every thread)
@@ -851,6 +851,21 @@ __global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1) patch_kernel
     }
     if (lane == 0) atomicMax(&a.ctl->smax[a.smax_wr], dbl_bits(double(smax)));
   }
+}
+
+// One simulation: block b is patch b.
+template <int SCH, int WV, typename T, int ST, int P, int L, int MODE>
+__global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1) patch_kernel(PatchArgs a) {
+  patch_body<SCH, WV, T, ST, P, L, MODE>(a, int(blockIdx.x));
+}
+
+// Many simulations in one launch: block b steps patch (work[b] & 0xfffff) of
+// simulation (work[b] >> 20), whose arguments are args[work[b] >> 20].
+template <int SCH, int WV, typename T, int ST, int P, int L>
+__global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1)
+    patch_kernel_batch(const PatchArgs* __restrict__ args, const unsigned int* __restrict__ work) {
+  const unsigned int wb = work[blockIdx.x];
+  patch_body<SCH, WV, T, ST, P, L, MODE_STEP>(args[wb >> 20], int(wb & 0xfffffu));
 }
 
 }  // namespace wcs

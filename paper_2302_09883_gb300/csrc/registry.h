@@ -15,6 +15,10 @@ struct KernelEntry {
   size_t smem;       // dynamic shared memory per CTA
   int threads;
   cudaError_t (*launch)(int mode, const PatchArgs& a, int npatch, cudaStream_t s);
+  // step of many simulations: nblocks entries of work, args in device memory
+  cudaError_t (*launch_batch)(const PatchArgs* args, const unsigned int* work, int nblocks, cudaStream_t s);
+  // sets the kernels' shared-memory attribute (once, before any capture)
+  cudaError_t (*prepare)();
 };
 
 void register_all(std::vector<KernelEntry>& v);
