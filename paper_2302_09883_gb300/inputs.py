@@ -97,3 +97,14 @@ def initial_fields(w, n=None, seed=0):
     if w["init"] == "quadrants":
         return four_quadrant(n)
     raise ValueError(w["init"])
+
+
+def gaussian_bump_device(n, amp, sigma, cx, cy, device="cuda"):
+    """gaussian_bump with an arbitrary centre, generated directly in device
+    memory (float64 torch tensors) for large batches."""
+    import torch
+    i = torch.arange(n, dtype=torch.float64, device=device)
+    r2 = (i[None, :] - cx) ** 2 + (i[:, None] - cy) ** 2
+    rho = 1.0 + amp * torch.exp(-r2 / (2.0 * sigma * sigma))
+    z = torch.zeros_like(rho)
+    return [rho, z, z.clone()]

@@ -47,6 +47,11 @@ def _field_ptrs(fields):
             dev = d
         elif dev != d:
             raise ValueError("mixed host/device inputs")
+    if dev:
+        # the tensors were produced on torch's stream; the library reads them
+        # on its own stream, so the producer must have finished
+        import torch
+        torch.cuda.synchronize()
     arr = (C.c_void_p * len(ptrs))(*ptrs)
     return keep, arr, dev or 0
 
