@@ -209,6 +209,55 @@ wcs_status wcs_autotune(const wcs_grid* grid, int scheme, const wcs_opts* opts, 
                         double* ms_per_step);
 
 /* ------------------------------------------------------------------------
+ * Learned per-patch threshold (not in the paper, which uses one constant c):
+ * a network in -> 64 -> 64 -> 1 (GELU, FP32) maps per-patch features to
+ * log10(eps).  Features of a patch: its detail nodes are grouped by (l, S),
+ * l = the largest per-axis class of the node, S = the axes of that class
+ * (x, y or both); per group, over all fields, log10(mean d^2 + 1e-30) and
+ * log10(max |d| + 1e-30) of the forward-transformed patch before the
+ * threshold; groups in the order l = 1..L, S = x, y, xy, so in = 6L.
+ * Label: log10 of the largest eps = 10^(-7 + k/8), k = 0..40, whose
+ * thresholding (constant rule, no quantisation) changes the patch by at
+ * most delta * ||patch||_2 after the inverse transform, refined by four
+ * bisections in log eps (steps under 2%); -7 if none passes, -2 if all do.
+ * ---------------------------------------------------------------------- */
+typedef struct wcs_mlp wcs_mlp;
+/* Features and labels of every patch of a dense FP32 state [F][ny][nx]
+ * (device; periodic axes), FP64 arithmetic, patches in row order
+ * (pid = py * (nx / patch) + px).  feat_dev: npatch x 6L floats, label_dev:
+ * npatch floats (log10 eps).  levels <= 8; (patch + 1)^2 FP64 values x 3 must
+ * fit in shared memory (patch <= 96); else WCS_E_UNSUPPORTED. */
+wcs_status wcs_features_labels(const float* dense_dev, int nfields, int64_t nx, int64_t ny, int wavelet, int patch,
+                               int levels, double delta, float* feat_dev, float* label_dev, void* stream);
+wcs_status wcs_mlp_create(int nin, wcs_mlp** out);
+void wcs_mlp_destroy(wcs_mlp* m);
+int wcs_mlp_nparam(const wcs_mlp* m);
+/* parameters: W1[64][in], b1[64], W2[64][64], b2[64], W3[64], b3 (host) */
+wcs_status wcs_mlp_set_weights(wcs_mlp* m, const float* w_host);
+wcs_status wcs_mlp_get_weights(const wcs_mlp* m, float* w_host);
+/* mean squared error of the outputs against t on n samples and its gradient */
+wcs_status wcs_mlp_grad(wcs_mlp* m, const float* X_dev, const float* t_dev, int n, float* grad_host, float* loss_host);
+/* Adam (lr, 0.9, 0.999) over minibatches: batches_host holds epochs x
+ * (n / batch) x batch sample indices; loss of the last minibatch of each
+ * epoch to loss_history_host[epochs]. */
+wcs_status wcs_mlp_train(wcs_mlp* m, const float* X_dev, const float* t_dev, int n, const int* batches_host, int epochs,
+                         int batch, float lr, float* loss_history_host);
+wcs_status wcs_mlp_forward(wcs_mlp* m, const float* X_dev, int n, float* y_dev);
+/* per-patch eps = clamp(10^network(features), lo, hi); non-finite -> fallback */
+wcs_status wcs_mlp_eps(wcs_mlp* m, const float* feat_dev, int n, double lo, double hi, double fallback, double* eps_dev,
+                       void* stream);
+/* Every following step of the simulation writes the features of its new
+ * state and sets each patch's eps for the next step from the network
+ * (patch edge lines keep the uniform eps so that shared nodes stay
+ * identical).  m = NULL returns to the uniform eps. */
+wcs_status wcs_sim_use_mlp(wcs_sim* sim, wcs_mlp* m, double eps_lo, double eps_hi);
+/* Sets the threshold constant of every patch (host array of npatch values,
+ * edge lines keep the uniform eps); NULL returns to the uniform eps. */
+wcs_status wcs_sim_set_patch_eps(wcs_sim* sim, const double* eps_host);
+/* current per-patch features (npatch x 6L) and eps (npatch), host copies */
+wcs_status wcs_sim_patch_data(wcs_sim* sim, float* feat_host, double* eps_host);
+
+/* ------------------------------------------------------------------------
  * Uncompressed baseline (the "uncompressed" side of the metric): the same
  * scheme on dense FP32 arrays, two lattices, one kernel per step.
  * ---------------------------------------------------------------------- */

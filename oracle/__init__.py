@@ -36,6 +36,9 @@ def lib():
         L.orc_step.argtypes = [vp, i64]
         L.orc_export_field.argtypes = [vp, i32, dp]
         L.orc_export_all.argtypes = [vp, dp]
+        L.orc_set_patch_eps.argtypes = [vp, C.POINTER(C.c_double)]
+        L.orc_track_features.argtypes = [vp, i32]
+        L.orc_features.argtypes = [vp, dp]
         L.orc_npatch.restype = i64
         L.orc_npatch.argtypes = [vp]
         L.orc_record_bytes.restype = i64
@@ -61,6 +64,13 @@ def lib():
         L.orc_d2q9_equilibrium.argtypes = [i32, dbl, dbl, dbl, dp]
         L.orc_d2q9_collide.argtypes = [i32, dp, dbl]
         L.orc_rusanov.argtypes = [dp, dp, i32, i32, dbl, dp]
+        L.orc_patch_features.argtypes = [i32, i32, i64, i32, i32, dp, dp]
+        L.orc_patch_label.argtypes = [i32, i32, i64, i32, i32, dp, dbl, dp]
+        L.orc_eps_grid.restype = dbl
+        L.orc_eps_grid.argtypes = [i32]
+        L.orc_mlp_forward.argtypes = [i32, i32, dp, dp, i32, dp]
+        L.orc_mlp_loss_grad.restype = dbl
+        L.orc_mlp_loss_grad.argtypes = [i32, i32, dp, dp, dp, i32, dp]
         L.orc_last_error.restype = C.c_char_p
         _lib = L
     return _lib
@@ -121,6 +131,20 @@ class OracleSim:
     def export_all(self):
         out = np.empty((self.F, self.G[1], self.G[0]), np.float64)
         _check(lib().orc_export_all(self.h, _dp(out)))
+        return out
+
+    def set_patch_eps(self, eps):
+        e = np.ascontiguousarray(eps, np.float64)
+        assert e.shape == (self.npatch,)
+        _check(lib().orc_set_patch_eps(self.h, _dp(e)))
+
+    def track_features(self, on=True):
+        lib().orc_track_features(self.h, int(on))
+
+    def features(self):
+        """Features (npatch, 6L) of every patch at its last encode."""
+        out = np.zeros((self.npatch, n_features(2, self.L)), np.float64)
+        _check(lib().orc_features(self.h, _dp(out)))
         return out
 
     @property
@@ -245,3 +269,50 @@ def rusanov(WL, WR, nx, ny, gamma=1.4):
     out = np.zeros(4, np.float64)
     lib().orc_rusanov(_dp(a), _dp(b), nx, ny, gamma, _dp(out))
     return out
+
+
+# ----------------------------------------------------------- learned part
+def n_features(dims, L):
+    return 2 * ((1 << dims) - 1) * L
+
+
+def patch_features(u, wavelet, P, L):
+    """u: (F, E, E) or (F, E, E, E) node values of one patch -> features
+    (groups (l, S) in order, energy then max)."""
+    a = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(n_features(a.ndim - 1, L), np.float64)
+    _check(lib().orc_patch_features(WAVELET[wavelet], a.ndim - 1, P, L, a.shape[0], _dp(a), _dp(out)))
+    return out
+
+
+def patch_label(u, wavelet, P, L, delta):
+    """log10 of the largest admissible eps of a patch (grid + bisection)."""
+    a = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(1, np.float64)
+    _check(lib().orc_patch_label(WAVELET[wavelet], a.ndim - 1, P, L, a.shape[0], _dp(a), delta, _dp(out)))
+    return float(out[0])
+
+
+def eps_grid(k):
+    return lib().orc_eps_grid(k)
+
+
+def mlp_nparam(nin, nh):
+    return nh * nin + nh + nh * nh + nh + nh + 1
+
+
+def mlp_forward(w, X, nin, nh):
+    w = np.ascontiguousarray(w, np.float64)
+    X = np.ascontiguousarray(X, np.float64)
+    y = np.zeros(X.shape[0], np.float64)
+    lib().orc_mlp_forward(nin, nh, _dp(w), _dp(X), X.shape[0], _dp(y))
+    return y
+
+
+def mlp_loss_grad(w, X, t, nin, nh):
+    w = np.ascontiguousarray(w, np.float64)
+    X = np.ascontiguousarray(X, np.float64)
+    t = np.ascontiguousarray(t, np.float64)
+    g = np.zeros(mlp_nparam(nin, nh), np.float64)
+    loss = lib().orc_mlp_loss_grad(nin, nh, _dp(w), _dp(X), _dp(t), X.shape[0], _dp(g))
+    return loss, g

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "codec.hpp"
+#include "mlp.hpp"
 #include "schemes.hpp"
 #include "sim.hpp"
 #include "wavelet.hpp"
@@ -115,6 +116,36 @@ int orc_export_all(void* p, double* dst) {
   return guard([&] {
     if (h->s64) export_all_of(*h->s64, dst);
     else export_all_of(*h->s32, dst);
+  });
+}
+
+// Per-patch threshold constants (npatch values; edge lines keep the uniform eps).
+int orc_set_patch_eps(void* p, const double* eps) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    auto& e = h->s64 ? h->s64->eps_patch : h->s32->eps_patch;
+    for (size_t i = 0; i < e.size(); ++i) e[i] = eps[i];
+  });
+}
+
+// Keep (on != 0) the features of each patch at its encode; orc_features
+// copies them (npatch x nfeat).
+int orc_track_features(void* p, int on) {
+  Handle* h = static_cast<Handle*>(p);
+  if (h->s64) h->s64->track_feat = on != 0;
+  else h->s32->track_feat = on != 0;
+  return 0;
+}
+
+int orc_features(void* p, double* out) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    const auto& fv = h->s64 ? h->s64->feat : h->s32->feat;
+    size_t o = 0;
+    for (const auto& f : fv) {
+      if (f.empty()) throw std::runtime_error("no features recorded");
+      for (double v : f) out[o++] = v;
+    }
   });
 }
 
@@ -308,6 +339,51 @@ int orc_d2q9_collide(int prec, double* f, double tau) {
 int orc_rusanov(const double* WL, const double* WR, int nx, int ny, double gamma, double* F) {
   rusanov<double>(WL, WR, double(nx), double(ny), gamma - 1.0, gamma, F);
   return 0;
+}
+
+// ------------------------------------------------------------ learned part
+// u: nfields blocks of E^dims node values of one patch.
+int orc_patch_features(int wavelet, int dims, int64_t P, int L, int nfields, const double* u, double* out) {
+  return guard([&] {
+    const int64_t E = wavelet == BL53 ? P + 1 : P;
+    int64_t n = 1;
+    for (int a = 0; a < dims; ++a) n *= E;
+    std::vector<std::vector<double>> c(nfields);
+    for (int f = 0; f < nfields; ++f) {
+      c[f].assign(u + f * n, u + (f + 1) * n);
+      fwd_nd<double>(wavelet, c[f].data(), dims, P, L);
+    }
+    auto v = patch_features(c, dims, E, L);
+    for (size_t i = 0; i < v.size(); ++i) out[i] = v[i];
+  });
+}
+
+int orc_patch_label(int wavelet, int dims, int64_t P, int L, int nfields, const double* u, double delta, double* out) {
+  return guard([&] {
+    const int64_t E = wavelet == BL53 ? P + 1 : P;
+    int64_t n = 1;
+    for (int a = 0; a < dims; ++a) n *= E;
+    std::vector<std::vector<double>> v(nfields);
+    for (int f = 0; f < nfields; ++f) v[f].assign(u + f * n, u + (f + 1) * n);
+    *out = patch_label(v, wavelet, dims, P, L, delta);
+  });
+}
+
+double orc_eps_grid(int k) { return eps_grid(k); }
+
+int orc_mlp_forward(int nin, int nh, const double* w, const double* X, int B, double* y) {
+  Mlp m;
+  m.nin = nin;
+  m.nh = nh;
+  for (int s = 0; s < B; ++s) y[s] = mlp_forward(m, w, X + size_t(s) * nin);
+  return 0;
+}
+
+double orc_mlp_loss_grad(int nin, int nh, const double* w, const double* X, const double* t, int B, double* g) {
+  Mlp m;
+  m.nin = nin;
+  m.nh = nh;
+  return mlp_loss_grad(m, w, X, t, B, g);
 }
 
 }  // extern "C"

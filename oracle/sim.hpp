@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "codec.hpp"
+#include "mlp.hpp"
 #include "schemes.hpp"
 #include "wavelet.hpp"
 
@@ -128,6 +129,8 @@ template <class T> struct Sim {
   Layout lay;
   std::vector<std::vector<uint8_t>> rec;
   std::vector<double> eps_patch;
+  bool track_feat = false;               // keep the features of every encoded patch
+  std::vector<std::vector<double>> feat;  // per patch, before the threshold
   int64_t nstep = 0;
   double time = 0;
   int64_t shared_mismatch = 0;
@@ -165,6 +168,12 @@ template <class T> struct Sim {
 
   void encode_patch_fields(int64_t pid, std::vector<std::vector<T>>& loc) {
     for (int f = 0; f < F; ++f) fwd_nd<T>(grid.wavelet, loc[f].data(), 2, P, L);
+    if (track_feat) {
+      std::vector<std::vector<double>> c(F);
+      for (int f = 0; f < F; ++f) c[f].assign(loc[f].begin(), loc[f].end());
+      if (feat.size() != size_t(npatch())) feat.resize(npatch());
+      feat[pid] = patch_features(c, 2, E, L);
+    }
     std::vector<double> ef(F, eps_patch[pid]);
     rec[pid] = encode_patch<T>(lay, loc, store, rule, ef, eps, uint32_t(pid), flags());
   }

@@ -76,6 +76,19 @@ def lib():
         L.wcs_batch_last_error.argtypes = [vp]
         L.wcs_autotune.argtypes = [C.POINTER(Grid), i32, C.POINTER(Opts), C.c_double, C.POINTER(i32), C.POINTER(i32),
                                    i32, C.POINTER(vp), i32, i32, i32, C.POINTER(i32), C.POINTER(C.c_double)]
+        fp = C.POINTER(C.c_float)
+        L.wcs_features_labels.argtypes = [vp, i32, i64, i64, i32, i32, i32, C.c_double, vp, vp, vp]
+        L.wcs_mlp_create.argtypes = [i32, C.POINTER(vp)]
+        L.wcs_mlp_destroy.argtypes = [vp]
+        L.wcs_mlp_nparam.argtypes = [vp]
+        L.wcs_mlp_set_weights.argtypes = [vp, fp]
+        L.wcs_mlp_get_weights.argtypes = [vp, fp]
+        L.wcs_mlp_grad.argtypes = [vp, vp, vp, i32, fp, fp]
+        L.wcs_mlp_train.argtypes = [vp, vp, vp, i32, C.POINTER(i32), i32, i32, C.c_float, fp]
+        L.wcs_mlp_forward.argtypes = [vp, vp, i32, vp]
+        L.wcs_sim_use_mlp.argtypes = [vp, vp, C.c_double, C.c_double]
+        L.wcs_sim_set_patch_eps.argtypes = [vp, C.POINTER(C.c_double)]
+        L.wcs_sim_patch_data.argtypes = [vp, fp, C.POINTER(C.c_double)]
         L.wcs_dense_create.argtypes = [C.POINTER(Grid), i32, C.POINTER(Opts), C.POINTER(vp)]
         L.wcs_dense_destroy.argtypes = [vp]
         L.wcs_dense_init_macro.argtypes = [vp, C.POINTER(vp), i32, i32]

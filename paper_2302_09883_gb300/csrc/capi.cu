@@ -86,6 +86,12 @@ struct wcs_sim {
   bool inited = false;
   int64_t resident = 0;
   std::string err;
+  // learned per-patch threshold
+  wcs_mlp* mlp = nullptr;
+  float* feat = nullptr;
+  double* eps_patch = nullptr;
+  double eps_lo = 1e-7, eps_hi = 1e-2;
+  bool eps_given = false;  // per-patch eps set by the caller
 };
 
 static wcs_status fail(wcs_sim* s, wcs_status st, const std::string& msg) {
@@ -127,7 +133,22 @@ static wcs::PatchArgs base_args(const wcs_sim* s) {
   a.band_factor = s->bfactor;
   a.eps = s->eps;
   a.eps_edge = s->eps;
-  a.eps_patch = nullptr;
+  a.eps_patch = (s->mlp || s->eps_given) ? s->eps_patch : nullptr;
+  a.feat = s->feat;
+  {  // 1 / (fields x nodes of group (l, S)) for the feature means: l = the
+     // largest axis class, S = the axes of that class (x 1, y 2, both 3)
+    const int E = s->E;
+    long long cnt[24] = {0};
+    auto cls = [&](int k) { return k % (1 << s->L) == 0 ? 0 : __builtin_ctz(unsigned(k)) + 1; };
+    for (int y = 0; y < E; ++y)
+      for (int x = 0; x < E; ++x) {
+        const int cx = cls(x), cy = cls(y), l = std::max(cx, cy);
+        if (l == 0) continue;
+        const int S = (cx == l ? 1 : 0) | (cy == l ? 2 : 0);
+        ++cnt[3 * (l - 1) + S - 1];
+      }
+    for (int g = 0; g < 24; ++g) a.feat_inv_cnt[g] = cnt[g] ? float(1.0 / (double(cnt[g]) * s->F)) : 0.0f;
+  }
   a.omega = 1.0 / s->tau;
   a.gamma = s->gamma;
   a.omega32 = float(1.0 / s->tau);
@@ -268,10 +289,63 @@ bad:
   return st;
 }
 
+wcs_status wcs_sim_use_mlp(wcs_sim* s, wcs_mlp* m, double eps_lo, double eps_hi) {
+  if (!s) return WCS_E_ARG;
+  if (!m) {
+    s->mlp = nullptr;
+    return WCS_OK;
+  }
+  if (s->ke.scheme != WCS_D2Q9 && s->ke.scheme != WCS_EULER2D) return WCS_E_UNSUPPORTED;
+  if (wcs_mlp_nparam(m) != 64 * (6 * s->L) + 64 + 64 * 64 + 64 + 64 + 1)
+    return fail(s, WCS_E_ARG, "the network's input size must be 6 x levels");
+  if (!(eps_lo > 0) || !(eps_hi >= eps_lo)) return fail(s, WCS_E_ARG, "bad eps range");
+  if (!s->feat) {
+    wcs_status st;
+    if ((st = dalloc(s, (void**)&s->feat, size_t(s->npatch) * 6 * s->L * 4)) != WCS_OK) return st;
+    if ((st = dalloc(s, (void**)&s->eps_patch, size_t(s->npatch) * 8)) != WCS_OK) return st;
+  }
+  std::vector<double> e(s->npatch, s->eps);
+  CK(cudaMemcpy(s->eps_patch, e.data(), e.size() * 8, cudaMemcpyHostToDevice));
+  s->mlp = m;
+  s->eps_lo = eps_lo;
+  s->eps_hi = eps_hi;
+  return WCS_OK;
+}
+
+wcs_status wcs_sim_set_patch_eps(wcs_sim* s, const double* eps_host) {
+  if (!s) return WCS_E_ARG;
+  if (!eps_host) {
+    s->eps_given = false;
+    return WCS_OK;
+  }
+  for (int p = 0; p < s->npatch; ++p)
+    if (!(eps_host[p] >= 0)) return fail(s, WCS_E_ARG, "per-patch eps must be >= 0");
+  if (!s->feat) {
+    wcs_status st;
+    if ((st = dalloc(s, (void**)&s->feat, size_t(s->npatch) * 6 * s->L * 4)) != WCS_OK) return st;
+    if ((st = dalloc(s, (void**)&s->eps_patch, size_t(s->npatch) * 8)) != WCS_OK) return st;
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemcpy(s->eps_patch, eps_host, size_t(s->npatch) * 8, cudaMemcpyHostToDevice));
+  s->eps_given = true;
+  s->mlp = nullptr;
+  return WCS_OK;
+}
+
+wcs_status wcs_sim_patch_data(wcs_sim* s, float* feat_host, double* eps_host) {
+  if (!s || !s->feat) return WCS_E_ARG;
+  CK(cudaStreamSynchronize(s->stream));
+  if (feat_host) CK(cudaMemcpy(feat_host, s->feat, size_t(s->npatch) * 6 * s->L * 4, cudaMemcpyDeviceToHost));
+  if (eps_host) CK(cudaMemcpy(eps_host, s->eps_patch, size_t(s->npatch) * 8, cudaMemcpyDeviceToHost));
+  return WCS_OK;
+}
+
 void wcs_destroy(wcs_sim* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
   else cudaDeviceSynchronize();
+  cudaFree(s->feat);
+  cudaFree(s->eps_patch);
   for (int b = 0; b < 2; ++b) {
     cudaFree(s->arena[b]);
     cudaFree(s->tab[b]);
@@ -333,7 +407,15 @@ wcs_status wcs_step(wcs_sim* s, int64_t n) {
   if (!s->inited) return fail(s, WCS_E_ARG, "wcs_step before wcs_init_macro");
   for (int64_t i = 0; i < n; ++i) {
     const int64_t k = s->nstep;
-    CK(s->ke.launch(wcs::MODE_STEP, step_args(s, k), s->npatch, s->stream));
+    if (s->mlp) {
+      // the step writes the features of the new state; the network turns
+      // them into the per-patch eps of the next step
+      CK(s->ke.launch_feat(step_args(s, k), s->npatch, s->stream));
+      const wcs_status st = wcs_mlp_eps(s->mlp, s->feat, s->npatch, s->eps_lo, s->eps_hi, s->eps, s->eps_patch, s->stream);
+      if (st != WCS_OK) return fail(s, st, "mlp inference launch failed");
+    } else {
+      CK(s->ke.launch(wcs::MODE_STEP, step_args(s, k), s->npatch, s->stream));
+    }
     s->nstep = k + 1;
   }
   return WCS_OK;

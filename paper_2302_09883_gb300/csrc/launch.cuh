@@ -18,8 +18,20 @@ cudaError_t prepare_patch() {
   if ((e = cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_EXPORT>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM))) != cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_STEP, 1>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM))) != cudaSuccess)
+    return e;
   return cudaFuncSetAttribute(patch_kernel_batch<SCH, WV, T, ST, P, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(C::SMEM));
+}
+
+// step that also writes the per-patch features of the new state
+template <int SCH, int WV, typename T, int ST, int P, int L>
+cudaError_t launch_feat(const PatchArgs& a, int npatch, cudaStream_t s) {
+  typedef Cfg<SCH, WV, T, ST, P, L> C;
+  if (npatch <= 0) return cudaSuccess;
+  patch_kernel<SCH, WV, T, ST, P, L, MODE_STEP, 1><<<npatch, C::NT, C::SMEM, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <int SCH, int WV, typename T, int ST, int P, int L, int MODE>
@@ -61,6 +73,7 @@ KernelEntry make_entry() {
   k.threads = C::NT;
   k.launch = &launch_patch<SCH, WV, T, ST, P, L>;
   k.launch_batch = &launch_batch<SCH, WV, T, ST, P, L>;
+  k.launch_feat = &launch_feat<SCH, WV, T, ST, P, L>;
   k.prepare = &prepare_patch<SCH, WV, T, ST, P, L>;
   return k;
 }

@@ -1,0 +1,571 @@
+// Learned per-patch threshold (the paper uses one uniform constant c,
+// Sec. 2.2; the per-patch choice is this library's addition): features and
+// labels of patches, a small MLP (in -> 64 -> 64 -> 1, GELU) trained with
+// these kernels, and its inference into the per-patch eps of a simulation.
+//
+//  * features: detail nodes grouped by (l, S), l = the largest per-axis
+//    class of the node, S = the axes of that class (x, y, both); per group,
+//    over all fields: log10(mean d^2 + 1e-30) and log10(max |d| + 1e-30) of
+//    the forward-transformed patch, groups ordered l = 1..L then S = x, y,
+//    xy -> 6L inputs.
+//  * label: log10 of the largest eps = 10^(-7 + k/8), k = 0..40, whose
+//    thresholding (constant rule, no quantisation) changes the patch by at
+//    most delta * ||patch||_2 after the inverse transform, refined by four
+//    bisections in log eps towards the next grid value (steps under 2%);
+//    -7 when no eps of the grid passes, -2 when all do.
+// Reductions are in a fixed order, so repeated runs give the same bits.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/wcsim.h"
+#include "common.cuh"
+
+namespace {
+
+constexpr int MLP_NH = 64;
+constexpr int MLP_MAXIN = 64;
+constexpr int EPS_N = 41;
+__constant__ double c_eps_grid[EPS_N];  // 10^(-7 + k/8), filled on the host
+
+__host__ __device__ inline int nparam(int nin) { return MLP_NH * nin + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1; }
+
+// ------------------------------------------------ in-smem lifting (FP64)
+template <typename T> __device__ void lift_line_smem(T* u, int stride, int P, int L, int wavelet, bool inverse) {
+  auto at = [&](int k, int st) -> T& { return u[k * st * stride]; };
+  if (!inverse) {
+    for (int lev = 1; lev <= L; ++lev) {
+      const int st = 1 << (lev - 1), K = (P / st) / 2;
+      if (wavelet == WCS_BL53) {
+        for (int k = 0; k < K; ++k) at(2 * k + 1, st) = wcs::fma_rn(T(-0.5), at(2 * k, st) + at(2 * k + 2, st), at(2 * k + 1, st));
+        for (int k = 1; k < K; ++k) {
+          const T e = wcs::fma_rn(wcs::bl53_alpha<T>(k - 1, K), at(2 * k - 1, st), at(2 * k, st));
+          at(2 * k, st) = wcs::fma_rn(wcs::bl53_alpha<T>(k, K), at(2 * k + 1, st), e);
+        }
+      } else {
+        for (int k = 0; k < K; ++k) {
+          const T a = at(2 * k, st), b = at(2 * k + 1, st), d = b - a;
+          at(2 * k, st) = wcs::fma_rn(T(0.5), d, a);
+          at(2 * k + 1, st) = d;
+        }
+      }
+    }
+  } else {
+    for (int lev = L; lev >= 1; --lev) {
+      const int st = 1 << (lev - 1), K = (P / st) / 2;
+      if (wavelet == WCS_BL53) {
+        for (int k = 1; k < K; ++k) {
+          const T e = wcs::fma_rn(-wcs::bl53_alpha<T>(k - 1, K), at(2 * k - 1, st), at(2 * k, st));
+          at(2 * k, st) = wcs::fma_rn(-wcs::bl53_alpha<T>(k, K), at(2 * k + 1, st), e);
+        }
+        for (int k = 0; k < K; ++k) at(2 * k + 1, st) = wcs::fma_rn(T(0.5), at(2 * k, st) + at(2 * k + 2, st), at(2 * k + 1, st));
+      } else {
+        for (int k = 0; k < K; ++k) {
+          const T s = at(2 * k, st), d = at(2 * k + 1, st);
+          const T a = wcs::fma_rn(T(-0.5), d, s);
+          at(2 * k, st) = a;
+          at(2 * k + 1, st) = a + d;
+        }
+      }
+    }
+  }
+}
+
+__device__ inline int cls(int k, int L) {
+  if ((k & ((1 << L) - 1)) == 0) return 0;
+  return __ffs(k);
+}
+// Feature group of node (kx, ky): -1 for a coarse node, else 3 (l - 1) + S - 1.
+__device__ inline int group_of(int kx, int ky, int L) {
+  const int cx = cls(kx, L), cy = cls(ky, L), l = cx > cy ? cx : cy;
+  if (l == 0) return -1;
+  return 3 * (l - 1) + (cx == l ? 1 : 0) + (cy == l ? 2 : 0) - 1;
+}
+
+// Block sum of a double in a fixed order (power-of-two tree over threads).
+__device__ double block_sum(double v, double* red) {
+  const int t = threadIdx.x;
+  red[t] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (t < o) red[t] = red[t] + red[t + o];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+__device__ double block_max(double v, double* red) {
+  const int t = threadIdx.x;
+  red[t] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (t < o) red[t] = red[t] > red[t + o] ? red[t] : red[t + o];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Squared L2 error, summed over all fields, of thresholding patch (px, py)
+// at eps: per field load, forward, threshold, inverse, compare.  Every
+// thread returns the same value.
+__device__ double patch_err2(const float* __restrict__ dense, int F, int G0, int G1, int px, int py, int P, int L,
+                             int wavelet, double eps, double* u, double* c, double* red) {
+  const int E = wavelet == WCS_BL53 ? P + 1 : P, n = E * E, tid = threadIdx.x;
+  double err2 = 0;
+  for (int f = 0; f < F; ++f) {
+    for (int i = tid; i < n; i += blockDim.x) {
+      const int y = i / E, x = i - y * E;
+      const int gx = (px * P + x) % G0, gy = (py * P + y) % G1;
+      u[i] = double(dense[(size_t(f) * G1 + gy) * G0 + gx]);
+      c[i] = u[i];
+    }
+    __syncthreads();
+    for (int y = tid; y < E; y += blockDim.x) lift_line_smem<double>(c + y * E, 1, P, L, wavelet, false);
+    __syncthreads();
+    for (int x = tid; x < E; x += blockDim.x) lift_line_smem<double>(c + x, E, P, L, wavelet, false);
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) {
+      const int y = i / E, x = i - y * E;
+      if (group_of(x, y, L) >= 0 && !(fabs(c[i]) >= eps)) c[i] = 0.0;
+    }
+    __syncthreads();
+    for (int x = tid; x < E; x += blockDim.x) lift_line_smem<double>(c + x, E, P, L, wavelet, true);
+    __syncthreads();
+    for (int y = tid; y < E; y += blockDim.x) lift_line_smem<double>(c + y * E, 1, P, L, wavelet, true);
+    __syncthreads();
+    double my = 0;
+    for (int i = tid; i < n; i += blockDim.x) my += (c[i] - u[i]) * (c[i] - u[i]);
+    err2 += block_sum(my, red);
+  }
+  return err2;
+}
+
+// One CTA per patch of a dense FP32 state [F][G1][G0] (periodic BL5/3 or
+// Haar grids), 256 threads, FP64 arithmetic.
+__global__ void __launch_bounds__(256) features_labels(const float* __restrict__ dense, int F, int G0, int G1, int npx,
+                                                        int P, int L, int wavelet, double delta, float* feat,
+                                                        float* label) {
+  extern __shared__ double sm[];
+  const int E = wavelet == WCS_BL53 ? P + 1 : P;
+  const int n = E * E;
+  double* u = sm;          // original nodes of one field
+  double* c = u + n;       // its coefficients
+  double* t = c + n;       // a trial
+  double* red = t + n;     // 256 doubles
+  const int pid = blockIdx.x, px = pid % npx, py = pid / npx;
+  const int tid = threadIdx.x;
+  const int G = 3 * L;
+  double e2[24], mx[24], err2[EPS_N];
+  for (int g = 0; g < 24; ++g) { e2[g] = 0; mx[g] = 0; }
+  for (int k = 0; k < EPS_N; ++k) err2[k] = 0;
+  double norm2 = 0;
+  for (int f = 0; f < F; ++f) {
+    for (int i = tid; i < n; i += blockDim.x) {
+      const int y = i / E, x = i - y * E;
+      const int gx = (px * P + x) % G0, gy = (py * P + y) % G1;
+      const double v = double(dense[(size_t(f) * G1 + gy) * G0 + gx]);
+      u[i] = v;
+      c[i] = v;
+    }
+    __syncthreads();
+    for (int y = tid; y < E; y += blockDim.x) lift_line_smem<double>(c + y * E, 1, P, L, wavelet, false);
+    __syncthreads();
+    for (int x = tid; x < E; x += blockDim.x) lift_line_smem<double>(c + x, E, P, L, wavelet, false);
+    __syncthreads();
+    double my_n2 = 0, my_e2[24], my_mx[24];
+    for (int g = 0; g < 24; ++g) { my_e2[g] = 0; my_mx[g] = 0; }
+    for (int i = tid; i < n; i += blockDim.x) {
+      const int y = i / E, x = i - y * E;
+      my_n2 += u[i] * u[i];
+      const int g = group_of(x, y, L);
+      if (g >= 0) {
+        my_e2[g] += c[i] * c[i];
+        my_mx[g] = fmax(my_mx[g], fabs(c[i]));
+      }
+    }
+    norm2 += block_sum(my_n2, red);
+    for (int g = 0; g < G; ++g) {
+      e2[g] += block_sum(my_e2[g], red);
+      mx[g] = fmax(mx[g], block_max(my_mx[g], red));
+    }
+    for (int k = 0; k < EPS_N; ++k) {
+      const double eps = c_eps_grid[k];
+      for (int i = tid; i < n; i += blockDim.x) {
+        const int y = i / E, x = i - y * E;
+        const double v = c[i];
+        t[i] = (group_of(x, y, L) >= 0 && !(fabs(v) >= eps)) ? 0.0 : v;
+      }
+      __syncthreads();
+      for (int x = tid; x < E; x += blockDim.x) lift_line_smem<double>(t + x, E, P, L, wavelet, true);
+      __syncthreads();
+      for (int y = tid; y < E; y += blockDim.x) lift_line_smem<double>(t + y * E, 1, P, L, wavelet, true);
+      __syncthreads();
+      double my = 0;
+      for (int i = tid; i < n; i += blockDim.x) my += (t[i] - u[i]) * (t[i] - u[i]);
+      err2[k] += block_sum(my, red);
+    }
+  }
+  if (tid == 0) {
+    for (int g = 0; g < G; ++g) {
+      long long cnt = 0;
+      for (int y = 0; y < E; ++y)
+        for (int x = 0; x < E; ++x) cnt += group_of(x, y, L) == g;
+      feat[size_t(pid) * 2 * G + 2 * g] = float(log10(e2[g] / double(cnt * F) + 1e-30));
+      feat[size_t(pid) * 2 * G + 2 * g + 1] = float(log10(mx[g] + 1e-30));
+    }
+  }
+  const double bound = delta * sqrt(norm2);
+  int best = -1;
+  for (int k = 0; k < EPS_N; ++k)
+    if (sqrt(err2[k]) <= bound) best = k;
+  double lab;
+  if (best < 0) {
+    lab = -7.0;
+  } else if (best == EPS_N - 1) {
+    lab = -2.0;
+  } else {
+    double lo = c_eps_grid[best], hi = c_eps_grid[best + 1];
+    for (int it = 0; it < 4; ++it) {
+      const double mid = sqrt(lo * hi);
+      if (sqrt(patch_err2(dense, F, G0, G1, px, py, P, L, wavelet, mid, u, c, red)) <= bound) lo = mid;
+      else hi = mid;
+    }
+    lab = log10(lo);
+  }
+  if (tid == 0) label[pid] = float(lab);
+}
+
+// ------------------------------------------------------------------ MLP
+__device__ inline float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ inline float gelu_grad(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+__device__ float mlp_fwd(const float* __restrict__ w, int nin, const float* x, float* p1, float* p2) {
+  const float* W1 = w;
+  const float* b1 = W1 + MLP_NH * nin;
+  const float* W2 = b1 + MLP_NH;
+  const float* b2 = W2 + MLP_NH * MLP_NH;
+  const float* W3 = b2 + MLP_NH;
+  const float* b3 = W3 + MLP_NH;
+  float a1[MLP_NH];
+  for (int j = 0; j < MLP_NH; ++j) {
+    float s = b1[j];
+    for (int i = 0; i < nin; ++i) s += W1[j * nin + i] * x[i];
+    p1[j] = s;
+    a1[j] = gelu(s);
+  }
+  float y = b3[0];
+  for (int j = 0; j < MLP_NH; ++j) {
+    float s = b2[j];
+    for (int i = 0; i < MLP_NH; ++i) s += W2[j * MLP_NH + i] * a1[i];
+    p2[j] = s;
+    y += W3[j] * gelu(s);
+  }
+  return y;
+}
+
+// thread per sample: forward, backward of 0.5-free MSE, per-sample gradient
+__global__ void mlp_sample_grads(const float* __restrict__ w, int nin, const float* __restrict__ X,
+                                 const float* __restrict__ t, const int* __restrict__ idx, int B, float* gs, float* ls) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  const int np = nparam(nin);
+  const float* x = X + size_t(idx ? idx[s] : s) * nin;
+  float p1[MLP_NH], p2[MLP_NH];
+  const float y = mlp_fwd(w, nin, x, p1, p2);
+  const float r = y - t[idx ? idx[s] : s];
+  ls[s] = r * r;
+  const float dy = 2.0f * r / float(B);
+  const float* W2 = w + MLP_NH * nin + MLP_NH;
+  const float* W3 = W2 + MLP_NH * MLP_NH + MLP_NH;
+  float* g = gs + size_t(s) * np;
+  float* gW1 = g;
+  float* gb1 = gW1 + MLP_NH * nin;
+  float* gW2 = gb1 + MLP_NH;
+  float* gb2 = gW2 + MLP_NH * MLP_NH;
+  float* gW3 = gb2 + MLP_NH;
+  float* gb3 = gW3 + MLP_NH;
+  gb3[0] = dy;
+  float d2[MLP_NH], a1[MLP_NH];
+  for (int j = 0; j < MLP_NH; ++j) {
+    gW3[j] = dy * gelu(p2[j]);
+    d2[j] = dy * W3[j] * gelu_grad(p2[j]);
+    gb2[j] = d2[j];
+    a1[j] = gelu(p1[j]);
+  }
+  for (int j = 0; j < MLP_NH; ++j)
+    for (int i = 0; i < MLP_NH; ++i) gW2[j * MLP_NH + i] = d2[j] * a1[i];
+  for (int i = 0; i < MLP_NH; ++i) {
+    float d1 = 0.0f;
+    for (int j = 0; j < MLP_NH; ++j) d1 += d2[j] * W2[j * MLP_NH + i];
+    const float d = d1 * gelu_grad(p1[i]);
+    gb1[i] = d;
+    for (int k = 0; k < nin; ++k) gW1[i * nin + k] = d * x[k];
+  }
+}
+
+// thread per parameter: sum over samples in order
+__global__ void mlp_reduce(const float* __restrict__ gs, int B, int np, float* g, const float* ls, float* loss) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < np) {
+    float a = 0.0f;
+    for (int s = 0; s < B; ++s) a += gs[size_t(s) * np + p];
+    g[p] = a;
+  }
+  if (p == 0) {
+    float a = 0.0f;
+    for (int s = 0; s < B; ++s) a += ls[s];
+    *loss = a / float(B);
+  }
+}
+
+__global__ void mlp_adam(float* w, const float* g, float* m1, float* m2, int np, float lr, float b1, float b2, float b1t,
+                         float b2t) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  m1[p] = b1 * m1[p] + (1.0f - b1) * g[p];
+  m2[p] = b2 * m2[p] + (1.0f - b2) * g[p] * g[p];
+  const float mh = m1[p] / (1.0f - b1t), vh = m2[p] / (1.0f - b2t);
+  w[p] -= lr * mh / (sqrtf(vh) + 1e-8f);
+}
+
+// Inference: a block of 256 threads takes four samples at a time, one
+// thread per hidden unit; the weights are staged in shared memory with W1
+// and W2 transposed and rows padded to 65 floats, so that staging writes and
+// the per-unit reads are free of bank conflicts.  Output y (if y) and
+// eps = clamp(10^y, lo, hi), non-finite -> fallback (if eps).
+constexpr int MLP_HP = MLP_NH + 1;
+__host__ __device__ inline size_t infer_smem(int nin) {
+  return size_t(nin * MLP_HP + MLP_NH * MLP_HP + 3 * MLP_NH + 1 + 4 * nin + 4 * MLP_NH + 8) * 4;
+}
+__global__ void __launch_bounds__(256) mlp_infer(const float* __restrict__ w, int nin, const float* __restrict__ X, int n,
+                                                 float* y, double lo, double hi, double fallback, double* eps) {
+  extern __shared__ float sw[];
+  constexpr int H = MLP_NH, HP = MLP_HP;
+  float* W1T = sw;              // [nin][HP]
+  float* W2T = W1T + nin * HP;  // [H][HP]
+  float* bb = W2T + H * HP;     // b1[H], b2[H], W3[H], b3
+  float* xs = bb + 3 * H + 1;   // [4][nin]
+  float* a1 = xs + 4 * nin;     // [4][H]
+  float* part = a1 + 4 * H;     // [4][2]
+  const float* gW1 = w;
+  const float* gb1 = gW1 + H * nin;
+  const float* gW2 = gb1 + H;
+  const float* gb2 = gW2 + H * H;
+  const float* gW3 = gb2 + H;
+  const float* gb3 = gW3 + H;
+  const int t = threadIdx.x;
+  for (int q = t; q < H * nin; q += blockDim.x) {
+    const int j = q / nin, i = q - j * nin;
+    W1T[i * HP + j] = gW1[q];
+  }
+  for (int q = t; q < H * H; q += blockDim.x) {
+    const int j = q / H, i = q - j * H;
+    W2T[i * HP + j] = gW2[q];
+  }
+  for (int q = t; q < H; q += blockDim.x) {
+    bb[q] = gb1[q];
+    bb[H + q] = gb2[q];
+    bb[2 * H + q] = gW3[q];
+  }
+  if (t == 0) bb[3 * H] = gb3[0];
+  const int g = t / H, j = t - g * H;
+  for (int s0 = blockIdx.x * 4; s0 < n; s0 += gridDim.x * 4) {
+    __syncthreads();
+    for (int q = t; q < 4 * nin; q += blockDim.x) {
+      const int gg = q / nin;
+      xs[q] = s0 + gg < n ? X[size_t(s0 + gg) * nin + (q - gg * nin)] : 0.0f;
+    }
+    __syncthreads();
+    float h1 = bb[j];
+    for (int i = 0; i < nin; ++i) h1 += W1T[i * HP + j] * xs[g * nin + i];
+    a1[g * H + j] = gelu(h1);
+    __syncthreads();
+    float h2 = bb[H + j];
+    for (int i = 0; i < H; ++i) h2 += W2T[i * HP + j] * a1[g * H + i];
+    float c = bb[2 * H + j] * gelu(h2);
+    for (int o = 16; o >= 1; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((t & 31) == 0) part[t >> 5] = c;
+    __syncthreads();
+    const int s = s0 + g;
+    if (j == 0 && s < n) {
+      const float out = bb[3 * H] + (part[2 * g] + part[2 * g + 1]);
+      if (y) y[s] = out;
+      if (eps) {
+        double e = pow(10.0, double(out));
+        if (!isfinite(e)) e = fallback;
+        eps[s] = e < lo ? lo : (e > hi ? hi : e);
+      }
+    }
+  }
+}
+
+cudaError_t launch_infer(const float* w, int nin, const float* X, int n, float* y, double lo, double hi,
+                         double fallback, double* eps, cudaStream_t st) {
+  const int blocks = std::min((n + 3) / 4, 304);
+  mlp_infer<<<blocks, 256, infer_smem(nin), st>>>(w, nin, X, n, y, lo, hi, fallback, eps);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+struct wcs_mlp {
+  int nin = 8;
+  float* w = nullptr;
+  float* m1 = nullptr;
+  float* m2 = nullptr;
+  float* g = nullptr;
+  float* loss = nullptr;
+  int64_t adam_t = 0;
+  std::string err;
+};
+
+extern "C" {
+
+wcs_status wcs_features_labels(const float* dense_dev, int nfields, int64_t nx, int64_t ny, int wavelet, int patch,
+                               int levels, double delta, float* feat_dev, float* label_dev, void* stream) {
+  if (!dense_dev || nfields <= 0 || patch <= 0 || levels <= 0 || levels > 8 || nx % patch || ny % patch || !feat_dev ||
+      !label_dev)
+    return WCS_E_ARG;
+  const int E = wavelet == WCS_BL53 ? patch + 1 : patch;
+  const size_t smem = (3 * size_t(E) * E + 256) * sizeof(double);
+  double grid[EPS_N];
+  for (int k = 0; k < EPS_N; ++k) grid[k] = std::pow(10.0, -7.0 + k / 8.0);
+  if (cudaMemcpyToSymbol(c_eps_grid, grid, sizeof(grid)) != cudaSuccess) return WCS_E_CUDA;
+  if (smem > 232448) return WCS_E_UNSUPPORTED;
+  if (cudaFuncSetAttribute(features_labels, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+    return WCS_E_CUDA;
+  const int npx = int(nx / patch), npy = int(ny / patch);
+  features_labels<<<npx * npy, 256, smem, static_cast<cudaStream_t>(stream)>>>(
+      dense_dev, nfields, int(nx), int(ny), npx, patch, levels, wavelet, delta, feat_dev, label_dev);
+  return cudaGetLastError() == cudaSuccess ? WCS_OK : WCS_E_CUDA;
+}
+
+wcs_status wcs_mlp_create(int nin, wcs_mlp** out) {
+  if (!out || nin <= 0 || nin > MLP_MAXIN) return WCS_E_ARG;
+  wcs_mlp* m = new wcs_mlp();
+  m->nin = nin;
+  const int np = nparam(nin);
+  if (cudaMalloc(&m->w, np * 4) != cudaSuccess || cudaMalloc(&m->m1, np * 4) != cudaSuccess ||
+      cudaMalloc(&m->m2, np * 4) != cudaSuccess || cudaMalloc(&m->g, np * 4) != cudaSuccess ||
+      cudaMalloc(&m->loss, 4) != cudaSuccess) {
+    cudaGetLastError();
+    wcs_mlp_destroy(m);
+    return WCS_E_OOM;
+  }
+  cudaMemset(m->w, 0, np * 4);
+  cudaMemset(m->m1, 0, np * 4);
+  cudaMemset(m->m2, 0, np * 4);
+  *out = m;
+  return WCS_OK;
+}
+
+void wcs_mlp_destroy(wcs_mlp* m) {
+  if (!m) return;
+  cudaDeviceSynchronize();
+  cudaFree(m->w);
+  cudaFree(m->m1);
+  cudaFree(m->m2);
+  cudaFree(m->g);
+  cudaFree(m->loss);
+  delete m;
+}
+
+int wcs_mlp_nparam(const wcs_mlp* m) { return m ? nparam(m->nin) : -1; }
+
+wcs_status wcs_mlp_set_weights(wcs_mlp* m, const float* w_host) {
+  if (!m || !w_host) return WCS_E_ARG;
+  m->adam_t = 0;
+  const int np = nparam(m->nin);
+  cudaMemset(m->m1, 0, np * 4);
+  cudaMemset(m->m2, 0, np * 4);
+  return cudaMemcpy(m->w, w_host, np * 4, cudaMemcpyHostToDevice) == cudaSuccess ? WCS_OK : WCS_E_CUDA;
+}
+
+wcs_status wcs_mlp_get_weights(const wcs_mlp* m, float* w_host) {
+  if (!m || !w_host) return WCS_E_ARG;
+  return cudaMemcpy(w_host, m->w, nparam(m->nin) * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? WCS_OK : WCS_E_CUDA;
+}
+
+// Loss and gradient of the mean squared error on n samples (device X [n][nin]
+// and t [n]); gradient to host.
+wcs_status wcs_mlp_grad(wcs_mlp* m, const float* X_dev, const float* t_dev, int n, float* grad_host, float* loss_host) {
+  if (!m || !X_dev || !t_dev || n <= 0) return WCS_E_ARG;
+  const int np = nparam(m->nin);
+  float *gs = nullptr, *ls = nullptr;
+  if (cudaMalloc(&gs, size_t(n) * np * 4) != cudaSuccess || cudaMalloc(&ls, size_t(n) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(gs);
+    return WCS_E_OOM;
+  }
+  mlp_sample_grads<<<(n + 127) / 128, 128>>>(m->w, m->nin, X_dev, t_dev, nullptr, n, gs, ls);
+  mlp_reduce<<<(np + 255) / 256, 256>>>(gs, n, np, m->g, ls, m->loss);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && grad_host) e = cudaMemcpy(grad_host, m->g, np * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && loss_host) e = cudaMemcpy(loss_host, m->loss, 4, cudaMemcpyDeviceToHost);
+  cudaFree(gs);
+  cudaFree(ls);
+  return e == cudaSuccess ? WCS_OK : WCS_E_CUDA;
+}
+
+// Adam on minibatches; batches[e*nb + b] lists minibatch b of epoch e as
+// indices into X / t (host array of epochs * n_batches * batch ints).
+wcs_status wcs_mlp_train(wcs_mlp* m, const float* X_dev, const float* t_dev, int n, const int* batches_host, int epochs,
+                         int batch, float lr, float* loss_history_host) {
+  if (!m || !X_dev || !t_dev || n <= 0 || batch <= 0 || batch > n || epochs <= 0 || !batches_host) return WCS_E_ARG;
+  const int np = nparam(m->nin);
+  const int nb = n / batch;
+  float *gs = nullptr, *ls = nullptr;
+  int* idx = nullptr;
+  if (cudaMalloc(&gs, size_t(batch) * np * 4) != cudaSuccess || cudaMalloc(&ls, size_t(batch) * 4) != cudaSuccess ||
+      cudaMalloc(&idx, size_t(epochs) * nb * batch * 4) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(gs);
+    cudaFree(ls);
+    return WCS_E_OOM;
+  }
+  cudaError_t e = cudaMemcpy(idx, batches_host, size_t(epochs) * nb * batch * 4, cudaMemcpyHostToDevice);
+  const float b1 = 0.9f, b2 = 0.999f;
+  for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+      mlp_sample_grads<<<(batch + 127) / 128, 128>>>(m->w, m->nin, X_dev, t_dev, idx + (size_t(ep) * nb + b) * batch,
+                                                     batch, gs, ls);
+      mlp_reduce<<<(np + 255) / 256, 256>>>(gs, batch, np, m->g, ls, m->loss);
+      ++m->adam_t;
+      mlp_adam<<<(np + 255) / 256, 256>>>(m->w, m->g, m->m1, m->m2, np, lr, b1, b2, powf(b1, float(m->adam_t)),
+                                          powf(b2, float(m->adam_t)));
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && loss_history_host) e = cudaMemcpy(loss_history_host + ep, m->loss, 4, cudaMemcpyDeviceToHost);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(gs);
+  cudaFree(ls);
+  cudaFree(idx);
+  return e == cudaSuccess ? WCS_OK : WCS_E_CUDA;
+}
+
+wcs_status wcs_mlp_forward(wcs_mlp* m, const float* X_dev, int n, float* y_dev) {
+  if (!m || !X_dev || !y_dev || n <= 0) return WCS_E_ARG;
+  return launch_infer(m->w, m->nin, X_dev, n, y_dev, 0, 0, 0, nullptr, nullptr) == cudaSuccess ? WCS_OK : WCS_E_CUDA;
+}
+
+// Used by the simulation: per-patch eps from per-patch features.
+wcs_status wcs_mlp_eps(wcs_mlp* m, const float* feat_dev, int n, double lo, double hi, double fallback, double* eps_dev,
+                       void* stream) {
+  if (!m || !feat_dev || !eps_dev || n <= 0) return WCS_E_ARG;
+  return launch_infer(m->w, m->nin, feat_dev, n, nullptr, lo, hi, fallback, eps_dev, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? WCS_OK
+             : WCS_E_CUDA;
+}
+
+}  // extern "C"

@@ -45,6 +45,8 @@ struct PatchArgs {
   double eps, eps_edge;
   const double* eps_patch;      // optional per-patch threshold constant
   double omega, gamma, cfl;
+  float* feat;                   // FEAT kernels: per patch 6L features of the new state
+  float feat_inv_cnt[24];        // per feature group g: 1 / (fields x nodes of g)
   float omega32, gamma32, gm1_32;   // the same parameters rounded once on the host
   double gm1_64;
   long long ncell_x;            // cells along x (time accounting)
@@ -141,7 +143,7 @@ template <typename U> __device__ __forceinline__ void stg(unsigned char* p, U v)
 __device__ __forceinline__ unsigned long long dbl_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
 // The whole patch step for patch `pid` of the simulation described by `a`.
-template <int SCH, int WV, typename T, int ST, int P, int L, int MODE>
+template <int SCH, int WV, typename T, int ST, int P, int L, int MODE, int FEAT = 0>
 __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
   typedef typename C::S S;
@@ -526,6 +528,13 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   // the shared column x = P of every field (lane = field).
   bool bad = false;
   static_assert(F * C::WR + (C::NCW > 0 ? 1 : 0) <= NWARP, "not enough warps for the fused pass");
+  // FEAT: energy and max of the details before the threshold per group
+  // (l, S): l = max(cx, cy), S = the axes of class l (x, y or both); sums
+  // per warp go to the record staging area (idle after the decode).
+  static_assert(size_t(NWARP) * 6 * L * 4 <= 4096, "feature sums do not fit in the staging area");
+  float cf2[L + 1], cfm[L + 1];  // the column warp's lane (its field): group (cy, y)
+#pragma unroll
+  for (int c = 0; c <= L; ++c) { cf2[c] = 0.0f; cfm[c] = 0.0f; }
   if (warp < F * C::WR) {
     const int f = warp / C::WR, h = warp - f * C::WR;
     const int x = 32 * h + lane;
@@ -540,11 +549,31 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     unsigned int myw[(E + 31) / 32];
 #pragma unroll
     for (int k = 0; k < (E + 31) / 32; ++k) myw[k] = 0u;
+    // FEAT, this lane: group (cx, x) for cy < cx, (cx, xy) for cy == cx,
+    // (cy, y) for cy > cx (cy is a constant of the unrolled row)
+    float fx2 = 0.0f, fxm = 0.0f, fb2 = 0.0f, fbm = 0.0f, fc2[L + 1], fcm[L + 1];
+#pragma unroll
+    for (int c = 0; c <= L; ++c) { fc2[c] = 0.0f; fcm[c] = 0.0f; }
     T v[E];
 #pragma unroll
     for (int y = 0; y < E; ++y) v[y] = valid ? col[y * PW] : T(0);
     auto node = [&](int y) {
       const int cy = node_class<L>(y);
+      if constexpr (FEAT) {
+        if (valid && (cx | cy)) {
+          const float d = float(v[y]), d2 = d * d, ad = fabsf(d);
+          if (cy > cx) {
+            fc2[cy] += d2;
+            fcm[cy] = fmaxf(fcm[cy], ad);
+          } else if (cy == cx) {
+            fb2 += d2;
+            fbm = fmaxf(fbm, ad);
+          } else {
+            fx2 += d2;
+            fxm = fmaxf(fxm, ad);
+          }
+        }
+      }
       bool keep = false;
       if (valid && (cx | cy)) {
         const bool yedge = WV == WV_BL53 && (y == 0 || y == P);  // folds: y is a constant here
@@ -567,6 +596,26 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       const int y = 32 * k + lane;
       if (y < E) mw[f * NW + y * C::WR + h] = myw[k];
     }
+    if constexpr (FEAT) {  // warp sums per group, fixed shuffle order
+      float* fw = reinterpret_cast<float*>(stage) + warp * 6 * L;
+#pragma unroll
+      for (int l = 1; l <= L; ++l) {
+        float e[3] = {cx == l ? fx2 : 0.0f, fc2[l], cx == l ? fb2 : 0.0f};
+        float m[3] = {cx == l ? fxm : 0.0f, fcm[l], cx == l ? fbm : 0.0f};
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+#pragma unroll
+          for (int o = 16; o >= 1; o >>= 1) {
+            e[g] = e[g] + __shfl_down_sync(0xffffffffu, e[g], o);
+            m[g] = fmaxf(m[g], __shfl_down_sync(0xffffffffu, m[g], o));
+          }
+          if (lane == 0) {
+            fw[2 * (3 * (l - 1) + g)] = e[g];
+            fw[2 * (3 * (l - 1) + g) + 1] = m[g];
+          }
+        }
+      }
+    }
   } else if (C::NCW > 0 && warp == F * C::WR && lane < F) {
     const int f = lane;
     T* col = tiles + win_out(f) + P;
@@ -578,6 +627,13 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     for (int y = 0; y < E; ++y) v[y] = col[y * PW];
     auto node = [&](int y) {
       const int cy = node_class<L>(y);
+      if constexpr (FEAT) {
+        if (cy) {
+          const float d = float(v[y]);
+          cf2[cy] += d * d;
+          cfm[cy] = fmaxf(cfm[cy], fabsf(d));
+        }
+      }
       if (!isfinite(v[y])) bad = true;
       if (cy) {  // x = P is a coarse x-node; every node of the column is on an edge line
         if (fabs(v[y]) >= tau_e[cy]) cw[y >> 5] |= 1u << (y & 31);
@@ -589,10 +645,46 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
 #pragma unroll
     for (int k = 0; k < C::NCW; ++k) mw[f * NW + C::NRW + k] = cw[k];
   }
+  if constexpr (FEAT && C::NCW > 0) {  // the column warp's lanes (fields) in lane order
+    if (warp == F * C::WR) {
+      float* fw = reinterpret_cast<float*>(stage) + warp * 6 * L;
+#pragma unroll
+      for (int l = 1; l <= L; ++l) {
+        float e = cf2[l], m = cfm[l];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+          e = e + __shfl_down_sync(0xffffffffu, e, o);
+          m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+        }
+        if (lane == 0) {
+          const int g = 3 * (l - 1);
+          fw[2 * g] = 0.0f;
+          fw[2 * g + 1] = 0.0f;
+          fw[2 * (g + 1)] = e;
+          fw[2 * (g + 1) + 1] = m;
+          fw[2 * (g + 2)] = 0.0f;
+          fw[2 * (g + 2) + 1] = 0.0f;
+        }
+      }
+    }
+  }
   if (bad) {
     if (atomicOr(&a.ctl->status, STAT_NAN) == 0u) a.ctl->err_step = int(a.step);
   }
   __syncthreads();
+  if constexpr (FEAT) {  // features of the new state: sums over the warps in warp order
+    if (warp == NWARP - 1 && lane < 3 * L) {
+      const float* fw = reinterpret_cast<const float*>(stage);
+      constexpr int NFW = F * C::WR + (C::NCW > 0 ? 1 : 0);
+      float e = 0.0f, m = 0.0f;
+      for (int w = 0; w < NFW; ++w) {
+        e = e + fw[w * 6 * L + 2 * lane];
+        m = fmaxf(m, fw[w * 6 * L + 2 * lane + 1]);
+      }
+      a.feat[size_t(pid) * 6 * L + 2 * lane] = log10f(e * a.feat_inv_cnt[lane] + 1e-30f);
+      a.feat[size_t(pid) * 6 * L + 2 * lane + 1] = log10f(m + 1e-30f);
+    }
+  }
   // per-field scans, list of non-zero words, band scales, section sizes
   if (warp < F) {
     const int f = warp;
@@ -854,9 +946,9 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
 }
 
 // One simulation: block b is patch b.
-template <int SCH, int WV, typename T, int ST, int P, int L, int MODE>
+template <int SCH, int WV, typename T, int ST, int P, int L, int MODE, int FEAT = 0>
 __global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1) patch_kernel(PatchArgs a) {
-  patch_body<SCH, WV, T, ST, P, L, MODE>(a, int(blockIdx.x));
+  patch_body<SCH, WV, T, ST, P, L, MODE, FEAT>(a, int(blockIdx.x));
 }
 
 // Many simulations in one launch: block b steps patch (work[b] & 0xfffff) of

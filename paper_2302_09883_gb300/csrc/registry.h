@@ -17,6 +17,8 @@ struct KernelEntry {
   cudaError_t (*launch)(int mode, const PatchArgs& a, int npatch, cudaStream_t s);
   // step of many simulations: nblocks entries of work, args in device memory
   cudaError_t (*launch_batch)(const PatchArgs* args, const unsigned int* work, int nblocks, cudaStream_t s);
+  // step that also writes the per-patch features (learned threshold)
+  cudaError_t (*launch_feat)(const PatchArgs& a, int npatch, cudaStream_t s);
   // sets the kernels' shared-memory attribute (once, before any capture)
   cudaError_t (*prepare)();
 };
