@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-euler", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     return ap.parse_args()
 
 
@@ -335,6 +336,113 @@ def batch_section(torch, K, W, flush, bs, nsims=96, quality_steps=500, eps_sweep
             "compression_ratio": unc / comp, "quality_steps": quality_steps, "quality": quality}
 
 
+def learned_section(torch, K, W, flush, bs, n_eval=1024, steps=1000, deltas=(3e-6, 1e-5, 3e-5),
+                    eps_sweep=(1e-6, 3e-6, 1e-5, 3e-5, 1e-4, 3e-4)):
+    """Per-patch eps from the network against one uniform eps, D2Q9 FP32/BF16,
+    BL5/3 P = 64, L = 4, tau 0.6.  Training data: dense FP32 snapshots
+    (t = 0, 100, 300, 600) of 512^2 runs from eight seeded initial states
+    (Gaussian bumps, amplitude U(0.01, 0.1), width U(4, 32), random centre;
+    shear waves with N(0, 1e-4) noise), features and labels by the library's
+    kernels for every delta.  Evaluation: a 1024^2 Gaussian bump (amplitude
+    0.05, width 40, centred) for `steps` steps against the uncompressed run;
+    the uniform sweep's ratio is interpolated (log-log) at the learned run's
+    error of u, and both step times are measured like the headline."""
+    from paper_2302_09883_gb300 import Dense, Sim, learned
+    P, L, tau = 64, 4, 0.6
+    rng = np.random.default_rng(123)
+    snaps = []
+    for k in range(8):
+        n = 512
+        if k % 2 == 0:
+            f = inputs.gaussian_bump_device(n, rng.uniform(0.01, 0.1), rng.uniform(4, 32), rng.uniform(0, n),
+                                            rng.uniform(0, n))
+        else:
+            f = inputs.shear_wave(n, seed=100 + k)
+        d = Dense("d2q9", n, n, tau=tau, stream=bs)
+        d.init_macro(f)
+        done = 0
+        for t in (0, 100, 300, 600):
+            d.step(t - done)
+            done = t
+            snaps.append(torch.from_numpy(np.stack([d.export_field(i) for i in range(9)]).astype(np.float32)).cuda())
+        d.close()
+    fe = lambda sp: inputs.gaussian_bump_device(n_eval, 0.05, 40.0, n_eval / 2, n_eval / 2)
+    d = Dense("d2q9", n_eval, n_eval, tau=tau, stream=bs)
+    d.init_macro(fe(None))
+    d.step(steps)
+    rd, uxd, uyd = velocity_rho(np.stack([d.export_field(i) for i in range(9)]))
+    d.close()
+
+    def evaluate(sim):
+        sim.init_macro(fe(None))
+        sim.step(steps)
+        sim.sync()
+        rc, uxc, uyc = velocity_rho(sim.export_field(-1))
+        st = sim.stats()
+        return {"rel_l2_u": rel_l2(np.stack([uxc, uyc]), np.stack([uxd, uyd])), "rel_l2_rho": rel_l2(rc, rd),
+                "compression_ratio": st["uncompressed_bytes"] / sim.compressed_bytes(),
+                "record_ratio": st["uncompressed_bytes"] / st["live_bytes"]}
+
+    uniform = []
+    for eps in eps_sweep:
+        c = Sim("d2q9", "bl53", n_eval, n_eval, P, L, eps, prec="f32", store="bf16", tau=tau, arena_factor=0.5,
+                stream=bs)
+        uniform.append(dict(eps=eps, **evaluate(c)))
+        c.close()
+    def uniform_ratio_at(err, key):
+        pts = sorted((q["rel_l2_u"], q[key]) for q in uniform)
+        xs = np.log([p[0] for p in pts])
+        ys = np.log([p[1] for p in pts])
+        if not (xs[0] <= np.log(err) <= xs[-1]):
+            return None
+        return float(np.exp(np.interp(np.log(err), xs, ys)))
+
+    runs = []
+    for delta in deltas:
+        X, T = [], []
+        for u in snaps:
+            f_, l_ = learned.features_labels(u, P, L, delta)
+            X.append(f_)
+            T.append(l_)
+        X, T = torch.cat(X), torch.cat(T)
+        m, hist = learned.fit(X, T, epochs=200, batch=128, lr=2e-3, seed=1)
+        c = Sim("d2q9", "bl53", n_eval, n_eval, P, L, 1e-5, prec="f32", store="bf16", tau=tau, arena_factor=0.5,
+                stream=bs)
+        learned.use_mlp(c, m, 1e-7, 1e-2)
+        r = evaluate(c)
+        _, eps_p = learned.patch_data(c, L)
+        c.close()
+        ur = uniform_ratio_at(r["rel_l2_u"], "compression_ratio")
+        urr = uniform_ratio_at(r["rel_l2_u"], "record_ratio")
+        runs.append(dict(delta=delta, n_train=int(X.shape[0]), label_mean=float(T.mean()), label_std=float(T.std()),
+                         train_loss_first=float(hist[0]), train_loss_last=float(hist[-1]),
+                         eps_patch_log10_min=float(np.log10(eps_p.min())),
+                         eps_patch_log10_max=float(np.log10(eps_p.max())),
+                         uniform_ratio_at_same_error=ur, ratio_gain=(r["compression_ratio"] / ur) if ur else None,
+                         uniform_record_ratio_at_same_error=urr,
+                         record_ratio_gain=(r["record_ratio"] / urr) if urr else None, **r))
+        keep = m
+    # step time: learned mode (features + inference) vs uniform at the same size
+    times = {}
+    for mode in ("uniform", "learned"):
+        c = Sim("d2q9", "bl53", n_eval, n_eval, P, L, 1e-5, prec="f32", store="bf16", tau=tau, arena_factor=0.5,
+                stream=bs)
+        if mode == "learned":
+            learned.use_mlp(c, keep, 1e-7, 1e-2)
+        c.init_macro(fe(None))
+        c.step(W)
+        c.sync()
+        torch.cuda.synchronize()
+        ms = timed_steps(torch, c, bs, K, flush)
+        c.sync()
+        c.close()
+        times[mode] = ms / K
+    return {"workload": "d2q9_bl53_bump_1024_learned_eps", "steps": steps, "P": P, "levels": L,
+            "network": "6L=24 -> 64 -> 64 -> 1 GELU FP32", "uniform": uniform, "learned": runs,
+            "ms_per_step_uniform": times["uniform"], "ms_per_step_learned": times["learned"],
+            "mlups_learned": n_eval * n_eval / (times["learned"] * 1e-3) / 1e6}
+
+
 def roofline_bytes(sim, w):
     """Algorithmic bytes of one step launch: records of state n read, records
     of state n+1 written, ghost rings read and written, patch tables, the
@@ -540,6 +648,10 @@ def main():
     if not args.no_batch:
         batch = batch_section(torch, K, W, flush, bs)
 
+    learned_eps = None
+    if not args.no_learned:
+        learned_eps = learned_section(torch, K, W, flush, bs)
+
     mlups = lu * K * world / (ms * 1e-3) / 1e6
     peaks = {}
     try:
@@ -594,6 +706,7 @@ def main():
             "gpu_launches": K,
             "euler": euler,
             "batch": batch,
+            "learned_eps": learned_eps,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

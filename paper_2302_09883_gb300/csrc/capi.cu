@@ -25,6 +25,10 @@
 #include "registry.h"
 
 namespace wcs {
+const float* mlp_kernel_weights(const wcs_mlp* m);  // defined with the network
+}
+
+namespace wcs {
 void reg_d2q9_haar_f64_p32l3(std::vector<KernelEntry>&);
 void reg_d2q9_bl53_f64_p32l3(std::vector<KernelEntry>&);
 void reg_d2q9_bl53_bf16_p64l4(std::vector<KernelEntry>&);
@@ -408,11 +412,14 @@ wcs_status wcs_step(wcs_sim* s, int64_t n) {
   for (int64_t i = 0; i < n; ++i) {
     const int64_t k = s->nstep;
     if (s->mlp) {
-      // the step writes the features of the new state; the network turns
-      // them into the per-patch eps of the next step
-      CK(s->ke.launch_feat(step_args(s, k), s->npatch, s->stream));
-      const wcs_status st = wcs_mlp_eps(s->mlp, s->feat, s->npatch, s->eps_lo, s->eps_hi, s->eps, s->eps_patch, s->stream);
-      if (st != WCS_OK) return fail(s, st, "mlp inference launch failed");
+      // the step writes the features of its new state, and one warp of
+      // each patch runs the network on them for the next step's eps
+      wcs::PatchArgs a = step_args(s, k);
+      a.mlp_wt = wcs::mlp_kernel_weights(s->mlp);
+      a.eps_next = s->eps_patch;
+      a.eps_lo = s->eps_lo;
+      a.eps_hi = s->eps_hi;
+      CK(s->ke.launch_feat(a, s->npatch, s->stream));
     } else {
       CK(s->ke.launch(wcs::MODE_STEP, step_args(s, k), s->npatch, s->stream));
     }

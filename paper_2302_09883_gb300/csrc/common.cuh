@@ -271,4 +271,7 @@ __device__ __forceinline__ unsigned warp_incl_scan(unsigned v) {
   return v;
 }
 
+// GELU(x) = x Phi(x) with the CUDA erff; the learned threshold's activation.
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
 }  // namespace wcs

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) features_labels(const float* __restrict__
 }
 
 // ------------------------------------------------------------------ MLP
-__device__ inline float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ inline float gelu(float x) { return wcs::gelu_f(x); }
 __device__ inline float gelu_grad(float x) {
   return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
@@ -420,6 +420,7 @@ cudaError_t launch_infer(const float* w, int nin, const float* X, int n, float* 
 struct wcs_mlp {
   int nin = 8;
   float* w = nullptr;
+  float* wt = nullptr;  // the step kernel's layout: W1 and W2 transposed
   float* m1 = nullptr;
   float* m2 = nullptr;
   float* g = nullptr;
@@ -427,6 +428,31 @@ struct wcs_mlp {
   int64_t adam_t = 0;
   std::string err;
 };
+
+namespace {
+// Rebuilds the kernel-layout copy from host weights w (parameter order).
+cudaError_t upload_kernel_layout(wcs_mlp* m, const float* w) {
+  const int H = MLP_NH, nin = m->nin;
+  std::vector<float> t(nparam(nin));
+  for (int j = 0; j < H; ++j)
+    for (int i = 0; i < nin; ++i) t[i * H + j] = w[j * nin + i];
+  const float* b1 = w + H * nin;
+  const float* W2 = b1 + H;
+  float* tb1 = t.data() + H * nin;
+  float* tW2 = tb1 + H;
+  for (int j = 0; j < H; ++j) tb1[j] = b1[j];
+  for (int j = 0; j < H; ++j)
+    for (int i = 0; i < H; ++i) tW2[i * H + j] = W2[j * H + i];
+  const int rest = H + H + 1;  // b2, W3, b3 unchanged
+  std::memcpy(tW2 + H * H, W2 + H * H, rest * sizeof(float));
+  return cudaMemcpy(m->wt, t.data(), t.size() * 4, cudaMemcpyHostToDevice);
+}
+}  // namespace
+
+namespace wcs {
+const float* mlp_kernel_weights(const wcs_mlp* m) { return m ? m->wt : nullptr; }
+int mlp_nin(const wcs_mlp* m) { return m ? m->nin : 0; }
+}  // namespace wcs
 
 extern "C" {
 
@@ -454,7 +480,8 @@ wcs_status wcs_mlp_create(int nin, wcs_mlp** out) {
   wcs_mlp* m = new wcs_mlp();
   m->nin = nin;
   const int np = nparam(nin);
-  if (cudaMalloc(&m->w, np * 4) != cudaSuccess || cudaMalloc(&m->m1, np * 4) != cudaSuccess ||
+  if (cudaMalloc(&m->w, np * 4) != cudaSuccess || cudaMalloc(&m->wt, np * 4) != cudaSuccess ||
+      cudaMalloc(&m->m1, np * 4) != cudaSuccess ||
       cudaMalloc(&m->m2, np * 4) != cudaSuccess || cudaMalloc(&m->g, np * 4) != cudaSuccess ||
       cudaMalloc(&m->loss, 4) != cudaSuccess) {
     cudaGetLastError();
@@ -462,6 +489,7 @@ wcs_status wcs_mlp_create(int nin, wcs_mlp** out) {
     return WCS_E_OOM;
   }
   cudaMemset(m->w, 0, np * 4);
+  cudaMemset(m->wt, 0, np * 4);
   cudaMemset(m->m1, 0, np * 4);
   cudaMemset(m->m2, 0, np * 4);
   *out = m;
@@ -472,6 +500,7 @@ void wcs_mlp_destroy(wcs_mlp* m) {
   if (!m) return;
   cudaDeviceSynchronize();
   cudaFree(m->w);
+  cudaFree(m->wt);
   cudaFree(m->m1);
   cudaFree(m->m2);
   cudaFree(m->g);
@@ -487,7 +516,8 @@ wcs_status wcs_mlp_set_weights(wcs_mlp* m, const float* w_host) {
   const int np = nparam(m->nin);
   cudaMemset(m->m1, 0, np * 4);
   cudaMemset(m->m2, 0, np * 4);
-  return cudaMemcpy(m->w, w_host, np * 4, cudaMemcpyHostToDevice) == cudaSuccess ? WCS_OK : WCS_E_CUDA;
+  if (cudaMemcpy(m->w, w_host, np * 4, cudaMemcpyHostToDevice) != cudaSuccess) return WCS_E_CUDA;
+  return upload_kernel_layout(m, w_host) == cudaSuccess ? WCS_OK : WCS_E_CUDA;
 }
 
 wcs_status wcs_mlp_get_weights(const wcs_mlp* m, float* w_host) {
@@ -547,6 +577,11 @@ wcs_status wcs_mlp_train(wcs_mlp* m, const float* X_dev, const float* t_dev, int
     if (e == cudaSuccess && loss_history_host) e = cudaMemcpy(loss_history_host + ep, m->loss, 4, cudaMemcpyDeviceToHost);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) {
+    std::vector<float> w(np);
+    e = cudaMemcpy(w.data(), m->w, np * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = upload_kernel_layout(m, w.data());
+  }
   cudaFree(gs);
   cudaFree(ls);
   cudaFree(idx);

@@ -47,6 +47,9 @@ struct PatchArgs {
   double omega, gamma, cfl;
   float* feat;                   // FEAT kernels: per patch 6L features of the new state
   float feat_inv_cnt[24];        // per feature group g: 1 / (fields x nodes of g)
+  const float* mlp_wt;           // FEAT kernels: network in kernel layout (null: none)
+  double* eps_next;              // FEAT kernels with a network: eps of the next step
+  double eps_lo, eps_hi;         // clamp of the network's eps; non-finite -> eps
   float omega32, gamma32, gm1_32;   // the same parameters rounded once on the host
   double gm1_64;
   long long ncell_x;            // cells along x (time accounting)
@@ -549,30 +552,20 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     unsigned int myw[(E + 31) / 32];
 #pragma unroll
     for (int k = 0; k < (E + 31) / 32; ++k) myw[k] = 0u;
-    // FEAT, this lane: group (cx, x) for cy < cx, (cx, xy) for cy == cx,
-    // (cy, y) for cy > cx (cy is a constant of the unrolled row)
-    float fx2 = 0.0f, fxm = 0.0f, fb2 = 0.0f, fbm = 0.0f, fc2[L + 1], fcm[L + 1];
+    // FEAT, this lane: energy and max per row class cy (branch-free; lanes
+    // past P hold zeros); the groups are formed once after the pass
+    float acc2[L + 1], accm[L + 1];
 #pragma unroll
-    for (int c = 0; c <= L; ++c) { fc2[c] = 0.0f; fcm[c] = 0.0f; }
+    for (int c = 0; c <= L; ++c) { acc2[c] = 0.0f; accm[c] = 0.0f; }
     T v[E];
 #pragma unroll
     for (int y = 0; y < E; ++y) v[y] = valid ? col[y * PW] : T(0);
     auto node = [&](int y) {
       const int cy = node_class<L>(y);
       if constexpr (FEAT) {
-        if (valid && (cx | cy)) {
-          const float d = float(v[y]), d2 = d * d, ad = fabsf(d);
-          if (cy > cx) {
-            fc2[cy] += d2;
-            fcm[cy] = fmaxf(fcm[cy], ad);
-          } else if (cy == cx) {
-            fb2 += d2;
-            fbm = fmaxf(fbm, ad);
-          } else {
-            fx2 += d2;
-            fxm = fmaxf(fxm, ad);
-          }
-        }
+        const float d = float(v[y]);
+        acc2[cy] = acc2[cy] + d * d;
+        accm[cy] = fmaxf(accm[cy], fabsf(d));
       }
       bool keep = false;
       if (valid && (cx | cy)) {
@@ -597,11 +590,16 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       if (y < E) mw[f * NW + y * C::WR + h] = myw[k];
     }
     if constexpr (FEAT) {  // warp sums per group, fixed shuffle order
+      // group (l, x): cx == l, rows cy < l; (l, y): cx < l, rows cy == l;
+      // (l, xy): cx == l, rows cy == l (the coarse node cx = cy = 0 is in none)
       float* fw = reinterpret_cast<float*>(stage) + warp * 6 * L;
+      float below2 = 0.0f, belowm = 0.0f;  // rows cy < l
 #pragma unroll
       for (int l = 1; l <= L; ++l) {
-        float e[3] = {cx == l ? fx2 : 0.0f, fc2[l], cx == l ? fb2 : 0.0f};
-        float m[3] = {cx == l ? fxm : 0.0f, fcm[l], cx == l ? fbm : 0.0f};
+        below2 = below2 + acc2[l - 1];
+        belowm = fmaxf(belowm, accm[l - 1]);
+        float e[3] = {cx == l ? below2 : 0.0f, cx < l ? acc2[l] : 0.0f, cx == l ? acc2[l] : 0.0f};
+        float m[3] = {cx == l ? belowm : 0.0f, cx < l ? accm[l] : 0.0f, cx == l ? accm[l] : 0.0f};
 #pragma unroll
         for (int g = 0; g < 3; ++g) {
 #pragma unroll
@@ -668,21 +666,83 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       }
     }
   }
+  constexpr int MLP_NP = 64 * 6 * L + 64 + 64 * 64 + 64 + 64 + 1;  // network parameters
+  if constexpr (FEAT) {
+    // the warps without a column of the fused pass stage the network's
+    // weights in the staging area, behind the feature sums
+    static_assert(NWARP > F * C::WR + 1, "no idle warp to stage the network");
+    static_assert(C::STG >= 4096 + MLP_NP * 4, "network weights do not fit in the staging area");
+    constexpr int W0 = F * C::WR + 1;
+    if (a.mlp_wt && warp >= W0) {
+      float* dst = reinterpret_cast<float*>(stage + 4096);
+      const int t = tid - W0 * 32, nt = (NWARP - W0) * 32;
+      const float4* src4 = reinterpret_cast<const float4*>(a.mlp_wt);
+      for (int i = t; i < MLP_NP / 4; i += nt) reinterpret_cast<float4*>(dst)[i] = __ldg(src4 + i);
+      for (int i = MLP_NP / 4 * 4 + t; i < MLP_NP; i += nt) dst[i] = __ldg(a.mlp_wt + i);
+    }
+  }
   if (bad) {
     if (atomicOr(&a.ctl->status, STAT_NAN) == 0u) a.ctl->err_step = int(a.step);
   }
   __syncthreads();
   if constexpr (FEAT) {  // features of the new state: sums over the warps in warp order
-    if (warp == NWARP - 1 && lane < 3 * L) {
+    if (warp == NWARP - 1) {
       const float* fw = reinterpret_cast<const float*>(stage);
       constexpr int NFW = F * C::WR + (C::NCW > 0 ? 1 : 0);
-      float e = 0.0f, m = 0.0f;
-      for (int w = 0; w < NFW; ++w) {
-        e = e + fw[w * 6 * L + 2 * lane];
-        m = fmaxf(m, fw[w * 6 * L + 2 * lane + 1]);
+      float fe = 0.0f, fm = 0.0f;
+      if (lane < 3 * L) {
+        float e = 0.0f, m = 0.0f;
+        for (int w = 0; w < NFW; ++w) {
+          e = e + fw[w * 6 * L + 2 * lane];
+          m = fmaxf(m, fw[w * 6 * L + 2 * lane + 1]);
+        }
+        fe = log10f(e * a.feat_inv_cnt[lane] + 1e-30f);
+        fm = log10f(m + 1e-30f);
+        a.feat[size_t(pid) * 6 * L + 2 * lane] = fe;
+        a.feat[size_t(pid) * 6 * L + 2 * lane + 1] = fm;
       }
-      a.feat[size_t(pid) * 6 * L + 2 * lane] = log10f(e * a.feat_inv_cnt[lane] + 1e-30f);
-      a.feat[size_t(pid) * 6 * L + 2 * lane + 1] = log10f(m + 1e-30f);
+      // the network (6L -> 64 -> 64 -> 1, GELU) on this warp alone, while
+      // the other warps go on: lane j owns hidden units j and j + 32
+      if (a.mlp_wt) {
+        constexpr int H = 64, NIN = 6 * L;
+        const float* W1T = reinterpret_cast<const float*>(stage + 4096);  // [NIN][H], staged above
+        const float* b1 = W1T + NIN * H;
+        const float* W2T = b1 + H;    // [H][H]
+        const float* b2 = W2T + H * H;
+        const float* W3 = b2 + H;
+        const float* b3 = W3 + H;
+        float h0 = b1[lane], h1 = b1[lane + 32];
+#pragma unroll
+        for (int g = 0; g < 3 * L; ++g) {
+          const float xe = __shfl_sync(0xffffffffu, fe, g), xm = __shfl_sync(0xffffffffu, fm, g);
+          h0 = __fmaf_rn(W1T[(2 * g) * H + lane], xe, h0);
+          h1 = __fmaf_rn(W1T[(2 * g) * H + lane + 32], xe, h1);
+          h0 = __fmaf_rn(W1T[(2 * g + 1) * H + lane], xm, h0);
+          h1 = __fmaf_rn(W1T[(2 * g + 1) * H + lane + 32], xm, h1);
+        }
+        const float a0 = gelu_f(h0), a1v = gelu_f(h1);
+        float z0 = b2[lane], z1 = b2[lane + 32];
+#pragma unroll 8
+        for (int i = 0; i < 32; ++i) {
+          const float u = __shfl_sync(0xffffffffu, a0, i);
+          z0 = __fmaf_rn(W2T[i * H + lane], u, z0);
+          z1 = __fmaf_rn(W2T[i * H + lane + 32], u, z1);
+        }
+#pragma unroll 8
+        for (int i = 0; i < 32; ++i) {
+          const float u = __shfl_sync(0xffffffffu, a1v, i);
+          z0 = __fmaf_rn(W2T[(i + 32) * H + lane], u, z0);
+          z1 = __fmaf_rn(W2T[(i + 32) * H + lane + 32], u, z1);
+        }
+        float y = W3[lane] * gelu_f(z0) + W3[lane + 32] * gelu_f(z1);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) y = y + __shfl_down_sync(0xffffffffu, y, o);
+        if (lane == 0) {
+          double e = pow(10.0, double(y + b3[0]));
+          if (!isfinite(e)) e = a.eps;
+          a.eps_next[pid] = e < a.eps_lo ? a.eps_lo : (e > a.eps_hi ? a.eps_hi : e);
+        }
+      }
     }
   }
   // per-field scans, list of non-zero words, band scales, section sizes

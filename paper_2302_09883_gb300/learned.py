@@ -111,3 +111,32 @@ def patch_data(sim, L):
     B.check(B.lib().wcs_sim_patch_data(sim.h, feat.ctypes.data_as(C.POINTER(C.c_float)),
                                        eps.ctypes.data_as(C.POINTER(C.c_double))), sim.h)
     return feat, eps
+
+
+def fit(X, t, epochs=200, batch=128, lr=2e-3, seed=0):
+    """Trains a network on features X (CUDA tensor (n, nin)) and targets t
+    (log10 eps).  The features are standardised for training (mean 0, unit
+    variance per input, on the device) and the standardisation is folded
+    into the first layer afterwards, so the returned network takes the raw
+    features that a learned-mode step writes.  Returns (Mlp, loss history)."""
+    import torch
+    X = X.float()
+    mu = X.mean(0)
+    sd = X.std(0).clamp_min(1e-3)
+    Xs = ((X - mu) / sd).contiguous()
+    nin = X.shape[1]
+    m = Mlp(nin, seed=seed)
+    w = m.weights()
+    w[-1] = float(t.float().mean())  # start at the mean target
+    m.set_weights(w)
+    hist = m.train(Xs, t.float().contiguous(), epochs=epochs, batch=batch, lr=lr, seed=seed)
+    w = m.weights()
+    W1 = w[:NH * nin].reshape(NH, nin).astype(np.float64)
+    b1 = w[NH * nin:NH * nin + NH].astype(np.float64)
+    mu_, sd_ = mu.double().cpu().numpy(), sd.double().cpu().numpy()
+    W1f = W1 / sd_[None, :]
+    b1f = b1 - W1f @ mu_
+    w[:NH * nin] = W1f.reshape(-1).astype(np.float32)
+    w[NH * nin:NH * nin + NH] = b1f.astype(np.float32)
+    m.set_weights(w)
+    return m, hist
