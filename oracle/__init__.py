@@ -71,6 +71,23 @@ def lib():
         L.orc_mlp_forward.argtypes = [i32, i32, dp, dp, i32, dp]
         L.orc_mlp_loss_grad.restype = dbl
         L.orc_mlp_loss_grad.argtypes = [i32, i32, dp, dp, dp, i32, dp]
+        L.orc_d3q19_equilibrium.argtypes = [i32, dbl, dbl, dbl, dbl, dp]
+        L.orc_d3q19_collide.argtypes = [i32, dp, dbl]
+        L.orc3_create.restype = vp
+        L.orc3_create.argtypes = [i32, i32, i32, i32, i64, i64, i64, i32, i32, dbl, dbl]
+        L.orc3_ref_create.restype = vp
+        L.orc3_ref_create.argtypes = [i32, i64, i64, i64, dbl]
+        L.orc3_destroy.argtypes = [vp]
+        L.orc3_init_macro.argtypes = [vp, dp, dp, dp, dp]
+        L.orc3_step.argtypes = [vp, i64]
+        L.orc3_export_all.argtypes = [vp, dp]
+        L.orc3_npatch.restype = i64
+        L.orc3_npatch.argtypes = [vp]
+        L.orc3_record_bytes.restype = i64
+        L.orc3_record_bytes.argtypes = [vp, i64]
+        L.orc3_record.argtypes = [vp, i64, C.c_char_p, i64]
+        L.orc3_stats.argtypes = [vp, dp]
+        L.orc3_set_patch_eps.argtypes = [vp, dp]
         L.orc_last_error.restype = C.c_char_p
         _lib = L
     return _lib
@@ -316,3 +333,82 @@ def mlp_loss_grad(w, X, t, nin, nh):
     g = np.zeros(mlp_nparam(nin, nh), np.float64)
     loss = lib().orc_mlp_loss_grad(nin, nh, _dp(w), _dp(X), _dp(t), X.shape[0], _dp(g))
     return loss, g
+
+
+# ------------------------------------------------------------------ D3Q19
+def d3q19_equilibrium(rho, ux, uy, uz, prec="f64"):
+    out = np.zeros(19, np.float64)
+    lib().orc_d3q19_equilibrium(PREC[prec], rho, ux, uy, uz, _dp(out))
+    return out
+
+
+def d3q19_collide(f, tau, prec="f64"):
+    a = np.array(f, np.float64)
+    lib().orc_d3q19_collide(PREC[prec], _dp(a), tau)
+    return a
+
+
+def _macro3(fields):
+    arrs = [np.ascontiguousarray(a, np.float64) for a in fields]
+    assert len(arrs) == 4 and all(a.ndim == 3 for a in arrs)
+    return arrs, [_dp(a) for a in arrs]
+
+
+class _Run3:
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc3_destroy(self.h)
+            self.h = None
+
+    def init_macro(self, fields):
+        """fields: rho, ux, uy, uz as (nz, ny, nx) arrays."""
+        arrs, ptrs = _macro3(fields)
+        _check(lib().orc3_init_macro(self.h, *ptrs))
+
+    def step(self, n=1):
+        _check(lib().orc3_step(self.h, n))
+
+    def export_all(self):
+        out = np.empty((19,) + self.shape, np.float64)
+        _check(lib().orc3_export_all(self.h, _dp(out)))
+        return out
+
+
+class OracleSim3(_Run3):
+    """Compressed-patch D3Q19 run on a periodic (nz, ny, nx) grid."""
+
+    def __init__(self, wavelet, nx, ny, nz, P, L, eps, prec="f64", store="f64", rule="const", tau=0.8):
+        self.P, self.L, self.shape = P, L, (nz, ny, nx)
+        self.h = lib().orc3_create(WAVELET[wavelet], PREC[prec], STORE[store], RULE[rule], nx, ny, nz, P, L, eps,
+                                   tau)
+        if not self.h:
+            raise RuntimeError("oracle: " + lib().orc_last_error().decode())
+
+    @property
+    def npatch(self):
+        return lib().orc3_npatch(self.h)
+
+    def record(self, p):
+        n = lib().orc3_record_bytes(self.h, p)
+        buf = C.create_string_buffer(n)
+        _check(lib().orc3_record(self.h, p, buf, n))
+        return buf.raw[:n]
+
+    def set_patch_eps(self, eps):
+        e = np.ascontiguousarray(eps, np.float64)
+        assert e.shape == (self.npatch,)
+        _check(lib().orc3_set_patch_eps(self.h, _dp(e)))
+
+    def stats(self):
+        out = np.zeros(32, np.float64)
+        _check(lib().orc3_stats(self.h, _dp(out)))
+        return {"coef_sums": out[:19].copy(), "nstep": int(out[20]), "shared_mismatch": int(out[22]),
+                "compressed_bytes": int(out[23])}
+
+
+class OracleRef3(_Run3):
+    """Uncompressed D3Q19 run on a periodic (nz, ny, nx) grid."""
+
+    def __init__(self, nx, ny, nz, prec="f64", tau=0.8):
+        self.shape = (nz, ny, nx)
+        self.h = lib().orc3_ref_create(PREC[prec], nx, ny, nz, tau)

@@ -13,6 +13,7 @@
 #include "mlp.hpp"
 #include "schemes.hpp"
 #include "sim.hpp"
+#include "sim3.hpp"
 #include "wavelet.hpp"
 
 using namespace orc;
@@ -27,6 +28,20 @@ struct Handle {
   std::unique_ptr<Ref<double>> r64;
   std::unique_ptr<Ref<float>> r32;
 };
+
+struct Handle3 {
+  std::unique_ptr<Sim3<double>> s64;
+  std::unique_ptr<Sim3<float>> s32;
+  std::unique_ptr<Ref3<double>> r64;
+  std::unique_ptr<Ref3<float>> r32;
+};
+
+template <class S> void export3(S& s, double* dst) {
+  auto U = s.decode_all();
+  const size_t n = U[0].size();
+  for (int f = 0; f < 19; ++f)
+    for (size_t g = 0; g < n; ++g) dst[f * n + g] = double(U[f][g]);
+}
 
 template <class F> int guard(F&& f) {
   try {
@@ -384,6 +399,132 @@ double orc_mlp_loss_grad(int nin, int nh, const double* w, const double* X, cons
   m.nin = nin;
   m.nh = nh;
   return mlp_loss_grad(m, w, X, t, B, g);
+}
+
+// ---------------------------------------------------------------- D3Q19
+int orc_d3q19_equilibrium(int prec, double rho, double ux, double uy, double uz, double* out) {
+  if (prec == 0) {
+    d3q19_equilibrium<double>(rho, ux, uy, uz, out);
+  } else {
+    float o[19];
+    d3q19_equilibrium<float>(float(rho), float(ux), float(uy), float(uz), o);
+    for (int i = 0; i < 19; ++i) out[i] = o[i];
+  }
+  return 0;
+}
+
+int orc_d3q19_collide(int prec, double* f, double tau) {
+  if (prec == 0) {
+    d3q19_collide<double>(f, 1.0 / tau);
+  } else {
+    float g[19];
+    for (int i = 0; i < 19; ++i) g[i] = float(f[i]);
+    d3q19_collide<float>(g, float(1.0 / tau));
+    for (int i = 0; i < 19; ++i) f[i] = g[i];
+  }
+  return 0;
+}
+
+// Compressed D3Q19 run on a periodic grid; prec 0 FP64, 1 FP32.
+void* orc3_create(int wavelet, int prec, int store, int rule, int64_t nx, int64_t ny, int64_t nz, int P, int L,
+                  double eps, double tau) {
+  Handle3* h = new Handle3();
+  const int rc = guard([&] {
+    if (prec == 0) h->s64.reset(new Sim3<double>(wavelet, store, rule, nx, ny, nz, P, L, eps, tau));
+    else h->s32.reset(new Sim3<float>(wavelet, store, rule, nx, ny, nz, P, L, eps, tau));
+  });
+  if (rc) {
+    delete h;
+    return nullptr;
+  }
+  return h;
+}
+
+void orc3_destroy(void* p) { delete static_cast<Handle3*>(p); }
+
+int orc3_init_macro(void* p, const double* rho, const double* ux, const double* uy, const double* uz) {
+  Handle3* h = static_cast<Handle3*>(p);
+  return guard([&] {
+    if (h->s64) h->s64->init_macro(rho, ux, uy, uz);
+    else if (h->s32) h->s32->init_macro(rho, ux, uy, uz);
+    else if (h->r64) h->r64->init_macro(rho, ux, uy, uz);
+    else h->r32->init_macro(rho, ux, uy, uz);
+  });
+}
+
+int orc3_step(void* p, int64_t n) {
+  Handle3* h = static_cast<Handle3*>(p);
+  return guard([&] {
+    for (int64_t i = 0; i < n; ++i) {
+      if (h->s64) h->s64->step();
+      else if (h->s32) h->s32->step();
+      else if (h->r64) h->r64->step();
+      else h->r32->step();
+    }
+  });
+}
+
+// All 19 fields, [f][z][y][x] (FP64 copies of the compute type).
+int orc3_export_all(void* p, double* dst) {
+  Handle3* h = static_cast<Handle3*>(p);
+  return guard([&] {
+    if (h->s64) export3(*h->s64, dst);
+    else if (h->s32) export3(*h->s32, dst);
+    else {
+      const size_t n = h->r64 ? h->r64->U[0].size() : h->r32->U[0].size();
+      for (int f = 0; f < 19; ++f)
+        for (size_t g = 0; g < n; ++g) dst[f * n + g] = h->r64 ? h->r64->U[f][g] : double(h->r32->U[f][g]);
+    }
+  });
+}
+
+int64_t orc3_npatch(void* p) {
+  Handle3* h = static_cast<Handle3*>(p);
+  return h->s64 ? h->s64->npatch() : h->s32->npatch();
+}
+
+int64_t orc3_record_bytes(void* p, int64_t patch) {
+  Handle3* h = static_cast<Handle3*>(p);
+  const auto& rec = h->s64 ? h->s64->rec : h->s32->rec;
+  if (patch < 0 || patch >= int64_t(rec.size())) return -1;
+  return int64_t(rec[patch].size());
+}
+
+int orc3_record(void* p, int64_t patch, uint8_t* dst, int64_t cap) {
+  Handle3* h = static_cast<Handle3*>(p);
+  const auto& rec = h->s64 ? h->s64->rec : h->s32->rec;
+  if (patch < 0 || patch >= int64_t(rec.size()) || cap < int64_t(rec[patch].size())) return 1;
+  std::memcpy(dst, rec[patch].data(), rec[patch].size());
+  return 0;
+}
+
+// out[0..18] coefficient sums, out[20] steps, out[22] shared mismatches,
+// out[23] record bytes.
+int orc3_stats(void* p, double* out) {
+  Handle3* h = static_cast<Handle3*>(p);
+  return guard([&] {
+    const auto cs = h->s64 ? h->s64->coef_sums() : h->s32->coef_sums();
+    for (int f = 0; f < 19; ++f) out[f] = cs[f];
+    out[20] = double(h->s64 ? h->s64->nstep : h->s32->nstep);
+    out[22] = double(h->s64 ? h->s64->shared_mismatch : h->s32->shared_mismatch);
+    out[23] = double(h->s64 ? h->s64->compressed_bytes() : h->s32->compressed_bytes());
+  });
+}
+
+int orc3_set_patch_eps(void* p, const double* eps) {
+  Handle3* h = static_cast<Handle3*>(p);
+  return guard([&] {
+    auto& e = h->s64 ? h->s64->eps_patch : h->s32->eps_patch;
+    for (size_t i = 0; i < e.size(); ++i) e[i] = eps[i];
+  });
+}
+
+// Uncompressed D3Q19 run.
+void* orc3_ref_create(int prec, int64_t nx, int64_t ny, int64_t nz, double tau) {
+  Handle3* h = new Handle3();
+  if (prec == 0) h->r64.reset(new Ref3<double>(nx, ny, nz, tau));
+  else h->r32.reset(new Ref3<float>(nx, ny, nz, tau));
+  return h;
 }
 
 }  // extern "C"

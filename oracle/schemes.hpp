@@ -5,7 +5,8 @@
 // with contraction off so that the float instantiation can be compared bit
 // for bit).
 //
-//  * D2Q9 BGK (not in the paper; textbook lattice Boltzmann): weights 4/9,
+//  * D2Q9 and D3Q19 BGK (not in the paper; textbook lattice Boltzmann).
+//    D2Q9 weights 4/9,
 //    1/9, 1/36; second-order equilibrium
 //      feq_i = w_i rho (1 + 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 |u|^2);
 //    collision f* = f - omega (f - feq), omega = 1/tau; pull streaming
@@ -70,6 +71,75 @@ template <class T> inline void d2q9_collide(T* f, T omega) {
   d2q9_moments<T>(f, rho, ux, uy);
   d2q9_equilibrium<T>(rho, ux, uy, feq);
   for (int i = 0; i < 9; ++i) f[i] = f[i] - omega * (f[i] - feq[i]);
+}
+
+// ---------------------------------------------------------------- D3Q19
+// D3Q19 BGK (not in the paper; textbook lattice Boltzmann): weights 1/3,
+// 1/18 (the six axis velocities), 1/36 (the twelve edge diagonals); the same
+// second-order equilibrium and BGK collision as D2Q9.  Numbering: 0 rest,
+// 1..6 = +x, -x, +y, -y, +z, -z, then the diagonals in pairs of opposites:
+// 7 (+,+,0) 8 (-,-,0) 9 (+,-,0) 10 (-,+,0) 11 (+,0,+) 12 (-,0,-) 13 (+,0,-)
+// 14 (-,0,+) 15 (0,+,+) 16 (0,-,-) 17 (0,+,-) 18 (0,-,+).
+static const int D3Q19_C[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                   {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                   {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                   {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+template <class T> inline T d3q19_w(int i) {
+  return i == 0 ? T(1.0 / 3.0) : (i <= 6 ? T(1.0 / 18.0) : T(1.0 / 36.0));
+}
+
+// c_i . u: the terms of the axes x, y, z in that order, the first one
+// taken with its sign, the others added or subtracted.
+template <class T> inline T d3q19_cu(int i, T ux, T uy, T uz) {
+  const T u[3] = {ux, uy, uz};
+  T s = T(0);
+  bool first = true;
+  for (int a = 0; a < 3; ++a) {
+    const int c = D3Q19_C[i][a];
+    if (c == 0) continue;
+    if (first) s = c > 0 ? u[a] : -u[a];
+    else s = c > 0 ? s + u[a] : s - u[a];
+    first = false;
+  }
+  return s;
+}
+
+template <class T> inline void d3q19_equilibrium(T rho, T ux, T uy, T uz, T* feq) {
+  const T usq = (ux * ux + uy * uy) + uz * uz;
+  for (int i = 0; i < 19; ++i) {
+    const T cu = d3q19_cu<T>(i, ux, uy, uz);
+    T t = T(1) + T(3) * cu;
+    t = t + (T(4.5) * cu) * cu;
+    t = t - T(1.5) * usq;
+    feq[i] = (d3q19_w<T>(i) * rho) * t;
+  }
+}
+
+// rho = f_0 + ... + f_18 left to right; j_a runs over i = 1..18 in order,
+// the first non-zero term taken with its sign.
+template <class T> inline void d3q19_moments(const T* f, T& rho, T* u) {
+  rho = f[0];
+  for (int i = 1; i < 19; ++i) rho = rho + f[i];
+  for (int a = 0; a < 3; ++a) {
+    T j = T(0);
+    bool first = true;
+    for (int i = 1; i < 19; ++i) {
+      const int c = D3Q19_C[i][a];
+      if (c == 0) continue;
+      if (first) j = c > 0 ? f[i] : -f[i];
+      else j = c > 0 ? j + f[i] : j - f[i];
+      first = false;
+    }
+    u[a] = j / rho;
+  }
+}
+
+template <class T> inline void d3q19_collide(T* f, T omega) {
+  T rho, u[3], feq[19];
+  d3q19_moments<T>(f, rho, u);
+  d3q19_equilibrium<T>(rho, u[0], u[1], u[2], feq);
+  for (int i = 0; i < 19; ++i) f[i] = f[i] - omega * (f[i] - feq[i]);
 }
 
 // ---------------------------------------------------------------- Euler 2-D

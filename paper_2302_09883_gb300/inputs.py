@@ -99,6 +99,33 @@ def initial_fields(w, n=None, seed=0):
     raise ValueError(w["init"])
 
 
+def taylor_green_3d(n, u0=0.04, rho0=1.0):
+    """Decaying Taylor-Green vortex on an n^3 periodic node grid (k = 2 pi/n):
+    u = u0 (sin kx cos ky cos kz, -cos kx sin ky cos kz, 0), pressure
+    rho0 u0^2/16 (cos 2kx + cos 2ky)(cos 2kz + 2), rho = rho0 + 3 p (lattice
+    c_s^2 = 1/3).  Arrays (z, y, x)."""
+    k = 2.0 * np.pi / n
+    i = np.arange(n, dtype=np.float64) * k
+    Z, Y, X = np.meshgrid(i, i, i, indexing="ij")
+    ux = u0 * np.sin(X) * np.cos(Y) * np.cos(Z)
+    uy = -u0 * np.cos(X) * np.sin(Y) * np.cos(Z)
+    uz = np.zeros_like(ux)
+    p = rho0 * u0 * u0 / 16.0 * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0)
+    return [rho0 + 3.0 * p, ux, uy, uz]
+
+
+def shear_wave_3d(nx, ny, nz, u0=0.01, axis=1, noise=0.0, seed=0):
+    """rho = 1, u_x = u0 sin(2 pi s / n_s) with s the coordinate along
+    `axis` (1 = y, 2 = z), plus N(0, noise) per node; arrays (z, y, x)."""
+    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    s, n = (Y, ny) if axis == 1 else (Z, nz)
+    ux = u0 * np.sin(2 * np.pi * s / n)
+    if noise:
+        ux = ux + np.random.default_rng(seed).normal(0.0, noise, ux.shape)
+    z = np.zeros(ux.shape)
+    return [np.ones(ux.shape), ux.astype(np.float64), z, z.copy()]
+
+
 def gaussian_bump_device(n, amp, sigma, cx, cy, device="cuda"):
     """gaussian_bump with an arbitrary centre, generated directly in device
     memory (float64 torch tensors) for large batches."""
