@@ -51,8 +51,10 @@ typedef enum {
 } wcs_status;
 
 /* Schemes.  D2Q9: 9 populations, lattice units, periodic axes only.
- * EULER2D: (rho, rho u, rho v, E), perfect gas, Rusanov flux in the form of
- * the paper's eq. vf_scheme, periodic or outflow axes. */
+ * D3Q19: 19 populations on a 3-D grid (dims = 3), lattice units, periodic
+ * axes only; compiled for BL5/3, FP32 compute, F32 or BF16 details, P = 32
+ * or 16, L = 3.  EULER2D: (rho, rho u, rho v, E), perfect gas, Rusanov flux
+ * in the form of the paper's eq. vf_scheme, periodic or outflow axes. */
 typedef enum { WCS_D2Q9 = 0, WCS_D3Q19 = 1, WCS_EULER2D = 2 } wcs_scheme;
 
 /* Wavelets: folded BL5/3 on P+1 nodes (Sec. 2.1.2), or Haar on P cells. */
@@ -69,7 +71,7 @@ typedef enum { WCS_STORE_F64 = 0, WCS_STORE_F32 = 1, WCS_STORE_BF16 = 2, WCS_STO
 typedef enum { WCS_FP64 = 0, WCS_FP32 = 1 } wcs_prec;
 
 typedef struct {
-  int dims;               /* 2 */
+  int dims;               /* 2, or 3 for D3Q19 */
   int64_t n[3];           /* cells per axis (multiple of the patch size) */
   uint32_t periodic_mask; /* bit a set: axis a periodic, else outflow */
 } wcs_grid;
@@ -120,7 +122,8 @@ void wcs_destroy(wcs_sim* sim);
 /* Initial state from macroscopic fields, each a dense array of doubles laid
  * out [ny][nx] over the unique nodes (nx = n[0] cells, or n[0]+1 nodes on a
  * non-periodic BL5/3 axis), x fastest.  D2Q9: (rho, u_x, u_y), the state is
- * the equilibrium.  EULER2D: (rho, u, v, p).  fields[k] are host pointers if
+ * the equilibrium.  D3Q19: (rho, u_x, u_y, u_z) laid out [nz][ny][nx], the
+ * equilibrium.  EULER2D: (rho, u, v, p).  fields[k] are host pointers if
  * src_is_device == 0, else device pointers.  Encodes state 0. */
 wcs_status wcs_init_macro(wcs_sim* sim, const double* const* fields, int nfields, int src_is_device);
 
@@ -131,8 +134,9 @@ wcs_status wcs_step(wcs_sim* sim, int64_t n);
 /* Waits for the stream and returns the sticky device status as a status. */
 wcs_status wcs_sync(wcs_sim* sim);
 
-/* Decodes the current state of one field (D2Q9: population i; EULER2D: 0..3)
- * into a dense [ny][nx] array over the unique nodes.  dtype: 0 = double,
+/* Decodes the current state of one field (D2Q9/D3Q19: population i;
+ * EULER2D: 0..3) into a dense [ny][nx] ([nz][ny][nx] in 3-D) array over the
+ * unique nodes.  dtype: 0 = double,
  * 1 = float.  dst is a device pointer if dst_is_device, else host.
  * field = -1 writes every field, one after the other. */
 wcs_status wcs_export_field(wcs_sim* sim, int field, void* dst, int dst_is_device, int dtype);
@@ -172,6 +176,8 @@ wcs_status wcs_export_field_noalloc(wcs_sim* sim, int field, void* host_dst, int
 
 /* Number of patches and fields, dense node counts. */
 wcs_status wcs_shape(const wcs_sim* sim, int64_t* npatch, int* nfields, int64_t* nodes_x, int64_t* nodes_y);
+/* The same with the node counts of all three axes (nodes[2] = 1 in 2-D). */
+wcs_status wcs_shape3(const wcs_sim* sim, int64_t* npatch, int* nfields, int64_t* nodes);
 
 /* Per-launch device time of the last wcs_step kernels is not tracked here;
  * callers time with events on the stream.  This returns the stream. */

@@ -64,6 +64,7 @@ def lib():
         L.wcs_stats.argtypes = [vp, C.POINTER(StepStats)]
         L.wcs_export_record.argtypes = [vp, i64, vp, i64, C.POINTER(i64)]
         L.wcs_shape.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64), C.POINTER(i64)]
+        L.wcs_shape3.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64)]
         L.wcs_stream.restype = vp
         L.wcs_stream.argtypes = [vp]
         L.wcs_last_error.restype = C.c_char_p

@@ -23,6 +23,7 @@
 #include "../../include/wcsim.h"
 #include "patch2d.cuh"
 #include "registry.h"
+#include "patch3d.cuh"
 
 namespace wcs {
 const float* mlp_kernel_weights(const wcs_mlp* m);  // defined with the network
@@ -39,6 +40,14 @@ void reg_euler_bl53_i8_p64l4(std::vector<KernelEntry>&);
 void reg_euler_bl53_f64_p32l3(std::vector<KernelEntry>&);
 void reg_euler_bl53_bf16_p64l4(std::vector<KernelEntry>&);
 
+void reg_d3q19_p32l3(std::vector<Kernel3Entry>&);
+void reg_d3q19_p16l3(std::vector<Kernel3Entry>&);
+
+void register_all3(std::vector<Kernel3Entry>& v) {
+  reg_d3q19_p32l3(v);
+  reg_d3q19_p16l3(v);
+}
+
 void register_all(std::vector<KernelEntry>& v) {
   reg_d2q9_haar_f64_p32l3(v);
   reg_d2q9_bl53_f64_p32l3(v);
@@ -52,6 +61,7 @@ void register_all(std::vector<KernelEntry>& v) {
 }
 }  // namespace wcs
 
+using wcs::Kernel3Entry;
 using wcs::KernelEntry;
 
 namespace {
@@ -67,15 +77,32 @@ const std::vector<KernelEntry>& kernels() {
   return v;
 }
 
+const std::vector<Kernel3Entry>& kernels3() {
+  static std::vector<Kernel3Entry> v;
+  static bool done = false;
+  if (!done) {
+    wcs::register_all3(v);
+    done = true;
+  }
+  return v;
+}
+
 }  // namespace
 
 struct wcs_sim {
   int scheme = 0, wavelet = 0, prec = 0, store = 0, rule = 0, P = 0, L = 0;
   double eps = 0, tau = 1, cfl = 0.4, gamma = 1.4;
-  int64_t n[2] = {0, 0};
-  int per[2] = {1, 1};
-  int64_t G[2] = {0, 0};
-  int npx = 0, npy = 0, npatch = 0, F = 0, E = 0, NC1 = 0, nc = 0, nb = 0;
+  int dims = 2;
+  int64_t n[3] = {0, 0, 1};
+  int per[3] = {1, 1, 1};
+  int64_t G[3] = {0, 0, 1};
+  int npx = 0, npy = 0, npz = 1, npatch = 0, F = 0, E = 0, NC1 = 0, nc = 0, nb = 0;
+  int ring_vals = 0;  // ghost-ring values exported per patch (compute type)
+  // 3-D path: kernel, persistent grid and its per-CTA scratch
+  const Kernel3Entry* k3 = nullptr;
+  int grid3 = 0;
+  float* scratch = nullptr;
+  unsigned char* rbuf = nullptr;
   size_t tsize = 8;
   KernelEntry ke;
   cudaStream_t stream = nullptr;
@@ -189,13 +216,216 @@ static wcs::PatchArgs step_args(const wcs_sim* s, int64_t k) {
   return a;
 }
 
+// ------------------------------------------------------------ 3-D path
+static wcs::Patch3Args base_args3(const wcs_sim* s) {
+  wcs::Patch3Args a;
+  std::memset(&a, 0, sizeof(a));
+  a.npx = s->npx;
+  a.npy = s->npy;
+  a.npz = s->npz;
+  a.cap_out = s->cap;
+  a.ctl = s->ctl;
+  a.pstats = s->pstats;
+  a.band_factor = s->bfactor;
+  a.eps = s->eps;
+  a.eps_edge = s->eps;
+  a.eps_patch = s->eps_given ? s->eps_patch : nullptr;
+  a.omega = float(1.0 / s->tau);
+  a.scratch = s->scratch;
+  a.rbuf = s->rbuf;
+  a.slot_floats = s->k3->slot_floats;
+  a.slot_rbytes = s->k3->slot_rbytes;
+  a.G0 = s->G[0];
+  a.G1 = s->G[1];
+  a.G2 = s->G[2];
+  a.flags = unsigned(s->store) | (unsigned(s->wavelet) << 8);
+  return a;
+}
+
+static wcs::Patch3Args step_args3(const wcs_sim* s, int64_t k) {
+  wcs::Patch3Args a = base_args3(s);
+  const int in = int(k % 2), out = 1 - in;
+  a.step = k;
+  a.arena_in = s->arena[in];
+  a.tab_in = s->tab[in];
+  a.ring_in = static_cast<const float*>(s->ring[in]);
+  a.arena_out = s->arena[out];
+  a.tab_out = s->tab[out];
+  a.ring_out = static_cast<float*>(s->ring[out]);
+  a.cur_out = out;
+  a.cur_rst = in;
+  return a;
+}
+
+void wcs_destroy(wcs_sim* s);
+
+static wcs_status create3(const wcs_grid* grid, int scheme, int patch, int levels, double eps, const wcs_opts* opts,
+                          wcs_sim** out) {
+  if (grid->dims != 3 || scheme != WCS_D3Q19) return fail(nullptr, WCS_E_ARG, "3-D grids take the D3Q19 scheme");
+  if (opts->wavelet != WCS_BL53 || opts->compute != WCS_FP32)
+    return fail(nullptr, WCS_E_UNSUPPORTED, "the 3-D path is compiled for BL5/3 with FP32 compute");
+  const Kernel3Entry* ke = nullptr;
+  for (const Kernel3Entry& k : kernels3())
+    if (k.store == opts->detail_store && k.P == patch && k.L == levels) ke = &k;
+  if (!ke)
+    return fail(nullptr, WCS_E_UNSUPPORTED,
+                "no compiled 3-D kernel for store " + std::to_string(opts->detail_store) + " P " + std::to_string(patch) +
+                    " L " + std::to_string(levels));
+  for (int a = 0; a < 3; ++a)
+    if (grid->n[a] <= 0 || grid->n[a] % patch) return fail(nullptr, WCS_E_ARG, "grid not a multiple of the patch size");
+  if ((grid->periodic_mask & 7u) != 7u) return fail(nullptr, WCS_E_ARG, "D3Q19 needs periodic axes");
+  if (opts->rule < 0 || opts->rule > 2) return fail(nullptr, WCS_E_ARG, "bad threshold rule");
+  {
+    static std::mutex mu;
+    static std::vector<const Kernel3Entry*> prepared;
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(prepared.begin(), prepared.end(), ke) == prepared.end()) {
+      const cudaError_t e = ke->prepare();
+      if (e != cudaSuccess) return fail(nullptr, WCS_E_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+      prepared.push_back(ke);
+    }
+  }
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(nullptr, WCS_E_CUDA, "device query failed");
+  wcs_sim* s = new wcs_sim();
+  s->dims = 3;
+  s->k3 = ke;
+  s->scheme = scheme;
+  s->wavelet = opts->wavelet;
+  s->prec = opts->compute;
+  s->store = opts->detail_store;
+  s->rule = opts->rule;
+  s->P = patch;
+  s->L = levels;
+  s->eps = eps;
+  s->tau = opts->tau > 0 ? opts->tau : 1.0;
+  s->stream = static_cast<cudaStream_t>(opts->cuda_stream);
+  for (int a = 0; a < 3; ++a) {
+    s->n[a] = grid->n[a];
+    s->per[a] = 1;
+    s->G[a] = grid->n[a];
+  }
+  s->npx = int(s->n[0] / patch);
+  s->npy = int(s->n[1] / patch);
+  s->npz = int(s->n[2] / patch);
+  s->npatch = s->npx * s->npy * s->npz;
+  s->F = 19;
+  s->E = patch + 1;
+  s->NC1 = (patch >> levels) + 1;
+  s->nc = s->NC1 * s->NC1 * s->NC1;
+  s->nb = (levels + 1) * (levels + 1) * (levels + 1);
+  s->tsize = 4;
+  s->ring_vals = ke->ring;
+  s->grid3 = std::min(s->npatch, nsm);
+
+  // threshold multiplier of each band (c_x slowest, then c_y, c_z fastest)
+  std::vector<double> bf(s->nb);
+  for (int cx = 0; cx <= levels; ++cx)
+    for (int cy = 0; cy <= levels; ++cy)
+      for (int cz = 0; cz <= levels; ++cz) {
+        const int b = (cx * (levels + 1) + cy) * (levels + 1) + cz;
+        int sum = 0, mx = 0;
+        for (int c : {cx, cy, cz}) {
+          const int m = c == 0 ? levels : c;
+          sum += m - 1;
+          mx = std::max(mx, m);
+        }
+        bf[b] = s->rule == WCS_RULE_CONST ? 1.0
+                                          : (s->rule == WCS_RULE_ACCUM ? std::ldexp(1.0, -sum) : std::ldexp(1.0, -(mx - 1)));
+      }
+
+  wcs_status st;
+  const size_t state_bytes = size_t(19) * size_t(s->G[0]) * size_t(s->G[1]) * size_t(s->G[2]) * 4;
+  const double factor = opts->arena_factor > 0 ? opts->arena_factor : 0.25;
+  s->cap = (unsigned long long)(std::max(double(state_bytes) * factor, double(s->npatch) * 65536.0) + 255) / 256 * 256;
+  for (int b = 0; b < 2; ++b) {
+    if ((st = dalloc(s, (void**)&s->arena[b], s->cap)) != WCS_OK) goto bad;
+    if ((st = dalloc(s, (void**)&s->tab[b], size_t(s->npatch) * 8)) != WCS_OK) goto bad;
+    if ((st = dalloc(s, &s->ring[b], size_t(s->npatch) * ke->ring * 4)) != WCS_OK) goto bad;
+  }
+  if ((st = dalloc(s, (void**)&s->ctl, sizeof(wcs::Ctl))) != WCS_OK) goto bad;
+  if ((st = dalloc(s, (void**)&s->pstats, size_t(s->npatch) * 19 * 8)) != WCS_OK) goto bad;
+  if ((st = dalloc(s, (void**)&s->bfactor, size_t(s->nb) * 8)) != WCS_OK) goto bad;
+  if ((st = dalloc(s, (void**)&s->scratch, size_t(s->grid3) * ke->slot_floats * 4)) != WCS_OK) goto bad;
+  if ((st = dalloc(s, (void**)&s->rbuf, size_t(s->grid3) * ke->slot_rbytes)) != WCS_OK) goto bad;
+  {
+    cudaError_t e;
+    if ((e = cudaMemcpy(s->bfactor, bf.data(), size_t(s->nb) * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(s->ctl, 0, sizeof(wcs::Ctl))) != cudaSuccess) {
+      st = cuda_fail(s, e, "table upload");
+      goto bad;
+    }
+  }
+  *out = s;
+  return WCS_OK;
+bad:
+  g_create_err = s->err;
+  wcs_destroy(s);
+  return st;
+}
+
+static wcs_status init3(wcs_sim* s, const double* const* fields, int nfields, int src_is_device) {
+  if (nfields < 4) return fail(s, WCS_E_ARG, "D3Q19 init needs rho, u_x, u_y, u_z");
+  const size_t vol = size_t(s->G[0]) * size_t(s->G[1]) * size_t(s->G[2]);
+  double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
+  wcs::Patch3Args a = base_args3(s);
+  for (int q = 0; q < 4; ++q) {
+    if (src_is_device) {
+      a.macro[q] = fields[q];
+    } else {
+      CK(cudaMalloc(&tmp[q], vol * 8));
+      CK(cudaMemcpyAsync(tmp[q], fields[q], vol * 8, cudaMemcpyHostToDevice, s->stream));
+      a.macro[q] = tmp[q];
+    }
+  }
+  CK(cudaMemsetAsync(s->ctl, 0, sizeof(wcs::Ctl), s->stream));
+  a.step = -1;
+  a.arena_out = s->arena[0];
+  a.tab_out = s->tab[0];
+  a.ring_out = static_cast<float*>(s->ring[0]);
+  a.cur_out = 0;
+  CK(s->k3->launch(wcs::MODE_INIT, a, s->grid3, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  for (int q = 0; q < 4; ++q)
+    if (tmp[q]) cudaFree(tmp[q]);
+  s->nstep = 0;
+  s->inited = true;
+  return WCS_OK;
+}
+
+// Decoded state to device memory d (field f or all fields, dtype 0/1).
+static wcs_status export_dev(wcs_sim* s, int field, void* d, int dtype) {
+  const int cur = int(s->nstep % 2);
+  if (s->dims == 3) {
+    wcs::Patch3Args a = base_args3(s);
+    a.arena_in = s->arena[cur];
+    a.tab_in = s->tab[cur];
+    a.dense = d;
+    a.dense_dtype = dtype;
+    a.field_sel = field;
+    CK(s->k3->launch(wcs::MODE_EXPORT, a, s->grid3, s->stream));
+    return WCS_OK;
+  }
+  wcs::PatchArgs a = base_args(s);
+  a.arena_in = s->arena[cur];
+  a.tab_in = s->tab[cur];
+  a.dense = d;
+  a.dense_dtype = dtype;
+  a.field_sel = field;
+  CK(s->ke.launch(wcs::MODE_EXPORT, a, s->npatch, s->stream));
+  return WCS_OK;
+}
+
 extern "C" {
 
 wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int levels, double eps, const wcs_opts* opts,
                           wcs_sim** out) {
   if (!grid || !opts || !out) return fail(nullptr, WCS_E_ARG, "null argument");
   *out = nullptr;
-  if (grid->dims != 2) return fail(nullptr, WCS_E_UNSUPPORTED, "only 2-D grids are compiled");
+  if (!(eps >= 0)) return fail(nullptr, WCS_E_ARG, "eps must be >= 0");
+  if (grid->dims == 3 || scheme == WCS_D3Q19) return create3(grid, scheme, patch, levels, eps, opts, out);
+  if (grid->dims != 2) return fail(nullptr, WCS_E_UNSUPPORTED, "grids are 2-D or 3-D");
   if (!(eps >= 0)) return fail(nullptr, WCS_E_ARG, "eps must be >= 0");
   const KernelEntry* ke = nullptr;
   for (const KernelEntry& k : kernels())
@@ -250,6 +480,7 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
   s->nc = s->NC1 * s->NC1;
   s->nb = (levels + 1) * (levels + 1);
   s->tsize = s->prec == WCS_FP64 ? 8 : 4;
+  s->ring_vals = ke->ring;
 
   // ---- threshold multiplier of each band (c_x slowest; Sec. 2.2)
   std::vector<double> bf(s->nb);
@@ -299,7 +530,7 @@ wcs_status wcs_sim_use_mlp(wcs_sim* s, wcs_mlp* m, double eps_lo, double eps_hi)
     s->mlp = nullptr;
     return WCS_OK;
   }
-  if (s->ke.scheme != WCS_D2Q9 && s->ke.scheme != WCS_EULER2D) return WCS_E_UNSUPPORTED;
+  if (s->dims != 2 || (s->ke.scheme != WCS_D2Q9 && s->ke.scheme != WCS_EULER2D)) return WCS_E_UNSUPPORTED;
   if (wcs_mlp_nparam(m) != 64 * (6 * s->L) + 64 + 64 * 64 + 64 + 64 + 1)
     return fail(s, WCS_E_ARG, "the network's input size must be 6 x levels");
   if (!(eps_lo > 0) || !(eps_hi >= eps_lo)) return fail(s, WCS_E_ARG, "bad eps range");
@@ -358,6 +589,8 @@ void wcs_destroy(wcs_sim* s) {
   cudaFree(s->ctl);
   cudaFree(s->pstats);
   cudaFree(s->bfactor);
+  cudaFree(s->scratch);
+  cudaFree(s->rbuf);
   delete s;
 }
 
@@ -374,8 +607,21 @@ wcs_status wcs_shape(const wcs_sim* s, int64_t* npatch, int* nfields, int64_t* n
   return WCS_OK;
 }
 
+wcs_status wcs_shape3(const wcs_sim* s, int64_t* npatch, int* nfields, int64_t* nodes) {
+  if (!s) return WCS_E_ARG;
+  if (npatch) *npatch = s->npatch;
+  if (nfields) *nfields = s->F;
+  if (nodes)
+    for (int a = 0; a < 3; ++a) nodes[a] = s->G[a];
+  return WCS_OK;
+}
+
 wcs_status wcs_init_macro(wcs_sim* s, const double* const* fields, int nfields, int src_is_device) {
   if (!s || !fields) return WCS_E_ARG;
+  if (s->dims == 3) {
+    const wcs_status st = init3(s, fields, nfields, src_is_device);
+    return st != WCS_OK ? st : wcs_sync(s);
+  }
   const int need = s->scheme == WCS_D2Q9 ? 3 : 4;
   if (nfields < need) return fail(s, WCS_E_ARG, "init needs " + std::to_string(need) + " macroscopic fields");
   const size_t plane = size_t(s->G[0]) * size_t(s->G[1]);
@@ -409,6 +655,13 @@ wcs_status wcs_init_macro(wcs_sim* s, const double* const* fields, int nfields, 
 wcs_status wcs_step(wcs_sim* s, int64_t n) {
   if (!s || n < 0) return WCS_E_ARG;
   if (!s->inited) return fail(s, WCS_E_ARG, "wcs_step before wcs_init_macro");
+  if (s->dims == 3) {
+    for (int64_t i = 0; i < n; ++i) {
+      CK(s->k3->launch(wcs::MODE_STEP, step_args3(s, s->nstep), s->grid3, s->stream));
+      s->nstep += 1;
+    }
+    return WCS_OK;
+  }
   for (int64_t i = 0; i < n; ++i) {
     const int64_t k = s->nstep;
     if (s->mlp) {
@@ -450,18 +703,20 @@ wcs_status wcs_export_field(wcs_sim* s, int field, void* dst, int dst_is_device,
   if (!s->inited) return fail(s, WCS_E_ARG, "export before init");
   wcs_status st = wcs_sync(s);
   if (st != WCS_OK) return st;
-  const size_t plane = size_t(s->G[0]) * size_t(s->G[1]);
+  const size_t plane = size_t(s->G[0]) * size_t(s->G[1]) * size_t(s->G[2]);
   const size_t bytes = plane * (field < 0 ? s->F : 1) * (dtype == 0 ? 8 : 4);
   void* d = dst;
-  if (!dst_is_device) CK(cudaMalloc(&d, bytes));
-  wcs::PatchArgs a = base_args(s);
-  const int cur = int(s->nstep % 2);
-  a.arena_in = s->arena[cur];
-  a.tab_in = s->tab[cur];
-  a.dense = d;
-  a.dense_dtype = dtype;
-  a.field_sel = field;
-  CK(s->ke.launch(wcs::MODE_EXPORT, a, s->npatch, s->stream));
+  if (!dst_is_device) {
+    const cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(s, WCS_E_OOM, "export buffer of " + std::to_string(bytes) + " bytes");
+    }
+  }
+  if ((st = export_dev(s, field, d, dtype)) != WCS_OK) {
+    if (!dst_is_device) cudaFree(d);
+    return st;
+  }
   if (!dst_is_device) {
     CK(cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
@@ -481,7 +736,7 @@ int64_t wcs_compressed_bytes(const wcs_sim* s) {
   if (!s || !s->inited) return -1;
   const int64_t live = live_bytes(s);
   if (live < 0) return -1;
-  return live + int64_t(s->npatch) * s->ke.ring * int64_t(s->tsize) + int64_t(s->npatch) * 8;
+  return live + int64_t(s->npatch) * s->ring_vals * int64_t(s->tsize) + int64_t(s->npatch) * 8;
 }
 
 wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
@@ -497,7 +752,14 @@ wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
     for (int p = 0; p < s->npatch; ++p) acc += ps[size_t(p) * s->F + f];
     o->field_sum[f] = acc;
   }
-  if (s->scheme == WCS_D2Q9) {
+  if (s->scheme == WCS_D3Q19) {
+    for (int i = 0; i < 19; ++i) {
+      o->mass += o->field_sum[i];
+      o->momentum[0] += wcs::d3_cx(i) * o->field_sum[i];
+      o->momentum[1] += wcs::d3_cy(i) * o->field_sum[i];
+      o->momentum[2] += wcs::d3_cz(i) * o->field_sum[i];
+    }
+  } else if (s->scheme == WCS_D2Q9) {
     static const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     for (int i = 0; i < 9; ++i) {
       o->mass += o->field_sum[i];
@@ -516,7 +778,7 @@ wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
   std::memcpy(&o->smax, &sb, 8);
   o->live_bytes = int64_t(c.cursor[s->nstep % 2]);
   o->resident_bytes = s->resident;
-  o->uncompressed_bytes = int64_t(s->F) * s->G[0] * s->G[1] * int64_t(s->tsize);
+  o->uncompressed_bytes = int64_t(s->F) * s->G[0] * s->G[1] * s->G[2] * int64_t(s->tsize);
   o->status = c.status;
   return WCS_OK;
 }
@@ -593,6 +855,11 @@ wcs_status wcs_batch_create(wcs_sim* const* sims, int nsims, wcs_batch** out) {
       g_create_err = "batch: every simulation must be initialised, share one stream and be at the same step";
       batch_free(b);
       return WCS_E_ARG;
+    }
+    if (s->dims != 2) {
+      g_create_err = "batch: 3-D simulations are stepped alone";
+      batch_free(b);
+      return WCS_E_UNSUPPORTED;
     }
     if (s->npatch >= (1 << 20)) {
       g_create_err = "batch: more than 2^20 patches in one simulation";
@@ -722,6 +989,7 @@ wcs_status wcs_autotune(const wcs_grid* grid, int scheme, const wcs_opts* opts, 
                         int ncand, const double* const* fields, int nfields, int src_is_device, int steps, int* best,
                         double* ms_per_step) {
   if (!grid || !opts || !P || !L || ncand <= 0 || !best || steps <= 0) return WCS_E_ARG;
+  if (grid->dims != 2 || scheme == WCS_D3Q19) return WCS_E_UNSUPPORTED;
   typedef std::tuple<int64_t, int64_t, unsigned, int, int, int, int, int, double, std::vector<int>> Key;
   static std::map<Key, std::pair<int, std::vector<double>>> cache;
   static std::mutex mu;
@@ -809,7 +1077,7 @@ static wcs_status noalloc_scratch(wcs_sim* s, void** ptr) {
 wcs_status wcs_export_field_noalloc(wcs_sim* s, int field, void* host_dst, int dtype) {
   if (!s || !host_dst || field < -1 || field >= s->F || (dtype != 0 && dtype != 1)) return WCS_E_ARG;
   if (!s->inited) return fail(s, WCS_E_ARG, "export before init");
-  const size_t plane = size_t(s->G[0]) * size_t(s->G[1]);
+  const size_t plane = size_t(s->G[0]) * size_t(s->G[1]) * size_t(s->G[2]);
   const size_t bytes = plane * (field < 0 ? s->F : 1) * (dtype == 0 ? 8 : 4);
   if (bytes > WCS_NOALLOC_SCRATCH_BYTES)
     return fail(s, WCS_E_ARG, "wcs_export_field_noalloc: " + std::to_string(bytes) +
@@ -819,14 +1087,7 @@ wcs_status wcs_export_field_noalloc(wcs_sim* s, int field, void* host_dst, int d
   if (st != WCS_OK) return st;
   void* scratch = nullptr;
   if ((st = noalloc_scratch(s, &scratch)) != WCS_OK) return st;
-  wcs::PatchArgs a = base_args(s);
-  const int cur = int(s->nstep % 2);
-  a.arena_in = s->arena[cur];
-  a.tab_in = s->tab[cur];
-  a.dense = scratch;
-  a.dense_dtype = dtype;
-  a.field_sel = field;
-  CK(s->ke.launch(wcs::MODE_EXPORT, a, s->npatch, s->stream));
+  if ((st = export_dev(s, field, scratch, dtype)) != WCS_OK) return st;
   CK(cudaMemcpyAsync(host_dst, scratch, bytes, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return WCS_OK;

@@ -151,6 +151,16 @@ __device__ __forceinline__ void line_transform(T* p, int stride) {
   for (int i = 0; i < E; ++i) p[i * stride] = v[i];
 }
 
+// Per-axis class of node index k after L levels: 0 = coarse sample, m =
+// detail of level m (k = 2^(m-1) mod 2^m).
+template <int L> __host__ __device__ __forceinline__ constexpr int node_class(int k) {
+  int c = 0;  // the lowest set bit below 2^L decides; folds for constant k
+#pragma unroll
+  for (int m = L; m >= 1; --m)
+    if (k & (1 << (m - 1))) c = m;
+  return c;
+}
+
 // ------------------------------------------------------------ quantisation
 // BF16 with a per-band power-of-two scale s = 2^e >= max|d| (exact scaling),
 // int8 with s = max|d|/127 and round-half-even.

@@ -103,15 +103,6 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   static_assert(OFF_STAGE + 4096 <= SMEM_MAX, "patch does not fit in shared memory");
 };
 
-// Per-axis class of node index k after L levels: 0 = coarse sample, m =
-// detail of level m (k = 2^(m-1) mod 2^m).
-template <int L> __host__ __device__ __forceinline__ constexpr int node_class(int k) {
-  int c = 0;  // the lowest set bit below 2^L decides; folds for constant k
-#pragma unroll
-  for (int m = L; m >= 1; --m)
-    if (k & (1 << (m - 1))) c = m;
-  return c;
-}
 
 // Edge-line bits of mask word w (BL5/3: nodes with x or y in {0, P}); coarse
 // nodes may be included, they never carry a mask bit.

@@ -24,4 +24,20 @@ struct KernelEntry {
 };
 
 void register_all(std::vector<KernelEntry>& v);
+
+// 3-D kernels (D3Q19, folded BL5/3, FP32 compute): persistent, one CTA per
+// SM, each with a scratch slot of slot_floats floats and slot_rbytes bytes.
+struct Patch3Args;
+struct Kernel3Entry {
+  int store, P, L;
+  int ring;                        // floats exported per patch
+  size_t smem;                     // dynamic shared memory per CTA
+  int threads;
+  unsigned long long slot_floats;  // scratch floats per CTA
+  unsigned long long slot_rbytes;  // record buffer bytes per CTA (largest record)
+  cudaError_t (*launch)(int mode, const Patch3Args& a, int grid, cudaStream_t s);
+  cudaError_t (*prepare)();
+};
+
+void register_all3(std::vector<Kernel3Entry>& v);
 }  // namespace wcs

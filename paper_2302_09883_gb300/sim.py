@@ -127,6 +127,48 @@ class Sim:
         return B.lib().wcs_stream(self.h)
 
 
+class Sim3(Sim):
+    """One compressed-patch D3Q19 simulation on a periodic (nz, ny, nx) grid
+    (folded BL5/3, FP32 compute)."""
+
+    def __init__(self, nx, ny, nz, P, L, eps, store="bf16", rule="const", tau=0.8, arena_factor=0.25, stream=None):
+        self.scheme = "d3q19"
+        o = B.Opts()
+        o.wavelet, o.rule, o.detail_store, o.compute = B.WAVELET["bl53"], B.RULE[rule], B.STORE[store], B.PREC["f32"]
+        o.tau, o.arena_factor = tau, arena_factor
+        o.cuda_stream = _stream_ptr(stream)
+        g = B.Grid()
+        g.dims = 3
+        g.n[0], g.n[1], g.n[2] = nx, ny, nz
+        g.periodic_mask = 7
+        h = C.c_void_p()
+        B.check(B.lib().wcs_create_sim(C.byref(g), B.SCHEME["d3q19"], P, L, eps, C.byref(o), C.byref(h)), None)
+        self.h = h
+        npatch, nf = C.c_int64(), C.c_int()
+        nodes = (C.c_int64 * 3)()
+        B.check(B.lib().wcs_shape3(h, C.byref(npatch), C.byref(nf), nodes), h)
+        self.npatch, self.F, self.G = npatch.value, nf.value, (nodes[0], nodes[1], nodes[2])
+
+    def export_field(self, f, out=None, dtype=np.float64):
+        """Decoded field f ([nz][ny][nx]); f = -1 gives all fields."""
+        shape = ((self.F,) if f < 0 else ()) + (self.G[2], self.G[1], self.G[0])
+        dt = 0 if np.dtype(dtype) == np.float64 else 1
+        if out is None:
+            out = np.empty(shape, dtype=dtype)
+        if hasattr(out, "data_ptr"):
+            B.check(B.lib().wcs_export_field(self.h, f, out.data_ptr(), 1 if out.is_cuda else 0, dt), self.h)
+        else:
+            B.check(B.lib().wcs_export_field(self.h, f, out.ctypes.data, 0, dt), self.h)
+        return out
+
+    def stats(self):
+        d = super().stats()
+        s = B.StepStats()
+        B.check(B.lib().wcs_stats(self.h, C.byref(s)), self.h)
+        d["momentum"] = np.array(s.momentum[:3])
+        return d
+
+
 class Dense:
     """Uncompressed FP32 baseline of the same scheme."""
 
