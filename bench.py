@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-euler", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-d3q19", action="store_true")
+    ap.add_argument("--d3q19-n", type=int, default=1024, help="D3Q19 timing grid (cells per axis)")
     return ap.parse_args()
 
 
@@ -443,6 +445,103 @@ def learned_section(torch, K, W, flush, bs, n_eval=1024, steps=1000, deltas=(3e-
             "mlups_learned": n_eval * n_eval / (times["learned"] * 1e-3) / 1e6}
 
 
+def _tgv_device(torch, n, u0=0.04):
+    """inputs.taylor_green_3d built in device memory (float64 tensors)."""
+    k = 2.0 * np.pi / n
+    i = torch.arange(n, dtype=torch.float64, device="cuda") * k
+    s, c = torch.sin(i), torch.cos(i)
+    ux = u0 * s[None, None, :] * c[None, :, None] * c[:, None, None]
+    uy = -u0 * c[None, None, :] * s[None, :, None] * c[:, None, None]
+    c2 = torch.cos(2 * i)
+    p = u0 * u0 / 16.0 * (c2[None, None, :] + c2[None, :, None]) * (c2[:, None, None] + 2.0)
+    return [(1.0 + 3.0 * p).contiguous(), ux.contiguous(), uy.contiguous(), torch.zeros_like(ux)]
+
+
+def d3q19_section(torch, K, W, flush, bs, n_quality=256, quality_steps=1000, n_time=1024,
+                  eps_sweep=(1e-7, 1e-6, 1e-5)):
+    """D3Q19 BGK, decaying Taylor-Green vortex u0 = 0.04, tau = 0.55, periodic,
+    BL5/3 P = 32, L = 3, FP32 compute, BF16 details.  Quality: n_quality^3
+    for quality_steps steps against the uncompressed FP32 run (rel. L2 of u
+    and rho on the device).  Timing: n_time^3, compressed and uncompressed,
+    W warm-up then K steps, each timed with CUDA events and the L2 flushed
+    before it."""
+    from paper_2302_09883_gb300 import Dense3, Sim3
+    P, L, tau = 32, 3, 0.55
+    cx = torch.tensor([0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0], dtype=torch.float64, device="cuda")
+    cy = torch.tensor([0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1], dtype=torch.float64, device="cuda")
+    cz = torch.tensor([0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1], dtype=torch.float64, device="cuda")
+
+    def moments(Fd):
+        rho = Fd.sum(0)
+        u = torch.stack([torch.tensordot(c, Fd, dims=([0], [0])) / rho for c in (cx, cy, cz)])
+        return rho, u
+
+    n = n_quality
+    d = Dense3(n, n, n, tau=tau, stream=bs)
+    d.init_macro(_tgv_device(torch, n))
+    d.step(quality_steps)
+    Fd = torch.empty((19, n, n, n), dtype=torch.float32, device="cuda")
+    for i in range(19):
+        d.export_field(i, out=Fd[i], dtype=np.float32)
+    d.close()
+    rho_d, u_d = moments(Fd.double())
+    m0 = float(_tgv_device(torch, n)[0].sum())
+    dense_drift = (float(Fd.double().sum()) - m0) / m0
+    del Fd
+    quality = []
+    for eps in eps_sweep:
+        c = Sim3(n, n, n, P, L, eps, store="bf16", tau=tau, arena_factor=0.3, stream=bs)
+        c.init_macro(_tgv_device(torch, n))
+        c.step(quality_steps)
+        c.sync()
+        Fc = torch.empty((19, n, n, n), dtype=torch.float32, device="cuda")
+        c.export_field(-1, out=Fc, dtype=np.float32)
+        rho_c, u_c = moments(Fc.double())
+        st = c.stats()
+        quality.append({"eps": eps, "rel_l2_u": float((u_c - u_d).norm() / u_d.norm()),
+                        "rel_l2_rho": float((rho_c - rho_d).norm() / rho_d.norm()),
+                        "compression_ratio": st["uncompressed_bytes"] / c.compressed_bytes(),
+                        "record_ratio": st["uncompressed_bytes"] / st["live_bytes"],
+                        "mass_drift": (st["mass"] - m0) / m0, "dense_mass_drift": dense_drift})
+        c.close()
+        del Fc
+    torch.cuda.empty_cache()
+    ok = [q for q in quality if q["rel_l2_u"] <= 1e-3 and q["rel_l2_rho"] <= 1e-3]
+    head = max(ok, key=lambda q: q["eps"]) if ok else quality[0]
+
+    def timed(obj):
+        obj.step(W)
+        torch.cuda.synchronize()
+        return timed_steps(torch, obj, bs, K, flush) / K
+
+    n = n_time
+    c = Sim3(n, n, n, P, L, head["eps"], store="bf16", tau=tau, arena_factor=0.05, stream=bs)
+    f = _tgv_device(torch, n)
+    c.init_macro(f)
+    del f
+    torch.cuda.empty_cache()
+    ms_c = timed(c)
+    c.sync()
+    st = c.stats()
+    ratio_big = st["uncompressed_bytes"] / c.compressed_bytes()
+    resident_c = st["resident_bytes"]
+    c.close()
+    d = Dense3(n, n, n, tau=tau, stream=bs)
+    f = _tgv_device(torch, n)
+    d.init_macro(f)
+    del f
+    torch.cuda.empty_cache()
+    ms_d = timed(d)
+    dense_bytes = d.nbytes()
+    d.close()
+    lu = n ** 3
+    return {"workload": "d3q19_bl53_tgv_%d" % n, "P": P, "levels": L, "store": "bf16", "tau": tau, "u0": 0.04,
+            "eps": head["eps"], "quality_grid": n_quality, "quality_steps": quality_steps, "quality": quality,
+            "mlups": lu / (ms_c * 1e-3) / 1e6, "ms_per_step": ms_c, "uncompressed_mlups": lu / (ms_d * 1e-3) / 1e6,
+            "uncompressed_ms_per_step": ms_d, "uncompressed_gbs": 152.0 * lu / (ms_d * 1e-3) / 1e9,
+            "compression_ratio": ratio_big, "resident_bytes": resident_c, "uncompressed_resident_bytes": dense_bytes}
+
+
 def roofline_bytes(sim, w):
     """Algorithmic bytes of one step launch: records of state n read, records
     of state n+1 written, ghost rings read and written, patch tables, the
@@ -652,6 +751,11 @@ def main():
     if not args.no_learned:
         learned_eps = learned_section(torch, K, W, flush, bs)
 
+    d3q19 = None
+    if not args.no_d3q19:
+        d3q19 = d3q19_section(torch, min(K, 10), W, flush, bs, n_time=args.d3q19_n,
+                              quality_steps=args.quality_steps or 1000)
+
     mlups = lu * K * world / (ms * 1e-3) / 1e6
     peaks = {}
     try:
@@ -707,6 +811,7 @@ def main():
             "euler": euler,
             "batch": batch,
             "learned_eps": learned_eps,
+            "d3q19": d3q19,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

@@ -3,6 +3,8 @@
 // structure-of-arrays, two lattices, one kernel per step.
 //   D2Q9: read the 9 populations of a node, BGK collide, push each one to
 //         x + c_i (periodic) -- 72 bytes per lattice update.
+//   D3Q19: the same with 19 populations on a periodic 3-D grid -- 152 bytes
+//         per lattice update.
 //   Euler: Rusanov update of one node from its 4 neighbours (outflow copies
 //          or periodic wrap), plus the max signal speed of the new state for
 //          the next step's dt -- 32 bytes per update after cache reuse.
@@ -13,6 +15,7 @@
 
 #include "../../include/wcsim.h"
 #include "common.cuh"
+#include "patch3d.cuh"
 
 namespace {
 
@@ -74,6 +77,35 @@ __global__ void __launch_bounds__(256) euler_update(const float* __restrict__ sr
   if ((threadIdx.x & 31) == 0) atomicMax(&smax[wr], (unsigned long long)__double_as_longlong(double(s_new)));
 }
 
+__global__ void __launch_bounds__(256) d3q19_push(const float* __restrict__ src, float* __restrict__ dst, int nx, int ny,
+                                                  int nz, float omega) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+  if (x >= nx) return;
+  const size_t vol = size_t(nx) * ny * nz, g = (size_t(z) * ny + y) * nx + x;
+  float f[19];
+#pragma unroll
+  for (int i = 0; i < 19; ++i) f[i] = __ldg(src + i * vol + g);
+  wcs::d3q19_collide<float>(f, omega);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    int xd = x + wcs::d3_cx(i), yd = y + wcs::d3_cy(i), zd = z + wcs::d3_cz(i);
+    xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
+    yd = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
+    zd = zd < 0 ? zd + nz : (zd >= nz ? zd - nz : zd);
+    dst[i * vol + (size_t(zd) * ny + yd) * nx + xd] = f[i];
+  }
+}
+
+__global__ void macro_init3(const double* m0, const double* m1, const double* m2, const double* m3, float* dst,
+                            size_t vol) {
+  const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (g >= vol) return;
+  float f[19];
+  wcs::d3q19_equilibrium<float>(float(m0[g]), float(m1[g]), float(m2[g]), float(m3[g]), f);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) dst[i * vol + g] = f[i];
+}
+
 __global__ void macro_init(const double* m0, const double* m1, const double* m2, const double* m3, float* dst,
                            size_t plane, int scheme, float gm1, unsigned long long* smax, float gamma) {
   const size_t g = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -106,8 +138,8 @@ __global__ void to_double(const float* src, double* dst, size_t n) {
 
 struct wcs_dense {
   int scheme = 0;
-  int64_t n[2] = {0, 0};
-  int per[2] = {1, 1};
+  int64_t n[3] = {0, 0, 1};
+  int per[3] = {1, 1, 1};
   int F = 0;
   float* buf[2] = {nullptr, nullptr};
   unsigned long long* smax = nullptr;
@@ -119,11 +151,19 @@ struct wcs_dense {
 extern "C" {
 
 wcs_status wcs_dense_create(const wcs_grid* grid, int scheme, const wcs_opts* opts, wcs_dense** out) {
-  if (!grid || !opts || !out || grid->dims != 2) return WCS_E_ARG;
-  if (scheme != WCS_D2Q9 && scheme != WCS_EULER2D) return WCS_E_UNSUPPORTED;
+  if (!grid || !opts || !out || (grid->dims != 2 && grid->dims != 3)) return WCS_E_ARG;
+  if (scheme != WCS_D2Q9 && scheme != WCS_EULER2D && scheme != WCS_D3Q19) return WCS_E_UNSUPPORTED;
+  if ((scheme == WCS_D3Q19) != (grid->dims == 3)) return WCS_E_ARG;
   wcs_dense* d = new wcs_dense();
   d->scheme = scheme;
-  for (int a = 0; a < 2; ++a) {
+  if (grid->dims == 3) {
+    for (int a = 0; a < 3; ++a) d->n[a] = grid->n[a];
+    if ((grid->periodic_mask & 7u) != 7u || grid->n[1] > 65535 || grid->n[2] > 65535) {
+      delete d;
+      return WCS_E_ARG;
+    }
+  }
+  for (int a = 0; a < 2 && grid->dims == 2; ++a) {
     d->per[a] = (grid->periodic_mask >> a) & 1u;
     // node counts: outflow axes carry n+1 nodes, like the BL5/3 patch grid
     d->n[a] = d->per[a] ? grid->n[a] : grid->n[a] + 1;
@@ -132,12 +172,12 @@ wcs_status wcs_dense_create(const wcs_grid* grid, int scheme, const wcs_opts* op
     delete d;
     return WCS_E_ARG;
   }
-  d->F = scheme == WCS_D2Q9 ? 9 : 4;
+  d->F = scheme == WCS_D2Q9 ? 9 : (scheme == WCS_D3Q19 ? 19 : 4);
   d->tau = opts->tau > 0 ? opts->tau : 1.0;
   d->cfl = opts->cfl != 0 ? opts->cfl : 0.4;
   d->gamma = opts->gamma > 1 ? opts->gamma : 1.4;
   d->stream = static_cast<cudaStream_t>(opts->cuda_stream);
-  const size_t bytes = size_t(d->F) * d->n[0] * d->n[1] * 4;
+  const size_t bytes = size_t(d->F) * d->n[0] * d->n[1] * d->n[2] * 4;
   if (cudaMalloc(&d->buf[0], bytes) != cudaSuccess || cudaMalloc(&d->buf[1], bytes) != cudaSuccess ||
       cudaMalloc(&d->smax, 3 * 8) != cudaSuccess) {
     cudaGetLastError();
@@ -157,11 +197,11 @@ void wcs_dense_destroy(wcs_dense* d) {
   delete d;
 }
 
-int64_t wcs_dense_bytes(const wcs_dense* d) { return d ? int64_t(d->F) * d->n[0] * d->n[1] * 4 * 2 : -1; }
+int64_t wcs_dense_bytes(const wcs_dense* d) { return d ? int64_t(d->F) * d->n[0] * d->n[1] * d->n[2] * 4 * 2 : -1; }
 
 wcs_status wcs_dense_init_macro(wcs_dense* d, const double* const* fields, int nfields, int src_is_device) {
   if (!d || !fields || nfields < (d->scheme == WCS_D2Q9 ? 3 : 4)) return WCS_E_ARG;
-  const size_t plane = size_t(d->n[0]) * d->n[1];
+  const size_t plane = size_t(d->n[0]) * d->n[1] * d->n[2];
   const int need = d->scheme == WCS_D2Q9 ? 3 : 4;
   double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
   const double* m[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -175,7 +215,10 @@ wcs_status wcs_dense_init_macro(wcs_dense* d, const double* const* fields, int n
   }
   if (need == 3) m[3] = m[0];
   cudaMemsetAsync(d->smax, 0, 24, d->stream);
-  macro_init<<<unsigned((plane + 255) / 256), 256, 0, d->stream>>>(m[0], m[1], m[2], m[3], d->buf[0], plane, d->scheme,
+  if (d->scheme == WCS_D3Q19)
+    macro_init3<<<unsigned((plane + 255) / 256), 256, 0, d->stream>>>(m[0], m[1], m[2], m[3], d->buf[0], plane);
+  else
+    macro_init<<<unsigned((plane + 255) / 256), 256, 0, d->stream>>>(m[0], m[1], m[2], m[3], d->buf[0], plane, d->scheme,
                                                                    float(d->gamma - 1.0), d->smax, float(d->gamma));
   cudaError_t e = cudaStreamSynchronize(d->stream);
   for (int q = 0; q < 4; ++q)
@@ -192,7 +235,10 @@ wcs_status wcs_dense_step(wcs_dense* d, int64_t n) {
     const int64_t k = d->nstep;
     const float* src = d->buf[k % 2];
     float* dst = d->buf[(k + 1) % 2];
-    if (d->scheme == WCS_D2Q9) {
+    if (d->scheme == WCS_D3Q19) {
+      const dim3 g3((nx + 255) / 256, ny, int(d->n[2]));
+      d3q19_push<<<g3, 256, 0, d->stream>>>(src, dst, nx, ny, int(d->n[2]), float(1.0 / d->tau));
+    } else if (d->scheme == WCS_D2Q9) {
       d2q9_push<<<grid, 256, 0, d->stream>>>(src, dst, nx, ny, float(1.0 / d->tau));
     } else {
       euler_update<<<grid, 256, 0, d->stream>>>(src, dst, nx, ny, d->per[0], d->per[1], d->smax, int(k % 3),
@@ -206,7 +252,7 @@ wcs_status wcs_dense_step(wcs_dense* d, int64_t n) {
 
 wcs_status wcs_dense_export_field(wcs_dense* d, int field, void* dst, int dst_is_device, int dtype) {
   if (!d || !dst || field < 0 || field >= d->F) return WCS_E_ARG;
-  const size_t plane = size_t(d->n[0]) * d->n[1];
+  const size_t plane = size_t(d->n[0]) * d->n[1] * d->n[2];
   const float* src = d->buf[d->nstep % 2] + size_t(field) * plane;
   if (cudaStreamSynchronize(d->stream) != cudaSuccess) return WCS_E_CUDA;
   if (dtype == 1) {

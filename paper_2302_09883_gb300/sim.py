@@ -100,6 +100,8 @@ class Sim:
             out = np.empty(shape, dtype=dtype)
         if hasattr(out, "data_ptr"):
             B.check(B.lib().wcs_export_field(self.h, f, out.data_ptr(), 1 if out.is_cuda else 0, dt), self.h)
+            if out.is_cuda:
+                self.sync()  # a device export is enqueued on the simulation's stream
         else:
             B.check(B.lib().wcs_export_field(self.h, f, out.ctypes.data, 0, dt), self.h)
         return out
@@ -157,6 +159,8 @@ class Sim3(Sim):
             out = np.empty(shape, dtype=dtype)
         if hasattr(out, "data_ptr"):
             B.check(B.lib().wcs_export_field(self.h, f, out.data_ptr(), 1 if out.is_cuda else 0, dt), self.h)
+            if out.is_cuda:
+                self.sync()  # a device export is enqueued on the simulation's stream
         else:
             B.check(B.lib().wcs_export_field(self.h, f, out.ctypes.data, 0, dt), self.h)
         return out
@@ -212,3 +216,36 @@ class Dense:
 
     def nbytes(self):
         return B.lib().wcs_dense_bytes(self.h)
+
+
+class Dense3(Dense):
+    """Uncompressed FP32 D3Q19 baseline on a periodic (nz, ny, nx) grid."""
+
+    def __init__(self, nx, ny, nz, tau=0.8, stream=None):
+        o = B.Opts()
+        o.tau = tau
+        o.cuda_stream = _stream_ptr(stream)
+        g = B.Grid()
+        g.dims = 3
+        g.n[0], g.n[1], g.n[2] = nx, ny, nz
+        g.periodic_mask = 7
+        h = C.c_void_p()
+        st = B.lib().wcs_dense_create(C.byref(g), B.SCHEME["d3q19"], C.byref(o), C.byref(h))
+        if st != 0:
+            raise B.WcsError(st, "dense baseline create failed")
+        self.h = h
+        self.F = 19
+        self.G = (nx, ny, nz)
+
+    def export_field(self, f, out=None, dtype=np.float64):
+        """Field f ([nz][ny][nx]); `out` may be a CUDA tensor (device copy)."""
+        dt = 0 if np.dtype(dtype) == np.float64 else 1
+        if out is None:
+            out = np.empty((self.G[2], self.G[1], self.G[0]), dtype=dtype)
+        if hasattr(out, "data_ptr"):
+            st = B.lib().wcs_dense_export_field(self.h, f, out.data_ptr(), 1 if out.is_cuda else 0, dt)
+        else:
+            st = B.lib().wcs_dense_export_field(self.h, f, out.ctypes.data, 0, dt)
+        if st != 0:
+            raise B.WcsError(st, "dense export failed")
+        return out

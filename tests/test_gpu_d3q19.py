@@ -78,3 +78,17 @@ def test_d3q19_arena_overflow_is_reported():
     with pytest.raises(WcsError) as ei:
         g.init_macro(f)
     assert ei.value.status == 3
+
+
+def test_d3q19_dense_baseline_matches_oracle_reference():
+    from paper_2302_09883_gb300 import Dense3
+    d = Dense3(32, 32, 16, tau=0.55)
+    r = O.OracleRef3(32, 32, 16, prec="f32", tau=0.55)
+    f16 = [a[:16] for a in inputs.taylor_green_3d(32, u0=0.04)]
+    d.init_macro(f16)
+    r.init_macro(f16)
+    d.step(7)
+    r.step(7)
+    b = r.export_all()
+    for i in range(19):
+        assert np.array_equal(d.export_field(i), b[i])
