@@ -446,15 +446,7 @@ def learned_section(torch, K, W, flush, bs, n_eval=1024, steps=1000, deltas=(3e-
 
 
 def _tgv_device(torch, n, u0=0.04):
-    """inputs.taylor_green_3d built in device memory (float64 tensors)."""
-    k = 2.0 * np.pi / n
-    i = torch.arange(n, dtype=torch.float64, device="cuda") * k
-    s, c = torch.sin(i), torch.cos(i)
-    ux = u0 * s[None, None, :] * c[None, :, None] * c[:, None, None]
-    uy = -u0 * c[None, None, :] * s[None, :, None] * c[:, None, None]
-    c2 = torch.cos(2 * i)
-    p = u0 * u0 / 16.0 * (c2[None, None, :] + c2[None, :, None]) * (c2[:, None, None] + 2.0)
-    return [(1.0 + 3.0 * p).contiguous(), ux.contiguous(), uy.contiguous(), torch.zeros_like(ux)]
+    return inputs.taylor_green_3d_device(n, u0=u0)
 
 
 def d3q19_section(torch, K, W, flush, bs, n_quality=256, quality_steps=1000, n_time=1024,

@@ -114,6 +114,19 @@ def taylor_green_3d(n, u0=0.04, rho0=1.0):
     return [rho0 + 3.0 * p, ux, uy, uz]
 
 
+def taylor_green_3d_device(n, u0=0.04, rho0=1.0, device="cuda"):
+    """taylor_green_3d generated directly in device memory (float64 torch
+    tensors), for grids too large to build on the host."""
+    import torch
+    k = 2.0 * np.pi / n
+    i = torch.arange(n, dtype=torch.float64, device=device) * k
+    s, c, c2 = torch.sin(i), torch.cos(i), torch.cos(2 * i)
+    ux = u0 * s[None, None, :] * c[None, :, None] * c[:, None, None]
+    uy = -u0 * c[None, None, :] * s[None, :, None] * c[:, None, None]
+    p = rho0 * u0 * u0 / 16.0 * (c2[None, None, :] + c2[None, :, None]) * (c2[:, None, None] + 2.0)
+    return [(rho0 + 3.0 * p).contiguous(), ux.contiguous(), uy.contiguous(), torch.zeros_like(ux)]
+
+
 def shear_wave_3d(nx, ny, nz, u0=0.01, axis=1, noise=0.0, seed=0):
     """rho = 1, u_x = u0 sin(2 pi s / n_s) with s the coordinate along
     `axis` (1 = y, 2 = z), plus N(0, noise) per node; arrays (z, y, x)."""

@@ -1,0 +1,131 @@
+"""Parity at the full sizes of the benchmarked workloads, in the launch
+configurations the bench times: the FP32 oracle runs the same full grid
+(D2Q9 2048^2, Euler 4096^2, sampled grids of the 96-grid batch, D3Q19
+128^3) and every record must be byte-identical; at 1024^3 (too large for the
+oracle) the D3Q19 run is checked by properties that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2302_09883_gb300 import Batch, Sim, Sim3, autotune, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _records_equal(g, o):
+    for p in range(g.npatch):
+        assert g.record(p) == o.record(p), "patch %d" % p
+
+
+def test_d2q9_2048_records_match_the_oracle():
+    # the headline workload: 2048^2 shear wave, BL5/3 P=64 L=4, FP32, BF16, eps 1e-3, tau 0.6
+    f = inputs.shear_wave(2048, seed=0)
+    g = Sim("d2q9", "bl53", 2048, 2048, 64, 4, 1e-3, prec="f32", store="bf16", tau=0.6, arena_factor=0.35)
+    o = O.OracleSim("d2q9", "bl53", 2048, 2048, 64, 4, 1e-3, prec="f32", store="bf16", tau=0.6)
+    g.init_macro(f)
+    o.init_macro(f)
+    g.step(3)
+    o.step(3)
+    g.sync()
+    _records_equal(g, o)
+    assert np.array_equal(g.stats()["field_sum"], o.stats()["coef_sums"])
+
+
+def test_euler_4096_records_match_the_oracle():
+    # four-quadrant Riemann problem, 4097^2 nodes, outflow, BF16 eps 1e-4, CFL 0.4
+    f = inputs.four_quadrant(4096)
+    g = Sim("euler2d", "bl53", 4096, 4096, 64, 4, 1e-4, prec="f32", store="bf16", periodic=(False, False), cfl=0.4,
+            arena_factor=0.35)
+    o = O.OracleSim("euler2d", "bl53", 4096, 4096, 64, 4, 1e-4, prec="f32", store="bf16", periodic=(False, False),
+                    cfl=0.4)
+    g.init_macro(f)
+    o.init_macro(f)
+    g.step(2)
+    o.step(2)
+    g.sync()
+    _records_equal(g, o)
+    assert g.stats()["time"] == o.stats()["time"]
+
+
+def test_batch_of_96_sampled_grids_match_the_oracle():
+    # the bench's batch: 96 seeded bumps, sides from {256, 512, 1024, 2048}, P by the autotuner
+    specs = inputs.batch_specs(96, seed=0)
+    tau, eps = 0.6, 1e-6
+    bump = lambda sp: inputs.gaussian_bump(sp["side"], amp=sp["amp"], sigma=sp["sigma"], center=(sp["cx"], sp["cy"]))
+    choice = {}
+    for sp in specs:
+        if sp["side"] not in choice:
+            best, _ = autotune("d2q9", "bl53", sp["side"], sp["side"], 1e-5, bump(sp), candidates=((64, 4), (32, 3)),
+                               tau=tau)
+            choice[sp["side"]] = [(64, 4), (32, 3)][best]
+    sims = []
+    for sp in specs:
+        n = sp["side"]
+        P, L = choice[n]
+        s = Sim("d2q9", "bl53", n, n, P, L, eps, prec="f32", store="bf16", tau=tau, arena_factor=0.5)
+        s.init_macro(bump(sp))
+        sims.append(s)
+    b = Batch(sims)
+    b.step(6)  # one graph replay
+    b.sync()
+    picked = {}
+    for k, sp in enumerate(specs):
+        picked.setdefault(sp["side"], k)
+    for n, k in sorted(picked.items()):
+        sp = specs[k]
+        P, L = choice[n]
+        o = O.OracleSim("d2q9", "bl53", n, n, P, L, eps, prec="f32", store="bf16", tau=tau)
+        o.init_macro(bump(sp))
+        o.step(6)
+        _records_equal(sims[k], o)
+    b.close()
+
+
+def test_d3q19_128_records_match_the_oracle():
+    # 64 patches of 32^3 (the 3-D workload's patch and level), Taylor-Green vortex, BF16
+    f = inputs.taylor_green_3d(128, u0=0.04)
+    g = Sim3(128, 128, 128, 32, 3, 1e-6, store="bf16", tau=0.55, arena_factor=0.5)
+    o = O.OracleSim3("bl53", 128, 128, 128, 32, 3, 1e-6, prec="f32", store="bf16", tau=0.55)
+    g.init_macro(f)
+    o.init_macro(f)
+    g.step(2)
+    o.step(2)
+    g.sync()
+    _records_equal(g, o)
+
+
+def test_d3q19_1024_properties():
+    # config 5's grid: 32768 patches.  Properties that hold at any size: the
+    # FP64 mass of the coarse blocks equals the sum of the decoded fields,
+    # momentum stays zero, the decoded velocity is still the vortex.
+    import torch
+    n = 1024
+    f = inputs.taylor_green_3d_device(n)
+    m0 = float(f[0].sum())
+    g = Sim3(n, n, n, 32, 3, 1e-7, store="bf16", tau=0.55, arena_factor=0.05)
+    g.init_macro(f)
+    g.step(2)
+    g.sync()
+    st = g.stats()
+    assert abs(st["mass"] - m0) <= 1e-6 * m0
+    assert np.all(np.abs(st["momentum"]) <= 1e-6 * m0)
+    buf = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    total = 0.0
+    j = torch.zeros((3, n, n, n), dtype=torch.float64, device="cuda")
+    c = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1), (1, 1, 0), (-1, -1, 0),
+         (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1), (1, 0, -1), (-1, 0, 1), (0, 1, 1), (0, -1, -1), (0, 1, -1),
+         (0, -1, 1)]
+    rho = torch.zeros((n, n, n), dtype=torch.float64, device="cuda")
+    for i in range(19):
+        g.export_field(i, out=buf, dtype=np.float32)
+        fi = buf.double()
+        total += float(fi.sum())
+        rho += fi
+        for a in range(3):
+            if c[i][a]:
+                j[a] += c[i][a] * fi
+    assert abs(total - st["mass"]) <= 1e-6 * m0
+    u = j / rho
+    for a in range(2):
+        err = float((u[a] - f[1 + a]).norm() / f[1 + a].norm())
+        assert err < 1e-2
