@@ -161,6 +161,174 @@ template <int L> __host__ __device__ __forceinline__ constexpr int node_class(in
   return c;
 }
 
+// ------------------------------------------- restricted inverse (BL5/3)
+// The nodes whose coefficients the inverse lifting of one line (P+1 nodes,
+// L levels) reads to produce node t: the dependency cone, closed level by
+// level (an odd node needs its detail and the two even neighbours after the
+// undone update; an interior even node needs the two details around it).
+// Bit n of (lo, hi) is node n (P <= 127).
+struct ConeMask {
+  unsigned long long lo, hi;
+};
+template <int P, int L> __host__ __device__ constexpr ConeMask cone_mask(int t) {
+  bool need[P + 1] = {};
+  bool coef[P + 1] = {};
+  need[t] = true;
+  for (int lev = 1; lev <= L; ++lev) {
+    const int st = 1 << (lev - 1), K = P / st / 2;
+    bool nxt[P + 1] = {};
+    for (int n = 0; n <= P; ++n) {
+      if (!need[n]) continue;
+      if (n % st) {
+        coef[n] = true;
+        continue;
+      }
+      int ev[2] = {n, n};
+      int ne = 1;
+      if ((n / st) & 1) {
+        coef[n] = true;
+        ev[0] = n - st;
+        ev[1] = n + st;
+        ne = 2;
+      }
+      for (int j = 0; j < ne; ++j) {
+        const int e = ev[j], k = e / (2 * st);
+        nxt[e] = true;
+        if (k > 0 && k < K) {
+          coef[e - st] = true;
+          coef[e + st] = true;
+        }
+      }
+    }
+    for (int n = 0; n <= P; ++n) need[n] = nxt[n];
+  }
+  ConeMask c{0ull, 0ull};
+  for (int n = 0; n <= P; ++n)
+    if (coef[n] || need[n]) {
+      if (n < 64) c.lo |= 1ull << n;
+      else c.hi |= 1ull << (n - 64);
+    }
+  return c;
+}
+__host__ __device__ constexpr bool cone_has(ConeMask c, int n) {
+  return n < 64 ? ((c.lo >> n) & 1ull) != 0ull : ((c.hi >> (n - 64)) & 1ull) != 0ull;
+}
+__host__ __device__ constexpr int cone_lowest(ConeMask c) {
+  int n = 0;
+  while (!cone_has(c, n)) ++n;
+  return n;
+}
+__host__ __device__ constexpr int cone_highest(ConeMask c) {
+  int n = 127;
+  while (!cone_has(c, n)) --n;
+  return n;
+}
+__host__ __device__ constexpr int cone_count(ConeMask c) {
+  int k = 0;
+  for (int n = 0; n < 128; ++n) k += cone_has(c, n) ? 1 : 0;
+  return k;
+}
+__host__ __device__ constexpr int cone_index_c(ConeMask c, int n) {
+  int k = 0;
+  for (int m = 0; m < n; ++m) k += cone_has(c, m) ? 1 : 0;
+  return k;
+}
+// Index of node n among the cone's nodes (n in the cone), at run time.
+__device__ __forceinline__ int cone_index(ConeMask c, int n) {
+  return n < 64 ? __popcll(c.lo & ((1ull << n) - 1ull)) : __popcll(c.lo) + __popcll(c.hi & ((1ull << (n - 64)) - 1ull));
+}
+
+// The operations of the inverse lifting that node t needs, per level: the
+// undone updates (even nodes) and the undone predicts (odd nodes), as bit
+// masks over the nodes (P <= 127, L <= 8).
+struct ConeOps {
+  unsigned long long upd[8][2], pred[8][2];
+};
+__host__ __device__ constexpr bool ops_bit(const unsigned long long* m, int n) {
+  return n < 64 ? ((m[0] >> n) & 1ull) != 0ull : ((m[1] >> (n - 64)) & 1ull) != 0ull;
+}
+__host__ __device__ constexpr void ops_set(unsigned long long* m, int n) {
+  if (n < 64) m[0] |= 1ull << n;
+  else m[1] |= 1ull << (n - 64);
+}
+template <int P, int L> __host__ __device__ constexpr ConeOps cone_ops(int t) {
+  ConeOps o{};
+  bool need[P + 1] = {};
+  need[t] = true;
+  for (int lev = 1; lev <= L; ++lev) {
+    const int st = 1 << (lev - 1), K = P / st / 2;
+    bool nxt[P + 1] = {};
+    for (int n = 0; n <= P; ++n) {
+      if (!need[n] || n % st) continue;
+      int ev[2] = {n, n};
+      int ne = 1;
+      if ((n / st) & 1) {
+        ops_set(o.pred[lev - 1], n);
+        ev[0] = n - st;
+        ev[1] = n + st;
+        ne = 2;
+      }
+      for (int j = 0; j < ne; ++j) {
+        const int e = ev[j], k = e / (2 * st);
+        nxt[e] = true;
+        if (k > 0 && k < K) ops_set(o.upd[lev - 1], e);
+      }
+    }
+    for (int n = 0; n <= P; ++n) need[n] = nxt[n];
+  }
+  return o;
+}
+
+// The inverse lifting restricted to the operations that node TT needs (its
+// inputs: v[i] is node LO + i over the cone's window), each one as in
+// inv_levels, so TT comes out bit-identical to the full inverse.
+template <int P, int L, int LEV, int LO, int HI, int TT, typename T>
+__device__ __forceinline__ void inv_levels_cone(T* v) {
+  if constexpr (LEV >= 1) {
+    constexpr ConeOps OPS = cone_ops<P, L>(TT);
+    constexpr int st = 1 << (LEV - 1);
+    constexpr int K = (P / st) / 2;
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+      if (ops_bit(OPS.upd[LEV - 1], 2 * k * st)) {
+        const T e = fma_rn(-bl53_alpha<T>(k - 1, K), v[(2 * k - 1) * st - LO], v[2 * k * st - LO]);
+        v[2 * k * st - LO] = fma_rn(-bl53_alpha<T>(k, K), v[(2 * k + 1) * st - LO], e);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (ops_bit(OPS.pred[LEV - 1], (2 * k + 1) * st))
+        v[(2 * k + 1) * st - LO] = fma_rn(T(0.5), v[2 * k * st - LO] + v[(2 * k + 2) * st - LO], v[(2 * k + 1) * st - LO]);
+    }
+    inv_levels_cone<P, L, LEV - 1, LO, HI, TT, T>(v);
+  }
+}
+
+// The inverse BL5/3 lifting of a line restricted to the window of nodes
+// [LO, HI] (v[i] is node LO + i): every operation whose nodes all lie in the
+// window, in the order and with the arithmetic of inv_levels, so the nodes
+// of a cone that fits in the window come out bit-identical to the full
+// inverse.
+template <int P, int LEV, int LO, int HI, typename T> __device__ __forceinline__ void inv_levels_win(T* v) {
+  if constexpr (LEV >= 1) {
+    constexpr int st = 1 << (LEV - 1);
+    constexpr int K = (P / st) / 2;
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+      if ((2 * k - 1) * st >= LO && (2 * k + 1) * st <= HI) {
+        const T e = fma_rn(-bl53_alpha<T>(k - 1, K), v[(2 * k - 1) * st - LO], v[2 * k * st - LO]);
+        v[2 * k * st - LO] = fma_rn(-bl53_alpha<T>(k, K), v[(2 * k + 1) * st - LO], e);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (2 * k * st >= LO && (2 * k + 2) * st <= HI)
+        v[(2 * k + 1) * st - LO] = fma_rn(T(0.5), v[2 * k * st - LO] + v[(2 * k + 2) * st - LO], v[(2 * k + 1) * st - LO]);
+    }
+    inv_levels_win<P, LEV - 1, LO, HI, T>(v);
+  }
+}
+
 // ------------------------------------------------------------ quantisation
 // BF16 with a per-band power-of-two scale s = 2^e >= max|d| (exact scaling),
 // int8 with s = max|d|/127 and round-half-even.

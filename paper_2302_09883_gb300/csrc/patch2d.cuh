@@ -80,7 +80,10 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   static constexpr bool QUANT = ST == ST_BF16 || ST == ST_I8;
   typedef typename StoreType<ST>::type S;
   static constexpr int SB = sizeof(S);
-  static constexpr int RING = SCH == SCH_D2Q9 ? 12 * E + 4 : 16 * E;
+  // D2Q9 on BL5/3 patches reads its ghosts from the neighbours' records
+  // (ring-free); the other kernels keep a ghost ring
+  static constexpr bool RINGFREE = SCH == SCH_D2Q9 && WV == WV_BL53;
+  static constexpr int RING = RINGFREE ? 0 : (SCH == SCH_D2Q9 ? 12 * E + 4 : 16 * E);
   static constexpr int NT = sizeof(T) == 8 ? 512 : 768;
   static constexpr int NWARP = NT / 32;
   static constexpr int XLO = WV == WV_BL53 ? 1 : 0;
@@ -96,7 +99,10 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   static constexpr size_t OFF_TAU = (OFF_SINV + size_t(F) * NB * 4 + 15) / 16 * 16;
   static constexpr size_t OFF_FINFO = OFF_TAU + size_t(2) * NB * sizeof(T);
   static constexpr size_t OFF_MISC = OFF_FINFO + size_t(F) * 16 * 4;  // 64 ints + 2F window offsets
-  static constexpr size_t OFF_STAGE = (OFF_MISC + (64 + 2 * F) * 4 + 15) / 16 * 16;
+  // ring-free kernels: per (neighbour, field) the record offset, the field's
+  // section offset, word count, edge count and band mask (8 ints each)
+  static constexpr size_t OFF_NBI = (OFF_MISC + (64 + 2 * F) * 4 + 15) / 16 * 16;
+  static constexpr size_t OFF_STAGE = (OFF_NBI + (RINGFREE ? size_t(8) * F * 8 * 4 : 0) + 15) / 16 * 16;
   static constexpr size_t SMEM_MAX = 232448;
   static constexpr size_t STG = (SMEM_MAX - OFF_STAGE) / 16 * 16 > 49152 ? 49152 : (SMEM_MAX - OFF_STAGE) / 16 * 16;
   static constexpr size_t SMEM = OFF_STAGE + STG;
@@ -135,6 +141,337 @@ template <typename U> __device__ __forceinline__ U ldr(const unsigned char* p) {
 template <typename U> __device__ __forceinline__ void stg(unsigned char* p, U v) { *reinterpret_cast<U*>(p) = v; }
 
 __device__ __forceinline__ unsigned long long dbl_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// Value of node TT after the inverse lifting across a cone held in
+// rg[cone_index(n) * stride + off] (TT's own slot receives the result).
+template <int P, int L, int TT> struct ConeSlots {  // slot of every window node (-1: not in the cone)
+  static constexpr ConeMask M = cone_mask<P, L>(TT);
+  static constexpr int LO = cone_lowest(M), HI = cone_highest(M);
+  int slot[HI - LO + 1];
+  constexpr ConeSlots() : slot() {
+    int k = 0;
+    for (int n = LO; n <= HI; ++n) slot[n - LO] = cone_has(M, n) ? k++ : -1;
+  }
+};
+template <int P, int L, int TT, typename T> __device__ __forceinline__ void cone_inverse(T* rg, int stride, int off) {
+  typedef ConeSlots<P, L, TT> CS;
+  constexpr CS cs{};
+  constexpr int LO = CS::LO, HI = CS::HI;
+  T v[HI - LO + 1];
+#pragma unroll
+  for (int n = LO; n <= HI; ++n) v[n - LO] = cs.slot[n - LO] >= 0 ? rg[cs.slot[n - LO] * stride + off] : T(0);
+  inv_levels_cone<P, L, L, LO, HI, TT, T>(v);
+  constexpr int ST = cs.slot[TT - LO];
+  rg[ST * stride + off] = v[TT - LO];
+}
+
+// Ghosts without a ring (D2Q9, folded BL5/3).  A ghost is the neighbour's
+// decoded value of the current state (its post-collision population that
+// streams in), so it is computed here from the neighbour's record: only the
+// coefficients in the dependency cone of the neighbour's node next to the
+// shared border are decoded (P-1 for the west and south neighbours, 1 for
+// the east and north ones); the lines along the border are inverse
+// transformed in full, the direction across it by the restricted inverse,
+// bit-identical to a full decode.  Three rounds through the record staging
+// area: west and east, south and north, the four corners.
+template <int WV, typename T, int ST, int P, int L, typename Coll>
+__device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, unsigned char* cmask, const int* nbi,
+                               T omega, Coll& collide) {
+  typedef Cfg<SCH_D2Q9, WV, T, ST, P, L> C;
+  typedef typename C::S S;
+  constexpr int F = 9, E = C::E, PW = C::PW, TS = C::TS, NT = C::NT, NWARP = C::NWARP, NC = C::NC, NPW = C::NPW;
+  constexpr ConeMask CH = cone_mask<P, L>(P - 1), CL = cone_mask<P, L>(1);
+  constexpr int NCN = cone_count(CH);
+  static_assert(cone_count(CL) == NCN, "the two border cones mirror each other");
+  static_assert(size_t(2) * F * NCN * E * sizeof(T) <= C::STG, "ghost regions fit in the staging area");
+  static_assert(size_t(4) * F * NCN * NCN * sizeof(T) <= C::STG, "corner regions fit in the staging area");
+  constexpr int IH = cone_index_c(CH, P - 1), IL = cone_index_c(CL, 1);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  (void)pid;
+  // Decode the coefficients of field f of neighbour n (0 SW, 1 S, 2 SE, 3 W,
+  // 4 E, 5 NW, 6 N, 7 NE; section headers from the table nbi) that lie in a
+  // region into
+  // rg (zeroed before): kind 0: columns of MX, all rows (rg[ix E + y]);
+  // kind 1: rows of MY, all columns (rg[iy E + x]); kind 2: both
+  // (rg[iy NCN + ix]).  One warp: present words with their survivor ranks
+  // 32 at a time, then their surviving nodes one word at a time.
+  auto scatter = [&](int n, int f, T* rg, int kind, ConeMask MX, ConeMask MY) {
+    const int* e = nbi + 8 * (n * F + f);
+    const unsigned char* R =
+        a.arena_in + ((unsigned long long)(unsigned int)e[0] | ((unsigned long long)(unsigned int)e[1] << 32));
+    const int off = e[2], nwords = e[3], nedge = e[4];
+    int p = off + NC * int(sizeof(T));
+    unsigned long long bm = 0ull;
+    if constexpr (C::QUANT) {
+      bm = (unsigned long long)(unsigned int)e[5] | ((unsigned long long)(unsigned int)e[6] << 32);
+      p += 8 + 4 * __popcll(bm);
+    }
+    const int p_pres = p, p_words = p + 4 * NPW;
+    const int p_edge = (p_words + 4 * nwords + 7) & ~7, p_int = p_edge + nedge * int(sizeof(T));
+    static_assert(NPW <= 32, "presence words fit in one warp");
+    const unsigned int presl = lane < NPW ? ldr<unsigned int>(R + p_pres + 4 * lane) : 0u;  // lane k: word k
+    auto inside = [&](int kx, int ky) -> bool {
+      return kind == 0 ? cone_has(MX, kx) : (kind == 1 ? cone_has(MY, ky) : (cone_has(MX, kx) && cone_has(MY, ky)));
+    };
+    auto slot = [&](int kx, int ky) -> int {
+      return kind == 0 ? cone_index(MX, kx) * E + ky
+                       : (kind == 1 ? cone_index(MY, ky) * E + kx : cone_index(MY, ky) * NCN + cone_index(MX, kx));
+    };
+    for (int c = lane; c < NC; c += 32) {
+      const int iy = c / C::NC1, ix = c - iy * C::NC1;
+      if (inside(ix << L, iy << L)) rg[slot(ix << L, iy << L)] = ldr<T>(R + off + c * int(sizeof(T)));
+    }
+    unsigned ce = 0u, ci = 0u;
+    for (int j0 = 0; j0 < nwords; j0 += 32) {
+      const int j = j0 + lane;
+      int w = 0;
+      unsigned int word = 0u;
+      {
+        int r = j;
+        bool found = false;
+#pragma unroll
+        for (int k = 0; k < NPW; ++k) {
+          const unsigned int pres = __shfl_sync(0xffffffffu, presl, k);
+          const int cnt = __popc(pres);
+          if (!found && r < cnt) {
+            w = 32 * k + __fns(pres, 0, r + 1);
+            found = true;
+          }
+          if (!found) r -= cnt;
+        }
+        if (j < nwords) word = ldr<unsigned int>(R + p_words + 4 * j);
+        else w = 0;
+      }
+      const unsigned int em = word_edges<WV, P, E, C::WR>(w);
+      const unsigned ve = __popc(word & em), vi = __popc(word & ~em);
+      const unsigned ie = warp_incl_scan(ve), ii = warp_incl_scan(vi);
+      const unsigned be = ce + ie - ve, bi = ci + ii - vi;
+      ce += __shfl_sync(0xffffffffu, ie, 31);
+      ci += __shfl_sync(0xffffffffu, ii, 31);
+      // words whose nodes can lie in the region (row words: the row and the
+      // 32 columns of the word; face words: x = P and 32 rows)
+      bool hit = word != 0u;
+      if (hit) {
+        const bool rowword = w < C::NRW;
+        const int y0 = rowword ? w / C::WR : 32 * (w - C::NRW), y1 = rowword ? y0 : y0 + 31;
+        const int x0 = rowword ? 32 * (w - y0 * C::WR) : P, x1 = rowword ? x0 + 31 : P;
+        bool hx = false, hy = false;
+        for (int n = x0; n <= x1 && n <= P && !hx; ++n) hx = cone_has(MX, n);
+        for (int n = y0; n <= y1 && n <= P && !hy; ++n) hy = cone_has(MY, n);
+        hit = kind == 0 ? hx : (kind == 1 ? hy : (hx && hy));
+      }
+      unsigned int todo = __ballot_sync(0xffffffffu, hit);
+      while (todo) {
+        const int k = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const unsigned int wk = __shfl_sync(0xffffffffu, word, k), emk = __shfl_sync(0xffffffffu, em, k);
+        const unsigned bek = __shfl_sync(0xffffffffu, be, k), bik = __shfl_sync(0xffffffffu, bi, k);
+        const int ww = __shfl_sync(0xffffffffu, w, k);
+        if (!((wk >> lane) & 1u)) continue;
+        int kx, ky;
+        bool valid;
+        word_node<P, E, C::WR>(ww, lane, kx, ky, valid);
+        if (!valid || !inside(kx, ky)) continue;
+        const unsigned int lt = (1u << lane) - 1u;
+        T v;
+        if ((emk >> lane) & 1u) {
+          v = ldr<T>(R + p_edge + int(bek + __popc(wk & emk & lt)) * int(sizeof(T)));
+        } else {
+          const S qv = ldr<S>(R + p_int + int(bik + __popc(wk & ~emk & lt)) * C::SB);
+          if constexpr (ST == ST_F64 || ST == ST_F32) {
+            v = T(qv);
+          } else {
+            const int b = node_class<L>(kx) * (L + 1) + node_class<L>(ky);
+            const float sc = ldr<float>(R + off + NC * int(sizeof(T)) + 8 + 4 * __popcll(bm & ((1ull << b) - 1ull)));
+            if constexpr (ST == ST_BF16) v = T(__uint_as_float((unsigned int)qv << 16) * sc);
+            else v = T(float(qv) * sc);
+          }
+        }
+        rg[slot(kx, ky)] = v;
+      }
+    }
+  };
+  auto tile_at = [&](int i, int x, int y) -> T& { return tiles[i * TS + (y + 1) * PW + (x + 1)]; };
+  // The patch's own collision (independent of the ghosts) fills the threads
+  // that a stage leaves idle: nodes [done, done + 2 idle) go to threads
+  // busy..NT-1 while threads 0..busy-1 run the stage.
+  int done = 0;
+  auto overlap = [&](int busy) {
+    const int idle = NT - busy, n = 2 * idle < E * E - done ? 2 * idle : E * E - done;
+    if (tid >= busy)
+      for (int k = tid - busy; k < n; k += idle) collide(done + k);
+    done += n;
+  };
+
+  // ---- west (its node P-1 of every row) and east (node 1) neighbours
+  for (int i = tid; i < 2 * F * NCN * E; i += NT) reg[i] = T(0);
+  __syncthreads();
+  for (int task = warp; task < 2 * F; task += NWARP) {
+    const int sd = task / F, f = task - sd * F;
+    scatter(sd == 0 ? 3 : 4, f, reg + (sd * F + f) * NCN * E, 0, sd == 0 ? CH : CL, CH);
+  }
+  __syncthreads();
+  static_assert(2 * F * NCN <= NT, "one column per thread");
+  if (tid < 2 * F * NCN) line_transform<WV, P, L, true, T>(reg + tid * E, 1);  // columns
+  overlap(2 * F * NCN);
+  __syncthreads();
+  for (int t = tid; t < F * E; t += NT) {  // west and east rows of one field in one thread
+    const int f = t / E, y = t - f * E;
+    cone_inverse<P, L, P - 1, T>(reg + f * NCN * E, E, y);
+    cone_inverse<P, L, 1, T>(reg + (F + f) * NCN * E, E, y);
+  }
+  __syncthreads();
+  for (int t = tid; t < 2 * E; t += NT) {
+    const int sd = t / E, y = t - sd * E;
+    T fv[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fv[i] = reg[(sd * F + i) * NCN * E + (sd == 0 ? IH : IL) * E + y];
+    d2q9_collide<T>(fv, omega);
+    if (sd == 0) {
+      tile_at(1, -1, y) = fv[1];
+      tile_at(5, -1, y) = fv[5];
+      tile_at(8, -1, y) = fv[8];
+    } else {
+      tile_at(3, E, y) = fv[3];
+      tile_at(6, E, y) = fv[6];
+      tile_at(7, E, y) = fv[7];
+    }
+  }
+  __syncthreads();
+  // ---- south (its row P-1) and north (row 1) neighbours, with the four
+  // corners: SW (node (P-1, P-1), population 5), SE ((1, P-1), 6), NE
+  // ((1, 1), 7), NW ((P-1, 1), 8).  The corner regions go after the rows'
+  // in the staging area, or into the idle mask-word arrays, or get a round
+  // of their own.
+  constexpr int NCC = NCN * NCN;
+  constexpr size_t BYTES_B = size_t(2) * F * NCN * E * sizeof(T), BYTES_C = size_t(4) * F * NCC * sizeof(T);
+  constexpr bool C_STAGE = BYTES_B + BYTES_C <= C::STG;
+  constexpr bool C_MASK = !C_STAGE && BYTES_C <= C::OFF_BMAX - C::OFF_MW;
+  constexpr bool MERGED = C_STAGE || C_MASK;
+  T* regc = C_STAGE ? reg + 2 * F * NCN * E : (C_MASK ? reinterpret_cast<T*>(cmask) : reg);
+  auto south_north = [&](bool with_corners) {
+    for (int i = tid; i < 2 * F * NCN * E; i += NT) reg[i] = T(0);
+    if (with_corners)
+      for (int i = tid; i < 4 * F * NCC; i += NT) regc[i] = T(0);
+    __syncthreads();
+    const int ntask = with_corners ? 6 * F : 2 * F;
+    for (int task = warp; task < ntask; task += NWARP) {
+      if (task < 2 * F) {
+        const int sd = task / F, f = task - sd * F;
+        scatter(sd == 0 ? 1 : 6, f, reg + (sd * F + f) * NCN * E, 1, CH, sd == 0 ? CH : CL);
+      } else {
+        const int c = (task - 2 * F) / F, f = task - 2 * F - c * F;
+        const int dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
+        scatter(dy < 0 ? (dx < 0 ? 0 : 2) : (dx < 0 ? 5 : 7), f, regc + (c * F + f) * NCC, 2, dx < 0 ? CH : CL,
+                dy < 0 ? CH : CL);
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < F * E; t += NT) {  // south and north columns of one field in one thread
+      const int f = t / E, x = t - f * E;
+      cone_inverse<P, L, P - 1, T>(reg + f * NCN * E, E, x);
+      cone_inverse<P, L, 1, T>(reg + (F + f) * NCN * E, E, x);
+    }
+    if (with_corners)
+      for (int t = tid; t < 4 * F * NCN; t += NT) {  // corners: across the rows, column by column of the cone
+        const int c = t / (F * NCN), r = t - c * F * NCN, f = r / NCN, ix = r - f * NCN;
+        T* rg = regc + (c * F + f) * NCC;
+        if (c <= 1) cone_inverse<P, L, P - 1, T>(rg, NCN, ix);
+        else cone_inverse<P, L, 1, T>(rg, NCN, ix);
+      }
+    __syncthreads();
+    if (tid < 2 * F) {
+      const int sd = tid / F, f = tid - sd * F;
+      line_transform<WV, P, L, true, T>(reg + (sd * F + f) * NCN * E + (sd == 0 ? IH : IL) * E, 1);  // the row
+    } else if (with_corners && tid >= 32 && tid < 32 + 4 * F) {  // corners: then across the columns
+      const int c = (tid - 32) / F, f = tid - 32 - c * F;
+      T* rg = regc + (c * F + f) * NCC;
+      if (c == 0) cone_inverse<P, L, P - 1, T>(rg + IH * NCN, 1, 0);
+      else if (c == 1) cone_inverse<P, L, 1, T>(rg + IH * NCN, 1, 0);
+      else if (c == 2) cone_inverse<P, L, 1, T>(rg + IL * NCN, 1, 0);
+      else cone_inverse<P, L, P - 1, T>(rg + IL * NCN, 1, 0);
+    }
+    overlap(with_corners ? ((32 + 4 * F + 31) / 32) * 32 : ((2 * F + 31) / 32) * 32);
+    __syncthreads();
+    for (int t = tid; t < 2 * E + (with_corners ? 4 : 0); t += NT) {
+      T fv[9];
+      if (t < 2 * E) {
+        const int sd = t / E, x = t - sd * E;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fv[i] = reg[(sd * F + i) * NCN * E + (sd == 0 ? IH : IL) * E + x];
+        d2q9_collide<T>(fv, omega);
+        if (sd == 0) {
+          tile_at(2, x, -1) = fv[2];
+          tile_at(5, x, -1) = fv[5];
+          tile_at(6, x, -1) = fv[6];
+        } else {
+          tile_at(4, x, E) = fv[4];
+          tile_at(7, x, E) = fv[7];
+          tile_at(8, x, E) = fv[8];
+        }
+      } else {
+        const int c = t - 2 * E;
+        const int iy = c <= 1 ? IH : IL, ix = (c == 0 || c == 3) ? IH : IL;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fv[i] = regc[(c * F + i) * NCC + iy * NCN + ix];
+        d2q9_collide<T>(fv, omega);
+        if (c == 0) tile_at(5, -1, -1) = fv[5];
+        else if (c == 1) tile_at(6, E, -1) = fv[6];
+        else if (c == 2) tile_at(7, E, E) = fv[7];
+        else tile_at(8, -1, E) = fv[8];
+      }
+    }
+    __syncthreads();
+  };
+  auto corners_alone = [&]() {
+    for (int i = tid; i < 4 * F * NCC; i += NT) reg[i] = T(0);
+    __syncthreads();
+    for (int task = warp; task < 4 * F; task += NWARP) {
+      const int c = task / F, f = task - c * F;
+      const int dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
+      scatter(dy < 0 ? (dx < 0 ? 0 : 2) : (dx < 0 ? 5 : 7), f, reg + (c * F + f) * NCC, 2, dx < 0 ? CH : CL,
+              dy < 0 ? CH : CL);
+    }
+    __syncthreads();
+    for (int t = tid; t < 4 * F * NCN; t += NT) {
+      const int c = t / (F * NCN), r = t - c * F * NCN, f = r / NCN, ix = r - f * NCN;
+      T* rg = reg + (c * F + f) * NCC;
+      if (c <= 1) cone_inverse<P, L, P - 1, T>(rg, NCN, ix);
+      else cone_inverse<P, L, 1, T>(rg, NCN, ix);
+    }
+    __syncthreads();
+    if (tid < 4 * F) {
+      const int c = tid / F, f = tid - c * F;
+      T* rg = reg + (c * F + f) * NCC;
+      if (c == 0) cone_inverse<P, L, P - 1, T>(rg + IH * NCN, 1, 0);
+      else if (c == 1) cone_inverse<P, L, 1, T>(rg + IH * NCN, 1, 0);
+      else if (c == 2) cone_inverse<P, L, 1, T>(rg + IL * NCN, 1, 0);
+      else cone_inverse<P, L, P - 1, T>(rg + IL * NCN, 1, 0);
+    }
+    overlap(((4 * F + 31) / 32) * 32);
+    __syncthreads();
+    if (tid < 4) {
+      const int c = tid;
+      const int iy = c <= 1 ? IH : IL, ix = (c == 0 || c == 3) ? IH : IL;
+      T fv[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fv[i] = reg[(c * F + i) * NCC + iy * NCN + ix];
+      d2q9_collide<T>(fv, omega);
+      if (c == 0) tile_at(5, -1, -1) = fv[5];
+      else if (c == 1) tile_at(6, E, -1) = fv[6];
+      else if (c == 2) tile_at(7, E, E) = fv[7];
+      else tile_at(8, -1, E) = fv[8];
+    }
+    __syncthreads();
+  };
+  if constexpr (MERGED) {
+    south_north(true);
+  } else {
+    south_north(false);
+    corners_alone();
+  }
+  return done;
+}
 
 // The whole patch step for patch `pid` of the simulation described by `a`.
 template <int SCH, int WV, typename T, int ST, int P, int L, int MODE, int FEAT = 0>
@@ -203,8 +540,9 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   // The status word (a failed earlier step freezes the state) and the ghost
   // ring values are fetched into registers now so that their latency hides
   // behind the record staging and the decode.
-  constexpr int NGH = SCH == SCH_D2Q9 ? 12 * E + 4 : 16 * E;  // ghost cells to fill
-  constexpr int NG = (NGH + NT - 1) / NT;
+  constexpr bool RF = C::RINGFREE;
+  constexpr int NGH = RF ? 0 : (SCH == SCH_D2Q9 ? 12 * E + 4 : 16 * E);  // ghost cells to fill from a ring
+  constexpr int NG = NGH > 0 ? (NGH + NT - 1) / NT : 1;
   T gv[NG];
   int gdst[NG], gsrc[NG];  // ghost tile index (-1: none); own-node source for outflow copies (-1: ring value)
   unsigned int status0 = 0u;
@@ -332,6 +670,38 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       const int iy = c / C::NC1, ix = c - iy * C::NC1;
       tiles[win_in(f) + (iy << L) * PW + (ix << L)] = ldr<T>(R + finfo[16 * f] + c * int(sizeof(T)));
     }
+    if constexpr (MODE == MODE_STEP && RF) {
+      // The eight neighbour records are read late in the step (ring-free
+      // ghosts).  Warps F.. are idle in this phase: they start pulling those
+      // records into L2 and fill the table of their section headers.
+      static_assert(NT >= 32 * F + 8 * F, "idle warps for the neighbour table");
+      const int tn = tid - 32 * F;
+      if (tn >= 0 && tn < 8 * F) {
+        const int n = tn / F, f = tn - n * F;  // n: 0 SW, 1 S, 2 SE, 3 W, 4 E, 5 NW, 6 N, 7 NE
+        const int dx = n < 3 ? n - 1 : (n < 5 ? (n == 3 ? -1 : 1) : n - 6);
+        const int dy = n < 3 ? -1 : (n < 5 ? 0 : 1);
+        const int q = ((py + dy + a.npy) % a.npy) * a.npx + (px + dx + a.npx) % a.npx;
+        const unsigned long long ent = a.tab_in[q], roff = ent >> 24;
+        const unsigned int nb = unsigned(ent & 0xffffffull);
+        if (f == 0 && nb >= 16u)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.arena_in + roff), "r"(nb & ~15u) : "memory");
+        const uint4 fe = *reinterpret_cast<const uint4*>(a.arena_in + roff + 16 + 16 * f);  // offset, words, edges, ints
+        unsigned int b0 = 0u, b1 = 0u;
+        if constexpr (C::QUANT) {  // the band mask is only 4-byte aligned (it follows NC coarse values)
+          const unsigned int* bmp = reinterpret_cast<const unsigned int*>(a.arena_in + roff + fe.x + NC * int(sizeof(T)));
+          b0 = bmp[0];
+          b1 = bmp[1];
+        }
+        int* e = reinterpret_cast<int*>(smem + C::OFF_NBI) + 8 * tn;
+        e[0] = int(roff & 0xffffffffull);
+        e[1] = int(roff >> 32);
+        e[2] = int(fe.x);
+        e[3] = int(fe.y);
+        e[4] = int(fe.z);
+        e[5] = int(b0);
+        e[6] = int(b1);
+      }
+    }
     // present mask words: word index, survivor prefix counts (warp per field)
     if (warp < F) {
       const int f = warp, *fi = finfo + 16 * f;
@@ -436,20 +806,27 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
 
   // -------------------------------------------------------- ghosts + scheme
   if constexpr (MODE == MODE_STEP) {
+    // BGK collision of own node t, in place (D2Q9)
+    auto collide_node = [&](int t) {
+      const int y = t / E, x = t - y * E;
+      T fv[9];
 #pragma unroll
-    for (int g = 0; g < NG; ++g)
-      if (gdst[g] >= 0) tiles[gdst[g]] = gsrc[g] >= 0 ? tiles[gsrc[g]] : gv[g];
+      for (int i = 0; i < 9; ++i) fv[i] = tiles[win_in(i) + y * PW + x];
+      d2q9_collide<T>(fv, omega);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) tiles[win_in(i) + y * PW + x] = fv[i];
+    };
+    int collided = 0;
+    if constexpr (RF) {
+      collided = ringfree_ghosts<WV, T, ST, P, L>(a, pid, tiles, reinterpret_cast<T*>(stage), smem + C::OFF_MW,
+                                                  reinterpret_cast<const int*>(smem + C::OFF_NBI), omega, collide_node);
+    } else {
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+        if (gdst[g] >= 0) tiles[gdst[g]] = gsrc[g] >= 0 ? tiles[gsrc[g]] : gv[g];
+    }
     if constexpr (SCH == SCH_D2Q9) {
-      // BGK collision of every own node, in place
-      for (int t = tid; t < E * E; t += NT) {
-        const int y = t / E, x = t - y * E;
-        T fv[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) fv[i] = tiles[win_in(i) + y * PW + x];
-        d2q9_collide<T>(fv, omega);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) tiles[win_in(i) + y * PW + x] = fv[i];
-      }
+      for (int t = collided + tid; t < E * E; t += NT) collide_node(t);
       __syncthreads();
     } else {
       __syncthreads();
@@ -928,6 +1305,8 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   __syncthreads();
 
   // --------------------------- re-decode: the state the neighbours will see
+  // (ring-free kernels: the neighbours decode it themselves next step)
+  if constexpr (RF) return;
   for (int t = tid; t < F * E; t += NT) {
     const int f = t / E, x = t - f * E;
     line_transform<WV, P, L, true, T>(tiles + win_out(f) + x, PW);
