@@ -235,6 +235,14 @@ typedef struct wcs_mlp wcs_mlp;
  * fit in shared memory (patch <= 96); else WCS_E_UNSUPPORTED. */
 wcs_status wcs_features_labels(const float* dense_dev, int nfields, int64_t nx, int64_t ny, int wavelet, int patch,
                                int levels, double delta, float* feat_dev, float* label_dev, void* stream);
+/* The same for cubic BL5/3 patches of a periodic 3-D state [F][nz][ny][nx]
+ * (the D3Q19 geometry; patch 32 or 16, levels 3): 7 axis sets per level, so
+ * npatch x 42 features; the transforms run in FP32 like the 3-D step, the
+ * threshold test and the error sums in FP64.  Patches in the order
+ * pid = (pz * npy + py) * npx + px.  Synchronises the stream; allocates a
+ * scratch of F (patch+1)^3 floats per SM for the call. */
+wcs_status wcs_features_labels3(const float* dense_dev, int nfields, int64_t nx, int64_t ny, int64_t nz, int patch,
+                                int levels, double delta, float* feat_dev, float* label_dev, void* stream);
 wcs_status wcs_mlp_create(int nin, wcs_mlp** out);
 void wcs_mlp_destroy(wcs_mlp* m);
 int wcs_mlp_nparam(const wcs_mlp* m);

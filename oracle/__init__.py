@@ -65,7 +65,8 @@ def lib():
         L.orc_d2q9_collide.argtypes = [i32, dp, dbl]
         L.orc_rusanov.argtypes = [dp, dp, i32, i32, dbl, dp]
         L.orc_patch_features.argtypes = [i32, i32, i64, i32, i32, dp, dp]
-        L.orc_patch_label.argtypes = [i32, i32, i64, i32, i32, dp, dbl, dp]
+        L.orc_patch_label.argtypes = [i32, i32, i64, i32, i32, dp, dbl, dp, i32]
+        L.orc_patch_features_f32.argtypes = [i32, i32, i64, i32, i32, dp, dp]
         L.orc_eps_grid.restype = dbl
         L.orc_eps_grid.argtypes = [i32]
         L.orc_mlp_forward.argtypes = [i32, i32, dp, dp, i32, dp]
@@ -88,6 +89,8 @@ def lib():
         L.orc3_record.argtypes = [vp, i64, C.c_char_p, i64]
         L.orc3_stats.argtypes = [vp, dp]
         L.orc3_set_patch_eps.argtypes = [vp, dp]
+        L.orc3_track_features.argtypes = [vp, i32]
+        L.orc3_features.argtypes = [vp, dp]
         L.orc_last_error.restype = C.c_char_p
         _lib = L
     return _lib
@@ -293,20 +296,23 @@ def n_features(dims, L):
     return 2 * ((1 << dims) - 1) * L
 
 
-def patch_features(u, wavelet, P, L):
+def patch_features(u, wavelet, P, L, prec="f64"):
     """u: (F, E, E) or (F, E, E, E) node values of one patch -> features
-    (groups (l, S) in order, energy then max)."""
+    (groups (l, S) in order, energy then max); prec: precision of the
+    transforms."""
     a = np.ascontiguousarray(u, dtype=np.float64)
     out = np.zeros(n_features(a.ndim - 1, L), np.float64)
-    _check(lib().orc_patch_features(WAVELET[wavelet], a.ndim - 1, P, L, a.shape[0], _dp(a), _dp(out)))
+    fn = lib().orc_patch_features if prec == "f64" else lib().orc_patch_features_f32
+    _check(fn(WAVELET[wavelet], a.ndim - 1, P, L, a.shape[0], _dp(a), _dp(out)))
     return out
 
 
-def patch_label(u, wavelet, P, L, delta):
-    """log10 of the largest admissible eps of a patch (grid + bisection)."""
+def patch_label(u, wavelet, P, L, delta, prec="f64"):
+    """log10 of the largest admissible eps of a patch (grid + bisection);
+    prec: precision of the transforms (tests and sums are FP64)."""
     a = np.ascontiguousarray(u, dtype=np.float64)
     out = np.zeros(1, np.float64)
-    _check(lib().orc_patch_label(WAVELET[wavelet], a.ndim - 1, P, L, a.shape[0], _dp(a), delta, _dp(out)))
+    _check(lib().orc_patch_label(WAVELET[wavelet], a.ndim - 1, P, L, a.shape[0], _dp(a), delta, _dp(out), PREC[prec]))
     return float(out[0])
 
 
@@ -398,6 +404,15 @@ class OracleSim3(_Run3):
         e = np.ascontiguousarray(eps, np.float64)
         assert e.shape == (self.npatch,)
         _check(lib().orc3_set_patch_eps(self.h, _dp(e)))
+
+    def track_features(self, on=True):
+        lib().orc3_track_features(self.h, int(on))
+
+    def features(self):
+        """Features (npatch, 42 for L = 3) of every patch at its last encode."""
+        out = np.zeros((self.npatch, n_features(3, self.L)), np.float64)
+        _check(lib().orc3_features(self.h, _dp(out)))
+        return out
 
     def stats(self):
         out = np.zeros(32, np.float64)

@@ -373,14 +373,34 @@ int orc_patch_features(int wavelet, int dims, int64_t P, int L, int nfields, con
   });
 }
 
-int orc_patch_label(int wavelet, int dims, int64_t P, int L, int nfields, const double* u, double delta, double* out) {
+// prec 0: FP64 transforms, 1: FP32 transforms (threshold test and sums in FP64).
+int orc_patch_label(int wavelet, int dims, int64_t P, int L, int nfields, const double* u, double delta, double* out,
+                    int prec) {
   return guard([&] {
     const int64_t E = wavelet == BL53 ? P + 1 : P;
     int64_t n = 1;
     for (int a = 0; a < dims; ++a) n *= E;
     std::vector<std::vector<double>> v(nfields);
     for (int f = 0; f < nfields; ++f) v[f].assign(u + f * n, u + (f + 1) * n);
-    *out = patch_label(v, wavelet, dims, P, L, delta);
+    *out = prec == 0 ? patch_label<double>(v, wavelet, dims, P, L, delta) : patch_label<float>(v, wavelet, dims, P, L, delta);
+  });
+}
+
+// Features of a patch whose transforms run in FP32 (coefficients converted
+// to FP64 for the sums).
+int orc_patch_features_f32(int wavelet, int dims, int64_t P, int L, int nfields, const double* u, double* out) {
+  return guard([&] {
+    const int64_t E = wavelet == BL53 ? P + 1 : P;
+    int64_t n = 1;
+    for (int a = 0; a < dims; ++a) n *= E;
+    std::vector<std::vector<double>> c(nfields);
+    for (int f = 0; f < nfields; ++f) {
+      std::vector<float> t(u + f * n, u + (f + 1) * n);
+      fwd_nd<float>(wavelet, t.data(), dims, P, L);
+      c[f].assign(t.begin(), t.end());
+    }
+    auto v = patch_features(c, dims, E, L);
+    for (size_t i = 0; i < v.size(); ++i) out[i] = v[i];
   });
 }
 
@@ -508,6 +528,25 @@ int orc3_stats(void* p, double* out) {
     out[20] = double(h->s64 ? h->s64->nstep : h->s32->nstep);
     out[22] = double(h->s64 ? h->s64->shared_mismatch : h->s32->shared_mismatch);
     out[23] = double(h->s64 ? h->s64->compressed_bytes() : h->s32->compressed_bytes());
+  });
+}
+
+int orc3_track_features(void* p, int on) {
+  Handle3* h = static_cast<Handle3*>(p);
+  if (h->s64) h->s64->track_feat = on != 0;
+  else h->s32->track_feat = on != 0;
+  return 0;
+}
+
+int orc3_features(void* p, double* out) {
+  Handle3* h = static_cast<Handle3*>(p);
+  return guard([&] {
+    const auto& fv = h->s64 ? h->s64->feat : h->s32->feat;
+    size_t o = 0;
+    for (const auto& f : fv) {
+      if (f.empty()) throw std::runtime_error("no features recorded");
+      for (double v : f) out[o++] = v;
+    }
   });
 }
 

@@ -73,28 +73,38 @@ inline double eps_grid(int k) { return std::pow(10.0, -7.0 + k / 8.0); }
 constexpr int EPS_GRID_N = 41;
 
 // Label of a patch state u (F blocks of E^dims node values): log10 of the
-// largest admissible eps (see the header).
+// largest admissible eps (see the header).  T is the precision of the
+// transforms (the threshold test and the error sums are FP64 either way):
+// double for the 2-D labels, float for the 3-D ones, which the library
+// computes with FP32 lifting.
+template <class T = double>
 inline double patch_label(const std::vector<std::vector<double>>& u, int wavelet, int dims, int64_t P, int L,
                           double delta) {
   const int64_t E = wavelet == BL53 ? P + 1 : P;
   int64_t n = 1;
   for (int a = 0; a < dims; ++a) n *= E;
-  std::vector<std::vector<double>> c = u;
+  std::vector<std::vector<T>> c(u.size());
+  std::vector<std::vector<T>> uT(u.size());
   double norm2 = 0;
-  for (auto& f : c) {
-    for (int64_t p = 0; p < n; ++p) norm2 += f[p] * f[p];
-    fwd_nd<double>(wavelet, f.data(), dims, P, L);
+  for (size_t f = 0; f < u.size(); ++f) {
+    uT[f].assign(u[f].begin(), u[f].end());
+    c[f] = uT[f];
+    for (int64_t p = 0; p < n; ++p) norm2 += double(uT[f][p]) * double(uT[f][p]);
+    fwd_nd<T>(wavelet, c[f].data(), dims, P, L);
   }
   auto admissible = [&](double eps) {
     double err2 = 0;
     for (size_t f = 0; f < c.size(); ++f) {
-      std::vector<double> t = c[f];
+      std::vector<T> t = c[f];
       for (int64_t p = 0; p < n; ++p) {
         int64_t kk[3] = {p % E, (p / E) % E, p / (E * E)};
-        if (node_group(kk, dims, L) != 0 && !(std::fabs(t[p]) >= eps)) t[p] = 0.0;
+        if (node_group(kk, dims, L) != 0 && !(std::fabs(double(t[p])) >= eps)) t[p] = T(0);
       }
-      inv_nd<double>(wavelet, t.data(), dims, P, L);
-      for (int64_t p = 0; p < n; ++p) err2 += (t[p] - u[f][p]) * (t[p] - u[f][p]);
+      inv_nd<T>(wavelet, t.data(), dims, P, L);
+      for (int64_t p = 0; p < n; ++p) {
+        const double d = double(t[p]) - double(uT[f][p]);
+        err2 += d * d;
+      }
     }
     return std::sqrt(err2) <= delta * std::sqrt(norm2);
   };

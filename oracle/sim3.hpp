@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "codec.hpp"
+#include "mlp.hpp"
 #include "schemes.hpp"
 #include "wavelet.hpp"
 
@@ -69,6 +70,8 @@ template <class T> struct Sim3 {
   Layout lay;
   std::vector<std::vector<uint8_t>> rec;
   std::vector<double> eps_patch;
+  bool track_feat = false;               // keep the features of every encoded patch
+  std::vector<std::vector<double>> feat;  // per patch, before the threshold
   int64_t nstep = 0;
   int64_t shared_mismatch = 0;
 
@@ -86,6 +89,7 @@ template <class T> struct Sim3 {
     E = wavelet == BL53 ? P + 1 : P;
     lay = Layout(wavelet, 3, P, L);
     rec.resize(npatch());
+    feat.resize(npatch());
     eps_patch.assign(npatch(), eps);
   }
   int64_t npatch() const { return np[0] * np[1] * np[2]; }
@@ -102,6 +106,11 @@ template <class T> struct Sim3 {
 
   void encode_patch_fields(int64_t pid, std::vector<std::vector<T>>& loc) {
     for (int f = 0; f < F; ++f) fwd_nd<T>(grid.wavelet, loc[f].data(), 3, P, L);
+    if (track_feat) {
+      std::vector<std::vector<double>> c(F);
+      for (int f = 0; f < F; ++f) c[f].assign(loc[f].begin(), loc[f].end());
+      feat[pid] = patch_features(c, 3, E, L);
+    }
     std::vector<double> ef(F, eps_patch[pid]);
     rec[pid] = encode_patch<T>(lay, loc, store, rule, ef, eps, uint32_t(pid), flags());
   }

@@ -79,6 +79,7 @@ def lib():
                                    i32, C.POINTER(vp), i32, i32, i32, C.POINTER(i32), C.POINTER(C.c_double)]
         fp = C.POINTER(C.c_float)
         L.wcs_features_labels.argtypes = [vp, i32, i64, i64, i32, i32, i32, C.c_double, vp, vp, vp]
+        L.wcs_features_labels3.argtypes = [vp, i32, i64, i64, i64, i32, i32, C.c_double, vp, vp, vp]
         L.wcs_mlp_create.argtypes = [i32, C.POINTER(vp)]
         L.wcs_mlp_destroy.argtypes = [vp]
         L.wcs_mlp_nparam.argtypes = [vp]

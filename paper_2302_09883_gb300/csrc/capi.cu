@@ -103,6 +103,7 @@ struct wcs_sim {
   int grid3 = 0;
   float* scratch = nullptr;
   unsigned char* rbuf = nullptr;
+  float inv_cnt3[24] = {0};  // 1 / (fields x nodes) of each 3-D feature group
   size_t tsize = 8;
   KernelEntry ke;
   cudaStream_t stream = nullptr;
@@ -150,6 +151,9 @@ static wcs_status dalloc(wcs_sim* s, void** p, size_t bytes) {
   s->resident += int64_t(bytes);
   return WCS_OK;
 }
+
+// Features per patch of the learned threshold: 2 (2^dims - 1) L.
+static int nfeat(const wcs_sim* s) { return 2 * ((1 << s->dims) - 1) * s->L; }
 
 static wcs::PatchArgs base_args(const wcs_sim* s) {
   wcs::PatchArgs a;
@@ -229,8 +233,10 @@ static wcs::Patch3Args base_args3(const wcs_sim* s) {
   a.band_factor = s->bfactor;
   a.eps = s->eps;
   a.eps_edge = s->eps;
-  a.eps_patch = s->eps_given ? s->eps_patch : nullptr;
+  a.eps_patch = (s->eps_given || s->mlp) ? s->eps_patch : nullptr;
   a.omega = float(1.0 / s->tau);
+  a.feat = s->feat;
+  for (int g = 0; g < 24; ++g) a.feat_inv_cnt[g] = s->inv_cnt3[g];
   a.scratch = s->scratch;
   a.rbuf = s->rbuf;
   a.slot_floats = s->k3->slot_floats;
@@ -318,6 +324,20 @@ static wcs_status create3(const wcs_grid* grid, int scheme, int patch, int level
   s->tsize = 4;
   s->ring_vals = ke->ring;
   s->grid3 = std::min(s->npatch, nsm);
+  {  // feature groups (l, S): l = the largest axis class, S = the axes of that class
+    long long cnt[24] = {0};
+    auto cls = [&](int k) { return k % (1 << levels) == 0 ? 0 : __builtin_ctz(unsigned(k)) + 1; };
+    for (int z = 0; z < s->E; ++z)
+      for (int y = 0; y < s->E; ++y)
+        for (int x = 0; x < s->E; ++x) {
+          const int c[3] = {cls(x), cls(y), cls(z)};
+          const int l = std::max(c[0], std::max(c[1], c[2]));
+          if (l == 0) continue;
+          const int S = (c[0] == l ? 1 : 0) | (c[1] == l ? 2 : 0) | (c[2] == l ? 4 : 0);
+          ++cnt[7 * (l - 1) + S - 1];
+        }
+    for (int g = 0; g < 24; ++g) s->inv_cnt3[g] = cnt[g] ? float(1.0 / (double(cnt[g]) * 19)) : 0.0f;
+  }
 
   // threshold multiplier of each band (c_x slowest, then c_y, c_z fastest)
   std::vector<double> bf(s->nb);
@@ -530,13 +550,15 @@ wcs_status wcs_sim_use_mlp(wcs_sim* s, wcs_mlp* m, double eps_lo, double eps_hi)
     s->mlp = nullptr;
     return WCS_OK;
   }
-  if (s->dims != 2 || (s->ke.scheme != WCS_D2Q9 && s->ke.scheme != WCS_EULER2D)) return WCS_E_UNSUPPORTED;
-  if (wcs_mlp_nparam(m) != 64 * (6 * s->L) + 64 + 64 * 64 + 64 + 64 + 1)
-    return fail(s, WCS_E_ARG, "the network's input size must be 6 x levels");
+  if (s->dims == 2 && s->ke.scheme != WCS_D2Q9 && s->ke.scheme != WCS_EULER2D) return WCS_E_UNSUPPORTED;
+  const int nin = nfeat(s);
+  if (wcs_mlp_nparam(m) != 64 * nin + 64 + 64 * 64 + 64 + 64 + 1)
+    return fail(s, WCS_E_ARG, "the network's input size must be " + std::to_string(nin) +
+                                  " (2 x (2^dims - 1) x levels)");
   if (!(eps_lo > 0) || !(eps_hi >= eps_lo)) return fail(s, WCS_E_ARG, "bad eps range");
   if (!s->feat) {
     wcs_status st;
-    if ((st = dalloc(s, (void**)&s->feat, size_t(s->npatch) * 6 * s->L * 4)) != WCS_OK) return st;
+    if ((st = dalloc(s, (void**)&s->feat, size_t(s->npatch) * nfeat(s) * 4)) != WCS_OK) return st;
     if ((st = dalloc(s, (void**)&s->eps_patch, size_t(s->npatch) * 8)) != WCS_OK) return st;
   }
   std::vector<double> e(s->npatch, s->eps);
@@ -557,7 +579,7 @@ wcs_status wcs_sim_set_patch_eps(wcs_sim* s, const double* eps_host) {
     if (!(eps_host[p] >= 0)) return fail(s, WCS_E_ARG, "per-patch eps must be >= 0");
   if (!s->feat) {
     wcs_status st;
-    if ((st = dalloc(s, (void**)&s->feat, size_t(s->npatch) * 6 * s->L * 4)) != WCS_OK) return st;
+    if ((st = dalloc(s, (void**)&s->feat, size_t(s->npatch) * nfeat(s) * 4)) != WCS_OK) return st;
     if ((st = dalloc(s, (void**)&s->eps_patch, size_t(s->npatch) * 8)) != WCS_OK) return st;
   }
   CK(cudaStreamSynchronize(s->stream));
@@ -570,7 +592,7 @@ wcs_status wcs_sim_set_patch_eps(wcs_sim* s, const double* eps_host) {
 wcs_status wcs_sim_patch_data(wcs_sim* s, float* feat_host, double* eps_host) {
   if (!s || !s->feat) return WCS_E_ARG;
   CK(cudaStreamSynchronize(s->stream));
-  if (feat_host) CK(cudaMemcpy(feat_host, s->feat, size_t(s->npatch) * 6 * s->L * 4, cudaMemcpyDeviceToHost));
+  if (feat_host) CK(cudaMemcpy(feat_host, s->feat, size_t(s->npatch) * nfeat(s) * 4, cudaMemcpyDeviceToHost));
   if (eps_host) CK(cudaMemcpy(eps_host, s->eps_patch, size_t(s->npatch) * 8, cudaMemcpyDeviceToHost));
   return WCS_OK;
 }
@@ -657,7 +679,16 @@ wcs_status wcs_step(wcs_sim* s, int64_t n) {
   if (!s->inited) return fail(s, WCS_E_ARG, "wcs_step before wcs_init_macro");
   if (s->dims == 3) {
     for (int64_t i = 0; i < n; ++i) {
-      CK(s->k3->launch(wcs::MODE_STEP, step_args3(s, s->nstep), s->grid3, s->stream));
+      wcs::Patch3Args a = step_args3(s, s->nstep);
+      if (s->mlp) {  // features of the new state and the network's eps for the next step
+        a.mlp_wt = wcs::mlp_kernel_weights(s->mlp);
+        a.eps_next = s->eps_patch;
+        a.eps_lo = s->eps_lo;
+        a.eps_hi = s->eps_hi;
+        CK(s->k3->launch_feat(a, s->grid3, s->stream));
+      } else {
+        CK(s->k3->launch(wcs::MODE_STEP, a, s->grid3, s->stream));
+      }
       s->nstep += 1;
     }
     return WCS_OK;

@@ -14,8 +14,20 @@ template <int ST, int P, int L> cudaError_t prepare3() {
   if ((e = cudaFuncSetAttribute(patch3_kernel<WV_BL53, ST, P, L, MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(C::SMEM))) != cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(patch3_kernel<WV_BL53, ST, P, L, MODE_STEP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(C::SMEM_FEAT))) != cudaSuccess)
+    return e;
   return cudaFuncSetAttribute(patch3_kernel<WV_BL53, ST, P, L, MODE_EXPORT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(C::SMEM));
+}
+
+// step that also writes the features of the new state and, with a network,
+// the next step's eps per patch
+template <int ST, int P, int L> cudaError_t launch3_feat(const Patch3Args& a, int grid, cudaStream_t s) {
+  typedef Cfg3<P, L, ST> C;
+  if (grid <= 0) return cudaSuccess;
+  patch3_kernel<WV_BL53, ST, P, L, MODE_STEP, 1><<<grid, C::NT, C::SMEM_FEAT, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <int ST, int P, int L> cudaError_t launch3(int mode, const Patch3Args& a, int grid, cudaStream_t s) {
@@ -48,6 +60,7 @@ template <int ST, int P, int L> Kernel3Entry make3() {
   k.slot_floats = (unsigned long long)C::F * C::EG3;
   k.slot_rbytes = (max_record3<ST, P, L>() + 255ull) / 256ull * 256ull;
   k.launch = &launch3<ST, P, L>;
+  k.launch_feat = &launch3_feat<ST, P, L>;
   k.prepare = &prepare3<ST, P, L>;
   return k;
 }

@@ -242,6 +242,197 @@ __global__ void __launch_bounds__(256) features_labels(const float* __restrict__
   if (tid == 0) label[pid] = float(lab);
 }
 
+// ------------------------------------------------ 3-D features and labels
+// Cubic BL5/3 patches of P cells (the D3Q19 path): FP32 lifting in a shared
+// tile (the precision of the 3-D step), one CTA of 1024 threads per patch in
+// a stride, the forward-transformed fields kept in a global scratch slot of
+// F (P+1)^3 floats per CTA.  Features: energy and max per band in a fixed
+// order (bands of a group added in band order), groups (l, S) over the 7
+// axis sets.  Labels as in 2-D; the threshold test compares in FP64 and the
+// squared errors are summed in FP64.
+template <int P, int L>
+__global__ void __launch_bounds__(1024, 1)
+    features_labels3(const float* __restrict__ dense, int F, int G0, int G1, int G2, int npx, int npy, int npz,
+                     double delta, float* __restrict__ cscr, unsigned long long slot, float* feat, float* label) {
+  constexpr int E = P + 1, E2 = E * E, E3 = E2 * E, NT = 1024, NWARP = NT / 32, G = 7 * L, NB = (L + 1) * (L + 1) * (L + 1);
+  extern __shared__ __align__(16) unsigned char sm3[];
+  float* tile = reinterpret_cast<float*>(sm3);
+  double* wred = reinterpret_cast<double*>(sm3 + (size_t(E3) * 4 + 15) / 16 * 16);  // NWARP partial sums
+  double* be = wred + NWARP;        // band energy (all fields)
+  float* bmx = reinterpret_cast<float*>(be + NB);  // band max
+  int* flag = reinterpret_cast<int*>(bmx + NB);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* C = cscr + size_t(blockIdx.x) * slot;
+  auto cls = [](int k) -> int { return wcs::node_class<L>(k); };
+  auto lines = [&](int axis, bool inverse) {
+    for (int l = tid; l < E2; l += NT) {
+      const int u = l % E, v = l / E;
+      float* q = axis == 0 ? tile + v * E2 + u * E : (axis == 1 ? tile + v * E2 + u : tile + v * E + u);
+      const int st = axis == 0 ? 1 : (axis == 1 ? E : E2);
+      if (inverse) wcs::line_transform<wcs::WV_BL53, P, L, true, float>(q, st);
+      else wcs::line_transform<wcs::WV_BL53, P, L, false, float>(q, st);
+    }
+    __syncthreads();
+  };
+  auto block_sum = [&](double v) -> double {  // fixed order: shuffle tree, then warps in order
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) wred[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int w = 0; w < NWARP; ++w) r += wred[w];
+    __syncthreads();
+    return r;
+  };
+  const int np = npx * npy * npz;
+  for (int pid = blockIdx.x; pid < np; pid += gridDim.x) {
+    const int px = pid % npx, py = (pid / npx) % npy, pz = pid / (npx * npy);
+    auto gidx = [&](int i) -> size_t {
+      const int x = i % E, y = (i / E) % E, z = i / E2;
+      const int gx = (px * P + x) % G0, gy = (py * P + y) % G1, gz = (pz * P + z) % G2;
+      return (size_t(gz) * G1 + gy) * G0 + gx;
+    };
+    if (tid < NB) {
+      be[tid] = 0.0;
+      bmx[tid] = 0.0f;
+    }
+    double n2 = 0.0;
+    for (int f = 0; f < F; ++f) {
+      const float* uf = dense + size_t(f) * G0 * G1 * G2;
+      for (int i = tid; i < E3; i += NT) {
+        const float v = uf[gidx(i)];
+        tile[i] = v;
+        n2 += double(v) * double(v);
+      }
+      __syncthreads();
+      lines(0, false);
+      lines(1, false);
+      lines(2, false);
+      for (int i = tid; i < E3; i += NT) C[size_t(f) * E3 + i] = tile[i];
+      // band sums of this field: thread b walks the band's nodes in order
+      if (tid < NB) {
+        const int b = tid, cx = b / ((L + 1) * (L + 1)), cy = (b / (L + 1)) % (L + 1), cz = b % (L + 1);
+        double e = 0.0;
+        float m = 0.0f;
+        if (b != 0)
+          for (int z = 0; z < E; ++z) {
+            if (cls(z) != cz) continue;
+            for (int y = 0; y < E; ++y) {
+              if (cls(y) != cy) continue;
+              for (int x = 0; x < E; ++x) {
+                if (cls(x) != cx) continue;
+                const float d = tile[(z * E + y) * E + x];
+                e += double(d) * double(d);
+                m = fmaxf(m, fabsf(d));
+              }
+            }
+          }
+        be[b] += e;
+        bmx[b] = fmaxf(bmx[b], m);
+      }
+      __syncthreads();
+    }
+    const double norm2 = block_sum(n2);
+    if (tid < G) {  // group g: level l, axes S; bands of the group in band order
+      const int g = tid, l = g / 7 + 1, S = g % 7 + 1;
+      double e = 0.0;
+      float m = 0.0f;
+      long long cnt = 0;
+      for (int b = 1; b < NB; ++b) {
+        const int c[3] = {b / ((L + 1) * (L + 1)), (b / (L + 1)) % (L + 1), b % (L + 1)};
+        const int bl = max(c[0], max(c[1], c[2]));
+        const int bs = (c[0] == bl ? 1 : 0) | (c[1] == bl ? 2 : 0) | (c[2] == bl ? 4 : 0);
+        if (bl != l || bs != S) continue;
+        e += be[b];
+        m = fmaxf(m, bmx[b]);
+        long long nb = 1;
+        for (int a = 0; a < 3; ++a) {
+          int k = 0;
+          for (int n = 0; n < E; ++n) k += cls(n) == c[a] ? 1 : 0;
+          nb *= k;
+        }
+        cnt += nb;
+      }
+      feat[size_t(pid) * 2 * G + 2 * g] = float(log10(e / double(cnt * F) + 1e-30));
+      feat[size_t(pid) * 2 * G + 2 * g + 1] = float(log10(double(m) + 1e-30));
+    }
+    // labels: the grid, then four bisections
+    auto err2_of = [&](double eps) -> double {
+      double acc = 0.0;
+      for (int f = 0; f < F; ++f) {
+        for (int i = tid; i < E3; i += NT) {
+          const int x = i % E, y = (i / E) % E, z = i / E2;
+          const float c = C[size_t(f) * E3 + i];
+          const bool coarse = (cls(x) | cls(y) | cls(z)) == 0;
+          tile[i] = (coarse || fabs(double(c)) >= eps) ? c : 0.0f;
+        }
+        __syncthreads();
+        lines(2, true);
+        lines(1, true);
+        lines(0, true);
+        const float* uf = dense + size_t(f) * G0 * G1 * G2;
+        for (int i = tid; i < E3; i += NT) {
+          const double d = double(tile[i]) - double(uf[gidx(i)]);
+          acc += d * d;
+        }
+        __syncthreads();
+      }
+      return block_sum(acc);
+    };
+    const double bound = delta * sqrt(norm2);
+    int best = -1;
+    for (int k = 0; k < EPS_N; ++k)
+      if (sqrt(err2_of(c_eps_grid[k])) <= bound) best = k;
+    double lab;
+    if (best < 0) {
+      lab = -7.0;
+    } else if (best == EPS_N - 1) {
+      lab = -2.0;
+    } else {
+      double lo = c_eps_grid[best], hi = c_eps_grid[best + 1];
+      for (int it = 0; it < 4; ++it) {
+        const double mid = sqrt(lo * hi);
+        if (sqrt(err2_of(mid)) <= bound) lo = mid;
+        else hi = mid;
+      }
+      lab = log10(lo);
+    }
+    if (tid == 0) label[pid] = float(lab);
+    (void)flag;
+    __syncthreads();
+  }
+}
+
+template <int P, int L> size_t fl3_smem() {
+  constexpr int E = P + 1, E3 = E * E * E, NB = (L + 1) * (L + 1) * (L + 1);
+  return (size_t(E3) * 4 + 15) / 16 * 16 + 32 * 8 + NB * 8 + NB * 4 + 16;
+}
+
+template <int P, int L>
+wcs_status run_features_labels3(const float* dense, int nfields, int64_t nx, int64_t ny, int64_t nz, double delta,
+                                float* feat, float* label, cudaStream_t st) {
+  const size_t smem = fl3_smem<P, L>();
+  if (cudaFuncSetAttribute(features_labels3<P, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+    return WCS_E_CUDA;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int npx = int(nx / P), npy = int(ny / P), npz = int(nz / P), np = npx * npy * npz;
+  const int grid = std::min(np, nsm);
+  const unsigned long long slot = (unsigned long long)nfields * (P + 1) * (P + 1) * (P + 1);
+  float* cscr = nullptr;
+  if (cudaMalloc(&cscr, size_t(grid) * slot * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return WCS_E_OOM;
+  }
+  features_labels3<P, L><<<grid, 1024, smem, st>>>(dense, nfields, int(nx), int(ny), int(nz), npx, npy, npz, delta, cscr,
+                                                   slot, feat, label);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(cscr);
+  return e == cudaSuccess ? WCS_OK : WCS_E_CUDA;
+}
+
 // ------------------------------------------------------------------ MLP
 __device__ inline float gelu(float x) { return wcs::gelu_f(x); }
 __device__ inline float gelu_grad(float x) {
@@ -473,6 +664,20 @@ wcs_status wcs_features_labels(const float* dense_dev, int nfields, int64_t nx, 
   features_labels<<<npx * npy, 256, smem, static_cast<cudaStream_t>(stream)>>>(
       dense_dev, nfields, int(nx), int(ny), npx, patch, levels, wavelet, delta, feat_dev, label_dev);
   return cudaGetLastError() == cudaSuccess ? WCS_OK : WCS_E_CUDA;
+}
+
+wcs_status wcs_features_labels3(const float* dense_dev, int nfields, int64_t nx, int64_t ny, int64_t nz, int patch,
+                                int levels, double delta, float* feat_dev, float* label_dev, void* stream) {
+  if (!dense_dev || nfields <= 0 || !feat_dev || !label_dev || patch <= 0 || nx <= 0 || ny <= 0 || nz <= 0 ||
+      nx % patch || ny % patch || nz % patch)
+    return WCS_E_ARG;
+  double grid[EPS_N];
+  for (int k = 0; k < EPS_N; ++k) grid[k] = std::pow(10.0, -7.0 + k / 8.0);
+  if (cudaMemcpyToSymbol(c_eps_grid, grid, sizeof(grid)) != cudaSuccess) return WCS_E_CUDA;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (patch == 32 && levels == 3) return run_features_labels3<32, 3>(dense_dev, nfields, nx, ny, nz, delta, feat_dev, label_dev, st);
+  if (patch == 16 && levels == 3) return run_features_labels3<16, 3>(dense_dev, nfields, nx, ny, nz, delta, feat_dev, label_dev, st);
+  return WCS_E_UNSUPPORTED;
 }
 
 wcs_status wcs_mlp_create(int nin, wcs_mlp** out) {

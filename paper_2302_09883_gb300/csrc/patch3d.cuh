@@ -145,6 +145,12 @@ struct Patch3Args {
   int field_sel;              // EXPORT: one field or -1 for all
   long long G0, G1, G2;       // global nodes per axis (periodic: cells)
   unsigned int flags;         // record flags word
+  // learned threshold (FEAT kernels)
+  float* feat;                // per patch 42 features of the new state
+  float feat_inv_cnt[24];     // per group: 1 / (fields x nodes of the group)
+  const float* mlp_wt;        // network in kernel layout (W1, W2 transposed)
+  double* eps_next;           // the eps of the next step, per patch
+  double eps_lo, eps_hi;      // clamp of the network's eps; non-finite -> eps
 };
 
 template <int P, int L, int ST> struct Cfg3 {
@@ -179,6 +185,15 @@ template <int P, int L, int ST> struct Cfg3 {
   static constexpr size_t OFF_MISC = OFF_WS + 3 * 32 * 4;
   static constexpr size_t SMEM = OFF_MISC + 64 * 4;
   static_assert(SMEM <= 232448, "patch does not fit in shared memory");
+  // learned-threshold kernels: per z-line class sums, band totals, the network
+  static constexpr int NG = 7 * L, NIN = 2 * NG;
+  static constexpr int MLP_NP = 64 * NIN + 64 + 64 * 64 + 64 + 64 + 1;
+  static constexpr size_t OFF_LACC = (SMEM + 15) / 16 * 16;                       // E2 x (L+1) x {e, m}
+  static constexpr size_t OFF_BAND = OFF_LACC + size_t(E2) * (L + 1) * 2 * 4;    // NB doubles + NB floats
+  static constexpr size_t OFF_FV = (OFF_BAND + size_t(NB) * 12 + 15) / 16 * 16;   // NIN features
+  static constexpr size_t OFF_W = (OFF_FV + size_t(NIN) * 4 + 15) / 16 * 16;
+  static constexpr size_t SMEM_FEAT = OFF_W + size_t(MLP_NP) * 4;
+  static_assert(SMEM_FEAT <= 232448, "the learned-threshold patch does not fit in shared memory");
   static_assert(E3 < 65536, "survivor ranks are kept in 16 bits");
   static_assert(NB <= 64, "band masks are 64 bits");
 };
@@ -274,7 +289,7 @@ __device__ __forceinline__ void block_scan3(unsigned int& a, unsigned int& b, un
 
 // One patch (pid) of one launch.  MODE_INIT encodes the equilibrium of the
 // macroscopic fields, MODE_STEP advances one step, MODE_EXPORT decodes.
-template <int WV, int ST, int P, int L, int MODE>
+template <int WV, int ST, int P, int L, int MODE, int FEAT = 0>
 __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned char* Rb, unsigned char* smem) {
   typedef Cfg3<P, L, ST> C;
   typedef float T;
@@ -501,6 +516,15 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
   }
   if (tid == 0) misc[0] = C::HDR;  // running offset of the next field section
   bool bad = false;
+  float* lacc = reinterpret_cast<float*>(smem + C::OFF_LACC);
+  double* band_e = reinterpret_cast<double*>(smem + C::OFF_BAND);
+  float* band_m = reinterpret_cast<float*>(band_e + NB);
+  if constexpr (FEAT) {
+    if (tid < NB) {
+      band_e[tid] = 0.0;
+      band_m[tid] = 0.0f;
+    }
+  }
   for (int f = 0; f < F; ++f) {
     const float* Sf = Sc + size_t(f) * EG3;
     {
@@ -533,11 +557,18 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
         unsigned int myw[(E + 31) / 32];
 #pragma unroll
         for (int k = 0; k < (E + 31) / 32; ++k) myw[k] = 0u;
+        float acc2[L + 1], accm[L + 1];  // FEAT: this z-line's energy and max per z class
+#pragma unroll
+        for (int c = 0; c <= L; ++c) { acc2[c] = 0.0f; accm[c] = 0.0f; }
         T v[E];
 #pragma unroll
         for (int z = 0; z < E; ++z) v[z] = valid ? col[z * E2] : T(0);
         auto node = [&](int z) {
           const int cz = node_class<L>(z);
+          if constexpr (FEAT) {
+            acc2[cz] = acc2[cz] + v[z] * v[z];
+            accm[cz] = fmaxf(accm[cz], fabsf(v[z]));
+          }
           bool keep = false;
           if (valid && (cx | cy | cz)) {
             const bool zedge = z == 0 || z == P;
@@ -561,17 +592,32 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
           const int z = 32 * k + lane;
           if (z < E) mw[(z * E + y) * WR + h] = myw[k];
         }
+        if constexpr (FEAT) {
+          if (valid)
+#pragma unroll
+            for (int c = 0; c <= L; ++c) {
+              lacc[((y * E + x) * (L + 1) + c) * 2] = acc2[c];
+              lacc[((y * E + x) * (L + 1) + c) * 2 + 1] = accm[c];
+            }
+        }
       } else {
         const int y = 32 * (g - C::RG) + lane;
         const bool valid = y < E;
         const int cy = node_class<L>(valid ? y : 0);
         T* col = tile + (valid ? y : 0) * E + P;
+        float acc2[L + 1], accm[L + 1];
+#pragma unroll
+        for (int c = 0; c <= L; ++c) { acc2[c] = 0.0f; accm[c] = 0.0f; }
         T v[E];
 #pragma unroll
         for (int z = 0; z < E; ++z) v[z] = valid ? col[z * E2] : T(0);
         auto node = [&](int z) {
           const int cz = node_class<L>(z);
           if (!valid) return;
+          if constexpr (FEAT) {
+            acc2[cz] = acc2[cz] + v[z] * v[z];
+            accm[cz] = fmaxf(accm[cz], fabsf(v[z]));
+          }
           if (!isfinite(v[z])) bad = true;
           if (cy | cz) {  // x = P is a coarse x-node; every node here is on a face
             const int b = cy * (L + 1) + cz;
@@ -585,9 +631,33 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
           col[z * E2] = v[z];
         };
         fwd_levels_cb<WV, P, 1, L, T>(v, node);
+        if constexpr (FEAT) {
+          if (valid)
+#pragma unroll
+            for (int c = 0; c <= L; ++c) {
+              lacc[((y * E + P) * (L + 1) + c) * 2] = acc2[c];
+              lacc[((y * E + P) * (L + 1) + c) * 2 + 1] = accm[c];
+            }
+        }
       }
     }
     __syncthreads();
+    if constexpr (FEAT) {  // band sums of this field: band b walks its z-lines in order
+      if (tid > 0 && tid < NB) {
+        const int b = tid, cx = b / ((L + 1) * (L + 1)), cy = (b / (L + 1)) % (L + 1), cz = b % (L + 1);
+        float e = 0.0f, m = 0.0f;
+        for (int y = 0; y < E; ++y) {
+          if (node_class<L>(y) != cy) continue;
+          for (int x = 0; x < E; ++x) {
+            if (node_class<L>(x) != cx) continue;
+            e = e + lacc[((y * E + x) * (L + 1) + cz) * 2];
+            m = fmaxf(m, lacc[((y * E + x) * (L + 1) + cz) * 2 + 1]);
+          }
+        }
+        band_e[b] += double(e);
+        band_m[b] = fmaxf(band_m[b], m);
+      }
+    }
 
     // band scales (Sec. 2.3 values, quantised): BF16 with a power-of-two
     // scale >= max|d|, int8 with max|d|/127, per band over interior survivors
@@ -752,6 +822,66 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
   if (bad) {
     if (atomicOr(&a.ctl->status, STAT_NAN) == 0u) a.ctl->err_step = int(a.step);
   }
+  if constexpr (FEAT) {
+    // features of the new state: group (l, S) = the bands whose largest
+    // class is l on exactly the axes S, in band order
+    float* fv = reinterpret_cast<float*>(smem + C::OFF_FV);
+    if (tid < C::NG) {
+      const int g = tid, l = g / 7 + 1, S = g % 7 + 1;
+      double e = 0.0;
+      float m = 0.0f;
+      for (int b = 1; b < NB; ++b) {
+        const int c0 = b / ((L + 1) * (L + 1)), c1 = (b / (L + 1)) % (L + 1), c2 = b % (L + 1);
+        const int bl = max(c0, max(c1, c2));
+        const int bs = (c0 == bl ? 1 : 0) | (c1 == bl ? 2 : 0) | (c2 == bl ? 4 : 0);
+        if (bl != l || bs != S) continue;
+        e += band_e[b];
+        m = fmaxf(m, band_m[b]);
+      }
+      fv[2 * g] = log10f(float(e) * a.feat_inv_cnt[g] + 1e-30f);
+      fv[2 * g + 1] = log10f(m + 1e-30f);
+      a.feat[size_t(pid) * C::NIN + 2 * g] = fv[2 * g];
+      a.feat[size_t(pid) * C::NIN + 2 * g + 1] = fv[2 * g + 1];
+    }
+    __syncthreads();
+    if (a.mlp_wt && warp == 0) {  // the network, lane j owns hidden units j and j + 32
+      constexpr int H = 64, NIN = C::NIN;
+      const float* W1T = reinterpret_cast<const float*>(smem + C::OFF_W);
+      const float* b1 = W1T + NIN * H;
+      const float* W2T = b1 + H;
+      const float* b2 = W2T + H * H;
+      const float* W3 = b2 + H;
+      const float* b3 = W3 + H;
+      float h0 = b1[lane], h1 = b1[lane + 32];
+      for (int i = 0; i < NIN; ++i) {
+        const float xi = fv[i];
+        h0 = __fmaf_rn(W1T[i * H + lane], xi, h0);
+        h1 = __fmaf_rn(W1T[i * H + lane + 32], xi, h1);
+      }
+      const float a0 = gelu_f(h0), a1v = gelu_f(h1);
+      float z0 = b2[lane], z1 = b2[lane + 32];
+#pragma unroll 8
+      for (int i = 0; i < 32; ++i) {
+        const float u = __shfl_sync(0xffffffffu, a0, i);
+        z0 = __fmaf_rn(W2T[i * H + lane], u, z0);
+        z1 = __fmaf_rn(W2T[i * H + lane + 32], u, z1);
+      }
+#pragma unroll 8
+      for (int i = 0; i < 32; ++i) {
+        const float u = __shfl_sync(0xffffffffu, a1v, i);
+        z0 = __fmaf_rn(W2T[(i + 32) * H + lane], u, z0);
+        z1 = __fmaf_rn(W2T[(i + 32) * H + lane + 32], u, z1);
+      }
+      float yv = W3[lane] * gelu_f(z0) + W3[lane + 32] * gelu_f(z1);
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) yv = yv + __shfl_down_sync(0xffffffffu, yv, o);
+      if (lane == 0) {
+        double ev = pow(10.0, double(yv + b3[0]));
+        if (!isfinite(ev)) ev = a.eps;
+        a.eps_next[pid] = ev < a.eps_lo ? a.eps_lo : (ev > a.eps_hi ? a.eps_hi : ev);
+      }
+    }
+  }
   // ring: post-collision inward populations of the export layers
   for (int t = tid; t < 6 * E2 + 12 * E; t += NT) {
     int x, y, z;
@@ -823,7 +953,7 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
 
 // Persistent launch: CTA b takes patches b, b + grid, ... with its own
 // scratch slot.
-template <int WV, int ST, int P, int L, int MODE>
+template <int WV, int ST, int P, int L, int MODE, int FEAT = 0>
 __global__ void __launch_bounds__(1024, 1) patch3_kernel(const Patch3Args a) {
   extern __shared__ __align__(16) unsigned char smem3[];
   const int np = a.npx * a.npy * a.npz;
@@ -841,7 +971,15 @@ __global__ void __launch_bounds__(1024, 1) patch3_kernel(const Patch3Args a) {
     __syncthreads();
     if (st0 & (STAT_ARENA_FULL | STAT_NAN | STAT_BAD_RECORD)) return;
   }
-  for (int pid = blockIdx.x; pid < np; pid += gridDim.x) patch3_body<WV, ST, P, L, MODE>(a, pid, Sc, Rb, smem3);
+  if constexpr (FEAT) {  // the network's weights, once per CTA
+    typedef Cfg3<P, L, ST> C;
+    if (a.mlp_wt) {
+      float* W = reinterpret_cast<float*>(smem3 + C::OFF_W);
+      for (int i = threadIdx.x; i < C::MLP_NP; i += C::NT) W[i] = __ldg(a.mlp_wt + i);
+    }
+    __syncthreads();
+  }
+  for (int pid = blockIdx.x; pid < np; pid += gridDim.x) patch3_body<WV, ST, P, L, MODE, FEAT>(a, pid, Sc, Rb, smem3);
 }
 
 }  // namespace wcs

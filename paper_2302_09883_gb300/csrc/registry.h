@@ -36,6 +36,7 @@ struct Kernel3Entry {
   unsigned long long slot_floats;  // scratch floats per CTA
   unsigned long long slot_rbytes;  // record buffer bytes per CTA (largest record)
   cudaError_t (*launch)(int mode, const Patch3Args& a, int grid, cudaStream_t s);
+  cudaError_t (*launch_feat)(const Patch3Args& a, int grid, cudaStream_t s);
   cudaError_t (*prepare)();
 };
 

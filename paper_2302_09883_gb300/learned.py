@@ -32,6 +32,23 @@ def features_labels(dense, P, L, delta, wavelet="bl53", stream=None):
     return feat, lab
 
 
+def features_labels3(dense, P, L, delta, stream=None):
+    """dense: CUDA float32 tensor (F, nz, ny, nx), periodic, cubic BL5/3
+    patches.  Returns CUDA tensors (npatch, 14L) float32 features and
+    (npatch,) float32 labels (log10 eps)."""
+    import torch
+    F, nz, ny, nx = dense.shape
+    npatch = (nx // P) * (ny // P) * (nz // P)
+    feat = torch.empty((npatch, 14 * L), dtype=torch.float32, device=dense.device)
+    lab = torch.empty((npatch,), dtype=torch.float32, device=dense.device)
+    d = dense.contiguous()
+    torch.cuda.synchronize()
+    st = B.lib().wcs_features_labels3(d.data_ptr(), F, nx, ny, nz, P, L, delta, feat.data_ptr(), lab.data_ptr(), stream)
+    B.check(st, None)
+    torch.cuda.synchronize()
+    return feat, lab
+
+
 class Mlp:
     def __init__(self, nin, weights=None, seed=0):
         h = C.c_void_p()
@@ -106,7 +123,8 @@ def set_patch_eps(sim, eps):
 
 
 def patch_data(sim, L):
-    feat = np.zeros((sim.npatch, 6 * L), np.float32)
+    dims = 3 if len(sim.G) == 3 else 2
+    feat = np.zeros((sim.npatch, 2 * ((1 << dims) - 1) * L), np.float32)
     eps = np.zeros(sim.npatch, np.float64)
     B.check(B.lib().wcs_sim_patch_data(sim.h, feat.ctypes.data_as(C.POINTER(C.c_float)),
                                        eps.ctypes.data_as(C.POINTER(C.c_double))), sim.h)

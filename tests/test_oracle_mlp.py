@@ -147,3 +147,53 @@ def test_label_bounds():
     # noise far below the smallest eps: every eps drops all of it, delta is tighter
     rough = np.stack([1 + 1e-9 * rng.normal(size=X.shape)])
     assert O.patch_label(rough, "bl53", P, L, 1e-12) == -7.0
+
+
+def _group3(k, L):
+    c = [_cls(v, L) for v in k]
+    l = max(c)
+    if l == 0:
+        return None
+    S = sum(1 << a for a in range(3) if c[a] == l)
+    return (l - 1) * 7 + S - 1
+
+
+def test_features_of_planted_coefficients_3d():
+    # 3-D: 7 groups per level (every non-empty set of axes); one planted
+    # coefficient per group, read back from the features after the inverse
+    # transform
+    P, L = 8, 3
+    E = P + 1
+    rng = np.random.default_rng(4)
+    nodes = {}
+    for kz in range(E):
+        for ky in range(E):
+            for kx in range(E):
+                g = _group3((kx, ky, kz), L)
+                if g is not None:
+                    nodes.setdefault(g, []).append((kz, ky, kx))
+    assert sorted(nodes) == list(range(7 * L))
+    c = np.zeros((E, E, E))
+    for g, lst in nodes.items():
+        kz, ky, kx = lst[rng.integers(len(lst))]
+        c[kz, ky, kx] = (g + 1) / 11.0
+    c[0, 0, 0] = 1.0  # a coarse value, not a feature
+    u = O.dwt(c, "bl53", P, L, inverse=True)
+    feat = O.patch_features(u[None], "bl53", P, L)
+    assert feat.shape == (2 * 7 * L,)
+    for g in range(7 * L):
+        v = c[tuple(np.array(nodes[g]).T)]
+        assert abs(feat[2 * g] - math.log10(np.sum(v * v) / len(v) + 1e-30)) < 1e-9
+        assert abs(feat[2 * g + 1] - math.log10(np.max(np.abs(v)) + 1e-30)) < 1e-9
+
+
+def test_fp32_label_is_close_to_fp64_label_3d():
+    P, L = 16, 3
+    x = np.arange(P + 1) / P
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    rng = np.random.default_rng(6)
+    u = np.stack([1 + 0.05 * np.sin(4 * X + 2 * Y) * np.cos(3 * Z) + 1e-5 * rng.normal(size=X.shape),
+                  0.02 * np.cos(2 * X - Z)])
+    l64 = O.patch_label(u, "bl53", P, L, 1e-4)
+    l32 = O.patch_label(u, "bl53", P, L, 1e-4, prec="f32")
+    assert -7 < l64 < -2 and abs(l64 - l32) <= 1 / 128 + 1e-9
