@@ -501,6 +501,71 @@ def d3q19_section(torch, K, W, flush, bs, n_quality=256, quality_steps=1000, n_t
     ok = [q for q in quality if q["rel_l2_u"] <= 1e-3 and q["rel_l2_rho"] <= 1e-3]
     head = max(ok, key=lambda q: q["eps"]) if ok else quality[0]
 
+    # learned eps (config 5's network, 42 inputs): trained on dense snapshots
+    # of 128^3 vortices (u0 0.02 / 0.04 / 0.06, with and without N(0, 1e-5)
+    # velocity noise, t = 0 and 300), compared with the uniform sweep at the
+    # same error of u on the quality grid
+    from paper_2302_09883_gb300 import learned
+    snaps = []
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    for u0 in (0.02, 0.04, 0.06):
+        for noise in (0.0, 1e-5):
+            m3 = 128
+            fm = _tgv_device(torch, m3, u0)
+            if noise:
+                fm[1] = fm[1] + noise * torch.randn(fm[1].shape, generator=gen, device="cuda", dtype=torch.float64)
+            d = Dense3(m3, m3, m3, tau=tau, stream=bs)
+            d.init_macro(fm)
+            done = 0
+            for t in (0, 300):
+                d.step(t - done)
+                done = t
+                Fs = torch.empty((19, m3, m3, m3), dtype=torch.float32, device="cuda")
+                for i in range(19):
+                    d.export_field(i, out=Fs[i], dtype=np.float32)
+                snaps.append(Fs)
+            d.close()
+    pts = sorted((q["rel_l2_u"], q["compression_ratio"]) for q in quality)
+
+    def uniform_ratio_at(err):
+        xs, ys = np.log([p[0] for p in pts]), np.log([p[1] for p in pts])
+        if not (xs[0] <= np.log(err) <= xs[-1]):
+            return None
+        return float(np.exp(np.interp(np.log(err), xs, ys)))
+
+    learned_runs = []
+    for delta in (3e-7, 3e-6):
+        X, T = [], []
+        for Fs in snaps:
+            f_, l_ = learned.features_labels3(Fs, P, L, delta)
+            X.append(f_)
+            T.append(l_)
+        X, T = torch.cat(X), torch.cat(T)
+        mdl, hist = learned.fit(X, T, epochs=300, batch=64, lr=2e-3, seed=3)
+        c = Sim3(n, n, n, P, L, 1e-6, store="bf16", tau=tau, arena_factor=0.3, stream=bs)
+        learned.use_mlp(c, mdl, 1e-8, 1e-2)
+        c.init_macro(_tgv_device(torch, n))
+        c.step(quality_steps)
+        c.sync()
+        Fc = torch.empty((19, n, n, n), dtype=torch.float32, device="cuda")
+        c.export_field(-1, out=Fc, dtype=np.float32)
+        rho_c, u_c = moments(Fc.double())
+        st = c.stats()
+        _, eps_p = learned.patch_data(c, L)
+        r = {"delta": delta, "n_train": int(X.shape[0]), "label_mean": float(T.mean()), "label_std": float(T.std()),
+             "train_loss_first": float(hist[0]), "train_loss_last": float(hist[-1]),
+             "rel_l2_u": float((u_c - u_d).norm() / u_d.norm()), "rel_l2_rho": float((rho_c - rho_d).norm() / rho_d.norm()),
+             "compression_ratio": st["uncompressed_bytes"] / c.compressed_bytes(),
+             "eps_patch_log10_min": float(np.log10(eps_p.min())), "eps_patch_log10_max": float(np.log10(eps_p.max()))}
+        ur = uniform_ratio_at(r["rel_l2_u"])
+        r["uniform_ratio_at_same_error"] = ur
+        r["ratio_gain"] = r["compression_ratio"] / ur if ur else None
+        learned_runs.append(r)
+        c.close()
+        del Fc
+    del snaps
+    torch.cuda.empty_cache()
+
     def timed(obj):
         obj.step(W)
         torch.cuda.synchronize()
@@ -531,7 +596,8 @@ def d3q19_section(torch, K, W, flush, bs, n_quality=256, quality_steps=1000, n_t
             "eps": head["eps"], "quality_grid": n_quality, "quality_steps": quality_steps, "quality": quality,
             "mlups": lu / (ms_c * 1e-3) / 1e6, "ms_per_step": ms_c, "uncompressed_mlups": lu / (ms_d * 1e-3) / 1e6,
             "uncompressed_ms_per_step": ms_d, "uncompressed_gbs": 152.0 * lu / (ms_d * 1e-3) / 1e9,
-            "compression_ratio": ratio_big, "resident_bytes": resident_c, "uncompressed_resident_bytes": dense_bytes}
+            "compression_ratio": ratio_big, "resident_bytes": resident_c, "uncompressed_resident_bytes": dense_bytes,
+            "learned": learned_runs}
 
 
 def roofline_bytes(sim, w):
