@@ -16,8 +16,10 @@ shear wave u_x = 0.05 sin(2 pi y/2048) + N(0, 1e-4), tau = 0.6.
   4. the uncompressed baseline timed the same way, the C-ABI end to end with
      host buffers, nvidia-smi clocks during the timed region, and the CPU
      oracle on a bounded sample (--impl reference times only the oracle);
-  5. the 2-D Euler workload (4096^2 cells, outflow) the same way, reported
-     under "euler"; the batch of 96 D2Q9 grids under "batch".
+  5. side sections: the 2-D Euler workload (4096^2 cells, outflow) under
+     "euler", the batch of 96 D2Q9 grids under "batch", learned against
+     uniform eps under "learned_eps", D3Q19 (quality on 256^3, timing on
+     1024^3, and the 42-input network) under "d3q19".
 
 --gpus N (under torchrun) runs N independent replicas (weak scaling); rank 0
 prints the line with the max time over ranks.
@@ -65,6 +67,13 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(torch, ms, device):
+    """The slowest replica's time, on every rank (the job's time at N > 1)."""
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
 
 
 def macro_fields(w, n=None):
@@ -752,9 +761,7 @@ def main():
     sim.sync()
     torch.cuda.synchronize()
     if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(torch, ms, "cuda")
     bytes_per_launch = roofline_bytes(sim, w)
     st = sim.stats()
     comp_bytes = sim.compressed_bytes()
