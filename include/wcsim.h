@@ -191,7 +191,8 @@ const char* wcs_last_error(const wcs_sim* sim);
  * Batches of independent simulations (many grids of different sizes, one
  * launch per kind of kernel per step, six steps captured in one CUDA graph
  * and replayed).  Every simulation must be initialised, created on the same
- * stream and at the same step.  The batch borrows the simulations (destroy
+ * stream and at the same step; 3-D simulations and simulations with a
+ * learned threshold are stepped alone (WCS_E_UNSUPPORTED).  The batch borrows the simulations (destroy
  * the batch before them); stepping one of them outside the batch makes the
  * next wcs_batch_step fail with WCS_E_ARG.
  * ---------------------------------------------------------------------- */

@@ -892,6 +892,11 @@ wcs_status wcs_batch_create(wcs_sim* const* sims, int nsims, wcs_batch** out) {
       batch_free(b);
       return WCS_E_UNSUPPORTED;
     }
+    if (s->mlp) {
+      g_create_err = "batch: a simulation with a learned threshold is stepped alone";
+      batch_free(b);
+      return WCS_E_UNSUPPORTED;
+    }
     if (s->npatch >= (1 << 20)) {
       g_create_err = "batch: more than 2^20 patches in one simulation";
       batch_free(b);
