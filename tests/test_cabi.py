@@ -58,6 +58,7 @@ def _create(L, g, scheme, P, Lv, eps, o):
 
 @pytest.mark.parametrize("case,want,msg", [
     ("ragged_2d", 1, "multiple of the patch"),
+    ("empty_grid", 1, "multiple of the patch"),
     ("negative_eps", 1, "eps"),
     ("no_kernel", 7, "no compiled kernel"),
     ("d2q9_outflow", 1, "periodic"),
@@ -73,6 +74,8 @@ def test_create_rejects_bad_arguments_without_a_gpu(L, case, want, msg):
     g3 = _grid(3, (64, 64, 64), 7)
     if case == "ragged_2d":
         r = _create(L, _grid(2, (250, 256, 1), 3), "d2q9", 64, 4, 1e-3, _opts())
+    elif case == "empty_grid":
+        r = _create(L, _grid(2, (0, 256, 1), 3), "d2q9", 64, 4, 1e-3, _opts())
     elif case == "negative_eps":
         r = _create(L, g2, "d2q9", 64, 4, -1.0, _opts())
     elif case == "no_kernel":

@@ -92,3 +92,10 @@ def test_d3q19_dense_baseline_matches_oracle_reference():
     b = r.export_all()
     for i in range(19):
         assert np.array_equal(d.export_field(i), b[i])
+
+
+def test_d3q19_only_coarse_blocks_survive_at_huge_eps():
+    f = inputs.taylor_green_3d(32, u0=0.04)
+    g, o = run_pair3((32, 32, 32), 16, 3, 1e30, "bf16", f, 3, check_at=(1,))
+    assert np.array_equal(g.export_field(-1), o.export_all())
+    assert np.array_equal(g.stats()["field_sum"], o.stats()["coef_sums"])

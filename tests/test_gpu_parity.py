@@ -163,3 +163,14 @@ def test_euler_nonfinite_state_is_reported_and_frozen():
     assert ei.value.status == 4
     st = g.stats()
     assert st["status"] != 0 and st["step"] < 200
+
+
+@pytest.mark.parametrize("store", ["bf16", "i8"])
+def test_d2q9_only_coarse_blocks_survive_at_huge_eps(store):
+    # eps 1e30: every detail (edge lines included) is dropped, the records
+    # hold coarse blocks and empty masks; ring-free ghosts then come from the
+    # neighbours' coarse blocks alone.  Mass stays that of the coarse blocks.
+    f = inputs.shear_wave(256, seed=9)
+    g, o = run_pair("d2q9", "bl53", 256, 64, 4, 1e30, "f32", store, 5, f, tau=0.6, check_records_at=(1,))
+    assert np.array_equal(g.export_field(-1), o.export_all())
+    assert np.array_equal(g.stats()["field_sum"], o.stats()["coef_sums"])
