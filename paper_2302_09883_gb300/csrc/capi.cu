@@ -4,7 +4,9 @@
 //   arena[2]   ping-pong compressed arenas; step n reads arena n%2 and
 //              bump-allocates the records of state n+1 in arena (n+1)%2
 //   tab[2]     per patch (record offset << 24 | record bytes)
-//   ring[2]    ghost rings exported by every patch for the next step
+//   ring[2]    ghost rings exported by every patch for the next step (none
+//              for D2Q9 on BL5/3, whose ghosts come from the records)
+//   scratch    3-D kernels: per resident CTA a scratch cube and record buffer
 //   ctl        cursors, max signal speed, time, sticky status
 //   pstats     FP64 coarse-block sums per patch and field
 //   bfactor    threshold multiplier per band (Sec. 2.2)

@@ -3,13 +3,16 @@
 //
 //   stage record (16-B vector loads) -> decode (zero the tiles, scatter the
 //   coarse block and the survivors of the non-zero mask words only) ->
-//   inverse tensor lifting -> ghost ring from the neighbours' exports ->
-//   scheme (D2Q9 collide in place + pull via per-population shifted windows,
-//   or the Rusanov FV update) -> forward tensor lifting -> threshold over the
-//   node order with warp ballots -> prefix sums, bump-allocate, write the
-//   record (survivors only) and the dequantised values back in place ->
-//   re-decode -> export the ghost ring the neighbours need next step
-//   (post-collision populations for D2Q9) and FP64 coarse-block sums.
+//   inverse tensor lifting -> ghosts -> scheme (D2Q9 collide in place + pull
+//   via per-population shifted windows, or the Rusanov FV update) -> forward
+//   tensor lifting -> threshold over the node order with warp ballots ->
+//   prefix sums, bump-allocate, write the record (survivors only) and the
+//   dequantised values back in place, FP64 coarse-block sums.
+//   Ghosts: D2Q9 on BL5/3 patches decodes them from the neighbours' records
+//   of the current state (only the dependency cone of the boundary node, see
+//   ringfree_ghosts); the other kernels read a ring that every patch exports
+//   at the end of the step by re-decoding its new record (post-collision
+//   inward populations for D2Q9 with Haar, the state for Euler).
 //
 // Record byte format (the paper's pipeline, Sec. 2: DWT of Sec. 2.1.2, hard
 // threshold of Sec. 2.2, a bitmask + values lossless stage in place of
