@@ -643,10 +643,15 @@ def algorithmic_flops_per_lu(P, L, F=9):
 
 
 def kernel_src_hash():
+    """sha256 (first 16 hex) of the step kernel's sources with comments and
+    blank lines removed: comment edits do not invalidate a profile."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ["common.cuh", "patch2d.cuh", "launch.cuh"]:
-        h.update(open(os.path.join(ROOT, "paper_2302_09883_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2302_09883_gb300", "csrc", f)).read()
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 
