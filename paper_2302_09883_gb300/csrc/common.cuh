@@ -233,6 +233,10 @@ __host__ __device__ constexpr int cone_index_c(ConeMask c, int n) {
   for (int m = 0; m < n; ++m) k += cone_has(c, m) ? 1 : 0;
   return k;
 }
+// Bits [x0, x0 + 32) of the cone mask (x0 a multiple of 32, below 128).
+__device__ __forceinline__ unsigned int cone_bits32(ConeMask c, int x0) {
+  return x0 < 64 ? (unsigned int)(c.lo >> x0) : (unsigned int)(c.hi >> (x0 - 64));
+}
 // Index of node n among the cone's nodes (n in the cone), at run time.
 __device__ __forceinline__ int cone_index(ConeMask c, int n) {
   return n < 64 ? __popcll(c.lo & ((1ull << n) - 1ull)) : __popcll(c.lo) + __popcll(c.hi & ((1ull << (n - 64)) - 1ull));

@@ -93,7 +93,7 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   static constexpr int XHI = P - 1;
   static constexpr int LMASK = (1 << L) - 1;
   // shared memory carve-up (bytes)
-  static constexpr size_t OFF_MW = size_t(NTILE) * TS * sizeof(T);
+  static constexpr size_t OFF_MW = (size_t(NTILE) * TS * sizeof(T) + 15) / 16 * 16;
   static constexpr size_t OFF_PRE = OFF_MW + size_t(F) * NW * 4;
   static constexpr size_t OFF_EMW = (OFF_PRE + size_t(3) * F * NW * 2 + 15) / 16 * 16;
   static constexpr size_t OFF_BMAX = OFF_EMW + size_t(F) * NW * 4;
@@ -247,20 +247,21 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
       }
       const unsigned int em = word_edges<WV, P, E, C::WR>(w);
       const unsigned ve = __popc(word & em), vi = __popc(word & ~em);
-      const unsigned ie = warp_incl_scan(ve), ii = warp_incl_scan(vi);
+      // both survivor counts in one scan (each lane <= 32, sums <= 1024)
+      const unsigned sc = warp_incl_scan(ve | (vi << 16));
+      const unsigned ie = sc & 0xffffu, ii = sc >> 16;
       const unsigned be = ce + ie - ve, bi = ci + ii - vi;
       ce += __shfl_sync(0xffffffffu, ie, 31);
       ci += __shfl_sync(0xffffffffu, ii, 31);
-      // words whose nodes can lie in the region (row words: the row and the
-      // 32 columns of the word; face words: x = P and 32 rows)
+      // words with a surviving node in the region (row words: one row y0,
+      // columns x0 + bit; face words: column P, rows y0 + bit)
       bool hit = word != 0u;
       if (hit) {
         const bool rowword = w < C::NRW;
-        const int y0 = rowword ? w / C::WR : 32 * (w - C::NRW), y1 = rowword ? y0 : y0 + 31;
-        const int x0 = rowword ? 32 * (w - y0 * C::WR) : P, x1 = rowword ? x0 + 31 : P;
-        bool hx = false, hy = false;
-        for (int n = x0; n <= x1 && n <= P && !hx; ++n) hx = cone_has(MX, n);
-        for (int n = y0; n <= y1 && n <= P && !hy; ++n) hy = cone_has(MY, n);
+        const int y0 = rowword ? w / C::WR : 32 * (w - C::NRW);
+        const int x0 = rowword ? 32 * (w - y0 * C::WR) : P;
+        const bool hx = rowword ? (word & cone_bits32(MX, x0)) != 0u : cone_has(MX, P);
+        const bool hy = rowword ? cone_has(MY, y0) : (word & cone_bits32(MY, y0)) != 0u;
         hit = kind == 0 ? hx : (kind == 1 ? hy : (hx && hy));
       }
       unsigned int todo = __ballot_sync(0xffffffffu, hit);
@@ -295,19 +296,25 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
     }
   };
   auto tile_at = [&](int i, int x, int y) -> T& { return tiles[i * TS + (y + 1) * PW + (x + 1)]; };
+  // zero n values at p (16-byte aligned) with vector stores
+  auto zero = [&](T* p, int n) {
+    const int n4 = int(n * sizeof(T) / 16);
+    for (int i = tid; i < n4; i += NT) reinterpret_cast<uint4*>(p)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = n4 * int(16 / sizeof(T)) + tid; i < n; i += NT) p[i] = T(0);
+  };
   // The patch's own collision (independent of the ghosts) fills the threads
-  // that a stage leaves idle: nodes [done, done + 2 idle) go to threads
+  // that a stage leaves idle: nodes [done, done + per idle) go to threads
   // busy..NT-1 while threads 0..busy-1 run the stage.
   int done = 0;
-  auto overlap = [&](int busy) {
-    const int idle = NT - busy, n = 2 * idle < E * E - done ? 2 * idle : E * E - done;
+  auto overlap = [&](int busy, int per) {
+    const int idle = NT - busy, n = per * idle < E * E - done ? per * idle : E * E - done;
     if (tid >= busy)
       for (int k = tid - busy; k < n; k += idle) collide(done + k);
     done += n;
   };
 
   // ---- west (its node P-1 of every row) and east (node 1) neighbours
-  for (int i = tid; i < 2 * F * NCN * E; i += NT) reg[i] = T(0);
+  zero(reg, 2 * F * NCN * E);
   __syncthreads();
   for (int task = warp; task < 2 * F; task += NWARP) {
     const int sd = task / F, f = task - sd * F;
@@ -316,7 +323,7 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   __syncthreads();
   static_assert(2 * F * NCN <= NT, "one column per thread");
   if (tid < 2 * F * NCN) line_transform<WV, P, L, true, T>(reg + tid * E, 1);  // columns
-  overlap(2 * F * NCN);
+  overlap(2 * F * NCN, 2);
   __syncthreads();
   for (int t = tid; t < F * E; t += NT) {  // west and east rows of one field in one thread
     const int f = t / E, y = t - f * E;
@@ -340,6 +347,7 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
       tile_at(7, E, y) = fv[7];
     }
   }
+  overlap((2 * E + 31) / 32 * 32, 1);
   __syncthreads();
   // ---- south (its row P-1) and north (row 1) neighbours, with the four
   // corners: SW (node (P-1, P-1), population 5), SE ((1, P-1), 6), NE
@@ -351,11 +359,11 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   constexpr bool C_STAGE = BYTES_B + BYTES_C <= C::STG;
   constexpr bool C_MASK = !C_STAGE && BYTES_C <= C::OFF_BMAX - C::OFF_MW;
   constexpr bool MERGED = C_STAGE || C_MASK;
+  static_assert(!C_STAGE || BYTES_B % 16 == 0, "corner regions start 16-byte aligned");
   T* regc = C_STAGE ? reg + 2 * F * NCN * E : (C_MASK ? reinterpret_cast<T*>(cmask) : reg);
   auto south_north = [&](bool with_corners) {
-    for (int i = tid; i < 2 * F * NCN * E; i += NT) reg[i] = T(0);
-    if (with_corners)
-      for (int i = tid; i < 4 * F * NCC; i += NT) regc[i] = T(0);
+    zero(reg, 2 * F * NCN * E);
+    if (with_corners) zero(regc, 4 * F * NCC);
     __syncthreads();
     const int ntask = with_corners ? 6 * F : 2 * F;
     for (int task = warp; task < ntask; task += NWARP) {
@@ -394,7 +402,7 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
       else if (c == 2) cone_inverse<P, L, 1, T>(rg + IL * NCN, 1, 0);
       else cone_inverse<P, L, P - 1, T>(rg + IL * NCN, 1, 0);
     }
-    overlap(with_corners ? ((32 + 4 * F + 31) / 32) * 32 : ((2 * F + 31) / 32) * 32);
+    overlap(with_corners ? ((32 + 4 * F + 31) / 32) * 32 : ((2 * F + 31) / 32) * 32, 2);
     __syncthreads();
     for (int t = tid; t < 2 * E + (with_corners ? 4 : 0); t += NT) {
       T fv[9];
@@ -424,10 +432,11 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
         else tile_at(8, -1, E) = fv[8];
       }
     }
+    overlap((2 * E + (with_corners ? 4 : 0) + 31) / 32 * 32, 2);
     __syncthreads();
   };
   auto corners_alone = [&]() {
-    for (int i = tid; i < 4 * F * NCC; i += NT) reg[i] = T(0);
+    zero(reg, 4 * F * NCC);
     __syncthreads();
     for (int task = warp; task < 4 * F; task += NWARP) {
       const int c = task / F, f = task - c * F;
@@ -451,7 +460,7 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
       else if (c == 2) cone_inverse<P, L, 1, T>(rg + IL * NCN, 1, 0);
       else cone_inverse<P, L, P - 1, T>(rg + IL * NCN, 1, 0);
     }
-    overlap(((4 * F + 31) / 32) * 32);
+    overlap(((4 * F + 31) / 32) * 32, 2);
     __syncthreads();
     if (tid < 4) {
       const int c = tid;
@@ -623,6 +632,23 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     if constexpr (MODE == MODE_STEP) {
       if (tid == 0) misc[63] = int(status0);
     }
+    // Ring-free kernels read the eight neighbour records late in the step.
+    // Threads 32F .. 32F+8F-1 (idle in the decode) walk each neighbour's
+    // section header one dependent load per decode phase, so that no
+    // barrier waits on the chain: table entry now, the field's table row
+    // next phase, its band mask after that, the shared table last.
+    static_assert(!(MODE == MODE_STEP && RF) || NT >= 32 * F + 8 * F, "idle threads for the neighbour table");
+    const int tn = tid - 32 * F;
+    const bool nbt = MODE == MODE_STEP && RF && tn >= 0 && tn < 8 * F;
+    unsigned long long nb_ent = 0ull;
+    uint4 nb_fe = make_uint4(0u, 0u, 0u, 0u);
+    unsigned int nb_b0 = 0u, nb_b1 = 0u;
+    if (nbt) {
+      const int n = tn / F;  // 0 SW, 1 S, 2 SE, 3 W, 4 E, 5 NW, 6 N, 7 NE
+      const int dx = n < 3 ? n - 1 : (n < 5 ? (n == 3 ? -1 : 1) : n - 6);
+      const int dy = n < 3 ? -1 : (n < 5 ? 0 : 1);
+      nb_ent = a.tab_in[((py + dy + a.npy) % a.npy) * a.npx + (px + dx + a.npx) % a.npx];
+    }
     __syncthreads();
     if constexpr (MODE == MODE_STEP) {
       if (misc[63] & int(STAT_ARENA_FULL | STAT_NAN | STAT_BAD_RECORD)) return;
@@ -643,6 +669,12 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       constexpr int NZ = int(size_t(F) * TS * sizeof(T) / 16), NREM = int(size_t(F) * TS - NZ * 16 / sizeof(T));
       for (int i = tid; i < NZ; i += NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
       if (tid < NREM) tiles[size_t(F) * TS - NREM + tid] = T(0);
+    }
+    if (nbt) {  // neighbour tn / F: start pulling its record into L2, read field tn % F's table row
+      const unsigned int nb = unsigned(nb_ent & 0xffffffull);
+      if (tn % F == 0 && nb >= 16u)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.arena_in + (nb_ent >> 24)), "r"(nb & ~15u) : "memory");
+      nb_fe = *reinterpret_cast<const uint4*>(a.arena_in + (nb_ent >> 24) + 16 + 16 * (tn % F));  // offset, words, edges, ints
     }
     if (tid < F) {
       const int f = tid;
@@ -673,36 +705,11 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       const int iy = c / C::NC1, ix = c - iy * C::NC1;
       tiles[win_in(f) + (iy << L) * PW + (ix << L)] = ldr<T>(R + finfo[16 * f] + c * int(sizeof(T)));
     }
-    if constexpr (MODE == MODE_STEP && RF) {
-      // The eight neighbour records are read late in the step (ring-free
-      // ghosts).  Warps F.. are idle in this phase: they start pulling those
-      // records into L2 and fill the table of their section headers.
-      static_assert(NT >= 32 * F + 8 * F, "idle warps for the neighbour table");
-      const int tn = tid - 32 * F;
-      if (tn >= 0 && tn < 8 * F) {
-        const int n = tn / F, f = tn - n * F;  // n: 0 SW, 1 S, 2 SE, 3 W, 4 E, 5 NW, 6 N, 7 NE
-        const int dx = n < 3 ? n - 1 : (n < 5 ? (n == 3 ? -1 : 1) : n - 6);
-        const int dy = n < 3 ? -1 : (n < 5 ? 0 : 1);
-        const int q = ((py + dy + a.npy) % a.npy) * a.npx + (px + dx + a.npx) % a.npx;
-        const unsigned long long ent = a.tab_in[q], roff = ent >> 24;
-        const unsigned int nb = unsigned(ent & 0xffffffull);
-        if (f == 0 && nb >= 16u)
-          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.arena_in + roff), "r"(nb & ~15u) : "memory");
-        const uint4 fe = *reinterpret_cast<const uint4*>(a.arena_in + roff + 16 + 16 * f);  // offset, words, edges, ints
-        unsigned int b0 = 0u, b1 = 0u;
-        if constexpr (C::QUANT) {  // the band mask is only 4-byte aligned (it follows NC coarse values)
-          const unsigned int* bmp = reinterpret_cast<const unsigned int*>(a.arena_in + roff + fe.x + NC * int(sizeof(T)));
-          b0 = bmp[0];
-          b1 = bmp[1];
-        }
-        int* e = reinterpret_cast<int*>(smem + C::OFF_NBI) + 8 * tn;
-        e[0] = int(roff & 0xffffffffull);
-        e[1] = int(roff >> 32);
-        e[2] = int(fe.x);
-        e[3] = int(fe.y);
-        e[4] = int(fe.z);
-        e[5] = int(b0);
-        e[6] = int(b1);
+    if constexpr (C::QUANT) {
+      if (nbt) {  // the band mask is only 4-byte aligned (it follows NC coarse values)
+        const unsigned int* bmp = reinterpret_cast<const unsigned int*>(a.arena_in + (nb_ent >> 24) + nb_fe.x + NC * int(sizeof(T)));
+        nb_b0 = bmp[0];
+        nb_b1 = bmp[1];
       }
     }
     // present mask words: word index, survivor prefix counts (warp per field)
@@ -734,7 +741,8 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
           vi = __popc(word & ~em_mine);
           emw_sm[f * NW + j] = em_mine;
         }
-        const unsigned ie = warp_incl_scan(ve), ii = warp_incl_scan(vi);
+        const unsigned sc = warp_incl_scan(ve | (vi << 16));  // both counts (<= 1024 each)
+        const unsigned ie = sc & 0xffffu, ii = sc >> 16;
         if (j < nwords) {
           plist[f * NW + j] = (unsigned short)w;
           mw[f * NW + j] = word;
@@ -746,6 +754,16 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       }
     }
     __syncthreads();
+    if (nbt) {
+      int* e = reinterpret_cast<int*>(smem + C::OFF_NBI) + 8 * tn;
+      e[0] = int(nb_ent >> 24 & 0xffffffffull);
+      e[1] = int(nb_ent >> 56);
+      e[2] = int(nb_fe.x);
+      e[3] = int(nb_fe.y);
+      e[4] = int(nb_fe.z);
+      e[5] = int(nb_b0);
+      e[6] = int(nb_b1);
+    }
     // survivors: one warp per non-zero mask word, one lane per node
     for (int f = 0; f < F; ++f) {
       const int* fi = finfo + 16 * f;
@@ -909,10 +927,13 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   float cf2[L + 1], cfm[L + 1];  // the column warp's lane (its field): group (cy, y)
 #pragma unroll
   for (int c = 0; c <= L; ++c) { cf2[c] = 0.0f; cfm[c] = 0.0f; }
+  // Ring-free kernels read back only the kept and the coarse coefficients
+  // (no re-decode), so the zeroed details are not written to the tiles.
+  constexpr bool STORE_ALL = !C::RINGFREE;
   if (warp < F * C::WR) {
     const int f = warp / C::WR, h = warp - f * C::WR;
     const int x = 32 * h + lane;
-    const bool valid = x < P;
+    const bool valid = (P % 32 == 0) || x < P;
     const int cx = cls_x[h];
     T* col = tiles + win_out(f) + (valid ? x : 0);
     const T* te = tau_e + cx * (L + 1);
@@ -920,9 +941,13 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     T thr[L + 1];  // this lane's threshold per y class (rows y = 0, P use te)
 #pragma unroll
     for (int c = 0; c <= L; ++c) thr[c] = xedge ? te[c] : tau_i[cx * (L + 1) + c];
-    unsigned int myw[(E + 31) / 32];
+    // largest kept |detail| of band (cx, cy) in this lane (-1: none); one
+    // shared-memory atomic per band after the pass
+    float mk[L + 1];
 #pragma unroll
-    for (int k = 0; k < (E + 31) / 32; ++k) myw[k] = 0u;
+    for (int c = 0; c <= L; ++c) mk[c] = -1.0f;
+    T nanacc = T(0);  // v * 0 summed: NaN iff some coefficient is not finite
+    unsigned int* mwf = mw + f * NW + h;
     // FEAT, this lane: energy and max per row class cy (branch-free; lanes
     // past P hold zeros); the groups are formed once after the pass
     float acc2[L + 1], accm[L + 1];
@@ -938,27 +963,26 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         acc2[cy] = acc2[cy] + d * d;
         accm[cy] = fmaxf(accm[cy], fabsf(d));
       }
+      nanacc = fma_rn(v[y], T(0), nanacc);
       bool keep = false;
-      if (valid && (cx | cy)) {
+      if (cx | cy) {
         const bool yedge = WV == WV_BL53 && (y == 0 || y == P);  // folds: y is a constant here
-        keep = fabs(v[y]) >= (yedge ? te[cy] : thr[cy]);
-        if (!isfinite(v[y])) bad = true;
+        keep = valid && fabs(v[y]) >= (yedge ? te[cy] : thr[cy]);
         if constexpr (C::QUANT) {
-          if (keep && !(yedge || xedge)) atomicMax(bmax + f * NB + cx * (L + 1) + cy, __float_as_uint(fabsf(float(v[y]))) + 1u);
+          if (!yedge) mk[cy] = (keep && !xedge) ? fmaxf(mk[cy], fabsf(float(v[y]))) : mk[cy];
         }
         if (!keep) v[y] = T(0);
-      } else if (valid && !isfinite(v[y])) {
-        bad = true;
       }
       const unsigned int bal = __ballot_sync(0xffffffffu, keep);
-      if (lane == (y & 31)) myw[y >> 5] = bal;
-      if (valid) col[y * PW] = v[y];
+      if (lane == 0) mwf[y * C::WR] = bal;
+      if (valid && (STORE_ALL || keep || (cx | cy) == 0)) col[y * PW] = v[y];
     };
     fwd_levels_cb<WV, P, 1, L, T>(v, node);
+    if (nanacc != nanacc) bad = true;
+    if constexpr (C::QUANT) {
 #pragma unroll
-    for (int k = 0; k < (E + 31) / 32; ++k) {
-      const int y = 32 * k + lane;
-      if (y < E) mw[f * NW + y * C::WR + h] = myw[k];
+      for (int c = 0; c <= L; ++c)
+        if (mk[c] >= 0.0f) atomicMax(bmax + f * NB + cx * (L + 1) + c, __float_as_uint(mk[c]) + 1u);
     }
     if constexpr (FEAT) {  // warp sums per group, fixed shuffle order
       // group (l, x): cx == l, rows cy < l; (l, y): cx < l, rows cy == l;
@@ -994,6 +1018,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     T v[E];
 #pragma unroll
     for (int y = 0; y < E; ++y) v[y] = col[y * PW];
+    T nanacc = T(0);
     auto node = [&](int y) {
       const int cy = node_class<L>(y);
       if constexpr (FEAT) {
@@ -1003,14 +1028,17 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
           cfm[cy] = fmaxf(cfm[cy], fabsf(d));
         }
       }
-      if (!isfinite(v[y])) bad = true;
+      nanacc = fma_rn(v[y], T(0), nanacc);
+      bool keep = true;
       if (cy) {  // x = P is a coarse x-node; every node of the column is on an edge line
-        if (fabs(v[y]) >= tau_e[cy]) cw[y >> 5] |= 1u << (y & 31);
+        keep = fabs(v[y]) >= tau_e[cy];
+        if (keep) cw[y >> 5] |= 1u << (y & 31);
         else v[y] = T(0);
       }
-      col[y * PW] = v[y];
+      if (STORE_ALL || keep) col[y * PW] = v[y];
     };
     fwd_levels_cb<WV, P, 1, L, T>(v, node);
+    if (nanacc != nanacc) bad = true;
 #pragma unroll
     for (int k = 0; k < C::NCW; ++k) mw[f * NW + C::NRW + k] = cw[k];
   }
@@ -1119,22 +1147,38 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   // per-field scans, list of non-zero words, band scales, section sizes
   if (warp < F) {
     const int f = warp;
-    unsigned ce = 0, ci = 0, cw = 0;
-    for (int b0 = 0; b0 < NW; b0 += 32) {
-      const int w = b0 + lane;
-      const unsigned int word = w < NW ? mw[f * NW + w] : 0u;
-      const unsigned int emw = w < NW ? word_edges<WV, P, E, C::WR>(w) : 0u;
-      const unsigned ve = __popc(word & emw), vi = __popc(word & ~emw), vw = word ? 1u : 0u;
-      const unsigned ie = warp_incl_scan(ve), ii = warp_incl_scan(vi), iw = warp_incl_scan(vw);
-      if (w < NW) {
-        pre_e[f * NW + w] = (unsigned short)(ce + ie - ve);
-        pre_i[f * NW + w] = (unsigned short)(ci + ii - vi);
-        if (word) plist[f * NW + cw + iw - 1] = (unsigned short)w;
-      }
-      ce += __shfl_sync(0xffffffffu, ie, 31);
-      ci += __shfl_sync(0xffffffffu, ii, 31);
-      cw += __shfl_sync(0xffffffffu, iw, 31);
+    // lane l takes the PWL consecutive words from l * PWL: one scan of the
+    // lane totals (edge survivors <= 4E, interior <= E^2, words <= NW; packed
+    // in 9 + 13 + 10 bits), then running sums over the lane's own words
+    constexpr int PWL = (NW + 31) / 32;
+    static_assert(4 * E < 512 && E * E < 8192 && NW < 1024, "scan fields overflow");
+    unsigned int wd[PWL], we[PWL];
+    unsigned le = 0, li = 0, lw = 0;
+#pragma unroll
+    for (int k = 0; k < PWL; ++k) {
+      const int w = lane * PWL + k;
+      wd[k] = w < NW ? mw[f * NW + w] : 0u;
+      we[k] = w < NW ? word_edges<WV, P, E, C::WR>(w) : 0u;
+      le += __popc(wd[k] & we[k]);
+      li += __popc(wd[k] & ~we[k]);
+      lw += wd[k] ? 1u : 0u;
     }
+    const unsigned sc = warp_incl_scan(le | (li << 9) | (lw << 22));
+    unsigned re = (sc & 0x1ffu) - le, ri = ((sc >> 9) & 0x1fffu) - li, rw = (sc >> 22) - lw;
+#pragma unroll
+    for (int k = 0; k < PWL; ++k) {
+      const int w = lane * PWL + k;
+      if (w < NW) {
+        pre_e[f * NW + w] = (unsigned short)re;
+        pre_i[f * NW + w] = (unsigned short)ri;
+        if (wd[k]) plist[f * NW + rw] = (unsigned short)w;
+      }
+      re += __popc(wd[k] & we[k]);
+      ri += __popc(wd[k] & ~we[k]);
+      rw += wd[k] ? 1u : 0u;
+    }
+    const unsigned tot = __shfl_sync(0xffffffffu, sc, 31);
+    const unsigned ce = tot & 0x1ffu, ci = (tot >> 9) & 0x1fffu, cw = tot >> 22;
     unsigned long long bm = 0ull;
     if constexpr (C::QUANT) {
       for (int b0 = 0; b0 < NB; b0 += 32) {
@@ -1173,6 +1217,44 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       fi[8] = int((unsigned int)(bm >> 32));
     }
   }
+  // FP64 coarse-block sums: 2^(2L) times the trapezoid sum of the coarse
+  // samples is the patch mass of the field (details carry no mass).  Fixed
+  // order: coarse sample c goes to slot c mod 32 (in order of c), then the
+  // slots are added pairwise, slot i += slot i + o for o = 16, 8, 4, 2, 1.
+  // Four warps that are idle in this phase do it for all fields side by
+  // side, so that the few FP64 instructions carry full warps.
+  constexpr int SUMW = 4;
+  constexpr size_t OFF_DSUM = (4096 + size_t(MLP_NP) * 4 + 15) / 16 * 16;  // behind the FEAT data
+  static_assert(F + SUMW < NWARP, "no idle warps for the coarse sums");
+  static_assert(OFF_DSUM + size_t(F) * 32 * 8 <= C::STG, "coarse-sum slots do not fit in the staging area");
+  if (warp >= F && warp < F + SUMW) {
+    double* ds = reinterpret_cast<double*>(stage + OFF_DSUM);
+    const int t0 = tid - 32 * F;
+    for (int t = t0; t < F * 32; t += 32 * SUMW) {
+      const int f = t >> 5;
+      double acc = 0.0;
+      for (int c = t & 31; c < NC; c += 32) {
+        const int iy = c / C::NC1, ix = c - iy * C::NC1;
+        double w = 1.0;
+        if constexpr (WV == WV_BL53) {
+          const bool ex = ix == 0 || ix == C::NC1 - 1, ey = iy == 0 || iy == C::NC1 - 1;
+          w = ex && ey ? 0.25 : (ex || ey ? 0.5 : 1.0);
+        }
+        acc = acc + w * double(tiles[win_out(f) + (iy << L) * PW + (ix << L)]);
+      }
+      ds[t] = acc;
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * SUMW) : "memory");
+      for (int t = t0; t < F * o; t += 32 * SUMW) {
+        const int f = t / o, i = t - f * o;
+        ds[f * 32 + i] = ds[f * 32 + i] + ds[f * 32 + i + o];
+      }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * SUMW) : "memory");
+    if (t0 < F) a.pstats[size_t(pid) * F + t0] = ds[t0 * 32] * double(1ll << (2 * L));
+  }
   __syncthreads();
   if (tid == 0) {
     int off = (16 + 16 * F + 15) & ~15;
@@ -1199,26 +1281,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   unsigned char* O = a.arena_out + ((unsigned long long)(unsigned int)misc[2] | ((unsigned long long)(unsigned int)misc[3] << 32));
 
   // ----------------------------- encode pass 2: the record, survivors only
-  // FP64 coarse-block sums: 2^(2L) times the trapezoid sum of the coarse
-  // samples is the patch mass of the field (details carry no mass).  One warp
-  // per field (the last warps, lightly loaded here): coarse sample c goes to
-  // lane c mod 32, then a shuffle tree.  Coarse nodes are read-only in pass 2.
-  if (warp >= NWARP - F) {
-    const int f = warp - (NWARP - F);
-    double acc = 0.0;
-    for (int c = lane; c < NC; c += 32) {
-      const int iy = c / C::NC1, ix = c - iy * C::NC1;
-      double w = 1.0;
-      if constexpr (WV == WV_BL53) {
-        if (ix == 0 || ix == C::NC1 - 1) w *= 0.5;
-        if (iy == 0 || iy == C::NC1 - 1) w *= 0.5;
-      }
-      acc = acc + w * double(tiles[win_out(f) + (iy << L) * PW + (ix << L)]);
-    }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) acc = acc + __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) a.pstats[size_t(pid) * F + f] = acc * double(1ll << (2 * L));
-  }
   if (tid == 0) stg<uint4>(O, make_uint4((unsigned)misc[1], (unsigned)pid, (unsigned)F, a.flags));
   if (tid < F) {
     const int* fi = finfo + 16 * tid;
@@ -1305,11 +1367,10 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       }
     }
   }
-  __syncthreads();
-
   // --------------------------- re-decode: the state the neighbours will see
   // (ring-free kernels: the neighbours decode it themselves next step)
   if constexpr (RF) return;
+  __syncthreads();
   for (int t = tid; t < F * E; t += NT) {
     const int f = t / E, x = t - f * E;
     line_transform<WV, P, L, true, T>(tiles + win_out(f) + x, PW);
