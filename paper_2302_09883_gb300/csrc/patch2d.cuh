@@ -168,6 +168,22 @@ template <int P, int L, int TT, typename T> __device__ __forceinline__ void cone
   rg[ST * stride + off] = v[TT - LO];
 }
 
+// BGK collision (D2Q9) in place of the own nodes t = t0, t0 + dt, ... below
+// t1 (node t = y E + x; window offsets woff).  Out of line: several stages
+// call it, and one copy of its code serves them all.
+template <typename T, int E, int PW>
+__device__ __noinline__ void collide_nodes(T* tiles, const int* woff, int t0, int t1, int dt, T omega) {
+  for (int t = t0; t < t1; t += dt) {
+    const int y = t / E, x = t - y * E;
+    T fv[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fv[i] = tiles[woff[i] + y * PW + x];
+    d2q9_collide<T>(fv, omega);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) tiles[woff[i] + y * PW + x] = fv[i];
+  }
+}
+
 // Ghosts without a ring (D2Q9, folded BL5/3).  A ghost is the neighbour's
 // decoded value of the current state (its post-collision population that
 // streams in), so it is computed here from the neighbour's record: only the
@@ -177,6 +193,141 @@ template <int P, int L, int TT, typename T> __device__ __forceinline__ void cone
 // transformed in full, the direction across it by the restricted inverse,
 // bit-identical to a full decode.  Three rounds through the record staging
 // area: west and east, south and north, the four corners.
+// Decode the coefficients of field f of neighbour n (0 SW, 1 S, 2 SE, 3 W,
+// 4 E, 5 NW, 6 N, 7 NE; section headers from the table nbi) that lie in a
+// region into rg (zeroed before): kind 0: columns of MX, all rows
+// (rg[ix E + y]); kind 1: rows of MY, all columns (rg[iy E + x]); kind 2:
+// both (rg[iy NCN + ix]).  One warp: present words with their survivor
+// ranks 32 at a time, then their surviving nodes one word at a time.  Out of
+// line: three stages call it.
+template <int WV, typename T, int ST, int P, int L>
+__device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, const int* nbi, int n, int f, T* rg, int kind,
+                                              ConeMask MX, ConeMask MY) {
+  typedef Cfg<SCH_D2Q9, WV, T, ST, P, L> C;
+  typedef typename C::S S;
+  constexpr int F = 9, E = C::E, NC = C::NC, NPW = C::NPW;
+  constexpr int NCN = cone_count(cone_mask<P, L>(P - 1));
+  const int lane = threadIdx.x & 31;
+    const int* e = nbi + 8 * (n * F + f);
+  const unsigned char* R =
+      arena_in + ((unsigned long long)(unsigned int)e[0] | ((unsigned long long)(unsigned int)e[1] << 32));
+  const int off = e[2], nwords = e[3], nedge = e[4];
+  int p = off + NC * int(sizeof(T));
+  unsigned long long bm = 0ull;
+  if constexpr (C::QUANT) {
+    bm = (unsigned long long)(unsigned int)e[5] | ((unsigned long long)(unsigned int)e[6] << 32);
+    p += 8 + 4 * __popcll(bm);
+  }
+  const int p_pres = p, p_words = p + 4 * NPW;
+  const int p_edge = (p_words + 4 * nwords + 7) & ~7, p_int = p_edge + nedge * int(sizeof(T));
+  static_assert(NPW <= 32, "presence words fit in one warp");
+  const unsigned int presl = lane < NPW ? ldr<unsigned int>(R + p_pres + 4 * lane) : 0u;  // lane k: word k
+  auto inside = [&](int kx, int ky) -> bool {
+    return kind == 0 ? cone_has(MX, kx) : (kind == 1 ? cone_has(MY, ky) : (cone_has(MX, kx) && cone_has(MY, ky)));
+  };
+  auto slot = [&](int kx, int ky) -> int {
+    return kind == 0 ? cone_index(MX, kx) * E + ky
+                     : (kind == 1 ? cone_index(MY, ky) * E + kx : cone_index(MY, ky) * NCN + cone_index(MX, kx));
+  };
+  for (int c = lane; c < NC; c += 32) {
+    const int iy = c / C::NC1, ix = c - iy * C::NC1;
+    if (inside(ix << L, iy << L)) rg[slot(ix << L, iy << L)] = ldr<T>(R + off + c * int(sizeof(T)));
+  }
+  unsigned ce = 0u, ci = 0u;
+  for (int j0 = 0; j0 < nwords; j0 += 32) {
+    const int j = j0 + lane;
+    int w = 0;
+    unsigned int word = 0u;
+    {
+      int r = j;
+      bool found = false;
+#pragma unroll
+      for (int k = 0; k < NPW; ++k) {
+        const unsigned int pres = __shfl_sync(0xffffffffu, presl, k);
+        const int cnt = __popc(pres);
+        if (!found && r < cnt) {
+          w = 32 * k + __fns(pres, 0, r + 1);
+          found = true;
+        }
+        if (!found) r -= cnt;
+      }
+      if (j < nwords) word = ldr<unsigned int>(R + p_words + 4 * j);
+      else w = 0;
+    }
+    const unsigned int em = word_edges<WV, P, E, C::WR>(w);
+    const unsigned ve = __popc(word & em), vi = __popc(word & ~em);
+    // both survivor counts in one scan (each lane <= 32, sums <= 1024)
+    const unsigned sc = warp_incl_scan(ve | (vi << 16));
+    const unsigned ie = sc & 0xffffu, ii = sc >> 16;
+    const unsigned be = ce + ie - ve, bi = ci + ii - vi;
+    ce += __shfl_sync(0xffffffffu, ie, 31);
+    ci += __shfl_sync(0xffffffffu, ii, 31);
+    // words with a surviving node in the region (row words: one row y0,
+    // columns x0 + bit; face words: column P, rows y0 + bit)
+    bool hit = word != 0u;
+    if (hit) {
+      const bool rowword = w < C::NRW;
+      const int y0 = rowword ? w / C::WR : 32 * (w - C::NRW);
+      const int x0 = rowword ? 32 * (w - y0 * C::WR) : P;
+      const bool hx = rowword ? (word & cone_bits32(MX, x0)) != 0u : cone_has(MX, P);
+      const bool hy = rowword ? cone_has(MY, y0) : (word & cone_bits32(MY, y0)) != 0u;
+      hit = kind == 0 ? hx : (kind == 1 ? hy : (hx && hy));
+    }
+    unsigned int todo = __ballot_sync(0xffffffffu, hit);
+    while (todo) {
+      const int k = __ffs(todo) - 1;
+      todo &= todo - 1u;
+      const unsigned int wk = __shfl_sync(0xffffffffu, word, k), emk = __shfl_sync(0xffffffffu, em, k);
+      const unsigned bek = __shfl_sync(0xffffffffu, be, k), bik = __shfl_sync(0xffffffffu, bi, k);
+      const int ww = __shfl_sync(0xffffffffu, w, k);
+      if (!((wk >> lane) & 1u)) continue;
+      int kx, ky;
+      bool valid;
+      word_node<P, E, C::WR>(ww, lane, kx, ky, valid);
+      if (!valid || !inside(kx, ky)) continue;
+      const unsigned int lt = (1u << lane) - 1u;
+      T v;
+      if ((emk >> lane) & 1u) {
+        v = ldr<T>(R + p_edge + int(bek + __popc(wk & emk & lt)) * int(sizeof(T)));
+      } else {
+        const S qv = ldr<S>(R + p_int + int(bik + __popc(wk & ~emk & lt)) * C::SB);
+        if constexpr (ST == ST_F64 || ST == ST_F32) {
+          v = T(qv);
+        } else {
+          const int b = node_class<L>(kx) * (L + 1) + node_class<L>(ky);
+          const float sc = ldr<float>(R + off + NC * int(sizeof(T)) + 8 + 4 * __popcll(bm & ((1ull << b) - 1ull)));
+          if constexpr (ST == ST_BF16) v = T(__uint_as_float((unsigned int)qv << 16) * sc);
+          else v = T(float(qv) * sc);
+        }
+      }
+      rg[slot(kx, ky)] = v;
+    }
+  }
+  }
+
+// BGK collision of one ghost node whose nine populations sit at
+// src[i * stride]; population p_k goes to tiles[d_k] (k < nout).  Out of
+// line: the ghost stages call it from two places.
+template <typename T>
+__device__ __noinline__ void ghost_collide(const T* src, int stride, T omega, T* tiles, int nout, int p0, int d0, int p1,
+                                           int d1, int p2, int d2) {
+  T fv[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fv[i] = src[i * stride];
+  d2q9_collide<T>(fv, omega);
+  auto pick = [&](int p) {
+    T r = fv[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) r = p == i ? fv[i] : r;
+    return r;
+  };
+  tiles[d0] = pick(p0);
+  if (nout > 1) {
+    tiles[d1] = pick(p1);
+    tiles[d2] = pick(p2);
+  }
+}
+
 template <int WV, typename T, int ST, int P, int L, typename Coll>
 __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, unsigned char* cmask, const int* nbi,
                                T omega, Coll& collide) {
@@ -191,109 +342,8 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   constexpr int IH = cone_index_c(CH, P - 1), IL = cone_index_c(CL, 1);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   (void)pid;
-  // Decode the coefficients of field f of neighbour n (0 SW, 1 S, 2 SE, 3 W,
-  // 4 E, 5 NW, 6 N, 7 NE; section headers from the table nbi) that lie in a
-  // region into
-  // rg (zeroed before): kind 0: columns of MX, all rows (rg[ix E + y]);
-  // kind 1: rows of MY, all columns (rg[iy E + x]); kind 2: both
-  // (rg[iy NCN + ix]).  One warp: present words with their survivor ranks
-  // 32 at a time, then their surviving nodes one word at a time.
   auto scatter = [&](int n, int f, T* rg, int kind, ConeMask MX, ConeMask MY) {
-    const int* e = nbi + 8 * (n * F + f);
-    const unsigned char* R =
-        a.arena_in + ((unsigned long long)(unsigned int)e[0] | ((unsigned long long)(unsigned int)e[1] << 32));
-    const int off = e[2], nwords = e[3], nedge = e[4];
-    int p = off + NC * int(sizeof(T));
-    unsigned long long bm = 0ull;
-    if constexpr (C::QUANT) {
-      bm = (unsigned long long)(unsigned int)e[5] | ((unsigned long long)(unsigned int)e[6] << 32);
-      p += 8 + 4 * __popcll(bm);
-    }
-    const int p_pres = p, p_words = p + 4 * NPW;
-    const int p_edge = (p_words + 4 * nwords + 7) & ~7, p_int = p_edge + nedge * int(sizeof(T));
-    static_assert(NPW <= 32, "presence words fit in one warp");
-    const unsigned int presl = lane < NPW ? ldr<unsigned int>(R + p_pres + 4 * lane) : 0u;  // lane k: word k
-    auto inside = [&](int kx, int ky) -> bool {
-      return kind == 0 ? cone_has(MX, kx) : (kind == 1 ? cone_has(MY, ky) : (cone_has(MX, kx) && cone_has(MY, ky)));
-    };
-    auto slot = [&](int kx, int ky) -> int {
-      return kind == 0 ? cone_index(MX, kx) * E + ky
-                       : (kind == 1 ? cone_index(MY, ky) * E + kx : cone_index(MY, ky) * NCN + cone_index(MX, kx));
-    };
-    for (int c = lane; c < NC; c += 32) {
-      const int iy = c / C::NC1, ix = c - iy * C::NC1;
-      if (inside(ix << L, iy << L)) rg[slot(ix << L, iy << L)] = ldr<T>(R + off + c * int(sizeof(T)));
-    }
-    unsigned ce = 0u, ci = 0u;
-    for (int j0 = 0; j0 < nwords; j0 += 32) {
-      const int j = j0 + lane;
-      int w = 0;
-      unsigned int word = 0u;
-      {
-        int r = j;
-        bool found = false;
-#pragma unroll
-        for (int k = 0; k < NPW; ++k) {
-          const unsigned int pres = __shfl_sync(0xffffffffu, presl, k);
-          const int cnt = __popc(pres);
-          if (!found && r < cnt) {
-            w = 32 * k + __fns(pres, 0, r + 1);
-            found = true;
-          }
-          if (!found) r -= cnt;
-        }
-        if (j < nwords) word = ldr<unsigned int>(R + p_words + 4 * j);
-        else w = 0;
-      }
-      const unsigned int em = word_edges<WV, P, E, C::WR>(w);
-      const unsigned ve = __popc(word & em), vi = __popc(word & ~em);
-      // both survivor counts in one scan (each lane <= 32, sums <= 1024)
-      const unsigned sc = warp_incl_scan(ve | (vi << 16));
-      const unsigned ie = sc & 0xffffu, ii = sc >> 16;
-      const unsigned be = ce + ie - ve, bi = ci + ii - vi;
-      ce += __shfl_sync(0xffffffffu, ie, 31);
-      ci += __shfl_sync(0xffffffffu, ii, 31);
-      // words with a surviving node in the region (row words: one row y0,
-      // columns x0 + bit; face words: column P, rows y0 + bit)
-      bool hit = word != 0u;
-      if (hit) {
-        const bool rowword = w < C::NRW;
-        const int y0 = rowword ? w / C::WR : 32 * (w - C::NRW);
-        const int x0 = rowword ? 32 * (w - y0 * C::WR) : P;
-        const bool hx = rowword ? (word & cone_bits32(MX, x0)) != 0u : cone_has(MX, P);
-        const bool hy = rowword ? cone_has(MY, y0) : (word & cone_bits32(MY, y0)) != 0u;
-        hit = kind == 0 ? hx : (kind == 1 ? hy : (hx && hy));
-      }
-      unsigned int todo = __ballot_sync(0xffffffffu, hit);
-      while (todo) {
-        const int k = __ffs(todo) - 1;
-        todo &= todo - 1u;
-        const unsigned int wk = __shfl_sync(0xffffffffu, word, k), emk = __shfl_sync(0xffffffffu, em, k);
-        const unsigned bek = __shfl_sync(0xffffffffu, be, k), bik = __shfl_sync(0xffffffffu, bi, k);
-        const int ww = __shfl_sync(0xffffffffu, w, k);
-        if (!((wk >> lane) & 1u)) continue;
-        int kx, ky;
-        bool valid;
-        word_node<P, E, C::WR>(ww, lane, kx, ky, valid);
-        if (!valid || !inside(kx, ky)) continue;
-        const unsigned int lt = (1u << lane) - 1u;
-        T v;
-        if ((emk >> lane) & 1u) {
-          v = ldr<T>(R + p_edge + int(bek + __popc(wk & emk & lt)) * int(sizeof(T)));
-        } else {
-          const S qv = ldr<S>(R + p_int + int(bik + __popc(wk & ~emk & lt)) * C::SB);
-          if constexpr (ST == ST_F64 || ST == ST_F32) {
-            v = T(qv);
-          } else {
-            const int b = node_class<L>(kx) * (L + 1) + node_class<L>(ky);
-            const float sc = ldr<float>(R + off + NC * int(sizeof(T)) + 8 + 4 * __popcll(bm & ((1ull << b) - 1ull)));
-            if constexpr (ST == ST_BF16) v = T(__uint_as_float((unsigned int)qv << 16) * sc);
-            else v = T(float(qv) * sc);
-          }
-        }
-        rg[slot(kx, ky)] = v;
-      }
-    }
+    ringfree_scatter<WV, T, ST, P, L>(a.arena_in, nbi, n, f, rg, kind, MX, MY);
   };
   auto tile_at = [&](int i, int x, int y) -> T& { return tiles[i * TS + (y + 1) * PW + (x + 1)]; };
   // zero n values at p (16-byte aligned) with vector stores
@@ -308,8 +358,7 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   int done = 0;
   auto overlap = [&](int busy, int per) {
     const int idle = NT - busy, n = per * idle < E * E - done ? per * idle : E * E - done;
-    if (tid >= busy)
-      for (int k = tid - busy; k < n; k += idle) collide(done + k);
+    if (tid >= busy) collide(done + tid - busy, done + n, idle);
     done += n;
   };
 
@@ -331,21 +380,12 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
     cone_inverse<P, L, 1, T>(reg + (F + f) * NCN * E, E, y);
   }
   __syncthreads();
-  for (int t = tid; t < 2 * E; t += NT) {
+  for (int t = tid; t < 2 * E; t += NT) {  // west ghosts take populations 1, 5, 8, east ones 3, 6, 7
     const int sd = t / E, y = t - sd * E;
-    T fv[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fv[i] = reg[(sd * F + i) * NCN * E + (sd == 0 ? IH : IL) * E + y];
-    d2q9_collide<T>(fv, omega);
-    if (sd == 0) {
-      tile_at(1, -1, y) = fv[1];
-      tile_at(5, -1, y) = fv[5];
-      tile_at(8, -1, y) = fv[8];
-    } else {
-      tile_at(3, E, y) = fv[3];
-      tile_at(6, E, y) = fv[6];
-      tile_at(7, E, y) = fv[7];
-    }
+    const int row = (y + 1) * PW + (sd == 0 ? 0 : E + 1);
+    ghost_collide<T>(reg + sd * F * NCN * E + (sd == 0 ? IH : IL) * E + y, NCN * E, omega, tiles, 3,
+                     sd == 0 ? 1 : 3, (sd == 0 ? 1 : 3) * TS + row, sd == 0 ? 5 : 6, (sd == 0 ? 5 : 6) * TS + row,
+                     sd == 0 ? 8 : 7, (sd == 0 ? 8 : 7) * TS + row);
   }
   overlap((2 * E + 31) / 32 * 32, 1);
   __syncthreads();
@@ -405,31 +445,18 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
     overlap(with_corners ? ((32 + 4 * F + 31) / 32) * 32 : ((2 * F + 31) / 32) * 32, 2);
     __syncthreads();
     for (int t = tid; t < 2 * E + (with_corners ? 4 : 0); t += NT) {
-      T fv[9];
-      if (t < 2 * E) {
+      if (t < 2 * E) {  // south ghosts take populations 2, 5, 6, north ones 4, 7, 8
         const int sd = t / E, x = t - sd * E;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) fv[i] = reg[(sd * F + i) * NCN * E + (sd == 0 ? IH : IL) * E + x];
-        d2q9_collide<T>(fv, omega);
-        if (sd == 0) {
-          tile_at(2, x, -1) = fv[2];
-          tile_at(5, x, -1) = fv[5];
-          tile_at(6, x, -1) = fv[6];
-        } else {
-          tile_at(4, x, E) = fv[4];
-          tile_at(7, x, E) = fv[7];
-          tile_at(8, x, E) = fv[8];
-        }
-      } else {
+        const int col = (sd == 0 ? 0 : (E + 1) * PW) + x + 1;
+        ghost_collide<T>(reg + sd * F * NCN * E + (sd == 0 ? IH : IL) * E + x, NCN * E, omega, tiles, 3,
+                         sd == 0 ? 2 : 4, (sd == 0 ? 2 : 4) * TS + col, sd == 0 ? 5 : 7, (sd == 0 ? 5 : 7) * TS + col,
+                         sd == 0 ? 6 : 8, (sd == 0 ? 6 : 8) * TS + col);
+      } else {  // corners: SW 5 at (-1, -1), SE 6 at (E, -1), NE 7 at (E, E), NW 8 at (-1, E)
         const int c = t - 2 * E;
         const int iy = c <= 1 ? IH : IL, ix = (c == 0 || c == 3) ? IH : IL;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) fv[i] = regc[(c * F + i) * NCC + iy * NCN + ix];
-        d2q9_collide<T>(fv, omega);
-        if (c == 0) tile_at(5, -1, -1) = fv[5];
-        else if (c == 1) tile_at(6, E, -1) = fv[6];
-        else if (c == 2) tile_at(7, E, E) = fv[7];
-        else tile_at(8, -1, E) = fv[8];
+        const int cx = (c == 1 || c == 2) ? E + 1 : 0, cy = c >= 2 ? (E + 1) * PW : 0;
+        ghost_collide<T>(regc + c * F * NCC + iy * NCN + ix, NCC, omega, tiles, 1, 5 + c, (5 + c) * TS + cy + cx, 0, 0,
+                         0, 0);
       }
     }
     overlap((2 * E + (with_corners ? 4 : 0) + 31) / 32 * 32, 2);
@@ -827,27 +854,19 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
 
   // -------------------------------------------------------- ghosts + scheme
   if constexpr (MODE == MODE_STEP) {
-    // BGK collision of own node t, in place (D2Q9)
-    auto collide_node = [&](int t) {
-      const int y = t / E, x = t - y * E;
-      T fv[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) fv[i] = tiles[win_in(i) + y * PW + x];
-      d2q9_collide<T>(fv, omega);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) tiles[win_in(i) + y * PW + x] = fv[i];
-    };
+    // BGK collision of own nodes t0, t0 + dt, ... < t1, in place (D2Q9)
+    auto collide_range = [&](int t0, int t1, int dt) { collide_nodes<T, E, PW>(tiles, woff_in, t0, t1, dt, omega); };
     int collided = 0;
     if constexpr (RF) {
       collided = ringfree_ghosts<WV, T, ST, P, L>(a, pid, tiles, reinterpret_cast<T*>(stage), smem + C::OFF_MW,
-                                                  reinterpret_cast<const int*>(smem + C::OFF_NBI), omega, collide_node);
+                                                  reinterpret_cast<const int*>(smem + C::OFF_NBI), omega, collide_range);
     } else {
 #pragma unroll
       for (int g = 0; g < NG; ++g)
         if (gdst[g] >= 0) tiles[gdst[g]] = gsrc[g] >= 0 ? tiles[gsrc[g]] : gv[g];
     }
     if constexpr (SCH == SCH_D2Q9) {
-      for (int t = collided + tid; t < E * E; t += NT) collide_node(t);
+      collide_range(collided + tid, E * E, NT);
       __syncthreads();
     } else {
       __syncthreads();
