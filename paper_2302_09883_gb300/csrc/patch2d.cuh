@@ -169,18 +169,20 @@ template <int P, int L, int TT, typename T> __device__ __forceinline__ void cone
 }
 
 // BGK collision (D2Q9) in place of the own nodes t = t0, t0 + dt, ... below
-// t1 (node t = y E + x; window offsets woff).  Out of line: several stages
-// call it, and one copy of its code serves them all.
-template <typename T, int E, int PW>
-__device__ __noinline__ void collide_nodes(T* tiles, const int* woff, int t0, int t1, int dt, T omega) {
+// t1 (node t = y E + x of the input windows, population i at i TS + PW + 1).
+// Out of line: several stages call it, and one copy of its code serves them
+// all.
+template <typename T, int E, int PW, int TS>
+__device__ __noinline__ void collide_nodes(T* tiles, int t0, int t1, int dt, T omega) {
   for (int t = t0; t < t1; t += dt) {
     const int y = t / E, x = t - y * E;
+    T* q = tiles + (y + 1) * PW + x + 1;
     T fv[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fv[i] = tiles[woff[i] + y * PW + x];
+    for (int i = 0; i < 9; ++i) fv[i] = q[i * TS];
     d2q9_collide<T>(fv, omega);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) tiles[woff[i] + y * PW + x] = fv[i];
+    for (int i = 0; i < 9; ++i) q[i * TS] = fv[i];
   }
 }
 
@@ -198,8 +200,8 @@ __device__ __noinline__ void collide_nodes(T* tiles, const int* woff, int t0, in
 // region into rg (zeroed before): kind 0: columns of MX, all rows
 // (rg[ix E + y]); kind 1: rows of MY, all columns (rg[iy E + x]); kind 2:
 // both (rg[iy NCN + ix]).  One warp: present words with their survivor
-// ranks 32 at a time, then their surviving nodes one word at a time.  Out of
-// line: three stages call it.
+// ranks 32 at a time, then their surviving nodes one word at a time (the
+// coarse block: ringfree_coarse).  Out of line: three stages call it.
 template <int WV, typename T, int ST, int P, int L>
 __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, const int* nbi, int n, int f, T* rg, int kind,
                                               ConeMask MX, ConeMask MY) {
@@ -212,6 +214,7 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
   const unsigned char* R =
       arena_in + ((unsigned long long)(unsigned int)e[0] | ((unsigned long long)(unsigned int)e[1] << 32));
   const int off = e[2], nwords = e[3], nedge = e[4];
+  if (nwords == 0) return;  // only the coarse block (done by ringfree_coarse)
   int p = off + NC * int(sizeof(T));
   unsigned long long bm = 0ull;
   if constexpr (C::QUANT) {
@@ -229,10 +232,6 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
     return kind == 0 ? cone_index(MX, kx) * E + ky
                      : (kind == 1 ? cone_index(MY, ky) * E + kx : cone_index(MY, ky) * NCN + cone_index(MX, kx));
   };
-  for (int c = lane; c < NC; c += 32) {
-    const int iy = c / C::NC1, ix = c - iy * C::NC1;
-    if (inside(ix << L, iy << L)) rg[slot(ix << L, iy << L)] = ldr<T>(R + off + c * int(sizeof(T)));
-  }
   unsigned ce = 0u, ci = 0u;
   for (int j0 = 0; j0 < nwords; j0 += 32) {
     const int j = j0 + lane;
@@ -305,6 +304,26 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
   }
   }
 
+// Coarse value c of field f of neighbour n into region rg if its node lies
+// there (kind and masks as in ringfree_scatter).  One thread per value: a
+// stage issues all its coarse loads at once.
+template <int WV, typename T, int ST, int P, int L>
+__device__ __forceinline__ void ringfree_coarse(const unsigned char* arena_in, const int* nbi, int n, int f, T* rg,
+                                                int kind, ConeMask MX, ConeMask MY, int c) {
+  typedef Cfg<SCH_D2Q9, WV, T, ST, P, L> C;
+  constexpr int F = 9, E = C::E;
+  constexpr int NCN = cone_count(cone_mask<P, L>(P - 1));
+  const int iy = c / C::NC1, ix = c - iy * C::NC1, kx = ix << L, ky = iy << L;
+  const bool in = kind == 0 ? cone_has(MX, kx) : (kind == 1 ? cone_has(MY, ky) : (cone_has(MX, kx) && cone_has(MY, ky)));
+  if (!in) return;
+  const int* e = nbi + 8 * (n * F + f);
+  const unsigned char* R =
+      arena_in + ((unsigned long long)(unsigned int)e[0] | ((unsigned long long)(unsigned int)e[1] << 32));
+  const int sl = kind == 0 ? cone_index(MX, kx) * E + ky
+                           : (kind == 1 ? cone_index(MY, ky) * E + kx : cone_index(MY, ky) * NCN + cone_index(MX, kx));
+  rg[sl] = ldr<T>(R + e[2] + c * int(sizeof(T)));
+}
+
 // BGK collision of one ghost node whose nine populations sit at
 // src[i * stride]; population p_k goes to tiles[d_k] (k < nout).  Out of
 // line: the ghost stages call it from two places.
@@ -365,6 +384,11 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   // ---- west (its node P-1 of every row) and east (node 1) neighbours
   zero(reg, 2 * F * NCN * E);
   __syncthreads();
+  for (int i = tid; i < 2 * F * NC; i += NT) {  // coarse blocks: every load of the stage at once
+    const int task = i / NC, sd = task / F, f = task - sd * F;
+    ringfree_coarse<WV, T, ST, P, L>(a.arena_in, nbi, sd == 0 ? 3 : 4, f, reg + (sd * F + f) * NCN * E, 0, sd == 0 ? CH : CL,
+                                     CH, i - task * NC);
+  }
   for (int task = warp; task < 2 * F; task += NWARP) {
     const int sd = task / F, f = task - sd * F;
     scatter(sd == 0 ? 3 : 4, f, reg + (sd * F + f) * NCN * E, 0, sd == 0 ? CH : CL, CH);
@@ -406,6 +430,19 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
     if (with_corners) zero(regc, 4 * F * NCC);
     __syncthreads();
     const int ntask = with_corners ? 6 * F : 2 * F;
+    for (int i = tid; i < ntask * NC; i += NT) {  // coarse blocks: every load of the stage at once
+      const int task = i / NC, cc = i - task * NC;
+      if (task < 2 * F) {
+        const int sd = task / F, f = task - sd * F;
+        ringfree_coarse<WV, T, ST, P, L>(a.arena_in, nbi, sd == 0 ? 1 : 6, f, reg + (sd * F + f) * NCN * E, 1, CH,
+                                         sd == 0 ? CH : CL, cc);
+      } else {
+        const int c = (task - 2 * F) / F, f = task - 2 * F - c * F;
+        const int dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
+        ringfree_coarse<WV, T, ST, P, L>(a.arena_in, nbi, dy < 0 ? (dx < 0 ? 0 : 2) : (dx < 0 ? 5 : 7), f,
+                                         regc + (c * F + f) * NCC, 2, dx < 0 ? CH : CL, dy < 0 ? CH : CL, cc);
+      }
+    }
     for (int task = warp; task < ntask; task += NWARP) {
       if (task < 2 * F) {
         const int sd = task / F, f = task - sd * F;
@@ -465,6 +502,12 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   auto corners_alone = [&]() {
     zero(reg, 4 * F * NCC);
     __syncthreads();
+    for (int i = tid; i < 4 * F * NC; i += NT) {
+      const int task = i / NC, c = task / F, f = task - c * F;
+      const int dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
+      ringfree_coarse<WV, T, ST, P, L>(a.arena_in, nbi, dy < 0 ? (dx < 0 ? 0 : 2) : (dx < 0 ? 5 : 7), f,
+                                       reg + (c * F + f) * NCC, 2, dx < 0 ? CH : CL, dy < 0 ? CH : CL, i - task * NC);
+    }
     for (int task = warp; task < 4 * F; task += NWARP) {
       const int c = task / F, f = task - c * F;
       const int dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
@@ -855,7 +898,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   // -------------------------------------------------------- ghosts + scheme
   if constexpr (MODE == MODE_STEP) {
     // BGK collision of own nodes t0, t0 + dt, ... < t1, in place (D2Q9)
-    auto collide_range = [&](int t0, int t1, int dt) { collide_nodes<T, E, PW>(tiles, woff_in, t0, t1, dt, omega); };
+    auto collide_range = [&](int t0, int t1, int dt) { collide_nodes<T, E, PW, TS>(tiles, t0, t1, dt, omega); };
     int collided = 0;
     if constexpr (RF) {
       collided = ringfree_ghosts<WV, T, ST, P, L>(a, pid, tiles, reinterpret_cast<T*>(stage), smem + C::OFF_MW,
