@@ -703,18 +703,19 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       if (tid == 0) misc[63] = int(status0);
     }
     // Ring-free kernels read the eight neighbour records late in the step.
-    // Threads 32F .. 32F+8F-1 (idle in the decode) walk each neighbour's
-    // section header one dependent load per decode phase, so that no
-    // barrier waits on the chain: table entry now, the field's table row
-    // next phase, its band mask after that, the shared table last.
-    static_assert(!(MODE == MODE_STEP && RF) || NT >= 32 * F + 8 * F, "idle threads for the neighbour table");
-    const int tn = tid - 32 * F;
-    const bool nbt = MODE == MODE_STEP && RF && tn >= 0 && tn < 8 * F;
+    // Their section headers are a chain of dependent loads (table entry,
+    // field table row, band mask), and a block barrier waits for the loads
+    // its threads have in flight; so each link goes where a phase is long
+    // anyway: the table entries here (beside the record load), the table rows
+    // in the column pass, the band masks in the row pass, both by threads
+    // NBT0 .. NBT0 + 8F - 1, which those passes leave idle.
+    constexpr bool NBTAB = MODE == MODE_STEP && RF;
+    constexpr int NBT0 = NT - 96;
+    static_assert(!NBTAB || 8 * F <= 96, "threads for the neighbour table");
+    unsigned long long* nbent = reinterpret_cast<unsigned long long*>(misc + 16);  // [8]: 0 SW, 1 S, 2 SE, 3 W, 4 E, 5 NW, 6 N, 7 NE
     unsigned long long nb_ent = 0ull;
-    uint4 nb_fe = make_uint4(0u, 0u, 0u, 0u);
-    unsigned int nb_b0 = 0u, nb_b1 = 0u;
-    if (nbt) {
-      const int n = tn / F;  // 0 SW, 1 S, 2 SE, 3 W, 4 E, 5 NW, 6 N, 7 NE
+    if (NBTAB && tid >= NBT0 && tid < NBT0 + 8) {
+      const int n = tid - NBT0;
       const int dx = n < 3 ? n - 1 : (n < 5 ? (n == 3 ? -1 : 1) : n - 6);
       const int dy = n < 3 ? -1 : (n < 5 ? 0 : 1);
       nb_ent = a.tab_in[((py + dy + a.npy) % a.npy) * a.npx + (px + dx + a.npx) % a.npx];
@@ -740,11 +741,11 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       for (int i = tid; i < NZ; i += NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
       if (tid < NREM) tiles[size_t(F) * TS - NREM + tid] = T(0);
     }
-    if (nbt) {  // neighbour tn / F: start pulling its record into L2, read field tn % F's table row
+    if (NBTAB && tid >= NBT0 && tid < NBT0 + 8) {  // start pulling the neighbour's record into L2
+      nbent[tid - NBT0] = nb_ent;
       const unsigned int nb = unsigned(nb_ent & 0xffffffull);
-      if (tn % F == 0 && nb >= 16u)
+      if (nb >= 16u)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.arena_in + (nb_ent >> 24)), "r"(nb & ~15u) : "memory");
-      nb_fe = *reinterpret_cast<const uint4*>(a.arena_in + (nb_ent >> 24) + 16 + 16 * (tn % F));  // offset, words, edges, ints
     }
     if (tid < F) {
       const int f = tid;
@@ -774,13 +775,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       const int f = t / NC, c = t - f * NC;
       const int iy = c / C::NC1, ix = c - iy * C::NC1;
       tiles[win_in(f) + (iy << L) * PW + (ix << L)] = ldr<T>(R + finfo[16 * f] + c * int(sizeof(T)));
-    }
-    if constexpr (C::QUANT) {
-      if (nbt) {  // the band mask is only 4-byte aligned (it follows NC coarse values)
-        const unsigned int* bmp = reinterpret_cast<const unsigned int*>(a.arena_in + (nb_ent >> 24) + nb_fe.x + NC * int(sizeof(T)));
-        nb_b0 = bmp[0];
-        nb_b1 = bmp[1];
-      }
     }
     // present mask words: word index, survivor prefix counts (warp per field)
     if (warp < F) {
@@ -824,16 +818,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       }
     }
     __syncthreads();
-    if (nbt) {
-      int* e = reinterpret_cast<int*>(smem + C::OFF_NBI) + 8 * tn;
-      e[0] = int(nb_ent >> 24 & 0xffffffffull);
-      e[1] = int(nb_ent >> 56);
-      e[2] = int(nb_fe.x);
-      e[3] = int(nb_fe.y);
-      e[4] = int(nb_fe.z);
-      e[5] = int(nb_b0);
-      e[6] = int(nb_b1);
-    }
     // survivors: one warp per non-zero mask word, one lane per node
     for (int f = 0; f < F; ++f) {
       const int* fi = finfo + 16 * f;
@@ -866,12 +850,38 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       }
     }
     __syncthreads();
-    // inverse tensor lifting: y lines (columns) then x lines (rows)
+    // inverse tensor lifting: y lines (columns) then x lines (rows); the
+    // neighbour table rows and band masks come in meanwhile (see above)
+    int* nbi_w = reinterpret_cast<int*>(smem + C::OFF_NBI);  // per (neighbour, field): 8 ints
+    if (NBTAB && tid >= NBT0 && tid < NBT0 + 8 * F) {
+      const int tn = tid - NBT0, n = tn / F, f = tn - n * F;
+      const unsigned long long ent = nbent[n];
+      const uint4 fe = *reinterpret_cast<const uint4*>(a.arena_in + (ent >> 24) + 16 + 16 * f);  // offset, words, edges, ints
+      int* e = nbi_w + 8 * tn;
+      e[0] = int((ent >> 24) & 0xffffffffull);
+      e[1] = int(ent >> 56);
+      e[2] = int(fe.x);
+      e[3] = int(fe.y);
+      e[4] = int(fe.z);
+    }
     for (int t = tid; t < F * E; t += NT) {
       const int f = t / E, x = t - f * E;
       line_transform<WV, P, L, true, T>(tiles + win_in(f) + x, PW);
     }
     __syncthreads();
+    if (NBTAB && tid >= NBT0 && tid < NBT0 + 8 * F) {
+      int* e = nbi_w + 8 * (tid - NBT0);
+      unsigned int b0 = 0u, b1 = 0u;
+      if constexpr (C::QUANT) {  // the band mask is only 4-byte aligned (it follows NC coarse values)
+        const unsigned int* bmp = reinterpret_cast<const unsigned int*>(
+            a.arena_in + ((unsigned long long)(unsigned int)e[0] | ((unsigned long long)(unsigned int)e[1] << 32)) + e[2] +
+            NC * int(sizeof(T)));
+        b0 = bmp[0];
+        b1 = bmp[1];
+      }
+      e[5] = int(b0);
+      e[6] = int(b1);
+    }
     for (int t = tid; t < F * E; t += NT) {
       const int f = t / E, y = t - f * E;
       line_transform<WV, P, L, true, T>(tiles + win_in(f) + y * PW, 1);
