@@ -145,6 +145,28 @@ template <typename U> __device__ __forceinline__ void stg(unsigned char* p, U v)
 
 __device__ __forceinline__ unsigned long long dbl_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
+// Bits of word k of the rows y = 32k + b that are coarse (y a multiple of
+// 2^L).
+template <int L> __device__ __forceinline__ constexpr unsigned int coarse_rows(int k) {
+  unsigned int m = 0u;
+  for (int b = 0; b < 32; ++b)
+    if (((32 * k + b) & ((1 << L) - 1)) == 0) m |= 1u << b;
+  return m;
+}
+
+// Inverse lifting of one column (p[y * stride]) whose rows without bit y in
+// cm hold no stored coefficient: those read as zero and are not loaded.
+template <int WV, int P, int L, typename T>
+__device__ __forceinline__ void inverse_column_masked(T* p, int stride, const unsigned int* cm) {
+  constexpr int E = WV == WV_BL53 ? P + 1 : P;
+  T v[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) v[i] = ((cm[i >> 5] >> (i & 31)) & 1u) ? p[i * stride] : T(0);
+  inv_levels<WV, P, L, T>(v);
+#pragma unroll
+  for (int i = 0; i < E; ++i) p[i * stride] = v[i];
+}
+
 // Value of node TT after the inverse lifting across a cone held in
 // rg[cone_index(n) * stride + off] (TT's own slot receives the result).
 template <int P, int L, int TT> struct ConeSlots {  // slot of every window node (-1: not in the cone)
@@ -568,7 +590,12 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   unsigned short* pre_e = reinterpret_cast<unsigned short*>(smem + C::OFF_PRE);
   unsigned short* pre_i = pre_e + F * NW;
   unsigned short* plist = pre_i + F * NW;  // non-zero mask words, in order
-  unsigned int* emw_sm = reinterpret_cast<unsigned int*>(smem + C::OFF_EMW);  // edge bits per present word
+  // Decode: per (field, column x) the rows that hold a stored coefficient
+  // (CW words of bits); the tiles are not zeroed, the column pass reads only
+  // these rows and the coarse ones.  Lives where the band data goes later.
+  constexpr int CW = (E + 31) / 32;
+  unsigned int* colm = reinterpret_cast<unsigned int*>(smem + C::OFF_EMW);
+  static_assert(size_t(F) * E * CW * 4 <= C::OFF_FINFO - C::OFF_EMW, "column masks do not fit");
   unsigned int* bmax = reinterpret_cast<unsigned int*>(smem + C::OFF_BMAX);
   float* scl = reinterpret_cast<float*>(smem + C::OFF_SCL);
   float* sinv = reinterpret_cast<float*>(smem + C::OFF_SINV);
@@ -735,12 +762,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         a.ctl->smax[a.smax_rst] = 0ull;
       }
     }
-    {  // zero every tile: the details that were not stored are zeros
-      uint4* z = reinterpret_cast<uint4*>(tiles);
-      constexpr int NZ = int(size_t(F) * TS * sizeof(T) / 16), NREM = int(size_t(F) * TS - NZ * 16 / sizeof(T));
-      for (int i = tid; i < NZ; i += NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
-      if (tid < NREM) tiles[size_t(F) * TS - NREM + tid] = T(0);
-    }
+    for (int i = tid; i < F * E * CW; i += NT) colm[i] = 0u;  // no row of any column holds a detail yet
     if (NBTAB && tid >= NBT0 && tid < NBT0 + 8) {  // start pulling the neighbour's record into L2
       nbent[tid - NBT0] = nb_ent;
       const unsigned int nb = unsigned(nb_ent & 0xffffffull);
@@ -803,7 +825,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         if (j < nwords) {
           ve = __popc(word & em_mine);
           vi = __popc(word & ~em_mine);
-          emw_sm[f * NW + j] = em_mine;
         }
         const unsigned sc = warp_incl_scan(ve | (vi << 16));  // both counts (<= 1024 each)
         const unsigned ie = sc & 0xffffu, ii = sc >> 16;
@@ -828,7 +849,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         int kx, ky;
         bool valid;
         word_node<P, E, C::WR>(w, lane, kx, ky, valid);
-        const unsigned int em = emw_sm[f * NW + j], lt = (1u << lane) - 1u;
+        const unsigned int em = word_edges<WV, P, E, C::WR>(w), lt = (1u << lane) - 1u;
         T v;
         if ((em >> lane) & 1u) {
           v = ldr<T>(R + fi[2] + int(pre_e[f * NW + j] + __popc(word & em & lt)) * int(sizeof(T)));
@@ -847,6 +868,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
           }
         }
         tiles[win_in(f) + ky * PW + kx] = v;
+        atomicOr(colm + (f * E + kx) * CW + (ky >> 5), 1u << (ky & 31));
       }
     }
     __syncthreads();
@@ -864,9 +886,12 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       e[3] = int(fe.y);
       e[4] = int(fe.z);
     }
-    for (int t = tid; t < F * E; t += NT) {
+    for (int t = tid; t < F * E; t += NT) {  // rows without a stored coefficient read as zero
       const int f = t / E, x = t - f * E;
-      line_transform<WV, P, L, true, T>(tiles + win_in(f) + x, PW);
+      unsigned int cm[CW];
+#pragma unroll
+      for (int k = 0; k < CW; ++k) cm[k] = colm[t * CW + k] | ((x & ((1 << L) - 1)) == 0 ? coarse_rows<L>(k) : 0u);
+      inverse_column_masked<WV, P, L, T>(tiles + win_in(f) + x, PW, cm);
     }
     __syncthreads();
     if (NBTAB && tid >= NBT0 && tid < NBT0 + 8 * F) {
