@@ -347,10 +347,10 @@ __device__ __forceinline__ void ringfree_coarse(const unsigned char* arena_in, c
 }
 
 // BGK collision of one ghost node whose nine populations sit at
-// src[i * stride]; population p_k goes to tiles[d_k] (k < nout).  Out of
-// line: the ghost stages call it from two places.
+// src[i * stride]; population p_k goes to tiles[d_k] (k < nout).  The ghost
+// stages call it from two places.
 template <typename T>
-__device__ __noinline__ void ghost_collide(const T* src, int stride, T omega, T* tiles, int nout, int p0, int d0, int p1,
+__device__ __forceinline__ void ghost_collide(const T* src, int stride, T omega, T* tiles, int nout, int p0, int d0, int p1,
                                            int d1, int p2, int d2) {
   T fv[9];
 #pragma unroll
@@ -384,7 +384,8 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   (void)pid;
   auto scatter = [&](int n, int f, T* rg, int kind, ConeMask MX, ConeMask MY) {
-    ringfree_scatter<WV, T, ST, P, L>(a.arena_in, nbi, n, f, rg, kind, MX, MY);
+    if (nbi[8 * (n * F + f) + 3] != 0)  // words to decode (the call is not free)
+      ringfree_scatter<WV, T, ST, P, L>(a.arena_in, nbi, n, f, rg, kind, MX, MY);
   };
   auto tile_at = [&](int i, int x, int y) -> T& { return tiles[i * TS + (y + 1) * PW + (x + 1)]; };
   // zero n values at p (16-byte aligned) with vector stores
