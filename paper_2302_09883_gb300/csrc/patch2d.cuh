@@ -195,7 +195,7 @@ template <int P, int L, int TT, typename T> __device__ __forceinline__ void cone
 // Out of line: several stages call it, and one copy of its code serves them
 // all.
 template <typename T, int E, int PW, int TS>
-__device__ __noinline__ void collide_nodes(T* tiles, int t0, int t1, int dt, T omega) {
+__device__ __forceinline__ void collide_nodes(T* tiles, int t0, int t1, int dt, T omega) {
   for (int t = t0; t < t1; t += dt) {
     const int y = t / E, x = t - y * E;
     T* q = tiles + (y + 1) * PW + x + 1;
