@@ -419,7 +419,7 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   __syncthreads();
   static_assert(2 * F * NCN <= NT, "one column per thread");
   if (tid < 2 * F * NCN) line_transform<WV, P, L, true, T>(reg + tid * E, 1);  // columns
-  overlap(2 * F * NCN, 2);
+  overlap((2 * F * NCN + 31) / 32 * 32, 2);  // whole warps: a warp never runs both paths
   __syncthreads();
   for (int t = tid; t < F * E; t += NT) {  // west and east rows of one field in one thread
     const int f = t / E, y = t - f * E;
@@ -505,19 +505,35 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
     overlap(with_corners ? ((32 + 4 * F + 31) / 32) * 32 : ((2 * F + 31) / 32) * 32, 2);
     __syncthreads();
     for (int t = tid; t < 2 * E + (with_corners ? 4 : 0); t += NT) {
-      if (t < 2 * E) {  // south ghosts take populations 2, 5, 6, north ones 4, 7, 8
+      // south ghosts take populations 2, 5, 6, north ones 4, 7, 8; corners:
+      // SW 5 at (-1, -1), SE 6 at (E, -1), NE 7 at (E, E), NW 8 at (-1, E).
+      // One call for both kinds: a warp holding both runs one collision.
+      const T* src;
+      int stride, nout, q0, q1, q2, o0, o1, o2;
+      if (t < 2 * E) {
         const int sd = t / E, x = t - sd * E;
         const int col = (sd == 0 ? 0 : (E + 1) * PW) + x + 1;
-        ghost_collide<T>(reg + sd * F * NCN * E + (sd == 0 ? IH : IL) * E + x, NCN * E, omega, tiles, 3,
-                         sd == 0 ? 2 : 4, (sd == 0 ? 2 : 4) * TS + col, sd == 0 ? 5 : 7, (sd == 0 ? 5 : 7) * TS + col,
-                         sd == 0 ? 6 : 8, (sd == 0 ? 6 : 8) * TS + col);
-      } else {  // corners: SW 5 at (-1, -1), SE 6 at (E, -1), NE 7 at (E, E), NW 8 at (-1, E)
+        src = reg + sd * F * NCN * E + (sd == 0 ? IH : IL) * E + x;
+        stride = NCN * E;
+        nout = 3;
+        q0 = sd == 0 ? 2 : 4;
+        q1 = sd == 0 ? 5 : 7;
+        q2 = sd == 0 ? 6 : 8;
+        o0 = q0 * TS + col;
+        o1 = q1 * TS + col;
+        o2 = q2 * TS + col;
+      } else {
         const int c = t - 2 * E;
         const int iy = c <= 1 ? IH : IL, ix = (c == 0 || c == 3) ? IH : IL;
         const int cx = (c == 1 || c == 2) ? E + 1 : 0, cy = c >= 2 ? (E + 1) * PW : 0;
-        ghost_collide<T>(regc + c * F * NCC + iy * NCN + ix, NCC, omega, tiles, 1, 5 + c, (5 + c) * TS + cy + cx, 0, 0,
-                         0, 0);
+        src = regc + c * F * NCC + iy * NCN + ix;
+        stride = NCC;
+        nout = 1;
+        q0 = 5 + c;
+        o0 = q0 * TS + cy + cx;
+        q1 = q2 = o1 = o2 = 0;
       }
+      ghost_collide<T>(src, stride, omega, tiles, nout, q0, o0, q1, o1, q2, o2);
     }
     overlap((2 * E + (with_corners ? 4 : 0) + 31) / 32 * 32, 2);
     __syncthreads();
