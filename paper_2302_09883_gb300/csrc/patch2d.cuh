@@ -223,7 +223,7 @@ __device__ __forceinline__ void collide_nodes(T* tiles, int t0, int t1, int dt, 
 // (rg[ix E + y]); kind 1: rows of MY, all columns (rg[iy E + x]); kind 2:
 // both (rg[iy NCN + ix]).  One warp: present words with their survivor
 // ranks 32 at a time, then their surviving nodes one word at a time (the
-// coarse block: ringfree_coarse).  Out of line: three stages call it.
+// coarse block: ringfree_coarse_at).  Out of line: three stages call it.
 template <int WV, typename T, int ST, int P, int L>
 __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, const int* nbi, int n, int f, T* rg, int kind,
                                               ConeMask MX, ConeMask MY) {
@@ -236,7 +236,7 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
   const unsigned char* R =
       arena_in + ((unsigned long long)(unsigned int)e[0] | ((unsigned long long)(unsigned int)e[1] << 32));
   const int off = e[2], nwords = e[3], nedge = e[4];
-  if (nwords == 0) return;  // only the coarse block (done by ringfree_coarse)
+  if (nwords == 0) return;  // only the coarse block (ringfree_coarse_at)
   int p = off + NC * int(sizeof(T));
   unsigned long long bm = 0ull;
   if constexpr (C::QUANT) {
@@ -326,24 +326,26 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
   }
   }
 
-// Coarse value c of field f of neighbour n into region rg if its node lies
-// there (kind and masks as in ringfree_scatter).  One thread per value: a
-// stage issues all its coarse loads at once.
+// Coarse value c of field f of neighbour n, if its node lies in region rg
+// (kind and masks as in ringfree_scatter): its address in the record (src)
+// and its slot in the region (dst).  One thread per value: a stage issues
+// all its coarse loads before any store.
 template <int WV, typename T, int ST, int P, int L>
-__device__ __forceinline__ void ringfree_coarse(const unsigned char* arena_in, const int* nbi, int n, int f, T* rg,
-                                                int kind, ConeMask MX, ConeMask MY, int c) {
+__device__ __forceinline__ bool ringfree_coarse_at(const unsigned char* arena_in, const int* nbi, int n, int f, T* rg,
+                                                   int kind, ConeMask MX, ConeMask MY, int c, const T*& src, T*& dst) {
   typedef Cfg<SCH_D2Q9, WV, T, ST, P, L> C;
   constexpr int F = 9, E = C::E;
   constexpr int NCN = cone_count(cone_mask<P, L>(P - 1));
   const int iy = c / C::NC1, ix = c - iy * C::NC1, kx = ix << L, ky = iy << L;
   const bool in = kind == 0 ? cone_has(MX, kx) : (kind == 1 ? cone_has(MY, ky) : (cone_has(MX, kx) && cone_has(MY, ky)));
-  if (!in) return;
+  if (!in) return false;
   const int* e = nbi + 8 * (n * F + f);
   const unsigned char* R =
       arena_in + ((unsigned long long)(unsigned int)e[0] | ((unsigned long long)(unsigned int)e[1] << 32));
-  const int sl = kind == 0 ? cone_index(MX, kx) * E + ky
-                           : (kind == 1 ? cone_index(MY, ky) * E + kx : cone_index(MY, ky) * NCN + cone_index(MX, kx));
-  rg[sl] = ldr<T>(R + e[2] + c * int(sizeof(T)));
+  src = reinterpret_cast<const T*>(R + e[2] + c * int(sizeof(T)));
+  dst = rg + (kind == 0 ? cone_index(MX, kx) * E + ky
+                        : (kind == 1 ? cone_index(MY, ky) * E + kx : cone_index(MY, ky) * NCN + cone_index(MX, kx)));
+  return true;
 }
 
 // BGK collision of one ghost node whose nine populations sit at
@@ -387,6 +389,31 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
     if (nbi[8 * (n * F + f) + 3] != 0)  // words to decode (the call is not free)
       ringfree_scatter<WV, T, ST, P, L>(a.arena_in, nbi, n, f, rg, kind, MX, MY);
   };
+  // coarse blocks of a stage: item i of NI goes through map(i, ...) to its
+  // neighbour, field, region and value; a thread loads all its items, then
+  // stores them
+  auto coarse_items = [&](int NI, auto map) {
+    constexpr int NIT = (6 * F * NC + NT - 1) / NT;
+    T val[NIT];
+    T* dst[NIT];
+#pragma unroll
+    for (int k = 0; k < NIT; ++k) {
+      const int i = tid + k * NT;
+      dst[k] = nullptr;
+      const T* src;
+      if (i < NI) {
+        int n, f, kind;
+        T* rg;
+        ConeMask MX, MY;
+        map(i / NC, n, f, rg, kind, MX, MY);
+        if (ringfree_coarse_at<WV, T, ST, P, L>(a.arena_in, nbi, n, f, rg, kind, MX, MY, i % NC, src, dst[k]))
+          val[k] = __ldg(src);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NIT; ++k)
+      if (dst[k]) *dst[k] = val[k];
+  };
   auto tile_at = [&](int i, int x, int y) -> T& { return tiles[i * TS + (y + 1) * PW + (x + 1)]; };
   // zero n values at p (16-byte aligned) with vector stores
   auto zero = [&](T* p, int n) {
@@ -407,11 +434,15 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   // ---- west (its node P-1 of every row) and east (node 1) neighbours
   zero(reg, 2 * F * NCN * E);
   __syncthreads();
-  for (int i = tid; i < 2 * F * NC; i += NT) {  // coarse blocks: every load of the stage at once
-    const int task = i / NC, sd = task / F, f = task - sd * F;
-    ringfree_coarse<WV, T, ST, P, L>(a.arena_in, nbi, sd == 0 ? 3 : 4, f, reg + (sd * F + f) * NCN * E, 0, sd == 0 ? CH : CL,
-                                     CH, i - task * NC);
-  }
+  coarse_items(2 * F * NC, [&](int task, int& n, int& f, T*& rg, int& kind, ConeMask& MX, ConeMask& MY) {
+    const int sd = task / F;
+    f = task - sd * F;
+    n = sd == 0 ? 3 : 4;
+    rg = reg + (sd * F + f) * NCN * E;
+    kind = 0;
+    MX = sd == 0 ? CH : CL;
+    MY = CH;
+  });
   for (int task = warp; task < 2 * F; task += NWARP) {
     const int sd = task / F, f = task - sd * F;
     scatter(sd == 0 ? 3 : 4, f, reg + (sd * F + f) * NCN * E, 0, sd == 0 ? CH : CL, CH);
@@ -453,19 +484,25 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
     if (with_corners) zero(regc, 4 * F * NCC);
     __syncthreads();
     const int ntask = with_corners ? 6 * F : 2 * F;
-    for (int i = tid; i < ntask * NC; i += NT) {  // coarse blocks: every load of the stage at once
-      const int task = i / NC, cc = i - task * NC;
+    coarse_items(ntask * NC, [&](int task, int& n, int& f, T*& rg, int& kind, ConeMask& MX, ConeMask& MY) {
       if (task < 2 * F) {
-        const int sd = task / F, f = task - sd * F;
-        ringfree_coarse<WV, T, ST, P, L>(a.arena_in, nbi, sd == 0 ? 1 : 6, f, reg + (sd * F + f) * NCN * E, 1, CH,
-                                         sd == 0 ? CH : CL, cc);
+        const int sd = task / F;
+        f = task - sd * F;
+        n = sd == 0 ? 1 : 6;
+        rg = reg + (sd * F + f) * NCN * E;
+        kind = 1;
+        MX = CH;
+        MY = sd == 0 ? CH : CL;
       } else {
-        const int c = (task - 2 * F) / F, f = task - 2 * F - c * F;
-        const int dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
-        ringfree_coarse<WV, T, ST, P, L>(a.arena_in, nbi, dy < 0 ? (dx < 0 ? 0 : 2) : (dx < 0 ? 5 : 7), f,
-                                         regc + (c * F + f) * NCC, 2, dx < 0 ? CH : CL, dy < 0 ? CH : CL, cc);
+        const int c = (task - 2 * F) / F, dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
+        f = task - 2 * F - c * F;
+        n = dy < 0 ? (dx < 0 ? 0 : 2) : (dx < 0 ? 5 : 7);
+        rg = regc + (c * F + f) * NCC;
+        kind = 2;
+        MX = dx < 0 ? CH : CL;
+        MY = dy < 0 ? CH : CL;
       }
-    }
+    });
     for (int task = warp; task < ntask; task += NWARP) {
       if (task < 2 * F) {
         const int sd = task / F, f = task - sd * F;
@@ -541,12 +578,15 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   auto corners_alone = [&]() {
     zero(reg, 4 * F * NCC);
     __syncthreads();
-    for (int i = tid; i < 4 * F * NC; i += NT) {
-      const int task = i / NC, c = task / F, f = task - c * F;
-      const int dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
-      ringfree_coarse<WV, T, ST, P, L>(a.arena_in, nbi, dy < 0 ? (dx < 0 ? 0 : 2) : (dx < 0 ? 5 : 7), f,
-                                       reg + (c * F + f) * NCC, 2, dx < 0 ? CH : CL, dy < 0 ? CH : CL, i - task * NC);
-    }
+    coarse_items(4 * F * NC, [&](int task, int& n, int& f, T*& rg, int& kind, ConeMask& MX, ConeMask& MY) {
+      const int c = task / F, dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
+      f = task - c * F;
+      n = dy < 0 ? (dx < 0 ? 0 : 2) : (dx < 0 ? 5 : 7);
+      rg = reg + (c * F + f) * NCC;
+      kind = 2;
+      MX = dx < 0 ? CH : CL;
+      MY = dy < 0 ? CH : CL;
+    });
     for (int task = warp; task < 4 * F; task += NWARP) {
       const int c = task / F, f = task - c * F;
       const int dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
