@@ -897,7 +897,12 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     }
     __syncthreads();
     // survivors: one warp per non-zero mask word, one lane per node
-    for (int f = 0; f < F; ++f) {
+    // (skipped as a whole when no field has a stored word: entering the
+    // loops costs even when they are empty)
+    int nw_all = 0;
+#pragma unroll
+    for (int f = 0; f < F; ++f) nw_all += finfo[16 * f + 6];
+    for (int f = 0; f < F && nw_all > 0; ++f) {
       const int* fi = finfo + 16 * f;
       for (int j = warp; j < fi[6]; j += NWARP) {
         const unsigned int word = mw[f * NW + j];
@@ -1463,7 +1468,10 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     const unsigned int bits = __ballot_sync(0xffffffffu, w < NW && mw[f * NW + (w < NW ? w : 0)] != 0u);
     if (lane == 0) stg<unsigned int>(O + finfo[16 * f + 9] + finfo[16 * f + 1] + 4 * j, bits);
   }
-  for (int f = 0; f < F; ++f) {
+  int nw_all = 0;  // non-zero words of all fields (the loops below are skipped when there are none)
+#pragma unroll
+  for (int f = 0; f < F; ++f) nw_all += finfo[16 * f + 4];
+  for (int f = 0; f < F && nw_all > 0; ++f) {
     const int* fi = finfo + 16 * f;
     for (int j = tid; j < fi[4]; j += NT)
       stg<unsigned int>(O + fi[9] + fi[1] + 4 * NPW + 4 * j, mw[f * NW + plist[f * NW + j]]);
@@ -1474,7 +1482,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     for (int p = fi[1] + 4 * NPW + 4 * fi[4]; p < fi[2]; ++p) base[p] = 0;
     for (int p = fi[3] + fi[6] * C::SB; p < fi[0]; ++p) base[p] = 0;
   }
-  for (int f = 0; f < F; ++f) {
+  for (int f = 0; f < F && nw_all > 0; ++f) {
     const int* fi = finfo + 16 * f;
     for (int j = warp; j < fi[4]; j += NWARP) {
       const int w = plist[f * NW + j];
