@@ -167,6 +167,19 @@ __device__ __forceinline__ void inverse_column_masked(T* p, int stride, const un
   for (int i = 0; i < E; ++i) p[i * stride] = v[i];
 }
 
+// Coarse nodes (multiples of 2^L) in a cone, and whether the border cones
+// hold exactly the top q of them (node P-1) and the bottom q (node 1).
+template <int P, int L> __host__ __device__ constexpr int cone_coarse_count(ConeMask m) {
+  int k = 0;
+  for (int n = 0; n <= P; n += 1 << L) k += cone_has(m, n) ? 1 : 0;
+  return k;
+}
+template <int P, int L> __host__ __device__ constexpr bool cone_coarse_ends(ConeMask h, ConeMask l, int q) {
+  for (int j = 0; j < q; ++j)
+    if (!cone_has(h, P - j * (1 << L)) || !cone_has(l, j * (1 << L))) return false;
+  return cone_coarse_count<P, L>(h) == q && cone_coarse_count<P, L>(l) == q;
+}
+
 // Value of node TT after the inverse lifting across a cone held in
 // rg[cone_index(n) * stride + off] (TT's own slot receives the result).
 template <int P, int L, int TT> struct ConeSlots {  // slot of every window node (-1: not in the cone)
@@ -385,6 +398,19 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   constexpr int IH = cone_index_c(CH, P - 1), IL = cone_index_c(CL, 1);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   (void)pid;
+  // the cones' coarse nodes: the top NCQ multiples of 2^L (west/south, node
+  // P-1) and the bottom NCQ (east/north, node 1)
+  constexpr int NCQ = cone_coarse_count<P, L>(CH);
+  static_assert(cone_coarse_ends<P, L>(CH, CL, NCQ), "border cones hold the end coarse nodes");
+  auto qh = [](int j) { return P - (NCQ - 1 - j) * (1 << L); };
+  auto ql = [](int j) { return j * (1 << L); };
+  // coarse value c of field f of neighbour n, from its record
+  auto coarse_val = [&](int n, int f, int c) -> T {
+    const int* e = nbi + 8 * (n * F + f);
+    const unsigned char* R =
+        a.arena_in + ((unsigned long long)(unsigned int)e[0] | ((unsigned long long)(unsigned int)e[1] << 32));
+    return __ldg(reinterpret_cast<const T*>(R + e[2] + c * int(sizeof(T))));
+  };
   auto scatter = [&](int n, int f, T* rg, int kind, ConeMask MX, ConeMask MY) {
     if (nbi[8 * (n * F + f) + 3] != 0)  // words to decode (the call is not free)
       ringfree_scatter<WV, T, ST, P, L>(a.arena_in, nbi, n, f, rg, kind, MX, MY);
@@ -434,15 +460,12 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   // ---- west (its node P-1 of every row) and east (node 1) neighbours
   zero(reg, 2 * F * NCN * E);
   __syncthreads();
-  coarse_items(2 * F * NC, [&](int task, int& n, int& f, T*& rg, int& kind, ConeMask& MX, ConeMask& MY) {
-    const int sd = task / F;
-    f = task - sd * F;
-    n = sd == 0 ? 3 : 4;
-    rg = reg + (sd * F + f) * NCN * E;
-    kind = 0;
-    MX = sd == 0 ? CH : CL;
-    MY = CH;
-  });
+  for (int i = tid; i < 2 * F * NCQ * C::NC1; i += NT) {  // coarse blocks: only the cone's coarse columns
+    const int task = i / (NCQ * C::NC1), r = i - task * NCQ * C::NC1, jx = r / C::NC1, iy = r - jx * C::NC1;
+    const int sd = task / F, f = task - sd * F, kx = sd == 0 ? qh(jx) : ql(jx);
+    reg[(sd * F + f) * NCN * E + (sd == 0 ? cone_index(CH, kx) : cone_index(CL, kx)) * E + (iy << L)] =
+        coarse_val(sd == 0 ? 3 : 4, f, iy * C::NC1 + (kx >> L));
+  }
   for (int task = warp; task < 2 * F; task += NWARP) {
     const int sd = task / F, f = task - sd * F;
     scatter(sd == 0 ? 3 : 4, f, reg + (sd * F + f) * NCN * E, 0, sd == 0 ? CH : CL, CH);
@@ -484,25 +507,25 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
     if (with_corners) zero(regc, 4 * F * NCC);
     __syncthreads();
     const int ntask = with_corners ? 6 * F : 2 * F;
-    coarse_items(ntask * NC, [&](int task, int& n, int& f, T*& rg, int& kind, ConeMask& MX, ConeMask& MY) {
-      if (task < 2 * F) {
-        const int sd = task / F;
-        f = task - sd * F;
-        n = sd == 0 ? 1 : 6;
-        rg = reg + (sd * F + f) * NCN * E;
-        kind = 1;
-        MX = CH;
-        MY = sd == 0 ? CH : CL;
-      } else {
-        const int c = (task - 2 * F) / F, dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
-        f = task - 2 * F - c * F;
-        n = dy < 0 ? (dx < 0 ? 0 : 2) : (dx < 0 ? 5 : 7);
-        rg = regc + (c * F + f) * NCC;
-        kind = 2;
-        MX = dx < 0 ? CH : CL;
-        MY = dy < 0 ? CH : CL;
+    {  // coarse blocks: only the coarse nodes in the cones (rows for south/north, both for the corners)
+      constexpr int NSN = 2 * F * NCQ * C::NC1;
+      const int nitem = NSN + (with_corners ? 4 * F * NCQ * NCQ : 0);
+      for (int i = tid; i < nitem; i += NT) {
+        if (i < NSN) {
+          const int task = i / (NCQ * C::NC1), r = i - task * NCQ * C::NC1, jy = r / C::NC1, ix = r - jy * C::NC1;
+          const int sd = task / F, f = task - sd * F, ky = sd == 0 ? qh(jy) : ql(jy);
+          reg[(sd * F + f) * NCN * E + (sd == 0 ? cone_index(CH, ky) : cone_index(CL, ky)) * E + (ix << L)] =
+              coarse_val(sd == 0 ? 1 : 6, f, (ky >> L) * C::NC1 + ix);
+        } else {
+          const int u = i - NSN, task = u / (NCQ * NCQ), r = u - task * NCQ * NCQ, jy = r / NCQ, jx = r - jy * NCQ;
+          const int c = task / F, f = task - c * F, dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
+          const int kx = dx < 0 ? qh(jx) : ql(jx), ky = dy < 0 ? qh(jy) : ql(jy);
+          regc[(c * F + f) * NCC + (dy < 0 ? cone_index(CH, ky) : cone_index(CL, ky)) * NCN +
+               (dx < 0 ? cone_index(CH, kx) : cone_index(CL, kx))] =
+              coarse_val(dy < 0 ? (dx < 0 ? 0 : 2) : (dx < 0 ? 5 : 7), f, (ky >> L) * C::NC1 + (kx >> L));
+        }
       }
-    });
+    }
     for (int task = warp; task < ntask; task += NWARP) {
       if (task < 2 * F) {
         const int sd = task / F, f = task - sd * F;
