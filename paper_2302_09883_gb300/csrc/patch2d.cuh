@@ -1153,7 +1153,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         if constexpr (C::QUANT) {
           if (!yedge) mk[cy] = (keep && !xedge) ? fmaxf(mk[cy], fabsf(float(v[y]))) : mk[cy];
         }
-        if (!keep) v[y] = T(0);
+        if (STORE_ALL && !keep) v[y] = T(0);  // ring-free: dropped details are not stored
       }
       const unsigned int bal = __ballot_sync(0xffffffffu, keep);
       if (lane == 0) mwf[y * C::WR] = bal;
@@ -1426,17 +1426,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       }
       ds[t] = acc;
     }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      asm volatile("bar.sync 1, %0;" ::"n"(32 * SUMW) : "memory");
-      for (int t = t0; t < F * o; t += 32 * SUMW) {
-        const int f = t / o, i = t - f * o;
-        ds[f * 32 + i] = ds[f * 32 + i] + ds[f * 32 + i + o];
-      }
-    }
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * SUMW) : "memory");
-    if (t0 < F) a.pstats[size_t(pid) * F + t0] = ds[t0 * 32] * double(1ll << (2 * L));
-  }
+  }  // the pairwise levels follow in the record-write phase (they only need these slots)
   __syncthreads();
   if (tid == 0) {
     int off = (16 + 16 * F + 15) & ~15;
@@ -1463,6 +1453,20 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   unsigned char* O = a.arena_out + ((unsigned long long)(unsigned int)misc[2] | ((unsigned long long)(unsigned int)misc[3] << 32));
 
   // ----------------------------- encode pass 2: the record, survivors only
+  if (warp >= F && warp < F + SUMW) {  // the coarse sums' pairwise levels (slots from the scan phase)
+    double* ds = reinterpret_cast<double*>(stage + OFF_DSUM);
+    const int t0 = tid - 32 * F;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * SUMW) : "memory");
+      for (int t = t0; t < F * o; t += 32 * SUMW) {
+        const int f = t / o, i = t - f * o;
+        ds[f * 32 + i] = ds[f * 32 + i] + ds[f * 32 + i + o];
+      }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * SUMW) : "memory");
+    if (t0 < F) a.pstats[size_t(pid) * F + t0] = ds[t0 * 32] * double(1ll << (2 * L));
+  }
   if (tid == 0) stg<uint4>(O, make_uint4((unsigned)misc[1], (unsigned)pid, (unsigned)F, a.flags));
   if (tid < F) {
     const int* fi = finfo + 16 * tid;
