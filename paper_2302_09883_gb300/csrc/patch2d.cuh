@@ -154,10 +154,10 @@ template <int L> __device__ __forceinline__ constexpr unsigned int coarse_rows(i
   return m;
 }
 
-// Inverse lifting of one column (p[y * stride]) whose rows without bit y in
-// cm hold no stored coefficient: those read as zero and are not loaded.
+// Inverse lifting of one line (p[i * stride]) whose nodes without bit i in
+// cm are zero: those read as zero and are not loaded.
 template <int WV, int P, int L, typename T>
-__device__ __forceinline__ void inverse_column_masked(T* p, int stride, const unsigned int* cm) {
+__device__ __forceinline__ void inverse_line_masked(T* p, int stride, const unsigned int* cm) {
   constexpr int E = WV == WV_BL53 ? P + 1 : P;
   T v[E];
 #pragma unroll
@@ -675,7 +675,11 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   // these rows and the coarse ones.  Lives where the band data goes later.
   constexpr int CW = (E + 31) / 32;
   unsigned int* colm = reinterpret_cast<unsigned int*>(smem + C::OFF_EMW);
-  static_assert(size_t(F) * E * CW * 4 <= C::OFF_FINFO - C::OFF_EMW, "column masks do not fit");
+  // then per field the columns that hold any stored or coarse coefficient
+  // (the others are zero after the column pass too: it skips them, the row
+  // pass reads them as zero)
+  unsigned int* ntc = colm + F * E * CW;  // [F][CW]
+  static_assert(size_t(F) * (E + 1) * CW * 4 <= C::OFF_FINFO - C::OFF_EMW, "column masks do not fit");
   unsigned int* bmax = reinterpret_cast<unsigned int*>(smem + C::OFF_BMAX);
   float* scl = reinterpret_cast<float*>(smem + C::OFF_SCL);
   float* sinv = reinterpret_cast<float*>(smem + C::OFF_SINV);
@@ -956,9 +960,33 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         atomicOr(colm + (f * E + kx) * CW + (ky >> 5), 1u << (ky & 31));
       }
     }
+    for (int i = tid; i < F * CW; i += NT) ntc[i] = 0u;
+    if (tid == 0) misc[60] = 0;
     __syncthreads();
-    // inverse tensor lifting: y lines (columns) then x lines (rows); the
-    // neighbour table rows and band masks come in meanwhile (see above)
+    // inverse tensor lifting: y lines (columns) then x lines (rows).  The
+    // columns with a stored or coarse coefficient go to a list (a warp
+    // ballot and one shared counter per warp); only they are transformed.
+    unsigned short* clist = reinterpret_cast<unsigned short*>(stage);  // the staging area is free from here on
+    for (int t0 = 0; t0 < F * E; t0 += NT) {
+      const int t = t0 + tid, f = t / E, x = t - f * E;
+      bool nt = false;
+      if (t < F * E) {
+        unsigned int any = (x & ((1 << L) - 1)) == 0 ? 1u : 0u;
+#pragma unroll
+        for (int k = 0; k < CW; ++k) any |= colm[t * CW + k];
+        nt = any != 0u;
+      }
+      const unsigned int bal = __ballot_sync(0xffffffffu, nt);
+      int base = 0;
+      if (lane == 0 && bal) base = atomicAdd(misc + 60, __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (nt) {
+        clist[base + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)t;
+        atomicOr(ntc + f * CW + (x >> 5), 1u << (x & 31));
+      }
+    }
+    __syncthreads();
+    // the neighbour table rows and band masks come in meanwhile (see above)
     int* nbi_w = reinterpret_cast<int*>(smem + C::OFF_NBI);  // per (neighbour, field): 8 ints
     if (NBTAB && tid >= NBT0 && tid < NBT0 + 8 * F) {
       const int tn = tid - NBT0, n = tn / F, f = tn - n * F;
@@ -971,12 +999,12 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       e[3] = int(fe.y);
       e[4] = int(fe.z);
     }
-    for (int t = tid; t < F * E; t += NT) {  // rows without a stored coefficient read as zero
-      const int f = t / E, x = t - f * E;
+    for (int i = tid; i < misc[60]; i += NT) {  // rows without a stored coefficient read as zero
+      const int t = clist[i], f = t / E, x = t - f * E;
       unsigned int cm[CW];
 #pragma unroll
       for (int k = 0; k < CW; ++k) cm[k] = colm[t * CW + k] | ((x & ((1 << L) - 1)) == 0 ? coarse_rows<L>(k) : 0u);
-      inverse_column_masked<WV, P, L, T>(tiles + win_in(f) + x, PW, cm);
+      inverse_line_masked<WV, P, L, T>(tiles + win_in(f) + x, PW, cm);
     }
     __syncthreads();
     if (NBTAB && tid >= NBT0 && tid < NBT0 + 8 * F) {
@@ -992,9 +1020,12 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       e[5] = int(b0);
       e[6] = int(b1);
     }
-    for (int t = tid; t < F * E; t += NT) {
+    for (int t = tid; t < F * E; t += NT) {  // columns left out above read as zero
       const int f = t / E, y = t - f * E;
-      line_transform<WV, P, L, true, T>(tiles + win_in(f) + y * PW, 1);
+      unsigned int cm[CW];
+#pragma unroll
+      for (int k = 0; k < CW; ++k) cm[k] = ntc[f * CW + k];
+      inverse_line_masked<WV, P, L, T>(tiles + win_in(f) + y * PW, 1, cm);
     }
     __syncthreads();
   }
