@@ -1,8 +1,9 @@
 // Oracle (test infrastructure only).
 //
-// The learned per-patch threshold (not in the paper; a reading of the
-// the benchmark spec's learned part): features of a patch, its label, and a small
-// MLP with FP64 forward and backward passes.
+// The learned per-patch threshold (an extension, not in the paper: a small
+// network maps per-level wavelet statistics of a patch to its threshold):
+// features of a patch, its label, and a small MLP with FP64 forward and
+// backward passes.
 //
 //  * Features: the detail nodes are grouped by (l, S): l = the largest
 //    per-axis class of the node (1..L; all classes 0 = coarse, skipped) and
