@@ -1154,11 +1154,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     T thr[L + 1];  // this lane's threshold per y class (rows y = 0, P use te)
 #pragma unroll
     for (int c = 0; c <= L; ++c) thr[c] = xedge ? te[c] : tau_i[cx * (L + 1) + c];
-    // largest kept |detail| of band (cx, cy) in this lane (-1: none); one
-    // shared-memory atomic per band after the pass
-    float mk[L + 1];
-#pragma unroll
-    for (int c = 0; c <= L; ++c) mk[c] = -1.0f;
     T nanacc = T(0);  // v * 0 summed: NaN iff some coefficient is not finite
     unsigned int* mwf = mw + f * NW + h;
     // FEAT, this lane: energy and max per row class cy (branch-free; lanes
@@ -1181,9 +1176,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       if (cx | cy) {
         const bool yedge = WV == WV_BL53 && (y == 0 || y == P);  // folds: y is a constant here
         keep = valid && fabs(v[y]) >= (yedge ? te[cy] : thr[cy]);
-        if constexpr (C::QUANT) {
-          if (!yedge) mk[cy] = (keep && !xedge) ? fmaxf(mk[cy], fabsf(float(v[y]))) : mk[cy];
-        }
         if (STORE_ALL && !keep) v[y] = T(0);  // ring-free: dropped details are not stored
       }
       const unsigned int bal = __ballot_sync(0xffffffffu, keep);
@@ -1192,11 +1184,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     };
     fwd_levels_cb<WV, P, 1, L, T>(v, node);
     if (nanacc != nanacc) bad = true;
-    if constexpr (C::QUANT) {
-#pragma unroll
-      for (int c = 0; c <= L; ++c)
-        if (mk[c] >= 0.0f) atomicMax(bmax + f * NB + cx * (L + 1) + c, __float_as_uint(mk[c]) + 1u);
-    }
     if constexpr (FEAT) {  // warp sums per group, fixed shuffle order
       // group (l, x): cx == l, rows cy < l; (l, y): cx < l, rows cy == l;
       // (l, xy): cx == l, rows cy == l (the coarse node cx = cy = 0 is in none)
@@ -1394,6 +1381,21 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     const unsigned ce = tot & 0x1ffu, ci = (tot >> 9) & 0x1fffu, cw = tot >> 22;
     unsigned long long bm = 0ull;
     if constexpr (C::QUANT) {
+      // band maxima of the kept interior details (the quantiser's scales),
+      // from the survivors themselves: a word at a time, lane = node
+      __syncwarp();
+      for (int j = 0; j < int(cw); ++j) {
+        const int w = plist[f * NW + j];
+        const unsigned int word = mw[f * NW + w] & ~word_edges<WV, P, E, C::WR>(w);
+        if ((word >> lane) & 1u) {
+          int kx, ky;
+          bool valid;
+          word_node<P, E, C::WR>(w, lane, kx, ky, valid);
+          const T v = tiles[win_out(f) + ky * PW + kx];
+          atomicMax(bmax + f * NB + node_class<L>(kx) * (L + 1) + node_class<L>(ky), __float_as_uint(fabsf(float(v))) + 1u);
+        }
+      }
+      __syncwarp();
       for (int b0 = 0; b0 < NB; b0 += 32) {
         const int b = b0 + lane;
         const unsigned int m = (b < NB) ? bmax[f * NB + b] : 0u;
