@@ -1131,7 +1131,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   // then for every row y one ballot gives mask word (y, h) directly; the
   // zeroed details go back to shared memory as zeros.  One more warp does
   // the shared column x = P of every field (lane = field).
-  bool bad = false;
   static_assert(F * C::WR + (C::NCW > 0 ? 1 : 0) <= NWARP, "not enough warps for the fused pass");
   // FEAT: energy and max of the details before the threshold per group
   // (l, S): l = max(cx, cy), S = the axes of class l (x, y or both); sums
@@ -1154,7 +1153,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     T thr[L + 1];  // this lane's threshold per y class (rows y = 0, P use te)
 #pragma unroll
     for (int c = 0; c <= L; ++c) thr[c] = xedge ? te[c] : tau_i[cx * (L + 1) + c];
-    T nanacc = T(0);  // v * 0 summed: NaN iff some coefficient is not finite
     unsigned int* mwf = mw + f * NW + h;
     // FEAT, this lane: energy and max per row class cy (branch-free; lanes
     // past P hold zeros); the groups are formed once after the pass
@@ -1171,7 +1169,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         acc2[cy] = acc2[cy] + d * d;
         accm[cy] = fmaxf(accm[cy], fabsf(d));
       }
-      nanacc = fma_rn(v[y], T(0), nanacc);
       bool keep = false;
       if (cx | cy) {
         const bool yedge = WV == WV_BL53 && (y == 0 || y == P);  // folds: y is a constant here
@@ -1183,7 +1180,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       if (valid && (STORE_ALL || keep || (cx | cy) == 0)) col[y * PW] = v[y];
     };
     fwd_levels_cb<WV, P, 1, L, T>(v, node);
-    if (nanacc != nanacc) bad = true;
     if constexpr (FEAT) {  // warp sums per group, fixed shuffle order
       // group (l, x): cx == l, rows cy < l; (l, y): cx < l, rows cy == l;
       // (l, xy): cx == l, rows cy == l (the coarse node cx = cy = 0 is in none)
@@ -1218,7 +1214,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     T v[E];
 #pragma unroll
     for (int y = 0; y < E; ++y) v[y] = col[y * PW];
-    T nanacc = T(0);
     auto node = [&](int y) {
       const int cy = node_class<L>(y);
       if constexpr (FEAT) {
@@ -1228,7 +1223,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
           cfm[cy] = fmaxf(cfm[cy], fabsf(d));
         }
       }
-      nanacc = fma_rn(v[y], T(0), nanacc);
       bool keep = true;
       if (cy) {  // x = P is a coarse x-node; every node of the column is on an edge line
         keep = fabs(v[y]) >= tau_e[cy];
@@ -1238,7 +1232,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       if (STORE_ALL || keep) col[y * PW] = v[y];
     };
     fwd_levels_cb<WV, P, 1, L, T>(v, node);
-    if (nanacc != nanacc) bad = true;
 #pragma unroll
     for (int k = 0; k < C::NCW; ++k) mw[f * NW + C::NRW + k] = cw[k];
   }
@@ -1279,9 +1272,6 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       for (int i = t; i < MLP_NP / 4; i += nt) reinterpret_cast<float4*>(dst)[i] = __ldg(src4 + i);
       for (int i = MLP_NP / 4 * 4 + t; i < MLP_NP; i += nt) dst[i] = __ldg(a.mlp_wt + i);
     }
-  }
-  if (bad) {
-    if (atomicOr(&a.ctl->status, STAT_NAN) == 0u) a.ctl->err_step = int(a.step);
   }
   __syncthreads();
   if constexpr (FEAT) {  // features of the new state: sums over the warps in warp order
@@ -1445,6 +1435,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   if (warp >= F && warp < F + SUMW) {
     double* ds = reinterpret_cast<double*>(stage + OFF_DSUM);
     const int t0 = tid - 32 * F;
+    bool bad = false;
     for (int t = t0; t < F * 32; t += 32 * SUMW) {
       const int f = t >> 5;
       double acc = 0.0;
@@ -1455,10 +1446,17 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
           const bool ex = ix == 0 || ix == C::NC1 - 1, ey = iy == 0 || iy == C::NC1 - 1;
           w = ex && ey ? 0.25 : (ex || ey ? 0.5 : 1.0);
         }
-        acc = acc + w * double(tiles[win_out(f) + (iy << L) * PW + (ix << L)]);
+        const T cv = tiles[win_out(f) + (iy << L) * PW + (ix << L)];
+        bad = bad || !isfinite(cv);
+        acc = acc + w * double(cv);
       }
       ds[t] = acc;
     }
+    // A non-finite coefficient anywhere makes a coarse one non-finite: the
+    // lifting updates carry every detail into even nodes, level by level,
+    // and neither an addition nor a multiplication by 1/2 or 1/4 turns a
+    // NaN or an infinity finite.  So the coarse block is the whole check.
+    if (__any_sync(0xffffffffu, bad) && lane == 0 && atomicOr(&a.ctl->status, STAT_NAN) == 0u) a.ctl->err_step = int(a.step);
   }  // the pairwise levels follow in the record-write phase (they only need these slots)
   __syncthreads();
   if (tid == 0) {
