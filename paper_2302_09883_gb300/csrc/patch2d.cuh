@@ -1,13 +1,16 @@
 // Fused compressed-patch time step for 2-D schemes: one CTA owns one patch
 // for the whole step, every intermediate lives in shared memory.
 //
-//   stage record (16-B vector loads) -> decode (zero the tiles, scatter the
-//   coarse block and the survivors of the non-zero mask words only) ->
-//   inverse tensor lifting -> ghosts -> scheme (D2Q9 collide in place + pull
-//   via per-population shifted windows, or the Rusanov FV update) -> forward
-//   tensor lifting -> threshold over the node order with warp ballots ->
-//   prefix sums, bump-allocate, write the record (survivors only) and the
-//   dequantised values back in place, FP64 coarse-block sums.
+//   stage record (16-B vector loads) -> decode (scatter the coarse block and
+//   the survivors of the non-zero mask words; the tiles are not zeroed, a
+//   per-column mask of the stored rows stands in for the zeros) -> inverse
+//   tensor lifting (only the columns holding a coefficient, then every row)
+//   -> ghosts -> scheme (D2Q9 collide in place + pull via per-population
+//   shifted windows, or the Rusanov FV update) -> forward tensor lifting ->
+//   threshold over the node order with warp ballots -> prefix sums, band
+//   scales, non-finite check on the coarse block, FP64 coarse-block sums,
+//   bump-allocate, write the record (survivors only) and the dequantised
+//   values back in place (the ring kernels re-decode them).
 //   Ghosts: D2Q9 on BL5/3 patches decodes them from the neighbours' records
 //   of the current state (only the dependency cone of the boundary node, see
 //   ringfree_ghosts); the other kernels read a ring that every patch exports
