@@ -404,7 +404,9 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
       const int pe0 = (p + 4 * C::NPW + 4 * int(fe.y) + 7) & ~7;
       const float* edge_v = reinterpret_cast<const float*>(sec + pe0);
       const S* int_v = reinterpret_cast<const S*>(sec + pe0 + 4 * int(fe.z));
-      for (int w = warp; w < NW; w += NWARP) {
+      // (skipped as a whole when the field stored no word: walking the empty
+      // mask costs even though nothing is found)
+      for (int w = warp; w < NW && fe.y != 0u; w += NWARP) {
         const unsigned int word = mw[w];
         if (word == 0u || !((word >> lane) & 1u)) continue;
         const unsigned int em = word3_edges<P, E, WR>(w), below = (1u << lane) - 1u;
@@ -752,15 +754,12 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
       if (tid < NB && ((bm >> tid) & 1ull))
         reinterpret_cast<float*>(sec + p_q + 8)[__popcll(bm & ((1ull << tid) - 1ull))] = scl[tid];
     }
-    for (int q = tid; q < C::NPW; q += NT) {
-      unsigned int pres = 0u;
-      for (int j = 0; j < 32; ++j) {
-        const int w = 32 * q + j;
-        if (w < NW && mw[w] != 0u) pres |= 1u << j;
-      }
-      reinterpret_cast<unsigned int*>(sec + p_pres)[q] = pres;
+    for (int q = warp; q < C::NPW; q += NWARP) {  // presence bitmap: one ballot per 32 words
+      const int w = 32 * q + lane;
+      const unsigned int pres = __ballot_sync(0xffffffffu, w < NW && mw[w < NW ? w : 0] != 0u);
+      if (lane == 0) reinterpret_cast<unsigned int*>(sec + p_pres)[q] = pres;
     }
-    for (int w = tid; w < NW; w += NT)
+    for (int w = tid; w < NW && nwords != 0u; w += NT)
       if (mw[w] != 0u) reinterpret_cast<unsigned int*>(sec + p_words)[pz[w]] = mw[w];
     if (tid == 0) {
       for (int b = p_wend; b < p_edge; ++b) sec[b] = 0;
@@ -769,7 +768,7 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
     }
     // survivors in bit order; the quantised values go back into the tile so
     // that the re-decode below sees what a decoder of the record sees
-    for (int w = warp; w < NW; w += NWARP) {
+    for (int w = warp; w < NW && nwords != 0u; w += NWARP) {
       const unsigned int word = mw[w];
       if (word == 0u || !((word >> lane) & 1u)) continue;
       const unsigned int em = word3_edges<P, E, WR>(w), below = (1u << lane) - 1u;
