@@ -474,9 +474,28 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
     scatter(sd == 0 ? 3 : 4, f, reg + (sd * F + f) * NCN * E, 0, sd == 0 ? CH : CL, CH);
   }
   __syncthreads();
-  static_assert(2 * F * NCN <= NT, "one column per thread");
-  if (tid < 2 * F * NCN) line_transform<WV, P, L, true, T>(reg + tid * E, 1);  // columns
-  overlap((2 * F * NCN + 31) / 32 * 32, 2);  // whole warps: a warp never runs both paths
+  // the cone columns: only the coarse ones hold coefficients, unless the
+  // neighbour field stored words (then every column of its region); the
+  // others are zero and stay zero
+  constexpr int NQC = 2 * F * NCQ;
+  static_assert(NQC <= NT, "one coarse column per thread");
+  auto coarse_ix = [&](int sd, int ix) {
+    bool c = false;
+#pragma unroll
+    for (int j = 0; j < NCQ; ++j) c = c || ix == (sd == 0 ? cone_index(CH, qh(j)) : cone_index(CL, ql(j)));
+    return c;
+  };
+  if (tid < NQC) {
+    const int task = tid / NCQ, j = tid - task * NCQ, sd = task / F;
+    line_transform<WV, P, L, true, T>(reg + (task * NCN + (sd == 0 ? cone_index(CH, qh(j)) : cone_index(CL, ql(j)))) * E, 1);
+  }
+  for (int task = warp; task < 2 * F; task += NWARP) {
+    const int sd = task / F, f = task - sd * F;
+    if (nbi[8 * ((sd == 0 ? 3 : 4) * F + f) + 3] == 0) continue;
+    for (int ix = lane; ix < NCN; ix += 32)
+      if (!coarse_ix(sd, ix)) line_transform<WV, P, L, true, T>(reg + (task * NCN + ix) * E, 1);
+  }
+  overlap((NQC + 31) / 32 * 32, 2);  // whole warps: a warp never runs both paths
   __syncthreads();
   for (int t = tid; t < F * E; t += NT) {  // west and east rows of one field in one thread
     const int f = t / E, y = t - f * E;
@@ -969,8 +988,10 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     // inverse tensor lifting: y lines (columns) then x lines (rows).  The
     // columns with a stored or coarse coefficient go to a list (a warp
     // ballot and one shared counter per warp); only they are transformed.
+    // (with no stored word at all the list is the coarse columns, known
+    // without it)
     unsigned short* clist = reinterpret_cast<unsigned short*>(stage);  // the staging area is free from here on
-    for (int t0 = 0; t0 < F * E; t0 += NT) {
+    for (int t0 = 0; t0 < F * E && nw_all > 0; t0 += NT) {
       const int t = t0 + tid, f = t / E, x = t - f * E;
       bool nt = false;
       if (t < F * E) {
@@ -988,7 +1009,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         atomicOr(ntc + f * CW + (x >> 5), 1u << (x & 31));
       }
     }
-    __syncthreads();
+    if (nw_all > 0) __syncthreads();
     // the neighbour table rows and band masks come in meanwhile (see above)
     int* nbi_w = reinterpret_cast<int*>(smem + C::OFF_NBI);  // per (neighbour, field): 8 ints
     if (NBTAB && tid >= NBT0 && tid < NBT0 + 8 * F) {
@@ -1002,8 +1023,9 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       e[3] = int(fe.y);
       e[4] = int(fe.z);
     }
-    for (int i = tid; i < misc[60]; i += NT) {  // rows without a stored coefficient read as zero
-      const int t = clist[i], f = t / E, x = t - f * E;
+    const int ncol = nw_all > 0 ? misc[60] : F * C::NC1;
+    for (int i = tid; i < ncol; i += NT) {  // rows without a stored coefficient read as zero
+      const int t = nw_all > 0 ? int(clist[i]) : (i / C::NC1) * E + ((i % C::NC1) << L), f = t / E, x = t - f * E;
       unsigned int cm[CW];
 #pragma unroll
       for (int k = 0; k < CW; ++k) cm[k] = colm[t * CW + k] | ((x & ((1 << L) - 1)) == 0 ? coarse_rows<L>(k) : 0u);
@@ -1027,7 +1049,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       const int f = t / E, y = t - f * E;
       unsigned int cm[CW];
 #pragma unroll
-      for (int k = 0; k < CW; ++k) cm[k] = ntc[f * CW + k];
+      for (int k = 0; k < CW; ++k) cm[k] = nw_all > 0 ? ntc[f * CW + k] : coarse_rows<L>(k);
       inverse_line_masked<WV, P, L, T>(tiles + win_in(f) + y * PW, 1, cm);
     }
     __syncthreads();
