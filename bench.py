@@ -610,15 +610,20 @@ def d3q19_section(torch, K, W, flush, bs, n_quality=256, quality_steps=1000, n_t
 
 
 def roofline_bytes(sim, w):
-    """Algorithmic bytes of one step launch: records of state n read, records
-    of state n+1 written, ghost rings read and written, patch tables, the
-    FP64 coarse-block sums."""
+    """Algorithmic bytes of one step launch: the records of state n read, the
+    records of state n+1 written (about as many), the ghost sources (D2Q9 on
+    BL5/3 patches: the eight neighbours' records of state n; the other
+    kernels: the ghost rings read and written), the patch tables (8 B read
+    and 8 B written per patch) and the FP64 coarse-block sums (8 B per field
+    and patch)."""
     st = sim.stats()
-    E = w["P"] + 1
-    ring = (12 * E + 4) * 4
     npatch = sim.npatch
     live = st["live_bytes"]
-    return 2 * live + 2 * npatch * ring + 2 * npatch * 8 + npatch * 9 * 8
+    if w["scheme"] == "d2q9" and w["wavelet"] == "bl53":
+        ghosts = 8 * live
+    else:
+        ghosts = 2 * npatch * (12 * (w["P"] + 1) + 4) * 4
+    return 2 * live + ghosts + 2 * npatch * 8 + npatch * 9 * 8
 
 
 def lifting_flops_per_line(P, L):

@@ -65,3 +65,22 @@ def test_max_over_ranks_with_two_gloo_processes():
         assert p.exitcode == 0
     got = sorted(q.get(timeout=10) for _ in range(2))
     assert got == [(0, 7.25), (1, 7.25)]
+
+
+class _FakeSim:
+    npatch = 1024
+
+    def stats(self):
+        return {"live_bytes": 1343488}
+
+
+def test_roofline_bytes_count_the_ghost_sources_of_each_kernel():
+    sys.path.insert(0, ROOT)
+    import bench
+    tables_sums = 2 * 1024 * 8 + 1024 * 9 * 8
+    # ring-free D2Q9 on BL5/3: own record read and written, eight neighbour records read
+    ringfree = bench.roofline_bytes(_FakeSim(), {"scheme": "d2q9", "wavelet": "bl53", "P": 64})
+    assert ringfree == 10 * 1343488 + tables_sums
+    # kernels with a ghost ring (Haar): the ring of 12 (P+1) + 4 FP32 values read and written per patch
+    ring = bench.roofline_bytes(_FakeSim(), {"scheme": "d2q9", "wavelet": "haar", "P": 64})
+    assert ring == 2 * 1343488 + 2 * 1024 * (12 * 65 + 4) * 4 + tables_sums
