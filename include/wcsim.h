@@ -170,7 +170,8 @@ wcs_status wcs_export_record(wcs_sim* sim, int64_t patch, void* dst, int64_t cap
  * Every call shares the array and overwrites it completely for the range it
  * exports; calls whose work overlaps on the GPU (several simulations on
  * different streams or host threads) race on it and must be serialised by
- * the caller.  Synchronises the simulation's stream; allocates nothing. */
+ * the caller.  The simulation's device must be the current device (else
+ * WCS_E_ARG).  Synchronises the simulation's stream; allocates nothing. */
 #define WCS_NOALLOC_SCRATCH_BYTES (16u << 20)
 wcs_status wcs_export_field_noalloc(wcs_sim* sim, int field, void* host_dst, int dtype);
 

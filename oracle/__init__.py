@@ -178,10 +178,15 @@ class OracleSim:
         return buf.raw[:n]
 
     def stats(self):
-        out = np.zeros(32, np.float64)
+        out = np.zeros(48, np.float64)
         _check(lib().orc_stats(self.h, _dp(out)))
         return {"coef_sums": out[:self.F].copy(), "nstep": int(out[20]), "time": out[21],
-                "shared_mismatch": int(out[22]), "compressed_bytes": int(out[23])}
+                "shared_mismatch": int(out[22]), "compressed_bytes": int(out[23]),
+                "coef_abs_sums": out[24:24 + self.F].copy(), "n_terms": self.npatch * self.n_coarse}
+
+    @property
+    def n_coarse(self):
+        return ((self.P >> self.L) + (1 if self.wavelet == "bl53" else 0)) ** 2
 
 
 class OracleRef:
@@ -415,10 +420,11 @@ class OracleSim3(_Run3):
         return out
 
     def stats(self):
-        out = np.zeros(32, np.float64)
+        out = np.zeros(48, np.float64)
         _check(lib().orc3_stats(self.h, _dp(out)))
         return {"coef_sums": out[:19].copy(), "nstep": int(out[20]), "shared_mismatch": int(out[22]),
-                "compressed_bytes": int(out[23])}
+                "compressed_bytes": int(out[23]), "coef_abs_sums": out[24:43].copy(),
+                "n_terms": self.npatch * ((self.P >> self.L) + 1) ** 3}
 
 
 class OracleRef3(_Run3):
@@ -427,3 +433,15 @@ class OracleRef3(_Run3):
     def __init__(self, nx, ny, nz, prec="f64", tau=0.8):
         self.shape = (nz, ny, nx)
         self.h = lib().orc3_ref_create(PREC[prec], nx, ny, nz, tau)
+
+
+def sums_agree(got, stats):
+    """True if GPU coarse-block sums equal the oracle's plain FP64 sums up to
+    the rounding of two summation orders: each order errs by at most
+    gamma_(n-1) * sum|terms| (n terms, gamma_k = k u / (1 - k u),
+    u = 2^-53), so two orders differ by at most twice that."""
+    u = 2.0 ** -53
+    k = stats["n_terms"] - 1
+    gamma = k * u / (1.0 - k * u)
+    want, ab = stats["coef_sums"], stats["coef_abs_sums"]
+    return bool(np.all(np.abs(np.asarray(got) - want) <= 2.0 * gamma * ab))

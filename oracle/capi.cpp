@@ -58,9 +58,12 @@ std::vector<const double*> fields4(const double* a, const double* b, const doubl
 }
 
 template <class T> void stats_of(Sim<T>& s, double* out) {
-  // out[0..F-1] coefficient-domain sums; out[20..] diagnostics
-  std::vector<double> cs = s.coef_sums();
+  // out[0..F-1] coefficient-domain sums; out[20..23] diagnostics;
+  // out[24..24+F) the sums of absolute terms
+  std::vector<double> ab;
+  std::vector<double> cs = s.coef_sums(&ab);
   for (int f = 0; f < s.F; ++f) out[f] = cs[f];
+  for (int f = 0; f < s.F; ++f) out[24 + f] = ab[f];
   out[20] = double(s.nstep);
   out[21] = s.time;
   out[22] = double(s.shared_mismatch);
@@ -519,12 +522,14 @@ int orc3_record(void* p, int64_t patch, uint8_t* dst, int64_t cap) {
 }
 
 // out[0..18] coefficient sums, out[20] steps, out[22] shared mismatches,
-// out[23] record bytes.
+// out[23] record bytes, out[24..42] the sums of absolute terms.
 int orc3_stats(void* p, double* out) {
   Handle3* h = static_cast<Handle3*>(p);
   return guard([&] {
-    const auto cs = h->s64 ? h->s64->coef_sums() : h->s32->coef_sums();
+    std::vector<double> ab;
+    const auto cs = h->s64 ? h->s64->coef_sums(&ab) : h->s32->coef_sums(&ab);
     for (int f = 0; f < 19; ++f) out[f] = cs[f];
+    for (int f = 0; f < 19; ++f) out[24 + f] = ab[f];
     out[20] = double(h->s64 ? h->s64->nstep : h->s32->nstep);
     out[22] = double(h->s64 ? h->s64->shared_mismatch : h->s32->shared_mismatch);
     out[23] = double(h->s64 ? h->s64->compressed_bytes() : h->s32->compressed_bytes());

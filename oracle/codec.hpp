@@ -9,9 +9,10 @@
 //    its own intent (coarser details should be harder to remove); the reading
 //    used here: with m_i = detail level on axis i (1 = finest; a coarse axis
 //    counts as L), constant tau = c, accumulation tau = c*2^-(sum(m_i-1)),
-//    capped tau = c*2^-(max(m_i)-1); the finest band gets c ("the threshold
-//    for the first level of details").  Parity unpinned for accumulation and
-//    capped (no number in the paper fixes them).
+//    capped tau = c*2^-(max(m_i)-1); the finest band gets c (the paper names
+//    c the threshold of the first detail level).  Parity unpinned for
+//    accumulation and capped: no number in the paper fixes them (the
+//    transport sweep of Sec. 3.2.2 compares the rules only in figures).
 //  * Sec. 2.3.1: the lossless stage stores only the surviving values plus
 //    their positions (the paper uses CSR).  Here positions are a bitmask in
 //    "row order" over the in-place nodes of the patch (the layout of the
@@ -22,9 +23,17 @@
 //    non-zero mask words; survivors are stored in bit order.
 //  * Quantisation (not in the paper): BF16 round-to-nearest-even with a
 //    per-band power-of-two scale, or int8 rint(d/s) with s = max|d|/127 per
-//    band.  Coefficients on a patch edge line (node index 0 or P along some
-//    axis, BL5/3 only) are never quantised: both patches sharing that line
-//    must decode it bit-identically so that the shared nodes agree.
+//    band.  The threshold of Sec. 2.2 is the method's error control: a
+//    dropped detail errs by less than tau.  A kept detail must not err by
+//    more, so int8 is used for a field's interior survivors only if, in every
+//    band that has some, half an int8 step is at most the band's threshold
+//    (0.5 * (max|d| / 127) <= tau, in FP32); otherwise that field's interior
+//    survivors are stored as BF16 with the power-of-two band scales (error
+//    at most 2^-8 |d|), and bit 0 of the band mask (the coarse band, which
+//    never has a scale) says so.  Coefficients on a patch edge line (node
+//    index 0 or P along some axis, BL5/3 only) are never quantised: both
+//    patches sharing that line must decode it bit-identically so that the
+//    shared nodes agree.
 //
 // Bands are tuples (c_x, c_y[, c_z]) of per-axis classes (0 = coarse sample,
 // m = detail of level m), numbered lexicographically with c_x slowest; band
@@ -35,7 +44,9 @@
 //   table    16 B per field : u32 offset, u32 nwords, u32 nedge, u32 nint
 //   field section at offset (16-byte aligned):
 //     coarse[n_c]            compute type T
-//     (BF16/I8 only) u32 bandmask[2], f32 scale[popcount(bandmask)]
+//     (BF16/I8 only) u32 bandmask[2], f32 scale[popcount(bandmask & ~1)]
+//                            (bit b: band b has interior survivors; bit 0,
+//                            I8 only: they are stored as BF16)
 //     presence[n_pw]         u32, bit w set iff mask word w is non-zero
 //     words[nwords]          u32, the non-zero mask words in order (bit p of
 //                            the mask = node p of the patch survives)
@@ -225,8 +236,14 @@ std::vector<uint8_t> encode_patch(const Layout& lay, const std::vector<std::vect
       p += sizeof(T);
     }
     std::vector<float> scale(lay.nb, 0.0f);
+    // I8: BF16 instead when half an int8 step would exceed a band's threshold
+    bool wide = false;
+    if (store == S_I8)
+      for (int b = 1; b < lay.nb; ++b)
+        if (bpresent[b] && double(0.5f * (bmax[b] / 127.0f)) > double(tau[b])) wide = true;
+    const bool as_bf16 = store == S_BF16 || wide;
     if (quant) {
-      uint64_t bm = 0;
+      uint64_t bm = wide ? 1u : 0u;
       for (int b = 1; b < lay.nb; ++b)
         if (bpresent[b]) bm |= (uint64_t(1) << b);
       put<uint32_t>(buf, p, uint32_t(bm & 0xffffffffu));
@@ -235,7 +252,7 @@ std::vector<uint8_t> encode_patch(const Layout& lay, const std::vector<std::vect
       for (int b = 1; b < lay.nb; ++b) {
         if (!bpresent[b]) continue;
         float s;
-        if (store == S_BF16) s = bmax[b] > 0.0f ? std::ldexp(1.0f, pow2_ceil_exp(bmax[b])) : 0.0f;
+        if (as_bf16) s = bmax[b] > 0.0f ? std::ldexp(1.0f, pow2_ceil_exp(bmax[b])) : 0.0f;
         else s = bmax[b] / 127.0f;
         scale[b] = s;
         put<float>(buf, p, s);
@@ -256,7 +273,7 @@ std::vector<uint8_t> encode_patch(const Layout& lay, const std::vector<std::vect
       const int b = lay.pos_band[pi];
       if (store == S_F64) { put<double>(buf, p, double(v)); p += 8; }
       else if (store == S_F32) { put<float>(buf, p, float(v)); p += 4; }
-      else if (store == S_BF16) {
+      else if (as_bf16) {
         const float s = scale[b];
         uint16_t q = 0;
         if (s != 0.0f) {
@@ -305,8 +322,13 @@ std::vector<std::vector<T>> decode_patch(const Layout& lay, const uint8_t* rec, 
     int64_t p = off;
     for (int64_t i = 0; i < lay.n_c; ++i) { c[lay.coarse_pos[i]] = get<T>(rec, nbytes, p); p += sizeof(T); }
     std::vector<float> scale(lay.nb, 0.0f);
+    bool as_bf16 = store == S_BF16;
     if (quant) {
       const uint64_t bm = uint64_t(get<uint32_t>(rec, nbytes, p)) | (uint64_t(get<uint32_t>(rec, nbytes, p + 4)) << 32);
+      if (bm & 1u) {
+        if (store != S_I8) throw std::runtime_error("record: BF16 flag on a non-int8 field");
+        as_bf16 = true;
+      }
       p += 8;
       for (int b = 1; b < lay.nb; ++b)
         if (bm & (uint64_t(1) << b)) { scale[b] = get<float>(rec, nbytes, p); p += 4; }
@@ -331,7 +353,7 @@ std::vector<std::vector<T>> decode_patch(const Layout& lay, const uint8_t* rec, 
       else {
         if (store == S_F64) { v = T(get<double>(rec, nbytes, pi)); pi += 8; }
         else if (store == S_F32) { v = T(get<float>(rec, nbytes, pi)); pi += 4; }
-        else if (store == S_BF16) { v = T(bf16_to_float(get<uint16_t>(rec, nbytes, pi)) * scale[b]); pi += 2; }
+        else if (as_bf16) { v = T(bf16_to_float(get<uint16_t>(rec, nbytes, pi)) * scale[b]); pi += 2; }
         else { v = T(float(get<int8_t>(rec, nbytes, pi)) * scale[b]); pi += 1; }
         ++ni;
       }

@@ -283,19 +283,18 @@ template <class T> struct Sim {
 
   // Mass (trapezoid-weighted sum) of every field from the coarse blocks alone:
   // the details carry no mass (eq. conservation), so 2^(L*dims) times the
-  // trapezoid sum of the coarse samples is the patch mass.  FP64, in one
-  // fixed order: coarse sample c (row-major) goes to partial sum c mod 32
-  // (added in increasing c), then the 32 partials are added pairwise
-  // (slot i += slot i+16, then +8, +4, +2, +1); patches are added in order.
-  std::vector<double> coef_sums() const {
-    std::vector<double> s(F, 0.0);
+  // trapezoid sum of the coarse samples is the patch mass.  A plain FP64 sum
+  // over the patches in order and their coarse samples in row-major order.
+  // abs_out (if given) receives the same sums of absolute terms, which bound
+  // the rounding of any other summation order.
+  std::vector<double> coef_sums(std::vector<double>* abs_out = nullptr) const {
+    std::vector<double> s(F, 0.0), a(F, 0.0);
     const int64_t nc1 = class_size(grid.wavelet, P, 0, L);
     const double scale = std::ldexp(1.0, 2 * L);
     for (int64_t pid = 0; pid < npatch(); ++pid) {
       const auto& r = rec[pid];
       for (int f = 0; f < F; ++f) {
         const int64_t off = get<uint32_t>(r.data(), int64_t(r.size()), 16 + 16 * f);
-        double part[32] = {0};
         for (int64_t c = 0; c < nc1 * nc1; ++c) {
           const int64_t iy = c / nc1, ix = c % nc1;
           double w = 1.0;
@@ -304,13 +303,13 @@ template <class T> struct Sim {
             if (iy == 0 || iy == nc1 - 1) w *= 0.5;
           }
           const T v = get<T>(r.data(), int64_t(r.size()), off + int64_t(sizeof(T)) * c);
-          part[c % 32] = part[c % 32] + w * double(v);
+          const double term = scale * (w * double(v));
+          s[f] += term;
+          a[f] += std::fabs(term);
         }
-        for (int o = 16; o >= 1; o /= 2)
-          for (int i = 0; i < o; ++i) part[i] = part[i] + part[i + o];
-        s[f] += part[0] * scale;
       }
     }
+    if (abs_out) *abs_out = a;
     return s;
   }
 

@@ -12,9 +12,9 @@
 //  * Haar (not in the paper; textbook unnormalised average/difference
 //    lifting on 2^j cells): d = b - a, s = a + d/2.
 //  * N-D: the 1-D transform is applied along x for every line, then along y,
-//    then z (Sec. 2.1.2, last paragraphs: "first all the rows and then all
-//    the columns").  This tensor reading is the one that reproduces the
-//    paper's 481 non-null coefficients of the 129x129 example.
+//    then z (Sec. 2.1.2, last paragraphs: every row is transformed before any
+//    column).  This tensor reading is the one that reproduces the paper's
+//    481 non-null coefficients of the 129x129 example.
 //
 // Coefficients stay at their node positions ("in place"): after L levels the
 // samples sit at positions multiple of 2^L and the level-m detail (m = 1 the

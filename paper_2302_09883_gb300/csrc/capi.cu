@@ -92,6 +92,7 @@ const std::vector<Kernel3Entry>& kernels3() {
 }  // namespace
 
 struct wcs_sim {
+  int device = 0;  // CUDA device current at creation (owns every buffer)
   int scheme = 0, wavelet = 0, prec = 0, store = 0, rule = 0, P = 0, L = 0;
   double eps = 0, tau = 1, cfl = 0.4, gamma = 1.4;
   int dims = 2;
@@ -297,6 +298,7 @@ static wcs_status create3(const wcs_grid* grid, int scheme, int patch, int level
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return fail(nullptr, WCS_E_CUDA, "device query failed");
   wcs_sim* s = new wcs_sim();
+  s->device = dev;
   s->dims = 3;
   s->k3 = ke;
   s->scheme = scheme;
@@ -475,6 +477,7 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
     }
   }
   wcs_sim* s = new wcs_sim();
+  cudaGetDevice(&s->device);
   s->ke = *ke;
   s->scheme = scheme;
   s->wavelet = opts->wavelet;
@@ -1095,12 +1098,18 @@ wcs_status wcs_autotune(const wcs_grid* grid, int scheme, const wcs_opts* opts, 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[WCS_NOALLOC_SCRATCH_BYTES];
 static void* g_noalloc_ptr[64];
 static bool g_noalloc_ready[64];
+static std::mutex g_noalloc_mu;  // first lookups from several host threads
 
 static wcs_status noalloc_scratch(wcs_sim* s, void** ptr) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(s, e, "cudaGetDevice");
+  // the address is per device: it must be that of the simulation's device
+  if (dev != s->device)
+    return fail(s, WCS_E_ARG, "wcs_export_field_noalloc: make the simulation's device (" + std::to_string(s->device) +
+                                  ") current before the call");
   if (dev < 0 || dev >= 64) return fail(s, WCS_E_ARG, "device index out of range for the staging table");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ready[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);

@@ -148,6 +148,27 @@ template <typename U> __device__ __forceinline__ void stg(unsigned char* p, U v)
 
 __device__ __forceinline__ unsigned long long dbl_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
+// Int8 fields whose band mask has bit 0 set store their interior survivors
+// as BF16 (half an int8 step would have exceeded a band's threshold, see the
+// scan phase); bit 0 is otherwise unused (the coarse band has no scale).
+template <int ST> __device__ __forceinline__ bool i8_wide(unsigned long long bm) { return ST == ST_I8 && (bm & 1ull) != 0ull; }
+// Index of band b's scale among the stored ones.
+__device__ __forceinline__ int band_scale_index(unsigned long long bm, int b) {
+  return __popcll(bm & ((1ull << b) - 1ull) & ~1ull);
+}
+// Dequantised interior survivor idx of a section whose values start at p.
+template <typename T, int ST> __device__ __forceinline__ T load_interior(const unsigned char* p, int idx, bool wide, float sc) {
+  typedef typename StoreType<ST>::type S;
+  if constexpr (ST == ST_F64 || ST == ST_F32) {
+    return T(ldr<S>(p + idx * int(sizeof(S))));
+  } else if constexpr (ST == ST_BF16) {
+    return T(__uint_as_float((unsigned int)ldr<unsigned short>(p + 2 * idx) << 16) * sc);
+  } else {
+    if (wide) return T(__uint_as_float((unsigned int)ldr<unsigned short>(p + 2 * idx) << 16) * sc);
+    return T(float(ldr<signed char>(p + idx)) * sc);
+  }
+}
+
 // Bits of word k of the rows y = 32k + b that are coarse (y a multiple of
 // 2^L).
 template <int L> __device__ __forceinline__ constexpr unsigned int coarse_rows(int k) {
@@ -257,8 +278,9 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
   unsigned long long bm = 0ull;
   if constexpr (C::QUANT) {
     bm = (unsigned long long)(unsigned int)e[5] | ((unsigned long long)(unsigned int)e[6] << 32);
-    p += 8 + 4 * __popcll(bm);
+    p += 8 + 4 * __popcll(bm & ~1ull);
   }
+  const bool wide = i8_wide<ST>(bm);
   const int p_pres = p, p_words = p + 4 * NPW;
   const int p_edge = (p_words + 4 * nwords + 7) & ~7, p_int = p_edge + nedge * int(sizeof(T));
   static_assert(NPW <= 32, "presence words fit in one warp");
@@ -327,15 +349,13 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
       if ((emk >> lane) & 1u) {
         v = ldr<T>(R + p_edge + int(bek + __popc(wk & emk & lt)) * int(sizeof(T)));
       } else {
-        const S qv = ldr<S>(R + p_int + int(bik + __popc(wk & ~emk & lt)) * C::SB);
-        if constexpr (ST == ST_F64 || ST == ST_F32) {
-          v = T(qv);
-        } else {
+        const int qi = int(bik + __popc(wk & ~emk & lt));
+        float sc = 0.0f;
+        if constexpr (C::QUANT) {
           const int b = node_class<L>(kx) * (L + 1) + node_class<L>(ky);
-          const float sc = ldr<float>(R + off + NC * int(sizeof(T)) + 8 + 4 * __popcll(bm & ((1ull << b) - 1ull)));
-          if constexpr (ST == ST_BF16) v = T(__uint_as_float((unsigned int)qv << 16) * sc);
-          else v = T(float(qv) * sc);
+          sc = ldr<float>(R + off + NC * int(sizeof(T)) + 8 + 4 * band_scale_index(bm, b));
         }
+        v = load_interior<T, ST>(R + p_int, qi, wide, sc);
       }
       rg[slot(kx, ky)] = v;
     }
@@ -495,7 +515,9 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
     for (int ix = lane; ix < NCN; ix += 32)
       if (!coarse_ix(sd, ix)) line_transform<WV, P, L, true, T>(reg + (task * NCN + ix) * E, 1);
   }
-  overlap((NQC + 31) / 32 * 32, 2);  // whole warps: a warp never runs both paths
+  // whole warps past the cone transforms collide; warps 0 .. 2F-1 may also
+  // have taken stored-word columns in the loop above and then run both
+  overlap((NQC + 31) / 32 * 32, 2);
   __syncthreads();
   for (int t = tid; t < F * E; t += NT) {  // west and east rows of one field in one thread
     const int f = t / E, y = t - f * E;
@@ -883,7 +905,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       if constexpr (C::QUANT) {
         bm0 = ldr<unsigned int>(R + p);
         bm1 = ldr<unsigned int>(R + p + 4);
-        p += 8 + 4 * (__popc(bm0) + __popc(bm1));
+        p += 8 + 4 * (__popc(bm0 & ~1u) + __popc(bm1));
       }
       const int nwords = int(ldr<unsigned int>(R + 16 + 16 * f + 4));
       const int nedge = int(ldr<unsigned int>(R + 16 + 16 * f + 8));
@@ -966,17 +988,13 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
           v = ldr<T>(R + fi[2] + int(pre_e[f * NW + j] + __popc(word & em & lt)) * int(sizeof(T)));
         } else {
           const int idx = pre_i[f * NW + j] + __popc(word & ~em & lt);
-          const S q = ldr<S>(R + fi[3] + idx * C::SB);
-          if constexpr (ST == ST_F64 || ST == ST_F32) {
-            v = T(q);
-          } else {
+          const unsigned long long bm = (unsigned long long)(unsigned int)fi[4] | ((unsigned long long)(unsigned int)fi[5] << 32);
+          float sc = 0.0f;
+          if constexpr (C::QUANT) {
             const int b = node_class<L>(kx) * (L + 1) + node_class<L>(ky);
-            const unsigned long long bm = (unsigned long long)(unsigned int)fi[4] | ((unsigned long long)(unsigned int)fi[5] << 32);
-            const int si = __popcll(bm & ((1ull << b) - 1ull));
-            const float sc = ldr<float>(R + fi[0] + NC * int(sizeof(T)) + 8 + 4 * si);
-            if constexpr (ST == ST_BF16) v = T(__uint_as_float((unsigned int)q << 16) * sc);
-            else v = T(float(q) * sc);
+            sc = ldr<float>(R + fi[0] + NC * int(sizeof(T)) + 8 + 4 * band_scale_index(bm, b));
           }
+          v = load_interior<T, ST>(R + fi[3], idx, i8_wide<ST>(bm), sc);
         }
         tiles[win_in(f) + ky * PW + kx] = v;
         atomicOr(colm + (f * E + kx) * CW + (ky >> 5), 1u << (ky & 31));
@@ -1411,6 +1429,18 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         }
       }
       __syncwarp();
+      // int8: if half a step (max|d|/127 / 2) exceeds the threshold of some
+      // band, the field's interior survivors go out as BF16 instead, so that
+      // no kept detail errs by more than a dropped one could (bit 0 of bm)
+      if constexpr (ST == ST_I8) {
+        for (int b0 = 0; b0 < NB; b0 += 32) {
+          const int b = b0 + lane;
+          const unsigned int m = (b > 0 && b < NB) ? bmax[f * NB + b] : 0u;
+          const bool over = m != 0u && 0.5f * (__uint_as_float(m - 1u) / 127.0f) > float(tau_i[b < NB ? b : 0]);
+          if (__any_sync(0xffffffffu, over)) bm = 1ull;
+        }
+      }
+      const bool wide = i8_wide<ST>(bm);
       for (int b0 = 0; b0 < NB; b0 += 32) {
         const int b = b0 + lane;
         const unsigned int m = (b < NB) ? bmax[f * NB + b] : 0u;
@@ -1418,7 +1448,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         bm |= (unsigned long long)bal << b0;
         if (b < NB && m != 0u) {
           const float mx = __uint_as_float(m - 1u);
-          if constexpr (ST == ST_BF16) {
+          if (ST == ST_BF16 || wide) {
             const int e = mx > 0.0f ? pow2_ceil_exp(mx) : 0;
             scl[f * NB + b] = mx > 0.0f ? exp2_int(e) : 0.0f;
             sinv[f * NB + b] = mx > 0.0f ? exp2_int(-e) : 0.0f;
@@ -1430,11 +1460,11 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     }
     if (lane == 0) {
       int p = NC * int(sizeof(T));
-      if constexpr (C::QUANT) p += 8 + 4 * __popcll(bm);
+      if constexpr (C::QUANT) p += 8 + 4 * __popcll(bm & ~1ull);
       const int p_pres = p;
       const int p_edge = (p_pres + 4 * NPW + 4 * int(cw) + 7) & ~7;
       const int p_int = p_edge + int(ce) * int(sizeof(T));
-      const int size = (p_int + int(ci) * C::SB + 15) & ~15;
+      const int size = (p_int + int(ci) * (i8_wide<ST>(bm) ? 2 : C::SB) + 15) & ~15;
       int* fi = finfo + 16 * f;
       fi[0] = size;
       fi[1] = p_pres;
@@ -1542,7 +1572,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         stg<unsigned int>(base, (unsigned int)(bm & 0xffffffffull));
         stg<unsigned int>(base + 4, (unsigned int)(bm >> 32));
       }
-      if ((bm >> b) & 1ull) stg<float>(base + 8 + 4 * __popcll(bm & ((1ull << b) - 1ull)), scl[t]);
+      if (b > 0 && ((bm >> b) & 1ull)) stg<float>(base + 8 + 4 * band_scale_index(bm, b), scl[t]);
     }
   }
   for (int t = warp; t < F * NPW; t += NWARP) {
@@ -1584,7 +1614,8 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         stg<T>(base + fi[2] + int(pre_e[f * NW + w] + __popc(word & em & lt)) * int(sizeof(T)), v);
       } else {
         const int idx = pre_i[f * NW + w] + __popc(word & ~em & lt);
-        unsigned char* dst = base + fi[3] + idx * C::SB;
+        const bool wide = ST == ST_I8 && (fi[7] & 1);  // int8 field stored as BF16 (scan phase)
+        unsigned char* dst = base + fi[3] + idx * (wide ? 2 : C::SB);
         T back;
         if constexpr (ST == ST_F64 || ST == ST_F32) {
           const S q = S(v);
@@ -1593,7 +1624,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         } else {
           const int b = node_class<L>(kx) * (L + 1) + node_class<L>(ky);
           const float sc = scl[f * NB + b];
-          if constexpr (ST == ST_BF16) {
+          if (ST == ST_BF16 || wide) {
             unsigned short q = 0;
             if (sc != 0.0f) q = __bfloat16_as_ushort(__float2bfloat16_rn(float(v) * sinv[f * NB + b]));
             stg<unsigned short>(dst, q);

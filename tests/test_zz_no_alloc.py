@@ -58,3 +58,40 @@ def test_noalloc_export_rejects_requests_above_the_staging_size():
     assert st == 0
     assert np.array_equal(got, sim.export_field(0))
     sim.close()
+
+
+def test_noalloc_export_3d_and_alternating_sizes():
+    # The 3-D decode goes through its own kernel; and the shared array keeps
+    # the previous call's bytes, so a smaller export right after a larger one
+    # (from another simulation) must still return exactly its own field.
+    from paper_2302_09883_gb300 import Sim3
+    n3 = 64
+    g = np.arange(n3, dtype=np.float64) * (2.0 * np.pi / n3)
+    z, y, x = np.meshgrid(g, g, g, indexing="ij")
+    u0 = 0.04
+    ux = u0 * np.sin(x) * np.cos(y) * np.cos(z)
+    uy = -u0 * np.cos(x) * np.sin(y) * np.cos(z)
+    s3 = Sim3(n3, n3, n3, 32, 3, 1e-6, store="bf16", tau=0.55)
+    s3.init_macro([np.ones_like(ux), ux, uy, np.zeros_like(ux)])
+    s3.step(2)
+    big = Sim("d2q9", "bl53", 512, 512, 64, 4, 1e-4, prec="f32", store="bf16", tau=0.6)
+    big.init_macro(inputs.shear_wave(512, seed=7))
+    small = Sim("d2q9", "bl53", 128, 128, 64, 4, 1e-4, prec="f32", store="bf16", tau=0.6)
+    small.init_macro(inputs.shear_wave(128, seed=8))
+    small.step(2)
+    for call in range(2):
+        out3 = np.empty((n3, n3, n3), np.float32)
+        st = B.lib().wcs_export_field_noalloc(s3.h, 5, out3.ctypes.data, 1)
+        assert st == 0, B.lib().wcs_last_error(s3.h)
+        assert np.array_equal(out3, s3.export_field(5, dtype=np.float32))
+        st, got = _noalloc(big, -1, 1)  # 9 x 512^2 floats = 9 MiB
+        assert st == 0
+        assert np.array_equal(got, big.export_field(-1, dtype=np.float32))
+        st, got = _noalloc(small, 4, 0)
+        assert st == 0
+        assert np.array_equal(got, small.export_field(4))
+        s3.step(1)
+        big.step(1)
+        small.step(1)
+    for s in (s3, big, small):
+        s.close()
