@@ -85,9 +85,17 @@ typedef struct {
   double cfl;             /* EULER2D: > 0: dt = cfl h / max(|u|+c, |v|+c) of
                              the current state; < 0: fixed step dt/h = -cfl */
   double gamma;           /* EULER2D ratio of specific heats */
-  double arena_factor;    /* arena capacity per buffer, as a fraction of the
-                             uncompressed state size in the compute type
-                             (0 = default 0.25) */
+  double arena_factor;    /* > 0: fixed arena capacity per buffer, as a
+                             fraction of the uncompressed state size in the
+                             compute type; an overflow is reported as
+                             WCS_E_ARENA_FULL.  0: automatic: after every
+                             encode of a whole state the capacity is set to
+                             1.5 x the live record bytes (+ 512 B per
+                             patch), synchronising calls keep it between
+                             1.25 x and 5 x the live bytes, and a step whose
+                             records overflowed is re-run with twice the
+                             capacity (not with a learned threshold, nor
+                             inside a batch) */
   void* cuda_stream;      /* cudaStream_t, NULL = default stream */
 } wcs_opts;
 
@@ -106,6 +114,9 @@ typedef struct {
   int64_t resident_bytes;    /* every device byte the simulation holds */
   int64_t uncompressed_bytes;/* one uncompressed copy of the state */
   uint32_t status;           /* sticky device status bits */
+  int64_t arena_capacity;    /* bytes of each of the two record arenas */
+  int64_t arena_reruns;      /* steps re-run after an arena overflow (auto
+                                arenas), since creation */
 } wcs_step_stats;
 
 /* Creates a simulation.  grid: cells per axis; patch: P (power of two,
@@ -145,12 +156,38 @@ wcs_status wcs_export_field(wcs_sim* sim, int field, void* dst, int dst_is_devic
  * the current state plus the ghost ring it needs and the patch table. */
 int64_t wcs_compressed_bytes(const wcs_sim* sim);
 
+/* Every byte of device memory the simulation holds: both record arenas at
+ * their capacity, rings, tables, control block, FP64 sums and (3-D) the
+ * per-SM scratch.  -1 for NULL. */
+int64_t wcs_resident_bytes(const wcs_sim* sim);
+
+/* Replaces the current state by dense values over the unique nodes (the
+ * layout of wcs_export_field: field = -1 takes F planes one after the
+ * other, else one field's plane) and encodes it again (threshold, quantise,
+ * records, ghost rings, FP64 sums and, EULER2D, the signal speed for the
+ * next step); the step count and time are kept.  dtype 0 = double, 1 =
+ * float, rounded to the compute type; src is a device pointer if
+ * src_is_device, else host.  Used to start from a given state, or to hand a
+ * state decoded elsewhere to the library (field = -1 also initialises a
+ * fresh simulation).  Takes one uncompressed copy of the state as temporary
+ * device memory (one field: the other fields are decoded into it first).
+ * Synchronises. */
+wcs_status wcs_import_field(wcs_sim* sim, int field, const void* src, int src_is_device, int dtype);
+
 /* FP64 diagnostics of the current state (synchronises). */
 wcs_status wcs_stats(wcs_sim* sim, wcs_step_stats* out);
 
+/* Detail coefficients kept in the current state (the survivors of the
+ * threshold, all patches and fields; coarse samples not counted), counted
+ * on the device from the records' tables.  Synchronises; -1 on error. */
+int64_t wcs_survivors(wcs_sim* sim);
+
 /* Copies the record of one patch of the current state (the byte format of
  * the oracle) to host memory.  *nbytes receives its size; if cap is too
- * small nothing is copied and WCS_E_ARG is returned. */
+ * small nothing is copied and WCS_E_ARG is returned.  A record holds at
+ * most 16 MiB - 1 bytes (the patch table packs offset << 24 | size); a
+ * larger one is reported as WCS_E_ARENA_FULL (P = 64 with 9 FP32 fields
+ * needs at most ~160 KB). */
 wcs_status wcs_export_record(wcs_sim* sim, int64_t patch, void* dst, int64_t cap, int64_t* nbytes);
 
 /* Export without device allocation.  Same result as wcs_export_field with a

@@ -34,6 +34,9 @@ def lib():
         L.orc_destroy.argtypes = [vp]
         L.orc_init_macro.argtypes = [vp, dp, dp, dp, dp]
         L.orc_step.argtypes = [vp, i64]
+        L.orc_import.argtypes = [vp, i32, dp]
+        L.orc_set_threads.restype = i32
+        L.orc_set_threads.argtypes = [i32]
         L.orc_export_field.argtypes = [vp, i32, dp]
         L.orc_export_all.argtypes = [vp, dp]
         L.orc_set_patch_eps.argtypes = [vp, C.POINTER(C.c_double)]
@@ -142,6 +145,11 @@ class OracleSim:
 
     def step(self, n=1):
         _check(lib().orc_step(self.h, n))
+
+    def import_field(self, f, values):
+        """Replace field f (-1: all, shape (F, ny, nx)) and re-encode."""
+        a = np.ascontiguousarray(values, np.float64)
+        _check(lib().orc_import(self.h, f, _dp(a)))
 
     def export_field(self, f):
         out = np.empty((self.G[1], self.G[0]), np.float64)
@@ -445,3 +453,8 @@ def sums_agree(got, stats):
     gamma = k * u / (1.0 - k * u)
     want, ab = stats["coef_sums"], stats["coef_abs_sums"]
     return bool(np.all(np.abs(np.asarray(got) - want) <= 2.0 * gamma * ab))
+
+
+def set_threads(n):
+    """Threads of the oracle's parallel loops (0: default); returns the count."""
+    return lib().orc_set_threads(int(n))

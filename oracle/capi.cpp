@@ -5,6 +5,7 @@
 // GPU kernel computes in).
 #include <cstdint>
 #include <cstring>
+#include <omp.h>
 #include <memory>
 #include <string>
 #include <vector>
@@ -108,6 +109,22 @@ int orc_init_macro(void* p, const double* a, const double* b, const double* c, c
   return guard([&] {
     if (h->s64) h->s64->init_macro(fields4(a, b, c, d));
     else h->s32->init_macro(fields4(a, b, c, d));
+  });
+}
+
+// Threads of the oracle's OpenMP loops (n <= 0: the runtime's default);
+// returns the number the next parallel loop will use.
+int orc_set_threads(int n) {
+  static const int dflt = omp_get_max_threads();
+  omp_set_num_threads(n > 0 ? n : dflt);
+  return omp_get_max_threads();
+}
+
+int orc_import(void* p, int field, const double* v) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    if (h->s64) h->s64->import_state(field, v);
+    else h->s32->import_state(field, v);
   });
 }
 

@@ -207,6 +207,30 @@ template <class T> struct Sim {
     time = 0;
   }
 
+  // Replaces field f (f = -1: every field, F planes one after the other) of
+  // the current state by dense values over the unique nodes (rounded to T)
+  // and encodes every patch again; step count and time are kept.
+  void import_state(int f, const double* v) {
+    std::vector<std::vector<T>> U;
+    if (f >= 0) U = decode_all();
+    else U.assign(F, std::vector<T>(grid.nodes()));
+    for (int q = 0; q < F; ++q) {
+      if (f >= 0 && q != f) continue;
+      const double* src = v + (f >= 0 ? 0 : int64_t(q) * grid.nodes());
+      for (int64_t g = 0; g < grid.nodes(); ++g) U[q][g] = T(src[g]);
+    }
+    for (int64_t pid = 0; pid < npatch(); ++pid) {
+      const int64_t px = pid % np[0], py = pid / np[0];
+      std::vector<std::vector<T>> loc(F, std::vector<T>(E * E));
+      for (int64_t y = 0; y < E; ++y)
+        for (int64_t x = 0; x < E; ++x) {
+          const int64_t g = gidx(1, py, y) * grid.G[0] + gidx(0, px, x);
+          for (int q = 0; q < F; ++q) loc[q][y * E + x] = U[q][g];
+        }
+      encode_patch_fields(pid, loc);
+    }
+  }
+
   std::vector<std::vector<T>> decode_all() {
     std::vector<std::vector<T>> U(F, std::vector<T>(grid.nodes()));
     std::vector<std::vector<uint8_t>> written(1, std::vector<uint8_t>(grid.nodes(), 0));

@@ -38,7 +38,7 @@ class StepStats(C.Structure):
     _fields_ = [("step", C.c_int64), ("time", C.c_double), ("field_sum", C.c_double * 19), ("mass", C.c_double),
                 ("momentum", C.c_double * 3), ("energy", C.c_double), ("smax", C.c_double),
                 ("live_bytes", C.c_int64), ("resident_bytes", C.c_int64), ("uncompressed_bytes", C.c_int64),
-                ("status", C.c_uint32)]
+                ("status", C.c_uint32), ("arena_capacity", C.c_int64), ("arena_reruns", C.c_int64)]
 
 
 _lib = None
@@ -61,6 +61,11 @@ def lib():
         L.wcs_export_field_noalloc.argtypes = [vp, i32, vp, i32]
         L.wcs_compressed_bytes.restype = i64
         L.wcs_compressed_bytes.argtypes = [vp]
+        L.wcs_resident_bytes.restype = i64
+        L.wcs_resident_bytes.argtypes = [vp]
+        L.wcs_import_field.argtypes = [vp, i32, vp, i32, i32]
+        L.wcs_survivors.restype = i64
+        L.wcs_survivors.argtypes = [vp]
         L.wcs_stats.argtypes = [vp, C.POINTER(StepStats)]
         L.wcs_export_record.argtypes = [vp, i64, vp, i64, C.POINTER(i64)]
         L.wcs_shape.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64), C.POINTER(i64)]

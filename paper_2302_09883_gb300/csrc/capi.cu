@@ -111,7 +111,12 @@ struct wcs_sim {
   KernelEntry ke;
   cudaStream_t stream = nullptr;
   unsigned char* arena[2] = {nullptr, nullptr};
-  unsigned long long cap = 0;
+  unsigned long long cap = 0;   // bytes of each arena
+  bool auto_arena = false;      // arenas sized from the measured live bytes
+  bool in_batch = false;        // a batch holds the arena pointers: no resizing
+  int64_t reruns = 0;           // steps re-run after an overflow
+  unsigned long long* cnt = nullptr;  // survivor counter (wcs_survivors)
+  unsigned long long cap_min = 0;
   unsigned long long* tab[2] = {nullptr, nullptr};
   void* ring[2] = {nullptr, nullptr};
   wcs::Ctl* ctl = nullptr;
@@ -152,6 +157,38 @@ static wcs_status dalloc(wcs_sim* s, void** p, size_t bytes) {
     return fail(s, WCS_E_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
   }
   s->resident += int64_t(bytes);
+  return WCS_OK;
+}
+
+// ---------------------------------------------------------------- arenas
+// Both arenas have capacity s->cap.  In auto mode (arena_factor 0) the
+// capacity follows the measured live bytes: after an encode of a whole
+// state it is set to live + live/2 + 512 B per patch, a synchronising call
+// grows it when the live bytes pass 80 % of it or shrinks it when they fall
+// under 20 %, and a step that overflowed anyway is re-run from its intact
+// input state with twice the capacity (wcs_sync).
+static unsigned long long arena_headroom(const wcs_sim* s, unsigned long long live) {
+  const unsigned long long want = live + live / 2 + (unsigned long long)s->npatch * 512ull;
+  return (std::max(want, s->cap_min) + 255ull) / 256ull * 256ull;
+}
+
+// New capacity for both arenas; arena `keep_arena` keeps its first
+// keep_bytes bytes (the records of the current state, whose offsets in the
+// patch table stay valid).  Synchronises the stream.
+static wcs_status resize_arenas(wcs_sim* s, unsigned long long cap, int keep_arena, unsigned long long keep_bytes) {
+  CK(cudaStreamSynchronize(s->stream));
+  for (int b = 0; b < 2; ++b) {
+    unsigned char* na = nullptr;
+    const wcs_status st = dalloc(s, (void**)&na, cap);
+    if (st != WCS_OK) return st;
+    if (b == keep_arena && keep_bytes > 0)
+      CK(cudaMemcpyAsync(na, s->arena[b], std::min(keep_bytes, cap), cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    cudaFree(s->arena[b]);
+    s->resident -= int64_t(s->cap);
+    s->arena[b] = na;
+  }
+  s->cap = cap;
   return WCS_OK;
 }
 
@@ -361,7 +398,11 @@ static wcs_status create3(const wcs_grid* grid, int scheme, int patch, int level
 
   wcs_status st;
   const size_t state_bytes = size_t(19) * size_t(s->G[0]) * size_t(s->G[1]) * size_t(s->G[2]) * 4;
-  const double factor = opts->arena_factor > 0 ? opts->arena_factor : 0.25;
+  // fixed fraction of the uncompressed state, or (0) a provisional eighth
+  // that the first encode resizes to the measured live bytes
+  s->auto_arena = !(opts->arena_factor > 0);
+  const double factor = s->auto_arena ? 0.125 : opts->arena_factor;
+  s->cap_min = (unsigned long long)s->npatch * 4096ull;
   s->cap = (unsigned long long)(std::max(double(state_bytes) * factor, double(s->npatch) * 65536.0) + 255) / 256 * 256;
   for (int b = 0; b < 2; ++b) {
     if ((st = dalloc(s, (void**)&s->arena[b], s->cap)) != WCS_OK) goto bad;
@@ -389,31 +430,83 @@ bad:
   return st;
 }
 
+// Encodes a whole state into arena nstep % 2 (MODE_INIT): the equilibrium
+// of macroscopic fields (macro, device pointers) or a dense state (state,
+// device, dtype 0 double / 1 float).  The step count and time are kept; the
+// arena's cursor restarts.  In auto-arena mode an overflow grows the arenas
+// and encodes again, and the capacity is then fitted to the live bytes.
+static wcs_status encode_state(wcs_sim* s, const double* const* macro, const void* state, int dtype) {
+  const int cur = int(s->nstep % 2);
+  for (int attempt = 0;; ++attempt) {
+    wcs::Ctl c;
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+    c.cursor[cur] = 0ull;
+    c.smax[s->nstep % 3] = 0ull;
+    c.status = 0u;
+    c.err_step = -1;
+    CK(cudaMemcpy(s->ctl, &c, sizeof(c), cudaMemcpyHostToDevice));
+    if (s->dims == 3) {
+      wcs::Patch3Args a = base_args3(s);
+      for (int q = 0; q < 4; ++q) a.macro[q] = macro ? macro[q] : nullptr;
+      a.state = state;
+      a.state_dtype = dtype;
+      a.step = -1;
+      a.arena_out = s->arena[cur];
+      a.tab_out = s->tab[cur];
+      a.ring_out = static_cast<float*>(s->ring[cur]);
+      a.cur_out = cur;
+      CK(s->k3->launch(wcs::MODE_INIT, a, s->grid3, s->stream));
+    } else {
+      wcs::PatchArgs a = base_args(s);
+      for (int q = 0; q < 4; ++q) a.macro[q] = macro ? macro[q] : nullptr;
+      a.state = state;
+      a.state_dtype = dtype;
+      a.step = -1;
+      a.arena_out = s->arena[cur];
+      a.tab_out = s->tab[cur];
+      a.ring_out = s->ring[cur];
+      a.cur_out = cur;
+      a.smax_wr = int(s->nstep % 3);
+      CK(s->ke.launch(wcs::MODE_INIT, a, s->npatch, s->stream));
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+    if (!(c.status & wcs::STAT_ARENA_FULL) || !s->auto_arena || attempt >= 8) break;
+    wcs_status st;
+    if ((st = resize_arenas(s, s->cap * 2, -1, 0)) != WCS_OK) return st;
+  }
+  if (s->auto_arena) {
+    wcs::Ctl c;
+    CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+    if (!c.status) {
+      const unsigned long long want = arena_headroom(s, c.cursor[cur]);
+      if (want != s->cap) return resize_arenas(s, want, cur, c.cursor[cur]);
+    }
+  }
+  return WCS_OK;
+}
+
 static wcs_status init3(wcs_sim* s, const double* const* fields, int nfields, int src_is_device) {
   if (nfields < 4) return fail(s, WCS_E_ARG, "D3Q19 init needs rho, u_x, u_y, u_z");
   const size_t vol = size_t(s->G[0]) * size_t(s->G[1]) * size_t(s->G[2]);
   double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
-  wcs::Patch3Args a = base_args3(s);
+  const double* mac[4];
   for (int q = 0; q < 4; ++q) {
     if (src_is_device) {
-      a.macro[q] = fields[q];
+      mac[q] = fields[q];
     } else {
       CK(cudaMalloc(&tmp[q], vol * 8));
       CK(cudaMemcpyAsync(tmp[q], fields[q], vol * 8, cudaMemcpyHostToDevice, s->stream));
-      a.macro[q] = tmp[q];
+      mac[q] = tmp[q];
     }
   }
   CK(cudaMemsetAsync(s->ctl, 0, sizeof(wcs::Ctl), s->stream));
-  a.step = -1;
-  a.arena_out = s->arena[0];
-  a.tab_out = s->tab[0];
-  a.ring_out = static_cast<float*>(s->ring[0]);
-  a.cur_out = 0;
-  CK(s->k3->launch(wcs::MODE_INIT, a, s->grid3, s->stream));
-  CK(cudaStreamSynchronize(s->stream));
+  s->nstep = 0;
+  const wcs_status st = encode_state(s, mac, nullptr, 0);
   for (int q = 0; q < 4; ++q)
     if (tmp[q]) cudaFree(tmp[q]);
-  s->nstep = 0;
+  if (st != WCS_OK) return st;
   s->inited = true;
   return WCS_OK;
 }
@@ -523,7 +616,11 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
 
   wcs_status st;
   const size_t state_bytes = size_t(s->F) * size_t(s->G[0]) * size_t(s->G[1]) * s->tsize;
-  const double factor = opts->arena_factor > 0 ? opts->arena_factor : 0.25;
+  // fixed fraction of the uncompressed state, or (0) a provisional quarter
+  // that the first encode resizes to the measured live bytes
+  s->auto_arena = !(opts->arena_factor > 0);
+  const double factor = s->auto_arena ? 0.25 : opts->arena_factor;
+  s->cap_min = (unsigned long long)s->npatch * 1024ull;
   s->cap = (unsigned long long)(std::max(double(state_bytes) * factor, double(s->npatch) * 4096.0) + 255) / 256 * 256;
   for (int b = 0; b < 2; ++b) {
     if ((st = dalloc(s, (void**)&s->arena[b], s->cap)) != WCS_OK) goto bad;
@@ -618,6 +715,7 @@ void wcs_destroy(wcs_sim* s) {
   cudaFree(s->bfactor);
   cudaFree(s->scratch);
   cudaFree(s->rbuf);
+  cudaFree(s->cnt);
   delete s;
 }
 
@@ -653,28 +751,22 @@ wcs_status wcs_init_macro(wcs_sim* s, const double* const* fields, int nfields, 
   if (nfields < need) return fail(s, WCS_E_ARG, "init needs " + std::to_string(need) + " macroscopic fields");
   const size_t plane = size_t(s->G[0]) * size_t(s->G[1]);
   double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
-  wcs::PatchArgs a = base_args(s);
+  const double* mac[4] = {nullptr, nullptr, nullptr, nullptr};
   for (int q = 0; q < need; ++q) {
     if (src_is_device) {
-      a.macro[q] = fields[q];
+      mac[q] = fields[q];
     } else {
       CK(cudaMalloc(&tmp[q], plane * 8));
       CK(cudaMemcpyAsync(tmp[q], fields[q], plane * 8, cudaMemcpyHostToDevice, s->stream));
-      a.macro[q] = tmp[q];
+      mac[q] = tmp[q];
     }
   }
   CK(cudaMemsetAsync(s->ctl, 0, sizeof(wcs::Ctl), s->stream));
-  a.step = -1;
-  a.arena_out = s->arena[0];
-  a.tab_out = s->tab[0];
-  a.ring_out = s->ring[0];
-  a.cur_out = 0;
-  a.smax_wr = 0;
-  CK(s->ke.launch(wcs::MODE_INIT, a, s->npatch, s->stream));
-  CK(cudaStreamSynchronize(s->stream));
+  s->nstep = 0;
+  const wcs_status st = encode_state(s, mac, nullptr, 0);
   for (int q = 0; q < 4; ++q)
     if (tmp[q]) cudaFree(tmp[q]);
-  s->nstep = 0;
+  if (st != WCS_OK) return st;
   s->inited = true;
   return wcs_sync(s);
 }
@@ -722,6 +814,32 @@ wcs_status wcs_sync(wcs_sim* s) {
   CK(cudaStreamSynchronize(s->stream));
   wcs::Ctl c;
   CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+  // Auto arenas: a step k whose records did not fit left its input state k
+  // intact in arena k % 2 and every later step of the call returned at once;
+  // undo what step k did to the control block (its output cursor, the
+  // input arena's cursor and the time it advanced), double the capacity and
+  // run the steps again.  Not with a learned threshold (its per-patch eps
+  // of state k were overwritten in place) nor inside a batch (which holds
+  // the arena pointers).
+  for (int attempt = 0; c.status == wcs::STAT_ARENA_FULL && s->auto_arena && !s->mlp && !s->in_batch && attempt < 8;
+       ++attempt) {
+    const int64_t target = s->nstep, k = c.err_step;
+    if (k < 0 || k >= target) break;
+    const int in = int(k % 2), out = 1 - in;
+    c.cursor[in] = c.live[in];
+    c.cursor[out] = 0ull;
+    if (s->dims == 2) c.time = c.time_in[in];
+    c.status = 0u;
+    c.err_step = -1;
+    wcs_status st;
+    if ((st = resize_arenas(s, s->cap * 2, in, c.cursor[in])) != WCS_OK) return st;
+    CK(cudaMemcpy(s->ctl, &c, sizeof(c), cudaMemcpyHostToDevice));
+    s->nstep = k;
+    s->reruns += target - k;
+    if ((st = wcs_step(s, target - k)) != WCS_OK) return st;
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+  }
   if (c.status) {
     // the state stays at the input of the failed step
     if (c.err_step >= 0 && c.err_step < s->nstep) s->nstep = c.err_step;
@@ -730,6 +848,12 @@ wcs_status wcs_sync(wcs_sim* s) {
                                            " (capacity " + std::to_string(s->cap) + " bytes)");
     if (c.status & wcs::STAT_NAN) return fail(s, WCS_E_NAN, "non-finite coefficient at step " + std::to_string(c.err_step));
     return fail(s, WCS_E_CUDA, "device status " + std::to_string(c.status));
+  }
+  if (s->auto_arena && !s->in_batch && s->inited) {  // keep the capacity near the live bytes
+    const int cur = int(s->nstep % 2);
+    const unsigned long long live = c.cursor[cur];
+    if (live * 5 > s->cap * 4 || (live * 5 < s->cap && s->cap > arena_headroom(s, live)))
+      return resize_arenas(s, arena_headroom(s, live), cur, live);
   }
   return WCS_OK;
 }
@@ -775,6 +899,99 @@ int64_t wcs_compressed_bytes(const wcs_sim* s) {
   return live + int64_t(s->npatch) * s->ring_vals * int64_t(s->tsize) + int64_t(s->npatch) * 8;
 }
 
+int64_t wcs_resident_bytes(const wcs_sim* s) { return s ? s->resident : -1; }
+
+}  // extern "C"
+
+// Kept detail coefficients of every record: the nedge + nint words of each
+// field's table row (thread per patch), summed into *out.
+__global__ void count_survivors(const unsigned char* arena, const unsigned long long* tab, int npatch, int F,
+                                unsigned long long* out) {
+  unsigned long long k = 0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npatch; p += gridDim.x * blockDim.x) {
+    const unsigned char* r = arena + (tab[p] >> 24);
+    for (int f = 0; f < F; ++f) {
+      const uint4 row = *reinterpret_cast<const uint4*>(r + 16 + 16 * f);
+      k += row.z + row.w;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) k += __shfl_down_sync(0xffffffffu, k, o);
+  if ((threadIdx.x & 31) == 0 && k) atomicAdd(out, k);
+}
+
+extern "C" int64_t wcs_survivors(wcs_sim* s) {
+  if (!s || !s->inited || wcs_sync(s) != WCS_OK) return -1;
+  if (!s->cnt && dalloc(s, (void**)&s->cnt, 8) != WCS_OK) return -1;
+  const int cur = int(s->nstep % 2);
+  unsigned long long k = 0;
+  if (cudaMemsetAsync(s->cnt, 0, 8, s->stream) != cudaSuccess) return -1;
+  count_survivors<<<std::min((s->npatch + 255) / 256, 1024), 256, 0, s->stream>>>(s->arena[cur], s->tab[cur], s->npatch,
+                                                                                   s->F, s->cnt);
+  if (cudaMemcpyAsync(&k, s->cnt, 8, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return -1;
+  return int64_t(k);
+}
+
+// n values from src (dtype sdt: 0 double, 1 float) to dst (dtype ddt).
+__global__ void convert_values(const void* src, int sdt, void* dst, int ddt, size_t n) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    const double v = sdt == 0 ? static_cast<const double*>(src)[i] : double(static_cast<const float*>(src)[i]);
+    if (ddt == 0) static_cast<double*>(dst)[i] = v;
+    else static_cast<float*>(dst)[i] = float(v);
+  }
+}
+
+extern "C" {
+
+wcs_status wcs_import_field(wcs_sim* s, int field, const void* src, int src_is_device, int dtype) {
+  if (!s || !src || field < -1 || field >= s->F || (dtype != 0 && dtype != 1)) return WCS_E_ARG;
+  if (!s->inited && field >= 0) return fail(s, WCS_E_ARG, "import of one field before the state exists");
+  if (s->inited) {
+    const wcs_status st = wcs_sync(s);
+    if (st != WCS_OK) return st;
+  }
+  const size_t plane = size_t(s->G[0]) * size_t(s->G[1]) * size_t(s->G[2]);
+  const int bdt = s->tsize == 8 ? 0 : 1;  // the state in its compute type: exact
+  const size_t bsz = s->tsize, ssz = dtype == 0 ? 8 : 4;
+  const size_t nin = plane * (field < 0 ? size_t(s->F) : 1);
+  void* buf = nullptr;
+  void* stage = nullptr;
+  if (cudaMalloc(&buf, plane * s->F * bsz) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(s, WCS_E_OOM, "import buffer of " + std::to_string(plane * s->F * bsz) + " bytes");
+  }
+  wcs_status st = WCS_OK;
+  const void* from = src;
+  cudaError_t e = cudaSuccess;
+  if (field >= 0) st = export_dev(s, -1, buf, bdt);  // the other fields as they are
+  if (st == WCS_OK && !src_is_device) {
+    e = cudaMalloc(&stage, nin * ssz);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stage, src, nin * ssz, cudaMemcpyHostToDevice, s->stream);
+    from = stage;
+  }
+  if (st == WCS_OK && e == cudaSuccess) {
+    void* to = static_cast<unsigned char*>(buf) + (field < 0 ? 0 : size_t(field) * plane * bsz);
+    const int nb = int(std::min<size_t>((nin + 255) / 256, 4096));
+    convert_values<<<nb, 256, 0, s->stream>>>(from, dtype, to, bdt, nin);
+    e = cudaGetLastError();
+  }
+  if (st == WCS_OK && e == cudaSuccess) {
+    if (!s->inited) {
+      e = cudaMemsetAsync(s->ctl, 0, sizeof(wcs::Ctl), s->stream);
+      s->nstep = 0;
+    }
+    if (e == cudaSuccess) st = encode_state(s, nullptr, buf, bdt);
+  }
+  cudaStreamSynchronize(s->stream);
+  if (stage) cudaFree(stage);
+  cudaFree(buf);
+  if (st != WCS_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(s, e, "import");
+  s->inited = true;
+  return wcs_sync(s);
+}
+
 wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
   if (!s || !o) return WCS_E_ARG;
   std::memset(o, 0, sizeof(*o));
@@ -816,6 +1033,8 @@ wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
   o->resident_bytes = s->resident;
   o->uncompressed_bytes = int64_t(s->F) * s->G[0] * s->G[1] * s->G[2] * int64_t(s->tsize);
   o->status = c.status;
+  o->arena_capacity = int64_t(s->cap);
+  o->arena_reruns = s->reruns;
   return WCS_OK;
 }
 
@@ -857,6 +1076,7 @@ struct wcs_batch {
 
 static void batch_free(wcs_batch* b) {
   if (!b) return;
+  for (wcs_sim* s : b->sims) s->in_batch = false;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
@@ -907,6 +1127,24 @@ wcs_status wcs_batch_create(wcs_sim* const* sims, int nsims, wcs_batch** out) {
       batch_free(b);
       return WCS_E_ARG;
     }
+    if (s->auto_arena) {  // the batch holds the arena pointers: room for growth now, no resizing later
+      const int cur = int(s->nstep % 2);
+      wcs::Ctl c;
+      if (cudaStreamSynchronize(s->stream) != cudaSuccess ||
+          cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_err = "batch: control block read failed";
+        batch_free(b);
+        return WCS_E_CUDA;
+      }
+      const unsigned long long want = arena_headroom(s, 2 * c.cursor[cur]);
+      if (want > s->cap && resize_arenas(s, want, cur, c.cursor[cur]) != WCS_OK) {
+        g_create_err = "batch: arena resize failed: " + s->err;
+        batch_free(b);
+        return WCS_E_OOM;
+      }
+    }
+    s->in_batch = true;
     b->sims.push_back(s);
     wcs_batch::Group* g = nullptr;
     for (auto& gg : b->groups)

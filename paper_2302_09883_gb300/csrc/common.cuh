@@ -26,6 +26,9 @@ struct Ctl {
   double time;                   // physical time (Euler) or step count
   unsigned int status;
   int err_step;
+  double time_in[2];             // time of the input state of the last step
+                                 // that read arena k (a step lost to an arena
+                                 // overflow is re-run from it)
 };
 
 template <int S> struct StoreType;

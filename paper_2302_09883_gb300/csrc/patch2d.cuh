@@ -60,6 +60,9 @@ struct PatchArgs {
   double gm1_64;
   long long ncell_x;            // cells along x (time accounting)
   const double* macro[4];       // MODE_INIT inputs, [G1][G0]
+  const void* state;            // MODE_INIT from a dense state instead
+                                // (F planes [G1][G0]; null: macro fields)
+  int state_dtype;              // 0 double, 1 float
   long long G0, G1;
   void* dense;                  // MODE_EXPORT output
   int dense_dtype;              // 0 double, 1 float
@@ -881,6 +884,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       if (pid == 0 && tid == 0) {
         a.ctl->live[a.cur_rst] = a.ctl->cursor[a.cur_rst];
         a.ctl->cursor[a.cur_rst] = 0ull;
+        a.ctl->time_in[a.cur_rst] = a.ctl->time;
         if constexpr (SCH == SCH_EULER2D) {
           const double smax = __longlong_as_double((long long)a.ctl->smax[a.smax_rd]);
           a.ctl->time += (a.cfl > 0 ? a.cfl / smax : -a.cfl) / double(a.ncell_x);
@@ -1144,7 +1148,13 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       if (a.per_y) gy %= a.G1;
       const long long g = gy * a.G0 + gx;
       T sv[9];
-      if constexpr (SCH == SCH_D2Q9) {
+      if (a.state) {  // a given state (import): the values themselves
+        const long long plane = a.G0 * a.G1;
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+          sv[f] = a.state_dtype == 0 ? T(reinterpret_cast<const double*>(a.state)[f * plane + g])
+                                     : T(reinterpret_cast<const float*>(a.state)[f * plane + g]);
+      } else if constexpr (SCH == SCH_D2Q9) {
         d2q9_equilibrium<T>(T(a.macro[0][g]), T(a.macro[1][g]), T(a.macro[2][g]), sv);
       } else {
         euler_cons<T>(T(a.macro[0][g]), T(a.macro[1][g]), T(a.macro[2][g]), T(a.macro[3][g]), gm1, sv);
@@ -1593,7 +1603,8 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     const int f = tid, *fi = finfo + 16 * f;
     unsigned char* base = O + fi[9];
     for (int p = fi[1] + 4 * NPW + 4 * fi[4]; p < fi[2]; ++p) base[p] = 0;
-    for (int p = fi[3] + fi[6] * C::SB; p < fi[0]; ++p) base[p] = 0;
+    const int sb = (ST == ST_I8 && (fi[7] & 1)) ? 2 : C::SB;  // int8 field stored as BF16
+    for (int p = fi[3] + fi[6] * sb; p < fi[0]; ++p) base[p] = 0;
   }
   for (int f = 0; f < F && nw_all > 0; ++f) {
     const int* fi = finfo + 16 * f;

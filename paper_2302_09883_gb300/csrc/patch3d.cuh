@@ -140,6 +140,9 @@ struct Patch3Args {
   unsigned char* rbuf;        // per CTA: one record under construction
   unsigned long long slot_floats, slot_rbytes;
   const double* macro[4];     // INIT: rho, ux, uy, uz on the global node grid
+  const void* state;          // INIT from a dense state instead (19 planes
+                              // [z][y][x]; null: macro fields)
+  int state_dtype;            // 0 double, 1 float
   void* dense;                // EXPORT: [field][z][y][x] over the global nodes
   int dense_dtype;            // 0 double, 1 float
   int field_sel;              // EXPORT: one field or -1 for all
@@ -456,7 +459,15 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
       const long long gx = (px * P + x) % a.G0, gy = (py * P + y) % a.G1, gz = (pzc * P + z) % a.G2;
       const size_t g = (size_t(gz) * a.G1 + gy) * a.G0 + gx;
       T fe[19];
-      d3q19_equilibrium<T>(T(a.macro[0][g]), T(a.macro[1][g]), T(a.macro[2][g]), T(a.macro[3][g]), fe);
+      if (a.state) {  // a given state (import): the values themselves
+        const size_t vol = size_t(a.G0) * size_t(a.G1) * size_t(a.G2);
+#pragma unroll
+        for (int q = 0; q < 19; ++q)
+          fe[q] = a.state_dtype == 0 ? T(reinterpret_cast<const double*>(a.state)[q * vol + g])
+                                     : T(reinterpret_cast<const float*>(a.state)[q * vol + g]);
+      } else {
+        d3q19_equilibrium<T>(T(a.macro[0][g]), T(a.macro[1][g]), T(a.macro[2][g]), T(a.macro[3][g]), fe);
+      }
 #pragma unroll
       for (int q = 0; q < 19; ++q) Sc[size_t(q) * EG3 + sidx(x, y, z)] = fe[q];
     }

@@ -14,7 +14,7 @@ WORKLOADS = {
                           store="f64", rule="const", tau=0.8, steps=100, init="bump"),
     # D2Q9 BGK, 2048^2 periodic, BL5/3 patches of 64 cells, 4 levels, FP32
     # compute, BF16 details with per-band scale, shear wave + noise.
-    "d2q9_bl53_2048": dict(scheme="d2q9", wavelet="bl53", n=2048, P=64, L=4, eps=1e-4, prec="f32",
+    "d2q9_bl53_2048": dict(scheme="d2q9", wavelet="bl53", n=2048, P=64, L=4, eps=1e-3, prec="f32",
                            store="bf16", rule="const", tau=0.6, steps=2000, init="shear"),
     # 2-D Euler, Rusanov, 4096 cells (4097 nodes) per axis, outflow, BL5/3
     # patches of 64, 4 levels, FP32 compute, int8 details.

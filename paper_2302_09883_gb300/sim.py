@@ -60,7 +60,7 @@ class Sim:
     """One compressed-patch simulation on the current CUDA device."""
 
     def __init__(self, scheme, wavelet, nx, ny, P, L, eps, prec="f32", store="bf16", rule="const",
-                 periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, arena_factor=0.25, stream=None):
+                 periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, arena_factor=0.0, stream=None):
         self.scheme = scheme
         o = B.Opts()
         o.wavelet, o.rule, o.detail_store, o.compute = B.WAVELET[wavelet], B.RULE[rule], B.STORE[store], B.PREC[prec]
@@ -109,13 +109,44 @@ class Sim:
     def compressed_bytes(self):
         return B.lib().wcs_compressed_bytes(self.h)
 
+    def resident_bytes(self):
+        return B.lib().wcs_resident_bytes(self.h)
+
+    def survivors(self):
+        """Detail coefficients kept in the current state (all patches, fields)."""
+        k = B.lib().wcs_survivors(self.h)
+        if k < 0:
+            B.check(6, self.h)
+        return k
+
+    def import_field(self, f, values):
+        """Replace field f (-1: all fields, shape (F, ...)) of the current
+        state by dense values (numpy float64/float32, or a CUDA tensor) and
+        re-encode."""
+        if hasattr(values, "data_ptr"):
+            import torch
+            t = values.contiguous()
+            dt = 0 if t.dtype == torch.float64 else 1
+            if dt == 1 and t.dtype != torch.float32:
+                t = t.to(torch.float32)
+            if t.is_cuda:
+                torch.cuda.synchronize()
+            B.check(B.lib().wcs_import_field(self.h, f, t.data_ptr(), 1 if t.is_cuda else 0, dt), self.h)
+            return
+        a = np.ascontiguousarray(values)
+        if a.dtype != np.float32:
+            a = a.astype(np.float64)
+        dt = 0 if a.dtype == np.float64 else 1
+        B.check(B.lib().wcs_import_field(self.h, f, a.ctypes.data, 0, dt), self.h)
+
     def stats(self):
         s = B.StepStats()
         B.check(B.lib().wcs_stats(self.h, C.byref(s)), self.h)
         return {"step": s.step, "time": s.time, "field_sum": np.array(s.field_sum[:self.F]), "mass": s.mass,
                 "momentum": np.array(s.momentum[:2]), "energy": s.energy, "smax": s.smax,
                 "live_bytes": s.live_bytes, "resident_bytes": s.resident_bytes,
-                "uncompressed_bytes": s.uncompressed_bytes, "status": s.status}
+                "uncompressed_bytes": s.uncompressed_bytes, "status": s.status,
+                "arena_capacity": s.arena_capacity, "arena_reruns": s.arena_reruns}
 
     def record(self, p):
         n = C.c_int64()
@@ -133,7 +164,7 @@ class Sim3(Sim):
     """One compressed-patch D3Q19 simulation on a periodic (nz, ny, nx) grid
     (folded BL5/3, FP32 compute)."""
 
-    def __init__(self, nx, ny, nz, P, L, eps, store="bf16", rule="const", tau=0.8, arena_factor=0.25, stream=None):
+    def __init__(self, nx, ny, nz, P, L, eps, store="bf16", rule="const", tau=0.8, arena_factor=0.0, stream=None):
         self.scheme = "d3q19"
         o = B.Opts()
         o.wavelet, o.rule, o.detail_store, o.compute = B.WAVELET["bl53"], B.RULE[rule], B.STORE[store], B.PREC["f32"]
