@@ -13,7 +13,7 @@ import numpy as np
 
 from .build import build_oracle
 
-SCHEME = {"d2q9": 0, "d3q19": 1, "euler2d": 2}
+SCHEME = {"d2q9": 0, "d3q19": 1, "euler2d": 2, "transport": 3, "swe": 4}
 WAVELET = {"bl53": 0, "haar": 1}
 STORE = {"f64": 0, "f32": 1, "bf16": 2, "i8": 3}
 RULE = {"const": 0, "accum": 1, "capped": 2}
@@ -35,6 +35,7 @@ def lib():
         L.orc_init_macro.argtypes = [vp, dp, dp, dp, dp]
         L.orc_step.argtypes = [vp, i64]
         L.orc_import.argtypes = [vp, i32, dp]
+        L.orc_set_fv.argtypes = [vp, dbl, dbl, dbl, dbl]
         L.orc_set_threads.restype = i32
         L.orc_set_threads.argtypes = [i32]
         L.orc_export_field.argtypes = [vp, i32, dp]
@@ -67,6 +68,8 @@ def lib():
         L.orc_d2q9_equilibrium.argtypes = [i32, dbl, dbl, dbl, dp]
         L.orc_d2q9_collide.argtypes = [i32, dp, dbl]
         L.orc_rusanov.argtypes = [dp, dp, i32, i32, dbl, dp]
+        L.orc_sw_riemann.argtypes = [dbl, dbl, dbl, dbl, dbl, dbl, dbl, dp]
+        L.orc_sw_flux.argtypes = [dp, dp, i32, i32, dbl, dp]
         L.orc_patch_features.argtypes = [i32, i32, i64, i32, i32, dp, dp]
         L.orc_patch_label.argtypes = [i32, i32, i64, i32, i32, dp, dbl, dp, i32]
         L.orc_patch_features_f32.argtypes = [i32, i32, i64, i32, i32, dp, dp]
@@ -116,14 +119,14 @@ def _macro_ptrs(fields):
 
 
 def nfields(scheme):
-    return {"d2q9": 9, "d3q19": 19, "euler2d": 4}[scheme]
+    return {"d2q9": 9, "d3q19": 19, "euler2d": 4, "transport": 1, "swe": 3}[scheme]
 
 
 class OracleSim:
     """Compressed-patch run (2-D).  Global arrays are (ny_nodes, nx_nodes)."""
 
     def __init__(self, scheme, wavelet, nx, ny, P, L, eps, prec="f64", store="f64", rule="const",
-                 periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4):
+                 periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, velocity=(0.0, 0.0), gravity=9.81, length=1.0):
         self.scheme, self.wavelet, self.prec = scheme, wavelet, prec
         self.P, self.L = P, L
         pmask = int(periodic[0]) | (int(periodic[1]) << 1)
@@ -133,6 +136,7 @@ class OracleSim:
                                   nx, ny, pmask, P, L, eps, tau, cfl, gamma)
         if not self.h:
             raise RuntimeError("oracle: " + lib().orc_last_error().decode())
+        _check(lib().orc_set_fv(self.h, velocity[0], velocity[1], gravity, length))
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -200,13 +204,15 @@ class OracleSim:
 class OracleRef:
     """Uncompressed run of the same scheme on the global arrays."""
 
-    def __init__(self, scheme, wavelet, nx, ny, prec="f64", periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4):
+    def __init__(self, scheme, wavelet, nx, ny, prec="f64", periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4,
+                 velocity=(0.0, 0.0), gravity=9.81, length=1.0):
         pmask = int(periodic[0]) | (int(periodic[1]) << 1)
         self.G = [n + 1 if (wavelet == "bl53" and not per) else n for n, per in zip((nx, ny), periodic)]
         self.F = nfields(scheme)
         self.h = lib().orc_ref_create(SCHEME[scheme], WAVELET[wavelet], PREC[prec], nx, ny, pmask, tau, cfl, gamma)
         if not self.h:
             raise RuntimeError("oracle: " + lib().orc_last_error().decode())
+        _check(lib().orc_set_fv(self.h, velocity[0], velocity[1], gravity, length))
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -458,3 +464,19 @@ def sums_agree(got, stats):
 def set_threads(n):
     """Threads of the oracle's parallel loops (0: default); returns the count."""
     return lib().orc_set_threads(int(n))
+
+
+def sw_riemann(hL, uL, tL, hR, uR, tR, g=9.81):
+    """Shallow-water Riemann solution along a normal: (h, un, ut) at x/t = 0
+    and the star state (h*, u*)."""
+    out = np.zeros(5, np.float64)
+    _check(lib().orc_sw_riemann(hL, uL, tL, hR, uR, tR, g, _dp(out)))
+    return out[:3], out[3], out[4]
+
+
+def sw_flux(WL, WR, nx, ny, g=9.81):
+    a = np.ascontiguousarray(WL, np.float64)
+    b = np.ascontiguousarray(WR, np.float64)
+    out = np.zeros(3, np.float64)
+    _check(lib().orc_sw_flux(_dp(a), _dp(b), nx, ny, g, _dp(out)))
+    return out

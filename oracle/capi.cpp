@@ -104,6 +104,18 @@ void* orc_create(int scheme, int wavelet, int prec, int store, int rule, int64_t
 
 void orc_destroy(void* p) { delete static_cast<Handle*>(p); }
 
+// FV parameters of a compressed or uncompressed run (before its init):
+// transport velocity (alpha, beta), shallow-water gravity, domain side.
+int orc_set_fv(void* p, double alpha, double beta, double gravity, double length) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    if (h->s64) h->s64->prm.set_fv(alpha, beta, gravity, length);
+    if (h->s32) h->s32->prm.set_fv(alpha, beta, gravity, length);
+    if (h->r64) h->r64->prm.set_fv(alpha, beta, gravity, length);
+    if (h->r32) h->r32->prm.set_fv(alpha, beta, gravity, length);
+  });
+}
+
 int orc_init_macro(void* p, const double* a, const double* b, const double* c, const double* d) {
   Handle* h = static_cast<Handle*>(p);
   return guard([&] {
@@ -369,6 +381,35 @@ int orc_d2q9_collide(int prec, double* f, double tau) {
     for (int i = 0; i < 9; ++i) f[i] = g[i];
   }
   return 0;
+}
+
+// Shallow-water Riemann state at x/t = 0 in the frame of the normal
+// (h, un, ut) and the star state (h*, u*); FP64.
+int orc_sw_riemann(double hL, double uL, double tL, double hR, double uR, double tR, double g, double* out) {
+  return guard([&] {
+    sw_riemann<double>(hL, uL, tL, hR, uR, tR, g, out[0], out[1], out[2]);
+    // the star state, from the same iteration
+    const double cL = std::sqrt(g * hL), cR = std::sqrt(g * hR);
+    double h0 = (0.5 * (cL + cR)) - (0.25 * (uR - uL));
+    h0 = h0 > 0 ? (h0 * h0) / g : 1e-6 * std::min(hL, hR);
+    double hs = h0;
+    for (int it = 0; it < SW_NEWTON; ++it) {
+      double fl, dl, fr, dr;
+      sw_fK<double>(hs, hL, cL, g, fl, dl);
+      sw_fK<double>(hs, hR, cR, g, fr, dr);
+      const double hn = hs - ((fl + fr) + (uR - uL)) / (dl + dr);
+      hs = hn > 0 ? hn : 0.5 * hs;
+    }
+    double fl, dl, fr, dr;
+    sw_fK<double>(hs, hL, cL, g, fl, dl);
+    sw_fK<double>(hs, hR, cR, g, fr, dr);
+    out[3] = hs;
+    out[4] = 0.5 * (uL + uR) + 0.5 * (fr - fl);
+  });
+}
+
+int orc_sw_flux(const double* WL, const double* WR, int nx, int ny, double g, double* F) {
+  return guard([&] { sw_godunov<double>(WL, WR, double(nx), double(ny), g, F); });
 }
 
 int orc_rusanov(const double* WL, const double* WR, int nx, int ny, double gamma, double* F) {

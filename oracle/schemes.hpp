@@ -215,3 +215,142 @@ template <class T> inline void euler_cons(T rho, T u, T v, T p, T gm1, T* W) {
 }
 
 }  // namespace orc
+
+namespace orc {
+
+// ---------------------------------------------------------------- transport
+// Linear transport of Sec. 3.1.2: Q(W, N) = W (alpha N^x + beta N^y), with
+// the upwind numerical flux of eq. upwind_trans,
+//   Q(WL, WR, N) = WL max(a.N, 0) + WR min(a.N, 0),
+// in the FV scheme eq. vf_scheme.  a.N for the four normals of eq.
+// directions is alpha, -alpha, beta, -beta.
+template <class T> inline T transport_aN(int k, T alpha, T beta) {
+  return k == 0 ? alpha : (k == 1 ? -alpha : (k == 2 ? beta : -beta));
+}
+
+template <class T> inline T transport_flux(T WL, T WR, T aN) {
+  const T pos = aN > T(0) ? aN : T(0);
+  const T neg = aN < T(0) ? aN : T(0);
+  return WL * pos + WR * neg;
+}
+
+template <class T> inline T transport_update(T W, const T* Wn, T lam_dt_h, T alpha, T beta) {
+  T acc = T(0);
+  for (int k = 0; k < 4; ++k) {
+    const T F = transport_flux<T>(W, Wn[k], transport_aN<T>(k, alpha, beta));
+    acc = k == 0 ? F : acc + F;
+  }
+  return W - lam_dt_h * acc;
+}
+
+// ------------------------------------------------------------ shallow water
+// Sec. 3.2.4: W = (h, hu, hv), Q(W, N) = (h u.N, hu u.N + g h^2/2 N^x,
+// hv u.N + g h^2/2 N^y), Godunov flux: the exact solution of the Riemann
+// problem along N sampled at the interface (textbook construction, wet bed
+// only).  In the frame of N (normal velocity un = u N^x + v N^y, tangential
+// ut = -u N^y + v N^x) the star depth h* solves
+//   f_L(h) + f_R(h) + un_R - un_L = 0,
+//   f_K(h) = 2 (sqrt(g h) - sqrt(g h_K))                    h <= h_K (rarefaction)
+//          = (h - h_K) sqrt(g/2 (h + h_K) / (h h_K))         h >  h_K (shock),
+// by a fixed number (SW_NEWTON) of Newton steps from the two-rarefaction
+// guess h0 = ((c_L + c_R)/2 - (un_R - un_L)/4)^2 / g (positive part; the
+// iteration count does not depend on the data, so FP32 results are exactly
+// reproducible); u* = (un_L + un_R)/2 + (f_R(h*) - f_L(h*))/2.  The state at
+// x/t = 0 is that of the side the contact leaves behind (the tangential
+// velocity jumps only across it): the side's own state outside its wave,
+// the star state (h*, u*) inside, or the sonic point of a transonic
+// rarefaction, c = (un_K + 2 c_K)/3 (left) or (-un_K + 2 c_K)/3 (right),
+// h = c^2 / g, un = +c (left) or -c (right).
+static const int SW_NEWTON = 12;
+
+template <class T> inline void sw_fK(T h, T hK, T cK, T g, T& f, T& df) {
+  if (h <= hK) {
+    const T c = std::sqrt(g * h);
+    f = T(2) * (c - cK);
+    df = g / c;
+  } else {
+    const T s = (h + hK) / (h * hK);
+    const T q = std::sqrt((T(0.5) * g) * s);
+    f = (h - hK) * q;
+    // d/dh [(h - hK) q] = q + (h - hK) dq/dh, dq/dh = -(g/4) / (h^2 q)
+    df = q - ((h - hK) * (T(0.25) * g)) / ((h * h) * q);
+  }
+}
+
+// Riemann state at x/t = 0 in the frame of the normal: (h, un, ut).
+template <class T>
+inline void sw_riemann(T hL, T uL, T tL, T hR, T uR, T tR, T g, T& h, T& un, T& ut) {
+  const T cL = std::sqrt(g * hL), cR = std::sqrt(g * hR);
+  T h0 = (T(0.5) * (cL + cR)) - (T(0.25) * (uR - uL));
+  h0 = h0 > T(0) ? (h0 * h0) / g : T(1e-6) * (hL < hR ? hL : hR);
+  T hs = h0;
+  for (int it = 0; it < SW_NEWTON; ++it) {
+    T fl, dl, fr, dr;
+    sw_fK<T>(hs, hL, cL, g, fl, dl);
+    sw_fK<T>(hs, hR, cR, g, fr, dr);
+    const T f = (fl + fr) + (uR - uL);
+    T hn = hs - f / (dl + dr);
+    hs = hn > T(0) ? hn : T(0.5) * hs;
+  }
+  T fl, dl, fr, dr;
+  sw_fK<T>(hs, hL, cL, g, fl, dl);
+  sw_fK<T>(hs, hR, cR, g, fr, dr);
+  const T us = (T(0.5) * (uL + uR)) + (T(0.5) * (fr - fl));
+  const T cs = std::sqrt(g * hs);
+  if (us >= T(0)) {  // the interface sees the left side of the contact
+    ut = tL;
+    if (hs > hL) {  // left shock, speed uL - cL sqrt(h*(h* + hL) / (2 hL^2))
+      const T sL = uL - cL * std::sqrt((hs * (hs + hL)) / (T(2) * (hL * hL)));
+      if (sL >= T(0)) { h = hL; un = uL; } else { h = hs; un = us; }
+    } else {  // left rarefaction, head uL - cL, tail u* - c*
+      if (uL - cL >= T(0)) { h = hL; un = uL; }
+      else if (us - cs <= T(0)) { h = hs; un = us; }
+      else { const T c = (uL + T(2) * cL) / T(3); h = (c * c) / g; un = c; }
+    }
+  } else {  // the right side of the contact
+    ut = tR;
+    if (hs > hR) {  // right shock, speed uR + cR sqrt(h*(h* + hR) / (2 hR^2))
+      const T sR = uR + cR * std::sqrt((hs * (hs + hR)) / (T(2) * (hR * hR)));
+      if (sR <= T(0)) { h = hR; un = uR; } else { h = hs; un = us; }
+    } else {  // right rarefaction, head uR + cR, tail u* + c*
+      if (uR + cR <= T(0)) { h = hR; un = uR; }
+      else if (us + cs >= T(0)) { h = hs; un = us; }
+      else { const T c = (T(2) * cR - uR) / T(3); h = (c * c) / g; un = -c; }
+    }
+  }
+}
+
+// Godunov flux Q(WL, WR, N) for a normal with components in {-1, 0, 1}.
+template <class T> inline void sw_godunov(const T* WL, const T* WR, T nx, T ny, T g, T* Q) {
+  const T uL = WL[1] / WL[0], vL = WL[2] / WL[0], uR = WR[1] / WR[0], vR = WR[2] / WR[0];
+  const T unL = uL * nx + vL * ny, utL = vL * nx - uL * ny;
+  const T unR = uR * nx + vR * ny, utR = vR * nx - uR * ny;
+  T h, un, ut;
+  sw_riemann<T>(WL[0], unL, utL, WR[0], unR, utR, g, h, un, ut);
+  const T f0 = h * un;
+  const T f1 = f0 * un + (T(0.5) * g) * (h * h);
+  const T f2 = f0 * ut;
+  Q[0] = f0;
+  Q[1] = f1 * nx - f2 * ny;
+  Q[2] = f1 * ny + f2 * nx;
+}
+
+template <class T> inline void sw_update(const T* W, const T* const* Wn, T lam_dt_h, T g, T* out) {
+  T acc[3] = {0, 0, 0};
+  for (int k = 0; k < 4; ++k) {
+    T F[3];
+    sw_godunov<T>(W, Wn[k], T(EULER_NX[k]), T(EULER_NY[k]), g, F);
+    for (int q = 0; q < 3; ++q) acc[q] = k == 0 ? F[q] : acc[q] + F[q];
+  }
+  for (int q = 0; q < 3; ++q) out[q] = W[q] - lam_dt_h * acc[q];
+}
+
+// Largest signal speed of one node: max(|u| + c, |v| + c), c = sqrt(g h).
+template <class T> inline T sw_speed(const T* W, T g) {
+  const T u = W[1] / W[0], v = W[2] / W[0];
+  const T c = std::sqrt(g * W[0]);
+  const T su = std::fabs(u) + c, sv = std::fabs(v) + c;
+  return su > sv ? su : sv;
+}
+
+}  // namespace orc

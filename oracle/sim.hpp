@@ -20,6 +20,7 @@
 //
 // The uncompressed reference runs the same scheme on the global arrays.
 #pragma once
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <stdexcept>
@@ -33,9 +34,16 @@
 
 namespace orc {
 
-enum Scheme { SC_D2Q9 = 0, SC_D3Q19 = 1, SC_EULER2D = 2 };
+enum Scheme { SC_D2Q9 = 0, SC_D3Q19 = 1, SC_EULER2D = 2, SC_TRANSPORT = 3, SC_SWE = 4 };
 
-inline int scheme_fields(int s) { return s == SC_D2Q9 ? 9 : s == SC_D3Q19 ? 19 : 4; }
+inline int scheme_fields(int s) {
+  return s == SC_D2Q9 ? 9 : s == SC_D3Q19 ? 19 : s == SC_EULER2D ? 4 : s == SC_TRANSPORT ? 1 : 3;
+}
+// Macroscopic input fields of the initial state.
+inline int scheme_macro_fields(int s) {
+  return s == SC_D2Q9 ? 3 : s == SC_D3Q19 ? 4 : s == SC_EULER2D ? 4 : s == SC_TRANSPORT ? 1 : 3;
+}
+inline bool scheme_fv(int s) { return s == SC_EULER2D || s == SC_TRANSPORT || s == SC_SWE; }
 
 struct Grid2 {
   int64_t N[2] = {0, 0};   // cells per axis
@@ -62,6 +70,18 @@ template <class T> struct Params {
   T omega = T(1);            // D2Q9: 1/tau
   T gamma = T(1.4), gm1 = T(0.4);
   double cfl = 0.4;
+  double alpha = 0.0, beta = 0.0;  // transport velocity (alpha, beta)
+  T alpha_t = T(0), beta_t = T(0);
+  T g = T(9.81);                   // shallow water gravity
+  double length = 1.0;             // side of the square domain (h = length / cells)
+  void set_fv(double a, double b, double grav, double len) {
+    alpha = a;
+    beta = b;
+    alpha_t = T(a);
+    beta_t = T(b);
+    g = T(grav > 0 ? grav : 9.81);
+    length = len > 0 ? len : 1.0;
+  }
 };
 
 // One scheme step of the nodes [0,E)^2 of a local block whose extended
@@ -84,16 +104,25 @@ void scheme_step_block(const Params<T>& prm, std::vector<std::vector<T>>& X, int
     for (int i = 0; i < 9; ++i)
       for (int64_t y = 0; y < E; ++y)
         for (int64_t x = 0; x < E; ++x) out[i][y * E + x] = X[i][id(x - D2Q9_CX[i], y - D2Q9_CY[i])];
-  } else if (prm.scheme == SC_EULER2D) {
+  } else if (prm.scheme == SC_EULER2D || prm.scheme == SC_SWE) {
+    const int nq = prm.scheme == SC_EULER2D ? 4 : 3;
     for (int64_t y = 0; y < E; ++y)
       for (int64_t x = 0; x < E; ++x) {
         T W0[4], Wn[4][4], o[4];
-        for (int q = 0; q < 4; ++q) W0[q] = X[q][id(x, y)];
+        for (int q = 0; q < nq; ++q) W0[q] = X[q][id(x, y)];
         for (int k = 0; k < 4; ++k)
-          for (int q = 0; q < 4; ++q) Wn[k][q] = X[q][id(x + EULER_NX[k], y + EULER_NY[k])];
+          for (int q = 0; q < nq; ++q) Wn[k][q] = X[q][id(x + EULER_NX[k], y + EULER_NY[k])];
         const T* nb[4] = {Wn[0], Wn[1], Wn[2], Wn[3]};
-        euler_update<T>(W0, nb, lam_dt_h, prm.gm1, prm.gamma, o);
-        for (int q = 0; q < 4; ++q) out[q][y * E + x] = o[q];
+        if (prm.scheme == SC_EULER2D) euler_update<T>(W0, nb, lam_dt_h, prm.gm1, prm.gamma, o);
+        else sw_update<T>(W0, nb, lam_dt_h, prm.g, o);
+        for (int q = 0; q < nq; ++q) out[q][y * E + x] = o[q];
+      }
+  } else if (prm.scheme == SC_TRANSPORT) {
+    for (int64_t y = 0; y < E; ++y)
+      for (int64_t x = 0; x < E; ++x) {
+        T Wn[4];
+        for (int k = 0; k < 4; ++k) Wn[k] = X[0][id(x + EULER_NX[k], y + EULER_NY[k])];
+        out[0][y * E + x] = transport_update<T>(X[0][id(x, y)], Wn, lam_dt_h, prm.alpha_t, prm.beta_t);
       }
   } else {
     throw std::runtime_error("scheme not supported by the 2-D oracle");
@@ -101,20 +130,49 @@ void scheme_step_block(const Params<T>& prm, std::vector<std::vector<T>>& X, int
 }
 
 // State fields from macroscopic fields at one node.
+// D2Q9: the equilibrium of (rho, u_x, u_y); Euler: (rho, u, v, p) ->
+// conservative; transport: W itself; shallow water: (h, u, v) -> (h, h u, h v).
 template <class T> void macro_to_state(const Params<T>& prm, const double* m, T* s) {
-  if (prm.scheme == SC_D2Q9) d2q9_equilibrium<T>(T(m[0]), T(m[1]), T(m[2]), s);
-  else euler_cons<T>(T(m[0]), T(m[1]), T(m[2]), T(m[3]), prm.gm1, s);
+  if (prm.scheme == SC_D2Q9) {
+    d2q9_equilibrium<T>(T(m[0]), T(m[1]), T(m[2]), s);
+  } else if (prm.scheme == SC_EULER2D) {
+    euler_cons<T>(T(m[0]), T(m[1]), T(m[2]), T(m[3]), prm.gm1, s);
+  } else if (prm.scheme == SC_TRANSPORT) {
+    s[0] = T(m[0]);
+  } else {
+    s[0] = T(m[0]);
+    s[1] = s[0] * T(m[1]);
+    s[2] = s[0] * T(m[2]);
+  }
 }
 
+// Largest signal speed over the nodes (Euler: max(|u|+c, |v|+c); shallow
+// water: the same with c = sqrt(g h)).
 template <class T> T global_speed_max(const Params<T>& prm, const std::vector<std::vector<T>>& U) {
   T smax = T(0);
   const int64_t n = int64_t(U[0].size());
   for (int64_t k = 0; k < n; ++k) {
-    T W[4] = {U[0][k], U[1][k], U[2][k], U[3][k]};
-    const T s = euler_speed<T>(W, prm.gm1, prm.gamma);
+    T s;
+    if (prm.scheme == SC_EULER2D) {
+      T W[4] = {U[0][k], U[1][k], U[2][k], U[3][k]};
+      s = euler_speed<T>(W, prm.gm1, prm.gamma);
+    } else {
+      T W[3] = {U[0][k], U[1][k], U[2][k]};
+      s = sw_speed<T>(W, prm.g);
+    }
     if (s > smax) smax = s;
   }
   return smax;
+}
+
+// dt/h of the next FV step and the physical time it advances.  cfl > 0:
+// dt = cfl h / v_max, with v_max the largest signal speed of the state
+// (Euler, shallow water) or max(|alpha|, |beta|) (transport, Sec. 3.1.2);
+// cfl < 0: a fixed step dt/h = -cfl.  h = length / cells along x.
+template <class T> double fv_dt_over_h(const Params<T>& prm, const std::vector<std::vector<T>>& U) {
+  if (prm.cfl <= 0) return -prm.cfl;
+  if (prm.scheme == SC_TRANSPORT) return prm.cfl / std::max(std::fabs(prm.alpha), std::fabs(prm.beta));
+  return prm.cfl / double(global_speed_max<T>(prm, U));
 }
 
 // ------------------------------------------------------------ compressed run
@@ -143,7 +201,7 @@ template <class T> struct Sim {
     prm.gamma = T(gamma);
     prm.gm1 = T(gamma - 1.0);
     prm.cfl = cfl;
-    if (scheme != SC_D2Q9 && scheme != SC_EULER2D) throw std::runtime_error("scheme not supported");
+    if (scheme != SC_D2Q9 && !scheme_fv(scheme)) throw std::runtime_error("scheme not supported");
     if (scheme == SC_D2Q9 && (!grid.periodic[0] || !grid.periodic[1]))
       throw std::runtime_error("D2Q9 needs periodic axes");
     // BL5/3 needs an interior coarse sample for eq. conservation: P/2^L >= 2.
@@ -179,7 +237,7 @@ template <class T> struct Sim {
   }
 
   void init_macro(const std::vector<const double*>& m) {
-    const int nm = prm.scheme == SC_D2Q9 ? 3 : 4;
+    const int nm = scheme_macro_fields(prm.scheme);
     if (int(m.size()) < nm) throw std::runtime_error("init: missing macroscopic fields");
     std::string err;
 #pragma omp parallel for schedule(dynamic)
@@ -271,13 +329,10 @@ template <class T> struct Sim {
   void step() {
     std::vector<std::vector<T>> U = decode_all();
     T lam = T(0);
-    if (prm.scheme == SC_EULER2D) {
-      const T smax = global_speed_max<T>(prm, U);
-      // cfl > 0: dt = cfl h / smax (eq. dt of Sec. 3.1.2 with Euler's max
-      // signal speed); cfl < 0: a fixed step dt/h = -cfl
-      const double dth = prm.cfl > 0 ? prm.cfl / double(smax) : -prm.cfl;
+    if (scheme_fv(prm.scheme)) {
+      const double dth = fv_dt_over_h<T>(prm, U);
       lam = T(dth);
-      time += dth / double(grid.N[0]);
+      time += dth * (prm.length / double(grid.N[0]));
     } else {
       time += 1.0;
     }
@@ -375,10 +430,10 @@ template <class T> struct Ref {
     prm.gm1 = T(gamma - 1.0);
     prm.cfl = cfl;
     F = scheme_fields(scheme);
-    if (scheme != SC_D2Q9 && scheme != SC_EULER2D) throw std::runtime_error("scheme not supported");
+    if (scheme != SC_D2Q9 && !scheme_fv(scheme)) throw std::runtime_error("scheme not supported");
   }
   void init_macro(const std::vector<const double*>& m) {
-    const int nm = prm.scheme == SC_D2Q9 ? 3 : 4;
+    const int nm = scheme_macro_fields(prm.scheme);
     U.assign(F, std::vector<T>(grid.nodes()));
     for (int64_t g = 0; g < grid.nodes(); ++g) {
       double mv[4];
@@ -390,13 +445,10 @@ template <class T> struct Ref {
   }
   void step() {
     T lam = T(0);
-    if (prm.scheme == SC_EULER2D) {
-      const T smax = global_speed_max<T>(prm, U);
-      // cfl > 0: dt = cfl h / smax (eq. dt of Sec. 3.1.2 with Euler's max
-      // signal speed); cfl < 0: a fixed step dt/h = -cfl
-      const double dth = prm.cfl > 0 ? prm.cfl / double(smax) : -prm.cfl;
+    if (scheme_fv(prm.scheme)) {
+      const double dth = fv_dt_over_h<T>(prm, U);
       lam = T(dth);
-      time += dth / double(grid.N[0]);
+      time += dth * (prm.length / double(grid.N[0]));
     } else {
       time += 1.0;
     }
@@ -417,18 +469,26 @@ template <class T> struct Ref {
           for (int i = 0; i < 9; ++i)
             V[i][y * G0 + x] = C[i][grid.wrap(1, y - D2Q9_CY[i]) * G0 + grid.wrap(0, x - D2Q9_CX[i])];
     } else {
+      const int nq = F;
 #pragma omp parallel for
       for (int64_t y = 0; y < G1; ++y)
         for (int64_t x = 0; x < G0; ++x) {
           T W0[4], Wn[4][4], o[4];
-          for (int q = 0; q < 4; ++q) W0[q] = U[q][y * G0 + x];
+          for (int q = 0; q < nq; ++q) W0[q] = U[q][y * G0 + x];
           for (int k = 0; k < 4; ++k) {
             const int64_t g = grid.wrap(1, y + EULER_NY[k]) * G0 + grid.wrap(0, x + EULER_NX[k]);
-            for (int q = 0; q < 4; ++q) Wn[k][q] = U[q][g];
+            for (int q = 0; q < nq; ++q) Wn[k][q] = U[q][g];
           }
           const T* nb[4] = {Wn[0], Wn[1], Wn[2], Wn[3]};
-          euler_update<T>(W0, nb, lam, prm.gm1, prm.gamma, o);
-          for (int q = 0; q < 4; ++q) V[q][y * G0 + x] = o[q];
+          if (prm.scheme == SC_EULER2D) {
+            euler_update<T>(W0, nb, lam, prm.gm1, prm.gamma, o);
+          } else if (prm.scheme == SC_SWE) {
+            sw_update<T>(W0, nb, lam, prm.g, o);
+          } else {
+            const T wn[4] = {Wn[0][0], Wn[1][0], Wn[2][0], Wn[3][0]};
+            o[0] = transport_update<T>(W0[0], wn, lam, prm.alpha_t, prm.beta_t);
+          }
+          for (int q = 0; q < nq; ++q) V[q][y * G0 + x] = o[q];
         }
     }
     U.swap(V);

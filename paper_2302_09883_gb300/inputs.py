@@ -21,6 +21,20 @@ WORKLOADS = {
     "euler_bl53_4096": dict(scheme="euler2d", wavelet="bl53", n=4096, P=64, L=4, eps=1e-3, prec="f32",
                             store="i8", rule="const", cfl=0.4, gamma=1.4, steps=1500, init="quadrants",
                             periodic=(False, False)),
+    # Linear transport (the paper's Sec. 3.1.2): 128 cells (129 nodes) per
+    # axis on [-1, 1]^2, 2 x 2 patches of 64 cells, outflow, velocity
+    # (0.9, 0.9), CFL 0.45, Gaussian 1 + exp(-30 r^2), run to t = 0.5;
+    # FP32 compute, thresholded details stored in FP32 (no quantisation).
+    "transport_128": dict(scheme="transport", wavelet="bl53", n=128, P=64, L=4, eps=0.01, prec="f32",
+                          store="f32", rule="capped", cfl=0.45, velocity=(0.9, 0.9), length=2.0, t_end=0.5,
+                          init="transport", periodic=(False, False)),
+    # Shallow water, Godunov flux with exact Riemann solver (the paper's
+    # Sec. 3.2.4 cost study): 128 cells (129 nodes) per axis on [0, 1]^2,
+    # outflow, h = 2 on the central 0.5 x 0.5 square and 1 elsewhere, at rest,
+    # g = 9.81, 38245 steps of dt = 10 s / 38245, 4 levels, c = 5e-4.
+    "swe_129": dict(scheme="swe", wavelet="bl53", n=128, P=64, L=4, eps=5e-4, prec="f32", store="f32",
+                    rule="capped", gravity=9.81, dt=10.0 / 38245, steps=38245, length=1.0, init="swe_square",
+                    periodic=(False, False)),
 }
 
 
@@ -49,6 +63,25 @@ QUADRANTS = {
     "SW": (0.138, 1.206, 1.206, 0.029),
     "SE": (0.5323, 0.0, 1.206, 0.3),
 }
+
+
+def transport_gaussian(n, t=0.0, velocity=(0.9, 0.9), lo=-1.0, hi=1.0):
+    """f(x, y) = 1 + exp(-30 ((x - a t)^2 + (y - b t)^2)) on the n + 1 nodes
+    per axis of [lo, hi]^2: the initial state (t = 0) of the transport
+    workload, and its exact solution at time t."""
+    x = lo + (hi - lo) * np.arange(n + 1, dtype=np.float64) / n
+    X, Y = np.meshgrid(x - velocity[0] * t, x - velocity[1] * t, indexing="xy")
+    return [1.0 + np.exp(-30.0 * (X * X + Y * Y))]
+
+
+def swe_square(n, h_in=2.0, h_out=1.0, half=0.25):
+    """Water at rest, h = h_in on the nodes with |x - 1/2| <= half and
+    |y - 1/2| <= half, h_out elsewhere; n + 1 nodes per axis on [0, 1]^2.
+    Returns (h, u, v)."""
+    x = np.arange(n + 1, dtype=np.float64) / n
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    h = np.where((np.abs(X - 0.5) <= half) & (np.abs(Y - 0.5) <= half), h_in, h_out)
+    return [h, np.zeros_like(h), np.zeros_like(h)]
 
 
 def four_quadrant(n):
@@ -96,6 +129,10 @@ def initial_fields(w, n=None, seed=0):
         return shear_wave(n, seed=seed)
     if w["init"] == "quadrants":
         return four_quadrant(n)
+    if w["init"] == "transport":
+        return transport_gaussian(n, velocity=w.get("velocity", (0.9, 0.9)))
+    if w["init"] == "swe_square":
+        return swe_square(n)
     raise ValueError(w["init"])
 
 

@@ -1,0 +1,207 @@
+"""Oracle pins for the paper's two FV workloads: linear transport with the
+upwind flux (Sec. 3.1.2, eq. upwind_trans) and shallow water with the
+Godunov flux of an exact Riemann solver (Sec. 3.2.4).  Each check is fixed
+by the mathematics, not by restating the code: an exact shift at Courant
+number 1, the maximum principle, first-order convergence to the exact
+translated solution, conservation, Riemann invariants and jump conditions,
+and the behaviour the paper reports for the transport sweep."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2302_09883_gb300 import inputs
+
+G = 9.81
+
+
+def transport_run(n, steps, eps=0.0, L=4, P=64, rule="capped", prec="f64", velocity=(0.9, 0.9), cfl=0.45,
+                  periodic=(False, False), field=None, compressed=True):
+    f = [field] if field is not None else inputs.transport_gaussian(n, velocity=velocity)
+    kw = dict(periodic=periodic, cfl=cfl, velocity=velocity, length=2.0)
+    if compressed:
+        o = O.OracleSim("transport", "bl53", n, n, P, L, eps, prec=prec, store="f64" if prec == "f64" else "f32",
+                        rule=rule, **kw)
+    else:
+        o = O.OracleRef("transport", "bl53", n, n, prec=prec, **kw)
+    o.init_macro(f)
+    o.step(steps)
+    return o
+
+
+def test_transport_courant_one_is_an_exact_shift():
+    # Upwind at dt/h * alpha = 1 (beta = 0) moves every value by one node:
+    # W(i, n+1) = W(i-1, n) up to rounding.  Periodic axes, random data.
+    rng = np.random.default_rng(1)
+    n = 64
+    w0 = rng.normal(size=(n, n))
+    r = transport_run(n, 5, velocity=(1.0, 0.0), cfl=-1.0, periodic=(True, True), field=w0, compressed=False)
+    # W - (W - W_left) rounds twice: a few ulps per step
+    assert np.max(np.abs(r.export_field(0) - np.roll(w0, 5, axis=1))) <= 5 * 4 * 2.0 ** -53 * np.abs(w0).max()
+    # the compressed run at eps 0 is the same up to the transforms' rounding
+    c = transport_run(n, 5, velocity=(1.0, 0.0), cfl=-1.0, periodic=(True, True), field=w0, P=32, L=3)
+    assert np.max(np.abs(c.export_field(0) - np.roll(w0, 5, axis=1))) <= 1e-13
+
+
+def test_transport_maximum_principle_and_conservation():
+    # CFL (alpha + beta) dt/h <= 1: every new value is a convex combination
+    # of old ones; with periodic axes the sum is conserved.
+    rng = np.random.default_rng(2)
+    n = 64
+    w0 = 1.0 + rng.random((n, n))
+    r = transport_run(n, 40, velocity=(0.7, -0.4), cfl=-0.9, periodic=(True, True), field=w0, compressed=False)
+    w = r.export_field(0)
+    assert w.min() >= w0.min() - 1e-15 and w.max() <= w0.max() + 1e-15
+    assert abs(w.sum() - w0.sum()) <= 1e-12 * w0.sum()
+    c = transport_run(n, 40, velocity=(0.7, -0.4), cfl=-0.9, periodic=(True, True), field=w0, P=32, L=3, eps=1e-3)
+    m = c.stats()["coef_sums"][0]
+    assert abs(m - w0.sum()) <= 1e-12 * w0.sum()  # compression keeps mass exactly (eq. conservation)
+
+
+def test_transport_first_order_convergence_to_exact_solution():
+    # The Gaussian of Sec. 3.1.2 moved by (0.45, 0.45) at t = 0.5: the
+    # upwind scheme is first order, so the L2 error halves with h.
+    errs = []
+    for n in (64, 128, 256):
+        steps = int(round(0.5 / (0.45 * (2.0 / n) / 0.9)))
+        r = transport_run(n, steps, compressed=False)
+        assert abs(r.time - 0.5) < 1e-12
+        ex = inputs.transport_gaussian(n, t=0.5)[0]
+        errs.append(np.sqrt(np.mean((r.export_field(0) - ex) ** 2)))
+    assert 1.6 < errs[0] / errs[1] < 2.4 and 1.6 < errs[1] / errs[2] < 2.4
+
+
+def _mean_ratio(eps, L, rule="capped", n=128):
+    o = O.OracleSim("transport", "bl53", n, n, 64, L, eps, prec="f32", store="f32", rule=rule,
+                    periodic=(False, False), cfl=0.45, velocity=(0.9, 0.9), length=2.0)
+    o.init_macro(inputs.transport_gaussian(n))
+    unc = (n + 1) ** 2 * 4
+    rs = []
+    for _ in range(64):
+        o.step(1)
+        rs.append(unc / o.stats()["compressed_bytes"])
+    return float(np.mean(rs))
+
+
+def test_transport_sweep_reproduces_the_papers_trends():
+    # Sec. 3.2.1-3.2.2 (threshold 0.0025-0.04, levels 1-5, capped rule): the
+    # ratio grows with the level up to 4 and falls at level 5; at level 1 it
+    # hardly moves across non-zero thresholds; at level 4 it grows with the
+    # threshold; a threshold of 0 keeps every coefficient (ratio ~1).
+    r = {(L, c): _mean_ratio(c, L) for L in (1, 2, 3, 4, 5) for c in (0.0025, 0.01, 0.04)}
+    for c in (0.0025, 0.01, 0.04):
+        assert r[(1, c)] < r[(2, c)] < r[(3, c)] <= r[(4, c)] * 1.05
+        assert r[(5, c)] < r[(4, c)]
+    lvl1 = [r[(1, c)] for c in (0.0025, 0.01, 0.04)]
+    assert max(lvl1) / min(lvl1) < 1.1
+    assert r[(4, 0.0025)] < r[(4, 0.01)] < r[(4, 0.04)]
+    assert _mean_ratio(0.0, 4) < 1.2
+
+
+# ------------------------------------------------------------ shallow water
+
+def _flux_exact(W, nx, ny):
+    h, hu, hv = W
+    un = (hu * nx + hv * ny) / h
+    return np.array([h * un, hu * un + 0.5 * G * h * h * nx, hv * un + 0.5 * G * h * h * ny])
+
+
+@pytest.mark.parametrize("hL,uL,hR,uR", [(2.0, 0.0, 1.0, 0.0), (1.0, 0.0, 2.0, 0.0), (1.0, 1.5, 1.0, -1.5),
+                                         (1.0, -1.0, 1.2, 1.0), (1.5, 0.3, 0.8, 0.1)])
+def test_sw_star_state_satisfies_jump_and_invariant_conditions(hL, uL, hR, uR):
+    # Across a shock the Rankine-Hugoniot conditions hold for mass and
+    # momentum with one speed S; across a rarefaction the Riemann invariant
+    # u +- 2 sqrt(g h) is constant.
+    _, hs, us = O.sw_riemann(hL, uL, 0.0, hR, uR, 0.0, G)
+    for side, (hk, uk) in (("L", (hL, uL)), ("R", (hR, uR))):
+        if hs > hk:  # shock
+            m0 = hs * us - hk * uk
+            dh = hs - hk
+            S = m0 / dh
+            mom = (hs * us * us + 0.5 * G * hs * hs) - (hk * uk * uk + 0.5 * G * hk * hk)
+            assert abs(S * m0 - mom) <= 1e-10 * max(1.0, abs(mom))
+            # entropy: the shock moves into the side's state faster than its characteristic
+            if side == "L":
+                assert S < uk - np.sqrt(G * hk) + 1e-12 or S < us
+            else:
+                assert S > uk + np.sqrt(G * hk) - 1e-12 or S > us
+        else:  # rarefaction: invariant u + 2c (left) or u - 2c (right)
+            sgn = 1.0 if side == "L" else -1.0
+            assert abs((us + sgn * 2 * np.sqrt(G * hs)) - (uk + sgn * 2 * np.sqrt(G * hk))) <= 1e-11
+
+
+def test_sw_flux_consistency_and_rotation():
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        h = 0.5 + rng.random()
+        W = np.array([h, h * rng.normal(), h * rng.normal()])
+        for nx, ny in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            # consistency: the flux of equal states is the physical flux
+            assert np.allclose(O.sw_flux(W, W, nx, ny, G), _flux_exact(W, nx, ny), rtol=1e-12, atol=1e-12)
+        # conservation: the flux leaving one cell enters its neighbour
+        W2 = np.array([0.5 + rng.random(), rng.normal(), rng.normal()])
+        a = O.sw_flux(W, W2, 1, 0, G)
+        b = O.sw_flux(W2, W, -1, 0, G)
+        assert np.allclose(a, -b, rtol=1e-12, atol=1e-12)
+
+
+def _swe_run(n, steps, dt_over_h, field, periodic=(False, False), compressed=False, eps=0.0, P=64, L=4,
+             prec="f64"):
+    kw = dict(periodic=periodic, cfl=-dt_over_h, gravity=G, length=1.0)
+    if compressed:
+        o = O.OracleSim("swe", "bl53", n, n, P, L, eps, prec=prec, store="f64" if prec == "f64" else "f32",
+                        rule="capped", **kw)
+    else:
+        o = O.OracleRef("swe", "bl53", n, n, prec=prec, **kw)
+    o.init_macro(field)
+    o.step(steps)
+    return o
+
+
+def test_sw_lake_at_rest_and_conservation():
+    n = 64
+    h = np.full((n, n), 1.3)
+    z = np.zeros_like(h)
+    r = _swe_run(n, 20, 0.1, [h, z, z], periodic=(True, True))
+    assert np.array_equal(r.export_field(0), h) and np.array_equal(r.export_field(1), z)
+    # a periodic hump: mass and momentum (zero) conserved
+    x = np.arange(n) / n
+    X, Y = np.meshgrid(x, x)
+    h2 = 1.0 + 0.3 * np.exp(-60 * ((X - 0.5) ** 2 + (Y - 0.4) ** 2))
+    r = _swe_run(n, 60, 0.03, [h2, z, z], periodic=(True, True))
+    assert abs(r.export_field(0).sum() - h2.sum()) <= 1e-12 * h2.sum()
+    assert abs(r.export_field(1).sum()) <= 1e-10 and abs(r.export_field(2).sum()) <= 1e-10
+    c = _swe_run(n, 60, 0.03, [h2, z, z], periodic=(True, True), compressed=True, eps=1e-4, P=32, L=3)
+    assert abs(c.stats()["coef_sums"][0] - h2.sum()) <= 1e-12 * h2.sum()
+
+
+def test_sw_dam_break_converges_to_the_exact_riemann_solution():
+    # 1-D dam break along x (2 m | 1 m at rest): the Godunov scheme
+    # converges to the self-similar exact solution, sampled from the same
+    # Riemann solution at x/t.
+    def exact(xi):
+        _, hs, us = O.sw_riemann(2.0, 0.0, 0.0, 1.0, 0.0, 0.0, G)
+        cl, cs = np.sqrt(G * 2.0), np.sqrt(G * hs)
+        sR = us * hs / (hs - 1.0)  # shock speed from mass conservation
+        if xi <= -cl:
+            return 2.0
+        if xi < us - cs:
+            c = (2 * cl - xi) / 3.0
+            return c * c / G
+        if xi < sR:
+            return hs
+        return 1.0
+    errs = []
+    for n in (64, 128, 256):
+        x = (np.arange(n + 1)) / n
+        X, Y = np.meshgrid(x, x)
+        h0 = np.where(X < 0.5, 2.0, 1.0)
+        z = np.zeros_like(h0)
+        dth = 0.1
+        steps = n // 4
+        r = _swe_run(n, steps, dth, [h0, z, z])
+        t = steps * dth / n
+        hx = r.export_field(0)[n // 2]
+        he = np.array([exact((xx - 0.5) / t) for xx in x])
+        errs.append(np.mean(np.abs(hx - he)))
+        assert np.allclose(r.export_field(2), 0.0, atol=1e-12)  # no transverse motion
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 0.02
