@@ -54,8 +54,15 @@ typedef enum {
  * D3Q19: 19 populations on a 3-D grid (dims = 3), lattice units, periodic
  * axes only; compiled for BL5/3, FP32 compute, F32 or BF16 details, P = 32
  * or 16, L = 3.  EULER2D: (rho, rho u, rho v, E), perfect gas, Rusanov flux
- * in the form of the paper's eq. vf_scheme, periodic or outflow axes. */
-typedef enum { WCS_D2Q9 = 0, WCS_D3Q19 = 1, WCS_EULER2D = 2 } wcs_scheme;
+ * in the form of the paper's eq. vf_scheme, periodic or outflow axes.
+ * TRANSPORT: one field W, the paper's linear transport (Sec. 3.1.2) with the
+ * upwind flux of eq. upwind_trans, velocity opts.velocity; compiled for
+ * BL5/3, FP32 compute with F32 details, P = 64, L = 1..5, and FP64 P = 32
+ * L = 3.  SWE: (h, h u, h v), shallow water with the Godunov flux of the
+ * exact Riemann solver (Sec. 3.2.4), gravity opts.gravity; BL5/3, FP32/F32
+ * P = 64 L = 4 and FP64 P = 32 L = 3.  The FV schemes (EULER2D, TRANSPORT,
+ * SWE) take periodic or outflow (zero-gradient) axes. */
+typedef enum { WCS_D2Q9 = 0, WCS_D3Q19 = 1, WCS_EULER2D = 2, WCS_TRANSPORT = 3, WCS_SWE = 4 } wcs_scheme;
 
 /* Wavelets: folded BL5/3 on P+1 nodes (Sec. 2.1.2), or Haar on P cells. */
 typedef enum { WCS_BL53 = 0, WCS_HAAR = 1 } wcs_wavelet;
@@ -82,8 +89,11 @@ typedef struct {
   int detail_store;       /* wcs_store */
   int compute;            /* wcs_prec */
   double tau;             /* D2Q9 relaxation time (omega = 1/tau) */
-  double cfl;             /* EULER2D: > 0: dt = cfl h / max(|u|+c, |v|+c) of
-                             the current state; < 0: fixed step dt/h = -cfl */
+  double cfl;             /* FV schemes: > 0: dt = cfl h / v_max, v_max the
+                             largest signal speed of the current state
+                             (EULER2D: max(|u|+c, |v|+c); SWE: the same with
+                             c = sqrt(g h)) or max(|alpha|, |beta|)
+                             (TRANSPORT); < 0: fixed step dt/h = -cfl */
   double gamma;           /* EULER2D ratio of specific heats */
   double arena_factor;    /* > 0: fixed arena capacity per buffer, as a
                              fraction of the uncompressed state size in the
@@ -97,6 +107,10 @@ typedef struct {
                              capacity (not with a learned threshold, nor
                              inside a batch) */
   void* cuda_stream;      /* cudaStream_t, NULL = default stream */
+  double velocity[2];     /* TRANSPORT: (alpha, beta) */
+  double gravity;         /* SWE: g (0 = 9.81) */
+  double length;          /* FV schemes: side of the square domain, so that
+                             h = length / cells and time = sum of dt (0 = 1) */
 } wcs_opts;
 
 /* Per-step diagnostics, all reductions in FP64 in a fixed order. */
@@ -106,8 +120,10 @@ typedef struct {
   double field_sum[19];      /* per field: trapezoid-weighted sum computed
                                 from the coarse coefficients (details carry
                                 no mass, eq. conservation) */
-  double mass;               /* D2Q9: sum of populations; EULER2D: rho */
-  double momentum[3];        /* D2Q9: sum c_i f_i; EULER2D: rho u, rho v */
+  double mass;               /* D2Q9: sum of populations; EULER2D: rho;
+                                TRANSPORT: W; SWE: h */
+  double momentum[3];        /* D2Q9: sum c_i f_i; EULER2D: rho u, rho v;
+                                SWE: h u, h v */
   double energy;             /* EULER2D: E */
   double smax;               /* EULER2D: largest signal speed of the state */
   int64_t live_bytes;        /* bytes of the records of the current state */
@@ -134,7 +150,7 @@ void wcs_destroy(wcs_sim* sim);
  * out [ny][nx] over the unique nodes (nx = n[0] cells, or n[0]+1 nodes on a
  * non-periodic BL5/3 axis), x fastest.  D2Q9: (rho, u_x, u_y), the state is
  * the equilibrium.  D3Q19: (rho, u_x, u_y, u_z) laid out [nz][ny][nx], the
- * equilibrium.  EULER2D: (rho, u, v, p).  fields[k] are host pointers if
+ * equilibrium.  EULER2D: (rho, u, v, p).  TRANSPORT: (W).  SWE: (h, u, v).  fields[k] are host pointers if
  * src_is_device == 0, else device pointers.  Encodes state 0. */
 wcs_status wcs_init_macro(wcs_sim* sim, const double* const* fields, int nfields, int src_is_device);
 

@@ -388,23 +388,11 @@ int orc_d2q9_collide(int prec, double* f, double tau) {
 int orc_sw_riemann(double hL, double uL, double tL, double hR, double uR, double tR, double g, double* out) {
   return guard([&] {
     sw_riemann<double>(hL, uL, tL, hR, uR, tR, g, out[0], out[1], out[2]);
-    // the star state, from the same iteration
-    const double cL = std::sqrt(g * hL), cR = std::sqrt(g * hR);
-    double h0 = (0.5 * (cL + cR)) - (0.25 * (uR - uL));
-    h0 = h0 > 0 ? (h0 * h0) / g : 1e-6 * std::min(hL, hR);
-    double hs = h0;
-    for (int it = 0; it < SW_NEWTON; ++it) {
-      double fl, dl, fr, dr;
-      sw_fK<double>(hs, hL, cL, g, fl, dl);
-      sw_fK<double>(hs, hR, cR, g, fr, dr);
-      const double hn = hs - ((fl + fr) + (uR - uL)) / (dl + dr);
-      hs = hn > 0 ? hn : 0.5 * hs;
-    }
-    double fl, dl, fr, dr;
-    sw_fK<double>(hs, hL, cL, g, fl, dl);
-    sw_fK<double>(hs, hR, cR, g, fr, dr);
+    // the star state
+    double hs, us;
+    sw_star<double>(hL, uL, hR, uR, g, std::sqrt(g * hL), std::sqrt(g * hR), hs, us);
     out[3] = hs;
-    out[4] = 0.5 * (uL + uR) + 0.5 * (fr - fl);
+    out[4] = us;
   });
 }
 

@@ -252,16 +252,17 @@ template <class T> inline T transport_update(T W, const T* Wn, T lam_dt_h, T alp
 //   f_L(h) + f_R(h) + un_R - un_L = 0,
 //   f_K(h) = 2 (sqrt(g h) - sqrt(g h_K))                    h <= h_K (rarefaction)
 //          = (h - h_K) sqrt(g/2 (h + h_K) / (h h_K))         h >  h_K (shock),
-// by a fixed number (SW_NEWTON) of Newton steps from the two-rarefaction
-// guess h0 = ((c_L + c_R)/2 - (un_R - un_L)/4)^2 / g (positive part; the
-// iteration count does not depend on the data, so FP32 results are exactly
-// reproducible); u* = (un_L + un_R)/2 + (f_R(h*) - f_L(h*))/2.  The state at
-// x/t = 0 is that of the side the contact leaves behind (the tangential
-// velocity jumps only across it): the side's own state outside its wave,
-// the star state (h*, u*) inside, or the sonic point of a transonic
-// rarefaction, c = (un_K + 2 c_K)/3 (left) or (-un_K + 2 c_K)/3 (right),
-// h = c^2 / g, un = +c (left) or -c (right).
-static const int SW_NEWTON = 12;
+// by Newton steps from the two-rarefaction guess h0 = ((c_L + c_R)/2 -
+// (un_R - un_L)/4)^2 / g (positive part), stopping once a step changes h* by
+// at most SW_TOL relative (2^-20 in FP32, 2^-45 in FP64) or after
+// SW_NEWTON_MAX steps; u* = (un_L + un_R)/2 + (f_R(h*) - f_L(h*))/2.  The
+// state at x/t = 0 is that of the side the contact leaves behind (the
+// tangential velocity jumps only across it): the side's own state outside
+// its wave, the star state (h*, u*) inside, or the sonic point of a
+// transonic rarefaction, c = (un_K + 2 c_K)/3 (left) or (-un_K + 2 c_K)/3
+// (right), h = c^2 / g, un = +c (left) or -c (right).
+static const int SW_NEWTON_MAX = 20;
+template <class T> inline T sw_tol() { return sizeof(T) == 4 ? T(9.5367431640625e-07) : T(2.8421709430404007e-14); }
 
 template <class T> inline void sw_fK(T h, T hK, T cK, T g, T& f, T& df) {
   if (h <= hK) {
@@ -277,25 +278,33 @@ template <class T> inline void sw_fK(T h, T hK, T cK, T g, T& f, T& df) {
   }
 }
 
-// Riemann state at x/t = 0 in the frame of the normal: (h, un, ut).
-template <class T>
-inline void sw_riemann(T hL, T uL, T tL, T hR, T uR, T tR, T g, T& h, T& un, T& ut) {
-  const T cL = std::sqrt(g * hL), cR = std::sqrt(g * hR);
+// Star state (h*, u*) of the Riemann problem along the normal.
+template <class T> inline void sw_star(T hL, T uL, T hR, T uR, T g, T cL, T cR, T& hs, T& us) {
   T h0 = (T(0.5) * (cL + cR)) - (T(0.25) * (uR - uL));
   h0 = h0 > T(0) ? (h0 * h0) / g : T(1e-6) * (hL < hR ? hL : hR);
-  T hs = h0;
-  for (int it = 0; it < SW_NEWTON; ++it) {
+  hs = h0;
+  for (int it = 0; it < SW_NEWTON_MAX; ++it) {
     T fl, dl, fr, dr;
     sw_fK<T>(hs, hL, cL, g, fl, dl);
     sw_fK<T>(hs, hR, cR, g, fr, dr);
     const T f = (fl + fr) + (uR - uL);
-    T hn = hs - f / (dl + dr);
+    const T hn = hs - f / (dl + dr);
+    const T step = hn > hs ? hn - hs : hs - hn;
     hs = hn > T(0) ? hn : T(0.5) * hs;
+    if (step <= sw_tol<T>() * hs) break;
   }
   T fl, dl, fr, dr;
   sw_fK<T>(hs, hL, cL, g, fl, dl);
   sw_fK<T>(hs, hR, cR, g, fr, dr);
-  const T us = (T(0.5) * (uL + uR)) + (T(0.5) * (fr - fl));
+  us = (T(0.5) * (uL + uR)) + (T(0.5) * (fr - fl));
+}
+
+// Riemann state at x/t = 0 in the frame of the normal: (h, un, ut).
+template <class T>
+inline void sw_riemann(T hL, T uL, T tL, T hR, T uR, T tR, T g, T& h, T& un, T& ut) {
+  const T cL = std::sqrt(g * hL), cR = std::sqrt(g * hR);
+  T hs, us;
+  sw_star<T>(hL, uL, hR, uR, g, cL, cR, hs, us);
   const T cs = std::sqrt(g * hs);
   if (us >= T(0)) {  // the interface sees the left side of the contact
     ut = tL;

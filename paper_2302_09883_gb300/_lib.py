@@ -9,7 +9,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libwcsim.so")
 
-SCHEME = {"d2q9": 0, "d3q19": 1, "euler2d": 2}
+SCHEME = {"d2q9": 0, "d3q19": 1, "euler2d": 2, "transport": 3, "swe": 4}
 WAVELET = {"bl53": 0, "haar": 1}
 RULE = {"const": 0, "accum": 1, "capped": 2}
 STORE = {"f64": 0, "f32": 1, "bf16": 2, "i8": 3}
@@ -31,7 +31,8 @@ class Grid(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("wavelet", C.c_int), ("rule", C.c_int), ("detail_store", C.c_int), ("compute", C.c_int),
                 ("tau", C.c_double), ("cfl", C.c_double), ("gamma", C.c_double), ("arena_factor", C.c_double),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("velocity", C.c_double * 2), ("gravity", C.c_double),
+                ("length", C.c_double)]
 
 
 class StepStats(C.Structure):

@@ -41,6 +41,15 @@ void reg_d2q9_bl53_i8_p64l4(std::vector<KernelEntry>&);
 void reg_euler_bl53_i8_p64l4(std::vector<KernelEntry>&);
 void reg_euler_bl53_f64_p32l3(std::vector<KernelEntry>&);
 void reg_euler_bl53_bf16_p64l4(std::vector<KernelEntry>&);
+void reg_transport_f32_p64l1(std::vector<KernelEntry>&);
+void reg_transport_f32_p64l2(std::vector<KernelEntry>&);
+void reg_transport_f32_p64l3(std::vector<KernelEntry>&);
+void reg_transport_f32_p64l4(std::vector<KernelEntry>&);
+void reg_transport_f32_p64l5(std::vector<KernelEntry>&);
+void reg_transport_f64_p32l3(std::vector<KernelEntry>&);
+void reg_swe_f32_p64l4(std::vector<KernelEntry>&);
+void reg_swe_f32_p32l4(std::vector<KernelEntry>&);
+void reg_swe_f64_p32l3(std::vector<KernelEntry>&);
 
 void reg_d3q19_p32l3(std::vector<Kernel3Entry>&);
 void reg_d3q19_p16l3(std::vector<Kernel3Entry>&);
@@ -60,6 +69,15 @@ void register_all(std::vector<KernelEntry>& v) {
   reg_euler_bl53_i8_p64l4(v);
   reg_euler_bl53_f64_p32l3(v);
   reg_euler_bl53_bf16_p64l4(v);
+  reg_transport_f32_p64l1(v);
+  reg_transport_f32_p64l2(v);
+  reg_transport_f32_p64l3(v);
+  reg_transport_f32_p64l4(v);
+  reg_transport_f32_p64l5(v);
+  reg_transport_f64_p32l3(v);
+  reg_swe_f32_p64l4(v);
+  reg_swe_f32_p32l4(v);
+  reg_swe_f64_p32l3(v);
 }
 }  // namespace wcs
 
@@ -95,6 +113,7 @@ struct wcs_sim {
   int device = 0;  // CUDA device current at creation (owns every buffer)
   int scheme = 0, wavelet = 0, prec = 0, store = 0, rule = 0, P = 0, L = 0;
   double eps = 0, tau = 1, cfl = 0.4, gamma = 1.4;
+  double alpha = 0, beta = 0, grav = 9.81, length = 1;  // FV: velocity, gravity, domain side
   int dims = 2;
   int64_t n[3] = {0, 0, 1};
   int per[3] = {1, 1, 1};
@@ -231,7 +250,13 @@ static wcs::PatchArgs base_args(const wcs_sim* s) {
   a.gm1_32 = float(s->gamma - 1.0);
   a.gm1_64 = s->gamma - 1.0;
   a.cfl = s->cfl;
-  a.ncell_x = s->n[0];
+  a.hcell = s->length / double(s->n[0]);
+  a.alpha64 = s->alpha;
+  a.beta64 = s->beta;
+  a.g64 = s->grav;
+  a.alpha32 = float(s->alpha);
+  a.beta32 = float(s->beta);
+  a.g32 = float(s->grav);
   a.G0 = s->G[0];
   a.G1 = s->G[1];
   a.field_sel = -1;
@@ -557,6 +582,9 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
   for (int a = 0; a < 2; ++a)
     if (grid->n[a] <= 0 || grid->n[a] % patch) return fail(nullptr, WCS_E_ARG, "grid not a multiple of the patch size");
   if (scheme == WCS_D2Q9 && (grid->periodic_mask & 3u) != 3u) return fail(nullptr, WCS_E_ARG, "D2Q9 needs periodic axes");
+  if (scheme == WCS_TRANSPORT && !(std::max(std::fabs(opts->velocity[0]), std::fabs(opts->velocity[1])) > 0) &&
+      opts->cfl > 0)
+    return fail(nullptr, WCS_E_ARG, "transport with a CFL time step needs a non-zero velocity");
   if (opts->rule < 0 || opts->rule > 2) return fail(nullptr, WCS_E_ARG, "bad threshold rule");
 
   {
@@ -583,6 +611,13 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
   s->tau = opts->tau > 0 ? opts->tau : 1.0;
   s->cfl = opts->cfl != 0 ? opts->cfl : 0.4;
   s->gamma = opts->gamma > 1 ? opts->gamma : 1.4;
+  s->alpha = opts->velocity[0];
+  s->beta = opts->velocity[1];
+  s->grav = opts->gravity > 0 ? opts->gravity : 9.81;
+  s->length = opts->length > 0 ? opts->length : 1.0;
+  // transport: v_max is the given velocity, so dt/h = cfl / max(|alpha|,
+  // |beta|) is fixed and handed to the kernel as such (cfl < 0)
+  if (scheme == WCS_TRANSPORT && s->cfl > 0) s->cfl = -(s->cfl / std::max(std::fabs(s->alpha), std::fabs(s->beta)));
   s->stream = static_cast<cudaStream_t>(opts->cuda_stream);
   for (int a = 0; a < 2; ++a) {
     s->n[a] = grid->n[a];
@@ -592,7 +627,7 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
   s->npx = int(s->n[0] / patch);
   s->npy = int(s->n[1] / patch);
   s->npatch = s->npx * s->npy;
-  s->F = scheme == WCS_D2Q9 ? 9 : 4;
+  s->F = wcs::scheme_fields(scheme);
   s->E = s->wavelet == WCS_BL53 ? patch + 1 : patch;
   s->NC1 = (patch >> levels) + (s->wavelet == WCS_BL53 ? 1 : 0);
   s->nc = s->NC1 * s->NC1;
@@ -652,7 +687,8 @@ wcs_status wcs_sim_use_mlp(wcs_sim* s, wcs_mlp* m, double eps_lo, double eps_hi)
     s->mlp = nullptr;
     return WCS_OK;
   }
-  if (s->dims == 2 && s->ke.scheme != WCS_D2Q9 && s->ke.scheme != WCS_EULER2D) return WCS_E_UNSUPPORTED;
+  if (s->dims == 2 && (!s->ke.launch_feat || (s->ke.scheme != WCS_D2Q9 && s->ke.scheme != WCS_EULER2D)))
+    return fail(s, WCS_E_UNSUPPORTED, "no learned-threshold kernel for this configuration");
   const int nin = nfeat(s);
   if (wcs_mlp_nparam(m) != 64 * nin + 64 + 64 * 64 + 64 + 64 + 1)
     return fail(s, WCS_E_ARG, "the network's input size must be " + std::to_string(nin) +
@@ -747,7 +783,7 @@ wcs_status wcs_init_macro(wcs_sim* s, const double* const* fields, int nfields, 
     const wcs_status st = init3(s, fields, nfields, src_is_device);
     return st != WCS_OK ? st : wcs_sync(s);
   }
-  const int need = s->scheme == WCS_D2Q9 ? 3 : 4;
+  const int need = s->scheme == WCS_D2Q9 ? 3 : (s->scheme == WCS_EULER2D ? 4 : (s->scheme == WCS_TRANSPORT ? 1 : 3));
   if (nfields < need) return fail(s, WCS_E_ARG, "init needs " + std::to_string(need) + " macroscopic fields");
   const size_t plane = size_t(s->G[0]) * size_t(s->G[1]);
   double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -1019,11 +1055,17 @@ wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
       o->momentum[0] += cx[i] * o->field_sum[i];
       o->momentum[1] += cy[i] * o->field_sum[i];
     }
-  } else {
+  } else if (s->scheme == WCS_EULER2D) {
     o->mass = o->field_sum[0];
     o->momentum[0] = o->field_sum[1];
     o->momentum[1] = o->field_sum[2];
     o->energy = o->field_sum[3];
+  } else if (s->scheme == WCS_SWE) {
+    o->mass = o->field_sum[0];
+    o->momentum[0] = o->field_sum[1];
+    o->momentum[1] = o->field_sum[2];
+  } else {
+    o->mass = o->field_sum[0];
   }
   o->step = s->nstep;
   o->time = c.time;
@@ -1119,6 +1161,11 @@ wcs_status wcs_batch_create(wcs_sim* const* sims, int nsims, wcs_batch** out) {
     }
     if (s->mlp) {
       g_create_err = "batch: a simulation with a learned threshold is stepped alone";
+      batch_free(b);
+      return WCS_E_UNSUPPORTED;
+    }
+    if (!s->ke.launch_batch) {
+      g_create_err = "batch: no batched kernel for this configuration";
       batch_free(b);
       return WCS_E_UNSUPPORTED;
     }

@@ -10,7 +10,14 @@
 
 namespace wcs {
 
-enum { SCH_D2Q9 = 0, SCH_D3Q19 = 1, SCH_EULER2D = 2 };
+enum { SCH_D2Q9 = 0, SCH_D3Q19 = 1, SCH_EULER2D = 2, SCH_TRANSPORT = 3, SCH_SWE = 4 };
+
+// Stored fields of a scheme and whether it is a finite-volume scheme
+// (eq. vf_scheme: a ghost ring of the state, a time step dt/h).
+__host__ __device__ constexpr int scheme_fields(int s) {
+  return s == SCH_D2Q9 ? 9 : (s == SCH_D3Q19 ? 19 : (s == SCH_EULER2D ? 4 : (s == SCH_TRANSPORT ? 1 : 3)));
+}
+__host__ __device__ constexpr bool scheme_fv(int s) { return s == SCH_EULER2D || s == SCH_TRANSPORT || s == SCH_SWE; }
 enum { WV_BL53 = 0, WV_HAAR = 1 };
 enum { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2, ST_I8 = 3 };
 enum { MODE_INIT = 0, MODE_STEP = 1, MODE_EXPORT = 2 };
@@ -443,6 +450,107 @@ template <typename T> __device__ __forceinline__ void euler_cons(T rho, T u, T v
   T ke = W[1] * u + W[2] * v;
   ke = T(0.5) * ke;
   W[3] = p / gm1 + ke;
+}
+
+// ------------------------------------------------------------- transport
+// Linear transport (Sec. 3.1.2) with the upwind flux of eq. upwind_trans:
+// Q(WL, WR, N) = WL max(a.N, 0) + WR min(a.N, 0); a.N of the four normals is
+// alpha, -alpha, beta, -beta.
+template <typename T> __device__ __forceinline__ T transport_flux(T WL, T WR, T aN) {
+  const T pos = aN > T(0) ? aN : T(0);
+  const T neg = aN < T(0) ? aN : T(0);
+  return WL * pos + WR * neg;
+}
+
+// --------------------------------------------------------- shallow water
+// Godunov flux of the shallow-water equations (Sec. 3.2.4) from the exact
+// Riemann solution in the frame of the normal (wet bed): the star depth by
+// Newton steps from the two-rarefaction guess, stopping once a step changes
+// it by at most 2^-20 (FP32) or 2^-45 (FP64) relative or after 20 steps; the
+// state at x/t = 0 on the side of the contact the interface sees (the side's
+// state, the star state or the sonic point of a transonic rarefaction).
+constexpr int SW_NEWTON_MAX = 20;
+template <typename T> __device__ __forceinline__ T sw_tol() {
+  return sizeof(T) == 4 ? T(9.5367431640625e-07) : T(2.8421709430404007e-14);
+}
+
+template <typename T> __device__ __forceinline__ void sw_fK(T h, T hK, T cK, T g, T& f, T& df) {
+  if (h <= hK) {
+    const T c = sqrt(g * h);
+    f = T(2) * (c - cK);
+    df = g / c;
+  } else {
+    const T s = (h + hK) / (h * hK);
+    const T q = sqrt((T(0.5) * g) * s);
+    f = (h - hK) * q;
+    df = q - ((h - hK) * (T(0.25) * g)) / ((h * h) * q);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void sw_riemann(T hL, T uL, T tL, T hR, T uR, T tR, T g, T& h, T& un, T& ut) {
+  const T cL = sqrt(g * hL), cR = sqrt(g * hR);
+  T h0 = (T(0.5) * (cL + cR)) - (T(0.25) * (uR - uL));
+  h0 = h0 > T(0) ? (h0 * h0) / g : T(1e-6) * (hL < hR ? hL : hR);
+  T hs = h0;
+#pragma unroll 1
+  for (int it = 0; it < SW_NEWTON_MAX; ++it) {
+    T fl, dl, fr, dr;
+    sw_fK<T>(hs, hL, cL, g, fl, dl);
+    sw_fK<T>(hs, hR, cR, g, fr, dr);
+    const T f = (fl + fr) + (uR - uL);
+    const T hn = hs - f / (dl + dr);
+    const T step = hn > hs ? hn - hs : hs - hn;
+    hs = hn > T(0) ? hn : T(0.5) * hs;
+    if (step <= sw_tol<T>() * hs) break;
+  }
+  T fl, dl, fr, dr;
+  sw_fK<T>(hs, hL, cL, g, fl, dl);
+  sw_fK<T>(hs, hR, cR, g, fr, dr);
+  const T us = (T(0.5) * (uL + uR)) + (T(0.5) * (fr - fl));
+  const T cs = sqrt(g * hs);
+  if (us >= T(0)) {
+    ut = tL;
+    if (hs > hL) {
+      const T sL = uL - cL * sqrt((hs * (hs + hL)) / (T(2) * (hL * hL)));
+      if (sL >= T(0)) { h = hL; un = uL; } else { h = hs; un = us; }
+    } else {
+      if (uL - cL >= T(0)) { h = hL; un = uL; }
+      else if (us - cs <= T(0)) { h = hs; un = us; }
+      else { const T c = (uL + T(2) * cL) / T(3); h = (c * c) / g; un = c; }
+    }
+  } else {
+    ut = tR;
+    if (hs > hR) {
+      const T sR = uR + cR * sqrt((hs * (hs + hR)) / (T(2) * (hR * hR)));
+      if (sR <= T(0)) { h = hR; un = uR; } else { h = hs; un = us; }
+    } else {
+      if (uR + cR <= T(0)) { h = hR; un = uR; }
+      else if (us + cs >= T(0)) { h = hs; un = us; }
+      else { const T c = (T(2) * cR - uR) / T(3); h = (c * c) / g; un = -c; }
+    }
+  }
+}
+
+template <typename T> __device__ __forceinline__ void sw_godunov(const T* WL, const T* WR, T nx, T ny, T g, T* Q) {
+  const T uL = WL[1] / WL[0], vL = WL[2] / WL[0], uR = WR[1] / WR[0], vR = WR[2] / WR[0];
+  const T unL = uL * nx + vL * ny, utL = vL * nx - uL * ny;
+  const T unR = uR * nx + vR * ny, utR = vR * nx - uR * ny;
+  T h, un, ut;
+  sw_riemann<T>(WL[0], unL, utL, WR[0], unR, utR, g, h, un, ut);
+  const T f0 = h * un;
+  const T f1 = f0 * un + (T(0.5) * g) * (h * h);
+  const T f2 = f0 * ut;
+  Q[0] = f0;
+  Q[1] = f1 * nx - f2 * ny;
+  Q[2] = f1 * ny + f2 * nx;
+}
+
+template <typename T> __device__ __forceinline__ T sw_speed(const T* W, T g) {
+  const T u = W[1] / W[0], v = W[2] / W[0];
+  const T c = sqrt(g * W[0]);
+  const T su = fabs(u) + c, sv = fabs(v) + c;
+  return su > sv ? su : sv;
 }
 
 // Warp exclusive scan helper.

@@ -57,6 +57,42 @@ cudaError_t launch_patch(int mode, const PatchArgs& a, int npatch, cudaStream_t 
   return launch_mode<SCH, WV, T, ST, P, L, MODE_EXPORT>(a, npatch, s);
 }
 
+// Init / step / export only (no batch and no learned-threshold variants).
+template <int SCH, int WV, typename T, int ST, int P, int L>
+cudaError_t prepare_patch_lite() {
+  typedef Cfg<SCH, WV, T, ST, P, L> C;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(C::SMEM))) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(C::SMEM))) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_EXPORT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(C::SMEM));
+}
+
+template <int SCH, int WV, typename T, int ST, int P, int L>
+KernelEntry make_entry_lite() {
+  typedef Cfg<SCH, WV, T, ST, P, L> C;
+  KernelEntry k;
+  k.scheme = SCH;
+  k.wavelet = WV;
+  k.prec = sizeof(T) == 8 ? 0 : 1;
+  k.store = ST;
+  k.P = P;
+  k.L = L;
+  k.ring = C::RING;
+  k.pitch = C::PW;
+  k.smem = C::SMEM;
+  k.threads = C::NT;
+  k.launch = &launch_patch<SCH, WV, T, ST, P, L>;
+  k.launch_batch = nullptr;
+  k.launch_feat = nullptr;
+  k.prepare = &prepare_patch_lite<SCH, WV, T, ST, P, L>;
+  return k;
+}
+
 template <int SCH, int WV, typename T, int ST, int P, int L>
 KernelEntry make_entry() {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
@@ -83,4 +119,9 @@ KernelEntry make_entry() {
 #define WCS_INSTANTIATE(NAME, SCH, WV, T, ST, P, L)                                        \
   namespace wcs {                                                                           \
   void NAME(std::vector<KernelEntry>& v) { v.push_back(make_entry<SCH, WV, T, ST, P, L>()); } \
+  }
+
+#define WCS_INSTANTIATE_LITE(NAME, SCH, WV, T, ST, P, L)                                        \
+  namespace wcs {                                                                                \
+  void NAME(std::vector<KernelEntry>& v) { v.push_back(make_entry_lite<SCH, WV, T, ST, P, L>()); } \
   }

@@ -58,7 +58,9 @@ struct PatchArgs {
   double eps_lo, eps_hi;         // clamp of the network's eps; non-finite -> eps
   float omega32, gamma32, gm1_32;   // the same parameters rounded once on the host
   double gm1_64;
-  long long ncell_x;            // cells along x (time accounting)
+  double hcell;                 // cell size (time accounting of FV schemes)
+  float alpha32, beta32, g32;   // transport velocity, shallow-water gravity
+  double alpha64, beta64, g64;  // (rounded once on the host)
   const double* macro[4];       // MODE_INIT inputs, [G1][G0]
   const void* state;            // MODE_INIT from a dense state instead
                                 // (F planes [G1][G0]; null: macro fields)
@@ -71,12 +73,13 @@ struct PatchArgs {
 };
 
 template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
-  static constexpr int F = SCH == SCH_D2Q9 ? 9 : 4;
+  static constexpr int F = scheme_fields(SCH);
+  static constexpr bool FV = scheme_fv(SCH);  // ghost ring of the state, dt/h
   static constexpr int E = WV == WV_BL53 ? P + 1 : P;
   static constexpr int W = E + 2;
   static constexpr int PW = (W % 2) ? W : W + 1;
   static constexpr int TS = W * PW;
-  static constexpr int NTILE = SCH == SCH_EULER2D ? 2 * F : F;
+  static constexpr int NTILE = FV ? 2 * F : F;
   static constexpr int NC1 = (P >> L) + (WV == WV_BL53 ? 1 : 0);
   static constexpr int NC = NC1 * NC1;
   static constexpr int NALL = E * E;
@@ -92,7 +95,7 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   // D2Q9 on BL5/3 patches reads its ghosts from the neighbours' records
   // (ring-free); the other kernels keep a ghost ring
   static constexpr bool RINGFREE = SCH == SCH_D2Q9 && WV == WV_BL53;
-  static constexpr int RING = RINGFREE ? 0 : (SCH == SCH_D2Q9 ? 12 * E + 4 : 16 * E);
+  static constexpr int RING = RINGFREE ? 0 : (SCH == SCH_D2Q9 ? 12 * E + 4 : 4 * F * E);
   static constexpr int NT = sizeof(T) == 8 ? 512 : 768;
   static constexpr int NWARP = NT / 32;
   static constexpr int XLO = WV == WV_BL53 ? 1 : 0;
@@ -102,7 +105,13 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   static constexpr size_t OFF_MW = (size_t(NTILE) * TS * sizeof(T) + 15) / 16 * 16;
   static constexpr size_t OFF_PRE = OFF_MW + size_t(F) * NW * 4;
   static constexpr size_t OFF_EMW = (OFF_PRE + size_t(3) * F * NW * 2 + 15) / 16 * 16;
-  static constexpr size_t OFF_BMAX = OFF_EMW + size_t(F) * NW * 4;
+  // the decode's column masks (F (E + 1) ceil(E/32) words) live at OFF_EMW
+  // and run on into the band data after it; with few fields that is not
+  // enough room, and the mask-word region grows by what is missing
+  static constexpr size_t COLM_BYTES = size_t(F) * (E + 1) * ((E + 31) / 32) * 4;
+  static constexpr size_t EMW_REST = size_t(F) * NW * 4 + size_t(F) * NB * 12 + size_t(2) * NB * sizeof(T);
+  static constexpr size_t EMW_BYTES = size_t(F) * NW * 4 + (COLM_BYTES > EMW_REST ? COLM_BYTES - EMW_REST : 0);
+  static constexpr size_t OFF_BMAX = OFF_EMW + EMW_BYTES;
   static constexpr size_t OFF_SCL = OFF_BMAX + size_t(F) * NB * 4;
   static constexpr size_t OFF_SINV = OFF_SCL + size_t(F) * NB * 4;
   static constexpr size_t OFF_TAU = (OFF_SINV + size_t(F) * NB * 4 + 15) / 16 * 16;
@@ -740,15 +749,21 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   const int px = pid % a.npx, py = pid / a.npx;
   // scheme parameters in the compute type (rounded once on the host: the
   // FP64 units of this GPU are too few to convert them in every thread)
-  T omega, gamma, gm1;
+  T omega, gamma, gm1, alpha, beta, grav;
   if constexpr (sizeof(T) == 8) {
     omega = T(a.omega);
     gamma = T(a.gamma);
     gm1 = T(a.gm1_64);
+    alpha = T(a.alpha64);
+    beta = T(a.beta64);
+    grav = T(a.g64);
   } else {
     omega = T(a.omega32);
     gamma = T(a.gamma32);
     gm1 = T(a.gm1_32);
+    alpha = T(a.alpha32);
+    beta = T(a.beta32);
+    grav = T(a.g32);
   }
 
   // Window of field f: where node (0,0) of the state being read (in) or
@@ -781,7 +796,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   // ring values are fetched into registers now so that their latency hides
   // behind the record staging and the decode.
   constexpr bool RF = C::RINGFREE;
-  constexpr int NGH = RF ? 0 : (SCH == SCH_D2Q9 ? 12 * E + 4 : 16 * E);  // ghost cells to fill from a ring
+  constexpr int NGH = RF ? 0 : (SCH == SCH_D2Q9 ? 12 * E + 4 : 4 * F * E);  // ghost cells to fill from a ring
   constexpr int NG = NGH > 0 ? (NGH + NT - 1) / NT : 1;
   T gv[NG];
   int gdst[NG], gsrc[NG];  // ghost tile index (-1: none); own-node source for outflow copies (-1: ring value)
@@ -820,23 +835,25 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
           else { gdst[g] = 8 * TS + (E + 1) * PW; gv[g] = rin[size_t(pyp * a.npx + pxm) * C::RING + 12 * E + 1]; }
         }
       } else {
-        const int sd = t / (4 * E), r = t - sd * 4 * E, k = r / 4, q = r - 4 * k;
+        // ring of a patch: side s (0 west, 1 east, 2 south, 3 north) at
+        // s F E, node k of the side at F k, field q
+        const int sd = t / (F * E), r = t - sd * F * E, k = r / F, q = r - F * k;
         const int base = q * TS + PW + 1;
         if (sd == 0) {
           gdst[g] = base + k * PW - 1;
-          if (a.per_x || px > 0) gv[g] = rin[size_t(py * a.npx + pxm) * C::RING + 4 * E + 4 * k + q];
+          if (a.per_x || px > 0) gv[g] = rin[size_t(py * a.npx + pxm) * C::RING + F * E + F * k + q];
           else gsrc[g] = base + k * PW;
         } else if (sd == 1) {
           gdst[g] = base + k * PW + E;
-          if (a.per_x || px < a.npx - 1) gv[g] = rin[size_t(py * a.npx + pxp) * C::RING + 4 * k + q];
+          if (a.per_x || px < a.npx - 1) gv[g] = rin[size_t(py * a.npx + pxp) * C::RING + F * k + q];
           else gsrc[g] = base + k * PW + (E - 1);
         } else if (sd == 2) {
           gdst[g] = base - PW + k;
-          if (a.per_y || py > 0) gv[g] = rin[size_t(pym * a.npx + px) * C::RING + 12 * E + 4 * k + q];
+          if (a.per_y || py > 0) gv[g] = rin[size_t(pym * a.npx + px) * C::RING + 3 * F * E + F * k + q];
           else gsrc[g] = base + k;
         } else {
           gdst[g] = base + E * PW + k;
-          if (a.per_y || py < a.npy - 1) gv[g] = rin[size_t(pyp * a.npx + px) * C::RING + 8 * E + 4 * k + q];
+          if (a.per_y || py < a.npy - 1) gv[g] = rin[size_t(pyp * a.npx + px) * C::RING + 2 * F * E + F * k + q];
           else gsrc[g] = base + (E - 1) * PW + k;
         }
       }
@@ -885,9 +902,9 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         a.ctl->live[a.cur_rst] = a.ctl->cursor[a.cur_rst];
         a.ctl->cursor[a.cur_rst] = 0ull;
         a.ctl->time_in[a.cur_rst] = a.ctl->time;
-        if constexpr (SCH == SCH_EULER2D) {
+        if constexpr (C::FV) {
           const double smax = __longlong_as_double((long long)a.ctl->smax[a.smax_rd]);
-          a.ctl->time += (a.cfl > 0 ? a.cfl / smax : -a.cfl) / double(a.ncell_x);
+          a.ctl->time += (a.cfl > 0 ? a.cfl / smax : -a.cfl) * a.hcell;
         } else {
           a.ctl->time += 1.0;
         }
@@ -1119,21 +1136,27 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       const T lam = *lam_sm;
       for (int t = tid; t < E * E; t += NT) {
         const int y = t / E, x = t - y * E;
-        T W0[4], acc[4];
+        T W0[F], acc[F];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) W0[q] = tiles[win_in(q) + y * PW + x];
+        for (int q = 0; q < F; ++q) W0[q] = tiles[win_in(q) + y * PW + x];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int nx = k == 0 ? 1 : (k == 1 ? -1 : 0), ny = k == 2 ? 1 : (k == 3 ? -1 : 0);
-          T Wn[4], Fl[4];
+          T Wn[F], Fl[F];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) Wn[q] = tiles[win_in(q) + (y + ny) * PW + (x + nx)];
-          euler_rusanov<T>(W0, Wn, T(nx), T(ny), gm1, gamma, Fl);
+          for (int q = 0; q < F; ++q) Wn[q] = tiles[win_in(q) + (y + ny) * PW + (x + nx)];
+          if constexpr (SCH == SCH_EULER2D) {
+            euler_rusanov<T>(W0, Wn, T(nx), T(ny), gm1, gamma, Fl);
+          } else if constexpr (SCH == SCH_SWE) {
+            sw_godunov<T>(W0, Wn, T(nx), T(ny), grav, Fl);
+          } else {  // transport: a.N = alpha, -alpha, beta, -beta
+            Fl[0] = transport_flux<T>(W0[0], Wn[0], k == 0 ? alpha : (k == 1 ? -alpha : (k == 2 ? beta : -beta)));
+          }
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q] = k == 0 ? Fl[q] : acc[q] + Fl[q];
+          for (int q = 0; q < F; ++q) acc[q] = k == 0 ? Fl[q] : acc[q] + Fl[q];
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) tiles[win_out(q) + y * PW + x] = W0[q] - lam * acc[q];
+        for (int q = 0; q < F; ++q) tiles[win_out(q) + y * PW + x] = W0[q] - lam * acc[q];
       }
       __syncthreads();
     }
@@ -1156,8 +1179,14 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
                                      : T(reinterpret_cast<const float*>(a.state)[f * plane + g]);
       } else if constexpr (SCH == SCH_D2Q9) {
         d2q9_equilibrium<T>(T(a.macro[0][g]), T(a.macro[1][g]), T(a.macro[2][g]), sv);
-      } else {
+      } else if constexpr (SCH == SCH_EULER2D) {
         euler_cons<T>(T(a.macro[0][g]), T(a.macro[1][g]), T(a.macro[2][g]), T(a.macro[3][g]), gm1, sv);
+      } else if constexpr (SCH == SCH_TRANSPORT) {
+        sv[0] = T(a.macro[0][g]);
+      } else {  // shallow water: (h, u, v) -> (h, h u, h v)
+        sv[0] = T(a.macro[0][g]);
+        sv[1] = sv[0] * T(a.macro[1][g]);
+        sv[2] = sv[0] * T(a.macro[2][g]);
       }
 #pragma unroll
       for (int f = 0; f < F; ++f) tiles[win_out(f) + y * PW + x] = sv[f];
@@ -1705,24 +1734,28 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       const int x = s == 0 ? C::XLO : (s == 1 ? C::XHI : k);
       const int y = s == 2 ? C::XLO : (s == 3 ? C::XHI : k);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) rout[s * 4 * E + 4 * k + q] = tiles[win_out(q) + y * PW + x];
+      for (int q = 0; q < F; ++q) rout[s * F * E + F * k + q] = tiles[win_out(q) + y * PW + x];
     }
-    // largest signal speed of the new state (next step's dt)
-    T smax = T(0);
-    for (int t = tid; t < E * E; t += NT) {
-      const int y = t / E, x = t - y * E;
-      T Wv[4];
+    if constexpr (SCH == SCH_EULER2D || SCH == SCH_SWE) {
+      // largest signal speed of the new state (next step's dt)
+      T smax = T(0);
+      for (int t = tid; t < E * E; t += NT) {
+        const int y = t / E, x = t - y * E;
+        T Wv[F];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) Wv[q] = tiles[win_out(q) + y * PW + x];
-      const T s = euler_speed<T>(Wv, gm1, gamma);
-      smax = s > smax ? s : smax;
-    }
+        for (int q = 0; q < F; ++q) Wv[q] = tiles[win_out(q) + y * PW + x];
+        T s;
+        if constexpr (SCH == SCH_EULER2D) s = euler_speed<T>(Wv, gm1, gamma);
+        else s = sw_speed<T>(Wv, grav);
+        smax = s > smax ? s : smax;
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T other = __shfl_xor_sync(0xffffffffu, smax, o);
-      smax = other > smax ? other : smax;
+      for (int o = 16; o > 0; o >>= 1) {
+        const T other = __shfl_xor_sync(0xffffffffu, smax, o);
+        smax = other > smax ? other : smax;
+      }
+      if (lane == 0) atomicMax(&a.ctl->smax[a.smax_wr], dbl_bits(double(smax)));
     }
-    if (lane == 0) atomicMax(&a.ctl->smax[a.smax_wr], dbl_bits(double(smax)));
   }
 }
 

@@ -60,11 +60,13 @@ class Sim:
     """One compressed-patch simulation on the current CUDA device."""
 
     def __init__(self, scheme, wavelet, nx, ny, P, L, eps, prec="f32", store="bf16", rule="const",
-                 periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, arena_factor=0.0, stream=None):
+                 periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, arena_factor=0.0, stream=None,
+                 velocity=(0.0, 0.0), gravity=9.81, length=1.0):
         self.scheme = scheme
         o = B.Opts()
         o.wavelet, o.rule, o.detail_store, o.compute = B.WAVELET[wavelet], B.RULE[rule], B.STORE[store], B.PREC[prec]
         o.tau, o.cfl, o.gamma, o.arena_factor = tau, cfl, gamma, arena_factor
+        o.velocity[0], o.velocity[1], o.gravity, o.length = velocity[0], velocity[1], gravity, length
         o.cuda_stream = _stream_ptr(stream)
         h = C.c_void_p()
         g = _grid(nx, ny, periodic)
@@ -207,9 +209,11 @@ class Sim3(Sim):
 class Dense:
     """Uncompressed FP32 baseline of the same scheme."""
 
-    def __init__(self, scheme, nx, ny, periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, stream=None):
+    def __init__(self, scheme, nx, ny, periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, stream=None,
+                 velocity=(0.0, 0.0), gravity=9.81, length=1.0):
         o = B.Opts()
         o.tau, o.cfl, o.gamma = tau, cfl, gamma
+        o.velocity[0], o.velocity[1], o.gravity, o.length = velocity[0], velocity[1], gravity, length
         o.cuda_stream = _stream_ptr(stream)
         g = _grid(nx, ny, periodic)
         h = C.c_void_p()
@@ -217,7 +221,7 @@ class Dense:
         if st != 0:
             raise B.WcsError(st, "dense baseline create failed")
         self.h = h
-        self.F = 9 if scheme == "d2q9" else 4
+        self.F = {"d2q9": 9, "euler2d": 4, "transport": 1, "swe": 3}[scheme]
         self.G = tuple(n if per else n + 1 for n, per in zip((nx, ny), periodic))
 
     def close(self):
