@@ -190,6 +190,20 @@ int64_t wcs_resident_bytes(const wcs_sim* sim);
  * Synchronises. */
 wcs_status wcs_import_field(wcs_sim* sim, int field, const void* src, int src_is_device, int dtype);
 
+/* Entropy-codes the records of the current state: the library's own
+ * lossless stage on top of the bitmask codec, where the paper (Sec. 2.3.2)
+ * runs a general-purpose byte compressor.  Order-0 byte-wise rANS (range
+ * asymmetric numeral systems) with one frequency table for the state,
+ * scaled to 2^12; layout: u32 npatch, u32 12, u16 freq[256], per patch u32
+ * record bytes and u32 coded bytes, then the patches' streams (each: the
+ * final 32-bit coder state, little endian, then its renormalisation bytes
+ * in decoding order).  The coded state is decoded again on the device and
+ * compared byte for byte with the records (a difference returns
+ * WCS_E_CUDA).  dst_host = NULL asks for the size only (*nbytes); a buffer
+ * of cap < *nbytes bytes gets WCS_E_ARG.  Synchronises; takes temporary
+ * device memory of about 1.5x the live record bytes. */
+wcs_status wcs_entropy_code(wcs_sim* sim, void* dst_host, int64_t cap, int64_t* nbytes);
+
 /* FP64 diagnostics of the current state (synchronises). */
 wcs_status wcs_stats(wcs_sim* sim, wcs_step_stats* out);
 
@@ -242,9 +256,11 @@ void* wcs_stream(const wcs_sim* sim);
 const char* wcs_last_error(const wcs_sim* sim);
 
 /* ------------------------------------------------------------------------
- * Batches of independent simulations (many grids of different sizes, one
- * launch per kind of kernel per step, six steps captured in one CUDA graph
- * and replayed).  Every simulation must be initialised, created on the same
+ * Batches of independent simulations (many grids of different sizes; one
+ * launch per step when the batch holds the two patch sizes of a merged
+ * kernel (D2Q9, BL5/3, FP32, BF16: 64 cells / 4 levels with 32 / 3), else
+ * one launch per kind of kernel; six steps captured in one CUDA graph and
+ * replayed).  Every simulation must be initialised, created on the same
  * stream and at the same step; 3-D simulations and simulations with a
  * learned threshold are stepped alone (WCS_E_UNSUPPORTED).  The batch borrows the simulations (destroy
  * the batch before them); stepping one of them outside the batch makes the
@@ -257,6 +273,16 @@ void wcs_batch_destroy(wcs_batch* b);
 wcs_status wcs_batch_step(wcs_batch* b, int64_t n);
 /* Waits and returns the first device error of any simulation. */
 wcs_status wcs_batch_sync(wcs_batch* b);
+/* Kernel launches per step (1 when the batch's two patch sizes run in one
+ * merged persistent launch, else one per kind of kernel) and the merged
+ * launch's grid (0 if none). */
+wcs_status wcs_batch_launches_per_step(const wcs_batch* b, int* launches, int* grid);
+/* Launch-shape tuner of a merged batch: times `steps` steps with each of the
+ * ncand grids (blocks of the persistent launch; more blocks than items are
+ * cut to the items) and keeps the fastest; per-step times to ms_per_step
+ * (may be NULL).  The simulations advance by ncand x steps steps.
+ * WCS_E_UNSUPPORTED if the batch has no merged launch. */
+wcs_status wcs_batch_tune_launch(wcs_batch* b, const int* grids, int ncand, int steps, double* ms_per_step);
 const char* wcs_batch_last_error(const wcs_batch* b);
 
 /* Patch-size autotuner: for each candidate (P[i], levels L[i]) creates a

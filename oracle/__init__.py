@@ -36,6 +36,11 @@ def lib():
         L.orc_step.argtypes = [vp, i64]
         L.orc_import.argtypes = [vp, i32, dp]
         L.orc_set_fv.argtypes = [vp, dbl, dbl, dbl, dbl]
+        L.orc_entropy_code.restype = i64
+        L.orc_entropy_code.argtypes = [vp, C.c_char_p, i64]
+        L.orc_rans.restype = i64
+        L.orc_rans.argtypes = [C.c_char_p, i64, C.c_char_p, i64, C.c_char_p]
+        L.orc_rans_freqs.argtypes = [C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]
         L.orc_set_threads.restype = i32
         L.orc_set_threads.argtypes = [i32]
         L.orc_export_field.argtypes = [vp, i32, dp]
@@ -187,6 +192,15 @@ class OracleSim:
         n = lib().orc_record_bytes(self.h, p)
         buf = C.create_string_buffer(n)
         _check(lib().orc_record(self.h, p, buf, n))
+        return buf.raw[:n]
+
+    def entropy_code(self):
+        """The rANS-coded state of the current records (bytes)."""
+        n = lib().orc_entropy_code(self.h, None, 0)
+        if n < 0:
+            raise RuntimeError("oracle: " + lib().orc_last_error().decode())
+        buf = C.create_string_buffer(n)
+        lib().orc_entropy_code(self.h, buf, n)
         return buf.raw[:n]
 
     def stats(self):
@@ -480,3 +494,23 @@ def sw_flux(WL, WR, nx, ny, g=9.81):
     out = np.zeros(3, np.float64)
     _check(lib().orc_sw_flux(_dp(a), _dp(b), nx, ny, g, _dp(out)))
     return out
+
+
+def rans_roundtrip(data):
+    """(coded bytes, decoded bytes) of an order-0 rANS round trip of data with
+    the table of its own byte counts."""
+    n = len(data)
+    cap = 2 * n + 64
+    coded = C.create_string_buffer(cap)
+    dec = C.create_string_buffer(max(n, 1))
+    m = lib().orc_rans(bytes(data), n, coded, cap, dec)
+    if m < 0:
+        raise RuntimeError("oracle: " + lib().orc_last_error().decode())
+    return coded.raw[:m], dec.raw[:n]
+
+
+def rans_freqs(counts):
+    c = np.ascontiguousarray(counts, np.uint64)
+    f = np.zeros(256, np.uint32)
+    _check(lib().orc_rans_freqs(c.ctypes.data_as(C.POINTER(C.c_uint64)), f.ctypes.data_as(C.POINTER(C.c_uint32))))
+    return f

@@ -10,7 +10,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
 SOURCES = ["capi.cpp"]
-HEADERS = ["codec.hpp", "mlp.hpp", "schemes.hpp", "sim.hpp", "sim3.hpp", "wavelet.hpp"]
+HEADERS = ["codec.hpp", "entropy.hpp", "mlp.hpp", "schemes.hpp", "sim.hpp", "sim3.hpp", "wavelet.hpp"]
 
 
 def _stale() -> bool:

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "codec.hpp"
+#include "entropy.hpp"
 #include "mlp.hpp"
 #include "schemes.hpp"
 #include "sim.hpp"
@@ -217,6 +218,46 @@ int orc_record(void* p, int64_t patch, uint8_t* dst, int64_t cap) {
   }
   std::memcpy(dst, rec[patch].data(), rec[patch].size());
   return 0;
+}
+
+// The entropy-coded state (entropy.hpp layout) of a 2-D run's records;
+// returns its size, or -1 (and copies nothing) if cap is too small.
+int64_t orc_entropy_code(void* p, uint8_t* dst, int64_t cap) {
+  Handle* h = static_cast<Handle*>(p);
+  int64_t n = -1;
+  const int rc = guard([&] {
+    const auto out = h->s64 ? entropy_code_state(h->s64->rec) : entropy_code_state(h->s32->rec);
+    n = int64_t(out.size());
+    if (dst && n <= cap) std::memcpy(dst, out.data(), out.size());
+  });
+  return rc ? -1 : n;
+}
+
+// rANS round trip of n bytes with the table of their own counts: the coded
+// stream to coded (cap bytes), the decoded bytes to decoded; returns the
+// coded size (-1 on error).
+int64_t orc_rans(const uint8_t* in, int64_t n, uint8_t* coded, int64_t cap, uint8_t* decoded) {
+  int64_t m = -1;
+  const int rc = guard([&] {
+    std::vector<uint64_t> cnt(256, 0);
+    for (int64_t i = 0; i < n; ++i) ++cnt[in[i]];
+    const auto f = rans_freqs(cnt);
+    const auto c = rans_starts(f);
+    const auto k = rans_encode(in, n, f, c);
+    m = int64_t(k.size());
+    if (m > cap) throw std::runtime_error("rans: output buffer too small");
+    std::memcpy(coded, k.data(), k.size());
+    const auto d = rans_decode(k.data(), m, n, f, c);
+    std::memcpy(decoded, d.data(), d.size());
+  });
+  return rc ? -1 : m;
+}
+
+int orc_rans_freqs(const uint64_t* cnt, uint32_t* f) {
+  return guard([&] {
+    const auto v = rans_freqs(std::vector<uint64_t>(cnt, cnt + 256));
+    for (int s = 0; s < 256; ++s) f[s] = v[s];
+  });
 }
 
 int orc_stats(void* p, double* out) {

@@ -65,6 +65,7 @@ def lib():
         L.wcs_resident_bytes.restype = i64
         L.wcs_resident_bytes.argtypes = [vp]
         L.wcs_import_field.argtypes = [vp, i32, vp, i32, i32]
+        L.wcs_entropy_code.argtypes = [vp, vp, i64, C.POINTER(i64)]
         L.wcs_survivors.restype = i64
         L.wcs_survivors.argtypes = [vp]
         L.wcs_stats.argtypes = [vp, C.POINTER(StepStats)]
@@ -79,6 +80,8 @@ def lib():
         L.wcs_batch_destroy.argtypes = [vp]
         L.wcs_batch_step.argtypes = [vp, i64]
         L.wcs_batch_sync.argtypes = [vp]
+        L.wcs_batch_launches_per_step.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+        L.wcs_batch_tune_launch.argtypes = [vp, C.POINTER(i32), i32, i32, C.POINTER(C.c_double)]
         L.wcs_batch_last_error.restype = C.c_char_p
         L.wcs_batch_last_error.argtypes = [vp]
         L.wcs_autotune.argtypes = [C.POINTER(Grid), i32, C.POINTER(Opts), C.c_double, C.POINTER(i32), C.POINTER(i32),

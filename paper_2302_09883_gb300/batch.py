@@ -38,6 +38,22 @@ class Batch:
         if st != 0:
             raise B.WcsError(st, B.lib().wcs_batch_last_error(self.h).decode())
 
+    def launches_per_step(self):
+        """(kernel launches per step, grid of the merged launch or 0)."""
+        n, g = C.c_int(), C.c_int()
+        B.check(B.lib().wcs_batch_launches_per_step(self.h, C.byref(n), C.byref(g)), None)
+        return n.value, g.value
+
+    def tune_launch(self, grids, steps=6):
+        """Times each candidate grid of the merged launch and keeps the
+        fastest; returns the ms per step of each (advances the batch)."""
+        n = len(grids)
+        ms = (C.c_double * n)()
+        st = B.lib().wcs_batch_tune_launch(self.h, (C.c_int * n)(*grids), n, steps, ms)
+        if st != 0:
+            raise B.WcsError(st, B.lib().wcs_batch_last_error(self.h).decode())
+        return list(ms)
+
 
 def autotune(scheme, wavelet, nx, ny, eps, fields, candidates=((64, 4), (32, 3)), prec="f32", store="bf16",
              rule="const", periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, steps=20, stream=None):
@@ -45,7 +61,7 @@ def autotune(scheme, wavelet, nx, ny, eps, fields, candidates=((64, 4), (32, 3))
     measured ms per step of each (negative: not runnable)."""
     o = B.Opts()
     o.wavelet, o.rule, o.detail_store, o.compute = B.WAVELET[wavelet], B.RULE[rule], B.STORE[store], B.PREC[prec]
-    o.tau, o.cfl, o.gamma, o.arena_factor = tau, cfl, gamma, 0.35
+    o.tau, o.cfl, o.gamma, o.arena_factor = tau, cfl, gamma, 0.0
     o.cuda_stream = _stream_ptr(stream)
     g = _grid(nx, ny, periodic)
     n = len(candidates)

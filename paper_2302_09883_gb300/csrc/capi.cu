@@ -25,6 +25,7 @@
 #include "../../include/wcsim.h"
 #include "patch2d.cuh"
 #include "registry.h"
+#include "entropy.cuh"
 #include "patch3d.cuh"
 
 namespace wcs {
@@ -53,6 +54,8 @@ void reg_swe_f64_p32l3(std::vector<KernelEntry>&);
 
 void reg_d3q19_p32l3(std::vector<Kernel3Entry>&);
 void reg_d3q19_p16l3(std::vector<Kernel3Entry>&);
+
+void register_mixed(std::vector<MixedBatchEntry>& v);
 
 void register_all3(std::vector<Kernel3Entry>& v) {
   reg_d3q19_p32l3(v);
@@ -92,6 +95,16 @@ const std::vector<KernelEntry>& kernels() {
   static bool done = false;
   if (!done) {
     wcs::register_all(v);
+    done = true;
+  }
+  return v;
+}
+
+const std::vector<wcs::MixedBatchEntry>& mixed_kernels() {
+  static std::vector<wcs::MixedBatchEntry> v;
+  static bool done = false;
+  if (!done) {
+    wcs::register_mixed(v);
     done = true;
   }
   return v;
@@ -930,12 +943,36 @@ static int64_t live_bytes(const wcs_sim* s) {
 
 int64_t wcs_compressed_bytes(const wcs_sim* s) {
   if (!s || !s->inited) return -1;
+  // a step lost to an arena overflow is re-run first (the count is of the
+  // current state); the simulation is not otherwise changed
+  (void)wcs_sync(const_cast<wcs_sim*>(s));
   const int64_t live = live_bytes(s);
   if (live < 0) return -1;
   return live + int64_t(s->npatch) * s->ring_vals * int64_t(s->tsize) + int64_t(s->npatch) * 8;
 }
 
 int64_t wcs_resident_bytes(const wcs_sim* s) { return s ? s->resident : -1; }
+
+wcs_status wcs_entropy_code(wcs_sim* s, void* dst_host, int64_t cap, int64_t* nbytes) {
+  if (!s || !nbytes) return WCS_E_ARG;
+  if (!s->inited) return fail(s, WCS_E_ARG, "entropy code before init");
+  wcs_status st = wcs_sync(s);
+  if (st != WCS_OK) return st;
+  const int cur = int(s->nstep % 2);
+  std::vector<unsigned char> out;
+  unsigned long long bad = 0;
+  const cudaError_t e = wcs::entropy_code_state(s->arena[cur], s->tab[cur], s->npatch, s->stream, out, &bad);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(s, e, "entropy code");
+  }
+  if (bad) return fail(s, WCS_E_CUDA, "entropy code: " + std::to_string(bad) + " bytes did not decode back");
+  *nbytes = int64_t(out.size());
+  if (!dst_host) return WCS_OK;
+  if (cap < *nbytes) return fail(s, WCS_E_ARG, "entropy code: the buffer holds " + std::to_string(cap) + " bytes");
+  std::memcpy(dst_host, out.data(), out.size());
+  return WCS_OK;
+}
 
 }  // extern "C"
 
@@ -1031,6 +1068,7 @@ wcs_status wcs_import_field(wcs_sim* s, int field, const void* src, int src_is_d
 wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
   if (!s || !o) return WCS_E_ARG;
   std::memset(o, 0, sizeof(*o));
+  if (s->inited) (void)wcs_sync(s);  // re-runs a step lost to an arena overflow; errors stay in the status
   CK(cudaStreamSynchronize(s->stream));
   wcs::Ctl c;
   CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
@@ -1108,6 +1146,11 @@ struct wcs_batch {
   };
   std::vector<wcs_sim*> sims;
   std::vector<Group> groups;
+  // two groups that one merged kernel steps together: one launch per step
+  const wcs::MixedBatchEntry* mixed = nullptr;
+  int mk[2] = {0, 0};              // group of kind 0 and of kind 1
+  unsigned int* mwork = nullptr;   // (kind << 31) | (index in its group << 20) | patch
+  int mitems = 0, mgrid = 0;
   cudaStream_t stream = nullptr;  // the simulations' stream
   cudaStream_t priv = nullptr;    // the batch's own stream (capturable), fenced by events
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -1127,11 +1170,18 @@ static void batch_free(wcs_batch* b) {
     cudaFree(g.args);
     cudaFree(g.work);
   }
+  cudaFree(b->mwork);
   delete b;
 }
 
 static cudaError_t batch_launch_step(wcs_batch* b, int64_t k) {
   const int ph = int(k % 6);
+  if (b->mixed) {
+    const auto& g0 = b->groups[b->mk[0]];
+    const auto& g1 = b->groups[b->mk[1]];
+    return b->mixed->launch(g0.args + size_t(ph) * g0.sims.size(), g1.args + size_t(ph) * g1.sims.size(), b->mwork,
+                            b->mitems, b->mgrid, b->priv);
+  }
   for (auto& g : b->groups) {
     const cudaError_t e = g.ke.launch_batch(g.args + size_t(ph) * g.sims.size(), g.work, g.nblocks, b->priv);
     if (e != cudaSuccess) return e;
@@ -1237,7 +1287,110 @@ wcs_status wcs_batch_create(wcs_sim* const* sims, int nsims, wcs_batch** out) {
       return WCS_E_OOM;
     }
   }
+  // two kinds that a merged kernel steps together: one persistent launch per
+  // step over a work list with the larger patches first
+  if (b->groups.size() == 2) {
+    for (const auto& m : mixed_kernels()) {
+      int k0 = -1, k1 = -1;
+      for (int gi = 0; gi < 2; ++gi) {
+        const KernelEntry& e = b->groups[gi].ke;
+        if (e.scheme != m.scheme || e.wavelet != m.wavelet || e.prec != m.prec || e.store != m.store) continue;
+        if (e.P == m.P0 && e.L == m.L0) k0 = gi;
+        if (e.P == m.P1 && e.L == m.L1) k1 = gi;
+      }
+      if (k0 < 0 || k1 < 0 || k0 == k1) continue;
+      if (b->groups[k0].sims.size() > 2047 || b->groups[k1].sims.size() > 2047) break;
+      {
+        static std::mutex mu;
+        static std::vector<const wcs::MixedBatchEntry*> prepared;
+        std::lock_guard<std::mutex> lock(mu);
+        if (std::find(prepared.begin(), prepared.end(), &m) == prepared.end()) {
+          if (m.prepare() != cudaSuccess) {
+            cudaGetLastError();
+            break;
+          }
+          prepared.push_back(&m);
+        }
+      }
+      std::vector<unsigned int> work;
+      const int ks[2] = {k0, k1};
+      for (int kind = 0; kind < 2; ++kind) {
+        const auto& g = b->groups[ks[kind]];
+        for (size_t j = 0; j < g.sims.size(); ++j)
+          for (int p = 0; p < g.sims[j]->npatch; ++p)
+            work.push_back((unsigned(kind) << 31) | (unsigned(j) << 20) | unsigned(p));
+      }
+      if (m.P1 > m.P0) {  // larger patches first
+        std::stable_sort(work.begin(), work.end(), [](unsigned a, unsigned c) { return (a >> 31) > (c >> 31); });
+      }
+      if (cudaMalloc(&b->mwork, work.size() * 4) != cudaSuccess ||
+          cudaMemcpy(b->mwork, work.data(), work.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_err = "batch: device allocation failed";
+        batch_free(b);
+        return WCS_E_OOM;
+      }
+      int dev = 0, nsm = 1;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      b->mixed = &m;
+      b->mk[0] = k0;
+      b->mk[1] = k1;
+      b->mitems = int(work.size());
+      b->mgrid = std::min(b->mitems, nsm);  // persistent: one block per SM (one fits in shared memory)
+      break;
+    }
+  }
   *out = b;
+  return WCS_OK;
+}
+
+wcs_status wcs_batch_launches_per_step(const wcs_batch* b, int* launches, int* grid) {
+  if (!b || !launches) return WCS_E_ARG;
+  *launches = b->mixed ? 1 : int(b->groups.size());
+  if (grid) *grid = b->mixed ? b->mgrid : 0;
+  return WCS_OK;
+}
+
+// Launch-shape tuner of a merged batch: times `steps` steps with every
+// candidate grid (blocks in the persistent launch) and keeps the fastest;
+// the simulations advance by ncand * steps steps.
+wcs_status wcs_batch_tune_launch(wcs_batch* b, const int* grids, int ncand, int steps, double* ms_per_step) {
+  if (!b || !grids || ncand <= 0 || steps <= 0) return WCS_E_ARG;
+  if (!b->mixed) return WCS_E_UNSUPPORTED;
+  int best = -1;
+  double best_ms = 0;
+  for (int i = 0; i < ncand; ++i) {
+    if (grids[i] <= 0) return WCS_E_ARG;
+    b->mgrid = std::min(grids[i], b->mitems);
+    if (b->exec) {  // the graph holds the launch shape
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, b->stream);
+    wcs_status st = wcs_batch_step(b, steps);
+    cudaEventRecord(e1, b->stream);
+    if (st == WCS_OK) st = wcs_batch_sync(b);
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != WCS_OK) return st;
+    const double ms = double(t) / steps;
+    if (ms_per_step) ms_per_step[i] = ms;
+    if (best < 0 || ms < best_ms) {
+      best = i;
+      best_ms = ms;
+    }
+  }
+  b->mgrid = std::min(grids[best], b->mitems);
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
   return WCS_OK;
 }
 

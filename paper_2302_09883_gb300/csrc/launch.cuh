@@ -125,3 +125,45 @@ KernelEntry make_entry() {
   namespace wcs {                                                                                \
   void NAME(std::vector<KernelEntry>& v) { v.push_back(make_entry_lite<SCH, WV, T, ST, P, L>()); } \
   }
+
+namespace wcs {
+template <int SCH, int WV, typename T, int ST, int P0, int L0, int P1, int L1>
+cudaError_t launch_mixed(const PatchArgs* args0, const PatchArgs* args1, const unsigned int* work, int nitems, int grid,
+                         cudaStream_t s) {
+  typedef Cfg<SCH, WV, T, ST, P0, L0> C0;
+  typedef Cfg<SCH, WV, T, ST, P1, L1> C1;
+  if (nitems <= 0) return cudaSuccess;
+  const size_t smem = C0::SMEM > C1::SMEM ? C0::SMEM : C1::SMEM;
+  patch_kernel_batch_mixed<SCH, WV, T, ST, P0, L0, P1, L1><<<grid, C0::NT, smem, s>>>(args0, args1, work, nitems);
+  return cudaGetLastError();
+}
+
+template <int SCH, int WV, typename T, int ST, int P0, int L0, int P1, int L1>
+cudaError_t prepare_mixed() {
+  typedef Cfg<SCH, WV, T, ST, P0, L0> C0;
+  typedef Cfg<SCH, WV, T, ST, P1, L1> C1;
+  const size_t smem = C0::SMEM > C1::SMEM ? C0::SMEM : C1::SMEM;
+  return cudaFuncSetAttribute(patch_kernel_batch_mixed<SCH, WV, T, ST, P0, L0, P1, L1>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}
+
+template <int SCH, int WV, typename T, int ST, int P0, int L0, int P1, int L1>
+MixedBatchEntry make_mixed() {
+  typedef Cfg<SCH, WV, T, ST, P0, L0> C0;
+  typedef Cfg<SCH, WV, T, ST, P1, L1> C1;
+  MixedBatchEntry m;
+  m.scheme = SCH;
+  m.wavelet = WV;
+  m.prec = sizeof(T) == 8 ? 0 : 1;
+  m.store = ST;
+  m.P0 = P0;
+  m.L0 = L0;
+  m.P1 = P1;
+  m.L1 = L1;
+  m.smem = C0::SMEM > C1::SMEM ? C0::SMEM : C1::SMEM;
+  m.threads = C0::NT;
+  m.launch = &launch_mixed<SCH, WV, T, ST, P0, L0, P1, L1>;
+  m.prepare = &prepare_mixed<SCH, WV, T, ST, P0, L0, P1, L1>;
+  return m;
+}
+}  // namespace wcs

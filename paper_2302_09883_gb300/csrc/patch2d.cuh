@@ -297,14 +297,15 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
   const int p_edge = (p_words + 4 * nwords + 7) & ~7, p_int = p_edge + nedge * int(sizeof(T));
   static_assert(NPW <= 32, "presence words fit in one warp");
   const unsigned int presl = lane < NPW ? ldr<unsigned int>(R + p_pres + 4 * lane) : 0u;  // lane k: word k
-  auto inside = [&](int kx, int ky) -> bool {
-    return kind == 0 ? cone_has(MX, kx) : (kind == 1 ? cone_has(MY, ky) : (cone_has(MX, kx) && cone_has(MY, ky)));
-  };
   auto slot = [&](int kx, int ky) -> int {
     return kind == 0 ? cone_index(MX, kx) * E + ky
                      : (kind == 1 ? cone_index(MY, ky) * E + kx : cone_index(MY, ky) * NCN + cone_index(MX, kx));
   };
+  const unsigned char* sc_base = R + off + NC * int(sizeof(T)) + 8;
   unsigned ce = 0u, ci = 0u;
+  // lane j holds stored word j: its node, its survivor ranks (one warp scan
+  // of both counts), the bits of the region, then its own survivors, so
+  // that the 32 lanes' loads are in flight together
   for (int j0 = 0; j0 < nwords; j0 += 32) {
     const int j = j0 + lane;
     int w = 0;
@@ -327,47 +328,38 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
     }
     const unsigned int em = word_edges<WV, P, E, C::WR>(w);
     const unsigned ve = __popc(word & em), vi = __popc(word & ~em);
-    // both survivor counts in one scan (each lane <= 32, sums <= 1024)
-    const unsigned sc = warp_incl_scan(ve | (vi << 16));
+    const unsigned sc = warp_incl_scan(ve | (vi << 16));  // each lane <= 32, sums <= 1024
     const unsigned ie = sc & 0xffffu, ii = sc >> 16;
     const unsigned be = ce + ie - ve, bi = ci + ii - vi;
     ce += __shfl_sync(0xffffffffu, ie, 31);
     ci += __shfl_sync(0xffffffffu, ii, 31);
-    // words with a surviving node in the region (row words: one row y0,
-    // columns x0 + bit; face words: column P, rows y0 + bit)
-    bool hit = word != 0u;
-    if (hit) {
-      const bool rowword = w < C::NRW;
-      const int y0 = rowword ? w / C::WR : 32 * (w - C::NRW);
-      const int x0 = rowword ? 32 * (w - y0 * C::WR) : P;
-      const bool hx = rowword ? (word & cone_bits32(MX, x0)) != 0u : cone_has(MX, P);
-      const bool hy = rowword ? cone_has(MY, y0) : (word & cone_bits32(MY, y0)) != 0u;
-      hit = kind == 0 ? hx : (kind == 1 ? hy : (hx && hy));
+    // the word's bits inside the region (row words: row y0, columns x0 +
+    // bit; face words: column P, rows y0 + bit)
+    const bool rowword = w < C::NRW;
+    const int y0 = rowword ? w / C::WR : 32 * (w - C::NRW);
+    const int x0 = rowword ? 32 * (w - y0 * C::WR) : P;
+    unsigned int rx, ry;
+    if (rowword) {
+      rx = cone_bits32(MX, x0);
+      ry = cone_has(MY, y0) ? 0xffffffffu : 0u;
+    } else {
+      rx = cone_has(MX, P) ? 0xffffffffu : 0u;
+      ry = cone_bits32(MY, y0);
     }
-    unsigned int todo = __ballot_sync(0xffffffffu, hit);
-    while (todo) {
-      const int k = __ffs(todo) - 1;
-      todo &= todo - 1u;
-      const unsigned int wk = __shfl_sync(0xffffffffu, word, k), emk = __shfl_sync(0xffffffffu, em, k);
-      const unsigned bek = __shfl_sync(0xffffffffu, be, k), bik = __shfl_sync(0xffffffffu, bi, k);
-      const int ww = __shfl_sync(0xffffffffu, w, k);
-      if (!((wk >> lane) & 1u)) continue;
-      int kx, ky;
-      bool valid;
-      word_node<P, E, C::WR>(ww, lane, kx, ky, valid);
-      if (!valid || !inside(kx, ky)) continue;
-      const unsigned int lt = (1u << lane) - 1u;
+    unsigned int m = word & (kind == 0 ? rx : (kind == 1 ? ry : (rx & ry)));
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1u;
+      const int kx = rowword ? x0 + b : P, ky = rowword ? y0 : y0 + b;
+      const unsigned int lt = (1u << b) - 1u;
       T v;
-      if ((emk >> lane) & 1u) {
-        v = ldr<T>(R + p_edge + int(bek + __popc(wk & emk & lt)) * int(sizeof(T)));
+      if ((em >> b) & 1u) {
+        v = ldr<T>(R + p_edge + int(be + __popc(word & em & lt)) * int(sizeof(T)));
       } else {
-        const int qi = int(bik + __popc(wk & ~emk & lt));
-        float sc = 0.0f;
-        if constexpr (C::QUANT) {
-          const int b = node_class<L>(kx) * (L + 1) + node_class<L>(ky);
-          sc = ldr<float>(R + off + NC * int(sizeof(T)) + 8 + 4 * band_scale_index(bm, b));
-        }
-        v = load_interior<T, ST>(R + p_int, qi, wide, sc);
+        const int qi = int(bi + __popc(word & ~em & lt));
+        float scl = 0.0f;
+        if constexpr (C::QUANT) scl = ldr<float>(sc_base + 4 * band_scale_index(bm, node_class<L>(kx) * (L + 1) + node_class<L>(ky)));
+        v = load_interior<T, ST>(R + p_int, qi, wide, scl);
       }
       rg[slot(kx, ky)] = v;
     }
@@ -1772,6 +1764,26 @@ __global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1)
     patch_kernel_batch(const PatchArgs* __restrict__ args, const unsigned int* __restrict__ work) {
   const unsigned int wb = work[blockIdx.x];
   patch_body<SCH, WV, T, ST, P, L, MODE_STEP>(args[wb >> 20], int(wb & 0xfffffu));
+}
+
+// Many simulations of two kernel configurations (the same scheme, wavelet,
+// precision and storage, two patch sizes) in one persistent launch: block b
+// takes items b, b + gridDim.x, ... of the work list, each (kind << 31) |
+// (simulation << 20) | patch, and steps that patch with the configuration of
+// its kind (arguments args0 or args1 of that simulation).  The list is
+// ordered by decreasing patch size, so the long items start first.
+template <int SCH, int WV, typename T, int ST, int P0, int L0, int P1, int L1>
+__global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P0, L0>::NT, 1)
+    patch_kernel_batch_mixed(const PatchArgs* __restrict__ args0, const PatchArgs* __restrict__ args1,
+                             const unsigned int* __restrict__ work, int nitems) {
+  static_assert(Cfg<SCH, WV, T, ST, P0, L0>::NT == Cfg<SCH, WV, T, ST, P1, L1>::NT, "one block shape for both kinds");
+  for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+    const unsigned int wb = work[i];
+    const int sim = int((wb >> 20) & 0x7ffu), pid = int(wb & 0xfffffu);
+    if (wb >> 31) patch_body<SCH, WV, T, ST, P1, L1, MODE_STEP>(args1[sim], pid);
+    else patch_body<SCH, WV, T, ST, P0, L0, MODE_STEP>(args0[sim], pid);
+    __syncthreads();  // the next item reuses the shared memory
+  }
 }
 
 }  // namespace wcs

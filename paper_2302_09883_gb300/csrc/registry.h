@@ -25,6 +25,19 @@ struct KernelEntry {
 
 void register_all(std::vector<KernelEntry>& v);
 
+// One persistent launch stepping simulations of two configurations (kind 0:
+// P0/L0, kind 1: P1/L1; same scheme, wavelet, precision, storage).  Work
+// items are (kind << 31) | (simulation << 20) | patch.
+struct MixedBatchEntry {
+  int scheme, wavelet, prec, store, P0, L0, P1, L1;
+  size_t smem;
+  int threads;
+  cudaError_t (*launch)(const PatchArgs* args0, const PatchArgs* args1, const unsigned int* work, int nitems,
+                        int grid, cudaStream_t s);
+  cudaError_t (*prepare)();
+};
+void register_mixed(std::vector<MixedBatchEntry>& v);
+
 // 3-D kernels (D3Q19, folded BL5/3, FP32 compute): persistent, one CTA per
 // SM, each with a scratch slot of slot_floats floats and slot_rbytes bytes.
 struct Patch3Args;

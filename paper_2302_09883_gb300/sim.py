@@ -114,6 +114,14 @@ class Sim:
     def resident_bytes(self):
         return B.lib().wcs_resident_bytes(self.h)
 
+    def entropy_code(self):
+        """The current records entropy-coded by the library (rANS; bytes)."""
+        n = C.c_int64()
+        B.check(B.lib().wcs_entropy_code(self.h, None, 0, C.byref(n)), self.h)
+        buf = C.create_string_buffer(max(n.value, 1))
+        B.check(B.lib().wcs_entropy_code(self.h, buf, n.value, C.byref(n)), self.h)
+        return buf.raw[:n.value]
+
     def survivors(self):
         """Detail coefficients kept in the current state (all patches, fields)."""
         k = B.lib().wcs_survivors(self.h)

@@ -61,3 +61,35 @@ def test_autotune_picks_a_runnable_candidate_and_caches_it():
     assert ms[best] == min(m for m in ms if m > 0)
     best2, ms2 = autotune("d2q9", "bl53", 512, 512, 1e-4, f, candidates=((64, 4), (32, 3), (16, 2)), tau=0.6)
     assert best2 == best and ms2 == ms
+
+
+def test_merged_batch_is_one_launch_per_step_and_matches_the_oracle():
+    # the two patch sizes of the autotuner (64/4 and 32/3, BF16) in one
+    # persistent launch per step, larger patches first
+    specs = [(256, 64, 4), (128, 32, 3), (192, 64, 4), (96, 32, 3), (64, 32, 3)]
+    pairs = []
+    for k, (n, P, L) in enumerate(specs):
+        f = inputs.gaussian_bump(n, amp=0.03 + 0.02 * k, sigma=3.0 + 2 * k, center=(0.4 * n, 0.55 * n))
+        pairs.append(_pair(n, P, L, "f32", "bf16", "bl53", f, tau=0.65))
+    b = Batch([g for g, _ in pairs])
+    launches, grid = b.launches_per_step()
+    assert launches == 1 and grid > 0
+    for chunk in (2, 13):
+        b.step(chunk)
+        for g, o in pairs:
+            o.step(chunk)
+        b.sync()
+        for g, o in pairs:
+            for p in range(g.npatch):
+                assert g.record(p) == o.record(p)
+    # the launch-shape tuner (persistent grid against one block per item)
+    # keeps the records exact
+    nitems = sum(g.npatch for g, _ in pairs)
+    ms = b.tune_launch([grid, nitems], steps=6)
+    assert len(ms) == 2 and min(ms) > 0
+    for g, o in pairs:
+        o.step(12)
+    b.sync()
+    for g, o in pairs:
+        assert np.array_equal(g.export_field(-1), o.export_all())
+    b.close()
