@@ -64,8 +64,12 @@ typedef enum {
  * SWE) take periodic or outflow (zero-gradient) axes. */
 typedef enum { WCS_D2Q9 = 0, WCS_D3Q19 = 1, WCS_EULER2D = 2, WCS_TRANSPORT = 3, WCS_SWE = 4 } wcs_scheme;
 
-/* Wavelets: folded BL5/3 on P+1 nodes (Sec. 2.1.2), or Haar on P cells. */
-typedef enum { WCS_BL53 = 0, WCS_HAAR = 1 } wcs_wavelet;
+/* Wavelets: folded BL5/3 on P+1 nodes (Sec. 2.1.2), Haar on P cells, or
+ * CDF 9/7 on P+1 nodes (the second-order alternative Sec. 2.1.2 names;
+ * lifting factorisation with whole-sample symmetric ends, low pass keeping
+ * constants; it keeps no trapezoid mass, so field_sum is an estimate);
+ * CDF 9/7 is compiled for TRANSPORT, FP32/F32, P = 64, L = 4. */
+typedef enum { WCS_BL53 = 0, WCS_HAAR = 1, WCS_CDF97 = 2 } wcs_wavelet;
 
 /* Threshold rules of Sec. 2.2 (accumulation / capped under the reading that
  * the finest band gets eps and coarser bands smaller thresholds). */

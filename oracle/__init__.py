@@ -14,7 +14,7 @@ import numpy as np
 from .build import build_oracle
 
 SCHEME = {"d2q9": 0, "d3q19": 1, "euler2d": 2, "transport": 3, "swe": 4}
-WAVELET = {"bl53": 0, "haar": 1}
+WAVELET = {"bl53": 0, "haar": 1, "cdf97": 2}
 STORE = {"f64": 0, "f32": 1, "bf16": 2, "i8": 3}
 RULE = {"const": 0, "accum": 1, "capped": 2}
 PREC = {"f64": 0, "f32": 1}
@@ -62,6 +62,7 @@ def lib():
         L.orc_ref_time.restype = dbl
         L.orc_ref_time.argtypes = [vp]
         L.orc_dwt.argtypes = [i32, i32, i64, i32, i32, i32, dp]
+        L.orc_dwt_pyramid.argtypes = [i32, i64, i32, i32, dp]
         L.orc_layout.argtypes = [i32, i32, i64, i32, C.POINTER(C.c_int32), C.POINTER(C.c_uint8),
                                  C.POINTER(C.c_uint8), C.POINTER(C.c_int64)]
         L.orc_band_factor.restype = dbl
@@ -135,7 +136,7 @@ class OracleSim:
         self.scheme, self.wavelet, self.prec = scheme, wavelet, prec
         self.P, self.L = P, L
         pmask = int(periodic[0]) | (int(periodic[1]) << 1)
-        self.G = [n + 1 if (wavelet == "bl53" and not per) else n for n, per in zip((nx, ny), periodic)]
+        self.G = [n + 1 if (wavelet != "haar" and not per) else n for n, per in zip((nx, ny), periodic)]
         self.F = nfields(scheme)
         self.h = lib().orc_create(SCHEME[scheme], WAVELET[wavelet], PREC[prec], STORE[store], RULE[rule],
                                   nx, ny, pmask, P, L, eps, tau, cfl, gamma)
@@ -212,7 +213,7 @@ class OracleSim:
 
     @property
     def n_coarse(self):
-        return ((self.P >> self.L) + (1 if self.wavelet == "bl53" else 0)) ** 2
+        return ((self.P >> self.L) + (1 if self.wavelet != "haar" else 0)) ** 2
 
 
 class OracleRef:
@@ -221,7 +222,7 @@ class OracleRef:
     def __init__(self, scheme, wavelet, nx, ny, prec="f64", periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4,
                  velocity=(0.0, 0.0), gravity=9.81, length=1.0):
         pmask = int(periodic[0]) | (int(periodic[1]) << 1)
-        self.G = [n + 1 if (wavelet == "bl53" and not per) else n for n, per in zip((nx, ny), periodic)]
+        self.G = [n + 1 if (wavelet != "haar" and not per) else n for n, per in zip((nx, ny), periodic)]
         self.F = nfields(scheme)
         self.h = lib().orc_ref_create(SCHEME[scheme], WAVELET[wavelet], PREC[prec], nx, ny, pmask, tau, cfl, gamma)
         if not self.h:
@@ -254,6 +255,13 @@ def dwt(u, wavelet, P, L, inverse=False, prec="f64"):
     """Tensor lifting transform of a d-D block (returns a new array)."""
     a = np.ascontiguousarray(u, dtype=np.float64).copy()
     _check(lib().orc_dwt(WAVELET[wavelet], a.ndim, P, L, int(inverse), PREC[prec], _dp(a)))
+    return a
+
+
+def dwt_pyramid(u, wavelet, P, L, inverse=False):
+    """Mallat-pyramid transform of a 2-D block (FP64; returns a new array)."""
+    a = np.ascontiguousarray(u, dtype=np.float64).copy()
+    _check(lib().orc_dwt_pyramid(WAVELET[wavelet], P, L, int(inverse), _dp(a)))
     return a
 
 

@@ -320,9 +320,17 @@ double orc_ref_time(void* p) {
 // ----------------------------------------------------------- pure helpers
 // In-place tensor transform of a dims-D block (FP64 arithmetic, or FP32 when
 // prec = 1, values passed as doubles).
+// Mallat pyramid of a 2-D block (FP64), in place.
+int orc_dwt_pyramid(int wavelet, int64_t P, int L, int inverse, double* u) {
+  return guard([&] {
+    if (inverse) inv_pyramid2<double>(wavelet, u, P, L);
+    else fwd_pyramid2<double>(wavelet, u, P, L);
+  });
+}
+
 int orc_dwt(int wavelet, int dims, int64_t P, int L, int inverse, int prec, double* u) {
   return guard([&] {
-    const int64_t E = wavelet == BL53 ? P + 1 : P;
+    const int64_t E = nodal(wavelet) ? P + 1 : P;
     int64_t n = 1;
     for (int a = 0; a < dims; ++a) n *= E;
     if (prec == 0) {
@@ -450,7 +458,7 @@ int orc_rusanov(const double* WL, const double* WR, int nx, int ny, double gamma
 // u: nfields blocks of E^dims node values of one patch.
 int orc_patch_features(int wavelet, int dims, int64_t P, int L, int nfields, const double* u, double* out) {
   return guard([&] {
-    const int64_t E = wavelet == BL53 ? P + 1 : P;
+    const int64_t E = nodal(wavelet) ? P + 1 : P;
     int64_t n = 1;
     for (int a = 0; a < dims; ++a) n *= E;
     std::vector<std::vector<double>> c(nfields);
@@ -467,7 +475,7 @@ int orc_patch_features(int wavelet, int dims, int64_t P, int L, int nfields, con
 int orc_patch_label(int wavelet, int dims, int64_t P, int L, int nfields, const double* u, double delta, double* out,
                     int prec) {
   return guard([&] {
-    const int64_t E = wavelet == BL53 ? P + 1 : P;
+    const int64_t E = nodal(wavelet) ? P + 1 : P;
     int64_t n = 1;
     for (int a = 0; a < dims; ++a) n *= E;
     std::vector<std::vector<double>> v(nfields);
@@ -480,7 +488,7 @@ int orc_patch_label(int wavelet, int dims, int64_t P, int L, int nfields, const 
 // to FP64 for the sums).
 int orc_patch_features_f32(int wavelet, int dims, int64_t P, int L, int nfields, const double* u, double* out) {
   return guard([&] {
-    const int64_t E = wavelet == BL53 ? P + 1 : P;
+    const int64_t E = nodal(wavelet) ? P + 1 : P;
     int64_t n = 1;
     for (int a = 0; a < dims; ++a) n *= E;
     std::vector<std::vector<double>> c(nfields);

@@ -87,7 +87,7 @@ struct Layout {
 
   Layout() = default;
   Layout(int wavelet_, int dims_, int64_t P_, int L_) : wavelet(wavelet_), dims(dims_), L(L_), P(P_) {
-    E = wavelet == BL53 ? P + 1 : P;
+    E = nodal(wavelet) ? P + 1 : P;
     n_all = 1;
     for (int a = 0; a < dims; ++a) n_all *= E;
     nb = 1;
@@ -111,7 +111,7 @@ struct Layout {
         r /= E;
         cls[a] = pos_class(k, L);
         if (cls[a] != 0) coarse = false;
-        if (wavelet == BL53 && (k == 0 || k == P)) edge = true;
+        if (nodal(wavelet) && (k == 0 || k == P)) edge = true;
       }
       for (int a = 0; a < dims; ++a) b = b * (L + 1) + cls[a];
       pos_band[p] = b;

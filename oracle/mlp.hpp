@@ -81,7 +81,7 @@ constexpr int EPS_GRID_N = 41;
 template <class T = double>
 inline double patch_label(const std::vector<std::vector<double>>& u, int wavelet, int dims, int64_t P, int L,
                           double delta) {
-  const int64_t E = wavelet == BL53 ? P + 1 : P;
+  const int64_t E = nodal(wavelet) ? P + 1 : P;
   int64_t n = 1;
   for (int a = 0; a < dims; ++a) n *= E;
   std::vector<std::vector<T>> c(u.size());

@@ -55,7 +55,7 @@ struct Grid2 {
     N[0] = nx; N[1] = ny;
     periodic[0] = pmask & 1;
     periodic[1] = (pmask >> 1) & 1;
-    for (int a = 0; a < 2; ++a) G[a] = (wavelet == BL53 && !periodic[a]) ? N[a] + 1 : N[a];
+    for (int a = 0; a < 2; ++a) G[a] = (nodal(wavelet) && !periodic[a]) ? N[a] + 1 : N[a];
   }
   int64_t nodes() const { return G[0] * G[1]; }
   // Global index along axis a of a (possibly ghost) coordinate g.
@@ -205,14 +205,14 @@ template <class T> struct Sim {
     if (scheme == SC_D2Q9 && (!grid.periodic[0] || !grid.periodic[1]))
       throw std::runtime_error("D2Q9 needs periodic axes");
     // BL5/3 needs an interior coarse sample for eq. conservation: P/2^L >= 2.
-    if (P < 2 || (P & (P - 1)) || L < 1 || (P >> L) < (wavelet == BL53 ? 2 : 1))
+    if (P < 2 || (P & (P - 1)) || L < 1 || (P >> L) < (nodal(wavelet) ? 2 : 1))
       throw std::runtime_error("bad patch/levels");
     if (nx % P || ny % P) throw std::runtime_error("grid not a multiple of the patch size");
     if (sizeof(T) == 8 && store != S_F64) throw std::runtime_error("FP64 compute stores FP64");
     if (sizeof(T) == 4 && store == S_F64) throw std::runtime_error("FP32 compute cannot store FP64");
     np[0] = nx / P;
     np[1] = ny / P;
-    E = wavelet == BL53 ? P + 1 : P;
+    E = nodal(wavelet) ? P + 1 : P;
     F = scheme_fields(scheme);
     lay = Layout(wavelet, 2, P, L);
     rec.resize(np[0] * np[1]);
@@ -377,7 +377,7 @@ template <class T> struct Sim {
         for (int64_t c = 0; c < nc1 * nc1; ++c) {
           const int64_t iy = c / nc1, ix = c % nc1;
           double w = 1.0;
-          if (grid.wavelet == BL53) {
+          if (nodal(grid.wavelet)) {
             if (ix == 0 || ix == nc1 - 1) w *= 0.5;
             if (iy == 0 || iy == nc1 - 1) w *= 0.5;
           }
@@ -406,8 +406,8 @@ template <class T> double field_sum(const Grid2& g, const std::vector<T>& u) {
   for (int64_t y = 0; y < g.G[1]; ++y)
     for (int64_t x = 0; x < g.G[0]; ++x) {
       double w = 1.0;
-      if (g.wavelet == BL53 && !g.periodic[0] && (x == 0 || x == g.G[0] - 1)) w *= 0.5;
-      if (g.wavelet == BL53 && !g.periodic[1] && (y == 0 || y == g.G[1] - 1)) w *= 0.5;
+      if (nodal(g.wavelet) && !g.periodic[0] && (x == 0 || x == g.G[0] - 1)) w *= 0.5;
+      if (nodal(g.wavelet) && !g.periodic[1] && (y == 0 || y == g.G[1] - 1)) w *= 0.5;
       s += w * double(u[y * g.G[0] + x]);
     }
   return s;

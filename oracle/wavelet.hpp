@@ -11,6 +11,16 @@
 //    conservation).  Repeated L times ("compression level").
 //  * Haar (not in the paper; textbook unnormalised average/difference
 //    lifting on 2^j cells): d = b - a, s = a + d/2.
+//  * CDF 9/7 (Sec. 2.1.2 names it as the second-order alternative to
+//    BL5/3; its lifting factorisation is I. Daubechies and W. Sweldens,
+//    "Factoring wavelet transforms into lifting steps", 1998): on the same
+//    2^j+1 nodes, per level four lifting steps d += a (s_k + s_k+1),
+//    s += b (d_k-1 + d_k), d += g (s_k + s_k+1), s += e (d_k-1 + d_k), with
+//    whole-sample symmetric ends (d_-1 = d_0, d_K = d_K-1: every predict has
+//    both neighbours), then s /= K, d *= K with K = 1 + 2b(1 + 2a), the gain
+//    of the first two steps on a constant, so that the low pass keeps
+//    constants.  It filters out cubic polynomials (four vanishing moments)
+//    but keeps no trapezoid mass.
 //  * N-D: the 1-D transform is applied along x for every line, then along y,
 //    then z (Sec. 2.1.2, last paragraphs: every row is transformed before any
 //    column).  This tensor reading is the one that reproduces the paper's
@@ -25,7 +35,17 @@
 
 namespace orc {
 
-enum Wavelet { BL53 = 0, HAAR = 1 };
+enum Wavelet { BL53 = 0, HAAR = 1, CDF97 = 2 };
+enum Decomposition { TENSOR = 0, PYRAMID = 1 };
+
+// Wavelets on 2^j+1 nodes whose end nodes a patch shares with its
+// neighbours (BL5/3, CDF 9/7); Haar works on 2^j cells.
+inline bool nodal(int wavelet) { return wavelet != HAAR; }
+
+// CDF 9/7 lifting constants (published factorisation) and the scale K.
+static const double CDF97_A = -1.586134342059924, CDF97_B = -0.052980118572961, CDF97_G = 0.882911075530934,
+                    CDF97_D = 0.443506852043971;
+inline double cdf97_K() { return 1.0 + 2.0 * CDF97_B * (1.0 + 2.0 * CDF97_A); }
 
 // Class of in-place position k along one axis after L levels: 0 = coarse
 // sample, m in 1..L = detail of level m (1 = finest).
@@ -43,7 +63,7 @@ inline int64_t class_pos(int c, int64_t i, int L) {
 }
 // Number of positions of class c on an axis of P cells (P+1 nodes for BL5/3).
 inline int64_t class_size(int wavelet, int64_t P, int c, int L) {
-  if (c == 0) return wavelet == BL53 ? (P >> L) + 1 : (P >> L);
+  if (c == 0) return nodal(wavelet) ? (P >> L) + 1 : (P >> L);
   return P >> c;
 }
 
@@ -71,6 +91,16 @@ template <class T> void fwd1(int wavelet, T* u, int64_t stride, int64_t P, int L
         e = e + bl53_alpha<T>(k, K) * d[k];
         at(2 * k) = e;
       }
+    } else if (wavelet == CDF97) {
+      const int64_t K = (P / st) / 2;  // details; samples 0..K
+      const T ka = T(CDF97_A), kb = T(CDF97_B), kg = T(CDF97_G), kd = T(CDF97_D), KK = T(cdf97_K());
+      auto dd = [&](int64_t k) -> T& { return at(2 * (k < 0 ? 0 : (k >= K ? K - 1 : k)) + 1); };
+      for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) + ka * (at(2 * k) + at(2 * k + 2));
+      for (int64_t k = 0; k <= K; ++k) at(2 * k) = at(2 * k) + kb * (dd(k - 1) + dd(k));
+      for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) + kg * (at(2 * k) + at(2 * k + 2));
+      for (int64_t k = 0; k <= K; ++k) at(2 * k) = at(2 * k) + kd * (dd(k - 1) + dd(k));
+      for (int64_t k = 0; k <= K; ++k) at(2 * k) = at(2 * k) / KK;
+      for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) * KK;
     } else {
       const int64_t K = (P / st) / 2;  // pairs
       for (int64_t k = 0; k < K; ++k) {
@@ -97,6 +127,16 @@ template <class T> void inv1(int wavelet, T* u, int64_t stride, int64_t P, int L
       }
       for (int64_t k = 0; k < K; ++k)
         at(2 * k + 1) = at(2 * k + 1) + T(0.5) * (at(2 * k) + at(2 * k + 2));
+    } else if (wavelet == CDF97) {
+      const int64_t K = (P / st) / 2;
+      const T ka = T(CDF97_A), kb = T(CDF97_B), kg = T(CDF97_G), kd = T(CDF97_D), KK = T(cdf97_K());
+      auto dd = [&](int64_t k) -> T& { return at(2 * (k < 0 ? 0 : (k >= K ? K - 1 : k)) + 1); };
+      for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) / KK;
+      for (int64_t k = 0; k <= K; ++k) at(2 * k) = at(2 * k) * KK;
+      for (int64_t k = 0; k <= K; ++k) at(2 * k) = at(2 * k) - kd * (dd(k - 1) + dd(k));
+      for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) - kg * (at(2 * k) + at(2 * k + 2));
+      for (int64_t k = 0; k <= K; ++k) at(2 * k) = at(2 * k) - kb * (dd(k - 1) + dd(k));
+      for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) - ka * (at(2 * k) + at(2 * k + 2));
     } else {
       const int64_t K = (P / st) / 2;
       for (int64_t k = 0; k < K; ++k) {
@@ -112,7 +152,7 @@ template <class T> void inv1(int wavelet, T* u, int64_t stride, int64_t P, int L
 // Tensor transform of a dims-dimensional block with E points per axis
 // (E = P+1 for BL5/3, P for Haar), x fastest.
 template <class T> void fwd_nd(int wavelet, T* u, int dims, int64_t P, int L) {
-  const int64_t E = wavelet == BL53 ? P + 1 : P;
+  const int64_t E = nodal(wavelet) ? P + 1 : P;
   int64_t n = 1;
   for (int a = 0; a < dims; ++a) n *= E;
   for (int a = 0; a < dims; ++a) {
@@ -126,7 +166,7 @@ template <class T> void fwd_nd(int wavelet, T* u, int dims, int64_t P, int L) {
 }
 
 template <class T> void inv_nd(int wavelet, T* u, int dims, int64_t P, int L) {
-  const int64_t E = wavelet == BL53 ? P + 1 : P;
+  const int64_t E = nodal(wavelet) ? P + 1 : P;
   int64_t n = 1;
   for (int a = 0; a < dims; ++a) n *= E;
   for (int a = dims - 1; a >= 0; --a) {
@@ -136,6 +176,32 @@ template <class T> void inv_nd(int wavelet, T* u, int dims, int64_t P, int L) {
       if ((base / stride) % E != 0) continue;
       inv1<T>(wavelet, u + base, stride, P, L);
     }
+  }
+}
+
+// Mallat pyramid (the paper's alternative layout, Sec. 2.1.2 and 3.2.4): one
+// level at a time, first along x on every row of the current coarse region,
+// then along y on its every column; the next level works on the region's
+// samples only (nodes whose coordinates are multiples of 2^l).  2-D, in
+// place.  Coefficient (x, y) is then a detail of level min(c_x, c_y) (the
+// smaller non-zero per-axis class) or a coarse sample.
+template <class T> void fwd_pyramid2(int wavelet, T* u, int64_t P, int L) {
+  const int64_t E = nodal(wavelet) ? P + 1 : P;
+  for (int l = 1; l <= L; ++l) {
+    const int64_t st = int64_t(1) << (l - 1);
+    const int64_t Pl = P / st;  // cells of the level's line
+    for (int64_t y = 0; y < E; y += st) fwd1<T>(wavelet, u + y * E, st, Pl, 1);
+    for (int64_t x = 0; x < E; x += st) fwd1<T>(wavelet, u + x, st * E, Pl, 1);
+  }
+}
+
+template <class T> void inv_pyramid2(int wavelet, T* u, int64_t P, int L) {
+  const int64_t E = nodal(wavelet) ? P + 1 : P;
+  for (int l = L; l >= 1; --l) {
+    const int64_t st = int64_t(1) << (l - 1);
+    const int64_t Pl = P / st;
+    for (int64_t x = 0; x < E; x += st) inv1<T>(wavelet, u + x, st * E, Pl, 1);
+    for (int64_t y = 0; y < E; y += st) inv1<T>(wavelet, u + y * E, st, Pl, 1);
   }
 }
 

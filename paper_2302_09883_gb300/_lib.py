@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libwcsim.so")
 
 SCHEME = {"d2q9": 0, "d3q19": 1, "euler2d": 2, "transport": 3, "swe": 4}
-WAVELET = {"bl53": 0, "haar": 1}
+WAVELET = {"bl53": 0, "haar": 1, "cdf97": 2}
 RULE = {"const": 0, "accum": 1, "capped": 2}
 STORE = {"f64": 0, "f32": 1, "bf16": 2, "i8": 3}
 PREC = {"f64": 0, "f32": 1}

@@ -48,6 +48,7 @@ void reg_transport_f32_p64l3(std::vector<KernelEntry>&);
 void reg_transport_f32_p64l4(std::vector<KernelEntry>&);
 void reg_transport_f32_p64l5(std::vector<KernelEntry>&);
 void reg_transport_f64_p32l3(std::vector<KernelEntry>&);
+void reg_transport_cdf97_f32_p64l4(std::vector<KernelEntry>&);
 void reg_swe_f32_p64l4(std::vector<KernelEntry>&);
 void reg_swe_f32_p32l4(std::vector<KernelEntry>&);
 void reg_swe_f64_p32l3(std::vector<KernelEntry>&);
@@ -78,6 +79,7 @@ void register_all(std::vector<KernelEntry>& v) {
   reg_transport_f32_p64l4(v);
   reg_transport_f32_p64l5(v);
   reg_transport_f64_p32l3(v);
+  reg_transport_cdf97_f32_p64l4(v);
   reg_swe_f32_p64l4(v);
   reg_swe_f32_p32l4(v);
   reg_swe_f64_p32l3(v);
@@ -635,14 +637,14 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
   for (int a = 0; a < 2; ++a) {
     s->n[a] = grid->n[a];
     s->per[a] = (grid->periodic_mask >> a) & 1u;
-    s->G[a] = (s->wavelet == WCS_BL53 && !s->per[a]) ? s->n[a] + 1 : s->n[a];
+    s->G[a] = (wcs::wv_nodal(s->wavelet) && !s->per[a]) ? s->n[a] + 1 : s->n[a];
   }
   s->npx = int(s->n[0] / patch);
   s->npy = int(s->n[1] / patch);
   s->npatch = s->npx * s->npy;
   s->F = wcs::scheme_fields(scheme);
-  s->E = s->wavelet == WCS_BL53 ? patch + 1 : patch;
-  s->NC1 = (patch >> levels) + (s->wavelet == WCS_BL53 ? 1 : 0);
+  s->E = wcs::wv_nodal(s->wavelet) ? patch + 1 : patch;
+  s->NC1 = (patch >> levels) + (wcs::wv_nodal(s->wavelet) ? 1 : 0);
   s->nc = s->NC1 * s->NC1;
   s->nb = (levels + 1) * (levels + 1);
   s->tsize = s->prec == WCS_FP64 ? 8 : 4;

@@ -18,7 +18,20 @@ __host__ __device__ constexpr int scheme_fields(int s) {
   return s == SCH_D2Q9 ? 9 : (s == SCH_D3Q19 ? 19 : (s == SCH_EULER2D ? 4 : (s == SCH_TRANSPORT ? 1 : 3)));
 }
 __host__ __device__ constexpr bool scheme_fv(int s) { return s == SCH_EULER2D || s == SCH_TRANSPORT || s == SCH_SWE; }
-enum { WV_BL53 = 0, WV_HAAR = 1 };
+enum { WV_BL53 = 0, WV_HAAR = 1, WV_CDF97 = 2 };
+
+// Wavelets on 2^j+1 nodes whose end nodes neighbouring patches share
+// (BL5/3, CDF 9/7); Haar works on 2^j cells.
+__host__ __device__ constexpr bool wv_nodal(int wv) { return wv != WV_HAAR; }
+
+// CDF 9/7 (the second-order alternative Sec. 2.1.2 names; lifting
+// factorisation of Daubechies and Sweldens): four lifting steps d += a (s +
+// s'), s += b (d + d'), d += g (s + s'), s += e (d + d') with whole-sample
+// symmetric ends (d_-1 = d_0, d_K = d_K-1), then s /= K, d *= K with K =
+// 1 + 2b(1 + 2a) so that the low pass keeps constants.
+constexpr double CDF97_A = -1.586134342059924, CDF97_B = -0.052980118572961, CDF97_G = 0.882911075530934,
+                 CDF97_D = 0.443506852043971;
+constexpr double CDF97_K = 1.0 + 2.0 * CDF97_B * (1.0 + 2.0 * CDF97_A);
 enum { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2, ST_I8 = 3 };
 enum { MODE_INIT = 0, MODE_STEP = 1, MODE_EXPORT = 2 };
 
@@ -72,6 +85,22 @@ template <int WV, int P, int LEV, int L, typename T> __device__ __forceinline__ 
         const T e = fma_rn(bl53_alpha<T>(k - 1, K), v[(2 * k - 1) * st], v[2 * k * st]);
         v[2 * k * st] = fma_rn(bl53_alpha<T>(k, K), v[(2 * k + 1) * st], e);
       }
+    } else if constexpr (WV == WV_CDF97) {
+      constexpr auto dd = [](int k) { return (2 * (k < 0 ? 0 : (k >= K ? K - 1 : k)) + 1) * st; };
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        v[(2 * k + 1) * st] = v[(2 * k + 1) * st] + T(CDF97_A) * (v[2 * k * st] + v[(2 * k + 2) * st]);
+#pragma unroll
+      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] + T(CDF97_B) * (v[dd(k - 1)] + v[dd(k)]);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        v[(2 * k + 1) * st] = v[(2 * k + 1) * st] + T(CDF97_G) * (v[2 * k * st] + v[(2 * k + 2) * st]);
+#pragma unroll
+      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] + T(CDF97_D) * (v[dd(k - 1)] + v[dd(k)]);
+#pragma unroll
+      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] / T(CDF97_K);
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] * T(CDF97_K);
     } else {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -98,6 +127,22 @@ template <int WV, int P, int LEV, typename T> __device__ __forceinline__ void in
 #pragma unroll
       for (int k = 0; k < K; ++k)
         v[(2 * k + 1) * st] = fma_rn(T(0.5), v[2 * k * st] + v[(2 * k + 2) * st], v[(2 * k + 1) * st]);
+    } else if constexpr (WV == WV_CDF97) {
+      constexpr auto dd = [](int k) { return (2 * (k < 0 ? 0 : (k >= K ? K - 1 : k)) + 1) * st; };
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] / T(CDF97_K);
+#pragma unroll
+      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] * T(CDF97_K);
+#pragma unroll
+      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] - T(CDF97_D) * (v[dd(k - 1)] + v[dd(k)]);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        v[(2 * k + 1) * st] = v[(2 * k + 1) * st] - T(CDF97_G) * (v[2 * k * st] + v[(2 * k + 2) * st]);
+#pragma unroll
+      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] - T(CDF97_B) * (v[dd(k - 1)] + v[dd(k)]);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        v[(2 * k + 1) * st] = v[(2 * k + 1) * st] - T(CDF97_A) * (v[2 * k * st] + v[(2 * k + 2) * st]);
     } else {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -128,6 +173,22 @@ __device__ __forceinline__ void fwd_levels_cb(T* v, CB& cb) {
         const T e = fma_rn(bl53_alpha<T>(k - 1, K), v[(2 * k - 1) * st], v[2 * k * st]);
         v[2 * k * st] = fma_rn(bl53_alpha<T>(k, K), v[(2 * k + 1) * st], e);
       }
+    } else if constexpr (WV == WV_CDF97) {
+      constexpr auto dd = [](int k) { return (2 * (k < 0 ? 0 : (k >= K ? K - 1 : k)) + 1) * st; };
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        v[(2 * k + 1) * st] = v[(2 * k + 1) * st] + T(CDF97_A) * (v[2 * k * st] + v[(2 * k + 2) * st]);
+#pragma unroll
+      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] + T(CDF97_B) * (v[dd(k - 1)] + v[dd(k)]);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        v[(2 * k + 1) * st] = v[(2 * k + 1) * st] + T(CDF97_G) * (v[2 * k * st] + v[(2 * k + 2) * st]);
+#pragma unroll
+      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] + T(CDF97_D) * (v[dd(k - 1)] + v[dd(k)]);
+#pragma unroll
+      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] / T(CDF97_K);
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] * T(CDF97_K);
     } else {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -141,7 +202,7 @@ __device__ __forceinline__ void fwd_levels_cb(T* v, CB& cb) {
     for (int k = 0; k < K; ++k) cb((2 * k + 1) * st);
     fwd_levels_cb<WV, P, LEV + 1, L, T, CB>(v, cb);
   } else {
-    constexpr int E = WV == WV_BL53 ? P + 1 : P;
+    constexpr int E = wv_nodal(WV) ? P + 1 : P;
 #pragma unroll
     for (int y = 0; y < E; y += (1 << L)) cb(y);
   }
@@ -151,7 +212,7 @@ __device__ __forceinline__ void fwd_levels_cb(T* v, CB& cb) {
 // registers.
 template <int WV, int P, int L, bool INVERSE, typename T>
 __device__ __forceinline__ void line_transform(T* p, int stride) {
-  constexpr int E = WV == WV_BL53 ? P + 1 : P;
+  constexpr int E = wv_nodal(WV) ? P + 1 : P;
   T v[E];
 #pragma unroll
   for (int i = 0; i < E; ++i) v[i] = p[i * stride];

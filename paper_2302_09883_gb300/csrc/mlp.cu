@@ -652,6 +652,7 @@ wcs_status wcs_features_labels(const float* dense_dev, int nfields, int64_t nx, 
   if (!dense_dev || nfields <= 0 || patch <= 0 || levels <= 0 || levels > 8 || nx % patch || ny % patch || !feat_dev ||
       !label_dev)
     return WCS_E_ARG;
+  if (wavelet != WCS_BL53 && wavelet != WCS_HAAR) return WCS_E_UNSUPPORTED;  // features of BL5/3 and Haar patches
   const int E = wavelet == WCS_BL53 ? patch + 1 : patch;
   const size_t smem = (3 * size_t(E) * E + 256) * sizeof(double);
   double grid[EPS_N];

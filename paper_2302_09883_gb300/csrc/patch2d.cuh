@@ -75,12 +75,12 @@ struct PatchArgs {
 template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   static constexpr int F = scheme_fields(SCH);
   static constexpr bool FV = scheme_fv(SCH);  // ghost ring of the state, dt/h
-  static constexpr int E = WV == WV_BL53 ? P + 1 : P;
+  static constexpr int E = wv_nodal(WV) ? P + 1 : P;
   static constexpr int W = E + 2;
   static constexpr int PW = (W % 2) ? W : W + 1;
   static constexpr int TS = W * PW;
   static constexpr int NTILE = FV ? 2 * F : F;
-  static constexpr int NC1 = (P >> L) + (WV == WV_BL53 ? 1 : 0);
+  static constexpr int NC1 = (P >> L) + (wv_nodal(WV) ? 1 : 0);
   static constexpr int NC = NC1 * NC1;
   static constexpr int NALL = E * E;
   static constexpr int WR = (P + 31) / 32;        // mask words per row
@@ -98,7 +98,7 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   static constexpr int RING = RINGFREE ? 0 : (SCH == SCH_D2Q9 ? 12 * E + 4 : 4 * F * E);
   static constexpr int NT = sizeof(T) == 8 ? 512 : 768;
   static constexpr int NWARP = NT / 32;
-  static constexpr int XLO = WV == WV_BL53 ? 1 : 0;
+  static constexpr int XLO = wv_nodal(WV) ? 1 : 0;
   static constexpr int XHI = P - 1;
   static constexpr int LMASK = (1 << L) - 1;
   // shared memory carve-up (bytes)
@@ -131,7 +131,7 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
 // Edge-line bits of mask word w (BL5/3: nodes with x or y in {0, P}); coarse
 // nodes may be included, they never carry a mask bit.
 template <int WV, int P, int E, int WR> __device__ __forceinline__ unsigned int word_edges(int w) {
-  if constexpr (WV != WV_BL53) return 0u;
+  if constexpr (!wv_nodal(WV)) return 0u;
   if (w < E * WR) {
     const int y = w / WR, h = w - y * WR;
     const int n = P - 32 * h;
@@ -194,7 +194,7 @@ template <int L> __device__ __forceinline__ constexpr unsigned int coarse_rows(i
 // cm are zero: those read as zero and are not loaded.
 template <int WV, int P, int L, typename T>
 __device__ __forceinline__ void inverse_line_masked(T* p, int stride, const unsigned int* cm) {
-  constexpr int E = WV == WV_BL53 ? P + 1 : P;
+  constexpr int E = wv_nodal(WV) ? P + 1 : P;
   T v[E];
 #pragma unroll
   for (int i = 0; i < E; ++i) v[i] = ((cm[i >> 5] >> (i & 31)) & 1u) ? p[i * stride] : T(0);
@@ -1088,7 +1088,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
 
   if constexpr (MODE == MODE_EXPORT) {
     const bool lastx = !a.per_x && px == a.npx - 1, lasty = !a.per_y && py == a.npy - 1;
-    const int XE = (WV == WV_BL53 && lastx) ? E : P, YE = (WV == WV_BL53 && lasty) ? E : P;
+    const int XE = (wv_nodal(WV) && lastx) ? E : P, YE = (wv_nodal(WV) && lasty) ? E : P;
     const int f0 = a.field_sel < 0 ? 0 : a.field_sel, f1 = a.field_sel < 0 ? F : a.field_sel + 1;
     const long long plane = a.G0 * a.G1;
     for (int f = f0; f < f1; ++f)
@@ -1223,7 +1223,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     const int cx = cls_x[h];
     T* col = tiles + win_out(f) + (valid ? x : 0);
     const T* te = tau_e + cx * (L + 1);
-    const bool xedge = WV == WV_BL53 && x == 0;
+    const bool xedge = wv_nodal(WV) && x == 0;
     T thr[L + 1];  // this lane's threshold per y class (rows y = 0, P use te)
 #pragma unroll
     for (int c = 0; c <= L; ++c) thr[c] = xedge ? te[c] : tau_i[cx * (L + 1) + c];
@@ -1245,7 +1245,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       }
       bool keep = false;
       if (cx | cy) {
-        const bool yedge = WV == WV_BL53 && (y == 0 || y == P);  // folds: y is a constant here
+        const bool yedge = wv_nodal(WV) && (y == 0 || y == P);  // folds: y is a constant here
         keep = valid && fabs(v[y]) >= (yedge ? te[cy] : thr[cy]);
         if (STORE_ALL && !keep) v[y] = T(0);  // ring-free: dropped details are not stored
       }
@@ -1528,7 +1528,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       for (int c = t & 31; c < NC; c += 32) {
         const int iy = c / C::NC1, ix = c - iy * C::NC1;
         double w = 1.0;
-        if constexpr (WV == WV_BL53) {
+        if constexpr (wv_nodal(WV)) {
           const bool ex = ix == 0 || ix == C::NC1 - 1, ey = iy == 0 || iy == C::NC1 - 1;
           w = ex && ey ? 0.25 : (ex || ey ? 0.5 : 1.0);
         }

@@ -98,3 +98,28 @@ def test_dense_fv_baselines_match_oracle_reference(scheme):
     r.step(steps)
     for q in range(d.F):
         assert np.array_equal(d.export_field(q), r.export_field(q))
+
+
+@pytest.mark.parametrize("rule", ["const", "capped"])
+def test_transport_cdf97_bitwise(rule):
+    # the CDF 9/7 wavelet (Sec. 2.1.2's second-order alternative) in the
+    # same fused step: records and fields bit for bit against the oracle
+    f = inputs.transport_gaussian(128)
+    g, o = pair_wv("transport", "cdf97", 128, 64, 4, 0.01, rule, f, (1, 20, 64), **TR)
+    assert np.array_equal(g.export_field(-1), o.export_all())
+
+
+def pair_wv(scheme, wv, n, P, L, eps, rule, fields, steps_at, **kw):
+    g = Sim(scheme, wv, n, n, P, L, eps, prec="f32", store="f32", rule=rule, **kw)
+    o = O.OracleSim(scheme, wv, n, n, P, L, eps, prec="f32", store="f32", rule=rule, **kw)
+    g.init_macro(fields)
+    o.init_macro(fields)
+    done = 0
+    for s in [0] + list(steps_at):
+        g.step(s - done)
+        o.step(s - done)
+        done = s
+        g.sync()
+        for p in range(g.npatch):
+            assert g.record(p) == o.record(p), "patch %d record differs after %d steps" % (p, s)
+    return g, o
