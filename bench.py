@@ -480,13 +480,14 @@ def _rel_dev(torch, a, b):
 
 
 def batch_section(torch, K, W, flush, bs, nsims=96, quality_steps=500,
-                  eps_ladder=(1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7, 1e-7)):
+                  eps_ladder=(1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 0.0)):
     """96 independent D2Q9 runs, sides drawn from {256,512,1024,2048} (seeded),
     Gaussian bumps with amplitude U(0.01,0.1) and width U(4,32), FP32/BF16,
     P chosen per side by the library's autotuner among (64,4) and (32,3).
-    Each simulation gets its own eps: the largest of a ladder whose 500-step
-    run keeps the relative L2 error of u and rho <= 1e-3 against its own
-    uncompressed run.  The batch steps both patch sizes in one persistent
+    Each simulation gets its own eps: the largest of a ladder (down to 0,
+    which keeps every coefficient) whose 500-step run keeps the relative L2
+    error of u and rho <= 1e-3 against its own uncompressed run, found by
+    bisection over the ladder (the error grows with eps).  The batch steps both patch sizes in one persistent
     launch per step (launch shape tuned), six steps per CUDA-graph replay;
     each replay is one timed unit with the L2 flushed before it."""
     from paper_2302_09883_gb300 import Batch, Dense, Sim, autotune
@@ -512,8 +513,7 @@ def batch_section(torch, K, W, flush, bs, nsims=96, quality_steps=500,
         d.close()
         rd, uxd, uyd = _velocity_rho_dev(torch, Fd)
         ud = torch.stack([uxd, uyd])
-        chosen = None
-        for eps in eps_ladder:
+        def trial(eps):
             c = Sim("d2q9", "bl53", n, n, P, L, eps, prec="f32", store="bf16", tau=tau, stream=bs)
             c.init_macro(dev(sp))
             c.step(quality_steps)
@@ -521,14 +521,20 @@ def batch_section(torch, K, W, flush, bs, nsims=96, quality_steps=500,
             c.export_field(-1, out=Fc)
             c.close()
             rc, uxc, uyc = _velocity_rho_dev(torch, Fc)
-            e_u, e_r = _rel_dev(torch, torch.stack([uxc, uyc]), ud), _rel_dev(torch, rc, rd)
-            if e_u <= 1e-3 and e_r <= 1e-3:
-                chosen = (eps, e_u, e_r)
-                break
-        if chosen is None:
-            chosen = (eps_ladder[-1], e_u, e_r)
-        eps_of.append(chosen[0])
-        err_of.append({"u": chosen[1], "rho": chosen[2]})
+            return _rel_dev(torch, torch.stack([uxc, uyc]), ud), _rel_dev(torch, rc, rd)
+        lo, hi = 0, len(eps_ladder) - 1  # find the first index that passes
+        res = {}
+        while lo < hi:
+            mid = (lo + hi) // 2
+            res[mid] = trial(eps_ladder[mid])
+            if res[mid][0] <= 1e-3 and res[mid][1] <= 1e-3:
+                hi = mid
+            else:
+                lo = mid + 1
+        if lo not in res:
+            res[lo] = trial(eps_ladder[lo])
+        eps_of.append(eps_ladder[lo])
+        err_of.append({"u": res[lo][0], "rho": res[lo][1]})
     sims = []
     for sp, eps in zip(specs, eps_of):
         n = sp["side"]

