@@ -66,9 +66,10 @@ typedef enum { WCS_D2Q9 = 0, WCS_D3Q19 = 1, WCS_EULER2D = 2, WCS_TRANSPORT = 3, 
 
 /* Wavelets: folded BL5/3 on P+1 nodes (Sec. 2.1.2), Haar on P cells, or
  * CDF 9/7 on P+1 nodes (the second-order alternative Sec. 2.1.2 names;
- * lifting factorisation with whole-sample symmetric ends, low pass keeping
- * constants; it keeps no trapezoid mass, so field_sum is an estimate);
- * CDF 9/7 is compiled for TRANSPORT, FP32/F32, P = 64, L = 4. */
+ * lifting factorisation folded like BL5/3: the end samples are kept, so
+ * shared edges decode alike in both patches; constants pass through; it
+ * keeps no trapezoid mass, so field_sum is an estimate); CDF 9/7 is
+ * compiled for TRANSPORT, FP32/F32, P = 64, L = 4. */
 typedef enum { WCS_BL53 = 0, WCS_HAAR = 1, WCS_CDF97 = 2 } wcs_wavelet;
 
 /* Threshold rules of Sec. 2.2 (accumulation / capped under the reading that
@@ -262,7 +263,8 @@ const char* wcs_last_error(const wcs_sim* sim);
 /* ------------------------------------------------------------------------
  * Batches of independent simulations (many grids of different sizes; one
  * launch per step when the batch holds the two patch sizes of a merged
- * kernel (D2Q9, BL5/3, FP32, BF16: 64 cells / 4 levels with 32 / 3), else
+ * kernel (D2Q9, BL5/3, FP32 compute, BF16 or FP32 details: 64 cells / 4
+ * levels with 32 / 3), else
  * one launch per kind of kernel; six steps captured in one CUDA graph and
  * replayed).  Every simulation must be initialised, created on the same
  * stream and at the same step; 3-D simulations and simulations with a
@@ -341,6 +343,18 @@ wcs_status wcs_mlp_grad(wcs_mlp* m, const float* X_dev, const float* t_dev, int 
  * epoch to loss_history_host[epochs]. */
 wcs_status wcs_mlp_train(wcs_mlp* m, const float* X_dev, const float* t_dev, int n, const int* batches_host, int epochs,
                          int batch, float lr, float* loss_history_host);
+/* Trains on raw features: the per-input mean and sample deviation of X_dev
+ * (n x nin, device, FP64 sums) and the mean of t_dev are taken on the device;
+ * the output bias starts at the mean target (Adam restarted); training
+ * (as wcs_mlp_train, same batches_host layout) runs on the standardised
+ * copy (x - mean) / max(deviation, sd_floor); the standardisation is then
+ * folded into the first layer (W1 / sd, b1 - (W1 / sd) mean), so that the
+ * network takes the raw features a learned-mode step writes.  n >= 2,
+ * sd_floor > 0.  stats_host (optional, 2 (nin + 1) doubles): mean and
+ * deviation of each input, then of t.  Allocates n x nin floats of scratch
+ * for the call; synchronises. */
+wcs_status wcs_mlp_fit(wcs_mlp* m, const float* X_dev, const float* t_dev, int n, const int* batches_host, int epochs,
+                       int batch, float lr, double sd_floor, float* loss_history_host, double* stats_host);
 wcs_status wcs_mlp_forward(wcs_mlp* m, const float* X_dev, int n, float* y_dev);
 /* per-patch eps = clamp(10^network(features), lo, hi); non-finite -> fallback */
 wcs_status wcs_mlp_eps(wcs_mlp* m, const float* feat_dev, int n, double lo, double hi, double fallback, double* eps_dev,

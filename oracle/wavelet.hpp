@@ -13,14 +13,17 @@
 //    lifting on 2^j cells): d = b - a, s = a + d/2.
 //  * CDF 9/7 (Sec. 2.1.2 names it as the second-order alternative to
 //    BL5/3; its lifting factorisation is I. Daubechies and W. Sweldens,
-//    "Factoring wavelet transforms into lifting steps", 1998): on the same
-//    2^j+1 nodes, per level four lifting steps d += a (s_k + s_k+1),
-//    s += b (d_k-1 + d_k), d += g (s_k + s_k+1), s += e (d_k-1 + d_k), with
-//    whole-sample symmetric ends (d_-1 = d_0, d_K = d_K-1: every predict has
-//    both neighbours), then s /= K, d *= K with K = 1 + 2b(1 + 2a), the gain
-//    of the first two steps on a constant, so that the low pass keeps
-//    constants.  It filters out cubic polynomials (four vanishing moments)
-//    but keeps no trapezoid mass.
+//    "Factoring wavelet transforms into lifting steps", 1998), folded onto
+//    the same 2^j+1 nodes the way the paper folds BL5/3: the two boundary
+//    samples are kept (never updated, never scaled), so a node that two
+//    patches share decodes from the shared edge line alone, identically in
+//    both.  Per level: d_k += a (s_k + s_k+1); s_k += b (d_k-1 + d_k) for the
+//    interior samples; d_k += g (s^_k + s^_k+1), where s^ is s inside and
+//    K s at the two ends (K = 1 + 2b(1 + 2a), the gain the interior samples
+//    got from the first two steps on a constant); s_k += e (d_k-1 + d_k)
+//    inside; then s_k /= K inside and d_k *= K.  Constants pass through
+//    unchanged with zero details; away from the ends it filters out cubic
+//    polynomials (four vanishing moments); it keeps no trapezoid mass.
 //  * N-D: the 1-D transform is applied along x for every line, then along y,
 //    then z (Sec. 2.1.2, last paragraphs: every row is transformed before any
 //    column).  This tensor reading is the one that reproduces the paper's
@@ -92,14 +95,15 @@ template <class T> void fwd1(int wavelet, T* u, int64_t stride, int64_t P, int L
         at(2 * k) = e;
       }
     } else if (wavelet == CDF97) {
-      const int64_t K = (P / st) / 2;  // details; samples 0..K
+      const int64_t K = (P / st) / 2;  // details; samples 0..K, the two ends kept
       const T ka = T(CDF97_A), kb = T(CDF97_B), kg = T(CDF97_G), kd = T(CDF97_D), KK = T(cdf97_K());
-      auto dd = [&](int64_t k) -> T& { return at(2 * (k < 0 ? 0 : (k >= K ? K - 1 : k)) + 1); };
+      // sample k as the second predict sees it: K times the kept ends
+      auto sh = [&](int64_t k) -> T { return (k == 0 || k == K) ? KK * at(2 * k) : at(2 * k); };
       for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) + ka * (at(2 * k) + at(2 * k + 2));
-      for (int64_t k = 0; k <= K; ++k) at(2 * k) = at(2 * k) + kb * (dd(k - 1) + dd(k));
-      for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) + kg * (at(2 * k) + at(2 * k + 2));
-      for (int64_t k = 0; k <= K; ++k) at(2 * k) = at(2 * k) + kd * (dd(k - 1) + dd(k));
-      for (int64_t k = 0; k <= K; ++k) at(2 * k) = at(2 * k) / KK;
+      for (int64_t k = 1; k < K; ++k) at(2 * k) = at(2 * k) + kb * (at(2 * k - 1) + at(2 * k + 1));
+      for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) + kg * (sh(k) + sh(k + 1));
+      for (int64_t k = 1; k < K; ++k) at(2 * k) = at(2 * k) + kd * (at(2 * k - 1) + at(2 * k + 1));
+      for (int64_t k = 1; k < K; ++k) at(2 * k) = at(2 * k) / KK;
       for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) * KK;
     } else {
       const int64_t K = (P / st) / 2;  // pairs
@@ -130,12 +134,12 @@ template <class T> void inv1(int wavelet, T* u, int64_t stride, int64_t P, int L
     } else if (wavelet == CDF97) {
       const int64_t K = (P / st) / 2;
       const T ka = T(CDF97_A), kb = T(CDF97_B), kg = T(CDF97_G), kd = T(CDF97_D), KK = T(cdf97_K());
-      auto dd = [&](int64_t k) -> T& { return at(2 * (k < 0 ? 0 : (k >= K ? K - 1 : k)) + 1); };
+      auto sh = [&](int64_t k) -> T { return (k == 0 || k == K) ? KK * at(2 * k) : at(2 * k); };
       for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) / KK;
-      for (int64_t k = 0; k <= K; ++k) at(2 * k) = at(2 * k) * KK;
-      for (int64_t k = 0; k <= K; ++k) at(2 * k) = at(2 * k) - kd * (dd(k - 1) + dd(k));
-      for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) - kg * (at(2 * k) + at(2 * k + 2));
-      for (int64_t k = 0; k <= K; ++k) at(2 * k) = at(2 * k) - kb * (dd(k - 1) + dd(k));
+      for (int64_t k = 1; k < K; ++k) at(2 * k) = at(2 * k) * KK;
+      for (int64_t k = 1; k < K; ++k) at(2 * k) = at(2 * k) - kd * (at(2 * k - 1) + at(2 * k + 1));
+      for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) - kg * (sh(k) + sh(k + 1));
+      for (int64_t k = 1; k < K; ++k) at(2 * k) = at(2 * k) - kb * (at(2 * k - 1) + at(2 * k + 1));
       for (int64_t k = 0; k < K; ++k) at(2 * k + 1) = at(2 * k + 1) - ka * (at(2 * k) + at(2 * k + 2));
     } else {
       const int64_t K = (P / st) / 2;

@@ -96,6 +96,8 @@ def lib():
         L.wcs_mlp_get_weights.argtypes = [vp, fp]
         L.wcs_mlp_grad.argtypes = [vp, vp, vp, i32, fp, fp]
         L.wcs_mlp_train.argtypes = [vp, vp, vp, i32, C.POINTER(i32), i32, i32, C.c_float, fp]
+        L.wcs_mlp_fit.argtypes = [vp, vp, vp, i32, C.POINTER(i32), i32, i32, C.c_float, C.c_double, fp,
+                                  C.POINTER(C.c_double)]
         L.wcs_mlp_forward.argtypes = [vp, vp, i32, vp]
         L.wcs_sim_use_mlp.argtypes = [vp, vp, C.c_double, C.c_double]
         L.wcs_sim_set_patch_eps.argtypes = [vp, C.POINTER(C.c_double)]

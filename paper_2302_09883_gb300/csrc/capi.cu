@@ -38,6 +38,7 @@ void reg_d2q9_bl53_f64_p32l3(std::vector<KernelEntry>&);
 void reg_d2q9_bl53_bf16_p64l4(std::vector<KernelEntry>&);
 void reg_d2q9_bl53_bf16_p32l3(std::vector<KernelEntry>&);
 void reg_d2q9_bl53_f32_p64l4(std::vector<KernelEntry>&);
+void reg_d2q9_bl53_f32_p32l3(std::vector<KernelEntry>&);
 void reg_d2q9_bl53_i8_p64l4(std::vector<KernelEntry>&);
 void reg_euler_bl53_i8_p64l4(std::vector<KernelEntry>&);
 void reg_euler_bl53_f64_p32l3(std::vector<KernelEntry>&);
@@ -69,6 +70,7 @@ void register_all(std::vector<KernelEntry>& v) {
   reg_d2q9_bl53_bf16_p64l4(v);
   reg_d2q9_bl53_bf16_p32l3(v);
   reg_d2q9_bl53_f32_p64l4(v);
+  reg_d2q9_bl53_f32_p32l3(v);
   reg_d2q9_bl53_i8_p64l4(v);
   reg_euler_bl53_i8_p64l4(v);
   reg_euler_bl53_f64_p32l3(v);

@@ -25,10 +25,12 @@ enum { WV_BL53 = 0, WV_HAAR = 1, WV_CDF97 = 2 };
 __host__ __device__ constexpr bool wv_nodal(int wv) { return wv != WV_HAAR; }
 
 // CDF 9/7 (the second-order alternative Sec. 2.1.2 names; lifting
-// factorisation of Daubechies and Sweldens): four lifting steps d += a (s +
-// s'), s += b (d + d'), d += g (s + s'), s += e (d + d') with whole-sample
-// symmetric ends (d_-1 = d_0, d_K = d_K-1), then s /= K, d *= K with K =
-// 1 + 2b(1 + 2a) so that the low pass keeps constants.
+// factorisation of Daubechies and Sweldens), folded onto the 2^j+1 node
+// lines like the paper's BL5/3: the two end samples are kept (never
+// updated or scaled), so a shared node decodes from its edge line alone.
+// d += a (s + s'); interior s += b (d + d'); d += g (s^ + s^') with s^ = K s
+// at the ends; interior s += e (d + d'); interior s /= K; d *= K, where K =
+// 1 + 2b(1 + 2a): constants pass through with zero details.
 constexpr double CDF97_A = -1.586134342059924, CDF97_B = -0.052980118572961, CDF97_G = 0.882911075530934,
                  CDF97_D = 0.443506852043971;
 constexpr double CDF97_K = 1.0 + 2.0 * CDF97_B * (1.0 + 2.0 * CDF97_A);
@@ -86,21 +88,24 @@ template <int WV, int P, int LEV, int L, typename T> __device__ __forceinline__ 
         v[2 * k * st] = fma_rn(bl53_alpha<T>(k, K), v[(2 * k + 1) * st], e);
       }
     } else if constexpr (WV == WV_CDF97) {
-      constexpr auto dd = [](int k) { return (2 * (k < 0 ? 0 : (k >= K ? K - 1 : k)) + 1) * st; };
+      const T KK = T(CDF97_K);
 #pragma unroll
       for (int k = 0; k < K; ++k)
         v[(2 * k + 1) * st] = v[(2 * k + 1) * st] + T(CDF97_A) * (v[2 * k * st] + v[(2 * k + 2) * st]);
 #pragma unroll
-      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] + T(CDF97_B) * (v[dd(k - 1)] + v[dd(k)]);
+      for (int k = 1; k < K; ++k) v[2 * k * st] = v[2 * k * st] + T(CDF97_B) * (v[(2 * k - 1) * st] + v[(2 * k + 1) * st]);
 #pragma unroll
-      for (int k = 0; k < K; ++k)
-        v[(2 * k + 1) * st] = v[(2 * k + 1) * st] + T(CDF97_G) * (v[2 * k * st] + v[(2 * k + 2) * st]);
+      for (int k = 0; k < K; ++k) {
+        const T sl = k == 0 ? KK * v[0] : v[2 * k * st];
+        const T sr = k == K - 1 ? KK * v[2 * K * st] : v[(2 * k + 2) * st];
+        v[(2 * k + 1) * st] = v[(2 * k + 1) * st] + T(CDF97_G) * (sl + sr);
+      }
 #pragma unroll
-      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] + T(CDF97_D) * (v[dd(k - 1)] + v[dd(k)]);
+      for (int k = 1; k < K; ++k) v[2 * k * st] = v[2 * k * st] + T(CDF97_D) * (v[(2 * k - 1) * st] + v[(2 * k + 1) * st]);
 #pragma unroll
-      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] / T(CDF97_K);
+      for (int k = 1; k < K; ++k) v[2 * k * st] = v[2 * k * st] / KK;
 #pragma unroll
-      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] * T(CDF97_K);
+      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] * KK;
     } else {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -128,18 +133,21 @@ template <int WV, int P, int LEV, typename T> __device__ __forceinline__ void in
       for (int k = 0; k < K; ++k)
         v[(2 * k + 1) * st] = fma_rn(T(0.5), v[2 * k * st] + v[(2 * k + 2) * st], v[(2 * k + 1) * st]);
     } else if constexpr (WV == WV_CDF97) {
-      constexpr auto dd = [](int k) { return (2 * (k < 0 ? 0 : (k >= K ? K - 1 : k)) + 1) * st; };
+      const T KK = T(CDF97_K);
 #pragma unroll
-      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] / T(CDF97_K);
+      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] / KK;
 #pragma unroll
-      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] * T(CDF97_K);
+      for (int k = 1; k < K; ++k) v[2 * k * st] = v[2 * k * st] * KK;
 #pragma unroll
-      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] - T(CDF97_D) * (v[dd(k - 1)] + v[dd(k)]);
+      for (int k = 1; k < K; ++k) v[2 * k * st] = v[2 * k * st] - T(CDF97_D) * (v[(2 * k - 1) * st] + v[(2 * k + 1) * st]);
 #pragma unroll
-      for (int k = 0; k < K; ++k)
-        v[(2 * k + 1) * st] = v[(2 * k + 1) * st] - T(CDF97_G) * (v[2 * k * st] + v[(2 * k + 2) * st]);
+      for (int k = 0; k < K; ++k) {
+        const T sl = k == 0 ? KK * v[0] : v[2 * k * st];
+        const T sr = k == K - 1 ? KK * v[2 * K * st] : v[(2 * k + 2) * st];
+        v[(2 * k + 1) * st] = v[(2 * k + 1) * st] - T(CDF97_G) * (sl + sr);
+      }
 #pragma unroll
-      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] - T(CDF97_B) * (v[dd(k - 1)] + v[dd(k)]);
+      for (int k = 1; k < K; ++k) v[2 * k * st] = v[2 * k * st] - T(CDF97_B) * (v[(2 * k - 1) * st] + v[(2 * k + 1) * st]);
 #pragma unroll
       for (int k = 0; k < K; ++k)
         v[(2 * k + 1) * st] = v[(2 * k + 1) * st] - T(CDF97_A) * (v[2 * k * st] + v[(2 * k + 2) * st]);
@@ -174,21 +182,24 @@ __device__ __forceinline__ void fwd_levels_cb(T* v, CB& cb) {
         v[2 * k * st] = fma_rn(bl53_alpha<T>(k, K), v[(2 * k + 1) * st], e);
       }
     } else if constexpr (WV == WV_CDF97) {
-      constexpr auto dd = [](int k) { return (2 * (k < 0 ? 0 : (k >= K ? K - 1 : k)) + 1) * st; };
+      const T KK = T(CDF97_K);
 #pragma unroll
       for (int k = 0; k < K; ++k)
         v[(2 * k + 1) * st] = v[(2 * k + 1) * st] + T(CDF97_A) * (v[2 * k * st] + v[(2 * k + 2) * st]);
 #pragma unroll
-      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] + T(CDF97_B) * (v[dd(k - 1)] + v[dd(k)]);
+      for (int k = 1; k < K; ++k) v[2 * k * st] = v[2 * k * st] + T(CDF97_B) * (v[(2 * k - 1) * st] + v[(2 * k + 1) * st]);
 #pragma unroll
-      for (int k = 0; k < K; ++k)
-        v[(2 * k + 1) * st] = v[(2 * k + 1) * st] + T(CDF97_G) * (v[2 * k * st] + v[(2 * k + 2) * st]);
+      for (int k = 0; k < K; ++k) {
+        const T sl = k == 0 ? KK * v[0] : v[2 * k * st];
+        const T sr = k == K - 1 ? KK * v[2 * K * st] : v[(2 * k + 2) * st];
+        v[(2 * k + 1) * st] = v[(2 * k + 1) * st] + T(CDF97_G) * (sl + sr);
+      }
 #pragma unroll
-      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] + T(CDF97_D) * (v[dd(k - 1)] + v[dd(k)]);
+      for (int k = 1; k < K; ++k) v[2 * k * st] = v[2 * k * st] + T(CDF97_D) * (v[(2 * k - 1) * st] + v[(2 * k + 1) * st]);
 #pragma unroll
-      for (int k = 0; k <= K; ++k) v[2 * k * st] = v[2 * k * st] / T(CDF97_K);
+      for (int k = 1; k < K; ++k) v[2 * k * st] = v[2 * k * st] / KK;
 #pragma unroll
-      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] * T(CDF97_K);
+      for (int k = 0; k < K; ++k) v[(2 * k + 1) * st] = v[(2 * k + 1) * st] * KK;
     } else {
 #pragma unroll
       for (int k = 0; k < K; ++k) {

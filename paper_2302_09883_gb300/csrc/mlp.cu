@@ -528,6 +528,46 @@ __global__ void mlp_adam(float* w, const float* g, float* m1, float* m2, int np,
   w[p] -= lr * mh / (sqrtf(vh) + 1e-8f);
 }
 
+// Per-column mean and sample deviation of X (n x ncol, row-major) in FP64,
+// one block per column; column ncol of the output is the target vector t
+// (its mean only).  stats[2c] = mean, stats[2c+1] = deviation.
+__global__ void __launch_bounds__(256) column_stats(const float* __restrict__ X, int n, int ncol,
+                                                    const float* __restrict__ t, double* stats) {
+  const int c = blockIdx.x;
+  double s = 0, s2 = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = c < ncol ? double(X[size_t(i) * ncol + c]) : double(t[i]);
+    s += v;
+    s2 += v * v;
+  }
+  __shared__ double rs[256], rs2[256];
+  rs[threadIdx.x] = s;
+  rs2[threadIdx.x] = s2;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      rs[threadIdx.x] += rs[threadIdx.x + h];
+      rs2[threadIdx.x] += rs2[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double mean = rs[0] / n;
+    const double var = n > 1 ? fmax(rs2[0] - n * mean * mean, 0.0) / (n - 1) : 0.0;
+    stats[2 * c] = mean;
+    stats[2 * c + 1] = sqrt(var);
+  }
+}
+
+// Xs = (X - mean) / max(deviation, floor), column by column.
+__global__ void standardise(const float* __restrict__ X, int n, int ncol, const double* __restrict__ stats,
+                            double floor_sd, float* __restrict__ Xs) {
+  const size_t k = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= size_t(n) * ncol) return;
+  const int c = int(k % ncol);
+  Xs[k] = float((double(X[k]) - stats[2 * c]) / fmax(stats[2 * c + 1], floor_sd));
+}
+
 // Inference: a block of 256 threads takes four samples at a time, one
 // thread per hidden unit; the weights are staged in shared memory with W1
 // and W2 transposed and rows padded to 65 floats, so that staging writes and
@@ -792,6 +832,55 @@ wcs_status wcs_mlp_train(wcs_mlp* m, const float* X_dev, const float* t_dev, int
   cudaFree(ls);
   cudaFree(idx);
   return e == cudaSuccess ? WCS_OK : WCS_E_CUDA;
+}
+
+wcs_status wcs_mlp_fit(wcs_mlp* m, const float* X_dev, const float* t_dev, int n, const int* batches_host, int epochs,
+                       int batch, float lr, double sd_floor, float* loss_history_host, double* stats_host) {
+  if (!m || !X_dev || !t_dev || n <= 1 || batch <= 0 || batch > n || epochs <= 0 || !batches_host || !(sd_floor > 0))
+    return WCS_E_ARG;
+  const int nin = m->nin, np = nparam(nin);
+  double* st = nullptr;
+  float* Xs = nullptr;
+  if (cudaMalloc(&st, size_t(2) * (nin + 1) * 8) != cudaSuccess ||
+      cudaMalloc(&Xs, size_t(n) * nin * 4) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(st);
+    return WCS_E_OOM;
+  }
+  column_stats<<<nin + 1, 256>>>(X_dev, n, nin, t_dev, st);
+  const size_t tot = size_t(n) * nin;
+  standardise<<<unsigned((tot + 255) / 256), 256>>>(X_dev, n, nin, st, sd_floor, Xs);
+  std::vector<double> s(2 * (nin + 1));
+  std::vector<float> w(np);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(s.data(), st, s.size() * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(w.data(), m->w, np * 4, cudaMemcpyDeviceToHost);
+  wcs_status r = WCS_E_CUDA;
+  if (e == cudaSuccess) {
+    w[np - 1] = float(s[2 * nin]);  // the output bias starts at the mean target
+    if (wcs_mlp_set_weights(m, w.data()) == WCS_OK)  // also restarts Adam
+      r = wcs_mlp_train(m, Xs, t_dev, n, batches_host, epochs, batch, lr, loss_history_host);
+  }
+  if (r == WCS_OK && cudaMemcpy(w.data(), m->w, np * 4, cudaMemcpyDeviceToHost) == cudaSuccess) {
+    // fold the standardisation into the first layer: W1 x' + b1 with
+    // x' = (x - mean) / sd equals (W1 / sd) x + (b1 - (W1 / sd) mean)
+    for (int h = 0; h < MLP_NH; ++h) {
+      double b = w[MLP_NH * nin + h];
+      for (int c = 0; c < nin; ++c) {
+        const double wf = double(w[h * nin + c]) / std::max(s[2 * c + 1], sd_floor);
+        b -= wf * s[2 * c];
+        w[h * nin + c] = float(wf);
+      }
+      w[MLP_NH * nin + h] = float(b);
+    }
+    r = wcs_mlp_set_weights(m, w.data());
+  } else if (r == WCS_OK) {
+    r = WCS_E_CUDA;
+  }
+  if (stats_host) std::copy(s.begin(), s.end(), stats_host);
+  cudaFree(st);
+  cudaFree(Xs);
+  return r;
 }
 
 wcs_status wcs_mlp_forward(wcs_mlp* m, const float* X_dev, int n, float* y_dev) {

@@ -301,7 +301,15 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
     return kind == 0 ? cone_index(MX, kx) * E + ky
                      : (kind == 1 ? cone_index(MY, ky) * E + kx : cone_index(MY, ky) * NCN + cone_index(MX, kx));
   };
-  const unsigned char* sc_base = R + off + NC * int(sizeof(T)) + 8;
+  // the field's band scales, lane b holding band b's (bands <= 64 for L <= 7)
+  static_assert(C::NB <= 64, "band scales in two registers per lane");
+  float sc_lane0 = 0.0f, sc_lane1 = 0.0f;
+  if constexpr (C::QUANT) {
+    const unsigned char* sc_base = R + off + NC * int(sizeof(T)) + 8;
+    if (lane > 0 && lane < C::NB && ((bm >> lane) & 1ull)) sc_lane0 = ldr<float>(sc_base + 4 * band_scale_index(bm, lane));
+    if (lane + 32 < C::NB && ((bm >> (lane + 32)) & 1ull))
+      sc_lane1 = ldr<float>(sc_base + 4 * band_scale_index(bm, lane + 32));
+  }
   unsigned ce = 0u, ci = 0u;
   // lane j holds stored word j: its node, its survivor ranks (one warp scan
   // of both counts), the bits of the region, then its own survivors, so
@@ -347,21 +355,45 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
       ry = cone_bits32(MY, y0);
     }
     unsigned int m = word & (kind == 0 ? rx : (kind == 1 ? ry : (rx & ry)));
-    while (m) {
-      const int b = __ffs(m) - 1;
-      m &= m - 1u;
-      const int kx = rowword ? x0 + b : P, ky = rowword ? y0 : y0 + b;
-      const unsigned int lt = (1u << b) - 1u;
-      T v;
-      if ((em >> b) & 1u) {
-        v = ldr<T>(R + p_edge + int(be + __popc(word & em & lt)) * int(sizeof(T)));
-      } else {
-        const int qi = int(bi + __popc(word & ~em & lt));
+    // every lane runs the same number of rounds (the warp's largest count),
+    // so that the band scales can be fetched from the other lanes; up to
+    // four survivors of a lane per round, their loads issued together
+    const int nb = __popc(m);
+    int rounds = nb;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, o));
+    for (int r0 = 0; r0 < rounds; r0 += 4) {
+      T v[4];
+      int sl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        sl[u] = -1;
+        v[u] = T(0);
+        int band = 0;
+        int b = 0;
+        const bool have = m != 0u;
+        if (have) {
+          b = __ffs(m) - 1;
+          m &= m - 1u;
+        }
+        const int kx = rowword ? x0 + b : P, ky = rowword ? y0 : y0 + b;
+        if constexpr (C::QUANT) band = node_class<L>(kx) * (L + 1) + node_class<L>(ky);
         float scl = 0.0f;
-        if constexpr (C::QUANT) scl = ldr<float>(sc_base + 4 * band_scale_index(bm, node_class<L>(kx) * (L + 1) + node_class<L>(ky)));
-        v = load_interior<T, ST>(R + p_int, qi, wide, scl);
+        if constexpr (C::QUANT) {
+          const float s0 = __shfl_sync(0xffffffffu, sc_lane0, band & 31);
+          const float s1 = __shfl_sync(0xffffffffu, sc_lane1, band & 31);
+          scl = band < 32 ? s0 : s1;
+        }
+        if (have) {
+          const unsigned int lt = (1u << b) - 1u;
+          if ((em >> b) & 1u) v[u] = ldr<T>(R + p_edge + int(be + __popc(word & em & lt)) * int(sizeof(T)));
+          else v[u] = load_interior<T, ST>(R + p_int, int(bi + __popc(word & ~em & lt)), wide, scl);
+          sl[u] = slot(kx, ky);
+        }
       }
-      rg[slot(kx, ky)] = v;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (sl[u] >= 0) rg[sl[u]] = v[u];
     }
   }
   }
@@ -1448,13 +1480,15 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       // band maxima of the kept interior details (the quantiser's scales),
       // from the survivors themselves: a word at a time, lane = node
       __syncwarp();
-      for (int j = 0; j < int(cw); ++j) {
+      for (int j = lane; j < int(cw); j += 32) {  // a lane per kept word, its survivors one by one
         const int w = plist[f * NW + j];
-        const unsigned int word = mw[f * NW + w] & ~word_edges<WV, P, E, C::WR>(w);
-        if ((word >> lane) & 1u) {
+        unsigned int word = mw[f * NW + w] & ~word_edges<WV, P, E, C::WR>(w);
+        while (word) {
+          const int b = __ffs(word) - 1;
+          word &= word - 1u;
           int kx, ky;
           bool valid;
-          word_node<P, E, C::WR>(w, lane, kx, ky, valid);
+          word_node<P, E, C::WR>(w, b, kx, ky, valid);
           const T v = tiles[win_out(f) + ky * PW + kx];
           atomicMax(bmax + f * NB + node_class<L>(kx) * (L + 1) + node_class<L>(ky), __float_as_uint(fabsf(float(v))) + 1u);
         }

@@ -131,30 +131,25 @@ def patch_data(sim, L):
     return feat, eps
 
 
-def fit(X, t, epochs=200, batch=128, lr=2e-3, seed=0):
-    """Trains a network on features X (CUDA tensor (n, nin)) and targets t
-    (log10 eps).  The features are standardised for training (mean 0, unit
-    variance per input, on the device) and the standardisation is folded
-    into the first layer afterwards, so the returned network takes the raw
-    features that a learned-mode step writes.  Returns (Mlp, loss history)."""
+def fit(X, t, epochs=200, batch=128, lr=2e-3, seed=0, sd_floor=1e-3):
+    """Trains a network on raw features X (CUDA tensor (n, nin)) and targets
+    t (log10 eps) in one library call: the library standardises the inputs
+    for training and folds the standardisation into the first layer, so the
+    returned network takes the raw features that a learned-mode step
+    writes.  Only the minibatch permutations are drawn here (seeded).
+    Returns (Mlp, loss history)."""
     import torch
-    X = X.float()
-    mu = X.mean(0)
-    sd = X.std(0).clamp_min(1e-3)
-    Xs = ((X - mu) / sd).contiguous()
-    nin = X.shape[1]
+    X, t = X.float().contiguous(), t.float().contiguous()
+    torch.cuda.synchronize()
+    n, nin = X.shape
     m = Mlp(nin, seed=seed)
-    w = m.weights()
-    w[-1] = float(t.float().mean())  # start at the mean target
-    m.set_weights(w)
-    hist = m.train(Xs, t.float().contiguous(), epochs=epochs, batch=batch, lr=lr, seed=seed)
-    w = m.weights()
-    W1 = w[:NH * nin].reshape(NH, nin).astype(np.float64)
-    b1 = w[NH * nin:NH * nin + NH].astype(np.float64)
-    mu_, sd_ = mu.double().cpu().numpy(), sd.double().cpu().numpy()
-    W1f = W1 / sd_[None, :]
-    b1f = b1 - W1f @ mu_
-    w[:NH * nin] = W1f.reshape(-1).astype(np.float32)
-    w[NH * nin:NH * nin + NH] = b1f.astype(np.float32)
-    m.set_weights(w)
+    nb = n // batch
+    rng = np.random.default_rng(seed)
+    idx = np.concatenate([rng.permutation(n)[:nb * batch] for _ in range(epochs)]).astype(np.int32)
+    hist = np.zeros(epochs, np.float32)
+    stats = np.zeros(2 * (nin + 1), np.float64)
+    B.check(B.lib().wcs_mlp_fit(m.h, X.data_ptr(), t.data_ptr(), n, idx.ctypes.data_as(C.POINTER(C.c_int)), epochs,
+                                batch, lr, sd_floor, hist.ctypes.data_as(C.POINTER(C.c_float)),
+                                stats.ctypes.data_as(C.POINTER(C.c_double))), None)
+    m.input_stats = stats.reshape(nin + 1, 2)  # (mean, deviation) per input, then of t
     return m, hist

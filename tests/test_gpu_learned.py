@@ -105,6 +105,37 @@ def test_mlp_training_fits_and_is_deterministic():
     assert np.array_equal(w, runs[1][3])  # fixed-order reductions: same bits
 
 
+def test_fit_standardises_in_the_library_and_folds_into_the_first_layer():
+    # wcs_mlp_fit against the same trainer run by hand: inputs standardised
+    # in FP64 here, output bias started at the mean target, the fold done
+    # here in FP64.  Columns of very different offsets and scales.
+    import torch
+    rng = np.random.default_rng(8)
+    nin, n, NH = 12, 1024, 64
+    X = (rng.normal(size=(n, nin)) * 10.0 ** np.arange(-3, 3, 0.5) + np.arange(nin) * 7.0).astype(np.float32)
+    t = (np.tanh(X[:, 0] * 1e3) - 0.2 * X[:, 11] / 300 - 4.0).astype(np.float32)
+    Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    m, hist = learned.fit(Xd, td, epochs=6, batch=128, lr=2e-3, seed=2)
+    X64 = X.astype(np.float64)
+    mu, sd = X64.mean(0), X64.std(0, ddof=1)
+    assert np.allclose(m.input_stats[:nin, 0], mu, rtol=1e-12, atol=1e-12 * np.abs(mu).max())
+    assert np.allclose(m.input_stats[:nin, 1], sd, rtol=1e-9)
+    assert abs(m.input_stats[nin, 0] - t.astype(np.float64).mean()) <= 1e-12 * 5
+    h = learned.Mlp(nin, seed=2)
+    w = h.weights()
+    w[-1] = np.float32(t.astype(np.float64).mean())
+    h.set_weights(w)
+    Xs = ((X64 - mu) / np.maximum(sd, 1e-3)).astype(np.float32)
+    hist_h = h.train(torch.from_numpy(Xs).cuda(), td, epochs=6, batch=128, lr=2e-3, seed=2)
+    assert np.allclose(hist, hist_h, rtol=1e-4)
+    w = h.weights().astype(np.float64)
+    W1, b1 = w[:NH * nin].reshape(NH, nin) / np.maximum(sd, 1e-3)[None, :], w[NH * nin:NH * nin + NH]
+    w[:NH * nin], w[NH * nin:NH * nin + NH] = W1.reshape(-1), b1 - W1 @ mu
+    y_fit = m.forward(Xd).cpu().numpy()
+    y_ref = O.mlp_forward(w, X64, nin, NH)
+    assert np.max(np.abs(y_fit - y_ref)) <= 1e-3 * (1 + np.abs(y_ref).max())
+
+
 @pytest.mark.parametrize("case", ["d2q9_bf16", "haar_f64"])
 def test_per_patch_eps_steps_match_oracle_bytewise(case):
     if case == "d2q9_bf16":

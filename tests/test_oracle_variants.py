@@ -45,7 +45,7 @@ def test_cdf97_keeps_constants_and_is_mirror_symmetric():
     coarse = np.arange(P + 1) % (1 << L) == 0
     assert np.max(np.abs(c[coarse] - 2.5)) <= 1e-13
     assert np.max(np.abs(c[~coarse])) <= 1e-13
-    # whole-sample symmetric ends: the transform commutes with reversal
+    # the folded ends treat both sides alike: the transform commutes with reversal
     rng = np.random.default_rng(9)
     u = rng.normal(size=P + 1)
     assert np.max(np.abs(O.dwt(u[::-1], "cdf97", P, L) - O.dwt(u, "cdf97", P, L)[::-1])) <= 1e-13
@@ -86,3 +86,19 @@ def test_e2_count_under_the_pyramid_reading():
     ct = O.dwt(f, "bl53", 128, L)
     count_t = np.count_nonzero(ct[coarse]) + np.count_nonzero(np.abs(ct[~coarse]) >= tau)
     assert count_t == int(meta["nonnull"]) == 481
+
+
+@pytest.mark.parametrize("wavelet", ["bl53", "cdf97"])
+def test_shared_edge_decodes_from_the_edge_line_alone(wavelet):
+    # Two patches share their edge column (Sec. 3.1.1); each decodes it from
+    # its own record, so the decoded edge must depend on the coefficients of
+    # the edge line only (the kept boundary samples of the folded lifting).
+    rng = np.random.default_rng(13)
+    P, L = 64, 4
+    c = rng.normal(size=(P + 1, P + 1))
+    u = O.dwt(c, wavelet, P, L, inverse=True)
+    c2 = rng.normal(size=(P + 1, P + 1))
+    c2[:, P] = c[:, P]  # same edge line x = P, everything else different
+    c2[:, 0] = c[:, 0]
+    u2 = O.dwt(c2, wavelet, P, L, inverse=True)
+    assert np.array_equal(u[:, P], u2[:, P]) and np.array_equal(u[:, 0], u2[:, 0])
