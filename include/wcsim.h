@@ -277,7 +277,14 @@ wcs_status wcs_batch_create(wcs_sim* const* sims, int nsims, wcs_batch** out);
 void wcs_batch_destroy(wcs_batch* b);
 /* Advances every simulation of the batch by n steps (asynchronous). */
 wcs_status wcs_batch_step(wcs_batch* b, int64_t n);
-/* Waits and returns the first device error of any simulation. */
+/* Waits and returns the first device error of any simulation.  Arenas:
+ * a simulation with automatic arenas gets room for its records to double
+ * when the batch is created (the batch holds its arena pointers, so they
+ * are not resized while it steps); one whose records outgrew them all the
+ * same froze at the input of the failed step, and this call re-runs its
+ * lost steps alone with doubled arenas (counted in arena_reruns) and
+ * updates the batch, so that every simulation is at the batch's step
+ * again.  Fixed arenas (arena_factor > 0) report WCS_E_ARENA_FULL. */
 wcs_status wcs_batch_sync(wcs_batch* b);
 /* Kernel launches per step (1 when the batch's two patch sizes run in one
  * merged persistent launch, else one per kind of kernel) and the merged

@@ -1450,8 +1450,51 @@ wcs_status wcs_batch_step(wcs_batch* b, int64_t n) {
   return WCS_OK;
 }
 
+// Catch-up of a simulation with automatic arenas whose records outgrew them
+// inside the batch: it froze at the input of the failed step while the
+// others went on, so it re-runs the lost steps alone with doubled arenas
+// (the recovery of wcs_sync), then gets the batch's growth headroom again.
+static wcs_status batch_regrow(wcs_sim* s) {
+  CK(cudaStreamSynchronize(s->stream));
+  wcs::Ctl c;
+  CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+  if (c.status != wcs::STAT_ARENA_FULL || !s->auto_arena) return WCS_OK;
+  s->in_batch = false;
+  wcs_status st = wcs_sync(s);
+  s->in_batch = true;
+  if (st != WCS_OK) return st;
+  CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+  const int cur = int(s->nstep % 2);
+  const unsigned long long want = arena_headroom(s, 2 * c.cursor[cur]);
+  if (want > s->cap && (st = resize_arenas(s, want, cur, c.cursor[cur])) != WCS_OK) return st;
+  return WCS_OK;
+}
+
 wcs_status wcs_batch_sync(wcs_batch* b) {
   if (!b) return WCS_E_ARG;
+  bool moved = false;
+  for (wcs_sim* s : b->sims) {
+    const void* a0 = s->arena[0];
+    const wcs_status st = batch_regrow(s);
+    if (st != WCS_OK) {
+      b->err = s->err;
+      return st;
+    }
+    moved = moved || s->arena[0] != a0;
+  }
+  if (moved) {  // new arenas: rewrite the argument tables (read by the captured graph at run time)
+    for (auto& g : b->groups) {
+      std::vector<wcs::PatchArgs> args(6 * g.sims.size());
+      for (size_t j = 0; j < g.sims.size(); ++j)
+        for (int ph = 0; ph < 6; ++ph) args[ph * g.sims.size() + j] = step_args(g.sims[j], ph);
+      if (cudaMemcpy(g.args, args.data(), args.size() * sizeof(wcs::PatchArgs), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        b->err = "batch: argument table update failed";
+        return WCS_E_CUDA;
+      }
+    }
+  }
   for (wcs_sim* s : b->sims) {
     const wcs_status st = wcs_sync(s);
     if (st != WCS_OK) {

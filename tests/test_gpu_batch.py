@@ -93,3 +93,30 @@ def test_merged_batch_is_one_launch_per_step_and_matches_the_oracle():
     for g, o in pairs:
         assert np.array_equal(g.export_field(-1), o.export_all())
     b.close()
+
+
+def test_batch_catches_up_after_an_arena_overflow():
+    # automatic arenas, a narrow bump and a tiny eps: the records grow many
+    # times over as the acoustic waves spread, so a simulation outgrows the
+    # room the batch gave it, freezes, and wcs_batch_sync re-runs its lost
+    # steps alone; the records stay those of the oracle, and the batch keeps
+    # stepping with the new arenas
+    specs = [(256, 64, 4), (128, 32, 3)]
+    pairs = []
+    for n, P, L in specs:
+        f = inputs.gaussian_bump(n, amp=0.05, sigma=2.0, center=(0.5 * n, 0.5 * n))
+        g = Sim("d2q9", "bl53", n, n, P, L, 1e-9, prec="f32", store="bf16", tau=0.6)
+        o = O.OracleSim("d2q9", "bl53", n, n, P, L, 1e-9, prec="f32", store="bf16", tau=0.6)
+        g.init_macro(f)
+        o.init_macro(f)
+        pairs.append((g, o))
+    b = Batch([g for g, _ in pairs])
+    for chunk in (60, 12):
+        b.step(chunk)
+        b.sync()
+        for g, o in pairs:
+            o.step(chunk)
+            for p in range(g.npatch):
+                assert g.record(p) == o.record(p)
+    assert sum(g.stats()["arena_reruns"] for g, _ in pairs) > 0
+    b.close()
