@@ -439,93 +439,137 @@ __device__ inline float gelu_grad(float x) {
   return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
-__device__ float mlp_fwd(const float* __restrict__ w, int nin, const float* x, float* p1, float* p2) {
-  const float* W1 = w;
-  const float* b1 = W1 + MLP_NH * nin;
-  const float* W2 = b1 + MLP_NH;
-  const float* b2 = W2 + MLP_NH * MLP_NH;
-  const float* W3 = b2 + MLP_NH;
-  const float* b3 = W3 + MLP_NH;
-  float a1[MLP_NH];
-  for (int j = 0; j < MLP_NH; ++j) {
-    float s = b1[j];
-    for (int i = 0; i < nin; ++i) s += W1[j * nin + i] * x[i];
-    p1[j] = s;
-    a1[j] = gelu(s);
+// Block per slice of a minibatch: CTA b takes samples [b S, b S + S) (S =
+// MLP_SPB), stages the weights, the inputs and every activation of its
+// samples in shared memory, and writes its partial gradient (the sum over
+// its samples, in sample order) to gpart[b][p] and its summed squared error
+// to lpart[b].  Per sample: z1 = b1 + W1 x and z2 = b2 + W2 gelu(z1) (sums
+// in input order), y = b3 + W3 gelu(z2), error r = y - t, loss r^2,
+// dy = 2 r / B, d2 = dy W3 gelu'(z2), d1 = (W2^T d2) gelu'(z1); the
+// gradients are the outer products of these with the layer inputs.
+// Threads take (sample, unit) pairs in the forward pass and parameters in
+// the backward pass.
+constexpr int MLP_SPB = 16;
+__host__ __device__ inline size_t block_grads_smem(int nin) {
+  return (size_t(nparam(nin)) + size_t(MLP_SPB) * (nin + 5 * MLP_NH + 2)) * 4;
+}
+__global__ void __launch_bounds__(256) mlp_block_grads(const float* __restrict__ w, int nin,
+                                                       const float* __restrict__ X, const float* __restrict__ t,
+                                                       const int* __restrict__ idx, int B, float* __restrict__ gpart,
+                                                       float* __restrict__ lpart) {
+  extern __shared__ float msm[];
+  constexpr int S = MLP_SPB, H = MLP_NH;
+  const int np = nparam(nin), tid = threadIdx.x, NT = blockDim.x;
+  const int s0 = blockIdx.x * S, ns = min(S, B - s0);
+  float* W = msm;
+  float* x = W + np;
+  float* z1 = x + S * nin;
+  float* a1 = z1 + S * H;
+  float* z2 = a1 + S * H;
+  float* d2 = z2 + S * H;
+  float* d1 = d2 + S * H;
+  float* dy = d1 + S * H;
+  float* ls = dy + S;
+  const float* W1 = W;
+  const float* b1 = W1 + H * nin;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + H * H;
+  const float* W3 = b2 + H;
+  const float* b3 = W3 + H;
+  for (int p = tid; p < np; p += NT) W[p] = w[p];
+  for (int q = tid; q < ns * nin; q += NT) {
+    const int sl = q / nin, i = q - sl * nin, g = s0 + sl;
+    x[q] = X[size_t(idx ? idx[g] : g) * nin + i];
   }
-  float y = b3[0];
-  for (int j = 0; j < MLP_NH; ++j) {
-    float s = b2[j];
-    for (int i = 0; i < MLP_NH; ++i) s += W2[j * MLP_NH + i] * a1[i];
-    p2[j] = s;
-    y += W3[j] * gelu(s);
+  __syncthreads();
+  for (int q = tid; q < ns * H; q += NT) {  // first layer
+    const int sl = q / H, j = q - sl * H;
+    float a = b1[j];
+    for (int i = 0; i < nin; ++i) a += W1[j * nin + i] * x[sl * nin + i];
+    z1[q] = a;
+    a1[q] = gelu(a);
   }
-  return y;
+  __syncthreads();
+  for (int q = tid; q < ns * H; q += NT) {  // second layer
+    const int sl = q / H, j = q - sl * H;
+    float a = b2[j];
+    for (int i = 0; i < H; ++i) a += W2[j * H + i] * a1[sl * H + i];
+    z2[q] = a;
+  }
+  __syncthreads();
+  if (tid < ns) {  // output, error and its derivative
+    float y = b3[0];
+    for (int j = 0; j < H; ++j) y += W3[j] * gelu(z2[tid * H + j]);
+    const int g = s0 + tid;
+    const float r = y - t[idx ? idx[g] : g];
+    ls[tid] = r * r;
+    dy[tid] = 2.0f * r / float(B);
+  }
+  __syncthreads();
+  for (int q = tid; q < ns * H; q += NT) {
+    const int sl = q / H, j = q - sl * H;
+    d2[q] = dy[sl] * W3[j] * gelu_grad(z2[q]);
+  }
+  __syncthreads();
+  for (int q = tid; q < ns * H; q += NT) {
+    const int sl = q / H, i = q - sl * H;
+    float a = 0.0f;
+    for (int j = 0; j < H; ++j) a += d2[sl * H + j] * W2[j * H + i];
+    d1[q] = a * gelu_grad(z1[q]);
+  }
+  __syncthreads();
+  float* gp = gpart + size_t(blockIdx.x) * np;
+  for (int p = tid; p < np; p += NT) {  // every parameter: its sum over the slice's samples
+    float a = 0.0f;
+    if (p < H * nin) {
+      const int j = p / nin, k = p - j * nin;
+      for (int sl = 0; sl < ns; ++sl) a += d1[sl * H + j] * x[sl * nin + k];
+    } else if (p < H * nin + H) {
+      const int j = p - H * nin;
+      for (int sl = 0; sl < ns; ++sl) a += d1[sl * H + j];
+    } else if (p < H * nin + H + H * H) {
+      const int r = p - H * nin - H, j = r / H, i = r - j * H;
+      for (int sl = 0; sl < ns; ++sl) a += d2[sl * H + j] * a1[sl * H + i];
+    } else if (p < H * nin + 2 * H + H * H) {
+      const int j = p - H * nin - H - H * H;
+      for (int sl = 0; sl < ns; ++sl) a += d2[sl * H + j];
+    } else if (p < np - 1) {
+      const int j = p - H * nin - 2 * H - H * H;
+      for (int sl = 0; sl < ns; ++sl) a += dy[sl] * gelu(z2[sl * H + j]);
+    } else {
+      for (int sl = 0; sl < ns; ++sl) a += dy[sl];
+    }
+    gp[p] = a;
+  }
+  if (tid == 0) {
+    float a = 0.0f;
+    for (int sl = 0; sl < ns; ++sl) a += ls[sl];
+    lpart[blockIdx.x] = a;
+  }
 }
 
-// thread per sample: forward, backward of 0.5-free MSE, per-sample gradient
-__global__ void mlp_sample_grads(const float* __restrict__ w, int nin, const float* __restrict__ X,
-                                 const float* __restrict__ t, const int* __restrict__ idx, int B, float* gs, float* ls) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= B) return;
-  const int np = nparam(nin);
-  const float* x = X + size_t(idx ? idx[s] : s) * nin;
-  float p1[MLP_NH], p2[MLP_NH];
-  const float y = mlp_fwd(w, nin, x, p1, p2);
-  const float r = y - t[idx ? idx[s] : s];
-  ls[s] = r * r;
-  const float dy = 2.0f * r / float(B);
-  const float* W2 = w + MLP_NH * nin + MLP_NH;
-  const float* W3 = W2 + MLP_NH * MLP_NH + MLP_NH;
-  float* g = gs + size_t(s) * np;
-  float* gW1 = g;
-  float* gb1 = gW1 + MLP_NH * nin;
-  float* gW2 = gb1 + MLP_NH;
-  float* gb2 = gW2 + MLP_NH * MLP_NH;
-  float* gW3 = gb2 + MLP_NH;
-  float* gb3 = gW3 + MLP_NH;
-  gb3[0] = dy;
-  float d2[MLP_NH], a1[MLP_NH];
-  for (int j = 0; j < MLP_NH; ++j) {
-    gW3[j] = dy * gelu(p2[j]);
-    d2[j] = dy * W3[j] * gelu_grad(p2[j]);
-    gb2[j] = d2[j];
-    a1[j] = gelu(p1[j]);
-  }
-  for (int j = 0; j < MLP_NH; ++j)
-    for (int i = 0; i < MLP_NH; ++i) gW2[j * MLP_NH + i] = d2[j] * a1[i];
-  for (int i = 0; i < MLP_NH; ++i) {
-    float d1 = 0.0f;
-    for (int j = 0; j < MLP_NH; ++j) d1 += d2[j] * W2[j * MLP_NH + i];
-    const float d = d1 * gelu_grad(p1[i]);
-    gb1[i] = d;
-    for (int k = 0; k < nin; ++k) gW1[i * nin + k] = d * x[k];
-  }
-}
-
-// thread per parameter: sum over samples in order
-__global__ void mlp_reduce(const float* __restrict__ gs, int B, int np, float* g, const float* ls, float* loss) {
+// Sum of the G partial gradients in block order (thread per parameter),
+// then, if adam, the Adam update of that parameter in the same thread.
+__global__ void mlp_reduce_partials(const float* __restrict__ gpart, int G, int np, int B, const float* lpart,
+                                    float* g, float* loss, bool adam, float* w, float* m1, float* m2, float lr,
+                                    float b1, float b2, float b1t, float b2t) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < np) {
     float a = 0.0f;
-    for (int s = 0; s < B; ++s) a += gs[size_t(s) * np + p];
+    for (int b = 0; b < G; ++b) a += gpart[size_t(b) * np + p];
     g[p] = a;
+    if (adam) {
+      m1[p] = b1 * m1[p] + (1.0f - b1) * a;
+      m2[p] = b2 * m2[p] + (1.0f - b2) * a * a;
+      const float mh = m1[p] / (1.0f - b1t), vh = m2[p] / (1.0f - b2t);
+      w[p] -= lr * mh / (sqrtf(vh) + 1e-8f);
+    }
   }
   if (p == 0) {
     float a = 0.0f;
-    for (int s = 0; s < B; ++s) a += ls[s];
+    for (int b = 0; b < G; ++b) a += lpart[b];
     *loss = a / float(B);
   }
-}
-
-__global__ void mlp_adam(float* w, const float* g, float* m1, float* m2, int np, float lr, float b1, float b2, float b1t,
-                         float b2t) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= np) return;
-  m1[p] = b1 * m1[p] + (1.0f - b1) * g[p];
-  m2[p] = b2 * m2[p] + (1.0f - b2) * g[p] * g[p];
-  const float mh = m1[p] / (1.0f - b1t), vh = m2[p] / (1.0f - b2t);
-  w[p] -= lr * mh / (sqrtf(vh) + 1e-8f);
 }
 
 // Per-column mean and sample deviation of X (n x ncol, row-major) in FP64,
@@ -775,20 +819,25 @@ wcs_status wcs_mlp_get_weights(const wcs_mlp* m, float* w_host) {
 // and t [n]); gradient to host.
 wcs_status wcs_mlp_grad(wcs_mlp* m, const float* X_dev, const float* t_dev, int n, float* grad_host, float* loss_host) {
   if (!m || !X_dev || !t_dev || n <= 0) return WCS_E_ARG;
-  const int np = nparam(m->nin);
-  float *gs = nullptr, *ls = nullptr;
-  if (cudaMalloc(&gs, size_t(n) * np * 4) != cudaSuccess || cudaMalloc(&ls, size_t(n) * 4) != cudaSuccess) {
+  const int np = nparam(m->nin), G = (n + MLP_SPB - 1) / MLP_SPB;
+  float *gp = nullptr, *lp = nullptr;
+  if (cudaMalloc(&gp, size_t(G) * np * 4) != cudaSuccess || cudaMalloc(&lp, size_t(G) * 4) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(gs);
+    cudaFree(gp);
     return WCS_E_OOM;
   }
-  mlp_sample_grads<<<(n + 127) / 128, 128>>>(m->w, m->nin, X_dev, t_dev, nullptr, n, gs, ls);
-  mlp_reduce<<<(np + 255) / 256, 256>>>(gs, n, np, m->g, ls, m->loss);
-  cudaError_t e = cudaDeviceSynchronize();
+  const size_t sm = block_grads_smem(m->nin);
+  cudaError_t e = cudaFuncSetAttribute(mlp_block_grads, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  if (e == cudaSuccess) {
+    mlp_block_grads<<<G, 256, sm>>>(m->w, m->nin, X_dev, t_dev, nullptr, n, gp, lp);
+    mlp_reduce_partials<<<(np + 255) / 256, 256>>>(gp, G, np, n, lp, m->g, m->loss, false, nullptr, nullptr, nullptr,
+                                                   0.f, 0.f, 0.f, 0.f, 0.f);
+    e = cudaDeviceSynchronize();
+  }
   if (e == cudaSuccess && grad_host) e = cudaMemcpy(grad_host, m->g, np * 4, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && loss_host) e = cudaMemcpy(loss_host, m->loss, 4, cudaMemcpyDeviceToHost);
-  cudaFree(gs);
-  cudaFree(ls);
+  cudaFree(gp);
+  cudaFree(lp);
   return e == cudaSuccess ? WCS_OK : WCS_E_CUDA;
 }
 
@@ -798,26 +847,26 @@ wcs_status wcs_mlp_train(wcs_mlp* m, const float* X_dev, const float* t_dev, int
                          int batch, float lr, float* loss_history_host) {
   if (!m || !X_dev || !t_dev || n <= 0 || batch <= 0 || batch > n || epochs <= 0 || !batches_host) return WCS_E_ARG;
   const int np = nparam(m->nin);
-  const int nb = n / batch;
-  float *gs = nullptr, *ls = nullptr;
+  const int nb = n / batch, G = (batch + MLP_SPB - 1) / MLP_SPB;
+  float *gp = nullptr, *lp = nullptr;
   int* idx = nullptr;
-  if (cudaMalloc(&gs, size_t(batch) * np * 4) != cudaSuccess || cudaMalloc(&ls, size_t(batch) * 4) != cudaSuccess ||
+  if (cudaMalloc(&gp, size_t(G) * np * 4) != cudaSuccess || cudaMalloc(&lp, size_t(G) * 4) != cudaSuccess ||
       cudaMalloc(&idx, size_t(epochs) * nb * batch * 4) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(gs);
-    cudaFree(ls);
+    cudaFree(gp);
+    cudaFree(lp);
     return WCS_E_OOM;
   }
   cudaError_t e = cudaMemcpy(idx, batches_host, size_t(epochs) * nb * batch * 4, cudaMemcpyHostToDevice);
+  const size_t sm = block_grads_smem(m->nin);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(mlp_block_grads, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   const float b1 = 0.9f, b2 = 0.999f;
   for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
     for (int b = 0; b < nb && e == cudaSuccess; ++b) {
-      mlp_sample_grads<<<(batch + 127) / 128, 128>>>(m->w, m->nin, X_dev, t_dev, idx + (size_t(ep) * nb + b) * batch,
-                                                     batch, gs, ls);
-      mlp_reduce<<<(np + 255) / 256, 256>>>(gs, batch, np, m->g, ls, m->loss);
+      mlp_block_grads<<<G, 256, sm>>>(m->w, m->nin, X_dev, t_dev, idx + (size_t(ep) * nb + b) * batch, batch, gp, lp);
       ++m->adam_t;
-      mlp_adam<<<(np + 255) / 256, 256>>>(m->w, m->g, m->m1, m->m2, np, lr, b1, b2, powf(b1, float(m->adam_t)),
-                                          powf(b2, float(m->adam_t)));
+      mlp_reduce_partials<<<(np + 255) / 256, 256>>>(gp, G, np, batch, lp, m->g, m->loss, true, m->w, m->m1, m->m2, lr,
+                                                     b1, b2, powf(b1, float(m->adam_t)), powf(b2, float(m->adam_t)));
       e = cudaGetLastError();
     }
     if (e == cudaSuccess && loss_history_host) e = cudaMemcpy(loss_history_host + ep, m->loss, 4, cudaMemcpyDeviceToHost);
@@ -828,8 +877,8 @@ wcs_status wcs_mlp_train(wcs_mlp* m, const float* X_dev, const float* t_dev, int
     e = cudaMemcpy(w.data(), m->w, np * 4, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = upload_kernel_layout(m, w.data());
   }
-  cudaFree(gs);
-  cudaFree(ls);
+  cudaFree(gp);
+  cudaFree(lp);
   cudaFree(idx);
   return e == cudaSuccess ? WCS_OK : WCS_E_CUDA;
 }
