@@ -92,9 +92,12 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   static constexpr bool QUANT = ST == ST_BF16 || ST == ST_I8;
   typedef typename StoreType<ST>::type S;
   static constexpr int SB = sizeof(S);
-  // D2Q9 on BL5/3 patches reads its ghosts from the neighbours' records
-  // (ring-free); the other kernels keep a ghost ring
-  static constexpr bool RINGFREE = SCH == SCH_D2Q9 && WV == WV_BL53;
+  // BL5/3 patches read their ghosts from the neighbours' records
+  // (ring-free); Haar and CDF 9/7 patches keep a ghost ring
+  static constexpr bool RINGFREE = WV == WV_BL53;
+  // the new state is decoded again inside the step: for a ring, or for the
+  // largest signal speed that sets the next dt (Euler, shallow water)
+  static constexpr bool REDECODE = !RINGFREE || SCH == SCH_EULER2D || SCH == SCH_SWE;
   static constexpr int RING = RINGFREE ? 0 : (SCH == SCH_D2Q9 ? 12 * E + 4 : 4 * F * E);
   static constexpr int NT = sizeof(T) == 8 ? 512 : 768;
   static constexpr int NWARP = NT / 32;
@@ -273,12 +276,12 @@ __device__ __forceinline__ void collide_nodes(T* tiles, int t0, int t1, int dt, 
 // both (rg[iy NCN + ix]).  One warp: present words with their survivor
 // ranks 32 at a time, then their surviving nodes one word at a time (the
 // coarse block: ringfree_coarse_at).  Out of line: three stages call it.
-template <int WV, typename T, int ST, int P, int L>
+template <int WV, typename T, int ST, int P, int L, int SCH = SCH_D2Q9>
 __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, const int* nbi, int n, int f, T* rg, int kind,
                                               ConeMask MX, ConeMask MY) {
-  typedef Cfg<SCH_D2Q9, WV, T, ST, P, L> C;
+  typedef Cfg<SCH, WV, T, ST, P, L> C;
   typedef typename C::S S;
-  constexpr int F = 9, E = C::E, NC = C::NC, NPW = C::NPW;
+  constexpr int F = C::F, E = C::E, NC = C::NC, NPW = C::NPW;
   constexpr int NCN = cone_count(cone_mask<P, L>(P - 1));
   const int lane = threadIdx.x & 31;
     const int* e = nbi + 8 * (n * F + f);
@@ -402,11 +405,11 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
 // (kind and masks as in ringfree_scatter): its address in the record (src)
 // and its slot in the region (dst).  One thread per value: a stage issues
 // all its coarse loads before any store.
-template <int WV, typename T, int ST, int P, int L>
+template <int WV, typename T, int ST, int P, int L, int SCH = SCH_D2Q9>
 __device__ __forceinline__ bool ringfree_coarse_at(const unsigned char* arena_in, const int* nbi, int n, int f, T* rg,
                                                    int kind, ConeMask MX, ConeMask MY, int c, const T*& src, T*& dst) {
-  typedef Cfg<SCH_D2Q9, WV, T, ST, P, L> C;
-  constexpr int F = 9, E = C::E;
+  typedef Cfg<SCH, WV, T, ST, P, L> C;
+  constexpr int F = C::F, E = C::E;
   constexpr int NCN = cone_count(cone_mask<P, L>(P - 1));
   const int iy = c / C::NC1, ix = c - iy * C::NC1, kx = ix << L, ky = iy << L;
   const bool in = kind == 0 ? cone_has(MX, kx) : (kind == 1 ? cone_has(MY, ky) : (cone_has(MX, kx) && cone_has(MY, ky)));
@@ -738,6 +741,125 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
 }
 
 // The whole patch step for patch `pid` of the simulation described by `a`.
+// Ghosts of an FV patch without a ring: the four lines beside its shared
+// borders, all F fields, decoded from the neighbours' records of the
+// current state (the west neighbour's node column P-1, the east one's 1,
+// the south one's row P-1, the north one's 1), by the cone decode of
+// ringfree_ghosts without the collision: west and east first (the cone
+// columns inverse transformed along y, then the restricted inverse along x
+// per row), then south and north (the restricted inverse along y per
+// column, then the one row along x).  The four-normal stencil needs no
+// corners.  An outflow border copies the patch's own boundary node.
+template <int SCH, int WV, typename T, int ST, int P, int L>
+__device__ void ringfree_ghosts_fv(const PatchArgs& a, int px, int py, T* tiles, T* reg, const int* nbi) {
+  typedef Cfg<SCH, WV, T, ST, P, L> C;
+  constexpr int F = C::F, E = C::E, PW = C::PW, TS = C::TS, NT = C::NT, NWARP = C::NWARP;
+  constexpr ConeMask CH = cone_mask<P, L>(P - 1), CL = cone_mask<P, L>(1);
+  constexpr int NCN = cone_count(CH);
+  static_assert(cone_count(CL) == NCN, "the two border cones mirror each other");
+  static_assert(size_t(2) * F * NCN * E * sizeof(T) <= C::STG, "ghost regions fit in the staging area");
+  constexpr int IH = cone_index_c(CH, P - 1), IL = cone_index_c(CL, 1);
+  constexpr int NCQ = cone_coarse_count<P, L>(CH);
+  static_assert(cone_coarse_ends<P, L>(CH, CL, NCQ), "border cones hold the end coarse nodes");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  (void)lane;
+  auto qh = [](int j) { return P - (NCQ - 1 - j) * (1 << L); };
+  auto ql = [](int j) { return j * (1 << L); };
+  auto coarse_val = [&](int n, int f, int c) -> T {
+    const int* e = nbi + 8 * (n * F + f);
+    const unsigned char* R =
+        a.arena_in + ((unsigned long long)(unsigned int)e[0] | ((unsigned long long)(unsigned int)e[1] << 32));
+    return __ldg(reinterpret_cast<const T*>(R + e[2] + c * int(sizeof(T))));
+  };
+  auto words = [&](int n, int f) { return nbi[8 * (n * F + f) + 3]; };
+  auto zero = [&](T* p, int n) {
+    const int n4 = int(n * sizeof(T) / 16);
+    for (int i = tid; i < n4; i += NT) reinterpret_cast<uint4*>(p)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = n4 * int(16 / sizeof(T)) + tid; i < n; i += NT) p[i] = T(0);
+  };
+  auto coarse_ix = [&](int sd, int ix) {
+    bool c = false;
+#pragma unroll
+    for (int j = 0; j < NCQ; ++j) c = c || ix == (sd == 0 ? cone_index(CH, qh(j)) : cone_index(CL, ql(j)));
+    return c;
+  };
+  const bool hasW = a.per_x || px > 0, hasE = a.per_x || px < a.npx - 1;
+  const bool hasS = a.per_y || py > 0, hasN = a.per_y || py < a.npy - 1;
+  static_assert(2 * F * NCN <= NT, "one cone column per thread");
+  // ---- west (neighbour 3, its node P-1 of every row) and east (4, node 1)
+  zero(reg, 2 * F * NCN * E);
+  __syncthreads();
+  for (int i = tid; i < 2 * F * NCQ * C::NC1; i += NT) {  // the coarse nodes of the cone columns
+    const int task = i / (NCQ * C::NC1), r = i - task * NCQ * C::NC1, jx = r / C::NC1, iy = r - jx * C::NC1;
+    const int sd = task / F, f = task - sd * F, kx = sd == 0 ? qh(jx) : ql(jx);
+    reg[(sd * F + f) * NCN * E + (sd == 0 ? cone_index(CH, kx) : cone_index(CL, kx)) * E + (iy << L)] =
+        coarse_val(sd == 0 ? 3 : 4, f, iy * C::NC1 + (kx >> L));
+  }
+  for (int task = warp; task < 2 * F; task += NWARP) {
+    const int sd = task / F, f = task - sd * F;
+    if (words(sd == 0 ? 3 : 4, f) != 0)
+      ringfree_scatter<WV, T, ST, P, L, SCH>(a.arena_in, nbi, sd == 0 ? 3 : 4, f, reg + (sd * F + f) * NCN * E, 0,
+                                             sd == 0 ? CH : CL, CH);
+  }
+  __syncthreads();
+  if (tid < 2 * F * NCN) {  // cone columns along y (the others hold zeros only)
+    const int task = tid / NCN, ix = tid - task * NCN, sd = task / F, f = task - sd * F;
+    if (coarse_ix(sd, ix) || words(sd == 0 ? 3 : 4, f) != 0)
+      line_transform<WV, P, L, true, T>(reg + (task * NCN + ix) * E, 1);
+  }
+  __syncthreads();
+  for (int t = tid; t < F * E; t += NT) {  // across the columns, row by row
+    const int f = t / E, y = t - f * E;
+    cone_inverse<P, L, P - 1, T>(reg + f * NCN * E, E, y);
+    cone_inverse<P, L, 1, T>(reg + (F + f) * NCN * E, E, y);
+  }
+  __syncthreads();
+  for (int t = tid; t < F * E; t += NT) {
+    const int q = t / E, y = t - q * E;
+    const int b = q * TS + PW + 1 + y * PW;  // node (0, y) of field q's input tile
+    const T w = hasW ? reg[q * NCN * E + IH * E + y] : tiles[b];
+    const T e = hasE ? reg[(F + q) * NCN * E + IL * E + y] : tiles[b + E - 1];
+    tiles[b - 1] = w;
+    tiles[b + E] = e;
+  }
+  __syncthreads();
+  // ---- south (neighbour 1, its row P-1) and north (6, row 1)
+  zero(reg, 2 * F * NCN * E);
+  __syncthreads();
+  for (int i = tid; i < 2 * F * NCQ * C::NC1; i += NT) {  // the coarse nodes of the cone rows
+    const int task = i / (NCQ * C::NC1), r = i - task * NCQ * C::NC1, jy = r / C::NC1, ix = r - jy * C::NC1;
+    const int sd = task / F, f = task - sd * F, ky = sd == 0 ? qh(jy) : ql(jy);
+    reg[(sd * F + f) * NCN * E + (sd == 0 ? cone_index(CH, ky) : cone_index(CL, ky)) * E + (ix << L)] =
+        coarse_val(sd == 0 ? 1 : 6, f, (ky >> L) * C::NC1 + ix);
+  }
+  for (int task = warp; task < 2 * F; task += NWARP) {
+    const int sd = task / F, f = task - sd * F;
+    if (words(sd == 0 ? 1 : 6, f) != 0)
+      ringfree_scatter<WV, T, ST, P, L, SCH>(a.arena_in, nbi, sd == 0 ? 1 : 6, f, reg + (sd * F + f) * NCN * E, 1, CH,
+                                             sd == 0 ? CH : CL);
+  }
+  __syncthreads();
+  for (int t = tid; t < F * E; t += NT) {  // across the rows, column by column
+    const int f = t / E, x = t - f * E;
+    cone_inverse<P, L, P - 1, T>(reg + f * NCN * E, E, x);
+    cone_inverse<P, L, 1, T>(reg + (F + f) * NCN * E, E, x);
+  }
+  __syncthreads();
+  if (tid < 2 * F) {  // the one row along x
+    const int sd = tid / F, f = tid - sd * F;
+    line_transform<WV, P, L, true, T>(reg + (sd * F + f) * NCN * E + (sd == 0 ? IH : IL) * E, 1);
+  }
+  __syncthreads();
+  for (int t = tid; t < F * E; t += NT) {
+    const int q = t / E, x = t - q * E;
+    const int b = q * TS + PW + 1 + x;  // node (x, 0) of field q's input tile
+    const T s = hasS ? reg[q * NCN * E + IH * E + x] : tiles[b];
+    const T n = hasN ? reg[(F + q) * NCN * E + IL * E + x] : tiles[b + (E - 1) * PW];
+    tiles[b - PW] = s;
+    tiles[b + E * PW] = n;
+  }
+}
+
 template <int SCH, int WV, typename T, int ST, int P, int L, int MODE, int FEAT = 0>
 __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
@@ -1135,8 +1257,8 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   }
 
   // -------------------------------------------------------- ghosts + scheme
-  if constexpr (MODE == MODE_STEP) {
-    // BGK collision of own nodes t0, t0 + dt, ... < t1, in place (D2Q9)
+  if constexpr (MODE == MODE_STEP && SCH == SCH_D2Q9) {
+    // BGK collision of own nodes t0, t0 + dt, ... < t1, in place
     auto collide_range = [&](int t0, int t1, int dt) { collide_nodes<T, E, PW, TS>(tiles, t0, t1, dt, omega); };
     int collided = 0;
     if constexpr (RF) {
@@ -1147,43 +1269,54 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       for (int g = 0; g < NG; ++g)
         if (gdst[g] >= 0) tiles[gdst[g]] = gsrc[g] >= 0 ? tiles[gsrc[g]] : gv[g];
     }
-    if constexpr (SCH == SCH_D2Q9) {
-      collide_range(collided + tid, E * E, NT);
-      __syncthreads();
-    } else {
-      __syncthreads();
-      // dt/h = CFL / max signal speed, formed in FP64 once per block
-      T* lam_sm = reinterpret_cast<T*>(misc + 48);
-      if (tid == 0)  // cfl < 0: fixed step dt/h = -cfl
-        *lam_sm = T(a.cfl > 0 ? a.cfl / __longlong_as_double((long long)a.ctl->smax[a.smax_rd]) : -a.cfl);
-      __syncthreads();
+    collide_range(collided + tid, E * E, NT);
+    __syncthreads();
+  } else if constexpr (MODE == MODE_STEP) {
+    // dt/h = CFL / max signal speed, formed in FP64 once per block (cfl < 0:
+    // fixed step dt/h = -cfl); read after the next block barrier
+    T* lam_sm = reinterpret_cast<T*>(misc + 48);
+    if (tid == 0)
+      *lam_sm = T(a.cfl > 0 ? a.cfl / __longlong_as_double((long long)a.ctl->smax[a.smax_rd]) : -a.cfl);
+    // the update of node t (y = t / E, x = t % E) from the input tiles
+    auto fv_node = [&](int t) {
       const T lam = *lam_sm;
-      for (int t = tid; t < E * E; t += NT) {
-        const int y = t / E, x = t - y * E;
-        T W0[F], acc[F];
+      const int y = t / E, x = t - y * E;
+      T W0[F], acc[F];
 #pragma unroll
-        for (int q = 0; q < F; ++q) W0[q] = tiles[win_in(q) + y * PW + x];
+      for (int q = 0; q < F; ++q) W0[q] = tiles[win_in(q) + y * PW + x];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int nx = k == 0 ? 1 : (k == 1 ? -1 : 0), ny = k == 2 ? 1 : (k == 3 ? -1 : 0);
-          T Wn[F], Fl[F];
+      for (int k = 0; k < 4; ++k) {
+        const int nx = k == 0 ? 1 : (k == 1 ? -1 : 0), ny = k == 2 ? 1 : (k == 3 ? -1 : 0);
+        T Wn[F], Fl[F];
 #pragma unroll
-          for (int q = 0; q < F; ++q) Wn[q] = tiles[win_in(q) + (y + ny) * PW + (x + nx)];
-          if constexpr (SCH == SCH_EULER2D) {
-            euler_rusanov<T>(W0, Wn, T(nx), T(ny), gm1, gamma, Fl);
-          } else if constexpr (SCH == SCH_SWE) {
-            sw_godunov<T>(W0, Wn, T(nx), T(ny), grav, Fl);
-          } else {  // transport: a.N = alpha, -alpha, beta, -beta
-            Fl[0] = transport_flux<T>(W0[0], Wn[0], k == 0 ? alpha : (k == 1 ? -alpha : (k == 2 ? beta : -beta)));
-          }
-#pragma unroll
-          for (int q = 0; q < F; ++q) acc[q] = k == 0 ? Fl[q] : acc[q] + Fl[q];
+        for (int q = 0; q < F; ++q) Wn[q] = tiles[win_in(q) + (y + ny) * PW + (x + nx)];
+        if constexpr (SCH == SCH_EULER2D) {
+          euler_rusanov<T>(W0, Wn, T(nx), T(ny), gm1, gamma, Fl);
+        } else if constexpr (SCH == SCH_SWE) {
+          sw_godunov<T>(W0, Wn, T(nx), T(ny), grav, Fl);
+        } else {  // transport: a.N = alpha, -alpha, beta, -beta
+          Fl[0] = transport_flux<T>(W0[0], Wn[0], k == 0 ? alpha : (k == 1 ? -alpha : (k == 2 ? beta : -beta)));
         }
 #pragma unroll
-        for (int q = 0; q < F; ++q) tiles[win_out(q) + y * PW + x] = W0[q] - lam * acc[q];
+        for (int q = 0; q < F; ++q) acc[q] = k == 0 ? Fl[q] : acc[q] + Fl[q];
       }
-      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < F; ++q) tiles[win_out(q) + y * PW + x] = W0[q] - lam * acc[q];
+    };
+    if constexpr (RF) {
+      ringfree_ghosts_fv<SCH, WV, T, ST, P, L>(a, px, py, tiles, reinterpret_cast<T*>(stage),
+                                               reinterpret_cast<const int*>(smem + C::OFF_NBI));
+    } else {
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+        if (gdst[g] >= 0) tiles[gdst[g]] = gsrc[g] >= 0 ? tiles[gsrc[g]] : gv[g];
     }
+    __syncthreads();
+    // (running the interior nodes' updates in the warps that the ghost
+    // stages leave idle was measured slower: the flux code, inlined at
+    // three sites, no longer fits the instruction cache)
+    for (int t = tid; t < E * E; t += NT) fv_node(t);
+    __syncthreads();
   }
 
   // ------------------------------------------------------------ init state
@@ -1245,9 +1378,9 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   float cf2[L + 1], cfm[L + 1];  // the column warp's lane (its field): group (cy, y)
 #pragma unroll
   for (int c = 0; c <= L; ++c) { cf2[c] = 0.0f; cfm[c] = 0.0f; }
-  // Ring-free kernels read back only the kept and the coarse coefficients
-  // (no re-decode), so the zeroed details are not written to the tiles.
-  constexpr bool STORE_ALL = !C::RINGFREE;
+  // Kernels that do not decode the new state again read back only the kept
+  // and the coarse coefficients, so the zeroed details are not written.
+  constexpr bool STORE_ALL = C::REDECODE;
   if (warp < F * C::WR) {
     const int f = warp / C::WR, h = warp - f * C::WR;
     const int x = 32 * h + lane;
@@ -1710,8 +1843,10 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     }
   }
   // --------------------------- re-decode: the state the neighbours will see
-  // (ring-free kernels: the neighbours decode it themselves next step)
-  if constexpr (RF) return;
+  // (ring-free kernels: the neighbours decode it themselves next step; the
+  // ring-free Euler and shallow-water kernels still need its largest
+  // signal speed)
+  if constexpr (!C::REDECODE) return;
   __syncthreads();
   for (int t = tid; t < F * E; t += NT) {
     const int f = t / E, x = t - f * E;
@@ -1755,13 +1890,14 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       }
     }
   } else {
-    for (int t = tid; t < 4 * E; t += NT) {
-      const int s = t / E, k = t - s * E;
-      const int x = s == 0 ? C::XLO : (s == 1 ? C::XHI : k);
-      const int y = s == 2 ? C::XLO : (s == 3 ? C::XHI : k);
+    if constexpr (!RF)
+      for (int t = tid; t < 4 * E; t += NT) {
+        const int s = t / E, k = t - s * E;
+        const int x = s == 0 ? C::XLO : (s == 1 ? C::XHI : k);
+        const int y = s == 2 ? C::XLO : (s == 3 ? C::XHI : k);
 #pragma unroll
-      for (int q = 0; q < F; ++q) rout[s * F * E + F * k + q] = tiles[win_out(q) + y * PW + x];
-    }
+        for (int q = 0; q < F; ++q) rout[s * F * E + F * k + q] = tiles[win_out(q) + y * PW + x];
+      }
     if constexpr (SCH == SCH_EULER2D || SCH == SCH_SWE) {
       // largest signal speed of the new state (next step's dt)
       T smax = T(0);
