@@ -244,11 +244,13 @@ def quality_pass(torch, w, steps, eps_list, timing=None):
             res[-1]["ms_per_step"] = ms / K
             res[-1]["mlups"] = n * n * K / (ms * 1e-3) / 1e6
             res[-1]["timed_from_step"] = steps
-        # the compression's own mass drift: one encode of the decoded state
-        # (FP64 sums of the FP32 nodes before and after), apart from the
-        # collision's FP32 drift that mass_drift and dense_mass_drift carry
-        m1 = float(Fc.astype(np.float64).sum())
-        s.import_field(-1, Fc)
+        # the compression's own mass drift: one encode and decode of the
+        # uncompressed run's final state (FP64 sums of its FP32 nodes before
+        # and after), apart from the collision's FP32 drift that mass_drift
+        # and dense_mass_drift carry (re-encoding a decoded state would give
+        # it back unchanged)
+        m1 = float(Fd.astype(np.float64).sum())
+        s.import_field(-1, Fd)
         res[-1]["encode_mass_drift"] = (float(s.export_field(-1).astype(np.float64).sum()) - m1) / m1
         s.close()
     return res

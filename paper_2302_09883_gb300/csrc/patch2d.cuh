@@ -744,27 +744,32 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
 // Ghosts of an FV patch without a ring: the four lines beside its shared
 // borders, all F fields, decoded from the neighbours' records of the
 // current state (the west neighbour's node column P-1, the east one's 1,
-// the south one's row P-1, the north one's 1), by the cone decode of
-// ringfree_ghosts without the collision: west and east first (the cone
-// columns inverse transformed along y, then the restricted inverse along x
-// per row), then south and north (the restricted inverse along y per
-// column, then the one row along x).  The four-normal stencil needs no
-// corners.  An outflow border copies the patch's own boundary node.
+// the south one's row P-1, the north one's 1) by the cone decode of
+// ringfree_ghosts without the collision.  The four-normal stencil needs no
+// corners, so the four sides go through one round: regions 0 (west) and 1
+// (east) hold the cone columns, 2 (south) and 3 (north) the cone rows;
+// then, side by side, the west/east cone columns are inverse transformed
+// along y while the south/north regions get the restricted inverse along y
+// per column; then the restricted inverse along x per row (west/east)
+// beside the one row along x (south/north).  An outflow border copies the
+// patch's own boundary node.
 template <int SCH, int WV, typename T, int ST, int P, int L>
 __device__ void ringfree_ghosts_fv(const PatchArgs& a, int px, int py, T* tiles, T* reg, const int* nbi) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
   constexpr int F = C::F, E = C::E, PW = C::PW, TS = C::TS, NT = C::NT, NWARP = C::NWARP;
   constexpr ConeMask CH = cone_mask<P, L>(P - 1), CL = cone_mask<P, L>(1);
-  constexpr int NCN = cone_count(CH);
+  constexpr int NCN = cone_count(CH), RG = NCN * E;  // values per (side, field) region
   static_assert(cone_count(CL) == NCN, "the two border cones mirror each other");
-  static_assert(size_t(2) * F * NCN * E * sizeof(T) <= C::STG, "ghost regions fit in the staging area");
+  static_assert(size_t(4) * F * RG * sizeof(T) <= C::STG, "ghost regions fit in the staging area");
+  static_assert(2 * F * NCN + F * E <= NT && F * E + 2 * F <= NT, "one line per thread in each round");
   constexpr int IH = cone_index_c(CH, P - 1), IL = cone_index_c(CL, 1);
   constexpr int NCQ = cone_coarse_count<P, L>(CH);
   static_assert(cone_coarse_ends<P, L>(CH, CL, NCQ), "border cones hold the end coarse nodes");
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  (void)lane;
+  const int tid = threadIdx.x, warp = tid >> 5;
   auto qh = [](int j) { return P - (NCQ - 1 - j) * (1 << L); };
   auto ql = [](int j) { return j * (1 << L); };
+  auto cidx = [&](int hi, int k) { return hi ? cone_index(CH, k) : cone_index(CL, k); };
+  constexpr int NBR[4] = {3, 4, 1, 6};  // neighbour of side sd: W, E, S, N
   auto coarse_val = [&](int n, int f, int c) -> T {
     const int* e = nbi + 8 * (n * F + f);
     const unsigned char* R =
@@ -772,91 +777,63 @@ __device__ void ringfree_ghosts_fv(const PatchArgs& a, int px, int py, T* tiles,
     return __ldg(reinterpret_cast<const T*>(R + e[2] + c * int(sizeof(T))));
   };
   auto words = [&](int n, int f) { return nbi[8 * (n * F + f) + 3]; };
-  auto zero = [&](T* p, int n) {
-    const int n4 = int(n * sizeof(T) / 16);
+  {  // zero the four regions
+    T* p = reg;
+    constexpr int n = 4 * F * RG, n4 = int(n * sizeof(T) / 16);
     for (int i = tid; i < n4; i += NT) reinterpret_cast<uint4*>(p)[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int i = n4 * int(16 / sizeof(T)) + tid; i < n; i += NT) p[i] = T(0);
-  };
-  auto coarse_ix = [&](int sd, int ix) {
-    bool c = false;
+  }
+  __syncthreads();
+  // coarse nodes of the cones: columns (west/east: rg[ix E + y]) and rows
+  // (south/north: rg[iy E + x])
+  constexpr int NQ = NCQ * C::NC1;
+  for (int i = tid; i < 4 * F * NQ; i += NT) {
+    const int task = i / NQ, r = i - task * NQ, j = r / C::NC1, o = r - j * C::NC1;
+    const int sd = task / F, f = task - sd * F, hi = (sd & 1) == 0, k = hi ? qh(j) : ql(j);
+    const int c = sd < 2 ? o * C::NC1 + (k >> L) : (k >> L) * C::NC1 + o;
+    reg[task * RG + cidx(hi, k) * E + (o << L)] = coarse_val(NBR[sd], f, c);
+  }
+  for (int task = warp; task < 4 * F; task += NWARP) {
+    const int sd = task / F, f = task - sd * F, hi = (sd & 1) == 0;
+    if (words(NBR[sd], f) != 0)
+      ringfree_scatter<WV, T, ST, P, L, SCH>(a.arena_in, nbi, NBR[sd], f, reg + task * RG, sd < 2 ? 0 : 1,
+                                             hi ? CH : CL, hi ? CH : CL);
+  }
+  __syncthreads();
+  if (tid < 2 * F * NCN) {  // west/east: cone columns along y (the others hold zeros only)
+    const int task = tid / NCN, ix = tid - task * NCN, sd = task / F, f = task - sd * F;
+    bool coarse = false;
 #pragma unroll
-    for (int j = 0; j < NCQ; ++j) c = c || ix == (sd == 0 ? cone_index(CH, qh(j)) : cone_index(CL, ql(j)));
-    return c;
-  };
+    for (int j = 0; j < NCQ; ++j) coarse = coarse || ix == cidx(sd == 0, sd == 0 ? qh(j) : ql(j));
+    if (coarse || words(NBR[sd], f) != 0) line_transform<WV, P, L, true, T>(reg + task * RG + ix * E, 1);
+  } else if (tid < 2 * F * NCN + F * E) {  // south/north: across the rows, column by column
+    const int t = tid - 2 * F * NCN, f = t / E, x = t - f * E;
+    cone_inverse<P, L, P - 1, T>(reg + (2 * F + f) * RG, E, x);
+    cone_inverse<P, L, 1, T>(reg + (3 * F + f) * RG, E, x);
+  }
+  __syncthreads();
+  if (tid < F * E) {  // west/east: across the columns, row by row
+    const int f = tid / E, y = tid - f * E;
+    cone_inverse<P, L, P - 1, T>(reg + f * RG, E, y);
+    cone_inverse<P, L, 1, T>(reg + (F + f) * RG, E, y);
+  } else if (tid < F * E + 2 * F) {  // south/north: the one row along x
+    const int t = tid - F * E, sd = 2 + t / F, f = t % F;
+    line_transform<WV, P, L, true, T>(reg + (sd * F + f) * RG + (sd == 2 ? IH : IL) * E, 1);
+  }
+  __syncthreads();
   const bool hasW = a.per_x || px > 0, hasE = a.per_x || px < a.npx - 1;
   const bool hasS = a.per_y || py > 0, hasN = a.per_y || py < a.npy - 1;
-  static_assert(2 * F * NCN <= NT, "one cone column per thread");
-  // ---- west (neighbour 3, its node P-1 of every row) and east (4, node 1)
-  zero(reg, 2 * F * NCN * E);
-  __syncthreads();
-  for (int i = tid; i < 2 * F * NCQ * C::NC1; i += NT) {  // the coarse nodes of the cone columns
-    const int task = i / (NCQ * C::NC1), r = i - task * NCQ * C::NC1, jx = r / C::NC1, iy = r - jx * C::NC1;
-    const int sd = task / F, f = task - sd * F, kx = sd == 0 ? qh(jx) : ql(jx);
-    reg[(sd * F + f) * NCN * E + (sd == 0 ? cone_index(CH, kx) : cone_index(CL, kx)) * E + (iy << L)] =
-        coarse_val(sd == 0 ? 3 : 4, f, iy * C::NC1 + (kx >> L));
-  }
-  for (int task = warp; task < 2 * F; task += NWARP) {
-    const int sd = task / F, f = task - sd * F;
-    if (words(sd == 0 ? 3 : 4, f) != 0)
-      ringfree_scatter<WV, T, ST, P, L, SCH>(a.arena_in, nbi, sd == 0 ? 3 : 4, f, reg + (sd * F + f) * NCN * E, 0,
-                                             sd == 0 ? CH : CL, CH);
-  }
-  __syncthreads();
-  if (tid < 2 * F * NCN) {  // cone columns along y (the others hold zeros only)
-    const int task = tid / NCN, ix = tid - task * NCN, sd = task / F, f = task - sd * F;
-    if (coarse_ix(sd, ix) || words(sd == 0 ? 3 : 4, f) != 0)
-      line_transform<WV, P, L, true, T>(reg + (task * NCN + ix) * E, 1);
-  }
-  __syncthreads();
-  for (int t = tid; t < F * E; t += NT) {  // across the columns, row by row
-    const int f = t / E, y = t - f * E;
-    cone_inverse<P, L, P - 1, T>(reg + f * NCN * E, E, y);
-    cone_inverse<P, L, 1, T>(reg + (F + f) * NCN * E, E, y);
-  }
-  __syncthreads();
   for (int t = tid; t < F * E; t += NT) {
-    const int q = t / E, y = t - q * E;
-    const int b = q * TS + PW + 1 + y * PW;  // node (0, y) of field q's input tile
-    const T w = hasW ? reg[q * NCN * E + IH * E + y] : tiles[b];
-    const T e = hasE ? reg[(F + q) * NCN * E + IL * E + y] : tiles[b + E - 1];
-    tiles[b - 1] = w;
-    tiles[b + E] = e;
-  }
-  __syncthreads();
-  // ---- south (neighbour 1, its row P-1) and north (6, row 1)
-  zero(reg, 2 * F * NCN * E);
-  __syncthreads();
-  for (int i = tid; i < 2 * F * NCQ * C::NC1; i += NT) {  // the coarse nodes of the cone rows
-    const int task = i / (NCQ * C::NC1), r = i - task * NCQ * C::NC1, jy = r / C::NC1, ix = r - jy * C::NC1;
-    const int sd = task / F, f = task - sd * F, ky = sd == 0 ? qh(jy) : ql(jy);
-    reg[(sd * F + f) * NCN * E + (sd == 0 ? cone_index(CH, ky) : cone_index(CL, ky)) * E + (ix << L)] =
-        coarse_val(sd == 0 ? 1 : 6, f, (ky >> L) * C::NC1 + ix);
-  }
-  for (int task = warp; task < 2 * F; task += NWARP) {
-    const int sd = task / F, f = task - sd * F;
-    if (words(sd == 0 ? 1 : 6, f) != 0)
-      ringfree_scatter<WV, T, ST, P, L, SCH>(a.arena_in, nbi, sd == 0 ? 1 : 6, f, reg + (sd * F + f) * NCN * E, 1, CH,
-                                             sd == 0 ? CH : CL);
-  }
-  __syncthreads();
-  for (int t = tid; t < F * E; t += NT) {  // across the rows, column by column
-    const int f = t / E, x = t - f * E;
-    cone_inverse<P, L, P - 1, T>(reg + f * NCN * E, E, x);
-    cone_inverse<P, L, 1, T>(reg + (F + f) * NCN * E, E, x);
-  }
-  __syncthreads();
-  if (tid < 2 * F) {  // the one row along x
-    const int sd = tid / F, f = tid - sd * F;
-    line_transform<WV, P, L, true, T>(reg + (sd * F + f) * NCN * E + (sd == 0 ? IH : IL) * E, 1);
-  }
-  __syncthreads();
-  for (int t = tid; t < F * E; t += NT) {
-    const int q = t / E, x = t - q * E;
-    const int b = q * TS + PW + 1 + x;  // node (x, 0) of field q's input tile
-    const T s = hasS ? reg[q * NCN * E + IH * E + x] : tiles[b];
-    const T n = hasN ? reg[(F + q) * NCN * E + IL * E + x] : tiles[b + (E - 1) * PW];
-    tiles[b - PW] = s;
-    tiles[b + E * PW] = n;
+    const int q = t / E, k = t - q * E;
+    const int bw = q * TS + PW + 1 + k * PW, bs = q * TS + PW + 1 + k;  // nodes (0, k) and (k, 0)
+    const T w = hasW ? reg[q * RG + IH * E + k] : tiles[bw];
+    const T e = hasE ? reg[(F + q) * RG + IL * E + k] : tiles[bw + E - 1];
+    const T so = hasS ? reg[(2 * F + q) * RG + IH * E + k] : tiles[bs];
+    const T no = hasN ? reg[(3 * F + q) * RG + IL * E + k] : tiles[bs + (E - 1) * PW];
+    tiles[bw - 1] = w;
+    tiles[bw + E] = e;
+    tiles[bs - PW] = so;
+    tiles[bs + E * PW] = no;
   }
 }
 
