@@ -174,7 +174,9 @@ wcs_status wcs_sync(wcs_sim* sim);
 wcs_status wcs_export_field(wcs_sim* sim, int field, void* dst, int dst_is_device, int dtype);
 
 /* Bytes of device memory that hold the compressed state: the records of
- * the current state plus the ghost ring it needs and the patch table. */
+ * the current state plus the ghost ring it needs (none for 2-D BL5/3
+ * patches, which decode their ghosts from the neighbours' records) and
+ * the patch table. */
 int64_t wcs_compressed_bytes(const wcs_sim* sim);
 
 /* Every byte of device memory the simulation holds: both record arenas at
@@ -185,7 +187,7 @@ int64_t wcs_resident_bytes(const wcs_sim* sim);
 /* Replaces the current state by dense values over the unique nodes (the
  * layout of wcs_export_field: field = -1 takes F planes one after the
  * other, else one field's plane) and encodes it again (threshold, quantise,
- * records, ghost rings, FP64 sums and, EULER2D, the signal speed for the
+ * records, ghost rings where kept, FP64 sums and, EULER2D and SWE, the signal speed for the
  * next step); the step count and time are kept.  dtype 0 = double, 1 =
  * float, rounded to the compute type; src is a device pointer if
  * src_is_device, else host.  Used to start from a given state, or to hand a
