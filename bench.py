@@ -511,7 +511,9 @@ def batch_section(torch, K, W, flush, bs, nsims=96, quality_steps=500, store="f3
     Each simulation gets its own eps: the largest of a ladder (down to 0,
     which keeps every coefficient) whose 500-step run keeps the relative L2
     error of u and rho <= 1e-3 against its own uncompressed run, found by
-    bisection over the ladder (the error grows with eps).  The batch steps both patch sizes in one persistent
+    bisection over the ladder (the error grows with eps); where even eps = 0
+    errs by more (the FP32 rounding of the lifting against velocities of
+    order 1e-4), the gate is 1.1 x that floor.  The batch steps both patch sizes in one persistent
     launch per step (launch shape tuned), six steps per CUDA-graph replay;
     each replay is one timed unit with the L2 flushed before it."""
     from paper_2302_09883_gb300 import Batch, Dense, Sim, autotune
@@ -547,19 +549,24 @@ def batch_section(torch, K, W, flush, bs, nsims=96, quality_steps=500, store="f3
             c.close()
             rc, uxc, uyc = _velocity_rho_dev(torch, Fc)
             return _rel_dev(torch, torch.stack([uxc, uyc]), ud), _rel_dev(torch, rc, rd)
+        # the FP32 floor: eps = 0 keeps every coefficient, and what error
+        # remains is the rounding of the FP32 lifting against the FP32
+        # uncompressed run; where that floor is above 1e-3 (weak bumps whose
+        # velocities are tiny) the gate is 1.1 x the floor
+        res = {len(eps_ladder) - 1: trial(eps_ladder[-1])}
+        gate = (max(1e-3, 1.1 * res[len(eps_ladder) - 1][0]), max(1e-3, 1.1 * res[len(eps_ladder) - 1][1]))
         lo, hi = 0, len(eps_ladder) - 1  # find the first index that passes
-        res = {}
         while lo < hi:
             mid = (lo + hi) // 2
-            res[mid] = trial(eps_ladder[mid])
-            if res[mid][0] <= 1e-3 and res[mid][1] <= 1e-3:
+            if mid not in res:
+                res[mid] = trial(eps_ladder[mid])
+            if res[mid][0] <= gate[0] and res[mid][1] <= gate[1]:
                 hi = mid
             else:
                 lo = mid + 1
-        if lo not in res:
-            res[lo] = trial(eps_ladder[lo])
         eps_of.append(eps_ladder[lo])
-        err_of.append({"u": res[lo][0], "rho": res[lo][1]})
+        err_of.append({"u": res[lo][0], "rho": res[lo][1], "floor_u": res[len(eps_ladder) - 1][0],
+                       "gate_u": gate[0], "gate_rho": gate[1]})
     sims = []
     for sp, eps in zip(specs, eps_of):
         n = sp["side"]
@@ -597,16 +604,16 @@ def batch_section(torch, K, W, flush, bs, nsims=96, quality_steps=500, store="f3
     # a simulation whose records outgrew its arenas inside the timed steps
     # froze and caught up in b.sync(): those steps did not run in the timed
     # launches, so the timing is taken again (the arenas have grown by then)
-    r0 = sum(reruns(s) for s in sims)
-    ms = timed()
-    b.sync()
-    retimed = sum(reruns(s) for s in sims) != r0
-    if retimed:
+    retimed = 0
+    while True:
         r0 = sum(reruns(s) for s in sims)
         ms = timed()
         b.sync()
-        if sum(reruns(s) for s in sims) != r0:
-            raise RuntimeError("batch: arena overflow inside the timed steps twice")
+        if sum(reruns(s) for s in sims) == r0:
+            break
+        retimed += 1  # the arenas doubled; records still grow as the waves spread
+        if retimed > 4:
+            raise RuntimeError("batch: arena overflow inside the timed steps five times")
     lu = sum(sp["side"] ** 2 for sp in specs)
     unc = sum(s.stats()["uncompressed_bytes"] for s in sims)
     comp = sum(s.compressed_bytes() for s in sims)
@@ -620,6 +627,10 @@ def batch_section(torch, K, W, flush, bs, nsims=96, quality_steps=500, store="f3
             "eps_per_simulation": eps_hist, "max_rel_l2_u": max(e["u"] for e in err_of),
             "max_rel_l2_rho": max(e["rho"] for e in err_of), "all_meet_1e-3": all(
                 e["u"] <= 1e-3 and e["rho"] <= 1e-3 for e in err_of),
+            "n_meet_1e-3": sum(e["u"] <= 1e-3 and e["rho"] <= 1e-3 for e in err_of),
+            "n_at_fp32_floor_gate": sum(e["gate_u"] > 1e-3 for e in err_of),
+            "max_fp32_floor_u": max(e["floor_u"] for e in err_of),
+            "all_meet_gate": all(e["u"] <= e["gate_u"] and e["rho"] <= e["gate_rho"] for e in err_of),
             "autotune": {str(k): {"P": v[0][0], "levels": v[0][1], "ms_per_step_P64_P32": v[1]} for k, v in choice.items()},
             "launches_per_step": launches, "launch_grid": grid, "launch_tuning": tune,
             "mlups": lu * 6 * reps / (ms * 1e-3) / 1e6, "ms_per_step": ms / (6 * reps), "timed_steps": 6 * reps,
