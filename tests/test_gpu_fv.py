@@ -123,3 +123,32 @@ def pair_wv(scheme, wv, n, P, L, eps, rule, fields, steps_at, **kw):
         for p in range(g.npatch):
             assert g.record(p) == o.record(p), "patch %d record differs after %d steps" % (p, s)
     return g, o
+
+
+@pytest.mark.parametrize("scheme", ["euler2d", "transport"])
+def test_ring_free_ghosts_one_patch_along_an_axis(scheme):
+    # ring-free FV ghosts when the neighbour across a periodic border is the
+    # patch itself (one patch along x) and the other axis has outflow
+    # borders: records byte for byte and fields bit for bit (FP64)
+    nx, ny, P = 32, 96, 32
+    x = np.arange(nx + 0) / nx
+    y = np.arange(ny + 1) / ny
+    X, Y = np.meshgrid(x, y)
+    if scheme == "euler2d":
+        f = [1.0 + 0.3 * np.exp(-40 * ((X - 0.5) ** 2 + (Y - 0.3) ** 2)), 0.2 * np.sin(2 * np.pi * X),
+             0.1 * np.cos(2 * np.pi * X) * Y, 1.0 + 0.2 * np.exp(-30 * ((X - 0.4) ** 2 + (Y - 0.6) ** 2))]
+        kw = dict(periodic=(True, False), cfl=0.4, gamma=1.4)
+    else:
+        f = [1.0 + np.exp(-30 * ((X - 0.5) ** 2 + (Y - 0.4) ** 2))]
+        kw = dict(periodic=(True, False), cfl=0.45, velocity=(0.7, -0.4), length=1.0)
+    g = Sim(scheme, "bl53", nx, ny, P, 3, 1e-4, prec="f64", store="f64", rule="capped", **kw)
+    o = O.OracleSim(scheme, "bl53", nx, ny, P, 3, 1e-4, prec="f64", store="f64", rule="capped", **kw)
+    g.init_macro(f)
+    o.init_macro(f)
+    for chunk in (1, 15):
+        g.step(chunk)
+        o.step(chunk)
+        g.sync()
+        for p in range(g.npatch):
+            assert g.record(p) == o.record(p)
+    assert np.array_equal(g.export_field(-1), o.export_all())
