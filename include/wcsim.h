@@ -213,6 +213,17 @@ wcs_status wcs_entropy_code(wcs_sim* sim, void* dst_host, int64_t cap, int64_t* 
 
 /* FP64 diagnostics of the current state (synchronises). */
 wcs_status wcs_stats(wcs_sim* sim, wcs_step_stats* out);
+/* The same without a synchronisation: wcs_stats_enqueue queues, on the
+ * simulation's stream behind the work already enqueued, a copy of the
+ * control block and of the per-patch FP64 sums into slot `slot` (0..3) of
+ * pinned host memory that the library owns (allocated at the first call:
+ * 4 x (npatch x F x 8 + 88) bytes); wcs_stats_collect waits for that copy
+ * and fills out exactly as wcs_stats would have for that step (same sums,
+ * same order).  A slot is free again after its collect; collecting an
+ * empty slot is WCS_E_ARG.  No arena-overflow recovery here: a failed step
+ * shows in out->status, and wcs_sync recovers or reports it. */
+wcs_status wcs_stats_enqueue(wcs_sim* sim, int slot);
+wcs_status wcs_stats_collect(wcs_sim* sim, int slot, wcs_step_stats* out);
 
 /* Detail coefficients kept in the current state (the survivors of the
  * threshold, all patches and fields; coarse samples not counted), counted

@@ -69,6 +69,8 @@ def lib():
         L.wcs_survivors.restype = i64
         L.wcs_survivors.argtypes = [vp]
         L.wcs_stats.argtypes = [vp, C.POINTER(StepStats)]
+        L.wcs_stats_enqueue.argtypes = [vp, i32]
+        L.wcs_stats_collect.argtypes = [vp, i32, C.POINTER(StepStats)]
         L.wcs_export_record.argtypes = [vp, i64, vp, i64, C.POINTER(i64)]
         L.wcs_shape.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64), C.POINTER(i64)]
         L.wcs_shape3.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64)]

@@ -168,6 +168,13 @@ struct wcs_sim {
   double* eps_patch = nullptr;
   double eps_lo = 1e-7, eps_hi = 1e-2;
   bool eps_given = false;  // per-patch eps set by the caller
+  // asynchronous statistics: per slot a pinned copy of the FP64 sums and the
+  // control block, the event that completes it, and the step it describes
+  static constexpr int NSTAT = 4;
+  unsigned char* stat_pin = nullptr;
+  size_t stat_slot = 0;
+  cudaEvent_t stat_ev[NSTAT] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t stat_step[NSTAT] = {-1, -1, -1, -1};
 };
 
 static wcs_status fail(wcs_sim* s, wcs_status st, const std::string& msg) {
@@ -769,6 +776,9 @@ void wcs_destroy(wcs_sim* s) {
   cudaFree(s->scratch);
   cudaFree(s->rbuf);
   cudaFree(s->cnt);
+  for (int k = 0; k < wcs_sim::NSTAT; ++k)
+    if (s->stat_ev[k]) cudaEventDestroy(s->stat_ev[k]);
+  cudaFreeHost(s->stat_pin);
   delete s;
 }
 
@@ -1069,15 +1079,11 @@ wcs_status wcs_import_field(wcs_sim* s, int field, const void* src, int src_is_d
   return wcs_sync(s);
 }
 
-wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
-  if (!s || !o) return WCS_E_ARG;
+// Step statistics from the control block c and the per-patch FP64 sums ps
+// (npatch x F) of the state after step nstep: the per-field sums over the
+// patches in patch order, then the scheme's mass, momentum and energy.
+static void fill_stats(const wcs_sim* s, const wcs::Ctl& c, const double* ps, int64_t nstep, wcs_step_stats* o) {
   std::memset(o, 0, sizeof(*o));
-  if (s->inited) (void)wcs_sync(s);  // re-runs a step lost to an arena overflow; errors stay in the status
-  CK(cudaStreamSynchronize(s->stream));
-  wcs::Ctl c;
-  CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
-  std::vector<double> ps(size_t(s->npatch) * s->F);
-  CK(cudaMemcpy(ps.data(), s->pstats, ps.size() * 8, cudaMemcpyDeviceToHost));
   for (int f = 0; f < s->F; ++f) {
     double acc = 0;
     for (int p = 0; p < s->npatch; ++p) acc += ps[size_t(p) * s->F + f];
@@ -1109,16 +1115,54 @@ wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
   } else {
     o->mass = o->field_sum[0];
   }
-  o->step = s->nstep;
+  o->step = nstep;
   o->time = c.time;
-  unsigned long long sb = c.smax[s->nstep % 3];
+  unsigned long long sb = c.smax[nstep % 3];
   std::memcpy(&o->smax, &sb, 8);
-  o->live_bytes = int64_t(c.cursor[s->nstep % 2]);
+  o->live_bytes = int64_t(c.cursor[nstep % 2]);
   o->resident_bytes = s->resident;
   o->uncompressed_bytes = int64_t(s->F) * s->G[0] * s->G[1] * s->G[2] * int64_t(s->tsize);
   o->status = c.status;
   o->arena_capacity = int64_t(s->cap);
   o->arena_reruns = s->reruns;
+}
+
+wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
+  if (!s || !o) return WCS_E_ARG;
+  std::memset(o, 0, sizeof(*o));
+  if (s->inited) (void)wcs_sync(s);  // re-runs a step lost to an arena overflow; errors stay in the status
+  CK(cudaStreamSynchronize(s->stream));
+  wcs::Ctl c;
+  CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+  std::vector<double> ps(size_t(s->npatch) * s->F);
+  CK(cudaMemcpy(ps.data(), s->pstats, ps.size() * 8, cudaMemcpyDeviceToHost));
+  fill_stats(s, c, ps.data(), s->nstep, o);
+  return WCS_OK;
+}
+
+wcs_status wcs_stats_enqueue(wcs_sim* s, int slot) {
+  if (!s || !s->inited || slot < 0 || slot >= wcs_sim::NSTAT) return WCS_E_ARG;
+  if (!s->stat_pin) {  // first use: four pinned slots and their events
+    s->stat_slot = (size_t(s->npatch) * s->F * 8 + sizeof(wcs::Ctl) + 255) / 256 * 256;
+    CK(cudaMallocHost(reinterpret_cast<void**>(&s->stat_pin), s->stat_slot * wcs_sim::NSTAT));
+    for (int k = 0; k < wcs_sim::NSTAT; ++k) CK(cudaEventCreateWithFlags(&s->stat_ev[k], cudaEventDisableTiming));
+  }
+  unsigned char* d = s->stat_pin + size_t(slot) * s->stat_slot;
+  CK(cudaMemcpyAsync(d, s->ctl, sizeof(wcs::Ctl), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(d + sizeof(wcs::Ctl), s->pstats, size_t(s->npatch) * s->F * 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaEventRecord(s->stat_ev[slot], s->stream));
+  s->stat_step[slot] = s->nstep;
+  return WCS_OK;
+}
+
+wcs_status wcs_stats_collect(wcs_sim* s, int slot, wcs_step_stats* o) {
+  if (!s || !o || slot < 0 || slot >= wcs_sim::NSTAT || s->stat_step[slot] < 0) return WCS_E_ARG;
+  CK(cudaEventSynchronize(s->stat_ev[slot]));
+  const unsigned char* d = s->stat_pin + size_t(slot) * s->stat_slot;
+  wcs::Ctl c;
+  std::memcpy(&c, d, sizeof(c));
+  fill_stats(s, c, reinterpret_cast<const double*>(d + sizeof(wcs::Ctl)), s->stat_step[slot], o);
+  s->stat_step[slot] = -1;
   return WCS_OK;
 }
 

@@ -149,14 +149,28 @@ class Sim:
         dt = 0 if a.dtype == np.float64 else 1
         B.check(B.lib().wcs_import_field(self.h, f, a.ctypes.data, 0, dt), self.h)
 
-    def stats(self):
-        s = B.StepStats()
-        B.check(B.lib().wcs_stats(self.h, C.byref(s)), self.h)
+    def _stats_dict(self, s):
         return {"step": s.step, "time": s.time, "field_sum": np.array(s.field_sum[:self.F]), "mass": s.mass,
-                "momentum": np.array(s.momentum[:2]), "energy": s.energy, "smax": s.smax,
+                "momentum": np.array(s.momentum[:3 if len(self.G) == 3 else 2]), "energy": s.energy, "smax": s.smax,
                 "live_bytes": s.live_bytes, "resident_bytes": s.resident_bytes,
                 "uncompressed_bytes": s.uncompressed_bytes, "status": s.status,
                 "arena_capacity": s.arena_capacity, "arena_reruns": s.arena_reruns}
+
+    def stats(self):
+        s = B.StepStats()
+        B.check(B.lib().wcs_stats(self.h, C.byref(s)), self.h)
+        return self._stats_dict(s)
+
+    def stats_enqueue(self, slot=0):
+        """Queues the statistics of the state the enqueued steps lead to into
+        pinned slot `slot` (0..3) without synchronising."""
+        B.check(B.lib().wcs_stats_enqueue(self.h, slot), self.h)
+
+    def stats_collect(self, slot=0):
+        """Waits for slot `slot` and returns what stats() gave for that step."""
+        s = B.StepStats()
+        B.check(B.lib().wcs_stats_collect(self.h, slot, C.byref(s)), self.h)
+        return self._stats_dict(s)
 
     def record(self, p):
         n = C.c_int64()
@@ -205,13 +219,6 @@ class Sim3(Sim):
         else:
             B.check(B.lib().wcs_export_field(self.h, f, out.ctypes.data, 0, dt), self.h)
         return out
-
-    def stats(self):
-        d = super().stats()
-        s = B.StepStats()
-        B.check(B.lib().wcs_stats(self.h, C.byref(s)), self.h)
-        d["momentum"] = np.array(s.momentum[:3])
-        return d
 
 
 class Dense:

@@ -156,3 +156,32 @@ def test_survivor_count_matches_oracle_records():
             want += int(rows[:, 2].sum() + rows[:, 3].sum())
         assert g.survivors() == want
         g.close()
+
+
+def test_async_stats_equal_the_synchronous_ones():
+    # wcs_stats_enqueue / wcs_stats_collect give, for each step, exactly what
+    # wcs_stats gives after that step (same sums in the same order)
+    n = 256
+    a = Sim("d2q9", "bl53", n, n, 64, 4, 1e-5, prec="f32", store="bf16", tau=0.6)
+    b = Sim("d2q9", "bl53", n, n, 64, 4, 1e-5, prec="f32", store="bf16", tau=0.6)
+    f = inputs.shear_wave(n, seed=3)
+    a.init_macro(f)
+    b.init_macro(f)
+    got = []
+    for k in range(6):
+        a.step(1)
+        a.stats_enqueue(k % 4)
+        if k >= 3:
+            got.append(a.stats_collect((k - 3) % 4))
+    for k in range(3, 6):
+        got.append(a.stats_collect(k % 4))
+    for k in range(6):
+        b.step(1)
+        want = b.stats()
+        g = got[k]
+        assert g["step"] == want["step"] == k + 1
+        assert np.array_equal(g["field_sum"], want["field_sum"]) and g["mass"] == want["mass"]
+        assert g["live_bytes"] == want["live_bytes"] and g["status"] == 0
+    from paper_2302_09883_gb300._lib import WcsError
+    with pytest.raises(WcsError):
+        a.stats_collect(0)  # nothing queued in that slot any more
