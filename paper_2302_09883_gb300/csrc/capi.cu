@@ -5,7 +5,7 @@
 //              bump-allocates the records of state n+1 in arena (n+1)%2
 //   tab[2]     per patch (record offset << 24 | record bytes)
 //   ring[2]    ghost rings exported by every patch for the next step (none
-//              for D2Q9 on BL5/3, whose ghosts come from the records)
+//              for 2-D BL5/3 patches, whose ghosts come from the records)
 //   scratch    3-D kernels: per resident CTA a scratch cube and record buffer
 //   ctl        cursors, max signal speed, time, sticky status
 //   pstats     FP64 coarse-block sums per patch and field

@@ -6,16 +6,18 @@
 //   per-column mask of the stored rows stands in for the zeros) -> inverse
 //   tensor lifting (only the columns holding a coefficient, then every row)
 //   -> ghosts -> scheme (D2Q9 collide in place + pull via per-population
-//   shifted windows, or the Rusanov FV update) -> forward tensor lifting ->
+//   shifted windows, or the FV update: Rusanov, upwind or Godunov fluxes)
+//   -> forward tensor lifting ->
 //   threshold over the node order with warp ballots -> prefix sums, band
 //   scales, non-finite check on the coarse block, FP64 coarse-block sums,
 //   bump-allocate, write the record (survivors only) and the dequantised
 //   values back in place (the ring kernels re-decode them).
-//   Ghosts: D2Q9 on BL5/3 patches decodes them from the neighbours' records
-//   of the current state (only the dependency cone of the boundary node, see
-//   ringfree_ghosts); the other kernels read a ring that every patch exports
-//   at the end of the step by re-decoding its new record (post-collision
-//   inward populations for D2Q9 with Haar, the state for Euler).
+//   Ghosts: BL5/3 patches decode them from the neighbours' records of the
+//   current state (only the dependency cone of the boundary node, see
+//   ringfree_ghosts and ringfree_ghosts_fv); Haar and CDF 9/7 patches read a
+//   ring that every patch exports at the end of the step by re-decoding its
+//   new record (post-collision inward populations for D2Q9, the state for
+//   the FV schemes).
 //
 // Record byte format (the paper's pipeline, Sec. 2: DWT of Sec. 2.1.2, hard
 // threshold of Sec. 2.2, a bitmask + values lossless stage in place of
