@@ -322,7 +322,9 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
   for (int j0 = 0; j0 < nwords; j0 += 32) {
     const int j = j0 + lane;
     int w = 0;
-    unsigned int word = 0u;
+    // the word's value does not depend on where it sits, so its load goes
+    // out together with the presence words (one memory round trip, not two)
+    const unsigned int word = j < nwords ? ldr<unsigned int>(R + p_words + 4 * j) : 0u;
     {
       int r = j;
       bool found = false;
@@ -336,8 +338,7 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
         }
         if (!found) r -= cnt;
       }
-      if (j < nwords) word = ldr<unsigned int>(R + p_words + 4 * j);
-      else w = 0;
+      if (!(j < nwords)) w = 0;
     }
     const unsigned int em = word_edges<WV, P, E, C::WR>(w);
     const unsigned ve = __popc(word & em), vi = __popc(word & ~em);
@@ -521,6 +522,34 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
     done += n;
   };
 
+  constexpr int NCC = NCN * NCN;
+  constexpr size_t BYTES_B = size_t(2) * F * NCN * E * sizeof(T), BYTES_C = size_t(4) * F * NCC * sizeof(T);
+  constexpr bool C_STAGE = BYTES_B + BYTES_C <= C::STG;
+  constexpr bool C_MASK = !C_STAGE && BYTES_C <= C::OFF_BMAX - C::OFF_MW;
+  constexpr bool MERGED = C_STAGE || C_MASK;
+  // The coarse values of the south/north stage (and of the corners when they
+  // share its round) are loaded now, one per thread, so that their latency
+  // hides behind the west/east stage; the stage stores them.
+  constexpr int NSN = 2 * F * NCQ * C::NC1, NSNC = NSN + (MERGED ? 4 * F * NCQ * NCQ : 0);
+  static_assert(NSNC <= NT, "one early coarse value per thread");
+  T sn_v = T(0);
+  int sn_slot = -1;  // slot in the south/north regions (< 2 F NCN E) or, minus that, in the corner regions
+  if (tid < NSNC) {
+    const int i = tid;
+    if (i < NSN) {
+      const int task = i / (NCQ * C::NC1), r = i - task * NCQ * C::NC1, jy = r / C::NC1, ix = r - jy * C::NC1;
+      const int sd = task / F, f = task - sd * F, ky = sd == 0 ? qh(jy) : ql(jy);
+      sn_slot = (sd * F + f) * NCN * E + (sd == 0 ? cone_index(CH, ky) : cone_index(CL, ky)) * E + (ix << L);
+      sn_v = coarse_val(sd == 0 ? 1 : 6, f, (ky >> L) * C::NC1 + ix);
+    } else {
+      const int u = i - NSN, task = u / (NCQ * NCQ), r = u - task * NCQ * NCQ, jy = r / NCQ, jx = r - jy * NCQ;
+      const int c = task / F, f = task - c * F, dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
+      const int kx = dx < 0 ? qh(jx) : ql(jx), ky = dy < 0 ? qh(jy) : ql(jy);
+      sn_slot = 2 * F * NCN * E + (c * F + f) * NCC + (dy < 0 ? cone_index(CH, ky) : cone_index(CL, ky)) * NCN +
+                (dx < 0 ? cone_index(CH, kx) : cone_index(CL, kx));
+      sn_v = coarse_val(dy < 0 ? (dx < 0 ? 0 : 2) : (dx < 0 ? 5 : 7), f, (ky >> L) * C::NC1 + (kx >> L));
+    }
+  }
   // ---- west (its node P-1 of every row) and east (node 1) neighbours
   zero(reg, 2 * F * NCN * E);
   __syncthreads();
@@ -580,11 +609,6 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   // ((1, 1), 7), NW ((P-1, 1), 8).  The corner regions go after the rows'
   // in the staging area, or into the idle mask-word arrays, or get a round
   // of their own.
-  constexpr int NCC = NCN * NCN;
-  constexpr size_t BYTES_B = size_t(2) * F * NCN * E * sizeof(T), BYTES_C = size_t(4) * F * NCC * sizeof(T);
-  constexpr bool C_STAGE = BYTES_B + BYTES_C <= C::STG;
-  constexpr bool C_MASK = !C_STAGE && BYTES_C <= C::OFF_BMAX - C::OFF_MW;
-  constexpr bool MERGED = C_STAGE || C_MASK;
   static_assert(!C_STAGE || BYTES_B % 16 == 0, "corner regions start 16-byte aligned");
   T* regc = C_STAGE ? reg + 2 * F * NCN * E : (C_MASK ? reinterpret_cast<T*>(cmask) : reg);
   auto south_north = [&](bool with_corners) {
@@ -592,25 +616,10 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
     if (with_corners) zero(regc, 4 * F * NCC);
     __syncthreads();
     const int ntask = with_corners ? 6 * F : 2 * F;
-    {  // coarse blocks: only the coarse nodes in the cones (rows for south/north, both for the corners)
-      constexpr int NSN = 2 * F * NCQ * C::NC1;
-      const int nitem = NSN + (with_corners ? 4 * F * NCQ * NCQ : 0);
-      for (int i = tid; i < nitem; i += NT) {
-        if (i < NSN) {
-          const int task = i / (NCQ * C::NC1), r = i - task * NCQ * C::NC1, jy = r / C::NC1, ix = r - jy * C::NC1;
-          const int sd = task / F, f = task - sd * F, ky = sd == 0 ? qh(jy) : ql(jy);
-          reg[(sd * F + f) * NCN * E + (sd == 0 ? cone_index(CH, ky) : cone_index(CL, ky)) * E + (ix << L)] =
-              coarse_val(sd == 0 ? 1 : 6, f, (ky >> L) * C::NC1 + ix);
-        } else {
-          const int u = i - NSN, task = u / (NCQ * NCQ), r = u - task * NCQ * NCQ, jy = r / NCQ, jx = r - jy * NCQ;
-          const int c = task / F, f = task - c * F, dx = (c == 1 || c == 2) ? 1 : -1, dy = c >= 2 ? 1 : -1;
-          const int kx = dx < 0 ? qh(jx) : ql(jx), ky = dy < 0 ? qh(jy) : ql(jy);
-          regc[(c * F + f) * NCC + (dy < 0 ? cone_index(CH, ky) : cone_index(CL, ky)) * NCN +
-               (dx < 0 ? cone_index(CH, kx) : cone_index(CL, kx))] =
-              coarse_val(dy < 0 ? (dx < 0 ? 0 : 2) : (dx < 0 ? 5 : 7), f, (ky >> L) * C::NC1 + (kx >> L));
-        }
-      }
-    }
+    // coarse blocks: only the coarse nodes in the cones (rows for south/north,
+    // both for the corners), loaded at the start of the ghost stages
+    if (sn_slot >= 0 && sn_slot < 2 * F * NCN * E) reg[sn_slot] = sn_v;
+    else if (sn_slot >= 0 && with_corners) regc[sn_slot - 2 * F * NCN * E] = sn_v;
     for (int task = warp; task < ntask; task += NWARP) {
       if (task < 2 * F) {
         const int sd = task / F, f = task - sd * F;
@@ -742,7 +751,6 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
   return done;
 }
 
-// The whole patch step for patch `pid` of the simulation described by `a`.
 // Ghosts of an FV patch without a ring: the four lines beside its shared
 // borders, all F fields, decoded from the neighbours' records of the
 // current state (the west neighbour's node column P-1, the east one's 1,
@@ -839,6 +847,7 @@ __device__ void ringfree_ghosts_fv(const PatchArgs& a, int px, int py, T* tiles,
   }
 }
 
+// The whole patch step for patch `pid` of the simulation described by `a`.
 template <int SCH, int WV, typename T, int ST, int P, int L, int MODE, int FEAT = 0>
 __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
