@@ -101,7 +101,11 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   // largest signal speed that sets the next dt (Euler, shallow water)
   static constexpr bool REDECODE = !RINGFREE || SCH == SCH_EULER2D || SCH == SCH_SWE;
   static constexpr int RING = RINGFREE ? 0 : (SCH == SCH_D2Q9 ? 12 * E + 4 : 4 * F * E);
-  static constexpr int NT = sizeof(T) == 8 ? 512 : 768;
+  // A one-field patch (transport) has 65 lines per pass: 256 threads and
+  // a smaller staging area let three patches share an SM; the others take
+  // one CTA per SM with as many threads as their registers allow.
+  static constexpr int NT = F == 1 ? 256 : (sizeof(T) == 8 ? 512 : 768);
+  static constexpr int MINB = F == 1 ? 3 : 1;
   static constexpr int NWARP = NT / 32;
   static constexpr int XLO = wv_nodal(WV) ? 1 : 0;
   static constexpr int XHI = P - 1;
@@ -127,7 +131,8 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   static constexpr size_t OFF_NBI = (OFF_MISC + (64 + 2 * F) * 4 + 15) / 16 * 16;
   static constexpr size_t OFF_STAGE = (OFF_NBI + (RINGFREE ? size_t(8) * F * 8 * 4 : 0) + 15) / 16 * 16;
   static constexpr size_t SMEM_MAX = 232448;
-  static constexpr size_t STG = (SMEM_MAX - OFF_STAGE) / 16 * 16 > 49152 ? 49152 : (SMEM_MAX - OFF_STAGE) / 16 * 16;
+  static constexpr size_t STG_CAP = F == 1 ? 20480 : 49152;
+  static constexpr size_t STG = (SMEM_MAX - OFF_STAGE) / 16 * 16 > STG_CAP ? STG_CAP : (SMEM_MAX - OFF_STAGE) / 16 * 16;
   static constexpr size_t SMEM = OFF_STAGE + STG;
   static_assert(OFF_STAGE + 4096 <= SMEM_MAX, "patch does not fit in shared memory");
 };
@@ -1670,7 +1675,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   // Four warps that are idle in this phase do it for all fields side by
   // side, so that the few FP64 instructions carry full warps.
   constexpr int SUMW = 4;
-  constexpr size_t OFF_DSUM = (4096 + size_t(MLP_NP) * 4 + 15) / 16 * 16;  // behind the FEAT data
+  constexpr size_t OFF_DSUM = FEAT ? (4096 + size_t(MLP_NP) * 4 + 15) / 16 * 16 : 0;  // behind the FEAT data
   static_assert(F + SUMW < NWARP, "no idle warps for the coarse sums");
   static_assert(OFF_DSUM + size_t(F) * 32 * 8 <= C::STG, "coarse-sum slots do not fit in the staging area");
   if (warp >= F && warp < F + SUMW) {
@@ -1911,7 +1916,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
 
 // One simulation: block b is patch b.
 template <int SCH, int WV, typename T, int ST, int P, int L, int MODE, int FEAT = 0>
-__global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, 1) patch_kernel(PatchArgs a) {
+__global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, Cfg<SCH, WV, T, ST, P, L>::MINB) patch_kernel(PatchArgs a) {
   patch_body<SCH, WV, T, ST, P, L, MODE, FEAT>(a, int(blockIdx.x));
 }
 
