@@ -1787,18 +1787,36 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     const int sb = (ST == ST_I8 && (fi[7] & 1)) ? 2 : C::SB;  // int8 field stored as BF16
     for (int p = fi[3] + fi[6] * sb; p < fi[0]; ++p) base[p] = 0;
   }
-  for (int f = 0; f < F && nw_all > 0; ++f) {
+  // the survivors: a thread per survivor (fields one after the other,
+  // survivors in bit order), so that neighbouring threads store to
+  // neighbouring slots; survivor r of a field sits in the last present word
+  // whose survivor prefix is <= r, at its (r - prefix + 1)-th set bit
+  int ns_all = 0;
+#pragma unroll
+  for (int f = 0; f < F; ++f) ns_all += finfo[16 * f + 5] + finfo[16 * f + 6];
+  for (int g = tid; g < ns_all; g += NT) {
+    int f = 0, r = g;
+    while (r >= finfo[16 * f + 5] + finfo[16 * f + 6]) {
+      r -= finfo[16 * f + 5] + finfo[16 * f + 6];
+      ++f;
+    }
     const int* fi = finfo + 16 * f;
-    for (int j = warp; j < fi[4]; j += NWARP) {
-      const int w = plist[f * NW + j];
+    {
+      int lo = 0, hi = fi[4] - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1, wm = plist[f * NW + mid];
+        if (int(pre_e[f * NW + wm]) + int(pre_i[f * NW + wm]) <= r) lo = mid;
+        else hi = mid - 1;
+      }
+      const int w = plist[f * NW + lo];
       const unsigned int word = mw[f * NW + w];
-      if (!((word >> lane) & 1u)) continue;
+      const int bit = __fns(word, 0, r - int(pre_e[f * NW + w]) - int(pre_i[f * NW + w]) + 1);
       int kx, ky;
       bool valid;
-      word_node<P, E, C::WR>(w, lane, kx, ky, valid);
+      word_node<P, E, C::WR>(w, bit, kx, ky, valid);
       const unsigned int em = word_edges<WV, P, E, C::WR>(w);
-      const bool edge = (em >> lane) & 1u;
-      const unsigned int lt = (1u << lane) - 1u;
+      const bool edge = (em >> bit) & 1u;
+      const unsigned int lt = (1u << bit) - 1u;
       const int to = win_out(f) + ky * PW + kx;
       const T v = tiles[to];
       unsigned char* base = O + fi[9];
