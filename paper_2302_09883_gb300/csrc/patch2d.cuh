@@ -365,40 +365,58 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
       rx = cone_has(MX, P) ? 0xffffffffu : 0u;
       ry = cone_bits32(MY, y0);
     }
-    unsigned int m = word & (kind == 0 ? rx : (kind == 1 ? ry : (rx & ry)));
-    // every lane runs the same number of rounds (the warp's largest count),
-    // so that the band scales can be fetched from the other lanes; up to
-    // four survivors of a lane per round, their loads issued together
+    const unsigned int m = word & (kind == 0 ? rx : (kind == 1 ? ry : (rx & ry)));
+    // the region's survivors of the 32 words are dealt out over the lanes,
+    // up to four per lane per round with their loads issued together:
+    // survivor s belongs to the first lane whose inclusive count exceeds s
     const int nb = __popc(m);
-    int rounds = nb;
+    int incl = nb;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, o));
-    for (int r0 = 0; r0 < rounds; r0 += 4) {
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int rowi = rowword ? 1 : 0;
+    for (int s0 = 0; s0 < total; s0 += 128) {
       T v[4];
       int sl[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 4; ++u) {  // every slot empty first: the loop below may stop early
         sl[u] = -1;
         v[u] = T(0);
-        int band = 0;
-        int b = 0;
-        const bool have = m != 0u;
-        if (have) {
-          b = __ffs(m) - 1;
-          m &= m - 1u;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (s0 + 32 * u >= total) break;  // the same for the whole warp
+        const int s = s0 + 32 * u + lane;
+        int src = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int c = __shfl_sync(0xffffffffu, incl, src + step - 1);
+          if (s >= c) src += step;
         }
-        const int kx = rowword ? x0 + b : P, ky = rowword ? y0 : y0 + b;
+        src = src > 31 ? 31 : src;
+        const unsigned int ms = __shfl_sync(0xffffffffu, m, src), ws = __shfl_sync(0xffffffffu, word, src);
+        const unsigned int ems = __shfl_sync(0xffffffffu, em, src);
+        const unsigned bes = __shfl_sync(0xffffffffu, be, src), bis = __shfl_sync(0xffffffffu, bi, src);
+        const int x0s = __shfl_sync(0xffffffffu, x0, src), y0s = __shfl_sync(0xffffffffu, y0, src);
+        const int rows = __shfl_sync(0xffffffffu, rowi, src), exs = __shfl_sync(0xffffffffu, incl - nb, src);
+        const bool have = s < total;
+        const int b = have ? __fns(ms, 0, s - exs + 1) : 0;
+        const int kx = rows ? x0s + b : P, ky = rows ? y0s : y0s + b;
+        int band = 0;
         if constexpr (C::QUANT) band = node_class<L>(kx) * (L + 1) + node_class<L>(ky);
         float scl = 0.0f;
         if constexpr (C::QUANT) {
-          const float s0 = __shfl_sync(0xffffffffu, sc_lane0, band & 31);
-          const float s1 = __shfl_sync(0xffffffffu, sc_lane1, band & 31);
-          scl = band < 32 ? s0 : s1;
+          const float s0v = __shfl_sync(0xffffffffu, sc_lane0, band & 31);
+          const float s1v = __shfl_sync(0xffffffffu, sc_lane1, band & 31);
+          scl = band < 32 ? s0v : s1v;
         }
         if (have) {
           const unsigned int lt = (1u << b) - 1u;
-          if ((em >> b) & 1u) v[u] = ldr<T>(R + p_edge + int(be + __popc(word & em & lt)) * int(sizeof(T)));
-          else v[u] = load_interior<T, ST>(R + p_int, int(bi + __popc(word & ~em & lt)), wide, scl);
+          if ((ems >> b) & 1u) v[u] = ldr<T>(R + p_edge + int(bes + __popc(ws & ems & lt)) * int(sizeof(T)));
+          else v[u] = load_interior<T, ST>(R + p_int, int(bis + __popc(ws & ~ems & lt)), wide, scl);
           sl[u] = slot(kx, ky);
         }
       }
@@ -407,7 +425,7 @@ __device__ __noinline__ void ringfree_scatter(const unsigned char* arena_in, con
         if (sl[u] >= 0) rg[sl[u]] = v[u];
     }
   }
-  }
+}
 
 // Coarse value c of field f of neighbour n, if its node lies in region rg
 // (kind and masks as in ringfree_scatter): its address in the record (src)
