@@ -1143,26 +1143,39 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         ce += __shfl_sync(0xffffffffu, ie, 31);
         ci += __shfl_sync(0xffffffffu, ii, 31);
       }
+      if (lane == 0) finfo[16 * f + 8] = int(ce + ci);  // the field's survivors
     }
     __syncthreads();
-    // survivors: one warp per non-zero mask word, one lane per node
-    // (skipped as a whole when no field has a stored word: entering the
-    // loops costs even when they are empty)
-    int nw_all = 0;
+    // survivors: a thread per survivor (fields one after the other, in bit
+    // order); survivor r of a field sits in the last present word whose
+    // survivor prefix is <= r, at its (r - prefix + 1)-th set bit
+    int ns_all = 0;
 #pragma unroll
-    for (int f = 0; f < F; ++f) nw_all += finfo[16 * f + 6];
-    for (int f = 0; f < F && nw_all > 0; ++f) {
+    for (int f = 0; f < F; ++f) ns_all += finfo[16 * f + 8];
+    const int nw_all = ns_all;  // > 0 iff some field stored a word (the column passes below test it)
+    for (int g = tid; g < ns_all; g += NT) {
+      int f = 0, r = g;
+      while (r >= finfo[16 * f + 8]) {
+        r -= finfo[16 * f + 8];
+        ++f;
+      }
       const int* fi = finfo + 16 * f;
-      for (int j = warp; j < fi[6]; j += NWARP) {
+      {
+        int j = 0, hi = fi[6] - 1;
+        while (j < hi) {
+          const int mid = (j + hi + 1) >> 1;
+          if (int(pre_e[f * NW + mid]) + int(pre_i[f * NW + mid]) <= r) j = mid;
+          else hi = mid - 1;
+        }
         const unsigned int word = mw[f * NW + j];
-        if (!((word >> lane) & 1u)) continue;
         const int w = plist[f * NW + j];
+        const int bit = __fns(word, 0, r - int(pre_e[f * NW + j]) - int(pre_i[f * NW + j]) + 1);
         int kx, ky;
         bool valid;
-        word_node<P, E, C::WR>(w, lane, kx, ky, valid);
-        const unsigned int em = word_edges<WV, P, E, C::WR>(w), lt = (1u << lane) - 1u;
+        word_node<P, E, C::WR>(w, bit, kx, ky, valid);
+        const unsigned int em = word_edges<WV, P, E, C::WR>(w), lt = (1u << bit) - 1u;
         T v;
-        if ((em >> lane) & 1u) {
+        if ((em >> bit) & 1u) {
           v = ldr<T>(R + fi[2] + int(pre_e[f * NW + j] + __popc(word & em & lt)) * int(sizeof(T)));
         } else {
           const int idx = pre_i[f * NW + j] + __popc(word & ~em & lt);
