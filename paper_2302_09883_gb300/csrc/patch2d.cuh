@@ -477,7 +477,7 @@ __device__ int ringfree_ghosts(const PatchArgs& a, int pid, T* tiles, T* reg, un
                                T omega, Coll& collide) {
   typedef Cfg<SCH_D2Q9, WV, T, ST, P, L> C;
   typedef typename C::S S;
-  constexpr int F = 9, E = C::E, PW = C::PW, TS = C::TS, NT = C::NT, NWARP = C::NWARP, NC = C::NC, NPW = C::NPW;
+  constexpr int F = 9, E = C::E, PW = C::PW, TS = C::TS, NT = C::NT, NWARP = C::NWARP, NC = C::NC;
   constexpr ConeMask CH = cone_mask<P, L>(P - 1), CL = cone_mask<P, L>(1);
   constexpr int NCN = cone_count(CH);
   static_assert(cone_count(CL) == NCN, "the two border cones mirror each other");
@@ -876,7 +876,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
   typedef typename C::S S;
   constexpr int F = C::F, E = C::E, PW = C::PW, TS = C::TS, NC = C::NC, NW = C::NW, NPW = C::NPW, NB = C::NB,
-                NT = C::NT, NWARP = C::NWARP, NALL = C::NALL;
+                NT = C::NT, NWARP = C::NWARP;
   extern __shared__ __align__(16) unsigned char smem[];
   T* tiles = reinterpret_cast<T*>(smem);
   unsigned int* mw = reinterpret_cast<unsigned int*>(smem + C::OFF_MW);
