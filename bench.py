@@ -872,7 +872,7 @@ def d3q19_section(torch, K, W, flush, bs, n_quality=256, quality_steps=1000, n_t
         return timed_steps(torch, obj, bs, K, flush) / K
 
     n = n_time
-    c = Sim3(n, n, n, P, L, head["eps"], store="bf16", tau=tau, arena_factor=0.05, stream=bs)
+    c = Sim3(n, n, n, P, L, head["eps"], store="bf16", tau=tau, stream=bs)  # automatic arenas
     f = _tgv_device(torch, n)
     c.init_macro(f)
     del f

@@ -107,7 +107,7 @@ typedef struct {
                              encode of a whole state the capacity is set to
                              1.5 x the live record bytes (+ 512 B per
                              patch), synchronising calls keep it between
-                             1.25 x and 5 x the live bytes, and a step whose
+                             1.25 x and 2 x the live bytes, and a step whose
                              records overflowed is re-run with twice the
                              capacity (not with a learned threshold, nor
                              inside a batch) */

@@ -208,7 +208,7 @@ static wcs_status dalloc(wcs_sim* s, void** p, size_t bytes) {
 // capacity follows the measured live bytes: after an encode of a whole
 // state it is set to live + live/2 + 512 B per patch, a synchronising call
 // grows it when the live bytes pass 80 % of it or shrinks it when they fall
-// under 20 %, and a step that overflowed anyway is re-run from its intact
+// under 50 %, and a step that overflowed anyway is re-run from its intact
 // input state with twice the capacity (wcs_sync).
 static unsigned long long arena_headroom(const wcs_sim* s, unsigned long long live) {
   const unsigned long long want = live + live / 2 + (unsigned long long)s->npatch * 512ull;
@@ -915,7 +915,7 @@ wcs_status wcs_sync(wcs_sim* s) {
   if (s->auto_arena && !s->in_batch && s->inited) {  // keep the capacity near the live bytes
     const int cur = int(s->nstep % 2);
     const unsigned long long live = c.cursor[cur];
-    if (live * 5 > s->cap * 4 || (live * 5 < s->cap && s->cap > arena_headroom(s, live)))
+    if (live * 5 > s->cap * 4 || (live * 2 < s->cap && s->cap > arena_headroom(s, live)))
       return resize_arenas(s, arena_headroom(s, live), cur, live);
   }
   return WCS_OK;
