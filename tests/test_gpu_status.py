@@ -55,3 +55,26 @@ def test_finite_state_steps_cleanly():
     g.step(3)
     g.sync()
     assert g.stats()["status"] == 0
+
+
+def test_zero_steps_change_nothing():
+    # the degenerate calls: zero steps (alone and in a batch) and repeated
+    # syncs leave records, step count and FP64 sums as they were
+    from paper_2302_09883_gb300 import Batch
+    n = 128
+    a = Sim("d2q9", "bl53", n, n, 64, 4, 1e-4, prec="f32", store="bf16", tau=0.6)
+    a.init_macro(inputs.shear_wave(n, seed=5))
+    a.step(3)
+    a.sync()
+    recs = [a.record(p) for p in range(a.npatch)]
+    st = a.stats()
+    a.step(0)
+    a.sync()
+    a.sync()
+    b = Batch([a])
+    b.step(0)
+    b.sync()
+    b.close()
+    st2 = a.stats()
+    assert [a.record(p) for p in range(a.npatch)] == recs
+    assert st2["step"] == st["step"] == 3 and np.array_equal(st2["field_sum"], st["field_sum"])
