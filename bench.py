@@ -1148,30 +1148,42 @@ def main():
     h2d = sum(x.nbytes for x in host_f)
     d2h = out.nbytes + K * ((n // w["P"]) ** 2 * 9 * 8 + 88)
 
+    def side(fn, *a, **kw):
+        # a side section that fails reports its error in its own key (the
+        # traceback goes to stderr) instead of taking the headline line down
+        try:
+            return fn(*a, **kw)
+        except Exception as exc:  # noqa: BLE001
+            import traceback
+            traceback.print_exc()
+            torch.cuda.synchronize()
+            return {"error": "%s: %s" % (type(exc).__name__, exc)}
+
     euler = None
     if not args.no_euler:
-        euler = euler_section(torch, K, W, flush, bs, qsteps=None if args.quality_steps is None else args.quality_steps)
+        euler = side(euler_section, torch, K, W, flush, bs,
+                     qsteps=None if args.quality_steps is None else args.quality_steps)
 
     batch = None
     if not args.no_batch:
-        batch = batch_section(torch, K, W, flush, bs)
+        batch = side(batch_section, torch, K, W, flush, bs)
 
     learned_eps = None
     if not args.no_learned:
-        learned_eps = learned_section(torch, K, W, flush, bs)
+        learned_eps = side(learned_section, torch, K, W, flush, bs)
 
     transport = None
     if not args.no_transport:
-        transport = transport_section(torch, K, W, flush, bs)
+        transport = side(transport_section, torch, K, W, flush, bs)
 
     swe = None
     if not args.no_swe:
-        swe = swe_section(torch, bs)
+        swe = side(swe_section, torch, bs)
 
     d3q19 = None
     if not args.no_d3q19:
-        d3q19 = d3q19_section(torch, min(K, 10), W, flush, bs, n_time=args.d3q19_n,
-                              quality_steps=args.quality_steps or 1000)
+        d3q19 = side(d3q19_section, torch, min(K, 10), W, flush, bs, n_time=args.d3q19_n,
+                     quality_steps=args.quality_steps or 1000)
 
     mlups = lu * K * world / (ms * 1e-3) / 1e6
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
