@@ -418,7 +418,9 @@ def transport_section(torch, K, W, flush, bs, levels=(1, 2, 3, 4, 5), thresholds
     return {"workload": "transport_128", "steps": steps, "sweep": sweep, "equal_error_level4": equal_error,
             "timing_level4_capped_c0.01": timing,
             "note": "mean_ratio = uncompressed FP32 bytes of the unique nodes / record bytes (bitmask codec, not "
-                    "the paper's CSR or LZ4); mean_ratio_with_ring also counts the ghost ring and patch table"}
+                    "the paper's CSR or LZ4); mean_ratio_with_ring also counts the patch table (BL5/3 patches "
+                    "keep no ghost ring); mean_value_count_ratio = values of the grid / stored values (coarse "
+                    "samples + kept details)"}
 
 
 def swe_section(torch, bs, patches=(64, 32)):
