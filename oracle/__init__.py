@@ -54,6 +54,9 @@ def lib():
         L.orc_record_bytes.argtypes = [vp, i64]
         L.orc_record.argtypes = [vp, i64, C.c_char_p, i64]
         L.orc_stats.argtypes = [vp, dp]
+        L.orc_set_hilo.argtypes = [vp, i32]
+        L.orc_coarse_lo.argtypes = [vp, C.POINTER(C.c_float)]
+        L.orc_hilo_sums.argtypes = [vp, dp]
         L.orc_ref_create.restype = vp
         L.orc_ref_create.argtypes = [i32, i32, i32, i64, i64, i32, dbl, dbl, dbl]
         L.orc_ref_init_macro.argtypes = [vp, dp, dp, dp, dp]
@@ -132,7 +135,8 @@ class OracleSim:
     """Compressed-patch run (2-D).  Global arrays are (ny_nodes, nx_nodes)."""
 
     def __init__(self, scheme, wavelet, nx, ny, P, L, eps, prec="f64", store="f64", rule="const",
-                 periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, velocity=(0.0, 0.0), gravity=9.81, length=1.0):
+                 periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, velocity=(0.0, 0.0), gravity=9.81, length=1.0,
+                 hilo=False):
         self.scheme, self.wavelet, self.prec = scheme, wavelet, prec
         self.P, self.L = P, L
         pmask = int(periodic[0]) | (int(periodic[1]) << 1)
@@ -143,6 +147,9 @@ class OracleSim:
         if not self.h:
             raise RuntimeError("oracle: " + lib().orc_last_error().decode())
         _check(lib().orc_set_fv(self.h, velocity[0], velocity[1], gravity, length))
+        self.hilo = bool(hilo)
+        if hilo:
+            _check(lib().orc_set_hilo(self.h, 1))
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -214,6 +221,22 @@ class OracleSim:
     @property
     def n_coarse(self):
         return ((self.P >> self.L) + (1 if self.wavelet != "haar" else 0)) ** 2
+
+    def coarse_lo(self):
+        """hi + lo coarse storage: the lo parts of the current state,
+        (npatch, F, NC1^2) float32, sample iy NC1 + ix."""
+        out = np.zeros((self.npatch, self.F, self.n_coarse), np.float32)
+        _check(lib().orc_coarse_lo(self.h, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
+    def hilo_sums(self):
+        """hi + lo: per field the lo parts' share of the coarse-domain mass,
+        the sums of its absolute terms, and the FP64 trapezoid node sums of
+        the state just before its encode."""
+        out = np.zeros(72, np.float64)
+        _check(lib().orc_hilo_sums(self.h, _dp(out)))
+        return {"lo_sums": out[:self.F].copy(), "lo_abs_sums": out[24:24 + self.F].copy(),
+                "pre_sums": out[48:48 + self.F].copy()}
 
 
 class OracleRef:

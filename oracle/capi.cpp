@@ -260,6 +260,44 @@ int orc_rans_freqs(const uint64_t* cnt, uint32_t* f) {
   });
 }
 
+// hi + lo coarse storage (FP32 compute on BL5/3); set before the init.
+int orc_set_hilo(void* p, int on) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    if (h->s64) h->s64->set_hilo(on != 0);
+    else h->s32->set_hilo(on != 0);
+  });
+}
+
+// The lo parts of the current state: npatch x F x NC1^2 floats.
+int orc_coarse_lo(void* p, float* out) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    if (!h->s32 || !h->s32->hilo) throw std::runtime_error("hi + lo coarse storage is off");
+    size_t o = 0;
+    for (const auto& v : h->s32->lo) {
+      if (v.empty()) throw std::runtime_error("patch not encoded with hi + lo");
+      for (float x : v) out[o++] = x;
+    }
+  });
+}
+
+// out[0..F) lo sums, out[24..24+F) their absolute terms, out[48..48+F) the
+// node sums before the last encode.
+int orc_hilo_sums(void* p, double* out) {
+  Handle* h = static_cast<Handle*>(p);
+  return guard([&] {
+    if (!h->s32) throw std::runtime_error("hi + lo coarse storage is off");
+    std::vector<double> a, b, c;
+    h->s32->hilo_sums(a, b, c);
+    for (int f = 0; f < h->s32->F; ++f) {
+      out[f] = a[f];
+      out[24 + f] = b[f];
+      out[48 + f] = c[f];
+    }
+  });
+}
+
 int orc_stats(void* p, double* out) {
   Handle* h = static_cast<Handle*>(p);
   return guard([&] {

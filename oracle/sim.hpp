@@ -192,6 +192,12 @@ template <class T> struct Sim {
   int64_t nstep = 0;
   double time = 0;
   int64_t shared_mismatch = 0;
+  // hi + lo coarse storage (FP32 compute on BL5/3): per patch the lo parts
+  // of the coarse samples (F x NC1^2, field-major, sample iy NC1 + ix) and
+  // the trapezoid node sums of every field just before the encode
+  bool hilo = false;
+  std::vector<std::vector<float>> lo;
+  std::vector<std::vector<double>> pre;
 
   Sim(int scheme, int wavelet, int store_, int rule_, int64_t nx, int64_t ny, int pmask, int P_, int L_,
       double eps_, double tau, double cfl, double gamma)
@@ -224,8 +230,33 @@ template <class T> struct Sim {
   // Global index of local node k of patch p along axis a.
   int64_t gidx(int a, int64_t p, int64_t k) const { return grid.wrap(a, p * P + k); }
 
+  void set_hilo(bool on) {
+    if (on && (sizeof(T) != 4 || grid.wavelet != BL53))
+      throw std::runtime_error("hi + lo coarse storage is for FP32 compute on BL5/3");
+    hilo = on;
+    lo.assign(on ? npatch() : 0, std::vector<float>());
+    pre.assign(on ? npatch() : 0, std::vector<double>());
+  }
+
   void encode_patch_fields(int64_t pid, std::vector<std::vector<T>>& loc) {
+    std::vector<std::vector<double>> c64(hilo ? F : 0);
+    if (hilo) {
+      pre[pid].assign(F, 0.0);
+      for (int f = 0; f < F; ++f) {
+        pre[pid][f] = patch_trapezoid_sum<T>(loc[f].data(), 2, E);
+        c64[f] = coarse_fp64<T>(loc[f].data(), 2, P, L);
+      }
+    }
     for (int f = 0; f < F; ++f) fwd_nd<T>(grid.wavelet, loc[f].data(), 2, P, L);
+    if (hilo) {
+      const int64_t nc1 = (P >> L) + 1, nc = nc1 * nc1;
+      lo[pid].assign(size_t(F * nc), 0.0f);
+      for (int f = 0; f < F; ++f)
+        for (int64_t c = 0; c < nc; ++c) {
+          const T hi = loc[f][((c / nc1) << L) * E + ((c % nc1) << L)];
+          lo[pid][f * nc + c] = float(c64[f][c] - double(hi));
+        }
+    }
     if (track_feat) {
       std::vector<std::vector<double>> c(F);
       for (int f = 0; f < F; ++f) c[f].assign(loc[f].begin(), loc[f].end());
@@ -390,6 +421,34 @@ template <class T> struct Sim {
     }
     if (abs_out) *abs_out = a;
     return s;
+  }
+
+  // hi + lo: per field the lo parts' share of the coarse-domain mass
+  // (2^(2L) times their trapezoid sum, a plain FP64 sum in the order of
+  // coef_sums), the sums of its absolute terms, and the trapezoid node sums
+  // before the last encode (patches in order).
+  void hilo_sums(std::vector<double>& lo_sum, std::vector<double>& lo_abs, std::vector<double>& pre_sum) const {
+    if (!hilo) throw std::runtime_error("hi + lo coarse storage is off");
+    const int64_t nc1 = (P >> L) + 1, nc = nc1 * nc1;
+    const double scale = std::ldexp(1.0, 2 * L);
+    lo_sum.assign(F, 0.0);
+    lo_abs.assign(F, 0.0);
+    pre_sum.assign(F, 0.0);
+    for (int64_t pid = 0; pid < npatch(); ++pid) {
+      if (lo[pid].empty()) throw std::runtime_error("patch not encoded with hi + lo");
+      for (int f = 0; f < F; ++f) {
+        for (int64_t c = 0; c < nc; ++c) {
+          const int64_t iy = c / nc1, ix = c % nc1;
+          double w = 1.0;
+          if (ix == 0 || ix == nc1 - 1) w *= 0.5;
+          if (iy == 0 || iy == nc1 - 1) w *= 0.5;
+          const double term = scale * (w * double(lo[pid][f * nc + c]));
+          lo_sum[f] += term;
+          lo_abs[f] += std::fabs(term);
+        }
+        pre_sum[f] += pre[pid][f];
+      }
+    }
   }
 
   int64_t compressed_bytes() const {

@@ -209,4 +209,59 @@ template <class T> void inv_pyramid2(int wavelet, T* u, int64_t P, int L) {
   }
 }
 
+// ------------------------------------------------ FP64 coarse path (hi + lo)
+// Sec. 2.1.2, eq. conservation: per line, BL5/3 keeps the trapezoid-weighted
+// sum of the nodes in its coarse samples, level by level (2^L times their
+// trapezoid sum), and in tensor form 2^(dims L) times the trapezoid sum of a
+// patch's coarse block is the trapezoid sum of its nodes.  An FP32 transform
+// rounds, so with FP32 coarse samples the identity holds only to about 1e-7
+// of a patch's sum.  With hi + lo coarse storage the coarse block is formed a
+// second time, in FP64, from the same nodes (an FP32 value is exact in FP64),
+// and each FP32 sample hi of the record gets the FP32 part
+// lo = fl32(c64 - hi) that it lacks; hi + lo is c64 to about 2^-48 of hi.
+
+// Trapezoid-weighted FP64 sum of the E^dims nodes of a patch (x fastest):
+// weight 1/2 for every axis on which the node is an end node.
+template <class T> double patch_trapezoid_sum(const T* u, int dims, int64_t E) {
+  int64_t n = 1;
+  for (int a = 0; a < dims; ++a) n *= E;
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double w = 1.0;
+    int64_t r = i;
+    for (int a = 0; a < dims; ++a) {
+      const int64_t k = r % E;
+      r /= E;
+      if (k == 0 || k == E - 1) w *= 0.5;
+    }
+    s += w * double(u[i]);
+  }
+  return s;
+}
+
+// The coarse block ((P/2^L + 1)^dims samples, x fastest) of the FP64 folded
+// BL5/3 forward transform of a patch's nodes.
+template <class T> std::vector<double> coarse_fp64(const T* u, int dims, int64_t P, int L) {
+  const int64_t E = P + 1, nc1 = (P >> L) + 1;
+  int64_t n = 1, nc = 1;
+  for (int a = 0; a < dims; ++a) {
+    n *= E;
+    nc *= nc1;
+  }
+  std::vector<double> d(n);
+  for (int64_t i = 0; i < n; ++i) d[i] = double(u[i]);
+  fwd_nd<double>(BL53, d.data(), dims, P, L);
+  std::vector<double> c(nc);
+  for (int64_t i = 0; i < nc; ++i) {
+    int64_t r = i, pos = 0, st = 1;
+    for (int a = 0; a < dims; ++a) {
+      pos += ((r % nc1) << L) * st;
+      r /= nc1;
+      st *= E;
+    }
+    c[i] = d[pos];
+  }
+  return c;
+}
+
 }  // namespace orc
