@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-d3q19", action="store_true")
     ap.add_argument("--no-transport", action="store_true")
     ap.add_argument("--no-swe", action="store_true")
+    ap.add_argument("--no-hilo", action="store_true")
     ap.add_argument("--d3q19-n", type=int, default=1024, help="D3Q19 timing grid (cells per axis)")
     return ap.parse_args()
 
@@ -755,6 +756,46 @@ def learned_section(torch, K, W, flush, bs, n_eval=1024, steps=1000, deltas=(3e-
             "mlups_learned": n_eval * n_eval / (times["learned"] * 1e-3) / 1e6}
 
 
+def hilo_section(torch, K, W, flush, bs, w, eps, steps=100):
+    """hi + lo coarse storage on the headline configuration (Sec. 2.1.2, eq.
+    conservation).  A state of the headline run (steps steps from its
+    initial fields, decoded to dense FP32 populations) is imported into a
+    simulation with the option on: Check A compares the FP64 coarse-domain
+    mass after that encode (field_sum + field_sum_lo) with the FP64 sum of
+    the imported values, and the FP32 coarse samples alone with the same.
+    Then the step is timed with the option on (W warm-up, K steps, L2
+    flushed before each)."""
+    from paper_2302_09883_gb300 import Sim
+    n = w["n"]
+    s = Sim("d2q9", "bl53", n, n, w["P"], w["L"], eps, prec="f32", store="bf16", tau=w["tau"], stream=bs,
+            coarse_hilo=True)
+    s.init_macro(macro_fields(w))
+    s.step(steps)
+    Fd = torch.empty((9, n, n), dtype=torch.float32, device="cuda")
+    s.export_field(-1, out=Fd, dtype=np.float32)
+    want = Fd.double().sum(dim=(1, 2))
+    scale = Fd.double().abs().sum(dim=(1, 2))
+    s.import_field(-1, Fd)
+    st = s.stats()
+    fs = torch.tensor(st["field_sum"], dtype=torch.float64, device="cuda")
+    fl = torch.tensor(st["field_sum_lo"], dtype=torch.float64, device="cuda")
+    rel = float(((fs + fl - want).abs() / scale).max())
+    rel_hi = float(((fs - want).abs() / scale).max())
+    del Fd
+    s.step(W)
+    torch.cuda.synchronize()
+    ms = timed_steps(torch, s, bs, K, flush) / K
+    s.sync()
+    st = s.stats()
+    out = {"workload": "d2q9_bl53_%d" % n, "eps": eps, "state": "headline run after %d steps, imported" % steps,
+           "check_a_rel": rel, "check_a_rel_hi_only": rel_hi, "check_a_bound": 1e-12,
+           "ms_per_step": ms, "mlups": n * n / (ms * 1e-3) / 1e6,
+           "compression_ratio": st["uncompressed_bytes"] / s.compressed_bytes(),
+           "lo_bytes": s.npatch * 9 * ((w["P"] >> w["L"]) + 1) ** 2 * 4}
+    s.close()
+    return out
+
+
 def _tgv_device(torch, n, u0=0.04):
     return inputs.taylor_green_3d_device(n, u0=u0)
 
@@ -1190,6 +1231,10 @@ def main():
     if not args.no_swe:
         swe = side(swe_section, torch, bs)
 
+    hilo = None
+    if not args.no_hilo:
+        hilo = side(hilo_section, torch, K, W, flush, bs, w, eps)
+
     d3q19 = None
     if not args.no_d3q19:
         d3q19 = side(d3q19_section, torch, min(K, 10), W, flush, bs, n_time=args.d3q19_n,
@@ -1258,6 +1303,7 @@ def main():
             "d3q19": d3q19,
             "transport": transport,
             "swe": swe,
+            "hilo": hilo,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

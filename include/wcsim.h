@@ -116,6 +116,17 @@ typedef struct {
   double gravity;         /* SWE: g (0 = 9.81) */
   double length;          /* FV schemes: side of the square domain, so that
                              h = length / cells and time = sum of dt (0 = 1) */
+  int coarse_hilo;        /* 1: hi + lo coarse storage (Sec. 2.1.2, eq.
+                             conservation; FP32 compute on BL5/3, 2-D): every
+                             encode also forms the coarse block in FP64 from
+                             the same FP32 nodes and keeps, beside each FP32
+                             coarse sample hi of the record, the FP32 part
+                             lo = fl32(c64 - hi) it lacks (wcs_coarse_lo), so
+                             that field_sum + field_sum_lo is the FP64 mass of
+                             the nodes before the encode to about 1e-14
+                             relative; the lo parts count as compressed
+                             bytes.  WCS_E_UNSUPPORTED where no kernel keeps
+                             them.  0: off */
 } wcs_opts;
 
 /* Per-step diagnostics, all reductions in FP64 in a fixed order. */
@@ -138,6 +149,10 @@ typedef struct {
   int64_t arena_capacity;    /* bytes of each of the two record arenas */
   int64_t arena_reruns;      /* steps re-run after an arena overflow (auto
                                 arenas), since creation */
+  double field_sum_lo[19];   /* coarse_hilo: per field the lo parts' share,
+                                2^(2L) times their trapezoid sum (0 when
+                                off); field_sum + field_sum_lo is the FP64
+                                coarse-domain mass */
 } wcs_step_stats;
 
 /* Creates a simulation.  grid: cells per axis; patch: P (power of two,
@@ -229,6 +244,13 @@ wcs_status wcs_stats_collect(wcs_sim* sim, int slot, wcs_step_stats* out);
  * threshold, all patches and fields; coarse samples not counted), counted
  * on the device from the records' tables.  Synchronises; -1 on error. */
 int64_t wcs_survivors(wcs_sim* sim);
+
+/* hi + lo coarse storage (opts.coarse_hilo): copies the lo parts of the
+ * current state into the host buffer out, npatch x nfields x NC1^2 floats
+ * (patch-major, then field, then coarse sample iy NC1 + ix with NC1 =
+ * P/2^L + 1), n = their count.  Synchronises the stream.  WCS_E_ARG if
+ * the option is off, before the init, or for a wrong n. */
+wcs_status wcs_coarse_lo(wcs_sim* sim, float* out, int64_t n);
 
 /* Copies the record of one patch of the current state (the byte format of
  * the oracle) to host memory.  *nbytes receives its size; if cap is too

@@ -32,14 +32,15 @@ class Opts(C.Structure):
     _fields_ = [("wavelet", C.c_int), ("rule", C.c_int), ("detail_store", C.c_int), ("compute", C.c_int),
                 ("tau", C.c_double), ("cfl", C.c_double), ("gamma", C.c_double), ("arena_factor", C.c_double),
                 ("cuda_stream", C.c_void_p), ("velocity", C.c_double * 2), ("gravity", C.c_double),
-                ("length", C.c_double)]
+                ("length", C.c_double), ("coarse_hilo", C.c_int)]
 
 
 class StepStats(C.Structure):
     _fields_ = [("step", C.c_int64), ("time", C.c_double), ("field_sum", C.c_double * 19), ("mass", C.c_double),
                 ("momentum", C.c_double * 3), ("energy", C.c_double), ("smax", C.c_double),
                 ("live_bytes", C.c_int64), ("resident_bytes", C.c_int64), ("uncompressed_bytes", C.c_int64),
-                ("status", C.c_uint32), ("arena_capacity", C.c_int64), ("arena_reruns", C.c_int64)]
+                ("status", C.c_uint32), ("arena_capacity", C.c_int64), ("arena_reruns", C.c_int64),
+                ("field_sum_lo", C.c_double * 19)]
 
 
 _lib = None
@@ -72,6 +73,7 @@ def lib():
         L.wcs_stats_enqueue.argtypes = [vp, i32]
         L.wcs_stats_collect.argtypes = [vp, i32, C.POINTER(StepStats)]
         L.wcs_export_record.argtypes = [vp, i64, vp, i64, C.POINTER(i64)]
+        L.wcs_coarse_lo.argtypes = [vp, C.POINTER(C.c_float), i64]
         L.wcs_shape.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64), C.POINTER(i64)]
         L.wcs_shape3.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64)]
         L.wcs_stream.restype = vp

@@ -8,7 +8,10 @@
 //              for 2-D BL5/3 patches, whose ghosts come from the records)
 //   scratch    3-D kernels: per resident CTA a scratch cube and record buffer
 //   ctl        cursors, max signal speed, time, sticky status
-//   pstats     FP64 coarse-block sums per patch and field
+//   pstats     FP64 coarse-block sums per patch and field (hi + lo coarse
+//              storage: then the lo parts' sums likewise)
+//   coarse_lo  hi + lo coarse storage: per patch and field the FP32 lo parts
+//              of the coarse samples (the records hold the hi parts)
 //   bfactor    threshold multiplier per band (Sec. 2.2)
 #include <cuda_runtime.h>
 
@@ -156,7 +159,9 @@ struct wcs_sim {
   unsigned long long* tab[2] = {nullptr, nullptr};
   void* ring[2] = {nullptr, nullptr};
   wcs::Ctl* ctl = nullptr;
-  double* pstats = nullptr;
+  double* pstats = nullptr;     // npatch x F coarse-block sums (then as many lo sums with hi + lo)
+  bool hilo = false;            // hi + lo coarse storage
+  float* coarse_lo = nullptr;   // npatch x F x nc lo parts
   double* bfactor = nullptr;
   int64_t nstep = 0;
   bool inited = false;
@@ -248,6 +253,8 @@ static wcs::PatchArgs base_args(const wcs_sim* s) {
   a.cap_out = s->cap;
   a.ctl = s->ctl;
   a.pstats = s->pstats;
+  a.coarse_lo = s->hilo ? s->coarse_lo : nullptr;
+  a.pstats_lo = s->hilo ? s->pstats + size_t(s->npatch) * s->F : nullptr;
   a.band_factor = s->bfactor;
   a.eps = s->eps;
   a.eps_edge = s->eps;
@@ -370,6 +377,7 @@ static wcs_status create3(const wcs_grid* grid, int scheme, int patch, int level
     if (grid->n[a] <= 0 || grid->n[a] % patch) return fail(nullptr, WCS_E_ARG, "grid not a multiple of the patch size");
   if ((grid->periodic_mask & 7u) != 7u) return fail(nullptr, WCS_E_ARG, "D3Q19 needs periodic axes");
   if (opts->rule < 0 || opts->rule > 2) return fail(nullptr, WCS_E_ARG, "bad threshold rule");
+  if (opts->coarse_hilo) return fail(nullptr, WCS_E_UNSUPPORTED, "hi + lo coarse storage is compiled for 2-D kernels");
   {
     static std::mutex mu;
     static std::vector<const Kernel3Entry*> prepared;
@@ -610,6 +618,8 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
       opts->cfl > 0)
     return fail(nullptr, WCS_E_ARG, "transport with a CFL time step needs a non-zero velocity");
   if (opts->rule < 0 || opts->rule > 2) return fail(nullptr, WCS_E_ARG, "bad threshold rule");
+  if (opts->coarse_hilo && !ke->hilo)
+    return fail(nullptr, WCS_E_UNSUPPORTED, "hi + lo coarse storage needs FP32 compute on BL5/3 (and room for it)");
 
   {
     static std::mutex mu;
@@ -658,6 +668,7 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
   s->nb = (levels + 1) * (levels + 1);
   s->tsize = s->prec == WCS_FP64 ? 8 : 4;
   s->ring_vals = ke->ring;
+  s->hilo = opts->coarse_hilo != 0;
 
   // ---- threshold multiplier of each band (c_x slowest; Sec. 2.2)
   std::vector<double> bf(s->nb);
@@ -687,7 +698,8 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
     if ((st = dalloc(s, &s->ring[b], size_t(s->npatch) * ke->ring * s->tsize)) != WCS_OK) goto bad;
   }
   if ((st = dalloc(s, (void**)&s->ctl, sizeof(wcs::Ctl))) != WCS_OK) goto bad;
-  if ((st = dalloc(s, (void**)&s->pstats, size_t(s->npatch) * s->F * 8)) != WCS_OK) goto bad;
+  if ((st = dalloc(s, (void**)&s->pstats, size_t(s->npatch) * s->F * 8 * (s->hilo ? 2 : 1))) != WCS_OK) goto bad;
+  if (s->hilo && (st = dalloc(s, (void**)&s->coarse_lo, size_t(s->npatch) * s->F * s->nc * 4)) != WCS_OK) goto bad;
   if ((st = dalloc(s, (void**)&s->bfactor, size_t(s->nb) * 8)) != WCS_OK) goto bad;
   {
     cudaError_t e;
@@ -772,6 +784,7 @@ void wcs_destroy(wcs_sim* s) {
   }
   cudaFree(s->ctl);
   cudaFree(s->pstats);
+  cudaFree(s->coarse_lo);
   cudaFree(s->bfactor);
   cudaFree(s->scratch);
   cudaFree(s->rbuf);
@@ -962,7 +975,8 @@ int64_t wcs_compressed_bytes(const wcs_sim* s) {
   (void)wcs_sync(const_cast<wcs_sim*>(s));
   const int64_t live = live_bytes(s);
   if (live < 0) return -1;
-  return live + int64_t(s->npatch) * s->ring_vals * int64_t(s->tsize) + int64_t(s->npatch) * 8;
+  return live + int64_t(s->npatch) * s->ring_vals * int64_t(s->tsize) + int64_t(s->npatch) * 8 +
+         (s->hilo ? int64_t(s->npatch) * s->F * s->nc * 4 : 0);
 }
 
 int64_t wcs_resident_bytes(const wcs_sim* s) { return s ? s->resident : -1; }
@@ -1085,9 +1099,12 @@ wcs_status wcs_import_field(wcs_sim* s, int field, const void* src, int src_is_d
 static void fill_stats(const wcs_sim* s, const wcs::Ctl& c, const double* ps, int64_t nstep, wcs_step_stats* o) {
   std::memset(o, 0, sizeof(*o));
   for (int f = 0; f < s->F; ++f) {
-    double acc = 0;
+    double acc = 0, acc_lo = 0;
     for (int p = 0; p < s->npatch; ++p) acc += ps[size_t(p) * s->F + f];
+    if (s->hilo)
+      for (int p = 0; p < s->npatch; ++p) acc_lo += ps[size_t(s->npatch + p) * s->F + f];
     o->field_sum[f] = acc;
+    o->field_sum_lo[f] = acc_lo;
   }
   if (s->scheme == WCS_D3Q19) {
     for (int i = 0; i < 19; ++i) {
@@ -1134,7 +1151,7 @@ wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
   CK(cudaStreamSynchronize(s->stream));
   wcs::Ctl c;
   CK(cudaMemcpy(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost));
-  std::vector<double> ps(size_t(s->npatch) * s->F);
+  std::vector<double> ps(size_t(s->npatch) * s->F * (s->hilo ? 2 : 1));
   CK(cudaMemcpy(ps.data(), s->pstats, ps.size() * 8, cudaMemcpyDeviceToHost));
   fill_stats(s, c, ps.data(), s->nstep, o);
   return WCS_OK;
@@ -1143,13 +1160,14 @@ wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
 wcs_status wcs_stats_enqueue(wcs_sim* s, int slot) {
   if (!s || !s->inited || slot < 0 || slot >= wcs_sim::NSTAT) return WCS_E_ARG;
   if (!s->stat_pin) {  // first use: four pinned slots and their events
-    s->stat_slot = (size_t(s->npatch) * s->F * 8 + sizeof(wcs::Ctl) + 255) / 256 * 256;
+    s->stat_slot = (size_t(s->npatch) * s->F * 8 * (s->hilo ? 2 : 1) + sizeof(wcs::Ctl) + 255) / 256 * 256;
     CK(cudaMallocHost(reinterpret_cast<void**>(&s->stat_pin), s->stat_slot * wcs_sim::NSTAT));
     for (int k = 0; k < wcs_sim::NSTAT; ++k) CK(cudaEventCreateWithFlags(&s->stat_ev[k], cudaEventDisableTiming));
   }
   unsigned char* d = s->stat_pin + size_t(slot) * s->stat_slot;
   CK(cudaMemcpyAsync(d, s->ctl, sizeof(wcs::Ctl), cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaMemcpyAsync(d + sizeof(wcs::Ctl), s->pstats, size_t(s->npatch) * s->F * 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(d + sizeof(wcs::Ctl), s->pstats, size_t(s->npatch) * s->F * 8 * (s->hilo ? 2 : 1),
+                     cudaMemcpyDeviceToHost, s->stream));
   CK(cudaEventRecord(s->stat_ev[slot], s->stream));
   s->stat_step[slot] = s->nstep;
   return WCS_OK;
@@ -1163,6 +1181,16 @@ wcs_status wcs_stats_collect(wcs_sim* s, int slot, wcs_step_stats* o) {
   std::memcpy(&c, d, sizeof(c));
   fill_stats(s, c, reinterpret_cast<const double*>(d + sizeof(wcs::Ctl)), s->stat_step[slot], o);
   s->stat_step[slot] = -1;
+  return WCS_OK;
+}
+
+wcs_status wcs_coarse_lo(wcs_sim* s, float* out, int64_t n) {
+  if (!s || !out) return WCS_E_ARG;
+  if (!s->hilo || !s->inited) return fail(s, WCS_E_ARG, "no lo parts (hi + lo coarse storage off, or no state)");
+  if (n != int64_t(s->npatch) * s->F * s->nc) return fail(s, WCS_E_ARG, "wrong count of lo parts");
+  wcs_status st = wcs_sync(s);
+  if (st != WCS_OK) return st;
+  CK(cudaMemcpy(out, s->coarse_lo, size_t(n) * 4, cudaMemcpyDeviceToHost));
   return WCS_OK;
 }
 

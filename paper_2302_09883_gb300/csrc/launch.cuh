@@ -84,6 +84,7 @@ KernelEntry make_entry_lite() {
   k.L = L;
   k.ring = C::RING;
   k.pitch = C::PW;
+  k.hilo = C::HILO ? 1 : 0;
   k.smem = C::SMEM;
   k.threads = C::NT;
   k.launch = &launch_patch<SCH, WV, T, ST, P, L>;
@@ -105,6 +106,7 @@ KernelEntry make_entry() {
   k.L = L;
   k.ring = C::RING;
   k.pitch = C::PW;
+  k.hilo = C::HILO ? 1 : 0;
   k.smem = C::SMEM;
   k.threads = C::NT;
   k.launch = &launch_patch<SCH, WV, T, ST, P, L>;

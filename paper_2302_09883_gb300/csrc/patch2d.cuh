@@ -49,6 +49,8 @@ struct PatchArgs {
   Ctl* ctl;
   int cur_out, cur_rst, smax_rd, smax_wr, smax_rst;
   double* pstats;               // npatch * F coarse-block sums
+  float* coarse_lo;             // hi + lo coarse storage: npatch * F * NC lo parts (null: off)
+  double* pstats_lo;            //   and npatch * F sums of them, scaled like pstats
   const double* band_factor;    // threshold multiplier per band
   double eps, eps_edge;
   const double* eps_patch;      // optional per-patch threshold constant
@@ -135,6 +137,13 @@ template <int SCH, int WV, typename T, int ST, int P, int L> struct Cfg {
   static constexpr size_t STG = (SMEM_MAX - OFF_STAGE) / 16 * 16 > STG_CAP ? STG_CAP : (SMEM_MAX - OFF_STAGE) / 16 * 16;
   static constexpr size_t SMEM = OFF_STAGE + STG;
   static_assert(OFF_STAGE + 4096 <= SMEM_MAX, "patch does not fit in shared memory");
+  // hi + lo coarse storage (FP32 compute on BL5/3): the FP64 row pass keeps
+  // the coarse columns (F NC1 E doubles) at the start of the staging area,
+  // the FP64 coarse block (F NC doubles) sits at its end until the lo parts
+  // are formed
+  static constexpr size_t HILO_BUF = size_t(F) * NC1 * E * 8;
+  static constexpr size_t HILO_C64 = (size_t(F) * NC * 8 + 15) / 16 * 16;
+  static constexpr bool HILO = sizeof(T) == 4 && WV == WV_BL53 && HILO_BUF + HILO_C64 <= STG;
 };
 
 
@@ -871,6 +880,40 @@ __device__ void ringfree_ghosts_fv(const PatchArgs& a, int px, int py, T* tiles,
 }
 
 // The whole patch step for patch `pid` of the simulation described by `a`.
+// hi + lo coarse storage (Sec. 2.1.2, eq. conservation): the coarse block of
+// every field formed a second time, in FP64, from the new FP32 nodes (exact
+// in FP64).  The row pass (x) runs on every row and keeps the values of the
+// coarse columns (buf, [f][ix][y]); the column pass (y) runs on those
+// columns only and leaves the coarse block in c64 ([f][iy NC1 + ix]).  The
+// lifting is the FP32 path's in FP64, so c64 is the FP64 transform of the
+// patch bit for bit.  Out of line: a row of E doubles lives in local memory
+// here, and kernels that keep no lo parts pay only the branch around the call.
+template <int P, int L, int F, int PW, int NT>
+__device__ __noinline__ void coarse_fp64(const float* tiles, const int* woff, double* buf, double* c64) {
+  constexpr int E = P + 1, NC1 = (P >> L) + 1;
+  const int tid = threadIdx.x;
+  for (int t = tid; t < F * E; t += NT) {
+    const int f = t / E, y = t - f * E;
+    const float* row = tiles + woff[f] + y * PW;
+    double v[E];
+#pragma unroll
+    for (int x = 0; x < E; ++x) v[x] = double(row[x]);
+    fwd_levels<WV_BL53, P, 1, L, double>(v);
+#pragma unroll
+    for (int ix = 0; ix < NC1; ++ix) buf[(f * NC1 + ix) * E + y] = v[ix << L];
+  }
+  __syncthreads();
+  for (int t = tid; t < F * NC1; t += NT) {
+    const int f = t / NC1, ix = t - f * NC1;
+    double v[E];
+#pragma unroll
+    for (int y = 0; y < E; ++y) v[y] = buf[(f * NC1 + ix) * E + y];
+    fwd_levels<WV_BL53, P, 1, L, double>(v);
+#pragma unroll
+    for (int iy = 0; iy < NC1; ++iy) c64[(f * NC1 + iy) * NC1 + ix] = v[iy << L];
+  }
+}
+
 template <int SCH, int WV, typename T, int ST, int P, int L, int MODE, int FEAT = 0>
 __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
@@ -1375,6 +1418,18 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
     __syncthreads();
   }
 
+  // ---------------------------- FP64 coarse path (hi + lo coarse storage)
+  constexpr bool HILO = C::HILO && MODE != MODE_EXPORT;
+  const bool hilo = HILO && a.coarse_lo != nullptr;
+  double* c64 = reinterpret_cast<double*>(stage + (C::STG - C::HILO_C64));
+  if constexpr (HILO) {
+    if (hilo) {
+      coarse_fp64<P, L, F, PW, NT>(reinterpret_cast<const float*>(tiles), woff_out, reinterpret_cast<double*>(stage),
+                                   c64);
+      __syncthreads();
+    }
+  }
+
   // ------------------------------------------ forward tensor lifting (x)
   for (int t = tid; t < F * E; t += NT) {
     const int f = t / E, y = t - f * E;
@@ -1709,13 +1764,16 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   constexpr size_t OFF_DSUM = FEAT ? (4096 + size_t(MLP_NP) * 4 + 15) / 16 * 16 : 0;  // behind the FEAT data
   static_assert(F + SUMW < NWARP, "no idle warps for the coarse sums");
   static_assert(OFF_DSUM + size_t(F) * 32 * 8 <= C::STG, "coarse-sum slots do not fit in the staging area");
+  // hi + lo: the lo parts' sums in F x 32 more slots, clear of the FP64 block
+  static_assert(!HILO || OFF_DSUM + size_t(2) * F * 32 * 8 <= C::STG - C::HILO_C64, "lo-sum slots overlap");
   if (warp >= F && warp < F + SUMW) {
     double* ds = reinterpret_cast<double*>(stage + OFF_DSUM);
+    double* dsl = ds + F * 32;
     const int t0 = tid - 32 * F;
     bool bad = false;
     for (int t = t0; t < F * 32; t += 32 * SUMW) {
       const int f = t >> 5;
-      double acc = 0.0;
+      double acc = 0.0, acc_lo = 0.0;
       for (int c = t & 31; c < NC; c += 32) {
         const int iy = c / C::NC1, ix = c - iy * C::NC1;
         double w = 1.0;
@@ -1726,8 +1784,16 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         const T cv = tiles[win_out(f) + (iy << L) * PW + (ix << L)];
         bad = bad || !isfinite(cv);
         acc = acc + w * double(cv);
+        if constexpr (HILO) {
+          if (hilo) {  // lo = fl32(c64 - hi)
+            const float lo = float(c64[f * NC + c] - double(cv));
+            a.coarse_lo[(size_t(pid) * F + f) * NC + c] = lo;
+            acc_lo = acc_lo + w * double(lo);
+          }
+        }
       }
       ds[t] = acc;
+      if (hilo) dsl[t] = acc_lo;
     }
     // A non-finite coefficient anywhere makes a coarse one non-finite: the
     // lifting updates carry every detail into even nodes, level by level,
@@ -1763,6 +1829,7 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   // ----------------------------- encode pass 2: the record, survivors only
   if (warp >= F && warp < F + SUMW) {  // the coarse sums' pairwise levels (slots from the scan phase)
     double* ds = reinterpret_cast<double*>(stage + OFF_DSUM);
+    double* dsl = ds + F * 32;
     const int t0 = tid - 32 * F;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
@@ -1770,10 +1837,12 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       for (int t = t0; t < F * o; t += 32 * SUMW) {
         const int f = t / o, i = t - f * o;
         ds[f * 32 + i] = ds[f * 32 + i] + ds[f * 32 + i + o];
+        if (hilo) dsl[f * 32 + i] = dsl[f * 32 + i] + dsl[f * 32 + i + o];
       }
     }
     asm volatile("bar.sync 1, %0;" ::"n"(32 * SUMW) : "memory");
     if (t0 < F) a.pstats[size_t(pid) * F + t0] = ds[t0 * 32] * double(1ll << (2 * L));
+    if (hilo && t0 < F) a.pstats_lo[size_t(pid) * F + t0] = dsl[t0 * 32] * double(1ll << (2 * L));
   }
   if (tid == 0) stg<uint4>(O, make_uint4((unsigned)misc[1], (unsigned)pid, (unsigned)F, a.flags));
   if (tid < F) {

@@ -14,6 +14,7 @@ struct KernelEntry {
   int pitch;         // shared-memory row pitch (canonical tile offsets)
   size_t smem;       // dynamic shared memory per CTA
   int threads;
+  int hilo;          // keeps hi + lo coarse samples when asked (FP32 compute on BL5/3)
   cudaError_t (*launch)(int mode, const PatchArgs& a, int npatch, cudaStream_t s);
   // step of many simulations: nblocks entries of work, args in device memory
   cudaError_t (*launch_batch)(const PatchArgs* args, const unsigned int* work, int nblocks, cudaStream_t s);

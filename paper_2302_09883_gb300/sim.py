@@ -61,12 +61,13 @@ class Sim:
 
     def __init__(self, scheme, wavelet, nx, ny, P, L, eps, prec="f32", store="bf16", rule="const",
                  periodic=(True, True), tau=0.8, cfl=0.4, gamma=1.4, arena_factor=0.0, stream=None,
-                 velocity=(0.0, 0.0), gravity=9.81, length=1.0):
-        self.scheme = scheme
+                 velocity=(0.0, 0.0), gravity=9.81, length=1.0, coarse_hilo=False):
+        self.scheme, self.P, self.L = scheme, P, L
         o = B.Opts()
         o.wavelet, o.rule, o.detail_store, o.compute = B.WAVELET[wavelet], B.RULE[rule], B.STORE[store], B.PREC[prec]
         o.tau, o.cfl, o.gamma, o.arena_factor = tau, cfl, gamma, arena_factor
         o.velocity[0], o.velocity[1], o.gravity, o.length = velocity[0], velocity[1], gravity, length
+        o.coarse_hilo = int(bool(coarse_hilo))
         o.cuda_stream = _stream_ptr(stream)
         h = C.c_void_p()
         g = _grid(nx, ny, periodic)
@@ -154,7 +155,8 @@ class Sim:
                 "momentum": np.array(s.momentum[:3 if len(self.G) == 3 else 2]), "energy": s.energy, "smax": s.smax,
                 "live_bytes": s.live_bytes, "resident_bytes": s.resident_bytes,
                 "uncompressed_bytes": s.uncompressed_bytes, "status": s.status,
-                "arena_capacity": s.arena_capacity, "arena_reruns": s.arena_reruns}
+                "arena_capacity": s.arena_capacity, "arena_reruns": s.arena_reruns,
+                "field_sum_lo": np.array(s.field_sum_lo[:self.F])}
 
     def stats(self):
         s = B.StepStats()
@@ -171,6 +173,14 @@ class Sim:
         s = B.StepStats()
         B.check(B.lib().wcs_stats_collect(self.h, slot, C.byref(s)), self.h)
         return self._stats_dict(s)
+
+    def coarse_lo(self):
+        """hi + lo coarse storage: the lo parts of the current state,
+        (npatch, F, NC1^2) float32, coarse sample iy NC1 + ix."""
+        nc = ((self.P >> self.L) + 1) ** 2
+        out = np.zeros((self.npatch, self.F, nc), np.float32)
+        B.check(B.lib().wcs_coarse_lo(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), out.size), self.h)
+        return out
 
     def record(self, p):
         n = C.c_int64()
