@@ -793,7 +793,38 @@ def hilo_section(torch, K, W, flush, bs, w, eps, steps=100):
            "compression_ratio": st["uncompressed_bytes"] / s.compressed_bytes(),
            "lo_bytes": s.npatch * 9 * ((w["P"] >> w["L"]) + 1) ** 2 * 4}
     s.close()
+    out["d3q19"] = _hilo_d3q19(torch, K, W, flush, bs)
     return out
+
+
+def _hilo_d3q19(torch, K, W, flush, bs, n=256, steps=20, P=32, L=3, eps=1e-7):
+    """The same for D3Q19 (Taylor-Green vortex, n^3, P 32, L 3, BF16):
+    Check A on an imported state of the run, and the step time with the
+    option on and off."""
+    from paper_2302_09883_gb300 import Sim3
+    res = {"workload": "d3q19_bl53_tgv_%d" % n, "eps": eps}
+    for on in (True, False):
+        s = Sim3(n, n, n, P, L, eps, store="bf16", tau=0.55, stream=bs, coarse_hilo=on)
+        s.init_macro(_tgv_device(torch, n))
+        s.step(steps)
+        if on:
+            Fd = torch.empty((19, n, n, n), dtype=torch.float32, device="cuda")
+            s.export_field(-1, out=Fd, dtype=np.float32)
+            want = Fd.double().sum(dim=(1, 2, 3))
+            scale = Fd.double().abs().sum(dim=(1, 2, 3))
+            s.import_field(-1, Fd)
+            del Fd
+            st = s.stats()
+            fs = torch.tensor(st["field_sum"], dtype=torch.float64, device="cuda")
+            fl = torch.tensor(st["field_sum_lo"], dtype=torch.float64, device="cuda")
+            res["check_a_rel"] = float(((fs + fl - want).abs() / scale).max())
+            res["check_a_rel_hi_only"] = float(((fs - want).abs() / scale).max())
+        s.step(W)
+        torch.cuda.synchronize()
+        res["ms_per_step_hilo" if on else "ms_per_step"] = timed_steps(torch, s, bs, K, flush) / K
+        s.close()
+        torch.cuda.empty_cache()
+    return res
 
 
 def _tgv_device(torch, n, u0=0.04):

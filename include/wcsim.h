@@ -117,7 +117,8 @@ typedef struct {
   double length;          /* FV schemes: side of the square domain, so that
                              h = length / cells and time = sum of dt (0 = 1) */
   int coarse_hilo;        /* 1: hi + lo coarse storage (Sec. 2.1.2, eq.
-                             conservation; FP32 compute on BL5/3, 2-D): every
+                             conservation; FP32 compute on BL5/3, 2-D and
+                             D3Q19): every
                              encode also forms the coarse block in FP64 from
                              the same FP32 nodes and keeps, beside each FP32
                              coarse sample hi of the record, the FP32 part
@@ -150,7 +151,7 @@ typedef struct {
   int64_t arena_reruns;      /* steps re-run after an arena overflow (auto
                                 arenas), since creation */
   double field_sum_lo[19];   /* coarse_hilo: per field the lo parts' share,
-                                2^(2L) times their trapezoid sum (0 when
+                                2^(dims L) times their trapezoid sum (0 when
                                 off); field_sum + field_sum_lo is the FP64
                                 coarse-domain mass */
 } wcs_step_stats;
@@ -246,9 +247,9 @@ wcs_status wcs_stats_collect(wcs_sim* sim, int slot, wcs_step_stats* out);
 int64_t wcs_survivors(wcs_sim* sim);
 
 /* hi + lo coarse storage (opts.coarse_hilo): copies the lo parts of the
- * current state into the host buffer out, npatch x nfields x NC1^2 floats
- * (patch-major, then field, then coarse sample iy NC1 + ix with NC1 =
- * P/2^L + 1), n = their count.  Synchronises the stream.  WCS_E_ARG if
+ * current state into the host buffer out, npatch x nfields x NC1^dims
+ * floats (patch-major, then field, then coarse sample iy NC1 + ix, or
+ * (iz NC1 + iy) NC1 + ix in 3-D, with NC1 = P/2^L + 1), n = their count.  Synchronises the stream.  WCS_E_ARG if
  * the option is off, before the init, or for a wrong n. */
 wcs_status wcs_coarse_lo(wcs_sim* sim, float* out, int64_t n);
 

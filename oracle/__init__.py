@@ -105,6 +105,9 @@ def lib():
         L.orc3_stats.argtypes = [vp, dp]
         L.orc3_set_patch_eps.argtypes = [vp, dp]
         L.orc3_track_features.argtypes = [vp, i32]
+        L.orc3_set_hilo.argtypes = [vp, i32]
+        L.orc3_coarse_lo.argtypes = [vp, C.POINTER(C.c_float)]
+        L.orc3_hilo_sums.argtypes = [vp, dp]
         L.orc3_features.argtypes = [vp, dp]
         L.orc_last_error.restype = C.c_char_p
         _lib = L
@@ -447,12 +450,28 @@ class _Run3:
 class OracleSim3(_Run3):
     """Compressed-patch D3Q19 run on a periodic (nz, ny, nx) grid."""
 
-    def __init__(self, wavelet, nx, ny, nz, P, L, eps, prec="f64", store="f64", rule="const", tau=0.8):
+    def __init__(self, wavelet, nx, ny, nz, P, L, eps, prec="f64", store="f64", rule="const", tau=0.8, hilo=False):
         self.P, self.L, self.shape = P, L, (nz, ny, nx)
         self.h = lib().orc3_create(WAVELET[wavelet], PREC[prec], STORE[store], RULE[rule], nx, ny, nz, P, L, eps,
                                    tau)
         if not self.h:
             raise RuntimeError("oracle: " + lib().orc_last_error().decode())
+        self.hilo = bool(hilo)
+        if hilo:
+            _check(lib().orc3_set_hilo(self.h, 1))
+
+    def coarse_lo(self):
+        """hi + lo: the lo parts, (npatch, 19, NC1^3) float32."""
+        out = np.zeros((self.npatch, 19, ((self.P >> self.L) + 1) ** 3), np.float32)
+        _check(lib().orc3_coarse_lo(self.h, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
+    def hilo_sums(self):
+        """hi + lo: lo sums, their absolute terms, node sums before the last
+        encode (per field)."""
+        out = np.zeros(72, np.float64)
+        _check(lib().orc3_hilo_sums(self.h, _dp(out)))
+        return {"lo_sums": out[:19].copy(), "lo_abs_sums": out[24:43].copy(), "pre_sums": out[48:67].copy()}
 
     @property
     def npatch(self):

@@ -669,6 +669,44 @@ int orc3_stats(void* p, double* out) {
   });
 }
 
+int orc3_set_hilo(void* p, int on) {
+  Handle3* h = static_cast<Handle3*>(p);
+  return guard([&] {
+    if (h->s64) h->s64->set_hilo(on != 0);
+    else if (h->s32) h->s32->set_hilo(on != 0);
+    else throw std::runtime_error("not a compressed run");
+  });
+}
+
+// The lo parts of the current state: npatch x 19 x NC1^3 floats.
+int orc3_coarse_lo(void* p, float* out) {
+  Handle3* h = static_cast<Handle3*>(p);
+  return guard([&] {
+    if (!h->s32 || !h->s32->hilo) throw std::runtime_error("hi + lo coarse storage is off");
+    size_t o = 0;
+    for (const auto& v : h->s32->lo) {
+      if (v.empty()) throw std::runtime_error("patch not encoded with hi + lo");
+      for (float x : v) out[o++] = x;
+    }
+  });
+}
+
+// As orc_hilo_sums: out[0..19) lo sums, out[24..43) absolute terms,
+// out[48..67) node sums before the last encode.
+int orc3_hilo_sums(void* p, double* out) {
+  Handle3* h = static_cast<Handle3*>(p);
+  return guard([&] {
+    if (!h->s32) throw std::runtime_error("hi + lo coarse storage is off");
+    std::vector<double> a, b, c;
+    h->s32->hilo_sums(a, b, c);
+    for (int f = 0; f < 19; ++f) {
+      out[f] = a[f];
+      out[24 + f] = b[f];
+      out[48 + f] = c[f];
+    }
+  });
+}
+
 int orc3_track_features(void* p, int on) {
   Handle3* h = static_cast<Handle3*>(p);
   if (h->s64) h->s64->track_feat = on != 0;

@@ -249,13 +249,9 @@ template <class T> struct Sim {
     }
     for (int f = 0; f < F; ++f) fwd_nd<T>(grid.wavelet, loc[f].data(), 2, P, L);
     if (hilo) {
-      const int64_t nc1 = (P >> L) + 1, nc = nc1 * nc1;
+      const int64_t nc = ((P >> L) + 1) * ((P >> L) + 1);
       lo[pid].assign(size_t(F * nc), 0.0f);
-      for (int f = 0; f < F; ++f)
-        for (int64_t c = 0; c < nc; ++c) {
-          const T hi = loc[f][((c / nc1) << L) * E + ((c % nc1) << L)];
-          lo[pid][f * nc + c] = float(c64[f][c] - double(hi));
-        }
+      for (int f = 0; f < F; ++f) coarse_lo_parts<T>(c64[f], loc[f].data(), 2, P, L, lo[pid].data() + f * nc);
     }
     if (track_feat) {
       std::vector<std::vector<double>> c(F);

@@ -74,6 +74,12 @@ template <class T> struct Sim3 {
   std::vector<std::vector<double>> feat;  // per patch, before the threshold
   int64_t nstep = 0;
   int64_t shared_mismatch = 0;
+  // hi + lo coarse storage (FP32 compute on BL5/3): per patch the lo parts
+  // (19 x NC1^3, sample (iz NC1 + iy) NC1 + ix) and the trapezoid node sums
+  // of every field just before the encode
+  bool hilo = false;
+  std::vector<std::vector<float>> lo;
+  std::vector<std::vector<double>> pre;
 
   Sim3(int wavelet, int store_, int rule_, int64_t nx, int64_t ny, int64_t nz, int P_, int L_, double eps_, double tau)
       : grid(nx, ny, nz, wavelet), P(P_), L(L_), store(store_), rule(rule_), eps(eps_) {
@@ -104,8 +110,29 @@ template <class T> struct Sim3 {
     return grid.id(p[0] * P + x, p[1] * P + y, p[2] * P + z);
   }
 
+  void set_hilo(bool on) {
+    if (on && (sizeof(T) != 4 || grid.wavelet != BL53))
+      throw std::runtime_error("hi + lo coarse storage is for FP32 compute on BL5/3");
+    hilo = on;
+    lo.assign(on ? npatch() : 0, std::vector<float>());
+    pre.assign(on ? npatch() : 0, std::vector<double>());
+  }
+
   void encode_patch_fields(int64_t pid, std::vector<std::vector<T>>& loc) {
+    std::vector<std::vector<double>> c64(hilo ? F : 0);
+    if (hilo) {
+      pre[pid].assign(F, 0.0);
+      for (int f = 0; f < F; ++f) {
+        pre[pid][f] = patch_trapezoid_sum<T>(loc[f].data(), 3, E);
+        c64[f] = coarse_fp64<T>(loc[f].data(), 3, P, L);
+      }
+    }
     for (int f = 0; f < F; ++f) fwd_nd<T>(grid.wavelet, loc[f].data(), 3, P, L);
+    if (hilo) {
+      const int64_t nc1 = (P >> L) + 1, nc = nc1 * nc1 * nc1;
+      lo[pid].assign(size_t(F * nc), 0.0f);
+      for (int f = 0; f < F; ++f) coarse_lo_parts<T>(c64[f], loc[f].data(), 3, P, L, lo[pid].data() + f * nc);
+    }
     if (track_feat) {
       std::vector<std::vector<double>> c(F);
       for (int f = 0; f < F; ++f) c[f].assign(loc[f].begin(), loc[f].end());
@@ -225,6 +252,32 @@ template <class T> struct Sim3 {
     }
     if (abs_out) *abs_out = a;
     return s;
+  }
+
+  // hi + lo: as Sim::hilo_sums with 2^(3L) and the three-axis trapezoid.
+  void hilo_sums(std::vector<double>& lo_sum, std::vector<double>& lo_abs, std::vector<double>& pre_sum) const {
+    if (!hilo) throw std::runtime_error("hi + lo coarse storage is off");
+    const int64_t nc1 = (P >> L) + 1, nc = nc1 * nc1 * nc1;
+    const double scale = std::ldexp(1.0, 3 * L);
+    lo_sum.assign(F, 0.0);
+    lo_abs.assign(F, 0.0);
+    pre_sum.assign(F, 0.0);
+    for (int64_t pid = 0; pid < npatch(); ++pid) {
+      if (lo[pid].empty()) throw std::runtime_error("patch not encoded with hi + lo");
+      for (int f = 0; f < F; ++f) {
+        for (int64_t c = 0; c < nc; ++c) {
+          const int64_t ix = c % nc1, iy = (c / nc1) % nc1, iz = c / (nc1 * nc1);
+          double w = 1.0;
+          if (ix == 0 || ix == nc1 - 1) w *= 0.5;
+          if (iy == 0 || iy == nc1 - 1) w *= 0.5;
+          if (iz == 0 || iz == nc1 - 1) w *= 0.5;
+          const double term = scale * (w * double(lo[pid][f * nc + c]));
+          lo_sum[f] += term;
+          lo_abs[f] += std::fabs(term);
+        }
+        pre_sum[f] += pre[pid][f];
+      }
+    }
   }
 
   int64_t compressed_bytes() const {

@@ -264,4 +264,20 @@ template <class T> std::vector<double> coarse_fp64(const T* u, int dims, int64_t
   return c;
 }
 
+// The lo parts fl32(c64 - hi) of a patch whose FP32 transform u (in place,
+// samples at their node positions) gives the coarse samples hi; c64 from
+// coarse_fp64 of the same nodes.  Sample order as coarse_fp64.
+template <class T> void coarse_lo_parts(const std::vector<double>& c64, const T* u, int dims, int64_t P, int L, float* lo) {
+  const int64_t E = P + 1, nc1 = (P >> L) + 1;
+  for (int64_t i = 0; i < int64_t(c64.size()); ++i) {
+    int64_t r = i, pos = 0, st = 1;
+    for (int a = 0; a < dims; ++a) {
+      pos += ((r % nc1) << L) * st;
+      r /= nc1;
+      st *= E;
+    }
+    lo[i] = float(c64[i] - double(u[pos]));
+  }
+}
+
 }  // namespace orc

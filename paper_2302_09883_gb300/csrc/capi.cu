@@ -162,6 +162,8 @@ struct wcs_sim {
   double* pstats = nullptr;     // npatch x F coarse-block sums (then as many lo sums with hi + lo)
   bool hilo = false;            // hi + lo coarse storage
   float* coarse_lo = nullptr;   // npatch x F x nc lo parts
+  double* hbuf = nullptr;       // 3-D: per resident CTA the FP64 work space of the hi + lo pass
+  unsigned long long hbuf_doubles = 0;
   double* bfactor = nullptr;
   int64_t nstep = 0;
   bool inited = false;
@@ -326,6 +328,10 @@ static wcs::Patch3Args base_args3(const wcs_sim* s) {
   a.cap_out = s->cap;
   a.ctl = s->ctl;
   a.pstats = s->pstats;
+  a.coarse_lo = s->hilo ? s->coarse_lo : nullptr;
+  a.pstats_lo = s->hilo ? s->pstats + size_t(s->npatch) * 19 : nullptr;
+  a.hbuf = s->hbuf;
+  a.hbuf_doubles = s->hbuf_doubles;
   a.band_factor = s->bfactor;
   a.eps = s->eps;
   a.eps_edge = s->eps;
@@ -377,7 +383,6 @@ static wcs_status create3(const wcs_grid* grid, int scheme, int patch, int level
     if (grid->n[a] <= 0 || grid->n[a] % patch) return fail(nullptr, WCS_E_ARG, "grid not a multiple of the patch size");
   if ((grid->periodic_mask & 7u) != 7u) return fail(nullptr, WCS_E_ARG, "D3Q19 needs periodic axes");
   if (opts->rule < 0 || opts->rule > 2) return fail(nullptr, WCS_E_ARG, "bad threshold rule");
-  if (opts->coarse_hilo) return fail(nullptr, WCS_E_UNSUPPORTED, "hi + lo coarse storage is compiled for 2-D kernels");
   {
     static std::mutex mu;
     static std::vector<const Kernel3Entry*> prepared;
@@ -422,6 +427,8 @@ static wcs_status create3(const wcs_grid* grid, int scheme, int patch, int level
   s->tsize = 4;
   s->ring_vals = ke->ring;
   s->grid3 = std::min(s->npatch, nsm);
+  s->hilo = opts->coarse_hilo != 0;
+  s->hbuf_doubles = s->hilo ? (unsigned long long)(s->NC1 * s->E * s->E + s->NC1 * s->NC1 * s->E + s->nc) : 0ull;
   {  // feature groups (l, S): l = the largest axis class, S = the axes of that class
     long long cnt[24] = {0};
     auto cls = [&](int k) { return k % (1 << levels) == 0 ? 0 : __builtin_ctz(unsigned(k)) + 1; };
@@ -467,7 +474,10 @@ static wcs_status create3(const wcs_grid* grid, int scheme, int patch, int level
     if ((st = dalloc(s, &s->ring[b], size_t(s->npatch) * ke->ring * 4)) != WCS_OK) goto bad;
   }
   if ((st = dalloc(s, (void**)&s->ctl, sizeof(wcs::Ctl))) != WCS_OK) goto bad;
-  if ((st = dalloc(s, (void**)&s->pstats, size_t(s->npatch) * 19 * 8)) != WCS_OK) goto bad;
+  if ((st = dalloc(s, (void**)&s->pstats, size_t(s->npatch) * 19 * 8 * (s->hilo ? 2 : 1))) != WCS_OK) goto bad;
+  if (s->hilo && ((st = dalloc(s, (void**)&s->coarse_lo, size_t(s->npatch) * 19 * s->nc * 4)) != WCS_OK ||
+                  (st = dalloc(s, (void**)&s->hbuf, size_t(s->grid3) * s->hbuf_doubles * 8)) != WCS_OK))
+    goto bad;
   if ((st = dalloc(s, (void**)&s->bfactor, size_t(s->nb) * 8)) != WCS_OK) goto bad;
   if ((st = dalloc(s, (void**)&s->scratch, size_t(s->grid3) * ke->slot_floats * 4)) != WCS_OK) goto bad;
   if ((st = dalloc(s, (void**)&s->rbuf, size_t(s->grid3) * ke->slot_rbytes)) != WCS_OK) goto bad;
@@ -725,6 +735,7 @@ wcs_status wcs_sim_use_mlp(wcs_sim* s, wcs_mlp* m, double eps_lo, double eps_hi)
   }
   if (s->dims == 2 && (!s->ke.launch_feat || (s->ke.scheme != WCS_D2Q9 && s->ke.scheme != WCS_EULER2D)))
     return fail(s, WCS_E_UNSUPPORTED, "no learned-threshold kernel for this configuration");
+  if (s->hilo) return fail(s, WCS_E_UNSUPPORTED, "no learned-threshold kernel keeps hi + lo coarse samples");
   const int nin = nfeat(s);
   if (wcs_mlp_nparam(m) != 64 * nin + 64 + 64 * 64 + 64 + 64 + 1)
     return fail(s, WCS_E_ARG, "the network's input size must be " + std::to_string(nin) +
@@ -785,6 +796,7 @@ void wcs_destroy(wcs_sim* s) {
   cudaFree(s->ctl);
   cudaFree(s->pstats);
   cudaFree(s->coarse_lo);
+  cudaFree(s->hbuf);
   cudaFree(s->bfactor);
   cudaFree(s->scratch);
   cudaFree(s->rbuf);
@@ -1279,6 +1291,11 @@ wcs_status wcs_batch_create(wcs_sim* const* sims, int nsims, wcs_batch** out) {
       g_create_err = "batch: every simulation must be initialised, share one stream and be at the same step";
       batch_free(b);
       return WCS_E_ARG;
+    }
+    if (s->hilo) {
+      g_create_err = "batch: no batch kernel keeps hi + lo coarse samples";
+      batch_free(b);
+      return WCS_E_UNSUPPORTED;
     }
     if (s->dims != 2) {
       g_create_err = "batch: 3-D simulations are stepped alone";

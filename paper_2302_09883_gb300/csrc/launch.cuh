@@ -5,6 +5,21 @@
 
 namespace wcs {
 
+// hi + lo coarse storage: INIT and STEP kernels of their own (HL = 1)
+template <int SCH, int WV, typename T, int ST, int P, int L>
+cudaError_t prepare_hilo() {
+  typedef Cfg<SCH, WV, T, ST, P, L> C;
+  if constexpr (C::HILO) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_INIT, 0, 1>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM))) != cudaSuccess)
+      return e;
+    return cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_STEP, 0, 1>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
+  }
+  return cudaSuccess;
+}
+
 template <int SCH, int WV, typename T, int ST, int P, int L>
 cudaError_t prepare_patch() {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
@@ -21,6 +36,7 @@ cudaError_t prepare_patch() {
   if ((e = cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_STEP, 1>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM))) != cudaSuccess)
     return e;
+  if ((e = prepare_hilo<SCH, WV, T, ST, P, L>()) != cudaSuccess) return e;
   return cudaFuncSetAttribute(patch_kernel_batch<SCH, WV, T, ST, P, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(C::SMEM));
 }
@@ -30,6 +46,7 @@ template <int SCH, int WV, typename T, int ST, int P, int L>
 cudaError_t launch_feat(const PatchArgs& a, int npatch, cudaStream_t s) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
   if (npatch <= 0) return cudaSuccess;
+  if (a.coarse_lo) return cudaErrorInvalidValue;  // no learned-threshold kernel keeps hi + lo
   patch_kernel<SCH, WV, T, ST, P, L, MODE_STEP, 1><<<npatch, C::NT, C::SMEM, s>>>(a);
   return cudaGetLastError();
 }
@@ -37,10 +54,16 @@ cudaError_t launch_feat(const PatchArgs& a, int npatch, cudaStream_t s) {
 template <int SCH, int WV, typename T, int ST, int P, int L, int MODE>
 cudaError_t launch_mode(const PatchArgs& a, int npatch, cudaStream_t s) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
-  patch_kernel<SCH, WV, T, ST, P, L, MODE><<<npatch, C::NT, C::SMEM, s>>>(a);
+  if (a.coarse_lo && MODE != MODE_EXPORT) {  // hi + lo coarse storage
+    if constexpr (C::HILO && MODE != MODE_EXPORT) patch_kernel<SCH, WV, T, ST, P, L, MODE, 0, 1><<<npatch, C::NT, C::SMEM, s>>>(a);
+    else return cudaErrorInvalidValue;
+  } else {
+    patch_kernel<SCH, WV, T, ST, P, L, MODE><<<npatch, C::NT, C::SMEM, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
+// (batches take no simulation with hi + lo coarse storage: wcs_batch_create)
 template <int SCH, int WV, typename T, int ST, int P, int L>
 cudaError_t launch_batch(const PatchArgs* args, const unsigned int* work, int nblocks, cudaStream_t s) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
@@ -68,6 +91,7 @@ cudaError_t prepare_patch_lite() {
   if ((e = cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(C::SMEM))) != cudaSuccess)
     return e;
+  if ((e = prepare_hilo<SCH, WV, T, ST, P, L>()) != cudaSuccess) return e;
   return cudaFuncSetAttribute(patch_kernel<SCH, WV, T, ST, P, L, MODE_EXPORT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(C::SMEM));
 }

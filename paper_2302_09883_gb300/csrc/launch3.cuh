@@ -17,6 +17,12 @@ template <int ST, int P, int L> cudaError_t prepare3() {
   if ((e = cudaFuncSetAttribute(patch3_kernel<WV_BL53, ST, P, L, MODE_STEP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(C::SMEM_FEAT))) != cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(patch3_kernel<WV_BL53, ST, P, L, MODE_INIT, 0, 1>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM))) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(patch3_kernel<WV_BL53, ST, P, L, MODE_STEP, 0, 1>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM))) != cudaSuccess)
+    return e;
   return cudaFuncSetAttribute(patch3_kernel<WV_BL53, ST, P, L, MODE_EXPORT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               int(C::SMEM));
 }
@@ -26,6 +32,7 @@ template <int ST, int P, int L> cudaError_t prepare3() {
 template <int ST, int P, int L> cudaError_t launch3_feat(const Patch3Args& a, int grid, cudaStream_t s) {
   typedef Cfg3<P, L, ST> C;
   if (grid <= 0) return cudaSuccess;
+  if (a.coarse_lo) return cudaErrorInvalidValue;  // no learned-threshold kernel keeps hi + lo
   patch3_kernel<WV_BL53, ST, P, L, MODE_STEP, 1><<<grid, C::NT, C::SMEM_FEAT, s>>>(a);
   return cudaGetLastError();
 }
@@ -33,7 +40,10 @@ template <int ST, int P, int L> cudaError_t launch3_feat(const Patch3Args& a, in
 template <int ST, int P, int L> cudaError_t launch3(int mode, const Patch3Args& a, int grid, cudaStream_t s) {
   typedef Cfg3<P, L, ST> C;
   if (grid <= 0) return cudaSuccess;
-  if (mode == MODE_INIT) patch3_kernel<WV_BL53, ST, P, L, MODE_INIT><<<grid, C::NT, C::SMEM, s>>>(a);
+  const bool hl = a.coarse_lo != nullptr;  // hi + lo coarse storage: kernels of their own
+  if (mode == MODE_INIT && hl) patch3_kernel<WV_BL53, ST, P, L, MODE_INIT, 0, 1><<<grid, C::NT, C::SMEM, s>>>(a);
+  else if (mode == MODE_INIT) patch3_kernel<WV_BL53, ST, P, L, MODE_INIT><<<grid, C::NT, C::SMEM, s>>>(a);
+  else if (mode == MODE_STEP && hl) patch3_kernel<WV_BL53, ST, P, L, MODE_STEP, 0, 1><<<grid, C::NT, C::SMEM, s>>>(a);
   else if (mode == MODE_STEP) patch3_kernel<WV_BL53, ST, P, L, MODE_STEP><<<grid, C::NT, C::SMEM, s>>>(a);
   else patch3_kernel<WV_BL53, ST, P, L, MODE_EXPORT><<<grid, C::NT, C::SMEM, s>>>(a);
   return cudaGetLastError();

@@ -914,7 +914,7 @@ __device__ __noinline__ void coarse_fp64(const float* tiles, const int* woff, do
   }
 }
 
-template <int SCH, int WV, typename T, int ST, int P, int L, int MODE, int FEAT = 0>
+template <int SCH, int WV, typename T, int ST, int P, int L, int MODE, int FEAT = 0, int HL = 0>
 __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   typedef Cfg<SCH, WV, T, ST, P, L> C;
   typedef typename C::S S;
@@ -1419,15 +1419,14 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   }
 
   // ---------------------------- FP64 coarse path (hi + lo coarse storage)
-  constexpr bool HILO = C::HILO && MODE != MODE_EXPORT;
-  const bool hilo = HILO && a.coarse_lo != nullptr;
+  // (its own kernel instantiations, HL = 1: the others stay as they are)
+  constexpr bool HILO = C::HILO && HL != 0 && MODE != MODE_EXPORT;
+  static_assert(HL == 0 || HILO, "no hi + lo kernel for this configuration");
   double* c64 = reinterpret_cast<double*>(stage + (C::STG - C::HILO_C64));
   if constexpr (HILO) {
-    if (hilo) {
-      coarse_fp64<P, L, F, PW, NT>(reinterpret_cast<const float*>(tiles), woff_out, reinterpret_cast<double*>(stage),
-                                   c64);
-      __syncthreads();
-    }
+    coarse_fp64<P, L, F, PW, NT>(reinterpret_cast<const float*>(tiles), woff_out, reinterpret_cast<double*>(stage),
+                                 c64);
+    __syncthreads();
   }
 
   // ------------------------------------------ forward tensor lifting (x)
@@ -1784,16 +1783,14 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
         const T cv = tiles[win_out(f) + (iy << L) * PW + (ix << L)];
         bad = bad || !isfinite(cv);
         acc = acc + w * double(cv);
-        if constexpr (HILO) {
-          if (hilo) {  // lo = fl32(c64 - hi)
-            const float lo = float(c64[f * NC + c] - double(cv));
-            a.coarse_lo[(size_t(pid) * F + f) * NC + c] = lo;
-            acc_lo = acc_lo + w * double(lo);
-          }
+        if constexpr (HILO) {  // lo = fl32(c64 - hi)
+          const float lo = float(c64[f * NC + c] - double(cv));
+          a.coarse_lo[(size_t(pid) * F + f) * NC + c] = lo;
+          acc_lo = acc_lo + w * double(lo);
         }
       }
       ds[t] = acc;
-      if (hilo) dsl[t] = acc_lo;
+      if constexpr (HILO) dsl[t] = acc_lo;
     }
     // A non-finite coefficient anywhere makes a coarse one non-finite: the
     // lifting updates carry every detail into even nodes, level by level,
@@ -1837,12 +1834,13 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
       for (int t = t0; t < F * o; t += 32 * SUMW) {
         const int f = t / o, i = t - f * o;
         ds[f * 32 + i] = ds[f * 32 + i] + ds[f * 32 + i + o];
-        if (hilo) dsl[f * 32 + i] = dsl[f * 32 + i] + dsl[f * 32 + i + o];
+        if constexpr (HILO) dsl[f * 32 + i] = dsl[f * 32 + i] + dsl[f * 32 + i + o];
       }
     }
     asm volatile("bar.sync 1, %0;" ::"n"(32 * SUMW) : "memory");
     if (t0 < F) a.pstats[size_t(pid) * F + t0] = ds[t0 * 32] * double(1ll << (2 * L));
-    if (hilo && t0 < F) a.pstats_lo[size_t(pid) * F + t0] = dsl[t0 * 32] * double(1ll << (2 * L));
+    if constexpr (HILO)
+      if (t0 < F) a.pstats_lo[size_t(pid) * F + t0] = dsl[t0 * 32] * double(1ll << (2 * L));
   }
   if (tid == 0) stg<uint4>(O, make_uint4((unsigned)misc[1], (unsigned)pid, (unsigned)F, a.flags));
   if (tid < F) {
@@ -2033,9 +2031,9 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
 }
 
 // One simulation: block b is patch b.
-template <int SCH, int WV, typename T, int ST, int P, int L, int MODE, int FEAT = 0>
+template <int SCH, int WV, typename T, int ST, int P, int L, int MODE, int FEAT = 0, int HL = 0>
 __global__ void __launch_bounds__(Cfg<SCH, WV, T, ST, P, L>::NT, Cfg<SCH, WV, T, ST, P, L>::MINB) patch_kernel(PatchArgs a) {
-  patch_body<SCH, WV, T, ST, P, L, MODE, FEAT>(a, int(blockIdx.x));
+  patch_body<SCH, WV, T, ST, P, L, MODE, FEAT, HL>(a, int(blockIdx.x));
 }
 
 // Many simulations in one launch: block b steps patch (work[b] & 0xfffff) of

@@ -132,6 +132,10 @@ struct Patch3Args {
   Ctl* ctl;
   int cur_out, cur_rst;
   double* pstats;             // npatch * 19 coarse-block sums
+  float* coarse_lo;           // hi + lo coarse storage: npatch * 19 * NC lo parts (null: off)
+  double* pstats_lo;          //   npatch * 19 sums of them, scaled like pstats
+  double* hbuf;               //   per CTA: hbuf_doubles of FP64 work space
+  unsigned long long hbuf_doubles;
   const double* band_factor;  // threshold multiplier per band
   double eps, eps_edge;
   const double* eps_patch;    // optional per-patch threshold constant
@@ -290,9 +294,54 @@ __device__ __forceinline__ void block_scan3(unsigned int& a, unsigned int& b, un
   __syncthreads();
 }
 
+// hi + lo coarse storage (Sec. 2.1.2, eq. conservation): the coarse block of
+// one field formed a second time, in FP64, from its FP32 nodes in the tile
+// ([z][y][x]); the x pass on every line keeps the coarse-x values (hb,
+// [ix][z][y]), the y pass on those keeps the coarse-y ones (hb + NC1 E^2,
+// [ix][iy][z]), the z pass leaves the block in c64 ([iz][iy][ix]).  The
+// FP32 path's lifting in FP64, so the oracle's FP64 transform bit for bit.
+// hb lives in global memory (a few tens of KB per CTA, L2-resident); all
+// threads of the block call this.
+template <int P, int L, int NT>
+__device__ __noinline__ void coarse3_fp64(const float* tile, double* hb, double* c64) {
+  constexpr int E = P + 1, E2 = E * E, NC1 = (P >> L) + 1;
+  const int tid = threadIdx.x;
+  double* hb2 = hb + NC1 * E2;
+  for (int l = tid; l < E2; l += NT) {
+    const int z = l / E, y = l - z * E;
+    double v[E];
+#pragma unroll
+    for (int x = 0; x < E; ++x) v[x] = double(tile[z * E2 + y * E + x]);
+    fwd_levels<WV_BL53, P, 1, L, double>(v);
+#pragma unroll
+    for (int ix = 0; ix < NC1; ++ix) hb[(ix * E + z) * E + y] = v[ix << L];
+  }
+  __syncthreads();
+  for (int t = tid; t < NC1 * E; t += NT) {
+    const int ix = t / E, z = t - ix * E;
+    double v[E];
+#pragma unroll
+    for (int y = 0; y < E; ++y) v[y] = hb[(ix * E + z) * E + y];
+    fwd_levels<WV_BL53, P, 1, L, double>(v);
+#pragma unroll
+    for (int iy = 0; iy < NC1; ++iy) hb2[(ix * NC1 + iy) * E + z] = v[iy << L];
+  }
+  __syncthreads();
+  for (int t = tid; t < NC1 * NC1; t += NT) {
+    const int ix = t / NC1, iy = t - ix * NC1;
+    double v[E];
+#pragma unroll
+    for (int z = 0; z < E; ++z) v[z] = hb2[(ix * NC1 + iy) * E + z];
+    fwd_levels<WV_BL53, P, 1, L, double>(v);
+#pragma unroll
+    for (int iz = 0; iz < NC1; ++iz) c64[(iz * NC1 + iy) * NC1 + ix] = v[iz << L];
+  }
+  __syncthreads();
+}
+
 // One patch (pid) of one launch.  MODE_INIT encodes the equilibrium of the
 // macroscopic fields, MODE_STEP advances one step, MODE_EXPORT decodes.
-template <int WV, int ST, int P, int L, int MODE, int FEAT = 0>
+template <int WV, int ST, int P, int L, int MODE, int FEAT = 0, int HL = 0>
 __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned char* Rb, unsigned char* smem) {
   typedef Cfg3<P, L, ST> C;
   typedef float T;
@@ -321,6 +370,11 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
     return (node_class<L>(x) * (L + 1) + node_class<L>(y)) * (L + 1) + node_class<L>(z);
   };
   const T omega = a.omega;
+  // hi + lo coarse storage (kernels of their own, HL = 1): this CTA's FP64
+  // work space, the FP64 coarse block of the field being encoded at its end
+  constexpr bool hilo = HL != 0 && MODE != MODE_EXPORT;
+  double* hb = hilo ? a.hbuf + size_t(blockIdx.x) * a.hbuf_doubles : nullptr;
+  double* c64 = hilo ? hb + (C::NC1 * E2 + C::NC1 * C::NC1 * E) : nullptr;
 
   // lifting of every line of the tile along one axis (0 x, 1 y, 2 z)
   auto lines = [&](int axis, bool inverse) {
@@ -551,6 +605,7 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
     for (int w = tid; w < NW; w += NT) mw[w] = 0u;
     if (tid < NB) bmax[tid] = 0u;
     __syncthreads();
+    if constexpr (hilo) coarse3_fp64<P, L, NT>(tile, hb, c64);
     lines(0, false);
     lines(1, false);
     // forward z lifting fused with the threshold (Sec. 2.2)
@@ -756,6 +811,22 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) acc = acc + __shfl_down_sync(0xffffffffu, acc, o);
       if (lane == 0 && MODE != MODE_EXPORT) a.pstats[size_t(pid) * F + f] = acc * double(1ll << (3 * L));
+      if constexpr (hilo) {  // lo = fl32(c64 - hi) and its share of the mass
+        double acc_lo = 0.0;
+        for (int c = lane; c < NC; c += 32) {
+          const int ix = c % C::NC1, iy = (c / C::NC1) % C::NC1, iz = c / (C::NC1 * C::NC1);
+          double w = 1.0;
+          if (ix == 0 || ix == C::NC1 - 1) w *= 0.5;
+          if (iy == 0 || iy == C::NC1 - 1) w *= 0.5;
+          if (iz == 0 || iz == C::NC1 - 1) w *= 0.5;
+          const float lo = float(c64[c] - double(tile[((iz << L) * E + (iy << L)) * E + (ix << L)]));
+          a.coarse_lo[(size_t(pid) * F + f) * NC + c] = lo;
+          acc_lo = acc_lo + w * double(lo);
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) acc_lo = acc_lo + __shfl_down_sync(0xffffffffu, acc_lo, o);
+        if (lane == 0) a.pstats_lo[size_t(pid) * F + f] = acc_lo * double(1ll << (3 * L));
+      }
     }
     if constexpr (C::QUANT) {
       if (tid == 0) {
@@ -963,7 +1034,7 @@ __device__ void patch3_body(const Patch3Args& a, int pid, float* Sc, unsigned ch
 
 // Persistent launch: CTA b takes patches b, b + grid, ... with its own
 // scratch slot.
-template <int WV, int ST, int P, int L, int MODE, int FEAT = 0>
+template <int WV, int ST, int P, int L, int MODE, int FEAT = 0, int HL = 0>
 __global__ void __launch_bounds__(1024, 1) patch3_kernel(const Patch3Args a) {
   extern __shared__ __align__(16) unsigned char smem3[];
   const int np = a.npx * a.npy * a.npz;
@@ -989,7 +1060,7 @@ __global__ void __launch_bounds__(1024, 1) patch3_kernel(const Patch3Args a) {
     }
     __syncthreads();
   }
-  for (int pid = blockIdx.x; pid < np; pid += gridDim.x) patch3_body<WV, ST, P, L, MODE, FEAT>(a, pid, Sc, Rb, smem3);
+  for (int pid = blockIdx.x; pid < np; pid += gridDim.x) patch3_body<WV, ST, P, L, MODE, FEAT, HL>(a, pid, Sc, Rb, smem3);
 }
 
 }  // namespace wcs

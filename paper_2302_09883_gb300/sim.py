@@ -176,8 +176,9 @@ class Sim:
 
     def coarse_lo(self):
         """hi + lo coarse storage: the lo parts of the current state,
-        (npatch, F, NC1^2) float32, coarse sample iy NC1 + ix."""
-        nc = ((self.P >> self.L) + 1) ** 2
+        (npatch, F, NC1^dims) float32, coarse sample iy NC1 + ix (3-D:
+        (iz NC1 + iy) NC1 + ix)."""
+        nc = ((self.P >> self.L) + 1) ** len(self.G)
         out = np.zeros((self.npatch, self.F, nc), np.float32)
         B.check(B.lib().wcs_coarse_lo(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), out.size), self.h)
         return out
@@ -198,11 +199,13 @@ class Sim3(Sim):
     """One compressed-patch D3Q19 simulation on a periodic (nz, ny, nx) grid
     (folded BL5/3, FP32 compute)."""
 
-    def __init__(self, nx, ny, nz, P, L, eps, store="bf16", rule="const", tau=0.8, arena_factor=0.0, stream=None):
-        self.scheme = "d3q19"
+    def __init__(self, nx, ny, nz, P, L, eps, store="bf16", rule="const", tau=0.8, arena_factor=0.0, stream=None,
+                 coarse_hilo=False):
+        self.scheme, self.P, self.L = "d3q19", P, L
         o = B.Opts()
         o.wavelet, o.rule, o.detail_store, o.compute = B.WAVELET["bl53"], B.RULE[rule], B.STORE[store], B.PREC["f32"]
         o.tau, o.arena_factor = tau, arena_factor
+        o.coarse_hilo = int(bool(coarse_hilo))
         o.cuda_stream = _stream_ptr(stream)
         g = B.Grid()
         g.dims = 3

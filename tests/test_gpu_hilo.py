@@ -106,3 +106,34 @@ def test_hilo_needs_a_kernel_that_keeps_it():
     g.init_macro(inputs.shear_wave(128))
     with pytest.raises(RuntimeError):  # the option is off
         g.coarse_lo()
+
+
+def test_hilo_d3q19_bitwise_and_check_a():
+    """D3Q19, 64^3, P 32, L 3, BF16 details: records unchanged by the option
+    and equal to the oracle's, lo parts bit for bit, Check A at the initial
+    encode and after each of two steps."""
+    from paper_2302_09883_gb300 import Sim3
+    n = 64
+    g = Sim3(n, n, n, 32, 3, 1e-6, store="bf16", tau=0.55, coarse_hilo=True)
+    ref = Sim3(n, n, n, 32, 3, 1e-6, store="bf16", tau=0.55)
+    o = O.OracleSim3("bl53", n, n, n, 32, 3, 1e-6, prec="f32", store="bf16", tau=0.55, hilo=True)
+    f = inputs.taylor_green_3d(n)
+    for s in (g, ref, o):
+        s.init_macro(f)
+    worst_hi = 0.0
+    for k in range(3):
+        if k:
+            for s in (g, ref, o):
+                s.step(1)
+        g.sync()
+        ref.sync()
+        for p in range(g.npatch):
+            rg = g.record(p)
+            assert rg == o.record(p) and rg == ref.record(p), (p, k)
+        assert np.array_equal(g.coarse_lo().view(np.uint32), o.coarse_lo().view(np.uint32)), k
+        st, ost, h = g.stats(), o.stats(), o.hilo_sums()
+        scale = ost["coef_abs_sums"] + h["lo_abs_sums"]
+        assert np.all(np.abs(st["field_sum_lo"] - h["lo_sums"]) <= 1e-15 * scale)
+        assert np.all(np.abs(st["field_sum"] + st["field_sum_lo"] - h["pre_sums"]) <= 1e-12 * scale), k
+        worst_hi = max(worst_hi, float(np.max(np.abs(st["field_sum"] - h["pre_sums"]) / scale)))
+    assert worst_hi > 1e-12

@@ -108,3 +108,23 @@ def test_hilo_needs_fp32_bl53():
         O.OracleSim("d2q9", "bl53", N, N, P, L, 1e-4, prec="f64", store="f64", hilo=True)
     with pytest.raises(RuntimeError):
         O.OracleSim("d2q9", "haar", N, N, P, L, 1e-4, prec="f32", store="f32", hilo=True)
+
+
+def test_check_a_d3q19():
+    """The same in three dimensions (2^(3L) times the trapezoid sum over the
+    three axes): D3Q19, 64^3, P 32, L 3, BF16 details, the initial encode
+    and two steps."""
+    n = 64
+    s = O.OracleSim3("bl53", n, n, n, 32, 3, 1e-6, prec="f32", store="bf16", tau=0.55, hilo=True)
+    s.init_macro(inputs.taylor_green_3d(n))
+    worst_hi = 0.0
+    for k in range(3):
+        st, h = s.stats(), s.hilo_sums()
+        scale = st["coef_abs_sums"] + h["lo_abs_sums"]
+        assert np.all(np.abs(st["coef_sums"] + h["lo_sums"] - h["pre_sums"]) <= 1e-12 * scale), k
+        worst_hi = max(worst_hi, float(np.max(np.abs(st["coef_sums"] - h["pre_sums"]) / scale)))
+        lo = s.coarse_lo()
+        assert 0.0 < np.max(np.abs(lo)) <= 2.0 ** -19 * (1.0 / 3.0) * 1.2
+        if k < 2:
+            s.step(1)
+    assert worst_hi > 1e-12
