@@ -160,9 +160,19 @@ typedef struct {
  * P/2^levels >= 2 for BL5/3); levels: L >= 1; eps: threshold constant c of
  * Sec. 2.2 (0 = lossless up to rounding).  Allocates all device memory.
  * Returns WCS_E_UNSUPPORTED if no kernel was compiled for the combination
- * (scheme, wavelet, compute, detail_store, P, L). */
+ * (scheme, wavelet, compute, detail_store, P, L).  patch = 0 and/or
+ * levels = 0: chosen by the patch autotuner (wcs_autotune) in
+ * wcs_init_macro, on the caller's initial fields, among the compiled
+ * kernels of the configuration whose P divides every axis (and that match
+ * the non-zero one); nothing is allocated before, the simulation must then
+ * start from wcs_init_macro, and wcs_patch_config tells the choice.
+ * WCS_E_UNSUPPORTED if no compiled kernel fits. */
 wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int levels, double eps,
                           const wcs_opts* opts, wcs_sim** out);
+
+/* The simulation's patch size and levels (0 while a choice deferred to
+ * wcs_init_macro is pending). */
+wcs_status wcs_patch_config(const wcs_sim* sim, int* patch, int* levels);
 
 /* Frees everything the simulation holds.  NULL is accepted. */
 void wcs_destroy(wcs_sim* sim);
@@ -334,7 +344,7 @@ wcs_status wcs_batch_launches_per_step(const wcs_batch* b, int* launches, int* g
 wcs_status wcs_batch_tune_launch(wcs_batch* b, const int* grids, int ncand, int steps, double* ms_per_step);
 const char* wcs_batch_last_error(const wcs_batch* b);
 
-/* Patch-size autotuner: for each candidate (P[i], levels L[i]) creates a
+/* Patch-size autotuner (2-D and D3Q19): for each candidate (P[i], levels L[i]) creates a
  * simulation on the caller's initial fields (layout of wcs_init_macro),
  * times `steps` steps with CUDA events and writes the index of the fastest
  * to *best (and the per-step times to ms_per_step[ncand] if not NULL).

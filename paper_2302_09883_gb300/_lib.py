@@ -74,6 +74,7 @@ def lib():
         L.wcs_stats_collect.argtypes = [vp, i32, C.POINTER(StepStats)]
         L.wcs_export_record.argtypes = [vp, i64, vp, i64, C.POINTER(i64)]
         L.wcs_coarse_lo.argtypes = [vp, C.POINTER(C.c_float), i64]
+        L.wcs_patch_config.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.wcs_shape.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64), C.POINTER(i64)]
         L.wcs_shape3.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64)]
         L.wcs_stream.restype = vp

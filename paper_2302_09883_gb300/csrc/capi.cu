@@ -182,6 +182,12 @@ struct wcs_sim {
   size_t stat_slot = 0;
   cudaEvent_t stat_ev[NSTAT] = {nullptr, nullptr, nullptr, nullptr};
   int64_t stat_step[NSTAT] = {-1, -1, -1, -1};
+  // created with patch 0 or levels 0: nothing allocated yet; wcs_init_macro
+  // picks the configuration (autotuner) and creates the simulation
+  bool deferred = false;
+  wcs_grid g0{};
+  wcs_opts o0{};
+  int req_P = 0, req_L = 0;
 };
 
 static wcs_status fail(wcs_sim* s, wcs_status st, const std::string& msg) {
@@ -366,6 +372,87 @@ static wcs::Patch3Args step_args3(const wcs_sim* s, int64_t k) {
 }
 
 void wcs_destroy(wcs_sim* s);
+
+// Compiled configurations a simulation created with patch 0 and/or levels 0
+// may take: the kernels of its scheme, wavelet, compute precision and
+// storage (and hi + lo where asked) whose P divides every axis and matches a
+// non-zero request.
+static std::vector<std::pair<int, int>> patch_candidates(const wcs_grid* g, int scheme, int patch, int levels,
+                                                         const wcs_opts* o) {
+  std::vector<std::pair<int, int>> c;
+  const int dims = (g->dims == 3 || scheme == WCS_D3Q19) ? 3 : 2;
+  auto fits = [&](int P, int L) {
+    if ((patch && P != patch) || (levels && L != levels)) return false;
+    for (int a = 0; a < dims; ++a)
+      if (g->n[a] <= 0 || g->n[a] % P) return false;
+    return std::find(c.begin(), c.end(), std::make_pair(P, L)) == c.end();
+  };
+  if (dims == 3) {
+    if (scheme != WCS_D3Q19 || o->wavelet != WCS_BL53 || o->compute != WCS_FP32) return c;
+    for (const Kernel3Entry& k : kernels3())
+      if (k.store == o->detail_store && fits(k.P, k.L)) c.emplace_back(k.P, k.L);
+  } else {
+    for (const KernelEntry& k : kernels())
+      if (k.scheme == scheme && k.wavelet == o->wavelet && k.prec == o->compute && k.store == o->detail_store &&
+          (!o->coarse_hilo || k.hilo) && fits(k.P, k.L))
+        c.emplace_back(k.P, k.L);
+  }
+  return c;
+}
+
+static wcs_status create_deferred(const wcs_grid* grid, int scheme, int patch, int levels, double eps,
+                                  const wcs_opts* opts, wcs_sim** out) {
+  if (patch < 0 || levels < 0) return fail(nullptr, WCS_E_ARG, "patch and levels must be >= 0");
+  if (patch_candidates(grid, scheme, patch, levels, opts).empty())
+    return fail(nullptr, WCS_E_UNSUPPORTED, "no compiled kernel of this configuration fits the grid");
+  wcs_sim* s = new wcs_sim();
+  cudaGetDevice(&s->device);
+  s->deferred = true;
+  s->g0 = *grid;
+  s->o0 = *opts;
+  s->req_P = patch;
+  s->req_L = levels;
+  s->scheme = scheme;
+  s->wavelet = opts->wavelet;
+  s->prec = opts->compute;
+  s->store = opts->detail_store;
+  s->rule = opts->rule;
+  s->eps = eps;
+  s->dims = (grid->dims == 3 || scheme == WCS_D3Q19) ? 3 : 2;
+  s->F = s->dims == 3 ? 19 : wcs::scheme_fields(scheme);
+  s->stream = static_cast<cudaStream_t>(opts->cuda_stream);
+  for (int a = 0; a < s->dims; ++a) {
+    s->n[a] = grid->n[a];
+    s->per[a] = s->dims == 3 ? 1 : int((grid->periodic_mask >> a) & 1u);
+    s->G[a] = (s->dims == 2 && wcs::wv_nodal(s->wavelet) && !s->per[a]) ? s->n[a] + 1 : s->n[a];
+  }
+  *out = s;
+  return WCS_OK;
+}
+
+// The deferred choice, on the caller's initial fields: the fastest candidate
+// (wcs_autotune, a few timed steps each) becomes the simulation.
+static wcs_status resolve_deferred(wcs_sim* s, const double* const* fields, int nfields, int src_is_device) {
+  const auto c = patch_candidates(&s->g0, s->scheme, s->req_P, s->req_L, &s->o0);
+  if (c.empty()) return fail(s, WCS_E_UNSUPPORTED, "no compiled kernel of this configuration fits the grid");
+  std::vector<int> Ps, Ls;
+  for (const auto& pl : c) {
+    Ps.push_back(pl.first);
+    Ls.push_back(pl.second);
+  }
+  int best = 0;
+  if (c.size() > 1) {
+    const wcs_status st = wcs_autotune(&s->g0, s->scheme, &s->o0, s->eps, Ps.data(), Ls.data(), int(c.size()), fields,
+                                       nfields, src_is_device, 3, &best, nullptr);
+    if (st != WCS_OK) return fail(s, st, "patch autotuner: " + g_create_err);
+  }
+  wcs_sim* t = nullptr;
+  const wcs_status st = wcs_create_sim(&s->g0, s->scheme, Ps[best], Ls[best], s->eps, &s->o0, &t);
+  if (st != WCS_OK) return fail(s, st, g_create_err);
+  std::swap(*s, *t);  // s is now the simulation, t the empty shell
+  wcs_destroy(t);
+  return WCS_OK;
+}
 
 static wcs_status create3(const wcs_grid* grid, int scheme, int patch, int levels, double eps, const wcs_opts* opts,
                           wcs_sim** out) {
@@ -608,6 +695,7 @@ wcs_status wcs_create_sim(const wcs_grid* grid, int scheme, int patch, int level
   if (!grid || !opts || !out) return fail(nullptr, WCS_E_ARG, "null argument");
   *out = nullptr;
   if (!(eps >= 0)) return fail(nullptr, WCS_E_ARG, "eps must be >= 0");
+  if (patch == 0 || levels == 0) return create_deferred(grid, scheme, patch, levels, eps, opts, out);
   if (grid->dims == 3 || scheme == WCS_D3Q19) return create3(grid, scheme, patch, levels, eps, opts, out);
   if (grid->dims != 2) return fail(nullptr, WCS_E_UNSUPPORTED, "grids are 2-D or 3-D");
   if (!(eps >= 0)) return fail(nullptr, WCS_E_ARG, "eps must be >= 0");
@@ -820,6 +908,13 @@ wcs_status wcs_shape(const wcs_sim* s, int64_t* npatch, int* nfields, int64_t* n
   return WCS_OK;
 }
 
+wcs_status wcs_patch_config(const wcs_sim* s, int* patch, int* levels) {
+  if (!s) return WCS_E_ARG;
+  if (patch) *patch = s->P;
+  if (levels) *levels = s->L;
+  return WCS_OK;
+}
+
 wcs_status wcs_shape3(const wcs_sim* s, int64_t* npatch, int* nfields, int64_t* nodes) {
   if (!s) return WCS_E_ARG;
   if (npatch) *npatch = s->npatch;
@@ -831,6 +926,10 @@ wcs_status wcs_shape3(const wcs_sim* s, int64_t* npatch, int* nfields, int64_t* 
 
 wcs_status wcs_init_macro(wcs_sim* s, const double* const* fields, int nfields, int src_is_device) {
   if (!s || !fields) return WCS_E_ARG;
+  if (s->deferred) {
+    const wcs_status st = resolve_deferred(s, fields, nfields, src_is_device);
+    if (st != WCS_OK) return st;
+  }
   if (s->dims == 3) {
     const wcs_status st = init3(s, fields, nfields, src_is_device);
     return st != WCS_OK ? st : wcs_sync(s);
@@ -1059,6 +1158,7 @@ extern "C" {
 
 wcs_status wcs_import_field(wcs_sim* s, int field, const void* src, int src_is_device, int dtype) {
   if (!s || !src || field < -1 || field >= s->F || (dtype != 0 && dtype != 1)) return WCS_E_ARG;
+  if (s->deferred) return fail(s, WCS_E_ARG, "a simulation created with patch or levels 0 starts from wcs_init_macro");
   if (!s->inited && field >= 0) return fail(s, WCS_E_ARG, "import of one field before the state exists");
   if (s->inited) {
     const wcs_status st = wcs_sync(s);
@@ -1159,6 +1259,7 @@ static void fill_stats(const wcs_sim* s, const wcs::Ctl& c, const double* ps, in
 wcs_status wcs_stats(wcs_sim* s, wcs_step_stats* o) {
   if (!s || !o) return WCS_E_ARG;
   std::memset(o, 0, sizeof(*o));
+  if (s->deferred) return fail(s, WCS_E_ARG, "no state before wcs_init_macro");
   if (s->inited) (void)wcs_sync(s);  // re-runs a step lost to an arena overflow; errors stay in the status
   CK(cudaStreamSynchronize(s->stream));
   wcs::Ctl c;
@@ -1604,8 +1705,7 @@ wcs_status wcs_autotune(const wcs_grid* grid, int scheme, const wcs_opts* opts, 
                         int ncand, const double* const* fields, int nfields, int src_is_device, int steps, int* best,
                         double* ms_per_step) {
   if (!grid || !opts || !P || !L || ncand <= 0 || !best || steps <= 0) return WCS_E_ARG;
-  if (grid->dims != 2 || scheme == WCS_D3Q19) return WCS_E_UNSUPPORTED;
-  typedef std::tuple<int64_t, int64_t, unsigned, int, int, int, int, int, double, std::vector<int>> Key;
+  typedef std::tuple<int64_t, int64_t, int64_t, unsigned, int, int, int, int, int, int, double, std::vector<int>> Key;
   static std::map<Key, std::pair<int, std::vector<double>>> cache;
   static std::mutex mu;
   std::vector<int> cand;
@@ -1613,8 +1713,8 @@ wcs_status wcs_autotune(const wcs_grid* grid, int scheme, const wcs_opts* opts, 
     cand.push_back(P[i]);
     cand.push_back(L[i]);
   }
-  const Key key(grid->n[0], grid->n[1], grid->periodic_mask, scheme, opts->wavelet, opts->compute, opts->detail_store,
-                opts->rule, eps, cand);
+  const Key key(grid->n[0], grid->n[1], grid->dims == 3 ? grid->n[2] : 1, grid->periodic_mask, scheme, opts->wavelet,
+                opts->compute, opts->detail_store, opts->rule, opts->coarse_hilo, eps, cand);
   {
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(key);

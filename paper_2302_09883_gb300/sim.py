@@ -87,6 +87,21 @@ class Sim:
     def init_macro(self, fields):
         keep, arr, dev = _field_ptrs(fields)
         B.check(B.lib().wcs_init_macro(self.h, arr, len(fields), dev), self.h)
+        if not (self.P and self.L):  # P or L 0: the autotuner chose them in the init
+            self._refresh_shape()
+
+    def _refresh_shape(self):
+        P, L = C.c_int(), C.c_int()
+        B.check(B.lib().wcs_patch_config(self.h, C.byref(P), C.byref(L)), self.h)
+        self.P, self.L = P.value, L.value
+        npatch, nf = C.c_int64(), C.c_int()
+        B.lib().wcs_shape(self.h, C.byref(npatch), C.byref(nf), None, None)
+        self.npatch = npatch.value
+
+    def patch_config(self):
+        """(P, L) of the simulation (0 before the init when left to the
+        autotuner)."""
+        return self.P, self.L
 
     def step(self, n=1):
         B.check(B.lib().wcs_step(self.h, n), self.h)

@@ -68,6 +68,9 @@ def _create(L, g, scheme, P, Lv, eps, o):
     ("d3q19_fp64", 7, "FP32"),
     ("d3q19_no_kernel", 7, "no compiled 3-D kernel"),
     ("d3q19_on_2d_grid", 1, "D3Q19"),
+    ("deferred_no_fit", 7, "fits the grid"),
+    ("deferred_negative", 1, ">= 0"),
+    ("hilo_fp64", 7, "hi + lo"),
 ])
 def test_create_rejects_bad_arguments_without_a_gpu(L, case, want, msg):
     g2 = _grid(2, (256, 256, 1), 3)
@@ -94,11 +97,36 @@ def test_create_rejects_bad_arguments_without_a_gpu(L, case, want, msg):
         r = _create(L, g3, "d3q19", 32, 3, 1e-3, _opts(store="f64", prec="f64"))
     elif case == "d3q19_no_kernel":
         r = _create(L, g3, "d3q19", 32, 2, 1e-3, _opts())
+    elif case == "deferred_no_fit":  # 80 cells: no compiled P (32, 64) divides them
+        r = _create(L, _grid(2, (80, 80, 1), 3), "d2q9", 0, 0, 1e-3, _opts())
+    elif case == "deferred_negative":
+        r = _create(L, g2, "d2q9", 0, -1, 1e-3, _opts())
+    elif case == "hilo_fp64":
+        o = _opts(store="f64", prec="f64")
+        o.coarse_hilo = 1
+        r = _create(L, _grid(2, (128, 128, 1), 3), "d2q9", 32, 3, 1e-3, o)
     else:
         r = _create(L, g2, "d3q19", 32, 3, 1e-3, _opts())
     st, h, text = r
     assert st == want and not h.value
     assert msg in text
+
+
+def test_deferred_patch_choice_waits_for_the_init(L):
+    """patch = levels = 0: the handle exists, nothing is chosen or allocated
+    before wcs_init_macro, and calls that need a state are refused."""
+    st, h, _ = _create(L, _grid(2, (256, 256, 1), 3), "d2q9", 0, 0, 1e-3, _opts())
+    assert st == 0 and h.value
+    P, Lv = C.c_int(-1), C.c_int(-1)
+    assert L.wcs_patch_config(h, C.byref(P), C.byref(Lv)) == 0 and (P.value, Lv.value) == (0, 0)
+    npatch, nf, gx, gy = C.c_int64(-1), C.c_int(), C.c_int64(), C.c_int64()
+    assert L.wcs_shape(h, C.byref(npatch), C.byref(nf), C.byref(gx), C.byref(gy)) == 0
+    assert (npatch.value, nf.value, gx.value, gy.value) == (0, 9, 256, 256)
+    assert L.wcs_step(h, 1) == 1 and "init" in L.wcs_last_error(h).decode()
+    stats = B.StepStats()
+    assert L.wcs_stats(h, C.byref(stats)) == 1
+    assert L.wcs_compressed_bytes(h) == -1
+    L.wcs_destroy(h)
 
 
 def test_null_arguments_are_rejected(L):
