@@ -137,3 +137,22 @@ def test_hilo_d3q19_bitwise_and_check_a():
         assert np.all(np.abs(st["field_sum"] + st["field_sum_lo"] - h["pre_sums"]) <= 1e-12 * scale), k
         worst_hi = max(worst_hi, float(np.max(np.abs(st["field_sum"] - h["pre_sums"]) / scale)))
     assert worst_hi > 1e-12
+
+
+def test_hilo_stats_paths_and_what_does_not_take_it():
+    """The queued statistics carry the lo sums like wcs_stats; batches and the
+    learned threshold have no hi + lo kernel and say so."""
+    from paper_2302_09883_gb300 import Batch, learned
+    n = 128
+    g = Sim("d2q9", "bl53", n, n, 32, 3, 1e-4, prec="f32", store="bf16", tau=0.6, coarse_hilo=True)
+    g.init_macro(inputs.shear_wave(n, seed=5))
+    g.step(2)
+    g.stats_enqueue(1)
+    q = g.stats_collect(1)
+    st = g.stats()
+    assert np.array_equal(q["field_sum_lo"], st["field_sum_lo"]) and np.any(st["field_sum_lo"] != 0.0)
+    assert np.array_equal(q["field_sum"], st["field_sum"])
+    with pytest.raises(RuntimeError):
+        Batch([g])
+    with pytest.raises(RuntimeError):
+        learned.use_mlp(g, learned.Mlp(18, seed=0))
