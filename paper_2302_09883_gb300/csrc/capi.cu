@@ -403,6 +403,14 @@ static std::vector<std::pair<int, int>> patch_candidates(const wcs_grid* g, int 
 static wcs_status create_deferred(const wcs_grid* grid, int scheme, int patch, int levels, double eps,
                                   const wcs_opts* opts, wcs_sim** out) {
   if (patch < 0 || levels < 0) return fail(nullptr, WCS_E_ARG, "patch and levels must be >= 0");
+  // what the creation in wcs_init_macro would refuse whatever (P, L) it takes
+  const bool three = grid->dims == 3 || scheme == WCS_D3Q19;
+  if (three && (grid->dims != 3 || scheme != WCS_D3Q19))
+    return fail(nullptr, WCS_E_ARG, "3-D grids take the D3Q19 scheme");
+  if (!three && grid->dims != 2) return fail(nullptr, WCS_E_UNSUPPORTED, "grids are 2-D or 3-D");
+  if (opts->rule < 0 || opts->rule > 2) return fail(nullptr, WCS_E_ARG, "bad threshold rule");
+  if ((three && (grid->periodic_mask & 7u) != 7u) || (scheme == WCS_D2Q9 && (grid->periodic_mask & 3u) != 3u))
+    return fail(nullptr, WCS_E_ARG, "lattice Boltzmann schemes need periodic axes");
   if (patch_candidates(grid, scheme, patch, levels, opts).empty())
     return fail(nullptr, WCS_E_UNSUPPORTED, "no compiled kernel of this configuration fits the grid");
   wcs_sim* s = new wcs_sim();

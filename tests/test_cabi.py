@@ -71,6 +71,8 @@ def _create(L, g, scheme, P, Lv, eps, o):
     ("deferred_no_fit", 7, "fits the grid"),
     ("deferred_negative", 1, ">= 0"),
     ("hilo_fp64", 7, "hi + lo"),
+    ("deferred_outflow_d2q9", 1, "periodic"),
+    ("deferred_bad_rule", 1, "rule"),
 ])
 def test_create_rejects_bad_arguments_without_a_gpu(L, case, want, msg):
     g2 = _grid(2, (256, 256, 1), 3)
@@ -101,6 +103,12 @@ def test_create_rejects_bad_arguments_without_a_gpu(L, case, want, msg):
         r = _create(L, _grid(2, (80, 80, 1), 3), "d2q9", 0, 0, 1e-3, _opts())
     elif case == "deferred_negative":
         r = _create(L, g2, "d2q9", 0, -1, 1e-3, _opts())
+    elif case == "deferred_outflow_d2q9":
+        r = _create(L, _grid(2, (256, 256, 1), 1), "d2q9", 0, 0, 1e-3, _opts())
+    elif case == "deferred_bad_rule":
+        o = _opts()
+        o.rule = 7
+        r = _create(L, g2, "d2q9", 0, 4, 1e-3, o)
     elif case == "hilo_fp64":
         o = _opts(store="f64", prec="f64")
         o.coarse_hilo = 1
