@@ -106,6 +106,7 @@ def lib():
         L.orc3_set_patch_eps.argtypes = [vp, dp]
         L.orc3_track_features.argtypes = [vp, i32]
         L.orc3_set_hilo.argtypes = [vp, i32]
+        L.orc3_step_patch.argtypes = [i32, i32, i32, i32, dbl, dbl, i64, dp, C.c_char_p, i64, C.POINTER(i64)]
         L.orc3_coarse_lo.argtypes = [vp, C.POINTER(C.c_float)]
         L.orc3_hilo_sums.argtypes = [vp, dp]
         L.orc3_features.argtypes = [vp, dp]
@@ -503,6 +504,20 @@ class OracleSim3(_Run3):
         return {"coef_sums": out[:19].copy(), "nstep": int(out[20]), "shared_mismatch": int(out[22]),
                 "compressed_bytes": int(out[23]), "coef_abs_sums": out[24:43].copy(),
                 "n_terms": self.npatch * ((self.P >> self.L) + 1) ** 3}
+
+
+def d3q19_patch_step(block, P, L, eps, tau, store="bf16", rule="const", pid=0):
+    """One FP32 D3Q19 step of a single patch: block (19, P+3, P+3, P+3) is
+    the decoded state on the patch's nodes and the layer around them
+    ([f][z][y][x], index 0 = node -1); returns the record (bytes) that
+    OracleSim3 would write for patch pid."""
+    b = np.ascontiguousarray(block, np.float64)
+    assert b.shape == (19, P + 3, P + 3, P + 3)
+    cap = 64 * 19 * (P + 1) ** 3 + 4096
+    buf = C.create_string_buffer(cap)
+    nb = C.c_int64()
+    _check(lib().orc3_step_patch(STORE[store], RULE[rule], P, L, eps, tau, pid, _dp(b), buf, cap, C.byref(nb)))
+    return buf.raw[:nb.value]
 
 
 class OracleRef3(_Run3):

@@ -707,6 +707,18 @@ int orc3_hilo_sums(void* p, double* out) {
   });
 }
 
+// One FP32 D3Q19 patch step from its decoded surroundings (d3q19_patch_step):
+// the record goes to out (cap bytes), its size to *nbytes.
+int orc3_step_patch(int store, int rule, int P, int L, double eps, double tau, int64_t pid, const double* blk,
+                    uint8_t* out, int64_t cap, int64_t* nbytes) {
+  return guard([&] {
+    const std::vector<uint8_t> r = d3q19_patch_step<float>(store, rule, P, L, eps, tau, uint32_t(pid), blk);
+    *nbytes = int64_t(r.size());
+    if (cap < int64_t(r.size())) throw std::runtime_error("record buffer too small");
+    std::memcpy(out, r.data(), r.size());
+  });
+}
+
 int orc3_track_features(void* p, int on) {
   Handle3* h = static_cast<Handle3*>(p);
   if (h->s64) h->s64->track_feat = on != 0;

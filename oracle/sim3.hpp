@@ -287,6 +287,40 @@ template <class T> struct Sim3 {
   }
 };
 
+// One step of a single D3Q19 patch from the decoded state around it, the
+// arithmetic of Sim3::step restricted to that patch: blk holds the 19 fields
+// (field-major) on the (E+2)^3 nodes x, y, z in [-1, E] around the patch, x
+// fastest; every node is collided, the patch's E^3 nodes pull their
+// populations, and the patch is encoded as Sim3 encodes patch pid.  Lets a
+// test check sampled records of a grid too large for a whole oracle run.
+template <class T>
+std::vector<uint8_t> d3q19_patch_step(int store, int rule, int64_t P, int L, double eps, double tau, uint32_t pid,
+                                      const double* blk) {
+  const int64_t E = P + 1, EG = E + 2, ng = EG * EG * EG;
+  const T omega = T(1.0 / tau);
+  std::vector<std::vector<T>> C(19, std::vector<T>(ng));
+  for (int i = 0; i < 19; ++i)
+    for (int64_t k = 0; k < ng; ++k) C[i][k] = T(blk[i * ng + k]);
+  for (int64_t k = 0; k < ng; ++k) {
+    T f[19];
+    for (int i = 0; i < 19; ++i) f[i] = C[i][k];
+    d3q19_collide<T>(f, omega);
+    for (int i = 0; i < 19; ++i) C[i][k] = f[i];
+  }
+  std::vector<std::vector<T>> loc(19, std::vector<T>(E * E * E));
+  for (int i = 0; i < 19; ++i)
+    for (int64_t z = 0; z < E; ++z)
+      for (int64_t y = 0; y < E; ++y)
+        for (int64_t x = 0; x < E; ++x)
+          loc[i][(z * E + y) * E + x] =
+              C[i][((z + 1 - D3Q19_C[i][2]) * EG + (y + 1 - D3Q19_C[i][1])) * EG + (x + 1 - D3Q19_C[i][0])];
+  for (int f = 0; f < 19; ++f) fwd_nd<T>(BL53, loc[f].data(), 3, P, L);
+  const Layout lay(BL53, 3, P, L);
+  const std::vector<double> ef(19, eps);
+  const uint32_t flags = uint32_t(store) | (uint32_t(BL53) << 8) | (sizeof(T) == 8 ? (1u << 16) : 0u);
+  return encode_patch<T>(lay, loc, store, rule, ef, eps, pid, flags);
+}
+
 // Uncompressed D3Q19 run on the global arrays.
 template <class T> struct Ref3 {
   T omega = T(1);

@@ -1,8 +1,10 @@
 """Parity at the full sizes of the benchmarked workloads, in the launch
 configurations the bench times: the FP32 oracle runs the same full grid
 (D2Q9 2048^2, Euler 4096^2, sampled grids of the 96-grid batch, D3Q19
-128^3) and every record must be byte-identical; at 1024^3 (too large for the
-oracle) the D3Q19 run is checked by properties that hold at any size."""
+128^3) and every record must be byte-identical; at 1024^3 (too large for a
+whole oracle run) the oracle steps sampled D3Q19 patches one by one from the
+GPU's decoded state around them, and the run is also checked by properties
+that hold at any size."""
 import numpy as np
 import pytest
 
@@ -92,6 +94,36 @@ def test_d3q19_128_records_match_the_oracle():
     o.step(2)
     g.sync()
     _records_equal(g, o)
+
+
+def test_d3q19_1024_sampled_records_match_the_oracle():
+    # config 5's grid and eps, automatic arenas as the bench: the oracle steps
+    # four patches (a corner, the last, the middle, one more) from the state
+    # the GPU decoded after one step, and the GPU's records of the second
+    # step must equal its records byte for byte
+    import torch
+    n, P, L, eps, tau = 1024, 32, 3, 1e-7, 0.55
+    g = Sim3(n, n, n, P, L, eps, store="bf16", tau=tau)
+    g.init_macro(inputs.taylor_green_3d_device(n))
+    g.step(1)
+    npp = n // P
+    sample = [0, 5 + npp * (7 + npp * 3), npp ** 3 - 1, (npp // 2) * (1 + npp + npp * npp)]
+    pos = [(pid % npp, (pid // npp) % npp, pid // (npp * npp)) for pid in sample]
+    idx = [[torch.tensor((p[a] * P + np.arange(-1, P + 2)) % n, device="cuda") for a in (2, 1, 0)] for p in pos]
+    blocks = np.zeros((len(sample), 19, P + 3, P + 3, P + 3))
+    buf = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    for i in range(19):
+        g.export_field(i, out=buf, dtype=np.float32)
+        for k in range(len(sample)):
+            iz, iy, ix = idx[k]
+            blocks[k, i] = buf.index_select(0, iz).index_select(1, iy).index_select(2, ix).double().cpu().numpy()
+    del buf
+    g.step(1)
+    g.sync()
+    for k, pid in enumerate(sample):
+        assert g.record(pid) == O.d3q19_patch_step(blocks[k], P, L, eps, tau, store="bf16", pid=pid), pid
+    g.close()
+    torch.cuda.empty_cache()
 
 
 def test_d3q19_1024_properties():

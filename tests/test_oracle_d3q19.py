@@ -154,3 +154,31 @@ def test_compressed_mass_is_conserved_fp64():
     assert st["shared_mismatch"] == 0
     # and the compression does compress
     assert st["compressed_bytes"] < 0.5 * 19 * 8 * n ** 3
+
+
+def patch_block(state, p, P):
+    """The decoded state on patch p's nodes and the layer around them,
+    (19, P+3, P+3, P+3), periodic wrap; p = (px, py, pz)."""
+    n = state.shape[1:]
+    idx = [(p[a] * P + np.arange(-1, P + 2)) % n[2 - a] for a in range(3)]
+    return state[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+
+
+def test_single_patch_step_equals_the_whole_grid_step():
+    """d3q19_patch_step (one patch from its decoded surroundings) writes the
+    record the whole-grid oracle step writes for that patch: 64^3, P 32,
+    L 3, BF16, every patch, after a step of a vortex with a perturbation."""
+    n, P, L, eps, tau = 64, 32, 3, 1e-6, 0.55
+    s = O.OracleSim3("bl53", n, n, n, P, L, eps, prec="f32", store="bf16", tau=tau)
+    f = inputs.taylor_green_3d(n)
+    rng = np.random.default_rng(2)
+    f[1] = f[1] + 1e-4 * rng.standard_normal(f[1].shape)
+    s.init_macro(f)
+    s.step(1)
+    state = s.export_all()
+    s.step(1)
+    npp = n // P
+    for pid in range(npp ** 3):
+        p = (pid % npp, (pid // npp) % npp, pid // (npp * npp))
+        rec = O.d3q19_patch_step(patch_block(state, p, P), P, L, eps, tau, store="bf16", pid=pid)
+        assert rec == s.record(pid), pid
