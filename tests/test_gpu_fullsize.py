@@ -1,7 +1,8 @@
 """Parity at the full sizes of the benchmarked workloads, in the launch
 configurations the bench times: the FP32 oracle runs the same full grid
-(D2Q9 2048^2, Euler 4096^2, sampled grids of the 96-grid batch, D3Q19
-128^3) and every record must be byte-identical; at 1024^3 (too large for a
+(D2Q9 2048^2, Euler 4096^2 with int8 and BF16 details, transport 4096^2,
+sampled grids of the 96-grid batch, D3Q19 128^3) and every record must be
+byte-identical; at 1024^3 (too large for a
 whole oracle run) the oracle steps sampled D3Q19 patches one by one from the
 GPU's decoded state around them, and the run is also checked by properties
 that hold at any size."""
@@ -33,13 +34,31 @@ def test_d2q9_2048_records_match_the_oracle():
     assert O.sums_agree(g.stats()["field_sum"], o.stats())
 
 
-def test_euler_4096_records_match_the_oracle():
-    # four-quadrant Riemann problem, 4097^2 nodes, outflow, BF16 eps 1e-4, CFL 0.4
+@pytest.mark.parametrize("store", ["i8", "bf16"])
+def test_euler_4096_records_match_the_oracle(store):
+    # four-quadrant Riemann problem, 4097^2 nodes, outflow, eps 1e-4, CFL 0.4;
+    # int8 details (the benchmarked storage) and BF16
     f = inputs.four_quadrant(4096)
-    g = Sim("euler2d", "bl53", 4096, 4096, 64, 4, 1e-4, prec="f32", store="bf16", periodic=(False, False), cfl=0.4,
+    g = Sim("euler2d", "bl53", 4096, 4096, 64, 4, 1e-4, prec="f32", store=store, periodic=(False, False), cfl=0.4,
             arena_factor=0.35)
-    o = O.OracleSim("euler2d", "bl53", 4096, 4096, 64, 4, 1e-4, prec="f32", store="bf16", periodic=(False, False),
+    o = O.OracleSim("euler2d", "bl53", 4096, 4096, 64, 4, 1e-4, prec="f32", store=store, periodic=(False, False),
                     cfl=0.4)
+    g.init_macro(f)
+    o.init_macro(f)
+    g.step(2)
+    o.step(2)
+    g.sync()
+    _records_equal(g, o)
+    assert g.stats()["time"] == o.stats()["time"]
+
+
+def test_transport_4096_records_match_the_oracle():
+    # the timed transport configuration: 4097^2 nodes on [-1, 1]^2, outflow,
+    # velocity (0.9, 0.9), CFL 0.45, level 4, capped rule, c = 0.01
+    kw = dict(periodic=(False, False), cfl=0.45, velocity=(0.9, 0.9), length=2.0)
+    f = inputs.transport_gaussian(4096)
+    g = Sim("transport", "bl53", 4096, 4096, 64, 4, 0.01, prec="f32", store="f32", rule="capped", **kw)
+    o = O.OracleSim("transport", "bl53", 4096, 4096, 64, 4, 0.01, prec="f32", store="f32", rule="capped", **kw)
     g.init_macro(f)
     o.init_macro(f)
     g.step(2)
