@@ -1304,6 +1304,9 @@ def main():
             "rel_l2": {"u": head["rel_l2_u"], "rho": head["rel_l2_rho"], "pop_max": head["rel_l2_pop_max"],
                        "steps": qsteps},
             "uncompressed_mlups": lu * K / (dms * 1e-3) / 1e6,
+            # the dense step moves 72 B per update (9 populations read and written)
+            "uncompressed_hbm": {"gbs": 72.0 * lu * K / (dms * 1e-3) / 1e9, "peak": hbm_peak,
+                                 "frac": 72.0 * lu * K / (dms * 1e-3) / 1e9 / hbm_peak},
             "speed_vs_uncompressed": dms / ms,
             "warm_mlups": lu * K / (warm_ms * 1e-3) / 1e6,
             "sweep": sweep,
