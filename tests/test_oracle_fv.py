@@ -205,3 +205,22 @@ def test_sw_dam_break_converges_to_the_exact_riemann_solution():
         errs.append(np.mean(np.abs(hx - he)))
         assert np.allclose(r.export_field(2), 0.0, atol=1e-12)  # no transverse motion
     assert errs[2] < errs[1] < errs[0] and errs[2] < 0.02
+
+
+def test_fluxes_are_antisymmetric_bit_for_bit():
+    """Q(W_b, W_a, -N) = -Q(W_a, W_b, N) exactly, for the Rusanov flux and the
+    exact-Riemann Godunov flux: every operation in them is symmetric under
+    the swap of the sides and the sign of the normal.  Conservation of the
+    FV update rests on it (what leaves one cell enters its neighbour), and
+    the shallow-water kernel computes each interface flux once because of it."""
+    rng = np.random.default_rng(0)
+    for _ in range(1000):
+        hL, hR = rng.uniform(0.5, 2.0, 2)
+        uL, vL, uR, vR = rng.uniform(-1.0, 1.0, 4)
+        WL, WR = np.array([hL, hL * uL, hL * vL]), np.array([hR, hR * uR, hR * vR])
+        rL, rR, pL, pR = rng.uniform(0.1, 2.0, 4)
+        EL, ER = pL / 0.4 + 0.5 * rL * (uL * uL + vL * vL), pR / 0.4 + 0.5 * rR * (uR * uR + vR * vR)
+        QL, QR = np.array([rL, rL * uL, rL * vL, EL]), np.array([rR, rR * uR, rR * vR, ER])
+        for nx, ny in ((1, 0), (0, 1)):
+            assert np.array_equal(O.sw_flux(WL, WR, nx, ny), -O.sw_flux(WR, WL, -nx, -ny))
+            assert np.array_equal(O.rusanov(QL, QR, nx, ny), -O.rusanov(QR, QL, -nx, -ny))
