@@ -55,6 +55,7 @@ def lib():
         L.orc_record.argtypes = [vp, i64, C.c_char_p, i64]
         L.orc_stats.argtypes = [vp, dp]
         L.orc_set_hilo.argtypes = [vp, i32]
+        L.orc_count_ops.argtypes = [i32, i32, C.POINTER(i64)]
         L.orc_coarse_lo.argtypes = [vp, C.POINTER(C.c_float)]
         L.orc_hilo_sums.argtypes = [vp, dp]
         L.orc_ref_create.restype = vp
@@ -504,6 +505,15 @@ class OracleSim3(_Run3):
         return {"coef_sums": out[:19].copy(), "nstep": int(out[20]), "shared_mismatch": int(out[22]),
                 "compressed_bytes": int(out[23]), "coef_abs_sums": out[24:43].copy(),
                 "n_terms": self.npatch * ((self.P >> self.L) + 1) ** 3}
+
+
+def count_ops(P, L):
+    """Operations (+, -, *, / each one) the oracle executes for one 2-D BL5/3
+    patch of P+1 nodes per axis: (forward transform of one field, its inverse,
+    one D2Q9 collision of a node)."""
+    out = (C.c_int64 * 3)()
+    _check(lib().orc_count_ops(P, L, out))
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def d3q19_patch_step(block, P, L, eps, tau, store="bf16", rule="const", pid=0):

@@ -45,6 +45,21 @@ template <class S> void export3(S& s, double* dst) {
     for (size_t g = 0; g < n; ++g) dst[f * n + g] = double(U[f][g]);
 }
 
+// Operation counting: a number type whose +, -, * and / count one operation
+// each (a negation counts none, as a sign flip folds into the next
+// operation), to count what the oracle's lifting and collision execute.
+thread_local int64_t g_ops = 0;
+struct Counted {
+  double v = 0.0;
+  Counted() = default;
+  Counted(double x) : v(x) {}
+};
+inline Counted operator+(Counted a, Counted b) { ++g_ops; return Counted(a.v + b.v); }
+inline Counted operator-(Counted a, Counted b) { ++g_ops; return Counted(a.v - b.v); }
+inline Counted operator*(Counted a, Counted b) { ++g_ops; return Counted(a.v * b.v); }
+inline Counted operator/(Counted a, Counted b) { ++g_ops; return Counted(a.v / b.v); }
+inline Counted operator-(Counted a) { return Counted(-a.v); }
+
 template <class F> int guard(F&& f) {
   try {
     f();
@@ -295,6 +310,28 @@ int orc_hilo_sums(void* p, double* out) {
       out[24 + f] = b[f];
       out[48 + f] = c[f];
     }
+  });
+}
+
+// Operations the oracle executes for one 2-D BL5/3 patch of E = P+1 nodes
+// per axis: out[0] its forward transform (one field), out[1] its inverse,
+// out[2] one D2Q9 BGK collision of a node.
+int orc_count_ops(int P, int L, int64_t* out) {
+  return guard([&] {
+    const int64_t E = int64_t(P) + 1;
+    std::vector<Counted> u(size_t(E * E));
+    for (int64_t i = 0; i < E * E; ++i) u[size_t(i)] = Counted(1.0 + 1e-3 * double(i % 7));
+    g_ops = 0;
+    fwd_nd<Counted>(BL53, u.data(), 2, P, L);
+    out[0] = g_ops;
+    g_ops = 0;
+    inv_nd<Counted>(BL53, u.data(), 2, P, L);
+    out[1] = g_ops;
+    Counted f[9];
+    for (int i = 0; i < 9; ++i) f[i] = Counted(0.1 + 0.01 * i);
+    g_ops = 0;
+    d2q9_collide<Counted>(f, Counted(1.0 / 0.6));
+    out[2] = g_ops;
   });
 }
 

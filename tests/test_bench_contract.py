@@ -86,3 +86,20 @@ def test_roofline_bytes_count_the_ghost_sources_of_each_kernel():
     # kernels with a ghost ring (Haar): the ring of 12 (P+1) + 4 FP32 values read and written per patch
     ring = bench.roofline_bytes(_FakeSim(), {"scheme": "d2q9", "wavelet": "haar", "P": 64})
     assert ring["compulsory"] == ring["with_l2_reuse"] == 2 * 1343488 + 2 * 1024 * (12 * 65 + 4) * 4 + tables_sums
+
+
+@pytest.mark.parametrize("P,L", [(64, 4), (32, 3)])
+def test_roofline_numerator_is_the_oracles_operation_count(P, L):
+    """The ALU roofline's numerator (algorithmic FP32 operations per lattice
+    update) against what the oracle executes, counted by a number type whose
+    +, -, * and / count one each: a forward and an inverse 2-D transform per
+    field, one BGK collision per node; the threshold's |d| and compare per
+    coefficient are the formula's own (two per coefficient)."""
+    import bench
+    import oracle as O
+    fwd, inv, coll = O.count_ops(P, L)
+    assert coll == 135
+    assert fwd == inv == 2 * (P + 1) * bench.lifting_flops_per_line(P, L)
+    E, F = P + 1, 9
+    want = F * (fwd + inv) / (P * P) + coll + 2 * F * E * E / (P * P)
+    assert abs(bench.algorithmic_flops_per_lu(P, L) - want) < 1e-9
