@@ -142,7 +142,9 @@ typedef struct {
   double momentum[3];        /* D2Q9: sum c_i f_i; EULER2D: rho u, rho v;
                                 SWE: h u, h v */
   double energy;             /* EULER2D: E */
-  double smax;               /* EULER2D: largest signal speed of the state */
+  double smax;               /* EULER2D, SWE: largest signal speed of the
+                                state (0 with a fixed step, cfl < 0, on
+                                BL5/3, where no step needs it) */
   int64_t live_bytes;        /* bytes of the records of the current state */
   int64_t resident_bytes;    /* every device byte the simulation holds */
   int64_t uncompressed_bytes;/* one uncompressed copy of the state */

@@ -2029,6 +2029,11 @@ __device__ __forceinline__ void patch_body(const PatchArgs& a, const int pid) {
   // ring-free Euler and shallow-water kernels still need its largest
   // signal speed)
   if constexpr (!C::REDECODE) return;
+  // A fixed step (cfl < 0) needs no signal speed, and a ring-free patch
+  // exports no ring: then nothing is decoded again.
+  if constexpr (RF) {
+    if (a.cfl <= 0) return;
+  }
   __syncthreads();
   for (int t = tid; t < F * E; t += NT) {
     const int f = t / E, x = t - f * E;
